@@ -1,0 +1,217 @@
+"""Pins for the oracle's semi-discrete right-hand side (Eq. dg-strong-explicit
+with the upwind flux of Eq. max2d-numflux) and its whole-solver behaviour."""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import cavity_mode, jittered_delaunay_mesh, random_fields, relabel_mesh, square_grid_mesh
+
+
+@pytest.fixture(scope="module")
+def jit4():
+    VX, VY, EToV = jittered_delaunay_mesh(4, seed=5)
+    return VX, VY, EToV
+
+
+def test_constant_magnetic_field_is_steady(jit4):
+    # rhs(Hx = c1, Hy = c2, Ez = 0) = 0: no derivative, no jump, PEC sees Ez = 0
+    d = O.Discretization(*jit4, N=3)
+    q = np.zeros((3, d.K, d.Np))
+    q[0] = 0.7
+    q[1] = -1.3
+    rhs = O.maxwell_rhs(d, q)
+    assert np.abs(rhs).max() < 1e-11
+
+
+@pytest.mark.parametrize("N", [1, 2, 4, 6])
+def test_volume_part_is_exact_for_polynomials(N, jit4):
+    d = O.Discretization(*jit4, N=N)
+    x, y = d.x, d.y
+    p = N
+    # global polynomials of total degree <= N
+    Hx = x ** p + 0.5 * y
+    Hy = x * y ** (p - 1) if p >= 1 else x
+    Ez = (x + 2 * y) ** p
+    q = np.stack([Hx, Hy, Ez])
+    rhs = O.maxwell_rhs(d, q, flux=False)
+    dEz_dx = p * (x + 2 * y) ** (p - 1)
+    dEz_dy = 2 * p * (x + 2 * y) ** (p - 1)
+    dHy_dx = y ** (p - 1)
+    dHx_dy = 0.5 * np.ones_like(y)
+    tol = 1e-13 * d.Np * np.abs(d.rx).max() * np.abs(q).max()
+    assert np.abs(rhs[0] + dEz_dy).max() < tol
+    assert np.abs(rhs[1] - dEz_dx).max() < tol
+    assert np.abs(rhs[2] - (dHy_dx - dHx_dy)).max() < tol
+
+
+@pytest.mark.parametrize("N", [4, 5])
+def test_full_rhs_exact_for_continuous_polynomial_with_pec_zero(N):
+    # Ez vanishes on the walls of [-1,1]^2 and all fields are continuous
+    # polynomials of degree <= N: every jump and PEC term is zero, so the full
+    # right-hand side equals the exact derivatives.
+    VX, VY, EToV = square_grid_mesh(3, 3)
+    d = O.Discretization(VX, VY, EToV, N)
+    x, y = d.x, d.y
+    Ez = (1 - x ** 2) * (1 - y ** 2)
+    Hx = x * y ** 2
+    Hy = x ** 3 - y
+    rhs = O.maxwell_rhs(d, np.stack([Hx, Hy, Ez]))
+    assert np.abs(rhs[0] - (-(1 - x ** 2) * (-2 * y))).max() < 1e-11
+    assert np.abs(rhs[1] - (-2 * x * (1 - y ** 2))).max() < 1e-11
+    assert np.abs(rhs[2] - (3 * x ** 2 - 2 * x * y)).max() < 1e-11
+
+
+def _operator_matrix(d, alpha):
+    n = 3 * d.K * d.Np
+    A = np.empty((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = O.maxwell_rhs(d, e.reshape(3, d.K, d.Np), alpha=alpha).reshape(-1)
+    return A
+
+
+def _energy_weight(d):
+    W = np.zeros((3 * d.K * d.Np,) * 2)
+    for f in range(3):
+        for k in range(d.K):
+            i0 = (f * d.K + k) * d.Np
+            W[i0:i0 + d.Np, i0:i0 + d.Np] = d.J[k, 0] * d.ref.M
+    return W
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_brute_force_operator_spectrum(N):
+    # K = 2 (one square) and K = 8: upwind operator has no growing mode;
+    # central flux (alpha = 0) makes the energy-weighted operator skew
+    for nsq in (1, 2):
+        VX, VY, EToV = square_grid_mesh(nsq, nsq)
+        d = O.Discretization(VX, VY, EToV, N)
+        W = _energy_weight(d)
+        A1 = _operator_matrix(d, 1.0)
+        assert np.linalg.eigvals(A1).real.max() < 1e-10
+        S1 = W @ A1
+        assert np.linalg.eigvalsh(S1 + S1.T).max() < 1e-10  # dissipative
+        A0 = _operator_matrix(d, 0.0)
+        S0 = W @ A0
+        assert np.abs(S0 + S0.T).max() < 1e-11 * np.abs(S0).max()
+
+
+def test_energy_rate_signs(jit4):
+    d = O.Discretization(*jit4, N=4)
+    q = random_fields(d.K, d.Np, seed=9)
+    assert O.energy_rate(d, q, O.maxwell_rhs(d, q, alpha=1.0)) < 0
+    r0 = O.energy_rate(d, q, O.maxwell_rhs(d, q, alpha=0.0))
+    assert abs(r0) < 1e-11 * O.energy(d, q) * np.abs(d.rx).max()
+
+
+def test_upwind_flux_matches_1d_riemann_solution():
+    # Along the normal the TM system reduces to Ez_t + (Ht)_xi = 0,
+    # Ht_t + (Ez)_xi = 0 for Ht = ny Hx - nx Hy; its upwind (Godunov) flux gives
+    # n.(F - F*)_Ez = ([Ht] - [Ez]) / 2 and the tangential H component
+    # ([Ez] - [Ht]) / 2; the normal H component has no flux.  Check the oracle
+    # on a two-element mesh with piecewise-constant states.
+    VX = np.array([0.0, 1.0, 0.0, 1.0])
+    VY = np.array([0.0, 0.0, 1.0, 1.0])
+    EToV = np.array([[0, 1, 3], [0, 3, 2]])
+    d = O.Discretization(VX, VY, EToV, 1)
+    rng = np.random.default_rng(0)
+    sM, sP = rng.normal(size=3), rng.normal(size=3)
+    q = np.zeros((3, 2, d.Np))
+    q[:, 0, :] = sM[:, None]
+    q[:, 1, :] = sP[:, None]
+    f = int(np.nonzero(d.EToE[0] == 1)[0][0])
+    sl = slice(f * d.Nfp, (f + 1) * d.Nfp)
+    nx, ny = d.nx[0, sl][0], d.ny[0, sl][0]
+    jump = sM - sP
+    jHt = ny * jump[0] - nx * jump[1]
+    fEz = (jHt - jump[2]) / 2
+    ft = (jump[2] - jHt) / 2  # coefficient along t = (ny, -nx)
+    expect = np.array([ft * ny, -ft * nx, fEz])
+    # isolate the shared face: the volume and PEC-face parts of element 0 do
+    # not depend on element 1, and a zero jump gives zero flux, so
+    # rhs0(sM, sP) - rhs0(sM, sM) = LIFT_f (Fscale flux) / 2.  With
+    # M LIFT_f = E_f and 1^T (1D face mass) 1 = 2, summing M * difference
+    # over the face rows gives 2 Fscale (flux / 2), flux / 2 being n.(F - F*).
+    q_same = q.copy()
+    q_same[:, 1, :] = sM[:, None]
+    diff = O.maxwell_rhs(d, q)[:, 0, :] - O.maxwell_rhs(d, q_same)[:, 0, :]
+    R = d.ref
+    got = (diff @ R.M.T)[:, R.Fmask[f]].sum(axis=1) / (2 * d.Fscale[0, sl][0])
+    assert np.allclose(got, expect, atol=1e-12)
+
+
+def test_permutation_invariance():
+    # relabelling elements and rotating their vertex lists gives the same
+    # physical right-hand side at the same physical points
+    VX, VY, EToV = jittered_delaunay_mesh(4, seed=21)
+    N = 4
+    ref = O.ReferenceElement(N)
+    d1 = O.Discretization(VX, VY, EToV, N, ref=ref)
+    E2, perm, rot = relabel_mesh(EToV, seed=4)
+    d2 = O.Discretization(VX, VY, E2, N, ref=ref)
+
+    def fields(d):
+        return np.stack([np.sin(2 * d.x + d.y), np.cos(3 * d.y) * d.x, np.exp(d.x - d.y)])
+
+    r1 = O.maxwell_rhs(d1, fields(d1))
+    r2 = O.maxwell_rhs(d2, fields(d2))
+    for i in range(d2.K):
+        k = perm[i]
+        # match nodes of element k (mesh 1) to nodes of element i (mesh 2)
+        dd = (d1.x[k][:, None] - d2.x[i][None, :]) ** 2 + (d1.y[k][:, None] - d2.y[i][None, :]) ** 2
+        m = np.argmin(dd, axis=1)
+        assert dd[np.arange(d1.Np), m].max() < 1e-26
+        assert np.abs(r1[:, k, :] - r2[:, i, m]).max() < 1e-11 * np.abs(r1).max()
+
+
+def test_cavity_mode_config_one():
+    # [-1,1]^2, 8x8 squares x 2, N = 4, T = 1, CFL dt: recorded oracle error
+    # 1.53e-4 (max nodal); pin it against the exact PEC eigenmode.
+    VX, VY, EToV = square_grid_mesh(8, 8)
+    d = O.Discretization(VX, VY, EToV, 4)
+    q0 = np.stack(cavity_mode(d.x, d.y, 0.0))
+    qT, t = O.solve(d, q0, 1.0, O.cfl_dt(d))
+    assert abs(t - 1.0) < 1e-12
+    err = np.abs(qT - np.stack(cavity_mode(d.x, d.y, t))).max()
+    assert err < 2.0e-4
+
+
+def test_h_convergence_rate():
+    # L2 error of the cavity mode at T = 0.25 on 4x4, 8x8, 16x16 grids:
+    # rate ~ N + 1 (accept >= N + 0.5)
+    for N in (1, 2, 3, 4):
+        ref = O.ReferenceElement(N)
+        errs = []
+        for n in (4, 8, 16):
+            VX, VY, EToV = square_grid_mesh(n, n)
+            d = O.Discretization(VX, VY, EToV, N, ref=ref)
+            q0 = np.stack(cavity_mode(d.x, d.y, 0.0))
+            qT, t = O.solve(d, q0, 0.25, 0.5 * O.cfl_dt(d))
+            e = qT - np.stack(cavity_mode(d.x, d.y, t))
+            errs.append(np.sqrt(2 * O.energy(d, e)))
+        rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+        assert rates[-1] >= N + 0.5, (N, errs, rates)
+
+
+def test_energy_does_not_increase_under_lsrk():
+    VX, VY, EToV = jittered_delaunay_mesh(5, seed=8)
+    d = O.Discretization(VX, VY, EToV, 3)
+    q = random_fields(d.K, d.Np, seed=1)
+    dt = O.cfl_dt(d)
+    e_prev = O.energy(d, q)
+    for _ in range(20):
+        q = O.lsrk_step(d, q, 0.0, dt)
+        e = O.energy(d, q)
+        assert e <= e_prev * (1 + 1e-13)
+        e_prev = e
+
+
+def test_rhs_flops_formula_golden():
+    # per-element FLOPs of the chapter's rhs_flops count, stored in
+    # tests/golden/rhs_flops_per_element.txt
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "rhs_flops_per_element.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    for N, flops in rows:
+        assert O.rhs_flops(1, int(N)) == int(flops)
