@@ -1,0 +1,368 @@
+"""Benchmark: LSRK(5,4) time steps of the nodal DG TM-Maxwell solver.
+
+One step = five fused stage kernels (right-hand side + 2N-storage update)
+over the whole mesh.  Default workload: seeded jittered-grid Delaunay mesh of
+the unit square with n = 707 (K = 999,698 triangles), order N = 5 (Np = 21),
+FP32 fields, Gaussian pulse (width 0.05) at (0.5, 0.5).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs an
+independent replica of the workload on its own GPU (the solver does not
+shard); value = all ranks' element-stage updates / max over ranks of the
+timed region.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("DG element-stage updates/s and RHS GFLOP/s (% roofline) at N=5; "
+          "served solves/s + p99 latency")
+UNIT = "element-stage updates/s"
+
+# algorithmic HBM bytes per element for one fused stage (FP32): q in/out and
+# residual in/out (12 Np floats) + 13 geometry floats + 6 int32 connectivity;
+# the first stage of a step does not read the residual (a_1 = 0).
+STAGE_BYTES = {1: 220, 2: 364, 3: 556, 4: 796, 5: 1084, 6: 1420, 7: 1804}
+
+
+def rhs_flops_per_element(N):
+    Np = (N + 1) * (N + 2) // 2
+    Nafp = 3 * (N + 1)
+    return 6 * 2 * Np * Np + 2 * Np * 13 + 3 * (2 * Np * Nafp + Np) + Nafp * 18
+
+
+def step_bytes_per_element(N):
+    Np = (N + 1) * (N + 2) // 2
+    first = STAGE_BYTES[N] - 3 * Np * 4
+    return 4 * STAGE_BYTES[N] + first
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id, period_ms=100):
+        self.gpu_id = gpu_id
+        self.period_ms = period_ms
+        self.proc = None
+        self.lines = []
+        self.error = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                   "-lms", str(self.period_ms)]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception as ex:  # no nvidia-smi
+            self.error = str(ex)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"error": self.error or "nvidia-smi unavailable"}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"error": "no samples", "raw": self.lines[:3]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- oracle
+def oracle_sample_rate(n, N, seconds, steps=None, warmup=0):
+    """Time the FP64 oracle's LSRK(5,4) steps on the n-mesh; returns
+    (element-stage updates/s, steps run, K)."""
+    import numpy as np
+
+    import oracle as O
+    from synth import gaussian_pulse, jittered_delaunay_mesh
+
+    mesh = jittered_delaunay_mesh(n, seed=2024)
+    d = O.Discretization(*mesh, N)
+    q = np.stack(gaussian_pulse(d.x, d.y))
+    dt = O.cfl_dt(d)
+    for _ in range(warmup):
+        q = O.lsrk_step(d, q, 0.0, dt)
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        q = O.lsrk_step(d, q, done * dt, dt)
+        done += 1
+        el = time.perf_counter() - t0
+        if steps is not None and done >= steps:
+            break
+        if steps is None and el >= seconds:
+            break
+    return d.K * 5 * done / el, done, d.K, el
+
+
+def cpu_baseline(n=100, N=5, seconds=10.0):
+    """The oracle on one host core (BLAS/OpenMP threads pinned to 1), in a
+    child process so the thread limit applies before numpy loads."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle-sample", str(n), str(N), str(seconds)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-500:]}
+    v = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": v["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 numpy oracle, %d LSRK(5,4) steps on the n=%d jittered mesh "
+                      "(K=%d, N=%d), 1 thread, %.1f s" % (v["steps"], n, v["K"], N, v["seconds"])}
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1304_5546_gb300 as P
+    from synth import gaussian_pulse, jittered_delaunay_mesh
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    N = args.order
+    mesh = jittered_delaunay_mesh(args.n, seed=2024)
+    s = P.Solver(*mesh, N=N, precision=args.precision, device=dev)
+    x, y = s.nodes()
+    q0 = np.stack(gaussian_pulse(x, y))
+    q = s.from_numpy(q0)
+    res = s.new_fields()
+    dt = s.cfl_dt()
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        s.step(q, res, dt, nsteps=1)
+    P.dg_sync_check(s.op)
+
+    clocks = ClockSampler(dev if world > 1 else None) if not args.no_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    launches0 = P.dg_launch_count(s.op)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    s.step(q, res, dt, nsteps=args.steps)
+    end.record(stream)
+    end.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = start.elapsed_time(end)
+    launches = P.dg_launch_count(s.op) - launches0
+    clk = clocks.stop() if clocks else None
+    P.dg_check_finite(s.op, q)
+
+    # end to end through the C ABI with host buffers: copy in, one step,
+    # copy out, every step
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    h = s.from_numpy(q0).cpu().pin_memory()
+    dq, dres = s.new_fields(), s.new_fields()
+    P.dg_step_host(s.op, h, dq, dres, 0.0, dt, 1)  # warm
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.dg_step_host(s.op, h, dq, dres, 0.0, dt, 1)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+
+    tmax = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms, e2e_s = float(tmax[0]), float(tmax[1])
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+
+    K = s.K
+    units = world * K * 5 * args.steps
+    value = units / (ms / 1e3)
+    peaks, peak_kind = measured_peaks()
+    bytes_step = K * step_bytes_per_element(N) * (2 if args.precision == "fp64" else 1)
+    achieved = bytes_step * args.steps / (ms / 1e3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            from paper_1304_5546_gb300.build import kernel_source_hash
+            t = json.load(open(tpath))
+            key = "N%d_%s" % (N, args.precision)
+            if t.get("kernel_hash") == kernel_source_hash() and key in t.get("per_element", {}):
+                traffic = t["per_element"][key] * K * 5 * args.steps / launches
+        except Exception:
+            traffic = None
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": "single large mesh: jittered Delaunay unit square n=%d (K=%d), N=%d, "
+                        "Gaussian pulse w=0.05, LSRK(5,4) steps" % (args.n, K, N),
+            "K": K, "N": N, "Np": s.Np, "precision": args.precision,
+            "mesh_seed": 2024,
+            "l2": "inputs larger than L2 (q, q_tmp, res: %.0f MB)" % (
+                3 * 3 * s.fstride * (4 if args.precision == "fp32" else 8) / 1e6),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+        },
+        "rhs_gflops": world * K * rhs_flops_per_element(N) * 5 * args.steps / (ms / 1e3) / 1e9,
+        "roofline": {
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": peaks["hbm_gbs"],
+            "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"],
+            "traffic": traffic,
+            "peak_kind": peak_kind,
+            "kernel": "dg_stage_kernel (fused RHS + LSRK stage)",
+            "bytes_per_element_step": step_bytes_per_element(N),
+        },
+        "e2e": {
+            "value": world * K * 5 * e2e_steps / e2e_s,
+            "unit": UNIT,
+            "h2d_bytes_per_step": 3 * s.fstride * (4 if args.precision == "fp32" else 8),
+            "d2h_bytes_per_step": 3 * s.fstride * (4 if args.precision == "fp32" else 8),
+            "steps": e2e_steps,
+            "api": "dg_step_host (pinned host buffer -> device, 1 step, device -> host)",
+        },
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    n, N = 100, args.order
+    value, steps, K, seconds = oracle_sample_rate(n, N, None, steps=args.steps, warmup=args.warmup)
+    sample = ("FP64 numpy oracle on the n=%d jittered mesh (K=%d, N=%d), %d timed LSRK(5,4) "
+              "steps after %d warm-up, default BLAS threads" % (n, K, N, steps, args.warmup))
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": seconds * 1e3 / steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "single large mesh workload, bounded sample: jittered Delaunay "
+                               "unit square n=%d (K=%d), N=%d, LSRK(5,4) steps" % (n, K, N),
+                   "K": K, "N": N},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--order", type=int, default=5)
+    ap.add_argument("--n", type=int, default=707, help="mesh resolution (K = 2 n^2)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--_oracle-sample", nargs=3, default=None)
+    args = ap.parse_args(argv)
+    if args._oracle_sample:
+        n, N, sec = int(args._oracle_sample[0]), int(args._oracle_sample[1]), float(args._oracle_sample[2])
+        v, steps, K, el = oracle_sample_rate(n, N, sec)
+        print(json.dumps({"value": v, "steps": steps, "K": K, "seconds": el}))
+        return 0
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,229 @@
+/*
+ * dgwave.h -- C ABI of the GB300 nodal discontinuous Galerkin wave solver.
+ *
+ * The library evaluates the semi-discrete right-hand side of the 2D
+ * transverse-magnetic Maxwell system (Hx, Hy, Ez; eps = mu = 1; PEC walls)
+ * on an unstructured, straight-sided triangle mesh with the nodal DG method
+ * of Kloeckner, Warburton and Hesthaven, "Solving Wave Equations on
+ * Unstructured Geometries", and advances it with the five-stage fourth-order
+ * low-storage Runge-Kutta scheme LSRK(5,4).
+ *
+ *   Problem:  Eq. tm-maxwells (Section "A Precise Mathematical Problem
+ *             Statement"), PEC condition Ez = 0 on the boundary.
+ *   Method:   Eq. dg-strong with the upwind flux of Eq. max2d-numflux
+ *             (alpha = 1), in the explicit form Eq. dg-strong-explicit:
+ *             element-local differentiation (Eq. dg-diff-local-to-global),
+ *             face-trace gather + flux, surface lift (Eq. dg-lift).
+ *   Time:     "a simple Runge-Kutta time integrator" (Section "Computing
+ *             the Surface Contribution"), here LSRK(5,4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Node numbering inside an element: Warburton warp-and-blend nodes of
+ *   order N on the reference triangle v1 = (-1,-1), v2 = (1,-1), v3 = (-1,1),
+ *   numbered row by row of the equidistant lattice (rows of constant s from
+ *   s = -1 upwards, r increasing within a row).  Np = (N+1)(N+2)/2.
+ * - Element k's vertices are EToV[3k..3k+2]; clockwise input triangles are
+ *   re-listed counter-clockwise by swapping their 2nd and 3rd vertex, and
+ *   the element's node coordinates follow that (possibly swapped) order.
+ *   Faces: face 0 = v1v2, face 1 = v2v3, face 2 = v3v1.
+ * - Field buffers ("q", "rhs", "res") are device arrays of 3 fields in the
+ *   order Hx, Hy, Ez.  Field f of element k, node n lives at index
+ *   f * field_stride + k * Np + n (element-major, node-minor, no padding
+ *   inside an element).  field_stride >= K * Np comes from dg_get_info; it
+ *   rounds K up to a whole number of kernel blocks and keeps every field
+ *   256-byte aligned.  A buffer therefore holds 3 * field_stride values of
+ *   the operator's precision (float for DG_FP32, double for DG_FP64).
+ *   Entries beyond K * Np in a field are never read for results and never
+ *   written.
+ * - Ownership: the caller owns every host array it passes in (the library
+ *   copies what it keeps) and every device field buffer (the library never
+ *   frees or reallocates them).  Handles are owned by the library until
+ *   their *_destroy call.  Streams belong to the caller; `stream` is a
+ *   cudaStream_t passed as void* (NULL = the legacy default stream).
+ * - Asynchrony: dg_rhs, dg_step and dg_solve only enqueue work on `stream`
+ *   and return; dg_step_host returns after its results are in host memory.
+ *   Launch errors are reported by the call; errors raised while kernels run
+ *   surface at the next dg_sync_check (or any later CUDA call).
+ * - Errors never abort the process.  A non-zero dg_status leaves every output
+ *   untouched for argument errors; dg_last_error() returns a thread-local
+ *   message describing the last failure on the calling thread.
+ */
+#ifndef DGWAVE_H
+#define DGWAVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_mesh dg_mesh;
+typedef struct dg_op dg_op;
+typedef int32_t dg_status;
+
+#define DG_OK 0
+#define DG_ERR_ARG 1                /* bad pointer, size or value            */
+#define DG_ERR_MESH_DEGENERATE 2    /* zero-area triangle                    */
+#define DG_ERR_MESH_NONCONFORMING 3 /* face shared by more than two elements */
+#define DG_ERR_ORDER 4              /* N outside 1..DG_N_MAX                 */
+#define DG_ERR_CUDA 5               /* CUDA runtime error / no device        */
+#define DG_ERR_OOM 6                /* device or host allocation failed      */
+#define DG_ERR_NONFINITE 7          /* NaN or Inf found in a field           */
+#define DG_ERR_NO_DEVICE 8          /* operator was set up host-only         */
+
+#define DG_FP64 0
+#define DG_FP32 1
+
+#define DG_SETUP_HOST_ONLY 1 /* dg_operator_setup flag: skip device upload */
+
+#define DG_N_MAX 7
+
+/* ---------------------------------------------------------------- mesh ---
+ * dg_mesh_create: build a conforming triangle mesh from vertex coordinates
+ * (vx[Nv], vy[Nv], FP64, host) and a 0-based element-to-vertex table
+ * (EToV[3K], int32, host).  Computes element-to-element / element-to-face
+ * connectivity (two faces are the same face when they join the same vertex
+ * pair; a boundary face points to itself), and re-lists clockwise triangles
+ * counter-clockwise.  This is the mesh of Section "Construction of the
+ * Method": disjoint, straight-sided, face-conforming triangles.
+ * Errors: DG_ERR_ARG (NULL pointer, K < 1, Nv < 3, vertex index out of
+ * range, K >= 2^28), DG_ERR_MESH_DEGENERATE (zero area),
+ * DG_ERR_MESH_NONCONFORMING (a face shared by three or more elements),
+ * DG_ERR_OOM.  *out is written only on success.                           */
+dg_status dg_mesh_create(const double* vx, const double* vy, int64_t Nv,
+                         const int32_t* EToV, int64_t K, dg_mesh** out);
+
+/* K, number of triangles re-listed counter-clockwise, number of boundary
+ * faces.  Any output pointer may be NULL.                                  */
+dg_status dg_mesh_info(const dg_mesh* mesh, int64_t* K, int64_t* n_flipped,
+                       int64_t* n_boundary_faces);
+
+/* Host copies (K*3 int32 each) of the connectivity: face f of element k
+ * joins face EToF[3k+f] of element EToE[3k+f]; boundary faces point to
+ * themselves.  Also the oriented EToV (K*3) if EToV_out is not NULL.       */
+dg_status dg_mesh_connectivity(const dg_mesh* mesh, int32_t* EToE, int32_t* EToF,
+                               int32_t* EToV_out);
+
+void dg_mesh_destroy(dg_mesh* mesh);
+
+/* ----------------------------------------------------------- operator ---
+ * dg_operator_setup: everything that needs FP64 is computed on the host in
+ * FP64 (Section "Implementation Aspects"): Warburton nodes (cited there for
+ * numerical stability), the orthonormal-basis Vandermonde matrix, the
+ * reference differentiation matrices Dr, Ds (Eq. dg-diff-local-to-global),
+ * face mass matrices and LIFT = M^-1 M^dI (Eq. dg-lift), the affine
+ * Jacobians and chain-rule factors rx, ry, sx, sy, outward unit normals and
+ * Fscale = surface Jacobian / volume Jacobian (Section "Computing the
+ * Surface Contribution"), and the trace maps.  Unless flags has
+ * DG_SETUP_HOST_ONLY, device-ready copies are uploaded once, cast to the
+ * operator's precision (DG_FP32 or DG_FP64), to the current CUDA device.
+ * The operator keeps its own copy of the mesh data; the mesh may be
+ * destroyed afterwards.
+ * Errors: DG_ERR_ARG, DG_ERR_ORDER (N < 1 or N > DG_N_MAX), DG_ERR_CUDA,
+ * DG_ERR_OOM.  *out is written only on success.                           */
+dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t precision,
+                            int32_t flags, dg_op** out);
+
+/* Np, Nfp = N+1, K and field_stride (see conventions).  NULL outputs are
+ * skipped.                                                                 */
+dg_status dg_get_info(const dg_op* op, int32_t* Np, int32_t* Nfp, int64_t* K,
+                      int64_t* field_stride);
+
+/* Host copies of the physical node coordinates, x[K*Np], y[K*Np] (FP64),
+ * index k*Np + n.                                                          */
+dg_status dg_get_nodes(const dg_op* op, double* x, double* y);
+
+/* Host copies of the reference element (FP64): r[Np], s[Np], Dr[Np*Np] and
+ * Ds[Np*Np] (row-major, row = output node), LIFT[Np*3Nfp] (row-major,
+ * column j = face j/Nfp, face node j%Nfp), Fmask[3*Nfp] (node index of each
+ * face node, increasing along each face).  NULL outputs are skipped.       */
+dg_status dg_get_reference(const dg_op* op, double* r, double* s, double* Dr,
+                           double* Ds, double* LIFT, int32_t* Fmask);
+
+/* Host copies of the FP64 geometry: per element rx, ry, sx, sy, J [K];
+ * per element face (index 3k+f) nx, ny, Fscale [3K].  NULL outputs are
+ * skipped.                                                                 */
+dg_status dg_get_geometry(const dg_op* op, double* rx, double* ry, double* sx,
+                          double* sy, double* J, double* nx, double* ny,
+                          double* Fscale);
+
+/* Host copies of the trace maps, vmapM[K*3Nfp] and vmapP[K*3Nfp] (int64
+ * global node numbers k*Np + n of the interior and exterior trace of every
+ * face node; boundary face nodes have vmapP = vmapM).                     */
+dg_status dg_get_maps(const dg_op* op, int64_t* vmapM, int64_t* vmapP);
+
+/* CFL time step: cfl * (2/3) * min over elements of the inradius *
+ * (spacing of the first two Gauss-Lobatto points of order N).             */
+dg_status dg_cfl_dt(const dg_op* op, double cfl, double* dt);
+
+/* LSRK(5,4) coefficients used by dg_step (each array of 5 doubles, NULL
+ * skipped): a, b (Carpenter-Kennedy 2N-storage) and stage times c.        */
+dg_status dg_lsrk_coefficients(double* a, double* b, double* c);
+
+void dg_op_destroy(dg_op* op);
+
+/* --------------------------------------------------------- hot path ----
+ * dg_rhs: rhs = the semi-discrete right-hand side of Eq. dg-strong-explicit
+ * for the three fields in d_q: volume derivative (Dr/Ds + chain rule),
+ * face-trace gather with the upwind flux (PEC: Ez+ = -Ez-, H+ = H-), LIFT
+ * apply with the factor Fscale/2.  d_q and d_rhs are device field buffers
+ * of the operator's precision (3 * field_stride values each) and must not
+ * overlap.  t is accepted for interface symmetry (the system is
+ * autonomous).  Enqueued on `stream`.
+ * Errors: DG_ERR_ARG (NULL / overlapping / misaligned buffers),
+ * DG_ERR_NO_DEVICE, DG_ERR_CUDA (launch failure).                          */
+dg_status dg_rhs(const dg_op* op, const void* d_q, void* d_rhs, double t, void* stream);
+
+/* dg_step: nsteps >= 0 LSRK(5,4) steps of size dt starting at t0, in place
+ * on d_q.  Each of the 5 stages is ONE fused kernel: right-hand side of the
+ * stage's input plus the 2N-storage update
+ *     res <- a_i res + dt rhs,   q <- q + b_i res.
+ * d_res is a caller-owned device field buffer for the residual (same size
+ * as d_q); it needs no initialisation (a_1 = 0: the first stage overwrites
+ * it) and holds the last stage's residual on return.  Stages alternate
+ * between d_q and an operator-owned device buffer; when nsteps is odd the
+ * result is copied back into d_q with one device-to-device copy.  Enqueued
+ * on `stream`.  Calls on one operator must not overlap in time (they share
+ * that buffer).
+ * Errors: DG_ERR_ARG (NULL/overlapping buffers, nsteps < 0, dt not
+ * finite), DG_ERR_NO_DEVICE, DG_ERR_CUDA.                                  */
+dg_status dg_step(const dg_op* op, void* d_q, void* d_res, double t0, double dt,
+                  int32_t nsteps, void* stream);
+
+/* dg_solve: advance d_q from t = 0 to T.  dt <= 0 selects dg_cfl_dt(op, 1).
+ * The step count is ceil(T/dt) and dt is shrunk to land on T exactly.
+ * Writes the step count and the final time (host values, known at enqueue
+ * time).  Same buffers and errors as dg_step.                              */
+dg_status dg_solve(const dg_op* op, void* d_q, void* d_res, double T, double dt,
+                   int32_t* nsteps_out, double* t_reached, void* stream);
+
+/* dg_step_host: dg_step on fields held in HOST memory.  Copies h_q (3 *
+ * field_stride values, pinned memory recommended) to the device buffer d_q,
+ * runs nsteps steps with d_res as residual buffer, copies the result back
+ * into h_q, and synchronises `stream` before returning.                    */
+dg_status dg_step_host(const dg_op* op, void* h_q, void* d_q, void* d_res, double t0,
+                       double dt, int32_t nsteps, void* stream);
+
+/* dg_check_finite: synchronises `stream`, then scans the first K*Np values
+ * of each field of d_q for NaN/Inf.  Returns DG_ERR_NONFINITE if any is
+ * found (blow-up detection), DG_OK otherwise.                              */
+dg_status dg_check_finite(const dg_op* op, const void* d_q, void* stream);
+
+/* dg_sync_check: synchronises `stream` and reports any pending CUDA error
+ * (DG_ERR_CUDA with its message in dg_last_error()).                      */
+dg_status dg_sync_check(const dg_op* op, void* stream);
+
+/* Number of kernel launches enqueued by this operator since setup (one per
+ * dg_rhs, five per step, plus one per dg_check_finite).                   */
+int64_t dg_launch_count(const dg_op* op);
+
+/* Thread-local message of the last failing call on this thread ("" if
+ * none).  The pointer stays valid until the next call on the thread.      */
+const char* dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGWAVE_H */

@@ -1,0 +1,267 @@
+"""GB300-native nodal discontinuous Galerkin solver for the 2D TM Maxwell
+system (Kloeckner, Warburton, Hesthaven, "Solving Wave Equations on
+Unstructured Geometries"): right-hand side + LSRK(5,4) in hand-written CUDA
+for sm_103a behind the C ABI of include/dgwave.h.
+
+This module is the thin Python binding: functions named like the C entry
+points marshal numpy arrays / torch tensors into pointers and call the
+library.  PyTorch supplies device memory and streams only.  There is no CPU
+fallback: every call raises if libdgwave.so is missing or the call fails.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    DG_FP32,
+    DG_FP64,
+    DG_N_MAX,
+    DG_SETUP_HOST_ONLY,
+    DGError,
+)
+
+__all__ = [
+    "dg_mesh_create", "dg_mesh_info", "dg_mesh_connectivity", "dg_mesh_destroy",
+    "dg_operator_setup", "dg_get_info", "dg_get_nodes", "dg_get_reference",
+    "dg_get_geometry", "dg_get_maps", "dg_cfl_dt", "dg_lsrk_coefficients",
+    "dg_op_destroy", "dg_rhs", "dg_step", "dg_solve", "dg_step_host",
+    "dg_check_finite", "dg_sync_check", "dg_launch_count", "dg_last_error",
+    "Solver", "DGError", "DG_FP32", "DG_FP64",
+]
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ mesh
+def dg_mesh_create(VX, VY, EToV):
+    VX = np.ascontiguousarray(VX, dtype=np.float64)
+    VY = np.ascontiguousarray(VY, dtype=np.float64)
+    E = np.ascontiguousarray(EToV, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _lib.check(_lib.load().dg_mesh_create(_ptr(VX), _ptr(VY), VX.size, _ptr(E), E.shape[0],
+                                          ctypes.byref(h)), "dg_mesh_create")
+    return h.value
+
+
+def dg_mesh_info(mesh):
+    K, nf, nb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _lib.check(_lib.load().dg_mesh_info(mesh, ctypes.byref(K), ctypes.byref(nf), ctypes.byref(nb)),
+               "dg_mesh_info")
+    return K.value, nf.value, nb.value
+
+
+def dg_mesh_connectivity(mesh):
+    K = dg_mesh_info(mesh)[0]
+    EToE = np.empty((K, 3), np.int32)
+    EToF = np.empty((K, 3), np.int32)
+    EToV = np.empty((K, 3), np.int32)
+    _lib.check(_lib.load().dg_mesh_connectivity(mesh, _ptr(EToE), _ptr(EToF), _ptr(EToV)),
+               "dg_mesh_connectivity")
+    return EToE, EToF, EToV
+
+
+def dg_mesh_destroy(mesh):
+    if mesh:
+        _lib.load().dg_mesh_destroy(mesh)
+
+
+# -------------------------------------------------------------- operator
+def dg_operator_setup(mesh, N, precision=DG_FP32, flags=0):
+    h = ctypes.c_void_p()
+    _lib.check(_lib.load().dg_operator_setup(mesh, N, precision, flags, ctypes.byref(h)),
+               "dg_operator_setup")
+    return h.value
+
+
+def dg_get_info(op):
+    Np, Nfp = ctypes.c_int32(), ctypes.c_int32()
+    K, fs = ctypes.c_int64(), ctypes.c_int64()
+    _lib.check(_lib.load().dg_get_info(op, ctypes.byref(Np), ctypes.byref(Nfp), ctypes.byref(K),
+                                       ctypes.byref(fs)), "dg_get_info")
+    return Np.value, Nfp.value, K.value, fs.value
+
+
+def dg_get_nodes(op):
+    Np, _, K, _ = dg_get_info(op)
+    x = np.empty((K, Np))
+    y = np.empty((K, Np))
+    _lib.check(_lib.load().dg_get_nodes(op, _ptr(x), _ptr(y)), "dg_get_nodes")
+    return x, y
+
+
+def dg_get_reference(op):
+    Np, Nfp, _, _ = dg_get_info(op)
+    out = {"r": np.empty(Np), "s": np.empty(Np), "Dr": np.empty((Np, Np)),
+           "Ds": np.empty((Np, Np)), "LIFT": np.empty((Np, 3 * Nfp)),
+           "Fmask": np.empty((3, Nfp), np.int32)}
+    _lib.check(_lib.load().dg_get_reference(op, *[_ptr(out[k]) for k in
+                                                  ("r", "s", "Dr", "Ds", "LIFT", "Fmask")]),
+               "dg_get_reference")
+    return out
+
+
+def dg_get_geometry(op):
+    _, _, K, _ = dg_get_info(op)
+    names = ("rx", "ry", "sx", "sy", "J", "nx", "ny", "Fscale")
+    out = {n: np.empty(K) for n in names[:5]}
+    out.update({n: np.empty((K, 3)) for n in names[5:]})
+    _lib.check(_lib.load().dg_get_geometry(op, *[_ptr(out[n]) for n in names]), "dg_get_geometry")
+    return out
+
+
+def dg_get_maps(op):
+    _, Nfp, K, _ = dg_get_info(op)
+    vM = np.empty((K, 3 * Nfp), np.int64)
+    vP = np.empty((K, 3 * Nfp), np.int64)
+    _lib.check(_lib.load().dg_get_maps(op, _ptr(vM), _ptr(vP)), "dg_get_maps")
+    return vM, vP
+
+
+def dg_cfl_dt(op, cfl=1.0):
+    dt = ctypes.c_double()
+    _lib.check(_lib.load().dg_cfl_dt(op, cfl, ctypes.byref(dt)), "dg_cfl_dt")
+    return dt.value
+
+
+def dg_lsrk_coefficients():
+    a, b, c = np.empty(5), np.empty(5), np.empty(5)
+    _lib.check(_lib.load().dg_lsrk_coefficients(_ptr(a), _ptr(b), _ptr(c)), "dg_lsrk_coefficients")
+    return a, b, c
+
+
+def dg_op_destroy(op):
+    if op:
+        _lib.load().dg_op_destroy(op)
+
+
+# -------------------------------------------------------------- hot path
+def dg_rhs(op, q, rhs, t=0.0, stream=None):
+    _lib.check(_lib.load().dg_rhs(op, _dptr(q), _dptr(rhs), t, _stream_handle(stream)), "dg_rhs")
+
+
+def dg_step(op, q, res, t0, dt, nsteps, stream=None):
+    _lib.check(_lib.load().dg_step(op, _dptr(q), _dptr(res), t0, dt, nsteps,
+                                   _stream_handle(stream)), "dg_step")
+
+
+def dg_solve(op, q, res, T, dt=0.0, stream=None):
+    n = ctypes.c_int32()
+    t = ctypes.c_double()
+    _lib.check(_lib.load().dg_solve(op, _dptr(q), _dptr(res), T, dt, ctypes.byref(n),
+                                    ctypes.byref(t), _stream_handle(stream)), "dg_solve")
+    return n.value, t.value
+
+
+def dg_step_host(op, h_q, d_q, d_res, t0, dt, nsteps, stream=None):
+    """h_q: host tensor (pinned recommended) or contiguous numpy array of
+    3 * field_stride values."""
+    hp = ctypes.c_void_p(h_q.data_ptr()) if hasattr(h_q, "data_ptr") else _ptr(h_q)
+    _lib.check(_lib.load().dg_step_host(op, hp, _dptr(d_q), _dptr(d_res), t0, dt, nsteps,
+                                        _stream_handle(stream)), "dg_step_host")
+
+
+def dg_check_finite(op, q, stream=None):
+    _lib.check(_lib.load().dg_check_finite(op, _dptr(q), _stream_handle(stream)), "dg_check_finite")
+
+
+def dg_sync_check(op, stream=None):
+    _lib.check(_lib.load().dg_sync_check(op, _stream_handle(stream)), "dg_sync_check")
+
+
+def dg_launch_count(op):
+    return int(_lib.load().dg_launch_count(op))
+
+
+def dg_last_error():
+    m = _lib.load().dg_last_error()
+    return m.decode() if m else ""
+
+
+# ------------------------------------------------------------ convenience
+class Solver:
+    """Owns a mesh + operator pair and the torch tensors that hold fields.
+
+    Field tensors have shape (3, field_stride) on the operator's device, in
+    the operator's precision; ``view(q)`` gives the (3, K, Np) window.
+    """
+
+    def __init__(self, VX, VY, EToV, N, precision="fp32", device=None, host_only=False):
+        import torch
+        self.precision = DG_FP32 if precision in ("fp32", DG_FP32) else DG_FP64
+        self.dtype = torch.float32 if self.precision == DG_FP32 else torch.float64
+        if device is not None and not host_only:
+            torch.cuda.set_device(device)
+        self.device = None if host_only else torch.device("cuda", torch.cuda.current_device())
+        self.mesh = dg_mesh_create(VX, VY, EToV)
+        try:
+            self.op = dg_operator_setup(self.mesh, N, self.precision,
+                                        DG_SETUP_HOST_ONLY if host_only else 0)
+        except Exception:
+            dg_mesh_destroy(self.mesh)
+            raise
+        self.N = N
+        self.Np, self.Nfp, self.K, self.fstride = dg_get_info(self.op)
+
+    def close(self):
+        dg_op_destroy(getattr(self, "op", None))
+        dg_mesh_destroy(getattr(self, "mesh", None))
+        self.op = self.mesh = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # fields
+    def new_fields(self, zero=True):
+        import torch
+        f = torch.zeros if zero else torch.empty
+        return f((3, self.fstride), dtype=self.dtype, device=self.device)
+
+    def view(self, q):
+        return q[:, : self.K * self.Np].view(3, self.K, self.Np)
+
+    def from_numpy(self, q3):
+        import torch
+        q = self.new_fields()
+        self.view(q).copy_(torch.as_tensor(np.asarray(q3), dtype=self.dtype))
+        return q
+
+    def to_numpy(self, q):
+        return self.view(q).detach().to("cpu", dtype=__import__("torch").float64).numpy()
+
+    # hot path
+    def rhs(self, q, out=None, stream=None):
+        out = self.new_fields(zero=False) if out is None else out
+        dg_rhs(self.op, q, out, 0.0, stream)
+        return out
+
+    def step(self, q, res, dt, nsteps=1, t0=0.0, stream=None):
+        dg_step(self.op, q, res, t0, dt, nsteps, stream)
+        return q
+
+    def solve(self, q, res, T, dt=0.0, stream=None):
+        return dg_solve(self.op, q, res, T, dt, stream)
+
+    def cfl_dt(self, cfl=1.0):
+        return dg_cfl_dt(self.op, cfl)
+
+    def nodes(self):
+        return dg_get_nodes(self.op)

@@ -1,0 +1,96 @@
+"""ctypes binding of the C ABI declared in include/dgwave.h.
+
+Argument marshalling only: every computation runs in libdgwave.so.  The
+functions keep the C names; pointers are plain integers (device pointers
+from ``tensor.data_ptr()``, streams from ``torch.cuda.Stream.cuda_stream``).
+Loading fails loudly when the library has not been built.
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdgwave.so")
+
+DG_OK = 0
+DG_ERR_ARG = 1
+DG_ERR_MESH_DEGENERATE = 2
+DG_ERR_MESH_NONCONFORMING = 3
+DG_ERR_ORDER = 4
+DG_ERR_CUDA = 5
+DG_ERR_OOM = 6
+DG_ERR_NONFINITE = 7
+DG_ERR_NO_DEVICE = 8
+DG_FP64 = 0
+DG_FP32 = 1
+DG_SETUP_HOST_ONLY = 1
+DG_N_MAX = 7
+
+_STATUS_NAMES = {
+    0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_MESH_DEGENERATE", 3: "DG_ERR_MESH_NONCONFORMING",
+    4: "DG_ERR_ORDER", 5: "DG_ERR_CUDA", 6: "DG_ERR_OOM", 7: "DG_ERR_NONFINITE",
+    8: "DG_ERR_NO_DEVICE",
+}
+
+c_void_p = ctypes.c_void_p
+c_i32 = ctypes.c_int32
+c_i64 = ctypes.c_int64
+c_dbl = ctypes.c_double
+P = ctypes.POINTER
+
+# (name, restype, argtypes) of every exported entry point
+SIGNATURES = [
+    ("dg_mesh_create", c_i32, [c_void_p, c_void_p, c_i64, c_void_p, c_i64, P(c_void_p)]),
+    ("dg_mesh_info", c_i32, [c_void_p, P(c_i64), P(c_i64), P(c_i64)]),
+    ("dg_mesh_connectivity", c_i32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("dg_mesh_destroy", None, [c_void_p]),
+    ("dg_operator_setup", c_i32, [c_void_p, c_i32, c_i32, c_i32, P(c_void_p)]),
+    ("dg_get_info", c_i32, [c_void_p, P(c_i32), P(c_i32), P(c_i64), P(c_i64)]),
+    ("dg_get_nodes", c_i32, [c_void_p, c_void_p, c_void_p]),
+    ("dg_get_reference", c_i32, [c_void_p] + [c_void_p] * 6),
+    ("dg_get_geometry", c_i32, [c_void_p] + [c_void_p] * 8),
+    ("dg_get_maps", c_i32, [c_void_p, c_void_p, c_void_p]),
+    ("dg_cfl_dt", c_i32, [c_void_p, c_dbl, P(c_dbl)]),
+    ("dg_lsrk_coefficients", c_i32, [c_void_p, c_void_p, c_void_p]),
+    ("dg_op_destroy", None, [c_void_p]),
+    ("dg_rhs", c_i32, [c_void_p, c_void_p, c_void_p, c_dbl, c_void_p]),
+    ("dg_step", c_i32, [c_void_p, c_void_p, c_void_p, c_dbl, c_dbl, c_i32, c_void_p]),
+    ("dg_solve", c_i32, [c_void_p, c_void_p, c_void_p, c_dbl, c_dbl, P(c_i32), P(c_dbl), c_void_p]),
+    ("dg_step_host", c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_dbl, c_dbl, c_i32, c_void_p]),
+    ("dg_check_finite", c_i32, [c_void_p, c_void_p, c_void_p]),
+    ("dg_sync_check", c_i32, [c_void_p, c_void_p]),
+    ("dg_launch_count", c_i64, [c_void_p]),
+    ("dg_last_error", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, where, message):
+        self.status = status
+        super().__init__("%s failed with %s: %s" % (where, _STATUS_NAMES.get(status, status), message))
+
+
+def load(path=None):
+    """Load libdgwave.so (once) and declare its signatures."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError("libdgwave.so not built (expected at %s); run __graft_entry__.build()" % p)
+    lib = ctypes.CDLL(p)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def check(status, where):
+    if status != DG_OK:
+        msg = load().dg_last_error()
+        raise DGError(status, where, msg.decode() if msg else "")
+    return status

@@ -1,0 +1,485 @@
+// C ABI of the nodal DG wave solver: operator set-up and upload, and the
+// hot-path entry points dg_rhs / dg_step / dg_solve / dg_step_host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "launch.h"
+
+namespace dgw {
+const char* last_error_cstr();
+}
+
+using dgw::fail;
+
+struct dg_op {
+  int N = 0, Np = 0, Nfp = 0, Nafp = 0;
+  int precision = DG_FP32;
+  int flags = 0;
+  int64_t K = 0, Kpad = 0, fstride = 0;
+  size_t elem_size = 4;
+  dgw::RefElement ref;
+  dgw::Geometry geo;
+  bool has_device = false;
+  int device = 0;
+  int num_sms = 0;
+  void* d_Dr = nullptr;
+  void* d_Ds = nullptr;
+  void* d_LIFT = nullptr;
+  void* d_geo = nullptr;
+  void* d_conn = nullptr;
+  void* d_qtmp = nullptr;  // second field buffer for the stage ping-pong
+  int* d_flag = nullptr;   // finiteness scan result
+  double lsrk_a[5], lsrk_b[5], lsrk_c[5];
+  mutable std::atomic<int64_t> launches{0};
+};
+
+namespace {
+
+constexpr int64_t kBlockPad = 64;  // K is padded to whole blocks of <= 64 elements
+
+dg_status cuda_fail(cudaError_t err, const char* where) {
+  return fail(err == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA, "%s: %s (%s)", where,
+              cudaGetErrorName(err), cudaGetErrorString(err));
+}
+
+void free_device(dg_op* op) {
+  void* ptrs[] = {op->d_Dr, op->d_Ds, op->d_LIFT, op->d_geo, op->d_conn, op->d_qtmp, op->d_flag};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  op->d_Dr = op->d_Ds = op->d_LIFT = op->d_geo = op->d_conn = op->d_qtmp = nullptr;
+  op->d_flag = nullptr;
+}
+
+template <typename T>
+dg_status upload(dg_op* op) {
+  const int Np = op->Np, Nafp = op->Nafp;
+  const int64_t K = op->K, Kpad = op->Kpad;
+  std::vector<T> Dr(op->ref.Dr.begin(), op->ref.Dr.end());
+  std::vector<T> Ds(op->ref.Ds.begin(), op->ref.Ds.end());
+  std::vector<T> LIFT(op->ref.LIFT.begin(), op->ref.LIFT.end());
+  std::vector<T> geo(static_cast<size_t>(Kpad) * dgw::kGeo, T(0));
+  std::vector<int32_t> conn(static_cast<size_t>(Kpad) * 3, -1);
+  for (int64_t k = 0; k < K; ++k) {
+    T* g = &geo[k * dgw::kGeo];
+    g[0] = static_cast<T>(op->geo.rx[k]);
+    g[1] = static_cast<T>(op->geo.ry[k]);
+    g[2] = static_cast<T>(op->geo.sx[k]);
+    g[3] = static_cast<T>(op->geo.sy[k]);
+    for (int f = 0; f < 3; ++f) {
+      g[4 + 3 * f] = static_cast<T>(op->geo.nx[3 * k + f]);
+      g[5 + 3 * f] = static_cast<T>(op->geo.ny[3 * k + f]);
+      g[6 + 3 * f] = static_cast<T>(0.5 * op->geo.Fscale[3 * k + f]);
+      conn[3 * k + f] = op->geo.conn[3 * k + f];
+    }
+  }
+  struct Up {
+    void** dst;
+    const void* src;
+    size_t bytes;
+  } ups[] = {
+      {&op->d_Dr, Dr.data(), Dr.size() * sizeof(T)},
+      {&op->d_Ds, Ds.data(), Ds.size() * sizeof(T)},
+      {&op->d_LIFT, LIFT.data(), LIFT.size() * sizeof(T)},
+      {&op->d_geo, geo.data(), geo.size() * sizeof(T)},
+      {&op->d_conn, conn.data(), conn.size() * sizeof(int32_t)},
+  };
+  for (const Up& u : ups) {
+    cudaError_t err = cudaMalloc(u.dst, u.bytes);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc");
+    err = cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMemcpy");
+  }
+  cudaError_t err = cudaMalloc(&op->d_qtmp, 3 * op->fstride * sizeof(T));
+  if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(field buffer)");
+  err = cudaMemset(op->d_qtmp, 0, 3 * op->fstride * sizeof(T));
+  if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMemset");
+  err = cudaMalloc(&op->d_flag, sizeof(int));
+  if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(flag)");
+  (void)Np;
+  (void)Nafp;
+  return DG_OK;
+}
+
+template <typename T>
+cudaError_t launch_order(const dg_op* op, const dgw::StageArgs<T>& a, int mode, cudaStream_t s) {
+  switch (op->N) {
+    case 1: return dgw::launch_stage<T, 1>(a, mode, op->num_sms, s);
+    case 2: return dgw::launch_stage<T, 2>(a, mode, op->num_sms, s);
+    case 3: return dgw::launch_stage<T, 3>(a, mode, op->num_sms, s);
+    case 4: return dgw::launch_stage<T, 4>(a, mode, op->num_sms, s);
+    case 5: return dgw::launch_stage<T, 5>(a, mode, op->num_sms, s);
+    case 6: return dgw::launch_stage<T, 6>(a, mode, op->num_sms, s);
+    case 7: return dgw::launch_stage<T, 7>(a, mode, op->num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+dgw::StageArgs<T> base_args(const dg_op* op) {
+  dgw::StageArgs<T> a;
+  a.K = op->K;
+  a.fstride = op->fstride;
+  a.geo = static_cast<const T*>(op->d_geo);
+  a.conn = static_cast<const int32_t*>(op->d_conn);
+  a.Dr = static_cast<const T*>(op->d_Dr);
+  a.Ds = static_cast<const T*>(op->d_Ds);
+  a.LIFT = static_cast<const T*>(op->d_LIFT);
+  return a;
+}
+
+dg_status check_device_op(const dg_op* op, const char* where) {
+  if (!op) return fail(DG_ERR_ARG, "%s: NULL operator", where);
+  if (!op->has_device)
+    return fail(DG_ERR_NO_DEVICE, "%s: operator was set up host-only", where);
+  cudaError_t err = cudaSetDevice(op->device);
+  if (err != cudaSuccess) return cuda_fail(err, where);
+  return DG_OK;
+}
+
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + bytes && pb < pa + bytes;
+}
+
+dg_status check_field(const dg_op* op, const void* p, const char* name, const char* where) {
+  if (!p) return fail(DG_ERR_ARG, "%s: %s is NULL", where, name);
+  if (reinterpret_cast<uintptr_t>(p) % op->elem_size != 0)
+    return fail(DG_ERR_ARG, "%s: %s is not %zu-byte aligned", where, name, op->elem_size);
+  return DG_OK;
+}
+
+template <typename T>
+dg_status run_steps(const dg_op* op, T* q, T* res, double dt, int32_t nsteps, cudaStream_t s) {
+  dgw::StageArgs<T> a = base_args<T>(op);
+  a.res = res;
+  a.dt = static_cast<T>(dt);
+  T* cur = q;
+  T* other = static_cast<T*>(op->d_qtmp);
+  for (int32_t n = 0; n < nsteps; ++n) {
+    for (int i = 0; i < 5; ++i) {
+      a.qin = cur;
+      a.qout = other;
+      a.a = static_cast<T>(op->lsrk_a[i]);
+      a.b = static_cast<T>(op->lsrk_b[i]);
+      const int mode = (i == 0) ? dgw::kModeFirstStage : dgw::kModeStage;
+      cudaError_t err = launch_order<T>(op, a, mode, s);
+      if (err != cudaSuccess) return cuda_fail(err, "dg_step: kernel launch");
+      op->launches.fetch_add(1, std::memory_order_relaxed);
+      std::swap(cur, other);
+    }
+  }
+  if (cur != q) {
+    cudaError_t err = cudaMemcpyAsync(q, cur, 3 * op->fstride * sizeof(T),
+                                      cudaMemcpyDeviceToDevice, s);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_step: copy-back");
+  }
+  return DG_OK;
+}
+
+__global__ void finite_scan_kernel(const float* q32, const double* q64, int64_t fstride,
+                                   int64_t n, int* flag) {
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < 3 * n;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t f = idx / n;
+    const int64_t o = f * fstride + (idx - f * n);
+    const double v = q32 ? static_cast<double>(q32[o]) : q64[o];
+    if (!isfinite(v)) {
+      atomicExch(flag, 1);
+      return;
+    }
+  }
+}
+
+}  // namespace
+
+// ============================================================ C ABI
+extern "C" dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t precision,
+                                       int32_t flags, dg_op** out) {
+  dgw::clear_error();
+  if (!mesh || !out) return fail(DG_ERR_ARG, "dg_operator_setup: NULL argument");
+  if (N < 1 || N > DG_N_MAX)
+    return fail(DG_ERR_ORDER, "dg_operator_setup: N = %d outside 1..%d", N, DG_N_MAX);
+  if (precision != DG_FP32 && precision != DG_FP64)
+    return fail(DG_ERR_ARG, "dg_operator_setup: unknown precision %d", precision);
+  dg_op* op = nullptr;
+  try {
+    op = new dg_op;
+    op->N = N;
+    op->ref = dgw::build_reference(N);
+    op->Np = op->ref.Np;
+    op->Nfp = op->ref.Nfp;
+    op->Nafp = op->ref.Nafp;
+    op->precision = precision;
+    op->flags = flags;
+    op->elem_size = (precision == DG_FP32) ? 4 : 8;
+    op->K = mesh->K;
+    op->Kpad = (mesh->K + kBlockPad - 1) / kBlockPad * kBlockPad;
+    // whole blocks, and every field 256-byte aligned (64 values)
+    op->fstride = (op->Kpad * op->Np + 63) / 64 * 64;
+    op->geo = dgw::build_geometry(*mesh, op->ref);
+    dgw::lsrk_coefficients(op->lsrk_a, op->lsrk_b, op->lsrk_c);
+  } catch (const std::bad_alloc&) {
+    delete op;
+    return fail(DG_ERR_OOM, "dg_operator_setup: out of host memory");
+  } catch (const std::exception& ex) {
+    delete op;
+    return fail(DG_ERR_ARG, "dg_operator_setup: %s", ex.what());
+  }
+  if (!(flags & DG_SETUP_HOST_ONLY)) {
+    cudaError_t err = cudaGetDevice(&op->device);
+    if (err != cudaSuccess) {
+      delete op;
+      return cuda_fail(err, "dg_operator_setup: cudaGetDevice");
+    }
+    err = cudaDeviceGetAttribute(&op->num_sms, cudaDevAttrMultiProcessorCount, op->device);
+    if (err != cudaSuccess) {
+      delete op;
+      return cuda_fail(err, "dg_operator_setup: device attribute");
+    }
+    const dg_status st = (precision == DG_FP32) ? upload<float>(op) : upload<double>(op);
+    if (st != DG_OK) {
+      free_device(op);
+      delete op;
+      return st;
+    }
+    op->has_device = true;
+  }
+  *out = op;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_get_info(const dg_op* op, int32_t* Np, int32_t* Nfp, int64_t* K,
+                                 int64_t* field_stride) {
+  dgw::clear_error();
+  if (!op) return fail(DG_ERR_ARG, "dg_get_info: NULL operator");
+  if (Np) *Np = op->Np;
+  if (Nfp) *Nfp = op->Nfp;
+  if (K) *K = op->K;
+  if (field_stride) *field_stride = op->fstride;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_get_nodes(const dg_op* op, double* x, double* y) {
+  dgw::clear_error();
+  if (!op || !x || !y) return fail(DG_ERR_ARG, "dg_get_nodes: NULL argument");
+  std::memcpy(x, op->geo.x.data(), op->geo.x.size() * sizeof(double));
+  std::memcpy(y, op->geo.y.data(), op->geo.y.size() * sizeof(double));
+  return DG_OK;
+}
+
+extern "C" dg_status dg_get_reference(const dg_op* op, double* r, double* s, double* Dr,
+                                      double* Ds, double* LIFT, int32_t* Fmask) {
+  dgw::clear_error();
+  if (!op) return fail(DG_ERR_ARG, "dg_get_reference: NULL operator");
+  const dgw::RefElement& R = op->ref;
+  if (r) std::copy(R.r.begin(), R.r.end(), r);
+  if (s) std::copy(R.s.begin(), R.s.end(), s);
+  if (Dr) std::copy(R.Dr.begin(), R.Dr.end(), Dr);
+  if (Ds) std::copy(R.Ds.begin(), R.Ds.end(), Ds);
+  if (LIFT) std::copy(R.LIFT.begin(), R.LIFT.end(), LIFT);
+  if (Fmask) std::copy(R.Fmask.begin(), R.Fmask.end(), Fmask);
+  return DG_OK;
+}
+
+extern "C" dg_status dg_get_geometry(const dg_op* op, double* rx, double* ry, double* sx,
+                                     double* sy, double* J, double* nx, double* ny,
+                                     double* Fscale) {
+  dgw::clear_error();
+  if (!op) return fail(DG_ERR_ARG, "dg_get_geometry: NULL operator");
+  const dgw::Geometry& G = op->geo;
+  if (rx) std::copy(G.rx.begin(), G.rx.end(), rx);
+  if (ry) std::copy(G.ry.begin(), G.ry.end(), ry);
+  if (sx) std::copy(G.sx.begin(), G.sx.end(), sx);
+  if (sy) std::copy(G.sy.begin(), G.sy.end(), sy);
+  if (J) std::copy(G.J.begin(), G.J.end(), J);
+  if (nx) std::copy(G.nx.begin(), G.nx.end(), nx);
+  if (ny) std::copy(G.ny.begin(), G.ny.end(), ny);
+  if (Fscale) std::copy(G.Fscale.begin(), G.Fscale.end(), Fscale);
+  return DG_OK;
+}
+
+extern "C" dg_status dg_get_maps(const dg_op* op, int64_t* vmapM, int64_t* vmapP) {
+  dgw::clear_error();
+  if (!op || !vmapM || !vmapP) return fail(DG_ERR_ARG, "dg_get_maps: NULL argument");
+  const int N = op->N, Np = op->Np, Nfp = op->Nfp, Nafp = op->Nafp;
+  for (int64_t k = 0; k < op->K; ++k)
+    for (int f = 0; f < 3; ++f) {
+      const int32_t code = op->geo.conn[3 * k + f];
+      for (int j = 0; j < Nfp; ++j) {
+        const int64_t pos = k * Nafp + f * Nfp + j;
+        vmapM[pos] = k * Np + dgw::face_node(N, f, j);
+        if (code < 0) {
+          vmapP[pos] = vmapM[pos];
+        } else {
+          const int64_t kP = code >> 3;
+          const int fP = (code >> 1) & 3;
+          const int jP = (code & 1) ? (N - j) : j;
+          vmapP[pos] = kP * Np + dgw::face_node(N, fP, jP);
+        }
+      }
+    }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_cfl_dt(const dg_op* op, double cfl, double* dt) {
+  dgw::clear_error();
+  if (!op || !dt) return fail(DG_ERR_ARG, "dg_cfl_dt: NULL argument");
+  if (!(cfl > 0) || !std::isfinite(cfl)) return fail(DG_ERR_ARG, "dg_cfl_dt: cfl must be > 0");
+  *dt = cfl * (2.0 / 3.0) * op->geo.min_inradius * op->ref.lgl_gap;
+  return DG_OK;
+}
+
+extern "C" void dg_op_destroy(dg_op* op) {
+  if (!op) return;
+  if (op->has_device) {
+    cudaSetDevice(op->device);
+    free_device(op);
+  }
+  delete op;
+}
+
+extern "C" dg_status dg_rhs(const dg_op* op, const void* d_q, void* d_rhs, double t,
+                            void* stream) {
+  dgw::clear_error();
+  (void)t;
+  dg_status st = check_device_op(op, "dg_rhs");
+  if (st) return st;
+  if ((st = check_field(op, d_q, "d_q", "dg_rhs"))) return st;
+  if ((st = check_field(op, d_rhs, "d_rhs", "dg_rhs"))) return st;
+  const size_t bytes = 3 * op->fstride * op->elem_size;
+  if (overlaps(d_q, d_rhs, bytes)) return fail(DG_ERR_ARG, "dg_rhs: d_q and d_rhs overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t err;
+  if (op->precision == DG_FP32) {
+    dgw::StageArgs<float> a = base_args<float>(op);
+    a.qin = static_cast<const float*>(d_q);
+    a.rhs = static_cast<float*>(d_rhs);
+    err = launch_order<float>(op, a, dgw::kModeRhs, s);
+  } else {
+    dgw::StageArgs<double> a = base_args<double>(op);
+    a.qin = static_cast<const double*>(d_q);
+    a.rhs = static_cast<double*>(d_rhs);
+    err = launch_order<double>(op, a, dgw::kModeRhs, s);
+  }
+  if (err != cudaSuccess) return cuda_fail(err, "dg_rhs: kernel launch");
+  op->launches.fetch_add(1, std::memory_order_relaxed);
+  return DG_OK;
+}
+
+extern "C" dg_status dg_step(const dg_op* op, void* d_q, void* d_res, double t0, double dt,
+                             int32_t nsteps, void* stream) {
+  dgw::clear_error();
+  (void)t0;
+  dg_status st = check_device_op(op, "dg_step");
+  if (st) return st;
+  if ((st = check_field(op, d_q, "d_q", "dg_step"))) return st;
+  if ((st = check_field(op, d_res, "d_res", "dg_step"))) return st;
+  if (nsteps < 0) return fail(DG_ERR_ARG, "dg_step: nsteps = %d < 0", nsteps);
+  if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dg_step: dt is not finite");
+  const size_t bytes = 3 * op->fstride * op->elem_size;
+  if (overlaps(d_q, d_res, bytes)) return fail(DG_ERR_ARG, "dg_step: d_q and d_res overlap");
+  if (overlaps(d_q, op->d_qtmp, bytes) || overlaps(d_res, op->d_qtmp, bytes))
+    return fail(DG_ERR_ARG, "dg_step: buffer overlaps the operator's internal buffer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (op->precision == DG_FP32)
+    return run_steps<float>(op, static_cast<float*>(d_q), static_cast<float*>(d_res), dt, nsteps,
+                            s);
+  return run_steps<double>(op, static_cast<double*>(d_q), static_cast<double*>(d_res), dt, nsteps,
+                           s);
+}
+
+extern "C" dg_status dg_solve(const dg_op* op, void* d_q, void* d_res, double T, double dt,
+                              int32_t* nsteps_out, double* t_reached, void* stream) {
+  dgw::clear_error();
+  if (!op) return fail(DG_ERR_ARG, "dg_solve: NULL operator");
+  if (!(T >= 0) || !std::isfinite(T)) return fail(DG_ERR_ARG, "dg_solve: bad final time");
+  if (!(dt > 0)) {
+    dg_status st = dg_cfl_dt(op, 1.0, &dt);
+    if (st) return st;
+  }
+  const double ns = std::ceil(T / dt - 1e-12);
+  if (ns > 2147483647.0) return fail(DG_ERR_ARG, "dg_solve: too many steps");
+  const int32_t nsteps = static_cast<int32_t>(std::max(0.0, ns));
+  const double dts = nsteps > 0 ? T / nsteps : 0.0;
+  dg_status st = dg_step(op, d_q, d_res, 0.0, dts, nsteps, stream);
+  if (st) return st;
+  if (nsteps_out) *nsteps_out = nsteps;
+  if (t_reached) *t_reached = nsteps * dts;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_step_host(const dg_op* op, void* h_q, void* d_q, void* d_res, double t0,
+                                  double dt, int32_t nsteps, void* stream) {
+  dgw::clear_error();
+  dg_status st = check_device_op(op, "dg_step_host");
+  if (st) return st;
+  if (!h_q) return fail(DG_ERR_ARG, "dg_step_host: h_q is NULL");
+  if ((st = check_field(op, d_q, "d_q", "dg_step_host"))) return st;
+  if ((st = check_field(op, d_res, "d_res", "dg_step_host"))) return st;
+  if (nsteps < 0 || !std::isfinite(dt)) return fail(DG_ERR_ARG, "dg_step_host: bad nsteps/dt");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = 3 * op->fstride * op->elem_size;
+  cudaError_t err = cudaMemcpyAsync(d_q, h_q, bytes, cudaMemcpyHostToDevice, s);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_step_host: host-to-device copy");
+  st = dg_step(op, d_q, d_res, t0, dt, nsteps, stream);
+  if (st) return st;
+  err = cudaMemcpyAsync(h_q, d_q, bytes, cudaMemcpyDeviceToHost, s);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_step_host: device-to-host copy");
+  err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_step_host: synchronize");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_check_finite(const dg_op* op, const void* d_q, void* stream) {
+  dgw::clear_error();
+  dg_status st = check_device_op(op, "dg_check_finite");
+  if (st) return st;
+  if ((st = check_field(op, d_q, "d_q", "dg_check_finite"))) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t err = cudaMemsetAsync(op->d_flag, 0, sizeof(int), s);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_check_finite: memset");
+  const int64_t n = op->K * op->Np;
+  const int threads = 256;
+  const int64_t want = (3 * n + threads - 1) / threads;
+  const int blocks = static_cast<int>(std::min<int64_t>(want, 8LL * std::max(op->num_sms, 1)));
+  if (op->precision == DG_FP32)
+    finite_scan_kernel<<<blocks, threads, 0, s>>>(static_cast<const float*>(d_q), nullptr,
+                                                  op->fstride, n, op->d_flag);
+  else
+    finite_scan_kernel<<<blocks, threads, 0, s>>>(nullptr, static_cast<const double*>(d_q),
+                                                  op->fstride, n, op->d_flag);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "dg_check_finite: launch");
+  op->launches.fetch_add(1, std::memory_order_relaxed);
+  int flag = 0;
+  err = cudaMemcpyAsync(&flag, op->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_check_finite: copy");
+  err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_check_finite: synchronize");
+  if (flag) return fail(DG_ERR_NONFINITE, "dg_check_finite: field holds NaN or Inf");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_sync_check(const dg_op* op, void* stream) {
+  dgw::clear_error();
+  dg_status st = check_device_op(op, "dg_sync_check");
+  if (st) return st;
+  cudaError_t err = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (err == cudaSuccess) err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "dg_sync_check");
+  return DG_OK;
+}
+
+extern "C" int64_t dg_launch_count(const dg_op* op) {
+  return op ? op->launches.load(std::memory_order_relaxed) : 0;
+}
+
+extern "C" const char* dg_last_error(void) { return dgw::last_error_cstr(); }

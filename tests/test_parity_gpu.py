@@ -1,0 +1,210 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (max nodal error relative to the max |value| of the compared
+quantity): FP64 runs <= 1e-12, FP32 runs <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import (cavity_mode, gaussian_pulse, jittered_delaunay_mesh, random_fields,
+                   square_grid_mesh)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1304_5546_gb300 import build as B
+    B.build()
+    import paper_1304_5546_gb300 as P
+    return P
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _solver(P, mesh, N, prec):
+    return P.Solver(*mesh, N=N, precision=prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("N", list(range(1, 8)))
+def test_rhs_parity_random_fields(P, N, prec):
+    # 2 * 9^2 = 162 elements: several CTAs and a ragged last block at every N
+    mesh = jittered_delaunay_mesh(9, seed=100 + N)
+    d = O.Discretization(*mesh, N)
+    q = random_fields(d.K, d.Np, seed=N)
+    want = O.maxwell_rhs(d, q)
+    s = _solver(P, mesh, N, prec)
+    got = s.to_numpy(s.rhs(s.from_numpy(q)))
+    P.dg_sync_check(s.op)
+    assert _rel(got, want) <= TOL[prec], _rel(got, want)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("N", [1, 3, 5, 7])
+def test_lsrk_steps_parity(P, N, prec):
+    mesh = jittered_delaunay_mesh(8, seed=7 * N)
+    d = O.Discretization(*mesh, N)
+    q0 = np.stack(gaussian_pulse(d.x, d.y, 0.5, 0.5, 0.15))
+    dt = O.cfl_dt(d)
+    want = q0
+    for n in range(3):
+        want = O.lsrk_step(d, want, n * dt, dt)
+    s = _solver(P, mesh, N, prec)
+    q = s.from_numpy(q0)
+    res = s.new_fields()
+    s.step(q, res, dt, nsteps=3)
+    got = s.to_numpy(q)
+    P.dg_sync_check(s.op)
+    assert _rel(got, want) <= TOL[prec], _rel(got, want)
+
+
+@pytest.mark.parametrize("nsteps", [0, 1, 2])
+def test_step_counts_and_residual(P, nsteps):
+    # odd/even step counts (ping-pong copy-back) and the residual of the last stage
+    mesh = jittered_delaunay_mesh(6, seed=3)
+    N = 4
+    d = O.Discretization(*mesh, N)
+    q0 = random_fields(d.K, d.Np, seed=11)
+    dt = 0.5 * O.cfl_dt(d)
+    want = q0
+    res_want = np.zeros_like(q0)
+    for n in range(nsteps):
+        for i in range(5):
+            want, res_want = O.lsrk_stage(d, want, res_want, i, 0.0, dt)
+    s = _solver(P, mesh, N, "fp64")
+    q = s.from_numpy(q0)
+    res = s.new_fields()
+    s.step(q, res, dt, nsteps=nsteps)
+    assert _rel(s.to_numpy(q), want) <= 1e-12
+    if nsteps:
+        assert _rel(s.to_numpy(res), res_want) <= 1e-12
+
+
+def test_config1_cavity_fp64(P):
+    # [-1,1]^2, 8x8 squares x 2 (K = 128), N = 4, FP64, T = 1, CFL dt
+    mesh = square_grid_mesh(8, 8)
+    d = O.Discretization(*mesh, 4)
+    q0 = np.stack(cavity_mode(d.x, d.y, 0.0))
+    dt = O.cfl_dt(d)
+    want, t = O.solve(d, q0, 1.0, dt)
+    s = _solver(P, mesh, 4, "fp64")
+    q = s.from_numpy(q0)
+    res = s.new_fields()
+    nsteps, t_gpu = s.solve(q, res, 1.0, 0.0)
+    got = s.to_numpy(q)
+    assert nsteps == int(np.ceil(1.0 / dt - 1e-12)) and abs(t_gpu - 1.0) < 1e-12
+    assert _rel(got, want) <= 1e-12
+    exact = np.stack(cavity_mode(d.x, d.y, 1.0))
+    assert np.abs(got - exact).max() < 2.0e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tiny_meshes(P, prec):
+    # K = 1 (all faces PEC), K = 2 and K = 3 at every order
+    meshes = [
+        (np.array([0.0, 1.0, 0.2]), np.array([0.0, 0.1, 0.9]), np.array([[0, 1, 2]])),
+        square_grid_mesh(1, 1),
+        (np.array([0.0, 1.0, 0.0, 1.0, 2.0]), np.array([0.0, 0.0, 1.0, 1.0, 0.5]),
+         np.array([[0, 1, 3], [0, 3, 2], [1, 4, 3]])),
+    ]
+    for mesh in meshes:
+        for N in range(1, 8):
+            d = O.Discretization(*mesh, N)
+            q = random_fields(d.K, d.Np, seed=N)
+            s = _solver(P, mesh, N, prec)
+            got = s.to_numpy(s.rhs(s.from_numpy(q)))
+            assert _rel(got, O.maxwell_rhs(d, q)) <= TOL[prec]
+
+
+def test_clockwise_and_relabelled_input(P):
+    from synth import relabel_mesh
+    VX, VY, EToV = jittered_delaunay_mesh(7, seed=5)
+    E2, _, _ = relabel_mesh(EToV, seed=9)
+    E2[::3] = E2[::3][:, [0, 2, 1]]
+    mesh = (VX, VY, E2)
+    d = O.Discretization(*mesh, 5)
+    q = random_fields(d.K, d.Np, seed=2)
+    s = _solver(P, mesh, 5, "fp64")
+    got = s.to_numpy(s.rhs(s.from_numpy(q)))
+    assert _rel(got, O.maxwell_rhs(d, q)) <= 1e-12
+
+
+def test_energy_decays_on_gpu(P):
+    mesh = jittered_delaunay_mesh(10, seed=4)
+    N = 3
+    d = O.Discretization(*mesh, N)
+    s = _solver(P, mesh, N, "fp64")
+    q = s.from_numpy(random_fields(d.K, d.Np, seed=4))
+    res = s.new_fields()
+    dt = O.cfl_dt(d)
+    e_prev = O.energy(d, s.to_numpy(q))
+    for _ in range(10):
+        s.step(q, res, dt, nsteps=1)
+        e = O.energy(d, s.to_numpy(q))
+        assert e <= e_prev * (1 + 1e-13)
+        e_prev = e
+
+
+def test_check_finite_and_errors(P):
+    from paper_1304_5546_gb300 import _lib
+    mesh = jittered_delaunay_mesh(4, seed=1)
+    s = _solver(P, mesh, 3, "fp32")
+    q = s.new_fields()
+    P.dg_check_finite(s.op, q)
+    s.view(q)[2, 5, 3] = float("nan")
+    with pytest.raises(P.DGError) as ei:
+        P.dg_check_finite(s.op, q)
+    assert ei.value.status == _lib.DG_ERR_NONFINITE
+    # overlapping buffers are refused before any launch
+    n0 = P.dg_launch_count(s.op)
+    with pytest.raises(P.DGError) as ei:
+        P.dg_rhs(s.op, q, q)
+    assert ei.value.status == _lib.DG_ERR_ARG
+    with pytest.raises(P.DGError):
+        P.dg_step(s.op, q, q, 0.0, 0.1, 1)
+    with pytest.raises(P.DGError):
+        P.dg_step(s.op, q, s.new_fields(), 0.0, 0.1, -1)
+    assert P.dg_launch_count(s.op) == n0
+
+
+def test_step_host_matches_device_step(P):
+    import torch
+    mesh = jittered_delaunay_mesh(12, seed=8)
+    s = _solver(P, mesh, 5, "fp32")
+    d = O.Discretization(*mesh, 5)
+    q0 = np.stack(gaussian_pulse(d.x, d.y, 0.5, 0.5, 0.1))
+    dt = s.cfl_dt()
+    qd = s.from_numpy(q0)
+    res = s.new_fields()
+    s.step(qd, res, dt, nsteps=2)
+    h = s.from_numpy(q0).cpu().pin_memory()
+    P.dg_step_host(s.op, h, s.new_fields(), s.new_fields(), 0.0, dt, 2)
+    assert torch.equal(h.cuda(), qd)
+
+
+def test_full_size_one_step_fp32(P):
+    # the benchmark workload: ~1.0M-element jittered Delaunay mesh, N = 5,
+    # FP32, Gaussian pulse (width 0.05) at (0.5, 0.5); one LSRK step in the
+    # launch configuration the benchmark times, every element compared.
+    mesh = jittered_delaunay_mesh(707, seed=2024)
+    N = 5
+    d = O.Discretization(*mesh, N)
+    q0 = np.stack(gaussian_pulse(d.x, d.y))
+    s = _solver(P, mesh, N, "fp32")
+    dt = s.cfl_dt()
+    q = s.from_numpy(q0)
+    res = s.new_fields()
+    rhs = s.to_numpy(s.rhs(q))
+    assert _rel(rhs, O.maxwell_rhs(d, q0)) <= TOL["fp32"]
+    s.step(q, res, dt, nsteps=1)
+    want = O.lsrk_step(d, q0, 0.0, dt)
+    assert _rel(s.to_numpy(q), want) <= TOL["fp32"]
