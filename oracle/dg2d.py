@@ -375,12 +375,15 @@ class Discretization:
         self.y = 0.5 * (-np.outer(self.VY[va], r + s) + np.outer(self.VY[vb], 1 + r)
                         + np.outer(self.VY[vc], 1 + s))
 
-        # geometric factors by differentiating the map (Eq.
-        # dg-diff-local-to-global needs the inverse Jacobian entries)
-        xr = self.x @ R.Dr.T
-        xs = self.x @ R.Ds.T
-        yr = self.y @ R.Dr.T
-        ys = self.y @ R.Ds.T
+        # geometric factors: entries of A_k of the affine map
+        # Psi(r, s) = A_k (r, s)^T + b_k and of its inverse (Eq.
+        # dg-diff-local-to-global), taken straight from the map's definition
+        # (constant on each element)
+        ones = np.ones(self.Np)
+        xr = np.outer(0.5 * (self.VX[vb] - self.VX[va]), ones)
+        xs = np.outer(0.5 * (self.VX[vc] - self.VX[va]), ones)
+        yr = np.outer(0.5 * (self.VY[vb] - self.VY[va]), ones)
+        ys = np.outer(0.5 * (self.VY[vc] - self.VY[va]), ones)
         J = xr * ys - xs * yr
         if np.any(J <= 0):
             raise MeshError("non-positive Jacobian")
