@@ -195,10 +195,14 @@ def test_full_size_one_step_fp32(P):
     # the benchmark workload: ~1.0M-element jittered Delaunay mesh, N = 5,
     # FP32, Gaussian pulse (width 0.05) at (0.5, 0.5); one LSRK step in the
     # launch configuration the benchmark times, every element compared.
+    # Both sides get the FP32-representable pulse the solver actually holds:
+    # on this mesh the rhs operator has norm ~ N^2 / h ~ 3.5e4, so rounding
+    # the input alone to FP32 moves the exact rhs by ~1e-4 relative, which
+    # is not an error of the arithmetic under test.
     mesh = jittered_delaunay_mesh(707, seed=2024)
     N = 5
     d = O.Discretization(*mesh, N)
-    q0 = np.stack(gaussian_pulse(d.x, d.y))
+    q0 = np.stack(gaussian_pulse(d.x, d.y)).astype(np.float32).astype(np.float64)
     s = _solver(P, mesh, N, "fp32")
     dt = s.cfl_dt()
     q = s.from_numpy(q0)
