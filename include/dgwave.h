@@ -71,6 +71,7 @@ typedef int32_t dg_status;
 #define DG_ERR_OOM 6                /* device or host allocation failed      */
 #define DG_ERR_NONFINITE 7          /* NaN or Inf found in a field           */
 #define DG_ERR_NO_DEVICE 8          /* operator was set up host-only         */
+#define DG_ERR_TIMEOUT 9            /* a kernel's bounded wait expired       */
 
 #define DG_FP64 0
 #define DG_FP32 1
@@ -168,8 +169,9 @@ void dg_op_destroy(dg_op* op);
  * for the three fields in d_q: volume derivative (Dr/Ds + chain rule),
  * face-trace gather with the upwind flux (PEC: Ez+ = -Ez-, H+ = H-), LIFT
  * apply with the factor Fscale/2.  d_q and d_rhs are device field buffers
- * of the operator's precision (3 * field_stride values each) and must not
- * overlap.  t is accepted for interface symmetry (the system is
+ * of the operator's precision (3 * field_stride values each, 16-byte
+ * aligned; the kernels read whole per-block chunks with bulk copies) and
+ * must not overlap.  t is accepted for interface symmetry (the system is
  * autonomous).  Enqueued on `stream`.
  * Errors: DG_ERR_ARG (NULL / overlapping / misaligned buffers),
  * DG_ERR_NO_DEVICE, DG_ERR_CUDA (launch failure).                          */
@@ -211,7 +213,9 @@ dg_status dg_step_host(const dg_op* op, void* h_q, void* d_q, void* d_res, doubl
 dg_status dg_check_finite(const dg_op* op, const void* d_q, void* stream);
 
 /* dg_sync_check: synchronises `stream` and reports any pending CUDA error
- * (DG_ERR_CUDA with its message in dg_last_error()).                      */
+ * (DG_ERR_CUDA with its message in dg_last_error()), then reads and clears
+ * the operator's kernel status word: DG_ERR_TIMEOUT if a stage kernel gave
+ * up waiting for its own shared-memory copies (bounded waits, ~2 s).       */
 dg_status dg_sync_check(const dg_op* op, void* stream);
 
 /* Number of kernel launches enqueued by this operator since setup (one per

@@ -20,6 +20,7 @@ DG_ERR_CUDA = 5
 DG_ERR_OOM = 6
 DG_ERR_NONFINITE = 7
 DG_ERR_NO_DEVICE = 8
+DG_ERR_TIMEOUT = 9
 DG_FP64 = 0
 DG_FP32 = 1
 DG_SETUP_HOST_ONLY = 1
@@ -28,7 +29,7 @@ DG_N_MAX = 7
 _STATUS_NAMES = {
     0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_MESH_DEGENERATE", 3: "DG_ERR_MESH_NONCONFORMING",
     4: "DG_ERR_ORDER", 5: "DG_ERR_CUDA", 6: "DG_ERR_OOM", 7: "DG_ERR_NONFINITE",
-    8: "DG_ERR_NO_DEVICE",
+    8: "DG_ERR_NO_DEVICE", 9: "DG_ERR_TIMEOUT",
 }
 
 c_void_p = ctypes.c_void_p

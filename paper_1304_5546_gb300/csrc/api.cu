@@ -36,13 +36,16 @@ struct dg_op {
   void* d_conn = nullptr;
   void* d_qtmp = nullptr;  // second field buffer for the stage ping-pong
   int* d_flag = nullptr;   // finiteness scan result
+  int* d_status = nullptr; // kernel status word (bounded-wait expiry)
   double lsrk_a[5], lsrk_b[5], lsrk_c[5];
   mutable std::atomic<int64_t> launches{0};
 };
 
 namespace {
 
-constexpr int64_t kBlockPad = 64;  // K is padded to whole blocks of <= 64 elements
+// K is padded to whole blocks of <= 64 elements plus at least one spare
+// element: the kernels' bulk copies round each block's chunks up to 16 bytes
+constexpr int64_t kBlockPad = 64;
 
 dg_status cuda_fail(cudaError_t err, const char* where) {
   return fail(err == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA, "%s: %s (%s)", where,
@@ -50,11 +53,13 @@ dg_status cuda_fail(cudaError_t err, const char* where) {
 }
 
 void free_device(dg_op* op) {
-  void* ptrs[] = {op->d_Dr, op->d_Ds, op->d_LIFT, op->d_geo, op->d_conn, op->d_qtmp, op->d_flag};
+  void* ptrs[] = {op->d_Dr,   op->d_Ds,   op->d_LIFT,  op->d_geo,
+                  op->d_conn, op->d_qtmp, op->d_flag, op->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   op->d_Dr = op->d_Ds = op->d_LIFT = op->d_geo = op->d_conn = op->d_qtmp = nullptr;
   op->d_flag = nullptr;
+  op->d_status = nullptr;
 }
 
 template <typename T>
@@ -102,6 +107,10 @@ dg_status upload(dg_op* op) {
   if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMemset");
   err = cudaMalloc(&op->d_flag, sizeof(int));
   if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(flag)");
+  err = cudaMalloc(&op->d_status, sizeof(int));
+  if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(status)");
+  err = cudaMemset(op->d_status, 0, sizeof(int));
+  if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMemset(status)");
   (void)Np;
   (void)Nafp;
   return DG_OK;
@@ -131,6 +140,7 @@ dgw::StageArgs<T> base_args(const dg_op* op) {
   a.Dr = static_cast<const T*>(op->d_Dr);
   a.Ds = static_cast<const T*>(op->d_Ds);
   a.LIFT = static_cast<const T*>(op->d_LIFT);
+  a.status = op->d_status;
   return a;
 }
 
@@ -151,8 +161,8 @@ bool overlaps(const void* a, const void* b, size_t bytes) {
 
 dg_status check_field(const dg_op* op, const void* p, const char* name, const char* where) {
   if (!p) return fail(DG_ERR_ARG, "%s: %s is NULL", where, name);
-  if (reinterpret_cast<uintptr_t>(p) % op->elem_size != 0)
-    return fail(DG_ERR_ARG, "%s: %s is not %zu-byte aligned", where, name, op->elem_size);
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0)
+    return fail(DG_ERR_ARG, "%s: %s is not 16-byte aligned", where, name);
   return DG_OK;
 }
 
@@ -221,7 +231,7 @@ extern "C" dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t p
     op->flags = flags;
     op->elem_size = (precision == DG_FP32) ? 4 : 8;
     op->K = mesh->K;
-    op->Kpad = (mesh->K + kBlockPad - 1) / kBlockPad * kBlockPad;
+    op->Kpad = (mesh->K + 1 + kBlockPad - 1) / kBlockPad * kBlockPad;
     // whole blocks, and every field 256-byte aligned (64 values)
     op->fstride = (op->Kpad * op->Np + 63) / 64 * 64;
     op->geo = dgw::build_geometry(*mesh, op->ref);
@@ -475,6 +485,13 @@ extern "C" dg_status dg_sync_check(const dg_op* op, void* stream) {
   cudaError_t err = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (err == cudaSuccess) err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(err, "dg_sync_check");
+  int status = 0;
+  err = cudaMemcpy(&status, op->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_sync_check: status read");
+  if (status != 0) {
+    cudaMemset(op->d_status, 0, sizeof(int));
+    return fail(DG_ERR_TIMEOUT, "dg_sync_check: a kernel's bounded wait expired");
+  }
   return DG_OK;
 }
 

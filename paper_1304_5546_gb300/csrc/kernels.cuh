@@ -8,16 +8,27 @@
 // depending on MODE, writes it out or applies one stage of the 2N-storage
 // LSRK(5,4) update res <- a res + dt rhs, q_out <- q_in + b res.
 //
-// Work decomposition: a CTA owns a block of E consecutive elements and has
-// one thread per (element, output node).  The CTAs are persistent and loop
-// over element blocks.  Each thread keeps its rows of Dr, Ds and LIFT in
-// registers for the whole launch (loaded once), so the element-local
-// matrix-vector products read only the field vectors, which sit in shared
-// memory and are read as 16-byte vectors broadcast to all threads of an
-// element.  Volume terms use the algebraically equal form
+// Work decomposition.  The grid is persistent; a CTA walks element blocks
+// blk = blockIdx.x + it * gridDim.x of E consecutive elements, one thread
+// per (element, output node).  Each thread keeps its rows of Dr, Ds and LIFT
+// in registers for the whole launch, so the element-local products read
+// only field vectors, from shared memory, as 16-byte vectors broadcast to
+// the threads of an element.  The volume term uses the algebraically equal
 //   dEz/dt = Dr (rx Hy - ry Hx) + Ds (sx Hy - sy Hx)
-// (geometric factors are constant on an affine element), which needs four
-// products per node instead of six.
+// (geometric factors are constant on an affine element): four products per
+// node instead of six.  Operands are centred on the element's node 0
+// (Dr 1 = Ds 1 = 0), which removes FP32 cancellation for smooth fields.
+//
+// Memory pipeline.  Everything a block owns is contiguous in HBM (its q and
+// residual values per field, its geometry records and face codes), so it is
+// fetched by 1D TMA bulk copies into a ring of kStages shared-memory stage
+// buffers, completion tracked by one mbarrier per stage; loads for block
+// it + kStages are issued while block it computes.  The neighbour traces a
+// block needs are gathered into registers one iteration ahead (their
+// addresses come from the next stage's face codes), so their L2 latency
+// hides behind the current block's products.  Every mbarrier wait is bounded
+// (about two seconds); on expiry the CTA sets the status word, waits
+// (bounded) for its own copies in flight and returns.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,16 +46,20 @@ struct Order {
   static constexpr int Nafp = 3 * (N + 1);
 };
 
-// elements per CTA (E * Np threads).  ptxas budgets registers for the CTA
-// rounded up to 4 warps, so E keeps E * Np <= 512 from N = 4 on: each
-// thread then has up to 128 registers for its matrix rows (2 Np + Nafp
-// values) without spilling.
+// Elements per block.  A multiple of 4, so every per-block chunk (E Np
+// values, E geometry records, E face-code triples) is a whole number of
+// 16-byte units as TMA requires; E Np <= 512 from N = 4 on, because ptxas
+// budgets registers for the CTA rounded up to 4 warps and each thread needs
+// 2 Np + Nafp registers for its matrix rows.
 template <typename T, int N>
 constexpr int elems_per_block() {
-  constexpr int e32[8] = {0, 64, 32, 32, 32, 24, 18, 14};
-  constexpr int e64[8] = {0, 32, 16, 16, 16, 12, 9, 7};
+  constexpr int e32[8] = {0, 64, 32, 32, 32, 24, 16, 12};
+  constexpr int e64[8] = {0, 32, 16, 16, 16, 12, 8, 8};
   return sizeof(T) == 8 ? e64[N] : e32[N];
 }
+
+constexpr int kStages = 3;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // ~2 s per wait
 
 template <typename T>
 struct Vec16;
@@ -64,22 +79,97 @@ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
 template <typename T, int N>
 struct Layout {
   static constexpr int Np = Order<N>::Np;
+  static constexpr int Nfp = Order<N>::Nfp;
   static constexpr int Nafp = Order<N>::Nafp;
   static constexpr int E = elems_per_block<T, N>();
   static constexpr int VW = Vec16<T>::width;
   static constexpr int NPAD = round_up(Np, VW);
   static constexpr int FPAD = round_up(Nafp, VW);
   static constexpr int THREADS = E * Np;
-  // shared: Hx, Hy, Ez (raw, for the traces); Ez - Ez_0,
-  // A = rx (Hy - Hy_0) - ry (Hx - Hx_0), B = sx (Hy - Hy_0) - sy (Hx - Hx_0)
-  // (centred on the element's node 0, for the volume products); 3 fluxes
-  static constexpr int SMEM_ELEMS = 6 * E * NPAD + 3 * E * FPAD;
-  static constexpr size_t SMEM_BYTES = sizeof(T) * SMEM_ELEMS;
+  static constexpr int TASKS = E * Nafp;                       // flux tasks per block
+  static constexpr int TPT = (TASKS + THREADS - 1) / THREADS;  // per thread
+  // stage buffer: q[3][E Np], res[3][E Np], geo[E][kGeo], conn[E][3]
+  static constexpr int QB = E * Np * static_cast<int>(sizeof(T));
+  static constexpr int GB = E * kGeo * static_cast<int>(sizeof(T));
+  static constexpr int CB = E * 3 * 4;
+  static constexpr int STAGE_BYTES = round_up(6 * QB + GB + CB, 128);
+  // double-buffered work arrays: centred volume operands and lifted fluxes
+  static constexpr int W_ELEMS = 3 * E * NPAD;
+  static constexpr int F_ELEMS = 3 * E * FPAD;
+  static constexpr int HEADER = 128;  // mbarriers
+  static constexpr size_t SMEM_BYTES =
+      HEADER + kStages * STAGE_BYTES + 2 * sizeof(T) * (W_ELEMS + F_ELEMS);
+  static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0, "16-byte TMA chunks");
 };
 
 __host__ __device__ constexpr int face_node_dev(int N, int f, int j) {
   return f == 0 ? j
                 : (f == 1 ? j * (N + 1) - j * (j - 1) / 2 + (N - j) : j * (N + 1) - j * (j - 1) / 2);
+}
+
+// ------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 1D bulk copy global -> this CTA's shared memory, completing on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of `bar`; false if it has not completed in limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
 }
 
 template <typename T, int W>
@@ -88,26 +178,66 @@ __device__ __forceinline__ void load_vec(T (&dst)[W], const T* src) {
   *reinterpret_cast<V*>(dst) = *reinterpret_cast<const V*>(src);
 }
 
+__host__ __device__ constexpr uint32_t round16(uint32_t x) { return (x + 15u) & ~15u; }
+
+// ------------------------------------------------------------ kernel
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(Layout<T, N>::THREADS)
     dg_stage_kernel(const StageArgs<T> p) {
   using L = Layout<T, N>;
-  constexpr int Np = L::Np, Nfp = Order<N>::Nfp, Nafp = L::Nafp;
+  constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp;
   constexpr int E = L::E, NPAD = L::NPAD, FPAD = L::FPAD, VW = L::VW;
-  constexpr int THREADS = L::THREADS;
+  constexpr int THREADS = L::THREADS, TASKS = L::TASKS, TPT = L::TPT;
+  constexpr int NQ = (MODE == kModeStage) ? 6 : 3;  // field chunks fetched per block
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sHx = reinterpret_cast<T*>(smem_raw);
-  T* sHy = sHx + E * NPAD;
-  T* sEz = sHy + E * NPAD;
-  T* sA = sEz + E * NPAD;
-  T* sB = sA + E * NPAD;
-  T* sEc = sB + E * NPAD;
-  T* sF = sEc + E * NPAD;  // 3 x E x FPAD
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  unsigned char* stages = smem + L::HEADER;
+  T* Wbuf = reinterpret_cast<T*>(stages + kStages * L::STAGE_BYTES);  // [2][3][E][NPAD]
+  T* Fbuf = Wbuf + 2 * L::W_ELEMS;                                    // [2][3][E][FPAD]
 
   const int t = threadIdx.x;
   const int e = t / Np;
   const int i = t - e * Np;
+
+  const int64_t K = p.K;
+  const int64_t fs = p.fstride;
+  const int64_t nblk = (K + E - 1) / E;
+  const int64_t G = gridDim.x;
+  const int64_t first = blockIdx.x;
+  const int64_t niter = first < nblk ? (nblk - 1 - first) / G + 1 : 0;
+
+  if (t == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // thread 0: fetch everything block `it` owns into stage it % kStages
+  auto issue = [&](int64_t it) {
+    const int s = static_cast<int>(it % kStages);
+    const int64_t k0 = (first + it * G) * E;
+    const int64_t n = (K - k0) < E ? (K - k0) : E;
+    const uint32_t qb = round16(static_cast<uint32_t>(n * Np * sizeof(T)));
+    const uint32_t gb = round16(static_cast<uint32_t>(n * kGeo * sizeof(T)));
+    const uint32_t cb = round16(static_cast<uint32_t>(n * 3 * 4));
+    unsigned char* st = stages + s * L::STAGE_BYTES;
+    mbar_expect_tx(&bars[s], NQ * qb + gb + cb);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) tma_load_1d(st + f * L::QB, p.qin + f * fs + k0 * Np, qb, &bars[s]);
+    if (MODE == kModeStage) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+        tma_load_1d(st + (3 + f) * L::QB, p.res + f * fs + k0 * Np, qb, &bars[s]);
+    }
+    tma_load_1d(st + 6 * L::QB, p.geo + k0 * kGeo, gb, &bars[s]);
+    tma_load_1d(st + 6 * L::QB + L::GB, p.conn + k0 * 3, cb, &bars[s]);
+  };
+
+  int64_t issued = 0;  // (thread 0) iterations whose loads were issued
+  if (t == 0) {
+    for (; issued < niter && issued < kStages; ++issued) issue(issued);
+  }
 
   // this thread's rows of Dr, Ds and LIFT, kept in registers
   T dr[Np], ds[Np], lf[Nafp];
@@ -119,95 +249,133 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
 #pragma unroll
   for (int j = 0; j < Nafp; ++j) lf[j] = __ldg(p.LIFT + i * Nafp + j);
 
-  const int64_t K = p.K;
-  const int64_t nblk = (K + E - 1) / E;
-  const int64_t fs = p.fstride;
+  // neighbour traces of this thread's flux tasks, one block ahead
+  T trc[TPT][3];
+  auto gather = [&](int64_t it) {
+    const int s = static_cast<int>(it % kStages);
+    const int32_t* sc =
+        reinterpret_cast<const int32_t*>(stages + s * L::STAGE_BYTES + 6 * L::QB + L::GB);
+    const int64_t k0 = (first + it * G) * E;
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const int tau = t + u * THREADS;
+      trc[u][0] = trc[u][1] = trc[u][2] = T(0);
+      if (tau < TASKS) {
+        const int ee = tau / Nafp;
+        const int j = tau - ee * Nafp;
+        const int f = j / Nfp;
+        const int jj = j - f * Nfp;
+        if (k0 + ee < K) {
+          const int32_t code = sc[ee * 3 + f];
+          if (code >= 0) {
+            const int64_t kP = code >> 3;
+            const int fP = (code >> 1) & 3;
+            const int jP = (code & 1) ? (N - jj) : jj;
+            const int64_t gP = kP * Np + face_node_dev(N, fP, jP);
+            trc[u][0] = __ldg(p.qin + gP);
+            trc[u][1] = __ldg(p.qin + fs + gP);
+            trc[u][2] = __ldg(p.qin + 2 * fs + gP);
+          }
+        }
+      }
+    }
+  };
 
-  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    const int64_t k0 = blk * E;
+  bool ok = true;
+  if (niter > 0) {
+    ok = mbar_wait_bounded(&bars[0], 0, kWaitLimitNs);
+    if (ok) gather(0);
+  }
+
+  int64_t it = 0;
+  for (; it < niter; ++it) {
+    const int s = static_cast<int>(it % kStages);
+    const uint32_t parity = static_cast<uint32_t>((it / kStages) & 1);
+    if (ok) ok = mbar_wait_bounded(&bars[s], parity, kWaitLimitNs);
+    const int64_t k0 = (first + it * G) * E;
     const int64_t k = k0 + e;
     const bool valid = k < K;
     const int64_t g = k0 * Np + t;  // == k * Np + i
+    const unsigned char* st = stages + s * L::STAGE_BYTES;
+    const T* sq = reinterpret_cast<const T*>(st);
+    const T* sg = reinterpret_cast<const T*>(st + 6 * L::QB);
+    const int32_t* sc = reinterpret_cast<const int32_t*>(st + 6 * L::QB + L::GB);
+    T* Wb = Wbuf + (it & 1) * L::W_ELEMS;
+    T* Fb = Fbuf + (it & 1) * L::F_ELEMS;
 
-    // ---- phase 1: own nodal values, residual, geometry
-    T hx = 0, hy = 0, ez = 0, r0 = 0, r1 = 0, r2 = 0;
-    T rx = 0, ry = 0, sx = 0, sy = 0;
-    if (valid) {
-      hx = __ldg(p.qin + g);
-      hy = __ldg(p.qin + fs + g);
-      ez = __ldg(p.qin + 2 * fs + g);
+    // ---- phase 1: own values, residual, geometry; centred volume operands
+    T hx = 0, hy = 0, ez = 0, r0 = 0, r1 = 0, r2 = 0, rx = 0, ry = 0, sx = 0, sy = 0;
+    if (ok) {
+      hx = sq[t];
+      hy = sq[E * Np + t];
+      ez = sq[2 * E * Np + t];
       if (MODE == kModeStage) {
-        r0 = p.res[g];
-        r1 = p.res[fs + g];
-        r2 = p.res[2 * fs + g];
+        r0 = sq[3 * E * Np + t];
+        r1 = sq[4 * E * Np + t];
+        r2 = sq[5 * E * Np + t];
       }
-      const T* gk = p.geo + k * kGeo;
-      rx = __ldg(gk + 0);
-      ry = __ldg(gk + 1);
-      sx = __ldg(gk + 2);
-      sy = __ldg(gk + 3);
+      rx = sg[e * kGeo + 0];
+      ry = sg[e * kGeo + 1];
+      sx = sg[e * kGeo + 2];
+      sy = sg[e * kGeo + 3];
+      const T dhx = hx - sq[e * Np], dhy = hy - sq[E * Np + e * Np];
+      Wb[(0 * E + e) * NPAD + i] = ez - sq[2 * E * Np + e * Np];
+      Wb[(1 * E + e) * NPAD + i] = rx * dhy - ry * dhx;
+      Wb[(2 * E + e) * NPAD + i] = sx * dhy - sy * dhx;
     }
-    __syncthreads();  // previous block's readers of shared memory are done
-    sHx[e * NPAD + i] = hx;
-    sHy[e * NPAD + i] = hy;
-    sEz[e * NPAD + i] = ez;
-    __syncthreads();
+    if (__syncthreads_or(!ok)) break;
 
-    // ---- volume operands, centred on the element's node 0.  Dr 1 = Ds 1 = 0,
-    // so this changes nothing in exact arithmetic; in FP32 it removes the
-    // cancellation of O(|u|) products that sum to O(h |grad u|).
-    {
-      const T hx0 = sHx[e * NPAD], hy0 = sHy[e * NPAD], ez0 = sEz[e * NPAD];
-      const T dhx = hx - hx0, dhy = hy - hy0;
-      sEc[e * NPAD + i] = ez - ez0;
-      sA[e * NPAD + i] = rx * dhy - ry * dhx;
-      sB[e * NPAD + i] = sx * dhy - sy * dhx;
-    }
-
-    // ---- phase 2: face-trace gather and upwind flux, one task per face node
-    for (int tau = t; tau < E * Nafp; tau += THREADS) {
-      const int ee = tau / Nafp;
-      const int j = tau - ee * Nafp;
-      const int64_t kk = k0 + ee;
-      if (kk >= K) continue;
-      const int f = j / Nfp;
-      const int jj = j - f * Nfp;
-      const int nM = face_node_dev(N, f, jj);
-      const T hxM = sHx[ee * NPAD + nM];
-      const T hyM = sHy[ee * NPAD + nM];
-      const T ezM = sEz[ee * NPAD + nM];
-      const int32_t code = __ldg(p.conn + kk * 3 + f);
-      T dHx, dHy, dEz;
-      if (code < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
-        dHx = 0;
-        dHy = 0;
-        dEz = 2 * ezM;
-      } else {
-        const int64_t kP = code >> 3;
-        const int fP = (code >> 1) & 3;
-        const int jP = (code & 1) ? (N - jj) : jj;
-        const int64_t gP = kP * Np + face_node_dev(N, fP, jP);
-        dHx = hxM - __ldg(p.qin + gP);
-        dHy = hyM - __ldg(p.qin + fs + gP);
-        dEz = ezM - __ldg(p.qin + 2 * fs + gP);
+    // ---- phase 2: upwind flux at every face node, scaled by Fscale/2
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const int tau = t + u * THREADS;
+      if (tau < TASKS) {
+        const int ee = tau / Nafp;
+        const int j = tau - ee * Nafp;
+        if (k0 + ee < K) {
+          const int f = j / Nfp;
+          const int jj = j - f * Nfp;
+          const int nM = ee * Np + face_node_dev(N, f, jj);
+          const T hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
+          T dHx, dHy, dEz;
+          if (sc[ee * 3 + f] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
+            dHx = 0;
+            dHy = 0;
+            dEz = 2 * ezM;
+          } else {
+            dHx = hxM - trc[u][0];
+            dHy = hyM - trc[u][1];
+            dEz = ezM - trc[u][2];
+          }
+          const T* gf = sg + ee * kGeo + 4 + 3 * f;
+          const T nx = gf[0], ny = gf[1], fsc = gf[2];
+          const T ndotdH = nx * dHx + ny * dHy;
+          Fb[(0 * E + ee) * FPAD + j] = fsc * (ny * dEz + (ndotdH * nx - dHx));
+          Fb[(1 * E + ee) * FPAD + j] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
+          Fb[(2 * E + ee) * FPAD + j] = fsc * (ny * dHx - nx * dHy - dEz);
+        }
       }
-      const T* gk = p.geo + kk * kGeo + 4 + 3 * f;
-      const T nx = __ldg(gk + 0), ny = __ldg(gk + 1), fsc = __ldg(gk + 2);
-      const T ndotdH = nx * dHx + ny * dHy;
-      const T fHx = ny * dEz + (ndotdH * nx - dHx);
-      const T fHy = -nx * dEz + (ndotdH * ny - dHy);
-      const T fEz = ny * dHx - nx * dHy - dEz;
-      sF[(0 * E + ee) * FPAD + j] = fsc * fHx;
-      sF[(1 * E + ee) * FPAD + j] = fsc * fHy;
-      sF[(2 * E + ee) * FPAD + j] = fsc * fEz;
     }
-    __syncthreads();
+    // next block's traces: their addresses are in the next stage's codes
+    if (it + 1 < niter) {
+      const int s1 = static_cast<int>((it + 1) % kStages);
+      const uint32_t par1 = static_cast<uint32_t>(((it + 1) / kStages) & 1);
+      ok = mbar_wait_bounded(&bars[s1], par1, kWaitLimitNs);
+      if (ok) gather(it + 1);
+    }
+    if (__syncthreads_or(!ok)) break;
+    // stage s is no longer read: refill it with block it + kStages
+    if (t == 0 && issued < niter) {
+      fence_proxy_async();
+      issue(issued);
+      ++issued;
+    }
 
     // ---- phase 3: volume products, lift, stage update
     T dEzdr = 0, dEzds = 0, cEz = 0;
-    const T* pEz = sEc + e * NPAD;
-    const T* pA = sA + e * NPAD;
-    const T* pB = sB + e * NPAD;
+    const T* pEz = Wb + (0 * E + e) * NPAD;
+    const T* pA = Wb + (1 * E + e) * NPAD;
+    const T* pB = Wb + (2 * E + e) * NPAD;
 #pragma unroll
     for (int m0 = 0; m0 < Np; m0 += VW) {
       T vz[VW], va[VW], vb[VW];
@@ -224,9 +392,9 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
       }
     }
     T l0 = 0, l1 = 0, l2 = 0;
-    const T* pF0 = sF + (0 * E + e) * FPAD;
-    const T* pF1 = sF + (1 * E + e) * FPAD;
-    const T* pF2 = sF + (2 * E + e) * FPAD;
+    const T* pF0 = Fb + (0 * E + e) * FPAD;
+    const T* pF1 = Fb + (1 * E + e) * FPAD;
+    const T* pF2 = Fb + (2 * E + e) * FPAD;
 #pragma unroll
     for (int j0 = 0; j0 < Nafp; j0 += VW) {
       T f0[VW], f1[VW], f2[VW];
@@ -270,6 +438,15 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
         p.qout[2 * fs + g] = ez + p.b * n2;
       }
     }
+  }
+
+  if (it < niter && t == 0) {
+    // a wait expired: report, then let this CTA's copies in flight land
+    // (each wait bounded) before the CTA's shared memory is released
+    atomicExch(p.status, 1);
+    for (int64_t j = it; j < issued; ++j)
+      mbar_wait_bounded(&bars[j % kStages], static_cast<uint32_t>((j / kStages) & 1),
+                        kWaitLimitNs);
   }
 }
 

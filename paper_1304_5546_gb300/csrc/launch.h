@@ -25,6 +25,7 @@ struct StageArgs {
   const T* Ds = nullptr;          // Np x Np
   const T* LIFT = nullptr;        // Np x Nafp
   T a = 0, b = 0, dt = 0;
+  int* status = nullptr;  // set to 1 by a CTA whose bounded wait expired
 };
 
 enum StageMode : int { kModeRhs = 0, kModeFirstStage = 1, kModeStage = 2 };
