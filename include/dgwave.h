@@ -121,8 +121,9 @@ void dg_mesh_destroy(dg_mesh* mesh);
  * operator's precision (DG_FP32 or DG_FP64), to the current CUDA device.
  * The operator keeps its own copy of the mesh data; the mesh may be
  * destroyed afterwards.
- * Errors: DG_ERR_ARG, DG_ERR_ORDER (N < 1 or N > DG_N_MAX), DG_ERR_CUDA,
- * DG_ERR_OOM.  *out is written only on success.                           */
+ * Errors: DG_ERR_ARG (also when a field would hold 2^31 or more values:
+ * kernel offsets inside a field are 32-bit), DG_ERR_ORDER (N < 1 or
+ * N > DG_N_MAX), DG_ERR_CUDA, DG_ERR_OOM.  *out is written only on success. */
 dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t precision,
                             int32_t flags, dg_op** out);
 

@@ -234,6 +234,12 @@ extern "C" dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t p
     op->Kpad = (mesh->K + 1 + kBlockPad - 1) / kBlockPad * kBlockPad;
     // whole blocks, and every field 256-byte aligned (64 values)
     op->fstride = (op->Kpad * op->Np + 63) / 64 * 64;
+    if (op->fstride >= (int64_t(1) << 31)) {
+      const long long fsz = static_cast<long long>(op->fstride);
+      delete op;
+      return fail(DG_ERR_ARG,
+                  "dg_operator_setup: K * Np = %lld nodes per field exceeds 2^31 - 1", fsz);
+    }
     op->geo = dgw::build_geometry(*mesh, op->ref);
     dgw::lsrk_coefficients(op->lsrk_a, op->lsrk_b, op->lsrk_c);
   } catch (const std::bad_alloc&) {

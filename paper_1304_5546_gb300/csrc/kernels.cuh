@@ -96,7 +96,8 @@ struct Layout {
   // double-buffered work arrays: centred volume operands and lifted fluxes
   static constexpr int W_ELEMS = 3 * E * NPAD;
   static constexpr int F_ELEMS = 3 * E * FPAD;
-  static constexpr int HEADER = 128;  // mbarriers
+  static constexpr int HEADER = 512;  // mbarriers + neighbour face-node table
+  static_assert(64 + 6 * Nfp * 4 <= HEADER, "header");
   static constexpr size_t SMEM_BYTES =
       HEADER + kStages * STAGE_BYTES + 2 * sizeof(T) * (W_ELEMS + F_ELEMS);
   static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0, "16-byte TMA chunks");
@@ -181,6 +182,8 @@ __device__ __forceinline__ void load_vec(T (&dst)[W], const T* src) {
 __host__ __device__ constexpr uint32_t round16(uint32_t x) { return (x + 15u) & ~15u; }
 
 // ------------------------------------------------------------ kernel
+// Offsets inside one field are 32-bit (the host guarantees field_stride <
+// 2^31); each field has its own 64-bit base pointer.
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(Layout<T, N>::THREADS)
     dg_stage_kernel(const StageArgs<T> p) {
@@ -192,6 +195,7 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
 
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  int* nbr = reinterpret_cast<int*>(smem + 64);  // [6][Nfp] neighbour face-node table
   unsigned char* stages = smem + L::HEADER;
   T* Wbuf = reinterpret_cast<T*>(stages + kStages * L::STAGE_BYTES);  // [2][3][E][NPAD]
   T* Fbuf = Wbuf + 2 * L::W_ELEMS;                                    // [2][3][E][FPAD]
@@ -200,41 +204,48 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
   const int e = t / Np;
   const int i = t - e * Np;
 
-  const int64_t K = p.K;
-  const int64_t fs = p.fstride;
-  const int64_t nblk = (K + E - 1) / E;
-  const int64_t G = gridDim.x;
-  const int64_t first = blockIdx.x;
-  const int64_t niter = first < nblk ? (nblk - 1 - first) / G + 1 : 0;
+  const int K = static_cast<int>(p.K);
+  const int nblk = (K + E - 1) / E;
+  const int G = gridDim.x;
+  const int first = blockIdx.x;
+  const int niter = first < nblk ? (nblk - 1 - first) / G + 1 : 0;
+  const T* qin[3] = {p.qin, p.qin + p.fstride, p.qin + 2 * p.fstride};
 
   if (t == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
     fence_mbar_init();
   }
+  // neighbour's node for face code bits (fP, rev) and own face-node slot jj:
+  // nbr[(2 fP + rev) * Nfp + jj]
+  if (t < 6 * Nfp) {
+    const int c = t / Nfp, jj = t - c * Nfp;
+    nbr[t] = face_node_dev(N, c >> 1, (c & 1) ? (N - jj) : jj);
+  }
   __syncthreads();
 
   // thread 0: fetch everything block `it` owns into stage it % kStages
-  auto issue = [&](int64_t it) {
-    const int s = static_cast<int>(it % kStages);
-    const int64_t k0 = (first + it * G) * E;
-    const int64_t n = (K - k0) < E ? (K - k0) : E;
+  auto issue = [&](int it) {
+    const int s = it % kStages;
+    const int k0 = (first + it * G) * E;
+    const int n = (K - k0) < E ? (K - k0) : E;
     const uint32_t qb = round16(static_cast<uint32_t>(n * Np * sizeof(T)));
     const uint32_t gb = round16(static_cast<uint32_t>(n * kGeo * sizeof(T)));
     const uint32_t cb = round16(static_cast<uint32_t>(n * 3 * 4));
     unsigned char* st = stages + s * L::STAGE_BYTES;
     mbar_expect_tx(&bars[s], NQ * qb + gb + cb);
 #pragma unroll
-    for (int f = 0; f < 3; ++f) tma_load_1d(st + f * L::QB, p.qin + f * fs + k0 * Np, qb, &bars[s]);
+    for (int f = 0; f < 3; ++f)
+      tma_load_1d(st + f * L::QB, p.qin + f * p.fstride + k0 * Np, qb, &bars[s]);
     if (MODE == kModeStage) {
 #pragma unroll
       for (int f = 0; f < 3; ++f)
-        tma_load_1d(st + (3 + f) * L::QB, p.res + f * fs + k0 * Np, qb, &bars[s]);
+        tma_load_1d(st + (3 + f) * L::QB, p.res + f * p.fstride + k0 * Np, qb, &bars[s]);
     }
-    tma_load_1d(st + 6 * L::QB, p.geo + k0 * kGeo, gb, &bars[s]);
-    tma_load_1d(st + 6 * L::QB + L::GB, p.conn + k0 * 3, cb, &bars[s]);
+    tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * kGeo, gb, &bars[s]);
+    tma_load_1d(st + 6 * L::QB + L::GB, p.conn + static_cast<int64_t>(k0) * 3, cb, &bars[s]);
   };
 
-  int64_t issued = 0;  // (thread 0) iterations whose loads were issued
+  int issued = 0;  // (thread 0) iterations whose loads were issued
   if (t == 0) {
     for (; issued < niter && issued < kStages; ++issued) issue(issued);
   }
@@ -249,33 +260,36 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
 #pragma unroll
   for (int j = 0; j < Nafp; ++j) lf[j] = __ldg(p.LIFT + i * Nafp + j);
 
+  // this thread's flux tasks (the same in every block): element slot, face
+  // node slot, face, node on the face
+  int task_e[TPT], task_j[TPT], task_f[TPT], task_jj[TPT];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int tau = t + u * THREADS;
+    task_e[u] = tau < TASKS ? tau / Nafp : E;  // E marks "no task"
+    task_j[u] = tau - (tau / Nafp) * Nafp;
+    task_f[u] = task_j[u] / Nfp;
+    task_jj[u] = task_j[u] - task_f[u] * Nfp;
+  }
+
   // neighbour traces of this thread's flux tasks, one block ahead
   T trc[TPT][3];
-  auto gather = [&](int64_t it) {
-    const int s = static_cast<int>(it % kStages);
+  auto gather = [&](int it) {
+    const int s = it % kStages;
     const int32_t* sc =
         reinterpret_cast<const int32_t*>(stages + s * L::STAGE_BYTES + 6 * L::QB + L::GB);
-    const int64_t k0 = (first + it * G) * E;
+    const int k0 = (first + it * G) * E;
 #pragma unroll
     for (int u = 0; u < TPT; ++u) {
-      const int tau = t + u * THREADS;
       trc[u][0] = trc[u][1] = trc[u][2] = T(0);
-      if (tau < TASKS) {
-        const int ee = tau / Nafp;
-        const int j = tau - ee * Nafp;
-        const int f = j / Nfp;
-        const int jj = j - f * Nfp;
-        if (k0 + ee < K) {
-          const int32_t code = sc[ee * 3 + f];
-          if (code >= 0) {
-            const int64_t kP = code >> 3;
-            const int fP = (code >> 1) & 3;
-            const int jP = (code & 1) ? (N - jj) : jj;
-            const int64_t gP = kP * Np + face_node_dev(N, fP, jP);
-            trc[u][0] = __ldg(p.qin + gP);
-            trc[u][1] = __ldg(p.qin + fs + gP);
-            trc[u][2] = __ldg(p.qin + 2 * fs + gP);
-          }
+      const int ee = task_e[u];
+      if (ee < E && k0 + ee < K) {
+        const int32_t code = sc[ee * 3 + task_f[u]];
+        if (code >= 0) {
+          const int gP = (code >> 3) * Np + nbr[(code & 7) * Nfp + task_jj[u]];
+          trc[u][0] = __ldg(qin[0] + gP);
+          trc[u][1] = __ldg(qin[1] + gP);
+          trc[u][2] = __ldg(qin[2] + gP);
         }
       }
     }
@@ -287,15 +301,14 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
     if (ok) gather(0);
   }
 
-  int64_t it = 0;
+  int it = 0;
   for (; it < niter; ++it) {
-    const int s = static_cast<int>(it % kStages);
+    const int s = it % kStages;
     const uint32_t parity = static_cast<uint32_t>((it / kStages) & 1);
     if (ok) ok = mbar_wait_bounded(&bars[s], parity, kWaitLimitNs);
-    const int64_t k0 = (first + it * G) * E;
-    const int64_t k = k0 + e;
-    const bool valid = k < K;
-    const int64_t g = k0 * Np + t;  // == k * Np + i
+    const int k0 = (first + it * G) * E;
+    const bool valid = k0 + e < K;
+    const int g = k0 * Np + t;  // == k * Np + i
     const unsigned char* st = stages + s * L::STAGE_BYTES;
     const T* sq = reinterpret_cast<const T*>(st);
     const T* sg = reinterpret_cast<const T*>(st + 6 * L::QB);
@@ -328,39 +341,33 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
     // ---- phase 2: upwind flux at every face node, scaled by Fscale/2
 #pragma unroll
     for (int u = 0; u < TPT; ++u) {
-      const int tau = t + u * THREADS;
-      if (tau < TASKS) {
-        const int ee = tau / Nafp;
-        const int j = tau - ee * Nafp;
-        if (k0 + ee < K) {
-          const int f = j / Nfp;
-          const int jj = j - f * Nfp;
-          const int nM = ee * Np + face_node_dev(N, f, jj);
-          const T hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
-          T dHx, dHy, dEz;
-          if (sc[ee * 3 + f] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
-            dHx = 0;
-            dHy = 0;
-            dEz = 2 * ezM;
-          } else {
-            dHx = hxM - trc[u][0];
-            dHy = hyM - trc[u][1];
-            dEz = ezM - trc[u][2];
-          }
-          const T* gf = sg + ee * kGeo + 4 + 3 * f;
-          const T nx = gf[0], ny = gf[1], fsc = gf[2];
-          const T ndotdH = nx * dHx + ny * dHy;
-          Fb[(0 * E + ee) * FPAD + j] = fsc * (ny * dEz + (ndotdH * nx - dHx));
-          Fb[(1 * E + ee) * FPAD + j] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
-          Fb[(2 * E + ee) * FPAD + j] = fsc * (ny * dHx - nx * dHy - dEz);
+      const int ee = task_e[u];
+      if (ee < E && k0 + ee < K) {
+        const int f = task_f[u], j = task_j[u];
+        const int nM = ee * Np + face_node_dev(N, f, task_jj[u]);
+        const T hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
+        T dHx, dHy, dEz;
+        if (sc[ee * 3 + f] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
+          dHx = 0;
+          dHy = 0;
+          dEz = 2 * ezM;
+        } else {
+          dHx = hxM - trc[u][0];
+          dHy = hyM - trc[u][1];
+          dEz = ezM - trc[u][2];
         }
+        const T* gf = sg + ee * kGeo + 4 + 3 * f;
+        const T nx = gf[0], ny = gf[1], fsc = gf[2];
+        const T ndotdH = nx * dHx + ny * dHy;
+        Fb[(0 * E + ee) * FPAD + j] = fsc * (ny * dEz + (ndotdH * nx - dHx));
+        Fb[(1 * E + ee) * FPAD + j] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
+        Fb[(2 * E + ee) * FPAD + j] = fsc * (ny * dHx - nx * dHy - dEz);
       }
     }
     // next block's traces: their addresses are in the next stage's codes
     if (it + 1 < niter) {
-      const int s1 = static_cast<int>((it + 1) % kStages);
       const uint32_t par1 = static_cast<uint32_t>(((it + 1) / kStages) & 1);
-      ok = mbar_wait_bounded(&bars[s1], par1, kWaitLimitNs);
+      ok = mbar_wait_bounded(&bars[(it + 1) % kStages], par1, kWaitLimitNs);
       if (ok) gather(it + 1);
     }
     if (__syncthreads_or(!ok)) break;
@@ -371,54 +378,74 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
       ++issued;
     }
 
-    // ---- phase 3: volume products, lift, stage update
-    T dEzdr = 0, dEzds = 0, cEz = 0;
+    // ---- phase 3: volume products, lift, stage update (seven independent
+    // accumulation chains)
+    T dEzdr = 0, dEzds = 0, cA = 0, cB = 0;
+    T l0 = 0, l1 = 0, l2 = 0;
     const T* pEz = Wb + (0 * E + e) * NPAD;
     const T* pA = Wb + (1 * E + e) * NPAD;
     const T* pB = Wb + (2 * E + e) * NPAD;
-#pragma unroll
-    for (int m0 = 0; m0 < Np; m0 += VW) {
-      T vz[VW], va[VW], vb[VW];
-      load_vec<T, VW>(vz, pEz + m0);
-      load_vec<T, VW>(va, pA + m0);
-      load_vec<T, VW>(vb, pB + m0);
-#pragma unroll
-      for (int u = 0; u < VW; ++u) {
-        if (m0 + u < Np) {
-          dEzdr += dr[m0 + u] * vz[u];
-          dEzds += ds[m0 + u] * vz[u];
-          cEz += dr[m0 + u] * va[u] + ds[m0 + u] * vb[u];
-        }
-      }
-    }
-    T l0 = 0, l1 = 0, l2 = 0;
     const T* pF0 = Fb + (0 * E + e) * FPAD;
     const T* pF1 = Fb + (1 * E + e) * FPAD;
     const T* pF2 = Fb + (2 * E + e) * FPAD;
 #pragma unroll
-    for (int j0 = 0; j0 < Nafp; j0 += VW) {
-      T f0[VW], f1[VW], f2[VW];
-      load_vec<T, VW>(f0, pF0 + j0);
-      load_vec<T, VW>(f1, pF1 + j0);
-      load_vec<T, VW>(f2, pF2 + j0);
+    for (int m0 = 0; m0 < NPAD; m0 += VW) {
+      if (m0 < Np) {
+        T vz[VW], va[VW], vb[VW];
+        load_vec<T, VW>(vz, pEz + m0);
+        load_vec<T, VW>(va, pA + m0);
+        load_vec<T, VW>(vb, pB + m0);
 #pragma unroll
-      for (int u = 0; u < VW; ++u) {
-        if (j0 + u < Nafp) {
-          l0 += lf[j0 + u] * f0[u];
-          l1 += lf[j0 + u] * f1[u];
-          l2 += lf[j0 + u] * f2[u];
+        for (int u = 0; u < VW; ++u) {
+          if (m0 + u < Np) {
+            dEzdr += dr[m0 + u] * vz[u];
+            dEzds += ds[m0 + u] * vz[u];
+            cA += dr[m0 + u] * va[u];
+            cB += ds[m0 + u] * vb[u];
+          }
+        }
+      }
+      if (m0 < Nafp) {
+        T f0[VW], f1[VW], f2[VW];
+        load_vec<T, VW>(f0, pF0 + m0);
+        load_vec<T, VW>(f1, pF1 + m0);
+        load_vec<T, VW>(f2, pF2 + m0);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+          if (m0 + u < Nafp) {
+            l0 += lf[m0 + u] * f0[u];
+            l1 += lf[m0 + u] * f1[u];
+            l2 += lf[m0 + u] * f2[u];
+          }
+        }
+      }
+    }
+    if (FPAD > NPAD) {  // lift columns beyond the volume loop (N = 1, 2)
+#pragma unroll
+      for (int m0 = NPAD; m0 < Nafp; m0 += VW) {
+        T f0[VW], f1[VW], f2[VW];
+        load_vec<T, VW>(f0, pF0 + m0);
+        load_vec<T, VW>(f1, pF1 + m0);
+        load_vec<T, VW>(f2, pF2 + m0);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+          if (m0 + u < Nafp) {
+            l0 += lf[m0 + u] * f0[u];
+            l1 += lf[m0 + u] * f1[u];
+            l2 += lf[m0 + u] * f2[u];
+          }
         }
       }
     }
     const T rhsHx = -(ry * dEzdr + sy * dEzds) + l0;
     const T rhsHy = (rx * dEzdr + sx * dEzds) + l1;
-    const T rhsEz = cEz + l2;
+    const T rhsEz = (cA + cB) + l2;
 
     if (valid) {
       if (MODE == kModeRhs) {
         p.rhs[g] = rhsHx;
-        p.rhs[fs + g] = rhsHy;
-        p.rhs[2 * fs + g] = rhsEz;
+        p.rhs[p.fstride + g] = rhsHy;
+        p.rhs[2 * p.fstride + g] = rhsEz;
       } else {
         T n0, n1, n2;
         if (MODE == kModeFirstStage) {
@@ -431,11 +458,11 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
           n2 = p.a * r2 + p.dt * rhsEz;
         }
         p.res[g] = n0;
-        p.res[fs + g] = n1;
-        p.res[2 * fs + g] = n2;
+        p.res[p.fstride + g] = n1;
+        p.res[2 * p.fstride + g] = n2;
         p.qout[g] = hx + p.b * n0;
-        p.qout[fs + g] = hy + p.b * n1;
-        p.qout[2 * fs + g] = ez + p.b * n2;
+        p.qout[p.fstride + g] = hy + p.b * n1;
+        p.qout[2 * p.fstride + g] = ez + p.b * n2;
       }
     }
   }
@@ -444,7 +471,7 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
     // a wait expired: report, then let this CTA's copies in flight land
     // (each wait bounded) before the CTA's shared memory is released
     atomicExch(p.status, 1);
-    for (int64_t j = it; j < issued; ++j)
+    for (int j = it; j < issued; ++j)
       mbar_wait_bounded(&bars[j % kStages], static_cast<uint32_t>((j / kStages) & 1),
                         kWaitLimitNs);
   }
