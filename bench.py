@@ -184,7 +184,7 @@ def run_ours(args):
 
     N = args.order
     mesh = jittered_delaunay_mesh(args.n, seed=2024)
-    s = P.Solver(*mesh, N=N, precision=args.precision, device=dev)
+    s = P.Solver(*mesh, N=N, precision=args.precision, device=dev, simt=args.simt)
     x, y = s.nodes()
     q0 = np.stack(gaussian_pulse(x, y))
     q = s.from_numpy(q0)
@@ -272,6 +272,8 @@ def run_ours(args):
             "workload": "single large mesh: jittered Delaunay unit square n=%d (K=%d), N=%d, "
                         "Gaussian pulse w=0.05, LSRK(5,4) steps" % (args.n, K, N),
             "K": K, "N": N, "Np": s.Np, "precision": args.precision,
+            "products": ("CUDA cores" if (args.simt or args.precision == "fp64")
+                         else "tensor cores (tcgen05, 3xTF32)"),
             "mesh_seed": 2024,
             "l2": "inputs larger than L2 (q, q_tmp, res: %.0f MB)" % (
                 3 * 3 * s.fstride * (4 if args.precision == "fp32" else 8) / 1e6),
@@ -286,7 +288,8 @@ def run_ours(args):
             "frac": achieved / peaks["hbm_gbs"],
             "traffic": traffic,
             "peak_kind": peak_kind,
-            "kernel": "dg_stage_kernel (fused RHS + LSRK stage)",
+            "kernel": ("dg_stage_kernel" if (args.simt or args.precision == "fp64")
+                       else "dg_stage_tc_kernel") + " (fused RHS + LSRK stage)",
             "bytes_per_element_step": step_bytes_per_element(N),
         },
         "e2e": {
@@ -348,6 +351,7 @@ def main(argv=None):
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--n", type=int, default=707, help="mesh resolution (K = 2 n^2)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--simt", action="store_true", help="FP32 products on CUDA cores")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")

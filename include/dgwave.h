@@ -77,6 +77,8 @@ typedef int32_t dg_status;
 #define DG_FP32 1
 
 #define DG_SETUP_HOST_ONLY 1 /* dg_operator_setup flag: skip device upload */
+#define DG_SETUP_SIMT 2      /* FP32: element-local products on the CUDA cores
+                                instead of the tensor cores (3xTF32)         */
 
 #define DG_N_MAX 7
 
@@ -116,7 +118,11 @@ void dg_mesh_destroy(dg_mesh* mesh);
  * face mass matrices and LIFT = M^-1 M^dI (Eq. dg-lift), the affine
  * Jacobians and chain-rule factors rx, ry, sx, sy, outward unit normals and
  * Fscale = surface Jacobian / volume Jacobian (Section "Computing the
- * Surface Contribution"), and the trace maps.  Unless flags has
+ * Surface Contribution"), and the trace maps.  FP32 operators run the
+ * element-local products (Dr, Ds, LIFT) on the tensor cores as three TF32
+ * products per term (hi/lo splits of both operands, FP32 accumulation);
+ * flags DG_SETUP_SIMT selects the CUDA-core FP32 kernel instead.  FP64
+ * operators always use the CUDA cores.  Unless flags has
  * DG_SETUP_HOST_ONLY, device-ready copies are uploaded once, cast to the
  * operator's precision (DG_FP32 or DG_FP64), to the current CUDA device.
  * The operator keeps its own copy of the mesh data; the mesh may be

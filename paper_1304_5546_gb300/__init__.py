@@ -201,8 +201,11 @@ class Solver:
     the operator's precision; ``view(q)`` gives the (3, K, Np) window.
     """
 
-    def __init__(self, VX, VY, EToV, N, precision="fp32", device=None, host_only=False):
+    def __init__(self, VX, VY, EToV, N, precision="fp32", device=None, host_only=False,
+                 simt=False):
         import torch
+        if precision == "fp32simt":
+            precision, simt = "fp32", True
         self.precision = DG_FP32 if precision in ("fp32", DG_FP32) else DG_FP64
         self.dtype = torch.float32 if self.precision == DG_FP32 else torch.float64
         if device is not None and not host_only:
@@ -210,8 +213,8 @@ class Solver:
         self.device = None if host_only else torch.device("cuda", torch.cuda.current_device())
         self.mesh = dg_mesh_create(VX, VY, EToV)
         try:
-            self.op = dg_operator_setup(self.mesh, N, self.precision,
-                                        DG_SETUP_HOST_ONLY if host_only else 0)
+            flags = (DG_SETUP_HOST_ONLY if host_only else 0) | (_lib.DG_SETUP_SIMT if simt else 0)
+            self.op = dg_operator_setup(self.mesh, N, self.precision, flags)
         except Exception:
             dg_mesh_destroy(self.mesh)
             raise

@@ -24,6 +24,7 @@ DG_ERR_TIMEOUT = 9
 DG_FP64 = 0
 DG_FP32 = 1
 DG_SETUP_HOST_ONLY = 1
+DG_SETUP_SIMT = 2
 DG_N_MAX = 7
 
 _STATUS_NAMES = {

@@ -26,7 +26,8 @@ def _nvcc():
 
 
 def sources():
-    names = ["host_setup.cpp", "api.cu"] + ["kernels_N%d.cu" % n for n in range(1, 8)]
+    names = (["host_setup.cpp", "api.cu"] + ["kernels_N%d.cu" % n for n in range(1, 8)]
+             + ["kernels_tc_N%d.cu" % n for n in range(1, 8)])
     return [os.path.join(CSRC, n) for n in names]
 
 
@@ -79,7 +80,7 @@ def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
     for name in sorted(os.listdir(CSRC)):
-        if name.startswith("kernels") or name == "launch.h":
+        if name.startswith("kernels") or name in ("launch.h", "ptx.cuh"):
             with open(os.path.join(CSRC, name), "rb") as f:
                 h.update(name.encode() + f.read())
     return h.hexdigest()[:16]

@@ -37,6 +37,8 @@ struct dg_op {
   void* d_qtmp = nullptr;  // second field buffer for the stage ping-pong
   int* d_flag = nullptr;   // finiteness scan result
   int* d_status = nullptr; // kernel status word (bounded-wait expiry)
+  float* d_tcop = nullptr; // tensor-core operator tiles (TF32 hi, lo) for FP32
+  bool use_tc = false;     // FP32 products on the tensor cores
   double lsrk_a[5], lsrk_b[5], lsrk_c[5];
   mutable std::atomic<int64_t> launches{0};
 };
@@ -53,13 +55,50 @@ dg_status cuda_fail(cudaError_t err, const char* where) {
 }
 
 void free_device(dg_op* op) {
-  void* ptrs[] = {op->d_Dr,   op->d_Ds,   op->d_LIFT,  op->d_geo,
-                  op->d_conn, op->d_qtmp, op->d_flag, op->d_status};
+  void* ptrs[] = {op->d_Dr,   op->d_Ds,   op->d_LIFT,   op->d_geo, op->d_conn,
+                  op->d_qtmp, op->d_flag, op->d_status, op->d_tcop};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   op->d_Dr = op->d_Ds = op->d_LIFT = op->d_geo = op->d_conn = op->d_qtmp = nullptr;
   op->d_flag = nullptr;
   op->d_status = nullptr;
+  op->d_tcop = nullptr;
+}
+
+// TF32 value nearest to v (ties away from zero), as a float with its 13 low
+// mantissa bits clear.
+float tf32_round(double v) {
+  float f = static_cast<float>(v);
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// [Dr | Ds | LIFT] as the B operand of the tensor-core kernel: hi and lo TF32
+// parts (v ~ hi + lo, split in FP64), each an nn x kp tile in the core-matrix
+// layout of dgw::tc_canon; rows >= Np and columns >= 2 Np + Nafp are zero.
+std::vector<float> tc_operator_tiles(const dgw::RefElement& R) {
+  const int N = R.N, Np = R.Np, Nafp = R.Nafp;
+  const int kp = dgw::tc_kp(N), nn = dgw::tc_nn(N);
+  std::vector<float> out(2 * static_cast<size_t>(nn) * kp, 0.0f);
+  for (int n = 0; n < Np; ++n)
+    for (int k = 0; k < 2 * Np + Nafp; ++k) {
+      double v;
+      if (k < Np)
+        v = R.Dr[n * Np + k];
+      else if (k < 2 * Np)
+        v = R.Ds[n * Np + (k - Np)];
+      else
+        v = R.LIFT[n * Nafp + (k - 2 * Np)];
+      const float hi = tf32_round(v);
+      const float lo = tf32_round(v - static_cast<double>(hi));
+      const int idx = dgw::tc_canon(n, k, kp);
+      out[idx] = hi;
+      out[static_cast<size_t>(nn) * kp + idx] = lo;
+    }
+  return out;
 }
 
 template <typename T>
@@ -107,6 +146,14 @@ dg_status upload(dg_op* op) {
   if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMemset");
   err = cudaMalloc(&op->d_flag, sizeof(int));
   if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(flag)");
+  if (op->use_tc) {
+    const std::vector<float> tiles = tc_operator_tiles(op->ref);
+    err = cudaMalloc(&op->d_tcop, tiles.size() * sizeof(float));
+    if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(operator tiles)");
+    err = cudaMemcpy(op->d_tcop, tiles.data(), tiles.size() * sizeof(float),
+                     cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMemcpy(operator tiles)");
+  }
   err = cudaMalloc(&op->d_status, sizeof(int));
   if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(status)");
   err = cudaMemset(op->d_status, 0, sizeof(int));
@@ -116,8 +163,25 @@ dg_status upload(dg_op* op) {
   return DG_OK;
 }
 
+cudaError_t launch_order_tc(const dg_op* op, const dgw::StageArgs<float>& a, int mode,
+                            cudaStream_t s) {
+  switch (op->N) {
+    case 1: return dgw::launch_stage_tc<1>(a, mode, op->num_sms, s);
+    case 2: return dgw::launch_stage_tc<2>(a, mode, op->num_sms, s);
+    case 3: return dgw::launch_stage_tc<3>(a, mode, op->num_sms, s);
+    case 4: return dgw::launch_stage_tc<4>(a, mode, op->num_sms, s);
+    case 5: return dgw::launch_stage_tc<5>(a, mode, op->num_sms, s);
+    case 6: return dgw::launch_stage_tc<6>(a, mode, op->num_sms, s);
+    case 7: return dgw::launch_stage_tc<7>(a, mode, op->num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
 cudaError_t launch_order(const dg_op* op, const dgw::StageArgs<T>& a, int mode, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (op->use_tc) return launch_order_tc(op, a, mode, s);
+  }
   switch (op->N) {
     case 1: return dgw::launch_stage<T, 1>(a, mode, op->num_sms, s);
     case 2: return dgw::launch_stage<T, 2>(a, mode, op->num_sms, s);
@@ -141,6 +205,7 @@ dgw::StageArgs<T> base_args(const dg_op* op) {
   a.Ds = static_cast<const T*>(op->d_Ds);
   a.LIFT = static_cast<const T*>(op->d_LIFT);
   a.status = op->d_status;
+  a.tc_op = op->d_tcop;
   return a;
 }
 
@@ -229,6 +294,7 @@ extern "C" dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t p
     op->Nafp = op->ref.Nafp;
     op->precision = precision;
     op->flags = flags;
+    op->use_tc = (precision == DG_FP32) && !(flags & DG_SETUP_SIMT);
     op->elem_size = (precision == DG_FP32) ? 4 : 8;
     op->K = mesh->K;
     op->Kpad = (mesh->K + 1 + kBlockPad - 1) / kBlockPad * kBlockPad;

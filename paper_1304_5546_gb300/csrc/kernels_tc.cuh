@@ -1,0 +1,439 @@
+// FP32 stage kernel with the element-local products on the 5th-generation
+// tensor cores (tcgen05, TMEM accumulator).
+//
+// Same result as dg_stage_kernel (kernels.cuh): right-hand side of Eq.
+// dg-strong-explicit -- volume derivative by Dr/Ds and the chain rule of Eq.
+// dg-diff-local-to-global, upwind flux of Eq. max2d-numflux at every face
+// node, LIFT of Eq. dg-lift -- followed by one 2N-storage LSRK(5,4) stage
+// update, or written out as the right-hand side.
+//
+// The products of a block of E elements form one dense contraction.  With
+// X rows per element (centred Ez_c = Ez - Ez_0, A = rx (Hy - Hy_0) - ry (Hx
+// - Hx_0), B = sx (Hy - Hy_0) - sy (Hx - Hx_0), F_c = Fscale/2 * flux_c):
+//   row 3e+0 = [ -ry Ez_c | -sy Ez_c | F_x ]  ->  dHx/dt
+//   row 3e+1 = [  rx Ez_c |  sx Ez_c | F_y ]  ->  dHy/dt
+//   row 3e+2 = [  A       |  B       | F_z ]  ->  dEz/dt
+// the right-hand side is D = X [Dr | Ds | LIFT]^T: M = 3E rows (<= 128),
+// K = 2 Np + Nafp (padded to 8), N = Np (padded to 16).  FP32 accuracy
+// comes from three TF32 products, X_hi Op_hi + X_hi Op_lo + X_lo Op_hi, with
+// hi = TF32 round-to-nearest of the value and lo = TF32 rounding of the rest
+// (Op's split is made on the host from FP64).  One thread issues the
+// tcgen05.mma instructions; the FP32 accumulator lives in TMEM (lane = row)
+// and four warps read it back (tcgen05.ld) for the stage update.
+//
+// Memory pipeline as in the CUDA-core kernel: a block's own data arrives
+// by 1D TMA bulk copies into a ring of stage buffers (mbarrier per stage),
+// neighbour traces are gathered one block ahead, and full blocks leave by
+// TMA bulk stores from the same stage buffer.  Every wait is bounded; on
+// expiry the CTA sets the status word, drains its copies (bounded), frees
+// its TMEM and returns.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace dgw {
+
+template <int N>
+struct TcLayout {
+  static constexpr int Np = Order<N>::Np;
+  static constexpr int Nfp = Order<N>::Nfp;
+  static constexpr int Nafp = Order<N>::Nafp;
+  static constexpr int E = (N == 7) ? 24 : 40;  // 3E <= 128 GEMM rows, E % 4 == 0
+  static constexpr int S = (N >= 6) ? 3 : 4;    // stage buffers
+  static constexpr int ROWS = 3 * E;
+  static constexpr int KD = tc_kd(N), KP = tc_kp(N), KG = KP / 4;
+  static constexpr int NN = tc_nn(N);
+  static constexpr int TMEM_COLS = NN <= 32 ? 32 : 64;
+  static constexpr int THREADS = 256;
+  static constexpr int FPAD = round_up(Nafp, 4);
+  static constexpr int TASKS = E * Nafp;
+  static constexpr int TPT = (TASKS + THREADS - 1) / THREADS;
+  static constexpr int KGU = (KD + 3) / 4;  // 16-byte K chunks that hold data
+  static constexpr int ITEMS = E * KGU;
+  static constexpr int IPT = (ITEMS + THREADS - 1) / THREADS;
+  static constexpr int QB = E * Np * 4;
+  static constexpr int GB = E * kGeo * 4;
+  static constexpr int CB = E * 3 * 4;
+  static constexpr int STAGE_BYTES = round_up(6 * QB + GB + CB, 128);
+  static constexpr int XB = 128 * KP * 4;  // one X tile (hi or lo)
+  static constexpr int OB = NN * KP * 4;   // one operator tile (hi or lo)
+  static constexpr int FB = E * 3 * FPAD * 4;
+  static constexpr int HEADER = 1024;
+  static constexpr int OFF_STAGES = HEADER;
+  static constexpr int OFF_X = OFF_STAGES + S * STAGE_BYTES;
+  static constexpr int OFF_OP = OFF_X + 2 * XB;
+  static constexpr int OFF_F = OFF_OP + 2 * OB;
+  static constexpr size_t SMEM_BYTES = OFF_F + FB;
+  static_assert(SMEM_BYTES <= 232448, "shared memory");
+  static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0 && OB % 16 == 0, "TMA chunks");
+  static_assert(ROWS <= 128 && NN <= 256 && NN % 16 == 0 && KP % 8 == 0, "UMMA shape");
+};
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
+    dg_stage_tc_kernel(const StageArgs<float> p) {
+  using L = TcLayout<N>;
+  constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
+  constexpr int KD = L::KD, KP = L::KP, NN = L::NN, FPAD = L::FPAD;
+  constexpr int THREADS = L::THREADS, TASKS = L::TASKS, TPT = L::TPT;
+  constexpr int KGU = L::KGU, ITEMS = L::ITEMS, IPT = L::IPT;
+  constexpr int NQ = (MODE == kModeStage) ? 6 : 3;
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);         // [S]
+  uint64_t* mma_bar = reinterpret_cast<uint64_t*>(smem + 64);  // MMA completion
+  uint64_t* op_bar = reinterpret_cast<uint64_t*>(smem + 72);   // operator tiles landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 80);
+  int* nbr = reinterpret_cast<int*>(smem + 128);  // [6][Nfp] neighbour face-node table
+  unsigned char* stages = smem + L::OFF_STAGES;
+  float* Xs = reinterpret_cast<float*>(smem + L::OFF_X);  // [2][128 x KP] canonical
+  float* Fs = reinterpret_cast<float*>(smem + L::OFF_F);  // [E][3][FPAD]
+
+  const int t = threadIdx.x;
+  const int warp = t >> 5, lane = t & 31;
+  const int K = static_cast<int>(p.K);
+  const int nblk = (K + E - 1) / E;
+  const int G = gridDim.x;
+  const int first = blockIdx.x;
+  const int niter = first < nblk ? (nblk - 1 - first) / G + 1 : 0;
+  const int64_t fs = p.fstride;
+  const float* qin[3] = {p.qin, p.qin + fs, p.qin + 2 * fs};
+
+  if (t == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+    mbar_init(mma_bar, 1);
+    mbar_init(op_bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, L::TMEM_COLS);
+  if (t < 6 * Nfp) {
+    const int c = t / Nfp, jj = t - c * Nfp;
+    nbr[t] = face_node_dev(N, c >> 1, (c & 1) ? (N - jj) : jj);
+  }
+  // zero both X tiles once: K padding columns and rows beyond 3E stay zero
+  {
+    float4* x4 = reinterpret_cast<float4*>(Xs);
+    for (int idx = t; idx < 2 * L::XB / 16; idx += THREADS) x4[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto issue = [&](int it) {
+    const int s = it % S;
+    const int k0 = (first + it * G) * E;
+    const int n = (K - k0) < E ? (K - k0) : E;
+    const uint32_t qb = round16(static_cast<uint32_t>(n * Np * 4));
+    const uint32_t gb = round16(static_cast<uint32_t>(n * kGeo * 4));
+    const uint32_t cb = round16(static_cast<uint32_t>(n * 3 * 4));
+    unsigned char* st = stages + s * L::STAGE_BYTES;
+    mbar_expect_tx(&full[s], NQ * qb + gb + cb);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) tma_load_1d(st + f * L::QB, p.qin + f * fs + k0 * Np, qb, &full[s]);
+    if (MODE == kModeStage) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+        tma_load_1d(st + (3 + f) * L::QB, p.res + f * fs + k0 * Np, qb, &full[s]);
+    }
+    tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * kGeo, gb, &full[s]);
+    tma_load_1d(st + 6 * L::QB + L::GB, p.conn + static_cast<int64_t>(k0) * 3, cb, &full[s]);
+  };
+
+  int issued = 0;
+  bool mma_inflight = false;  // (thread 0) an MMA group was committed, not yet seen done
+  if (t == 0) {
+    mbar_expect_tx(op_bar, 2 * L::OB);
+    tma_load_1d(smem + L::OFF_OP, p.tc_op, 2 * L::OB, op_bar);
+    for (; issued < niter && issued < S; ++issued) issue(issued);
+  }
+
+  // flux tasks of this thread (fixed across blocks)
+  int task_e[TPT], task_j[TPT], task_f[TPT], task_jj[TPT];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int tau = t + u * THREADS;
+    task_e[u] = tau < TASKS ? tau / Nafp : E;
+    task_j[u] = tau - (tau / Nafp) * Nafp;
+    task_f[u] = task_j[u] / Nfp;
+    task_jj[u] = task_j[u] - task_f[u] * Nfp;
+  }
+  // X build items of this thread: (element, 16-byte K chunk), element fastest
+  int item_e[IPT], item_kc[IPT];
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    const int idx = t + u * THREADS;
+    item_kc[u] = idx < ITEMS ? idx / E : KGU;  // KGU marks "no item"
+    item_e[u] = idx - (idx / E) * E;
+  }
+
+  float trc[TPT][3];
+  auto gather = [&](int it) {
+    const int32_t* sc = reinterpret_cast<const int32_t*>(stages + (it % S) * L::STAGE_BYTES +
+                                                         6 * L::QB + L::GB);
+    const int k0 = (first + it * G) * E;
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      trc[u][0] = trc[u][1] = trc[u][2] = 0.f;
+      const int ee = task_e[u];
+      if (ee < E && k0 + ee < K) {
+        const int32_t code = sc[ee * 3 + task_f[u]];
+        if (code >= 0) {
+          const int gP = (code >> 3) * Np + nbr[(code & 7) * Nfp + task_jj[u]];
+          trc[u][0] = __ldg(qin[0] + gP);
+          trc[u][1] = __ldg(qin[1] + gP);
+          trc[u][2] = __ldg(qin[2] + gP);
+        }
+      }
+    }
+  };
+
+  bool ok = mbar_wait_bounded(op_bar, 0, kWaitLimitNs);
+  if (ok && niter > 0) {
+    ok = mbar_wait_bounded(&full[0], 0, kWaitLimitNs);
+    if (ok) gather(0);
+  }
+  const uint32_t xaddr = smem_u32(Xs);
+  const uint32_t oaddr = smem_u32(smem + L::OFF_OP);
+  constexpr uint32_t LBO = 128, SBO = L::KG * 128;
+  constexpr uint32_t IDESC = umma_idesc_tf32(128, NN);
+
+  int it = 0;
+  for (; it < niter; ++it) {
+    const int s = it % S;
+    if (ok) ok = mbar_wait_bounded(&full[s], static_cast<uint32_t>((it / S) & 1), kWaitLimitNs);
+    const int k0 = (first + it * G) * E;
+    const int nvalid = (K - k0) < E ? (K - k0) : E;
+    unsigned char* st = stages + s * L::STAGE_BYTES;
+    float* sq = reinterpret_cast<float*>(st);  // [3][E Np] q (then the outputs)
+    float* sres = sq + 3 * E * Np;             // [3][E Np] residual
+    const float* sg = reinterpret_cast<const float*>(st + 6 * L::QB);
+    const int32_t* sc = reinterpret_cast<const int32_t*>(st + 6 * L::QB + L::GB);
+
+    // ---- phase A: upwind flux at every face node -> Fs[e][c][j]
+    if (ok) {
+#pragma unroll
+      for (int u = 0; u < TPT; ++u) {
+        const int ee = task_e[u];
+        if (ee < nvalid) {
+          const int f = task_f[u], j = task_j[u];
+          const int nM = ee * Np + face_node_dev(N, f, task_jj[u]);
+          const float hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
+          float dHx, dHy, dEz;
+          if (sc[ee * 3 + f] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
+            dHx = 0.f;
+            dHy = 0.f;
+            dEz = 2.f * ezM;
+          } else {
+            dHx = hxM - trc[u][0];
+            dHy = hyM - trc[u][1];
+            dEz = ezM - trc[u][2];
+          }
+          const float* gf = sg + ee * kGeo + 4 + 3 * f;
+          const float nx = gf[0], ny = gf[1], fsc = gf[2];
+          const float ndotdH = nx * dHx + ny * dHy;
+          float* fo = Fs + (ee * 3) * FPAD + j;
+          fo[0] = fsc * (ny * dEz + (ndotdH * nx - dHx));
+          fo[FPAD] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
+          fo[2 * FPAD] = fsc * (ny * dHx - nx * dHy - dEz);
+        }
+      }
+    }
+    if (ok && it + 1 < niter) {
+      ok = mbar_wait_bounded(&full[(it + 1) % S], static_cast<uint32_t>(((it + 1) / S) & 1),
+                             kWaitLimitNs);
+      if (ok) gather(it + 1);
+    }
+    if (__syncthreads_or(!ok)) break;
+
+    // ---- phase B: GEMM rows of every element, split into TF32 hi / lo
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      const int kc = item_kc[u], e = item_e[u];
+      if (kc < KGU && e < nvalid) {
+        const float* qe = sq + e * Np;
+        const float* ge = sg + e * kGeo;
+        const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
+        const float hx0 = qe[0], hy0 = qe[E * Np], ez0 = qe[2 * E * Np];
+        float v[3][4];
+#pragma unroll
+        for (int uu = 0; uu < 4; ++uu) {
+          const int k = 4 * kc + uu;
+          if (k < 2 * Np) {
+            const int m = k < Np ? k : k - Np;
+            const float ec = qe[2 * E * Np + m] - ez0;
+            const float dhx = qe[m] - hx0, dhy = qe[E * Np + m] - hy0;
+            if (k < Np) {
+              v[0][uu] = -ry * ec;
+              v[1][uu] = rx * ec;
+              v[2][uu] = rx * dhy - ry * dhx;
+            } else {
+              v[0][uu] = -sy * ec;
+              v[1][uu] = sx * ec;
+              v[2][uu] = sx * dhy - sy * dhx;
+            }
+          } else if (k < KD) {
+            const float* fe = Fs + (e * 3) * FPAD + (k - 2 * Np);
+            v[0][uu] = fe[0];
+            v[1][uu] = fe[FPAD];
+            v[2][uu] = fe[2 * FPAD];
+          } else {
+            v[0][uu] = v[1][uu] = v[2][uu] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float4 hi, lo;
+          hi.x = tf32_rna(v[c][0]);
+          hi.y = tf32_rna(v[c][1]);
+          hi.z = tf32_rna(v[c][2]);
+          hi.w = tf32_rna(v[c][3]);
+          lo.x = tf32_rna(v[c][0] - hi.x);
+          lo.y = tf32_rna(v[c][1] - hi.y);
+          lo.z = tf32_rna(v[c][2] - hi.z);
+          lo.w = tf32_rna(v[c][3] - hi.w);
+          const int idx = tc_canon(3 * e + c, 4 * kc, KP);
+          *reinterpret_cast<float4*>(Xs + idx) = hi;
+          *reinterpret_cast<float4*>(Xs + L::XB / 4 + idx) = lo;
+        }
+      }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+
+    // ---- phase C: 3 x (KP / 8) tensor-core MMAs into TMEM
+    if (t == 0) {
+      tc_fence_after();
+      uint32_t acc = 0;
+#pragma unroll
+      for (int pr = 0; pr < 3; ++pr) {
+        const uint32_t xa = xaddr + (pr == 2 ? L::XB : 0);
+        const uint32_t ob = oaddr + (pr == 1 ? L::OB : 0);
+#pragma unroll
+        for (int ks = 0; ks < KP / 8; ++ks) {
+          umma_tf32(tmem, umma_desc(xa + ks * 256, LBO, SBO), umma_desc(ob + ks * 256, LBO, SBO),
+                    IDESC, acc);
+          acc = 1;
+        }
+      }
+      umma_commit(mma_bar);
+      mma_inflight = true;
+    }
+    ok = mbar_wait_bounded(mma_bar, static_cast<uint32_t>(it & 1), kWaitLimitNs);
+    if (t == 0 && ok) mma_inflight = false;
+    tc_fence_after();
+
+    // ---- phase D: stage update from the accumulator (warps 0-3, one row each)
+    if (warp < 4) {
+      float acc[NN];
+#pragma unroll
+      for (int c0 = 0; c0 < NN; c0 += 16) {
+        float v16[16];
+        tmem_ld16(tmem + (static_cast<uint32_t>(32 * warp) << 16) + c0, v16);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[c0 + j] = v16[j];
+      }
+      tmem_ld_wait();
+      const int r = 32 * warp + lane;
+      const int e = r / 3, c = r - 3 * (r / 3);
+      if (ok && r < L::ROWS && e < nvalid) {
+        const int off = c * E * Np + e * Np;
+        const bool full_block = nvalid == E;
+        const int64_t g = static_cast<int64_t>(c) * fs + static_cast<int64_t>(k0 + e) * Np;
+#pragma unroll
+        for (int n = 0; n < Np; ++n) {
+          if (MODE == kModeRhs) {
+            if (full_block)
+              sq[off + n] = acc[n];
+            else
+              p.rhs[g + n] = acc[n];
+          } else {
+            const float rn =
+                (MODE == kModeFirstStage) ? p.dt * acc[n] : p.a * sres[off + n] + p.dt * acc[n];
+            const float qn = sq[off + n] + p.b * rn;
+            if (full_block) {
+              sq[off + n] = qn;
+              sres[off + n] = rn;
+            } else {
+              p.qout[g + n] = qn;
+              p.res[g + n] = rn;
+            }
+          }
+        }
+      }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    if (__syncthreads_or(!ok)) break;
+
+    // ---- stores of a full block, then refill this stage buffer
+    if (t == 0) {
+      if (nvalid == E) {
+        if (MODE == kModeRhs) {
+#pragma unroll
+          for (int f = 0; f < 3; ++f) tma_store_1d(p.rhs + f * fs + k0 * Np, sq + f * E * Np, L::QB);
+        } else {
+#pragma unroll
+          for (int f = 0; f < 3; ++f) {
+            tma_store_1d(p.qout + f * fs + k0 * Np, sq + f * E * Np, L::QB);
+            tma_store_1d(p.res + f * fs + k0 * Np, sres + f * E * Np, L::QB);
+          }
+        }
+        bulk_commit();
+      }
+      if (issued < niter) {
+        bulk_wait_read_all();  // stores have read the stage buffer
+        fence_proxy_async();
+        issue(issued);
+        ++issued;
+      }
+    }
+  }
+
+  if (t == 0) {
+    if (it < niter) {
+      // a wait expired: report, then drain this CTA's loads in flight
+      atomicExch(p.status, 1);
+      for (int j = it; j < issued; ++j)
+        mbar_wait_bounded(&full[j % S], static_cast<uint32_t>((j / S) & 1), kWaitLimitNs);
+      if (mma_inflight) mbar_wait_bounded(mma_bar, static_cast<uint32_t>(it & 1), kWaitLimitNs);
+    }
+    bulk_wait_all();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, L::TMEM_COLS);
+}
+
+template <int N, int MODE>
+cudaError_t launch_stage_tc_mode(const StageArgs<float>& args, int num_sms, cudaStream_t stream) {
+  using L = TcLayout<N>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t err = cudaFuncSetAttribute(dg_stage_tc_kernel<N, MODE>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(L::SMEM_BYTES));
+    if (err != cudaSuccess) return err;
+    configured = true;
+  }
+  const int64_t nblk = (args.K + L::E - 1) / L::E;
+  int64_t grid = num_sms;  // one CTA per SM (shared memory and TMEM sized for it)
+  if (grid > nblk) grid = nblk;
+  if (grid < 1) grid = 1;
+  dg_stage_tc_kernel<N, MODE>
+      <<<static_cast<unsigned>(grid), L::THREADS, L::SMEM_BYTES, stream>>>(args);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_stage_tc(const StageArgs<float>& args, int mode, int num_sms,
+                            cudaStream_t stream) {
+  if (mode == kModeRhs) return launch_stage_tc_mode<N, kModeRhs>(args, num_sms, stream);
+  if (mode == kModeFirstStage) return launch_stage_tc_mode<N, kModeFirstStage>(args, num_sms, stream);
+  return launch_stage_tc_mode<N, kModeStage>(args, num_sms, stream);
+}
+
+}  // namespace dgw

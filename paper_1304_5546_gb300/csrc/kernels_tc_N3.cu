@@ -1,0 +1,6 @@
+// Order-3 instantiation of the FP32 tensor-core stage kernel.
+#include "kernels_tc.cuh"
+
+namespace dgw {
+template cudaError_t launch_stage_tc<3>(const StageArgs<float>&, int, int, cudaStream_t);
+}  // namespace dgw

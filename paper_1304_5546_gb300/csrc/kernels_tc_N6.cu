@@ -1,0 +1,6 @@
+// Order-6 instantiation of the FP32 tensor-core stage kernel.
+#include "kernels_tc.cuh"
+
+namespace dgw {
+template cudaError_t launch_stage_tc<6>(const StageArgs<float>&, int, int, cudaStream_t);
+}  // namespace dgw

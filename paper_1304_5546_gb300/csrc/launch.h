@@ -26,12 +26,36 @@ struct StageArgs {
   const T* LIFT = nullptr;        // Np x Nafp
   T a = 0, b = 0, dt = 0;
   int* status = nullptr;  // set to 1 by a CTA whose bounded wait expired
+  // tensor-core path only: [Dr | Ds | LIFT] as TF32 hi and lo parts, each an
+  // tc_nn(N) x tc_kp(N) tile in the core-matrix layout of tc_canon
+  const float* tc_op = nullptr;
 };
 
 enum StageMode : int { kModeRhs = 0, kModeFirstStage = 1, kModeStage = 2 };
 
-// One fused stage launch for order N in precision T (see kernels.cuh).
+// One fused stage launch for order N in precision T on the CUDA cores (see
+// kernels.cuh).
 template <typename T, int N>
 cudaError_t launch_stage(const StageArgs<T>& args, int mode, int num_sms, cudaStream_t stream);
+
+// Tensor-core path (FP32 fields, 3xTF32 products; see kernels_tc.cuh).  The
+// element-local products of a block of elements form one GEMM
+//   D[3E x Np] = X[3E x KD] [Dr | Ds | LIFT]^T,   KD = 2 Np + Nafp,
+// K padded to tc_kp(N) (multiple of 8), N padded to tc_nn(N) (multiple of 16).
+__host__ __device__ constexpr int tc_np(int N) { return (N + 1) * (N + 2) / 2; }
+__host__ __device__ constexpr int tc_kd(int N) { return 2 * tc_np(N) + 3 * (N + 1); }
+__host__ __device__ constexpr int tc_kp(int N) { return (tc_kd(N) + 7) / 8 * 8; }
+__host__ __device__ constexpr int tc_nn(int N) { return (tc_np(N) + 15) / 16 * 16; }
+// Float index of element (row n, column k) of a K-major operand tile with kp
+// columns in the no-swizzle canonical layout: 8-row x 16-byte core matrices
+// of 128 contiguous bytes, K-adjacent core matrices 128 bytes apart, 8-row
+// groups kp/4 * 128 bytes apart.
+__host__ __device__ constexpr int tc_canon(int n, int k, int kp) {
+  return ((n / 8) * (kp / 4) + k / 4) * 32 + (n % 8) * 4 + (k % 4);
+}
+
+template <int N>
+cudaError_t launch_stage_tc(const StageArgs<float>& args, int mode, int num_sms,
+                            cudaStream_t stream);
 
 }  // namespace dgw

@@ -13,7 +13,7 @@ from synth import (cavity_mode, gaussian_pulse, jittered_delaunay_mesh, random_f
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp32simt": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +34,7 @@ def _solver(P, mesh, N, prec):
     return P.Solver(*mesh, N=N, precision=prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32simt"])
 @pytest.mark.parametrize("N", list(range(1, 8)))
 def test_rhs_parity_random_fields(P, N, prec):
     # 2 * 9^2 = 162 elements: several CTAs and a ragged last block at every N
@@ -48,7 +48,7 @@ def test_rhs_parity_random_fields(P, N, prec):
     assert _rel(got, want) <= TOL[prec], _rel(got, want)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32simt"])
 @pytest.mark.parametrize("N", [1, 3, 5, 7])
 def test_lsrk_steps_parity(P, N, prec):
     mesh = jittered_delaunay_mesh(8, seed=7 * N)
@@ -107,7 +107,7 @@ def test_config1_cavity_fp64(P):
     assert np.abs(got - exact).max() < 2.0e-4
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32simt"])
 def test_tiny_meshes(P, prec):
     # K = 1 (all faces PEC), K = 2 and K = 3 at every order
     meshes = [
@@ -191,7 +191,8 @@ def test_step_host_matches_device_step(P):
     assert torch.equal(h.cuda(), qd)
 
 
-def test_full_size_one_step_fp32(P):
+@pytest.mark.parametrize("prec", ["fp32", "fp32simt"])
+def test_full_size_one_step_fp32(P, prec):
     # the benchmark workload: ~1.0M-element jittered Delaunay mesh, N = 5,
     # FP32, Gaussian pulse (width 0.05) at (0.5, 0.5); one LSRK step in the
     # launch configuration the benchmark times, every element compared.
@@ -203,7 +204,7 @@ def test_full_size_one_step_fp32(P):
     N = 5
     d = O.Discretization(*mesh, N)
     q0 = np.stack(gaussian_pulse(d.x, d.y)).astype(np.float32).astype(np.float64)
-    s = _solver(P, mesh, N, "fp32")
+    s = _solver(P, mesh, N, prec)
     dt = s.cfl_dt()
     q = s.from_numpy(q0)
     res = s.new_fields()
