@@ -32,6 +32,7 @@ struct dg_op {
   void* d_Dr = nullptr;
   void* d_Ds = nullptr;
   void* d_LIFT = nullptr;
+  void* d_lam = nullptr;   // vertex-interpolant weights per node
   void* d_geo = nullptr;
   void* d_conn = nullptr;
   void* d_qtmp = nullptr;  // second field buffer for the stage ping-pong
@@ -55,14 +56,15 @@ dg_status cuda_fail(cudaError_t err, const char* where) {
 }
 
 void free_device(dg_op* op) {
-  void* ptrs[] = {op->d_Dr,   op->d_Ds,   op->d_LIFT,   op->d_geo, op->d_conn,
-                  op->d_qtmp, op->d_flag, op->d_status, op->d_tcop};
+  void* ptrs[] = {op->d_Dr,   op->d_Ds,   op->d_LIFT,   op->d_geo,  op->d_conn,
+                  op->d_qtmp, op->d_flag, op->d_status, op->d_tcop, op->d_lam};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   op->d_Dr = op->d_Ds = op->d_LIFT = op->d_geo = op->d_conn = op->d_qtmp = nullptr;
   op->d_flag = nullptr;
   op->d_status = nullptr;
   op->d_tcop = nullptr;
+  op->d_lam = nullptr;
 }
 
 // TF32 value nearest to v (ties away from zero), as a float with its 13 low
@@ -108,6 +110,13 @@ dg_status upload(dg_op* op) {
   std::vector<T> Dr(op->ref.Dr.begin(), op->ref.Dr.end());
   std::vector<T> Ds(op->ref.Ds.begin(), op->ref.Ds.end());
   std::vector<T> LIFT(op->ref.LIFT.begin(), op->ref.LIFT.end());
+  // barycentric weights of vertices 2 and 3 at every node: the linear
+  // interpolant through the vertex nodes is u1 + (u2 - u1) lam2 + (u3 - u1) lam3
+  std::vector<T> lam(2 * static_cast<size_t>(Np));
+  for (int n = 0; n < Np; ++n) {
+    lam[n] = static_cast<T>(0.5 * (1.0 + op->ref.r[n]));
+    lam[Np + n] = static_cast<T>(0.5 * (1.0 + op->ref.s[n]));
+  }
   std::vector<T> geo(static_cast<size_t>(Kpad) * dgw::kGeo, T(0));
   std::vector<int32_t> conn(static_cast<size_t>(Kpad) * 3, -1);
   for (int64_t k = 0; k < K; ++k) {
@@ -131,6 +140,7 @@ dg_status upload(dg_op* op) {
       {&op->d_Dr, Dr.data(), Dr.size() * sizeof(T)},
       {&op->d_Ds, Ds.data(), Ds.size() * sizeof(T)},
       {&op->d_LIFT, LIFT.data(), LIFT.size() * sizeof(T)},
+      {&op->d_lam, lam.data(), lam.size() * sizeof(T)},
       {&op->d_geo, geo.data(), geo.size() * sizeof(T)},
       {&op->d_conn, conn.data(), conn.size() * sizeof(int32_t)},
   };
@@ -204,6 +214,7 @@ dgw::StageArgs<T> base_args(const dg_op* op) {
   a.Dr = static_cast<const T*>(op->d_Dr);
   a.Ds = static_cast<const T*>(op->d_Ds);
   a.LIFT = static_cast<const T*>(op->d_LIFT);
+  a.lam = static_cast<const T*>(op->d_lam);
   a.status = op->d_status;
   a.tc_op = op->d_tcop;
   return a;

@@ -16,8 +16,12 @@
 // the threads of an element.  The volume term uses the algebraically equal
 //   dEz/dt = Dr (rx Hy - ry Hx) + Ds (sx Hy - sy Hx)
 // (geometric factors are constant on an affine element): four products per
-// node instead of six.  Operands are centred on the element's node 0
-// (Dr 1 = Ds 1 = 0), which removes FP32 cancellation for smooth fields.
+// node instead of six.  The product operands are the fields minus their
+// linear interpolant through the element's three vertex nodes; Dr and Ds
+// differentiate that linear part exactly ((u_v2 - u_v1)/2 along r,
+// (u_v3 - u_v1)/2 along s), which is added back per element.  Equal in exact
+// arithmetic, this keeps FP32 products small for smooth fields (no
+// cancellation of O(|u|) or O(h |grad u|) terms).
 //
 // Memory pipeline.  Everything a block owns is contiguous in HBM (its q and
 // residual values per field, its geometry records and face codes), so it is
@@ -186,6 +190,7 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
   }
 
   // this thread's rows of Dr, Ds and LIFT, kept in registers
+  const T lam2 = __ldg(p.lam + i), lam3 = __ldg(p.lam + Np + i);
   T dr[Np], ds[Np], lf[Nafp];
 #pragma unroll
   for (int m = 0; m < Np; ++m) {
@@ -251,8 +256,10 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
     T* Wb = Wbuf + (it & 1) * L::W_ELEMS;
     T* Fb = Fbuf + (it & 1) * L::F_ELEMS;
 
-    // ---- phase 1: own values, residual, geometry; centred volume operands
+    // ---- phase 1: own values, residual, geometry; volume operands minus
+    // their linear part
     T hx = 0, hy = 0, ez = 0, r0 = 0, r1 = 0, r2 = 0, rx = 0, ry = 0, sx = 0, sy = 0;
+    T lin0 = 0, lin1 = 0, lin2 = 0;
     if (ok) {
       hx = sq[t];
       hy = sq[E * Np + t];
@@ -266,10 +273,20 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
       ry = sg[e * kGeo + 1];
       sx = sg[e * kGeo + 2];
       sy = sg[e * kGeo + 3];
-      const T dhx = hx - sq[e * Np], dhy = hy - sq[E * Np + e * Np];
-      Wb[(0 * E + e) * NPAD + i] = ez - sq[2 * E * Np + e * Np];
+      const T* qe = sq + e * Np;  // vertex nodes: 0, N, Np - 1
+      const T x1 = qe[0], x2 = qe[N], x3 = qe[Np - 1];
+      const T y1 = qe[E * Np], y2 = qe[E * Np + N], y3 = qe[E * Np + Np - 1];
+      const T z1 = qe[2 * E * Np], z2 = qe[2 * E * Np + N], z3 = qe[2 * E * Np + Np - 1];
+      const T dhx = (hx - x1) - ((x2 - x1) * lam2 + (x3 - x1) * lam3);
+      const T dhy = (hy - y1) - ((y2 - y1) * lam2 + (y3 - y1) * lam3);
+      Wb[(0 * E + e) * NPAD + i] = (ez - z1) - ((z2 - z1) * lam2 + (z3 - z1) * lam3);
       Wb[(1 * E + e) * NPAD + i] = rx * dhy - ry * dhx;
       Wb[(2 * E + e) * NPAD + i] = sx * dhy - sy * dhx;
+      // derivatives of the linear part along r and s
+      const T grz = T(0.5) * (z2 - z1), gsz = T(0.5) * (z3 - z1);
+      lin0 = -(ry * grz + sy * gsz);
+      lin1 = rx * grz + sx * gsz;
+      lin2 = T(0.5) * (rx * (y2 - y1) - ry * (x2 - x1) + sx * (y3 - y1) - sy * (x3 - x1));
     }
     if (__syncthreads_or(!ok)) break;
 
@@ -372,9 +389,9 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
         }
       }
     }
-    const T rhsHx = -(ry * dEzdr + sy * dEzds) + l0;
-    const T rhsHy = (rx * dEzdr + sx * dEzds) + l1;
-    const T rhsEz = (cA + cB) + l2;
+    const T rhsHx = -(ry * dEzdr + sy * dEzds) + lin0 + l0;
+    const T rhsHy = (rx * dEzdr + sx * dEzds) + lin1 + l1;
+    const T rhsEz = (cA + cB) + lin2 + l2;
 
     if (valid) {
       if (MODE == kModeRhs) {

@@ -8,12 +8,17 @@
 // update, or written out as the right-hand side.
 //
 // The products of a block of E elements form one dense contraction.  With
-// X rows per element (centred Ez_c = Ez - Ez_0, A = rx (Hy - Hy_0) - ry (Hx
-// - Hx_0), B = sx (Hy - Hy_0) - sy (Hx - Hx_0), F_c = Fscale/2 * flux_c):
-//   row 3e+0 = [ -ry Ez_c | -sy Ez_c | F_x ]  ->  dHx/dt
-//   row 3e+1 = [  rx Ez_c |  sx Ez_c | F_y ]  ->  dHy/dt
+// X rows per element (u_d = u minus its linear interpolant through the
+// element's vertex nodes; A = rx Hy_d - ry Hx_d, B = sx Hy_d - sy Hx_d;
+// F_c = Fscale/2 * flux_c):
+//   row 3e+0 = [ -ry Ez_d | -sy Ez_d | F_x ]  ->  dHx/dt
+//   row 3e+1 = [  rx Ez_d |  sx Ez_d | F_y ]  ->  dHy/dt
 //   row 3e+2 = [  A       |  B       | F_z ]  ->  dEz/dt
-// the right-hand side is D = X [Dr | Ds | LIFT]^T: M = 3E rows (<= 128),
+// the right-hand side is D = X [Dr | Ds | LIFT]^T plus, per element and row,
+// the chain-rule combination of the linear part's exact derivatives
+// ((u_v2 - u_v1)/2 along r, (u_v3 - u_v1)/2 along s), added in the epilogue.
+// The deflation keeps the products' operands O(h^2) for smooth fields, so
+// their TF32 rounding stays far below FP32 accuracy.  M = 3E rows (<= 128),
 // K = 2 Np + Nafp (padded to 8), N = Np (padded to 16).  FP32 accuracy
 // comes from three TF32 products, X_hi Op_hi + X_hi Op_lo + X_lo Op_hi, with
 // hi = TF32 round-to-nearest of the value and lo = TF32 rounding of the rest
@@ -85,6 +90,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
   uint64_t* op_bar = reinterpret_cast<uint64_t*>(smem + 72);   // operator tiles landed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 80);
   int* nbr = reinterpret_cast<int*>(smem + 128);  // [6][Nfp] neighbour face-node table
+  float* lam = reinterpret_cast<float*>(smem + 384);  // [2][Np] vertex-interpolant weights
   unsigned char* stages = smem + L::OFF_STAGES;
   float* Xs = reinterpret_cast<float*>(smem + L::OFF_X);  // [2][128 x KP] canonical
   float* Fs = reinterpret_cast<float*>(smem + L::OFF_F);  // [E][3][FPAD]
@@ -110,6 +116,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     const int c = t / Nfp, jj = t - c * Nfp;
     nbr[t] = face_node_dev(N, c >> 1, (c & 1) ? (N - jj) : jj);
   }
+  if (t < 2 * Np) lam[t] = __ldg(p.lam + t);
   // zero both X tiles once: K padding columns and rows beyond 3E stay zero
   {
     float4* x4 = reinterpret_cast<float4*>(Xs);
@@ -255,15 +262,19 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
         const float* qe = sq + e * Np;
         const float* ge = sg + e * kGeo;
         const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
-        const float hx0 = qe[0], hy0 = qe[E * Np], ez0 = qe[2 * E * Np];
+        const float x1 = qe[0], x2 = qe[N], x3 = qe[Np - 1];
+        const float y1 = qe[E * Np], y2 = qe[E * Np + N], y3 = qe[E * Np + Np - 1];
+        const float z1 = qe[2 * E * Np], z2 = qe[2 * E * Np + N], z3 = qe[2 * E * Np + Np - 1];
         float v[3][4];
 #pragma unroll
         for (int uu = 0; uu < 4; ++uu) {
           const int k = 4 * kc + uu;
           if (k < 2 * Np) {
             const int m = k < Np ? k : k - Np;
-            const float ec = qe[2 * E * Np + m] - ez0;
-            const float dhx = qe[m] - hx0, dhy = qe[E * Np + m] - hy0;
+            const float l2 = lam[m], l3 = lam[Np + m];
+            const float ec = (qe[2 * E * Np + m] - z1) - ((z2 - z1) * l2 + (z3 - z1) * l3);
+            const float dhx = (qe[m] - x1) - ((x2 - x1) * l2 + (x3 - x1) * l3);
+            const float dhy = (qe[E * Np + m] - y1) - ((y2 - y1) * l2 + (y3 - y1) * l3);
             if (k < Np) {
               v[0][uu] = -ry * ec;
               v[1][uu] = rx * ec;
@@ -339,6 +350,23 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       const int r = 32 * warp + lane;
       const int e = r / 3, c = r - 3 * (r / 3);
       if (ok && r < L::ROWS && e < nvalid) {
+        // chain-rule combination of the linear part's derivatives for row c
+        const float* qe = sq + e * Np;
+        const float* ge = sg + e * kGeo;
+        const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
+        float lin;
+        if (c < 2) {
+          const float z1 = qe[2 * E * Np];
+          const float grz = 0.5f * (qe[2 * E * Np + N] - z1);
+          const float gsz = 0.5f * (qe[2 * E * Np + Np - 1] - z1);
+          lin = (c == 0) ? -(ry * grz + sy * gsz) : (rx * grz + sx * gsz);
+        } else {
+          const float x1 = qe[0], y1 = qe[E * Np];
+          lin = 0.5f * (rx * (qe[E * Np + N] - y1) - ry * (qe[N] - x1) +
+                        sx * (qe[E * Np + Np - 1] - y1) - sy * (qe[Np - 1] - x1));
+        }
+#pragma unroll
+        for (int n = 0; n < Np; ++n) acc[n] += lin;
         const int off = c * E * Np + e * Np;
         const bool full_block = nvalid == E;
         const int64_t g = static_cast<int64_t>(c) * fs + static_cast<int64_t>(k0 + e) * Np;

@@ -24,6 +24,7 @@ struct StageArgs {
   const T* Dr = nullptr;          // Np x Np
   const T* Ds = nullptr;          // Np x Np
   const T* LIFT = nullptr;        // Np x Nafp
+  const T* lam = nullptr;         // [2][Np]: (1 + r_n) / 2, (1 + s_n) / 2 per node
   T a = 0, b = 0, dt = 0;
   int* status = nullptr;  // set to 1 by a CTA whose bounded wait expired
   // tensor-core path only: [Dr | Ds | LIFT] as TF32 hi and lo parts, each an
