@@ -48,14 +48,19 @@ struct TcLayout {
   static constexpr int ROWS = 3 * E;
   static constexpr int KD = tc_kd(N), KP = tc_kp(N), KG = KP / 4;
   static constexpr int NN = tc_nn(N);
-  static constexpr int TMEM_COLS = NN <= 32 ? 32 : 64;
-  static constexpr int THREADS = 256;
+  static constexpr int ACC_COLS = NN <= 32 ? 32 : 64;  // TMEM columns per accumulator
+  static constexpr int TMEM_COLS = 2 * ACC_COLS;       // two accumulators
+  // warp roles: 0-3 epilogue (TMEM lane quarters), 4-11 flux + operand
+  // build, 12 control (TMA loads and stores, MMA issue)
+  static constexpr int EPI_WARPS = 4, BUILD_WARPS = 8;
+  static constexpr int THREADS = 32 * (EPI_WARPS + BUILD_WARPS + 1);
+  static constexpr int BUILD_THREADS = 32 * BUILD_WARPS;
   static constexpr int FPAD = round_up(Nafp, 4);
   static constexpr int TASKS = E * Nafp;
-  static constexpr int TPT = (TASKS + THREADS - 1) / THREADS;
+  static constexpr int TPT = (TASKS + BUILD_THREADS - 1) / BUILD_THREADS;
   static constexpr int KGU = (KD + 3) / 4;  // 16-byte K chunks that hold data
   static constexpr int ITEMS = E * KGU;
-  static constexpr int IPT = (ITEMS + THREADS - 1) / THREADS;
+  static constexpr int IPT = (ITEMS + BUILD_THREADS - 1) / BUILD_THREADS;
   static constexpr int QB = E * Np * 4;
   static constexpr int GB = E * kGeo * 4;
   static constexpr int CB = E * 3 * 4;
@@ -72,6 +77,7 @@ struct TcLayout {
   static_assert(SMEM_BYTES <= 232448, "shared memory");
   static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0 && OB % 16 == 0, "TMA chunks");
   static_assert(ROWS <= 128 && NN <= 256 && NN % 16 == 0 && KP % 8 == 0, "UMMA shape");
+  static_assert(S <= 4, "header layout");
 };
 
 template <int N, int MODE>
@@ -80,16 +86,21 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
   using L = TcLayout<N>;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
   constexpr int KD = L::KD, KP = L::KP, NN = L::NN, FPAD = L::FPAD;
-  constexpr int THREADS = L::THREADS, TASKS = L::TASKS, TPT = L::TPT;
+  constexpr int BT = L::BUILD_THREADS, TASKS = L::TASKS, TPT = L::TPT;
   constexpr int KGU = L::KGU, ITEMS = L::ITEMS, IPT = L::IPT;
   constexpr int NQ = (MODE == kModeStage) ? 6 : 3;
 
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem);         // [S]
-  uint64_t* mma_bar = reinterpret_cast<uint64_t*>(smem + 64);  // MMA completion
-  uint64_t* op_bar = reinterpret_cast<uint64_t*>(smem + 72);   // operator tiles landed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 80);
-  int* nbr = reinterpret_cast<int*>(smem + 128);  // [6][Nfp] neighbour face-node table
+  // header: mbarriers, TMEM base, abort flag, tables
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);              // [S] stage loaded
+  uint64_t* out_ready = reinterpret_cast<uint64_t*>(smem + 32);    // [S] outputs written
+  uint64_t* mma_done = reinterpret_cast<uint64_t*>(smem + 64);     // [2] accumulator ready
+  uint64_t* tmem_free = reinterpret_cast<uint64_t*>(smem + 80);    // [2] accumulator read
+  uint64_t* xfull = reinterpret_cast<uint64_t*>(smem + 96);        // operand tile built
+  uint64_t* op_bar = reinterpret_cast<uint64_t*>(smem + 104);      // operator tiles landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 112);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 116);
+  int* nbr = reinterpret_cast<int*>(smem + 128);      // [6][Nfp] neighbour face-node table
   float* lam = reinterpret_cast<float*>(smem + 384);  // [2][Np] vertex-interpolant weights
   unsigned char* stages = smem + L::OFF_STAGES;
   float* Xs = reinterpret_cast<float*>(smem + L::OFF_X);  // [2][128 x KP] canonical
@@ -103,12 +114,19 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
   const int first = blockIdx.x;
   const int niter = first < nblk ? (nblk - 1 - first) / G + 1 : 0;
   const int64_t fs = p.fstride;
-  const float* qin[3] = {p.qin, p.qin + fs, p.qin + 2 * fs};
 
   if (t == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
-    mbar_init(mma_bar, 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&out_ready[s], 32 * L::EPI_WARPS);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&mma_done[b], 1);
+      mbar_init(&tmem_free[b], 32 * L::EPI_WARPS);
+    }
+    mbar_init(xfull, BT);
     mbar_init(op_bar, 1);
+    *abort_flag = 0;
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(tmem_slot, L::TMEM_COLS);
@@ -117,10 +135,10 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     nbr[t] = face_node_dev(N, c >> 1, (c & 1) ? (N - jj) : jj);
   }
   if (t < 2 * Np) lam[t] = __ldg(p.lam + t);
-  // zero both X tiles once: K padding columns and rows beyond 3E stay zero
-  {
+  {  // zero both X tiles once: K padding columns and rows beyond 3E stay zero
     float4* x4 = reinterpret_cast<float4*>(Xs);
-    for (int idx = t; idx < 2 * L::XB / 16; idx += THREADS) x4[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int idx = t; idx < 2 * L::XB / 16; idx += L::THREADS)
+      x4[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   fence_proxy_async();
   tc_fence_before();
@@ -128,228 +146,300 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  auto issue = [&](int it) {
-    const int s = it % S;
-    const int k0 = (first + it * G) * E;
-    const int n = (K - k0) < E ? (K - k0) : E;
-    const uint32_t qb = round16(static_cast<uint32_t>(n * Np * 4));
-    const uint32_t gb = round16(static_cast<uint32_t>(n * kGeo * 4));
-    const uint32_t cb = round16(static_cast<uint32_t>(n * 3 * 4));
-    unsigned char* st = stages + s * L::STAGE_BYTES;
-    mbar_expect_tx(&full[s], NQ * qb + gb + cb);
-#pragma unroll
-    for (int f = 0; f < 3; ++f) tma_load_1d(st + f * L::QB, p.qin + f * fs + k0 * Np, qb, &full[s]);
-    if (MODE == kModeStage) {
-#pragma unroll
-      for (int f = 0; f < 3; ++f)
-        tma_load_1d(st + (3 + f) * L::QB, p.res + f * fs + k0 * Np, qb, &full[s]);
-    }
-    tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * kGeo, gb, &full[s]);
-    tma_load_1d(st + 6 * L::QB + L::GB, p.conn + static_cast<int64_t>(k0) * 3, cb, &full[s]);
+  auto fail = [&]() {
+    *abort_flag = 1;
+    atomicExch(p.status, 1);
   };
 
-  int issued = 0;
-  bool mma_inflight = false;  // (thread 0) an MMA group was committed, not yet seen done
-  if (t == 0) {
-    mbar_expect_tx(op_bar, 2 * L::OB);
-    tma_load_1d(smem + L::OFF_OP, p.tc_op, 2 * L::OB, op_bar);
-    for (; issued < niter && issued < S; ++issued) issue(issued);
-  }
-
-  // flux tasks of this thread (fixed across blocks)
-  int task_e[TPT], task_j[TPT], task_f[TPT], task_jj[TPT];
+  if (warp == L::EPI_WARPS + L::BUILD_WARPS) {
+    // ======================= control warp: loads, MMAs, stores (lane 0)
+    if (lane == 0) {
+      int issued = 0;
+      auto issue = [&](int it) {
+        const int s = it % S;
+        const int k0 = (first + it * G) * E;
+        const int n = (K - k0) < E ? (K - k0) : E;
+        const uint32_t qb = round16(static_cast<uint32_t>(n * Np * 4));
+        const uint32_t gb = round16(static_cast<uint32_t>(n * kGeo * 4));
+        const uint32_t cb = round16(static_cast<uint32_t>(n * 3 * 4));
+        unsigned char* st = stages + s * L::STAGE_BYTES;
+        mbar_expect_tx(&full[s], NQ * qb + gb + cb);
 #pragma unroll
-  for (int u = 0; u < TPT; ++u) {
-    const int tau = t + u * THREADS;
-    task_e[u] = tau < TASKS ? tau / Nafp : E;
-    task_j[u] = tau - (tau / Nafp) * Nafp;
-    task_f[u] = task_j[u] / Nfp;
-    task_jj[u] = task_j[u] - task_f[u] * Nfp;
-  }
-  // X build items of this thread: (element, 16-byte K chunk), element fastest
-  int item_e[IPT], item_kc[IPT];
+        for (int f = 0; f < 3; ++f)
+          tma_load_1d(st + f * L::QB, p.qin + f * fs + k0 * Np, qb, &full[s]);
+        if (MODE == kModeStage) {
 #pragma unroll
-  for (int u = 0; u < IPT; ++u) {
-    const int idx = t + u * THREADS;
-    item_kc[u] = idx < ITEMS ? idx / E : KGU;  // KGU marks "no item"
-    item_e[u] = idx - (idx / E) * E;
-  }
+          for (int f = 0; f < 3; ++f)
+            tma_load_1d(st + (3 + f) * L::QB, p.res + f * fs + k0 * Np, qb, &full[s]);
+        }
+        tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * kGeo, gb, &full[s]);
+        tma_load_1d(st + 6 * L::QB + L::GB, p.conn + static_cast<int64_t>(k0) * 3, cb, &full[s]);
+      };
+      // outputs of block jj leave by bulk stores; its stage is then refilled
+      auto drain_block = [&](int jj) -> bool {
+        const int s = jj % S;
+        if (!mbar_wait_or_abort(&out_ready[s], static_cast<uint32_t>((jj / S) & 1), abort_flag))
+          return false;
+        const int k0 = (first + jj * G) * E;
+        if (K - k0 >= E) {
+          const float* sq = reinterpret_cast<const float*>(stages + s * L::STAGE_BYTES);
+          if (MODE == kModeRhs) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+              tma_store_1d(p.rhs + f * fs + k0 * Np, sq + f * E * Np, L::QB);
+          } else {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+              tma_store_1d(p.qout + f * fs + k0 * Np, sq + f * E * Np, L::QB);
+              tma_store_1d(p.res + f * fs + k0 * Np, sq + (3 + f) * E * Np, L::QB);
+            }
+          }
+          bulk_commit();
+        }
+        if (issued < niter) {  // issued == jj + S: same stage
+          bulk_wait_read_all();
+          fence_proxy_async();
+          issue(issued);
+          ++issued;
+        }
+        return true;
+      };
 
-  float trc[TPT][3];
-  auto gather = [&](int it) {
-    const int32_t* sc = reinterpret_cast<const int32_t*>(stages + (it % S) * L::STAGE_BYTES +
-                                                         6 * L::QB + L::GB);
-    const int k0 = (first + it * G) * E;
+      mbar_expect_tx(op_bar, 2 * L::OB);
+      tma_load_1d(smem + L::OFF_OP, p.tc_op, 2 * L::OB, op_bar);
+      for (; issued < niter && issued < S; ++issued) issue(issued);
+      bool ok = mbar_wait_or_abort(op_bar, 0, abort_flag);
+      const uint32_t xaddr = smem_u32(Xs);
+      const uint32_t oaddr = smem_u32(smem + L::OFF_OP);
+      constexpr uint32_t LBO = 128, SBO = L::KG * 128;
+      constexpr uint32_t IDESC = umma_idesc_tf32(128, NN);
+      int mma_pending = -1;  // block whose MMA group may still run
+      for (int j = 0; ok && j < niter; ++j) {
+        ok = mbar_wait_or_abort(xfull, static_cast<uint32_t>(j & 1), abort_flag);
+        if (ok && j >= 2)
+          ok = mbar_wait_or_abort(&tmem_free[j & 1], static_cast<uint32_t>(((j - 2) >> 1) & 1),
+                                  abort_flag);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t dacc = tmem + static_cast<uint32_t>((j & 1) * L::ACC_COLS);
+        uint32_t acc = 0;
+#pragma unroll
+        for (int pr = 0; pr < 3; ++pr) {  // X_hi Op_hi, X_hi Op_lo, X_lo Op_hi
+          const uint32_t xa = xaddr + (pr == 2 ? L::XB : 0);
+          const uint32_t ob = oaddr + (pr == 1 ? L::OB : 0);
+#pragma unroll
+          for (int ks = 0; ks < KP / 8; ++ks) {
+            umma_tf32(dacc, umma_desc(xa + ks * 256, LBO, SBO),
+                      umma_desc(ob + ks * 256, LBO, SBO), IDESC, acc);
+            acc = 1;
+          }
+        }
+        umma_commit(&mma_done[j & 1]);
+        mma_pending = j;
+        if (j >= 1) ok = drain_block(j - 1);
+      }
+      if (ok && niter > 0) ok = drain_block(niter - 1);
+      if (!ok) {
+        fail();
+        // let this CTA's asynchronous work land (each wait bounded)
+        for (int jj = (issued > S ? issued - S : 0); jj < issued; ++jj)
+          mbar_wait_bounded(&full[jj % S], static_cast<uint32_t>((jj / S) & 1), kWaitLimitNs);
+        if (mma_pending >= 0)
+          mbar_wait_bounded(&mma_done[mma_pending & 1],
+                            static_cast<uint32_t>((mma_pending >> 1) & 1), kWaitLimitNs);
+      }
+      bulk_wait_all();
+    }
+  } else if (warp >= L::EPI_WARPS) {
+    // ======================= build warps: flux, then GEMM operand rows
+    const int bt = t - 32 * L::EPI_WARPS;
+    const float* qin[3] = {p.qin, p.qin + fs, p.qin + 2 * fs};
+    int task_e[TPT], task_j[TPT], task_f[TPT], task_jj[TPT];
 #pragma unroll
     for (int u = 0; u < TPT; ++u) {
-      trc[u][0] = trc[u][1] = trc[u][2] = 0.f;
-      const int ee = task_e[u];
-      if (ee < E && k0 + ee < K) {
-        const int32_t code = sc[ee * 3 + task_f[u]];
-        if (code >= 0) {
-          const int gP = (code >> 3) * Np + nbr[(code & 7) * Nfp + task_jj[u]];
-          trc[u][0] = __ldg(qin[0] + gP);
-          trc[u][1] = __ldg(qin[1] + gP);
-          trc[u][2] = __ldg(qin[2] + gP);
-        }
-      }
+      const int tau = bt + u * BT;
+      task_e[u] = tau < TASKS ? tau / Nafp : E;
+      task_j[u] = tau - (tau / Nafp) * Nafp;
+      task_f[u] = task_j[u] / Nfp;
+      task_jj[u] = task_j[u] - task_f[u] * Nfp;
     }
-  };
-
-  bool ok = mbar_wait_bounded(op_bar, 0, kWaitLimitNs);
-  if (ok && niter > 0) {
-    ok = mbar_wait_bounded(&full[0], 0, kWaitLimitNs);
-    if (ok) gather(0);
-  }
-  const uint32_t xaddr = smem_u32(Xs);
-  const uint32_t oaddr = smem_u32(smem + L::OFF_OP);
-  constexpr uint32_t LBO = 128, SBO = L::KG * 128;
-  constexpr uint32_t IDESC = umma_idesc_tf32(128, NN);
-
-  int it = 0;
-  for (; it < niter; ++it) {
-    const int s = it % S;
-    if (ok) ok = mbar_wait_bounded(&full[s], static_cast<uint32_t>((it / S) & 1), kWaitLimitNs);
-    const int k0 = (first + it * G) * E;
-    const int nvalid = (K - k0) < E ? (K - k0) : E;
-    unsigned char* st = stages + s * L::STAGE_BYTES;
-    float* sq = reinterpret_cast<float*>(st);  // [3][E Np] q (then the outputs)
-    float* sres = sq + 3 * E * Np;             // [3][E Np] residual
-    const float* sg = reinterpret_cast<const float*>(st + 6 * L::QB);
-    const int32_t* sc = reinterpret_cast<const int32_t*>(st + 6 * L::QB + L::GB);
-
-    // ---- phase A: upwind flux at every face node -> Fs[e][c][j]
-    if (ok) {
-#pragma unroll
-      for (int u = 0; u < TPT; ++u) {
-        const int ee = task_e[u];
-        if (ee < nvalid) {
-          const int f = task_f[u], j = task_j[u];
-          const int nM = ee * Np + face_node_dev(N, f, task_jj[u]);
-          const float hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
-          float dHx, dHy, dEz;
-          if (sc[ee * 3 + f] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
-            dHx = 0.f;
-            dHy = 0.f;
-            dEz = 2.f * ezM;
-          } else {
-            dHx = hxM - trc[u][0];
-            dHy = hyM - trc[u][1];
-            dEz = ezM - trc[u][2];
-          }
-          const float* gf = sg + ee * kGeo + 4 + 3 * f;
-          const float nx = gf[0], ny = gf[1], fsc = gf[2];
-          const float ndotdH = nx * dHx + ny * dHy;
-          float* fo = Fs + (ee * 3) * FPAD + j;
-          fo[0] = fsc * (ny * dEz + (ndotdH * nx - dHx));
-          fo[FPAD] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
-          fo[2 * FPAD] = fsc * (ny * dHx - nx * dHy - dEz);
-        }
-      }
-    }
-    if (ok && it + 1 < niter) {
-      ok = mbar_wait_bounded(&full[(it + 1) % S], static_cast<uint32_t>(((it + 1) / S) & 1),
-                             kWaitLimitNs);
-      if (ok) gather(it + 1);
-    }
-    if (__syncthreads_or(!ok)) break;
-
-    // ---- phase B: GEMM rows of every element, split into TF32 hi / lo
+    int item_e[IPT], item_kc[IPT];  // (element, 16-byte K chunk), element fastest
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
-      const int kc = item_kc[u], e = item_e[u];
-      if (kc < KGU && e < nvalid) {
-        const float* qe = sq + e * Np;
-        const float* ge = sg + e * kGeo;
-        const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
-        const float x1 = qe[0], x2 = qe[N], x3 = qe[Np - 1];
-        const float y1 = qe[E * Np], y2 = qe[E * Np + N], y3 = qe[E * Np + Np - 1];
-        const float z1 = qe[2 * E * Np], z2 = qe[2 * E * Np + N], z3 = qe[2 * E * Np + Np - 1];
-        float v[3][4];
+      const int idx = bt + u * BT;
+      item_kc[u] = idx < ITEMS ? idx / E : KGU;
+      item_e[u] = idx - (idx / E) * E;
+    }
+    float trc[TPT][3];
+    auto gather = [&](int it) {
+      const int32_t* sc = reinterpret_cast<const int32_t*>(stages + (it % S) * L::STAGE_BYTES +
+                                                           6 * L::QB + L::GB);
+      const int k0 = (first + it * G) * E;
 #pragma unroll
-        for (int uu = 0; uu < 4; ++uu) {
-          const int k = 4 * kc + uu;
-          if (k < 2 * Np) {
-            const int m = k < Np ? k : k - Np;
-            const float l2 = lam[m], l3 = lam[Np + m];
-            const float ec = (qe[2 * E * Np + m] - z1) - ((z2 - z1) * l2 + (z3 - z1) * l3);
-            const float dhx = (qe[m] - x1) - ((x2 - x1) * l2 + (x3 - x1) * l3);
-            const float dhy = (qe[E * Np + m] - y1) - ((y2 - y1) * l2 + (y3 - y1) * l3);
-            if (k < Np) {
-              v[0][uu] = -ry * ec;
-              v[1][uu] = rx * ec;
-              v[2][uu] = rx * dhy - ry * dhx;
-            } else {
-              v[0][uu] = -sy * ec;
-              v[1][uu] = sx * ec;
-              v[2][uu] = sx * dhy - sy * dhx;
-            }
-          } else if (k < KD) {
-            const float* fe = Fs + (e * 3) * FPAD + (k - 2 * Np);
-            v[0][uu] = fe[0];
-            v[1][uu] = fe[FPAD];
-            v[2][uu] = fe[2 * FPAD];
-          } else {
-            v[0][uu] = v[1][uu] = v[2][uu] = 0.f;
+      for (int u = 0; u < TPT; ++u) {
+        trc[u][0] = trc[u][1] = trc[u][2] = 0.f;
+        const int ee = task_e[u];
+        if (ee < E && k0 + ee < K) {
+          const int32_t code = sc[ee * 3 + task_f[u]];
+          if (code >= 0) {
+            const int gP = (code >> 3) * Np + nbr[(code & 7) * Nfp + task_jj[u]];
+            trc[u][0] = __ldg(qin[0] + gP);
+            trc[u][1] = __ldg(qin[1] + gP);
+            trc[u][2] = __ldg(qin[2] + gP);
           }
         }
+      }
+    };
+    bool ok = true;
+    if (niter > 0) {
+      ok = mbar_wait_or_abort(&full[0], 0, abort_flag);
+      if (ok) gather(0);
+    }
+    for (int j = 0; j < niter; ++j) {
+      const int s = j % S;
+      if (ok) ok = mbar_wait_or_abort(&full[s], static_cast<uint32_t>((j / S) & 1), abort_flag);
+      const int k0 = (first + j * G) * E;
+      const int nvalid = (K - k0) < E ? (K - k0) : E;
+      const unsigned char* st = stages + s * L::STAGE_BYTES;
+      const float* sq = reinterpret_cast<const float*>(st);
+      const float* sg = reinterpret_cast<const float*>(st + 6 * L::QB);
+      const int32_t* sc = reinterpret_cast<const int32_t*>(st + 6 * L::QB + L::GB);
+
+      // ---- upwind flux at every face node -> Fs[e][c][j], scaled by Fscale/2
+      if (ok) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          float4 hi, lo;
-          hi.x = tf32_rna(v[c][0]);
-          hi.y = tf32_rna(v[c][1]);
-          hi.z = tf32_rna(v[c][2]);
-          hi.w = tf32_rna(v[c][3]);
-          lo.x = tf32_rna(v[c][0] - hi.x);
-          lo.y = tf32_rna(v[c][1] - hi.y);
-          lo.z = tf32_rna(v[c][2] - hi.z);
-          lo.w = tf32_rna(v[c][3] - hi.w);
-          const int idx = tc_canon(3 * e + c, 4 * kc, KP);
-          *reinterpret_cast<float4*>(Xs + idx) = hi;
-          *reinterpret_cast<float4*>(Xs + L::XB / 4 + idx) = lo;
+        for (int u = 0; u < TPT; ++u) {
+          const int ee = task_e[u];
+          if (ee < nvalid) {
+            const int f = task_f[u], jf = task_j[u];
+            const int nM = ee * Np + face_node_dev(N, f, task_jj[u]);
+            const float hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
+            float dHx, dHy, dEz;
+            if (sc[ee * 3 + f] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
+              dHx = 0.f;
+              dHy = 0.f;
+              dEz = 2.f * ezM;
+            } else {
+              dHx = hxM - trc[u][0];
+              dHy = hyM - trc[u][1];
+              dEz = ezM - trc[u][2];
+            }
+            const float* gf = sg + ee * kGeo + 4 + 3 * f;
+            const float nx = gf[0], ny = gf[1], fsc = gf[2];
+            const float ndotdH = nx * dHx + ny * dHy;
+            float* fo = Fs + (ee * 3) * FPAD + jf;
+            fo[0] = fsc * (ny * dEz + (ndotdH * nx - dHx));
+            fo[FPAD] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
+            fo[2 * FPAD] = fsc * (ny * dHx - nx * dHy - dEz);
+          }
         }
       }
-    }
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
+      if (ok && j + 1 < niter) {  // next block's traces, one block ahead
+        ok = mbar_wait_or_abort(&full[(j + 1) % S], static_cast<uint32_t>(((j + 1) / S) & 1),
+                                abort_flag);
+        if (ok) gather(j + 1);
+      }
+      // previous MMA has finished reading the operand tiles
+      if (ok && j >= 1)
+        ok = mbar_wait_or_abort(&mma_done[(j - 1) & 1], static_cast<uint32_t>(((j - 1) >> 1) & 1),
+                                abort_flag);
+      if (named_barrier_or(1, BT, !ok)) break;
 
-    // ---- phase C: 3 x (KP / 8) tensor-core MMAs into TMEM
-    if (t == 0) {
+      // ---- GEMM rows of every element, split into TF32 hi / lo
+#pragma unroll
+      for (int u = 0; u < IPT; ++u) {
+        const int kc = item_kc[u], e = item_e[u];
+        if (kc < KGU && e < nvalid) {
+          const float* qe = sq + e * Np;
+          const float* ge = sg + e * kGeo;
+          const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
+          const float x1 = qe[0], x2 = qe[N], x3 = qe[Np - 1];
+          const float y1 = qe[E * Np], y2 = qe[E * Np + N], y3 = qe[E * Np + Np - 1];
+          const float z1 = qe[2 * E * Np], z2 = qe[2 * E * Np + N], z3 = qe[2 * E * Np + Np - 1];
+          float v[3][4];
+#pragma unroll
+          for (int uu = 0; uu < 4; ++uu) {
+            const int k = 4 * kc + uu;
+            if (k < 2 * Np) {
+              const int m = k < Np ? k : k - Np;
+              const float l2 = lam[m], l3 = lam[Np + m];
+              const float ec = (qe[2 * E * Np + m] - z1) - ((z2 - z1) * l2 + (z3 - z1) * l3);
+              const float dhx = (qe[m] - x1) - ((x2 - x1) * l2 + (x3 - x1) * l3);
+              const float dhy = (qe[E * Np + m] - y1) - ((y2 - y1) * l2 + (y3 - y1) * l3);
+              if (k < Np) {
+                v[0][uu] = -ry * ec;
+                v[1][uu] = rx * ec;
+                v[2][uu] = rx * dhy - ry * dhx;
+              } else {
+                v[0][uu] = -sy * ec;
+                v[1][uu] = sx * ec;
+                v[2][uu] = sx * dhy - sy * dhx;
+              }
+            } else if (k < KD) {
+              const float* fe = Fs + (e * 3) * FPAD + (k - 2 * Np);
+              v[0][uu] = fe[0];
+              v[1][uu] = fe[FPAD];
+              v[2][uu] = fe[2 * FPAD];
+            } else {
+              v[0][uu] = v[1][uu] = v[2][uu] = 0.f;
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float4 hi, lo;
+            hi.x = tf32_rna(v[c][0]);
+            hi.y = tf32_rna(v[c][1]);
+            hi.z = tf32_rna(v[c][2]);
+            hi.w = tf32_rna(v[c][3]);
+            lo.x = tf32_rna(v[c][0] - hi.x);
+            lo.y = tf32_rna(v[c][1] - hi.y);
+            lo.z = tf32_rna(v[c][2] - hi.z);
+            lo.w = tf32_rna(v[c][3] - hi.w);
+            const int idx = tc_canon(3 * e + c, 4 * kc, KP);
+            *reinterpret_cast<float4*>(Xs + idx) = hi;
+            *reinterpret_cast<float4*>(Xs + L::XB / 4 + idx) = lo;
+          }
+        }
+      }
+      fence_proxy_async();
+      mbar_arrive(xfull);
+      // every build thread is done with Fs before the next block's flux
+      if (named_barrier_or(1, BT, false)) break;
+    }
+    if (!ok) fail();
+  } else {
+    // ======================= epilogue warps: accumulator -> stage update
+    bool ok = true;
+    for (int j = 0; j < niter; ++j) {
+      const int s = j % S;
+      ok = ok && mbar_wait_or_abort(&mma_done[j & 1], static_cast<uint32_t>((j >> 1) & 1),
+                                    abort_flag);
+      ok = ok && mbar_wait_or_abort(&full[s], static_cast<uint32_t>((j / S) & 1), abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
       tc_fence_after();
-      uint32_t acc = 0;
-#pragma unroll
-      for (int pr = 0; pr < 3; ++pr) {
-        const uint32_t xa = xaddr + (pr == 2 ? L::XB : 0);
-        const uint32_t ob = oaddr + (pr == 1 ? L::OB : 0);
-#pragma unroll
-        for (int ks = 0; ks < KP / 8; ++ks) {
-          umma_tf32(tmem, umma_desc(xa + ks * 256, LBO, SBO), umma_desc(ob + ks * 256, LBO, SBO),
-                    IDESC, acc);
-          acc = 1;
-        }
-      }
-      umma_commit(mma_bar);
-      mma_inflight = true;
-    }
-    ok = mbar_wait_bounded(mma_bar, static_cast<uint32_t>(it & 1), kWaitLimitNs);
-    if (t == 0 && ok) mma_inflight = false;
-    tc_fence_after();
-
-    // ---- phase D: stage update from the accumulator (warps 0-3, one row each)
-    if (warp < 4) {
       float acc[NN];
+      const uint32_t dacc = tmem + static_cast<uint32_t>((j & 1) * L::ACC_COLS) +
+                            (static_cast<uint32_t>(32 * warp) << 16);
 #pragma unroll
       for (int c0 = 0; c0 < NN; c0 += 16) {
         float v16[16];
-        tmem_ld16(tmem + (static_cast<uint32_t>(32 * warp) << 16) + c0, v16);
+        tmem_ld16(dacc + c0, v16);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[c0 + j] = v16[j];
+        for (int q = 0; q < 16; ++q) acc[c0 + q] = v16[q];
       }
       tmem_ld_wait();
+      tc_fence_before();
+      mbar_arrive(&tmem_free[j & 1]);
+
+      const int k0 = (first + j * G) * E;
+      const int nvalid = (K - k0) < E ? (K - k0) : E;
+      float* sq = reinterpret_cast<float*>(stages + s * L::STAGE_BYTES);  // q, then outputs
+      float* sres = sq + 3 * E * Np;
+      const float* sg = reinterpret_cast<const float*>(stages + s * L::STAGE_BYTES + 6 * L::QB);
       const int r = 32 * warp + lane;
       const int e = r / 3, c = r - 3 * (r / 3);
-      if (ok && r < L::ROWS && e < nvalid) {
+      if (r < L::ROWS && e < nvalid) {
         // chain-rule combination of the linear part's derivatives for row c
         const float* qe = sq + e * Np;
         const float* ge = sg + e * kGeo;
@@ -365,21 +455,20 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
           lin = 0.5f * (rx * (qe[E * Np + N] - y1) - ry * (qe[N] - x1) +
                         sx * (qe[E * Np + Np - 1] - y1) - sy * (qe[Np - 1] - x1));
         }
-#pragma unroll
-        for (int n = 0; n < Np; ++n) acc[n] += lin;
         const int off = c * E * Np + e * Np;
         const bool full_block = nvalid == E;
         const int64_t g = static_cast<int64_t>(c) * fs + static_cast<int64_t>(k0 + e) * Np;
 #pragma unroll
         for (int n = 0; n < Np; ++n) {
+          const float rhs = acc[n] + lin;
           if (MODE == kModeRhs) {
             if (full_block)
-              sq[off + n] = acc[n];
+              sq[off + n] = rhs;
             else
-              p.rhs[g + n] = acc[n];
+              p.rhs[g + n] = rhs;
           } else {
             const float rn =
-                (MODE == kModeFirstStage) ? p.dt * acc[n] : p.a * sres[off + n] + p.dt * acc[n];
+                (MODE == kModeFirstStage) ? p.dt * rhs : p.a * sres[off + n] + p.dt * rhs;
             const float qn = sq[off + n] + p.b * rn;
             if (full_block) {
               sq[off + n] = qn;
@@ -391,45 +480,12 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
           }
         }
       }
+      fence_proxy_async();
+      mbar_arrive(&out_ready[s]);
     }
-    fence_proxy_async();
-    tc_fence_before();
-    if (__syncthreads_or(!ok)) break;
-
-    // ---- stores of a full block, then refill this stage buffer
-    if (t == 0) {
-      if (nvalid == E) {
-        if (MODE == kModeRhs) {
-#pragma unroll
-          for (int f = 0; f < 3; ++f) tma_store_1d(p.rhs + f * fs + k0 * Np, sq + f * E * Np, L::QB);
-        } else {
-#pragma unroll
-          for (int f = 0; f < 3; ++f) {
-            tma_store_1d(p.qout + f * fs + k0 * Np, sq + f * E * Np, L::QB);
-            tma_store_1d(p.res + f * fs + k0 * Np, sres + f * E * Np, L::QB);
-          }
-        }
-        bulk_commit();
-      }
-      if (issued < niter) {
-        bulk_wait_read_all();  // stores have read the stage buffer
-        fence_proxy_async();
-        issue(issued);
-        ++issued;
-      }
-    }
+    if (!ok) fail();
   }
 
-  if (t == 0) {
-    if (it < niter) {
-      // a wait expired: report, then drain this CTA's loads in flight
-      atomicExch(p.status, 1);
-      for (int j = it; j < issued; ++j)
-        mbar_wait_bounded(&full[j % S], static_cast<uint32_t>((j / S) & 1), kWaitLimitNs);
-      if (mma_inflight) mbar_wait_bounded(mma_bar, static_cast<uint32_t>(it & 1), kWaitLimitNs);
-    }
-    bulk_wait_all();
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
