@@ -80,26 +80,26 @@ float tf32_round(double v) {
 
 // [Dr | Ds | LIFT] as the B operand of the tensor-core kernel: hi and lo TF32
 // parts (v ~ hi + lo, split in FP64), each an nn x kp tile in the core-matrix
-// layout of dgw::tc_canon; rows >= Np and columns >= 2 Np + Nafp are zero.
+// layout of dgw::tc_canon, parts at the columns dgw::tc_kd describes; rows
+// >= Np and padding columns are zero.
 std::vector<float> tc_operator_tiles(const dgw::RefElement& R) {
   const int N = R.N, Np = R.Np, Nafp = R.Nafp;
-  const int kp = dgw::tc_kp(N), nn = dgw::tc_nn(N);
+  const int kp = dgw::tc_kp(N), nn = dgw::tc_nn(N), npad = dgw::tc_npad(N);
   std::vector<float> out(2 * static_cast<size_t>(nn) * kp, 0.0f);
-  for (int n = 0; n < Np; ++n)
-    for (int k = 0; k < 2 * Np + Nafp; ++k) {
-      double v;
-      if (k < Np)
-        v = R.Dr[n * Np + k];
-      else if (k < 2 * Np)
-        v = R.Ds[n * Np + (k - Np)];
-      else
-        v = R.LIFT[n * Nafp + (k - 2 * Np)];
-      const float hi = tf32_round(v);
-      const float lo = tf32_round(v - static_cast<double>(hi));
-      const int idx = dgw::tc_canon(n, k, kp);
-      out[idx] = hi;
-      out[static_cast<size_t>(nn) * kp + idx] = lo;
+  auto put = [&](int n, int k, double v) {
+    const float hi = tf32_round(v);
+    const float lo = tf32_round(v - static_cast<double>(hi));
+    const int idx = dgw::tc_canon(n, k, kp);
+    out[idx] = hi;
+    out[static_cast<size_t>(nn) * kp + idx] = lo;
+  };
+  for (int n = 0; n < Np; ++n) {
+    for (int m = 0; m < Np; ++m) {
+      put(n, m, R.Dr[n * Np + m]);
+      put(n, npad + m, R.Ds[n * Np + m]);
     }
+    for (int j = 0; j < Nafp; ++j) put(n, 2 * npad + j, R.LIFT[n * Nafp + j]);
+  }
   return out;
 }
 

@@ -14,6 +14,7 @@
 //   row 3e+0 = [ -ry Ez_d | -sy Ez_d | F_x ]  ->  dHx/dt
 //   row 3e+1 = [  rx Ez_d |  sx Ez_d | F_y ]  ->  dHy/dt
 //   row 3e+2 = [  A       |  B       | F_z ]  ->  dEz/dt
+// (each part of a row starts on a 16-byte boundary, see tc_kd)
 // the right-hand side is D = X [Dr | Ds | LIFT]^T plus, per element and row,
 // the chain-rule combination of the linear part's exact derivatives
 // ((u_v2 - u_v1)/2 along r, (u_v3 - u_v1)/2 along s), added in the epilogue.
@@ -55,11 +56,14 @@ struct TcLayout {
   static constexpr int EPI_WARPS = 4, BUILD_WARPS = 8;
   static constexpr int THREADS = 32 * (EPI_WARPS + BUILD_WARPS + 1);
   static constexpr int BUILD_THREADS = 32 * BUILD_WARPS;
+  static constexpr int NPAD = tc_npad(N);
   static constexpr int FPAD = round_up(Nafp, 4);
   static constexpr int TASKS = E * Nafp;
   static constexpr int TPT = (TASKS + BUILD_THREADS - 1) / BUILD_THREADS;
-  static constexpr int KGU = (KD + 3) / 4;  // 16-byte K chunks that hold data
-  static constexpr int ITEMS = E * KGU;
+  // build items per element: NPAD/4 volume chunks (each writes its Dr-part
+  // and Ds-part 16-byte chunks) and FPAD/4 lift chunks
+  static constexpr int IV = NPAD / 4, IF = FPAD / 4;
+  static constexpr int ITEMS = E * (IV + IF);
   static constexpr int IPT = (ITEMS + BUILD_THREADS - 1) / BUILD_THREADS;
   static constexpr int QB = E * Np * 4;
   static constexpr int GB = E * kGeo * 4;
@@ -85,9 +89,9 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     dg_stage_tc_kernel(const StageArgs<float> p) {
   using L = TcLayout<N>;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
-  constexpr int KD = L::KD, KP = L::KP, NN = L::NN, FPAD = L::FPAD;
+  constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FPAD = L::FPAD;
   constexpr int BT = L::BUILD_THREADS, TASKS = L::TASKS, TPT = L::TPT;
-  constexpr int KGU = L::KGU, ITEMS = L::ITEMS, IPT = L::IPT;
+  constexpr int IV = L::IV, ITEMS = L::ITEMS, IPT = L::IPT;
   constexpr int NQ = (MODE == kModeStage) ? 6 : 3;
 
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 112);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 116);
   int* nbr = reinterpret_cast<int*>(smem + 128);      // [6][Nfp] neighbour face-node table
-  float* lam = reinterpret_cast<float*>(smem + 384);  // [2][Np] vertex-interpolant weights
+  float* lam = reinterpret_cast<float*>(smem + 384);  // [2][NPAD] vertex-interpolant weights
   unsigned char* stages = smem + L::OFF_STAGES;
   float* Xs = reinterpret_cast<float*>(smem + L::OFF_X);  // [2][128 x KP] canonical
   float* Fs = reinterpret_cast<float*>(smem + L::OFF_F);  // [E][3][FPAD]
@@ -134,11 +138,15 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     const int c = t / Nfp, jj = t - c * Nfp;
     nbr[t] = face_node_dev(N, c >> 1, (c & 1) ? (N - jj) : jj);
   }
-  if (t < 2 * Np) lam[t] = __ldg(p.lam + t);
-  {  // zero both X tiles once: K padding columns and rows beyond 3E stay zero
+  if (t < 2 * NPAD) {  // [2][NPAD], zero beyond Np
+    const int m = t % NPAD;
+    lam[t] = m < Np ? __ldg(p.lam + (t / NPAD) * Np + m) : 0.f;
+  }
+  {  // zero the X tiles (padding columns and rows beyond 3E stay zero) and Fs
     float4* x4 = reinterpret_cast<float4*>(Xs);
     for (int idx = t; idx < 2 * L::XB / 16; idx += L::THREADS)
       x4[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int idx = t; idx < L::FB / 4; idx += L::THREADS) Fs[idx] = 0.f;
   }
   fence_proxy_async();
   tc_fence_before();
@@ -263,11 +271,11 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       task_f[u] = task_j[u] / Nfp;
       task_jj[u] = task_j[u] - task_f[u] * Nfp;
     }
-    int item_e[IPT], item_kc[IPT];  // (element, 16-byte K chunk), element fastest
+    int item_e[IPT], item_c[IPT];  // (element, chunk), element fastest
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
       const int idx = bt + u * BT;
-      item_kc[u] = idx < ITEMS ? idx / E : KGU;
+      item_c[u] = idx < ITEMS ? idx / E : -1;  // -1: no item
       item_e[u] = idx - (idx / E) * E;
     }
     float trc[TPT][3];
@@ -348,54 +356,71 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       // ---- GEMM rows of every element, split into TF32 hi / lo
 #pragma unroll
       for (int u = 0; u < IPT; ++u) {
-        const int kc = item_kc[u], e = item_e[u];
-        if (kc < KGU && e < nvalid) {
+        const int ch = item_c[u], e = item_e[u];
+        if (ch < 0 || e >= nvalid) continue;
+        float v[6][4];  // rows 3e+0..2: [0..2] first chunk, [3..5] second chunk
+        int k_a, k_b;   // K column of the first / second chunk (k_b < 0: none)
+        if (ch < IV) {
+          // nodes m0..m0+3 minus the vertex-node interpolant; Dr- and Ds-part chunks
+          const int m0 = 4 * ch;
           const float* qe = sq + e * Np;
           const float* ge = sg + e * kGeo;
           const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
           const float x1 = qe[0], x2 = qe[N], x3 = qe[Np - 1];
           const float y1 = qe[E * Np], y2 = qe[E * Np + N], y3 = qe[E * Np + Np - 1];
           const float z1 = qe[2 * E * Np], z2 = qe[2 * E * Np + N], z3 = qe[2 * E * Np + Np - 1];
-          float v[3][4];
+          const float4 l2v = *reinterpret_cast<const float4*>(lam + m0);
+          const float4 l3v = *reinterpret_cast<const float4*>(lam + NPAD + m0);
+          const float l2a[4] = {l2v.x, l2v.y, l2v.z, l2v.w};
+          const float l3a[4] = {l3v.x, l3v.y, l3v.z, l3v.w};
 #pragma unroll
           for (int uu = 0; uu < 4; ++uu) {
-            const int k = 4 * kc + uu;
-            if (k < 2 * Np) {
-              const int m = k < Np ? k : k - Np;
-              const float l2 = lam[m], l3 = lam[Np + m];
-              const float ec = (qe[2 * E * Np + m] - z1) - ((z2 - z1) * l2 + (z3 - z1) * l3);
-              const float dhx = (qe[m] - x1) - ((x2 - x1) * l2 + (x3 - x1) * l3);
-              const float dhy = (qe[E * Np + m] - y1) - ((y2 - y1) * l2 + (y3 - y1) * l3);
-              if (k < Np) {
-                v[0][uu] = -ry * ec;
-                v[1][uu] = rx * ec;
-                v[2][uu] = rx * dhy - ry * dhx;
-              } else {
-                v[0][uu] = -sy * ec;
-                v[1][uu] = sx * ec;
-                v[2][uu] = sx * dhy - sy * dhx;
-              }
-            } else if (k < KD) {
-              const float* fe = Fs + (e * 3) * FPAD + (k - 2 * Np);
-              v[0][uu] = fe[0];
-              v[1][uu] = fe[FPAD];
-              v[2][uu] = fe[2 * FPAD];
-            } else {
-              v[0][uu] = v[1][uu] = v[2][uu] = 0.f;
+            const int m = m0 + uu;
+            float ec = 0.f, dhx = 0.f, dhy = 0.f;
+            if (m < Np) {
+              ec = (qe[2 * E * Np + m] - z1) - ((z2 - z1) * l2a[uu] + (z3 - z1) * l3a[uu]);
+              dhx = (qe[m] - x1) - ((x2 - x1) * l2a[uu] + (x3 - x1) * l3a[uu]);
+              dhy = (qe[E * Np + m] - y1) - ((y2 - y1) * l2a[uu] + (y3 - y1) * l3a[uu]);
             }
+            v[0][uu] = -ry * ec;
+            v[1][uu] = rx * ec;
+            v[2][uu] = rx * dhy - ry * dhx;
+            v[3][uu] = -sy * ec;
+            v[4][uu] = sx * ec;
+            v[5][uu] = sx * dhy - sy * dhx;
           }
+          k_a = m0;
+          k_b = NPAD + m0;
+        } else {
+          const int j0 = 4 * (ch - IV);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
+            const float4 f4 = *reinterpret_cast<const float4*>(Fs + (e * 3 + c) * FPAD + j0);
+            v[c][0] = f4.x;
+            v[c][1] = f4.y;
+            v[c][2] = f4.z;
+            v[c][3] = f4.w;
+          }
+          k_a = 2 * NPAD + j0;
+          k_b = -1;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && k_b < 0) break;
+          const int k = h == 0 ? k_a : k_b;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float* w = v[3 * h + c];
             float4 hi, lo;
-            hi.x = tf32_rna(v[c][0]);
-            hi.y = tf32_rna(v[c][1]);
-            hi.z = tf32_rna(v[c][2]);
-            hi.w = tf32_rna(v[c][3]);
-            lo.x = tf32_rna(v[c][0] - hi.x);
-            lo.y = tf32_rna(v[c][1] - hi.y);
-            lo.z = tf32_rna(v[c][2] - hi.z);
-            lo.w = tf32_rna(v[c][3] - hi.w);
-            const int idx = tc_canon(3 * e + c, 4 * kc, KP);
+            hi.x = tf32_rna(w[0]);
+            hi.y = tf32_rna(w[1]);
+            hi.z = tf32_rna(w[2]);
+            hi.w = tf32_rna(w[3]);
+            lo.x = tf32_rna(w[0] - hi.x);
+            lo.y = tf32_rna(w[1] - hi.y);
+            lo.z = tf32_rna(w[2] - hi.z);
+            lo.w = tf32_rna(w[3] - hi.w);
+            const int idx = tc_canon(3 * e + c, k, KP);
             *reinterpret_cast<float4*>(Xs + idx) = hi;
             *reinterpret_cast<float4*>(Xs + L::XB / 4 + idx) = lo;
           }
