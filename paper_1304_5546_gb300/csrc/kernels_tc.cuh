@@ -51,9 +51,9 @@ struct TcLayout {
   static constexpr int NN = tc_nn(N);
   static constexpr int ACC_COLS = NN <= 32 ? 32 : 64;  // TMEM columns per accumulator
   static constexpr int TMEM_COLS = 2 * ACC_COLS;       // two accumulators
-  // warp roles: 0-3 epilogue (TMEM lane quarters), 4-11 flux + operand
-  // build, 12 control (TMA loads and stores, MMA issue)
-  static constexpr int EPI_WARPS = 4, BUILD_WARPS = 8;
+  // warp roles: 0-3 epilogue (TMEM lane quarters), 4-15 flux + operand
+  // build, 16 control (TMA loads and stores, MMA issue)
+  static constexpr int EPI_WARPS = 4, BUILD_WARPS = 12;
   static constexpr int THREADS = 32 * (EPI_WARPS + BUILD_WARPS + 1);
   static constexpr int BUILD_THREADS = 32 * BUILD_WARPS;
   static constexpr int NPAD = tc_npad(N);
@@ -262,14 +262,19 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     // ======================= build warps: flux, then GEMM operand rows
     const int bt = t - 32 * L::EPI_WARPS;
     const float* qin[3] = {p.qin, p.qin + fs, p.qin + 2 * fs};
-    int task_e[TPT], task_j[TPT], task_f[TPT], task_jj[TPT];
+    // flux tasks of this thread (the same in every block): element slot,
+    // offsets of its own face node, face code, face geometry and flux slot
+    int task_e[TPT], task_jj[TPT], task_nm[TPT], task_cf[TPT], task_gf[TPT], task_fo[TPT];
 #pragma unroll
     for (int u = 0; u < TPT; ++u) {
       const int tau = bt + u * BT;
-      task_e[u] = tau < TASKS ? tau / Nafp : E;
-      task_j[u] = tau - (tau / Nafp) * Nafp;
-      task_f[u] = task_j[u] / Nfp;
-      task_jj[u] = task_j[u] - task_f[u] * Nfp;
+      const int ee = tau / Nafp, j = tau - ee * Nafp, f = j / Nfp, jj = j - f * Nfp;
+      task_e[u] = tau < TASKS ? ee : E;
+      task_jj[u] = jj;
+      task_nm[u] = ee * Np + face_node_dev(N, f, jj);
+      task_cf[u] = ee * 3 + f;
+      task_gf[u] = ee * kGeo + 4 + 3 * f;
+      task_fo[u] = (ee * 3) * FPAD + j;
     }
     int item_e[IPT], item_c[IPT];  // (element, chunk), element fastest
 #pragma unroll
@@ -288,7 +293,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
         trc[u][0] = trc[u][1] = trc[u][2] = 0.f;
         const int ee = task_e[u];
         if (ee < E && k0 + ee < K) {
-          const int32_t code = sc[ee * 3 + task_f[u]];
+          const int32_t code = sc[task_cf[u]];
           if (code >= 0) {
             const int gP = (code >> 3) * Np + nbr[(code & 7) * Nfp + task_jj[u]];
             trc[u][0] = __ldg(qin[0] + gP);
@@ -319,11 +324,10 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
         for (int u = 0; u < TPT; ++u) {
           const int ee = task_e[u];
           if (ee < nvalid) {
-            const int f = task_f[u], jf = task_j[u];
-            const int nM = ee * Np + face_node_dev(N, f, task_jj[u]);
+            const int nM = task_nm[u];
             const float hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
             float dHx, dHy, dEz;
-            if (sc[ee * 3 + f] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
+            if (sc[task_cf[u]] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
               dHx = 0.f;
               dHy = 0.f;
               dEz = 2.f * ezM;
@@ -332,10 +336,10 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
               dHy = hyM - trc[u][1];
               dEz = ezM - trc[u][2];
             }
-            const float* gf = sg + ee * kGeo + 4 + 3 * f;
+            const float* gf = sg + task_gf[u];
             const float nx = gf[0], ny = gf[1], fsc = gf[2];
             const float ndotdH = nx * dHx + ny * dHy;
-            float* fo = Fs + (ee * 3) * FPAD + jf;
+            float* fo = Fs + task_fo[u];
             fo[0] = fsc * (ny * dEz + (ndotdH * nx - dHx));
             fo[FPAD] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
             fo[2 * FPAD] = fsc * (ny * dHx - nx * dHy - dEz);
