@@ -21,11 +21,14 @@
 // The deflation keeps the products' operands O(h^2) for smooth fields, so
 // their TF32 rounding stays far below FP32 accuracy.  M = 3E rows (<= 128),
 // K = 2 Np + Nafp (padded to 8), N = Np (padded to 16).  FP32 accuracy
-// comes from three TF32 products, X_hi Op_hi + X_hi Op_lo + X_lo Op_hi, with
-// hi = TF32 round-to-nearest of the value and lo = TF32 rounding of the rest
-// (Op's split is made on the host from FP64).  One thread issues the
-// tcgen05.mma instructions; the FP32 accumulator lives in TMEM (lane = row)
-// and four warps read it back (tcgen05.ld) for the stage update.
+// comes from three TF32 products, X_hi Op_hi + X_hi Op_lo + X_lo Op_hi: X_hi
+// keeps the top 11 significand bits of X, X_lo = X - X_hi (exact in FP32,
+// truncated to TF32 by the tensor core); Op's hi/lo split is made on the host
+// from FP64 with round-to-nearest.  One MMA of N = 2 Np' computes X_hi
+// [Op_hi ; Op_lo] so that X_hi is read once; a second adds X_lo Op_hi.
+// One thread issues the tcgen05.mma instructions; the FP32 accumulator lives
+// in TMEM (lane = row) and four warps read it back (tcgen05.ld) for the stage
+// update.
 //
 // Memory pipeline as in the CUDA-core kernel: a block's own data arrives
 // by 1D TMA bulk copies into a ring of stage buffers (mbarrier per stage),
@@ -49,12 +52,15 @@ struct TcLayout {
   static constexpr int ROWS = 3 * E;
   static constexpr int KD = tc_kd(N), KP = tc_kp(N), KG = KP / 4;
   static constexpr int NN = tc_nn(N);
-  static constexpr int ACC_COLS = NN <= 32 ? 32 : 64;  // TMEM columns per accumulator
-  static constexpr int TMEM_COLS = 2 * ACC_COLS;       // two accumulators
-  // warp roles: 0-3 epilogue (TMEM lane quarters), 4-15 flux + operand
-  // build, 16 control (TMA loads and stores, MMA issue)
-  static constexpr int EPI_WARPS = 4, BUILD_WARPS = 12;
-  static constexpr int THREADS = 32 * (EPI_WARPS + BUILD_WARPS + 1);
+  // accumulator: columns [0, NN) hold X_hi Op_hi + X_lo Op_hi, columns
+  // [NN, 2 NN) hold X_hi Op_lo (one N = 2 NN MMA reads X_hi once for both)
+  static constexpr int ACC_COLS = 2 * NN <= 64 ? 64 : 128;  // TMEM columns per accumulator
+  static constexpr int TMEM_COLS = 2 * ACC_COLS;            // two accumulators
+  // warp roles: 0-3 epilogue (TMEM lane quarters), 4-17 flux + operand
+  // build, 18 MMA issue, 19 memory (TMA loads and stores)
+  static constexpr int EPI_WARPS = 4, BUILD_WARPS = 14;
+  static constexpr int MMA_WARP = EPI_WARPS + BUILD_WARPS, IO_WARP = MMA_WARP + 1;
+  static constexpr int THREADS = 32 * (EPI_WARPS + BUILD_WARPS + 2);
   static constexpr int BUILD_THREADS = 32 * BUILD_WARPS;
   static constexpr int NPAD = tc_npad(N);
   static constexpr int FPAD = round_up(Nafp, 4);
@@ -159,8 +165,8 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     atomicExch(p.status, 1);
   };
 
-  if (warp == L::EPI_WARPS + L::BUILD_WARPS) {
-    // ======================= control warp: loads, MMAs, stores (lane 0)
+  if (warp == L::IO_WARP) {
+    // ======================= memory warp: TMA loads, bulk stores (lane 0)
     if (lane == 0) {
       int issued = 0;
       auto issue = [&](int it) {
@@ -183,11 +189,15 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
         tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * kGeo, gb, &full[s]);
         tma_load_1d(st + 6 * L::QB + L::GB, p.conn + static_cast<int64_t>(k0) * 3, cb, &full[s]);
       };
+      mbar_expect_tx(op_bar, 2 * L::OB);
+      tma_load_1d(smem + L::OFF_OP, p.tc_op, 2 * L::OB, op_bar);
+      for (; issued < niter && issued < S; ++issued) issue(issued);
+      bool ok = true;
       // outputs of block jj leave by bulk stores; its stage is then refilled
-      auto drain_block = [&](int jj) -> bool {
+      for (int jj = 0; ok && jj < niter; ++jj) {
         const int s = jj % S;
-        if (!mbar_wait_or_abort(&out_ready[s], static_cast<uint32_t>((jj / S) & 1), abort_flag))
-          return false;
+        ok = mbar_wait_or_abort(&out_ready[s], static_cast<uint32_t>((jj / S) & 1), abort_flag);
+        if (!ok) break;
         const int k0 = (first + jj * G) * E;
         if (K - k0 >= E) {
           const float* sq = reinterpret_cast<const float*>(stages + s * L::STAGE_BYTES);
@@ -204,23 +214,30 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
           }
           bulk_commit();
         }
-        if (issued < niter) {  // issued == jj + S: same stage
+        if (issued < niter) {  // issued == jj + S: the same stage buffer
           bulk_wait_read_all();
           fence_proxy_async();
           issue(issued);
           ++issued;
         }
-        return true;
-      };
-
-      mbar_expect_tx(op_bar, 2 * L::OB);
-      tma_load_1d(smem + L::OFF_OP, p.tc_op, 2 * L::OB, op_bar);
-      for (; issued < niter && issued < S; ++issued) issue(issued);
+      }
+      if (!ok) {
+        fail();
+        // let this CTA's loads in flight land (each wait bounded)
+        for (int jj = (issued > S ? issued - S : 0); jj < issued; ++jj)
+          mbar_wait_bounded(&full[jj % S], static_cast<uint32_t>((jj / S) & 1), kWaitLimitNs);
+      }
+      bulk_wait_all();
+    }
+  } else if (warp == L::MMA_WARP) {
+    // ======================= MMA warp: 2 x (KP / 8) tcgen05.mma per block (lane 0)
+    if (lane == 0) {
       bool ok = mbar_wait_or_abort(op_bar, 0, abort_flag);
       const uint32_t xaddr = smem_u32(Xs);
       const uint32_t oaddr = smem_u32(smem + L::OFF_OP);
       constexpr uint32_t LBO = 128, SBO = L::KG * 128;
-      constexpr uint32_t IDESC = umma_idesc_tf32(128, NN);
+      constexpr uint32_t IDESC2 = umma_idesc_tf32(128, 2 * NN);  // B = [Op_hi ; Op_lo]
+      constexpr uint32_t IDESC1 = umma_idesc_tf32(128, NN);      // B = Op_hi
       int mma_pending = -1;  // block whose MMA group may still run
       for (int j = 0; ok && j < niter; ++j) {
         ok = mbar_wait_or_abort(xfull, static_cast<uint32_t>(j & 1), abort_flag);
@@ -230,33 +247,23 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
         if (!ok) break;
         tc_fence_after();
         const uint32_t dacc = tmem + static_cast<uint32_t>((j & 1) * L::ACC_COLS);
-        uint32_t acc = 0;
 #pragma unroll
-        for (int pr = 0; pr < 3; ++pr) {  // X_hi Op_hi, X_hi Op_lo, X_lo Op_hi
-          const uint32_t xa = xaddr + (pr == 2 ? L::XB : 0);
-          const uint32_t ob = oaddr + (pr == 1 ? L::OB : 0);
+        for (int ks = 0; ks < KP / 8; ++ks)  // X_hi [Op_hi ; Op_lo] -> columns [0, 2 NN)
+          umma_tf32(dacc, umma_desc(xaddr + ks * 256, LBO, SBO),
+                    umma_desc(oaddr + ks * 256, LBO, SBO), IDESC2, ks > 0 ? 1u : 0u);
 #pragma unroll
-          for (int ks = 0; ks < KP / 8; ++ks) {
-            umma_tf32(dacc, umma_desc(xa + ks * 256, LBO, SBO),
-                      umma_desc(ob + ks * 256, LBO, SBO), IDESC, acc);
-            acc = 1;
-          }
-        }
+        for (int ks = 0; ks < KP / 8; ++ks)  // + X_lo Op_hi -> columns [0, NN)
+          umma_tf32(dacc, umma_desc(xaddr + L::XB + ks * 256, LBO, SBO),
+                    umma_desc(oaddr + ks * 256, LBO, SBO), IDESC1, 1u);
         umma_commit(&mma_done[j & 1]);
         mma_pending = j;
-        if (j >= 1) ok = drain_block(j - 1);
       }
-      if (ok && niter > 0) ok = drain_block(niter - 1);
       if (!ok) {
         fail();
-        // let this CTA's asynchronous work land (each wait bounded)
-        for (int jj = (issued > S ? issued - S : 0); jj < issued; ++jj)
-          mbar_wait_bounded(&full[jj % S], static_cast<uint32_t>((jj / S) & 1), kWaitLimitNs);
         if (mma_pending >= 0)
           mbar_wait_bounded(&mma_done[mma_pending & 1],
                             static_cast<uint32_t>((mma_pending >> 1) & 1), kWaitLimitNs);
       }
-      bulk_wait_all();
     }
   } else if (warp >= L::EPI_WARPS) {
     // ======================= build warps: flux, then GEMM operand rows
@@ -415,15 +422,15 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const float* w = v[3 * h + c];
-            float4 hi, lo;
-            hi.x = tf32_rna(w[0]);
-            hi.y = tf32_rna(w[1]);
-            hi.z = tf32_rna(w[2]);
-            hi.w = tf32_rna(w[3]);
-            lo.x = tf32_rna(w[0] - hi.x);
-            lo.y = tf32_rna(w[1] - hi.y);
-            lo.z = tf32_rna(w[2] - hi.z);
-            lo.w = tf32_rna(w[3] - hi.w);
+            float4 hi, lo;  // hi: top 11 significand bits; lo: the exact rest
+            hi.x = tf32_trunc(w[0]);
+            hi.y = tf32_trunc(w[1]);
+            hi.z = tf32_trunc(w[2]);
+            hi.w = tf32_trunc(w[3]);
+            lo.x = w[0] - hi.x;
+            lo.y = w[1] - hi.y;
+            lo.z = w[2] - hi.z;
+            lo.w = w[3] - hi.w;
             const int idx = tc_canon(3 * e + c, k, KP);
             *reinterpret_cast<float4*>(Xs + idx) = hi;
             *reinterpret_cast<float4*>(Xs + L::XB / 4 + idx) = lo;
@@ -452,10 +459,11 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
                             (static_cast<uint32_t>(32 * warp) << 16);
 #pragma unroll
       for (int c0 = 0; c0 < NN; c0 += 16) {
-        float v16[16];
-        tmem_ld16(dacc + c0, v16);
+        float va[16], vb[16];
+        tmem_ld16(dacc + c0, va);       // X_hi Op_hi + X_lo Op_hi
+        tmem_ld16(dacc + NN + c0, vb);  // X_hi Op_lo
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[c0 + q] = v16[q];
+        for (int q = 0; q < 16; ++q) acc[c0 + q] = va[q] + vb[q];
       }
       tmem_ld_wait();
       tc_fence_before();

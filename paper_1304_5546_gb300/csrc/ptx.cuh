@@ -207,6 +207,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// TF32 value with the top 11 significand bits of x (low 13 bits cleared)
+__device__ __forceinline__ float tf32_trunc(float x) {
+  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
 // round to the nearest TF32 value (ties away from zero); low 13 bits zero
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t y;
