@@ -63,31 +63,28 @@ struct TcLayout {
   static constexpr int THREADS = 32 * (EPI_WARPS + BUILD_WARPS + 2);
   static constexpr int BUILD_THREADS = 32 * BUILD_WARPS;
   static constexpr int NPAD = tc_npad(N);
-  static constexpr int FPAD = round_up(Nafp, 4);
-  static constexpr int TASKS = E * Nafp;
-  static constexpr int TPT = (TASKS + BUILD_THREADS - 1) / BUILD_THREADS;
-  // build items per element: NPAD/4 volume chunks (each writes its Dr-part
-  // and Ds-part 16-byte chunks) and FPAD/4 lift chunks
-  static constexpr int IV = NPAD / 4, IF = FPAD / 4;
-  static constexpr int ITEMS = E * (IV + IF);
-  static constexpr int IPT = (ITEMS + BUILD_THREADS - 1) / BUILD_THREADS;
+  // build tasks per block, one per thread: 3E face tasks (upwind flux at the
+  // face's Nfp nodes, written into the LIFT part of X), then E * NPAD/4
+  // volume items (4 nodes each, written into the Dr and Ds parts)
+  static constexpr int IV = NPAD / 4;
+  static constexpr int FACE_TASKS = 3 * E;
+  static constexpr int TASKS = FACE_TASKS + E * IV;
   static constexpr int QB = E * Np * 4;
   static constexpr int GB = E * kGeo * 4;
   static constexpr int CB = E * 3 * 4;
   static constexpr int STAGE_BYTES = round_up(6 * QB + GB + CB, 128);
   static constexpr int XB = 128 * KP * 4;  // one X tile (hi or lo)
   static constexpr int OB = NN * KP * 4;   // one operator tile (hi or lo)
-  static constexpr int FB = E * 3 * FPAD * 4;
   static constexpr int HEADER = 1024;
   static constexpr int OFF_STAGES = HEADER;
   static constexpr int OFF_X = OFF_STAGES + S * STAGE_BYTES;
   static constexpr int OFF_OP = OFF_X + 2 * XB;
-  static constexpr int OFF_F = OFF_OP + 2 * OB;
-  static constexpr size_t SMEM_BYTES = OFF_F + FB;
+  static constexpr size_t SMEM_BYTES = OFF_OP + 2 * OB;
   static_assert(SMEM_BYTES <= 232448, "shared memory");
   static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0 && OB % 16 == 0, "TMA chunks");
   static_assert(ROWS <= 128 && NN <= 256 && NN % 16 == 0 && KP % 8 == 0, "UMMA shape");
   static_assert(S <= 4, "header layout");
+  static_assert(TASKS <= BUILD_THREADS, "one build task per thread");
 };
 
 template <int N, int MODE>
@@ -95,9 +92,8 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     dg_stage_tc_kernel(const StageArgs<float> p) {
   using L = TcLayout<N>;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
-  constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FPAD = L::FPAD;
-  constexpr int BT = L::BUILD_THREADS, TASKS = L::TASKS, TPT = L::TPT;
-  constexpr int IV = L::IV, ITEMS = L::ITEMS, IPT = L::IPT;
+  constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD;
+  constexpr int BT = L::BUILD_THREADS, TASKS = L::TASKS, FACE_TASKS = L::FACE_TASKS;
   constexpr int NQ = (MODE == kModeStage) ? 6 : 3;
 
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -114,7 +110,6 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
   float* lam = reinterpret_cast<float*>(smem + 384);  // [2][NPAD] vertex-interpolant weights
   unsigned char* stages = smem + L::OFF_STAGES;
   float* Xs = reinterpret_cast<float*>(smem + L::OFF_X);  // [2][128 x KP] canonical
-  float* Fs = reinterpret_cast<float*>(smem + L::OFF_F);  // [E][3][FPAD]
 
   const int t = threadIdx.x;
   const int warp = t >> 5, lane = t & 31;
@@ -148,11 +143,10 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     const int m = t % NPAD;
     lam[t] = m < Np ? __ldg(p.lam + (t / NPAD) * Np + m) : 0.f;
   }
-  {  // zero the X tiles (padding columns and rows beyond 3E stay zero) and Fs
+  {  // zero the X tiles: padding columns and rows beyond 3E stay zero
     float4* x4 = reinterpret_cast<float4*>(Xs);
     for (int idx = t; idx < 2 * L::XB / 16; idx += L::THREADS)
       x4[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int idx = t; idx < L::FB / 4; idx += L::THREADS) Fs[idx] = 0.f;
   }
   fence_proxy_async();
   tc_fence_before();
@@ -266,58 +260,54 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       }
     }
   } else if (warp >= L::EPI_WARPS) {
-    // ======================= build warps: flux, then GEMM operand rows
+    // ======================= build warps: GEMM operand rows (one task each)
     const int bt = t - 32 * L::EPI_WARPS;
     const float* qin[3] = {p.qin, p.qin + fs, p.qin + 2 * fs};
-    // flux tasks of this thread (the same in every block): element slot,
-    // offsets of its own face node, face code, face geometry and flux slot
-    int task_e[TPT], task_jj[TPT], task_nm[TPT], task_cf[TPT], task_gf[TPT], task_fo[TPT];
-#pragma unroll
-    for (int u = 0; u < TPT; ++u) {
-      const int tau = bt + u * BT;
-      const int ee = tau / Nafp, j = tau - ee * Nafp, f = j / Nfp, jj = j - f * Nfp;
-      task_e[u] = tau < TASKS ? ee : E;
-      task_jj[u] = jj;
-      task_nm[u] = ee * Np + face_node_dev(N, f, jj);
-      task_cf[u] = ee * 3 + f;
-      task_gf[u] = ee * kGeo + 4 + 3 * f;
-      task_fo[u] = (ee * 3) * FPAD + j;
-    }
-    int item_e[IPT], item_c[IPT];  // (element, chunk), element fastest
-#pragma unroll
-    for (int u = 0; u < IPT; ++u) {
-      const int idx = bt + u * BT;
-      item_c[u] = idx < ITEMS ? idx / E : -1;  // -1: no item
-      item_e[u] = idx - (idx / E) * E;
-    }
-    float trc[TPT][3];
+    const bool face_task = bt < FACE_TASKS;
+    const bool vol_task = !face_task && bt < TASKS;
+    // face task (element e, face f), element fastest; volume item (e, chunk)
+    const int fe = bt % E, ff = bt / E;
+    const int ve = (bt - FACE_TASKS) % E, vc = (bt - FACE_TASKS) / E;
+    float trc[Nfp][3];  // the face's neighbour traces, one block ahead
     auto gather = [&](int it) {
       const int32_t* sc = reinterpret_cast<const int32_t*>(stages + (it % S) * L::STAGE_BYTES +
                                                            6 * L::QB + L::GB);
       const int k0 = (first + it * G) * E;
+      const int32_t code = (k0 + fe < K) ? sc[fe * 3 + ff] : -1;
+      const int nb = (code & 7) * Nfp;
+      const int gb = (code >> 3) * Np;
 #pragma unroll
-      for (int u = 0; u < TPT; ++u) {
-        trc[u][0] = trc[u][1] = trc[u][2] = 0.f;
-        const int ee = task_e[u];
-        if (ee < E && k0 + ee < K) {
-          const int32_t code = sc[task_cf[u]];
-          if (code >= 0) {
-            const int gP = (code >> 3) * Np + nbr[(code & 7) * Nfp + task_jj[u]];
-            trc[u][0] = __ldg(qin[0] + gP);
-            trc[u][1] = __ldg(qin[1] + gP);
-            trc[u][2] = __ldg(qin[2] + gP);
-          }
+      for (int jj = 0; jj < Nfp; ++jj) {
+        if (code >= 0) {
+          const int gP = gb + nbr[nb + jj];
+          trc[jj][0] = __ldg(qin[0] + gP);
+          trc[jj][1] = __ldg(qin[1] + gP);
+          trc[jj][2] = __ldg(qin[2] + gP);
+        } else {
+          trc[jj][0] = trc[jj][1] = trc[jj][2] = 0.f;
         }
       }
     };
+    // value v at (row r, column k) of X as TF32 hi and exact rest
+    auto put = [&](int r, int k, float v) {
+      const float hi = tf32_trunc(v);
+      const int idx = tc_canon(r, k, KP);
+      Xs[idx] = hi;
+      Xs[L::XB / 4 + idx] = v - hi;
+    };
     bool ok = true;
-    if (niter > 0) {
+    if (face_task && niter > 0) {
       ok = mbar_wait_or_abort(&full[0], 0, abort_flag);
       if (ok) gather(0);
     }
-    for (int j = 0; j < niter; ++j) {
+    for (int j = 0; ok && j < niter; ++j) {
       const int s = j % S;
-      if (ok) ok = mbar_wait_or_abort(&full[s], static_cast<uint32_t>((j / S) & 1), abort_flag);
+      ok = mbar_wait_or_abort(&full[s], static_cast<uint32_t>((j / S) & 1), abort_flag);
+      // the previous block's MMAs have finished reading the operand tiles
+      if (ok && j >= 1)
+        ok = mbar_wait_or_abort(&mma_done[(j - 1) & 1], static_cast<uint32_t>(((j - 1) >> 1) & 1),
+                                abort_flag);
+      if (!ok) break;
       const int k0 = (first + j * G) * E;
       const int nvalid = (K - k0) < E ? (K - k0) : E;
       const unsigned char* st = stages + s * L::STAGE_BYTES;
@@ -325,122 +315,81 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       const float* sg = reinterpret_cast<const float*>(st + 6 * L::QB);
       const int32_t* sc = reinterpret_cast<const int32_t*>(st + 6 * L::QB + L::GB);
 
-      // ---- upwind flux at every face node -> Fs[e][c][j], scaled by Fscale/2
-      if (ok) {
+      if (face_task && fe < nvalid) {
+        // ---- upwind flux at the face's nodes, scaled by Fscale/2, into the
+        // LIFT part of rows 3e .. 3e+2
+        const bool pec = sc[fe * 3 + ff] < 0;  // PEC wall: Ez+ = -Ez-, H+ = H-
+        const float* gf = sg + fe * kGeo + 4 + 3 * ff;
+        const float nx = gf[0], ny = gf[1], fsc = gf[2];
+        const float* qe = sq + fe * Np;
 #pragma unroll
-        for (int u = 0; u < TPT; ++u) {
-          const int ee = task_e[u];
-          if (ee < nvalid) {
-            const int nM = task_nm[u];
-            const float hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
-            float dHx, dHy, dEz;
-            if (sc[task_cf[u]] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
-              dHx = 0.f;
-              dHy = 0.f;
-              dEz = 2.f * ezM;
-            } else {
-              dHx = hxM - trc[u][0];
-              dHy = hyM - trc[u][1];
-              dEz = ezM - trc[u][2];
-            }
-            const float* gf = sg + task_gf[u];
-            const float nx = gf[0], ny = gf[1], fsc = gf[2];
-            const float ndotdH = nx * dHx + ny * dHy;
-            float* fo = Fs + task_fo[u];
-            fo[0] = fsc * (ny * dEz + (ndotdH * nx - dHx));
-            fo[FPAD] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
-            fo[2 * FPAD] = fsc * (ny * dHx - nx * dHy - dEz);
-          }
+        for (int jj = 0; jj < Nfp; ++jj) {
+          const int nM = face_node_dev(N, ff, jj);
+          const float hxM = qe[nM], hyM = qe[E * Np + nM], ezM = qe[2 * E * Np + nM];
+          const float dHx = pec ? 0.f : hxM - trc[jj][0];
+          const float dHy = pec ? 0.f : hyM - trc[jj][1];
+          const float dEz = pec ? 2.f * ezM : ezM - trc[jj][2];
+          const float ndotdH = nx * dHx + ny * dHy;
+          const int k = 2 * NPAD + ff * Nfp + jj;
+          put(3 * fe + 0, k, fsc * (ny * dEz + (ndotdH * nx - dHx)));
+          put(3 * fe + 1, k, fsc * (-nx * dEz + (ndotdH * ny - dHy)));
+          put(3 * fe + 2, k, fsc * (ny * dHx - nx * dHy - dEz));
         }
-      }
-      if (ok && j + 1 < niter) {  // next block's traces, one block ahead
-        ok = mbar_wait_or_abort(&full[(j + 1) % S], static_cast<uint32_t>(((j + 1) / S) & 1),
-                                abort_flag);
-        if (ok) gather(j + 1);
-      }
-      // previous MMA has finished reading the operand tiles
-      if (ok && j >= 1)
-        ok = mbar_wait_or_abort(&mma_done[(j - 1) & 1], static_cast<uint32_t>(((j - 1) >> 1) & 1),
-                                abort_flag);
-      if (named_barrier_or(1, BT, !ok)) break;
-
-      // ---- GEMM rows of every element, split into TF32 hi / lo
+      } else if (vol_task && ve < nvalid) {
+        // ---- nodes m0 .. m0+3 minus the vertex-node interpolant, into the
+        // Dr and Ds parts of rows 3e .. 3e+2
+        const int m0 = 4 * vc;
+        const float* qe = sq + ve * Np;
+        const float* ge = sg + ve * kGeo;
+        const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
+        const float x1 = qe[0], x2 = qe[N], x3 = qe[Np - 1];
+        const float y1 = qe[E * Np], y2 = qe[E * Np + N], y3 = qe[E * Np + Np - 1];
+        const float z1 = qe[2 * E * Np], z2 = qe[2 * E * Np + N], z3 = qe[2 * E * Np + Np - 1];
+        const float4 l2v = *reinterpret_cast<const float4*>(lam + m0);
+        const float4 l3v = *reinterpret_cast<const float4*>(lam + NPAD + m0);
+        const float l2a[4] = {l2v.x, l2v.y, l2v.z, l2v.w};
+        const float l3a[4] = {l3v.x, l3v.y, l3v.z, l3v.w};
+        float v[6][4];
 #pragma unroll
-      for (int u = 0; u < IPT; ++u) {
-        const int ch = item_c[u], e = item_e[u];
-        if (ch < 0 || e >= nvalid) continue;
-        float v[6][4];  // rows 3e+0..2: [0..2] first chunk, [3..5] second chunk
-        int k_a, k_b;   // K column of the first / second chunk (k_b < 0: none)
-        if (ch < IV) {
-          // nodes m0..m0+3 minus the vertex-node interpolant; Dr- and Ds-part chunks
-          const int m0 = 4 * ch;
-          const float* qe = sq + e * Np;
-          const float* ge = sg + e * kGeo;
-          const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
-          const float x1 = qe[0], x2 = qe[N], x3 = qe[Np - 1];
-          const float y1 = qe[E * Np], y2 = qe[E * Np + N], y3 = qe[E * Np + Np - 1];
-          const float z1 = qe[2 * E * Np], z2 = qe[2 * E * Np + N], z3 = qe[2 * E * Np + Np - 1];
-          const float4 l2v = *reinterpret_cast<const float4*>(lam + m0);
-          const float4 l3v = *reinterpret_cast<const float4*>(lam + NPAD + m0);
-          const float l2a[4] = {l2v.x, l2v.y, l2v.z, l2v.w};
-          const float l3a[4] = {l3v.x, l3v.y, l3v.z, l3v.w};
-#pragma unroll
-          for (int uu = 0; uu < 4; ++uu) {
-            const int m = m0 + uu;
-            float ec = 0.f, dhx = 0.f, dhy = 0.f;
-            if (m < Np) {
-              ec = (qe[2 * E * Np + m] - z1) - ((z2 - z1) * l2a[uu] + (z3 - z1) * l3a[uu]);
-              dhx = (qe[m] - x1) - ((x2 - x1) * l2a[uu] + (x3 - x1) * l3a[uu]);
-              dhy = (qe[E * Np + m] - y1) - ((y2 - y1) * l2a[uu] + (y3 - y1) * l3a[uu]);
-            }
-            v[0][uu] = -ry * ec;
-            v[1][uu] = rx * ec;
-            v[2][uu] = rx * dhy - ry * dhx;
-            v[3][uu] = -sy * ec;
-            v[4][uu] = sx * ec;
-            v[5][uu] = sx * dhy - sy * dhx;
+        for (int uu = 0; uu < 4; ++uu) {
+          const int m = m0 + uu;
+          float ec = 0.f, dhx = 0.f, dhy = 0.f;
+          if (m < Np) {
+            ec = (qe[2 * E * Np + m] - z1) - ((z2 - z1) * l2a[uu] + (z3 - z1) * l3a[uu]);
+            dhx = (qe[m] - x1) - ((x2 - x1) * l2a[uu] + (x3 - x1) * l3a[uu]);
+            dhy = (qe[E * Np + m] - y1) - ((y2 - y1) * l2a[uu] + (y3 - y1) * l3a[uu]);
           }
-          k_a = m0;
-          k_b = NPAD + m0;
-        } else {
-          const int j0 = 4 * (ch - IV);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float4 f4 = *reinterpret_cast<const float4*>(Fs + (e * 3 + c) * FPAD + j0);
-            v[c][0] = f4.x;
-            v[c][1] = f4.y;
-            v[c][2] = f4.z;
-            v[c][3] = f4.w;
-          }
-          k_a = 2 * NPAD + j0;
-          k_b = -1;
+          v[0][uu] = -ry * ec;
+          v[1][uu] = rx * ec;
+          v[2][uu] = rx * dhy - ry * dhx;
+          v[3][uu] = -sy * ec;
+          v[4][uu] = sx * ec;
+          v[5][uu] = sx * dhy - sy * dhx;
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h == 1 && k_b < 0) break;
-          const int k = h == 0 ? k_a : k_b;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float* w = v[3 * h + c];
-            float4 hi, lo;  // hi: top 11 significand bits; lo: the exact rest
-            hi.x = tf32_trunc(w[0]);
-            hi.y = tf32_trunc(w[1]);
-            hi.z = tf32_trunc(w[2]);
-            hi.w = tf32_trunc(w[3]);
-            lo.x = w[0] - hi.x;
-            lo.y = w[1] - hi.y;
-            lo.z = w[2] - hi.z;
-            lo.w = w[3] - hi.w;
-            const int idx = tc_canon(3 * e + c, k, KP);
-            *reinterpret_cast<float4*>(Xs + idx) = hi;
-            *reinterpret_cast<float4*>(Xs + L::XB / 4 + idx) = lo;
-          }
+        for (int h = 0; h < 6; ++h) {
+          const float* w = v[h];
+          float4 hi, lo;  // hi: top 11 significand bits; lo: the exact rest
+          hi.x = tf32_trunc(w[0]);
+          hi.y = tf32_trunc(w[1]);
+          hi.z = tf32_trunc(w[2]);
+          hi.w = tf32_trunc(w[3]);
+          lo.x = w[0] - hi.x;
+          lo.y = w[1] - hi.y;
+          lo.z = w[2] - hi.z;
+          lo.w = w[3] - hi.w;
+          const int idx = tc_canon(3 * ve + (h % 3), (h < 3 ? 0 : NPAD) + m0, KP);
+          *reinterpret_cast<float4*>(Xs + idx) = hi;
+          *reinterpret_cast<float4*>(Xs + L::XB / 4 + idx) = lo;
         }
       }
       fence_proxy_async();
       mbar_arrive(xfull);
-      // every build thread is done with Fs before the next block's flux
-      if (named_barrier_or(1, BT, false)) break;
+      if (face_task && j + 1 < niter) {  // next block's traces, one block ahead
+        ok = mbar_wait_or_abort(&full[(j + 1) % S], static_cast<uint32_t>(((j + 1) / S) & 1),
+                                abort_flag);
+        if (ok) gather(j + 1);
+      }
     }
     if (!ok) fail();
   } else {
