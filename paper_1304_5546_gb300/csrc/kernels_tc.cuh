@@ -400,8 +400,11 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       ok = ok && mbar_wait_or_abort(&mma_done[j & 1], static_cast<uint32_t>((j >> 1) & 1),
                                     abort_flag);
       ok = ok && mbar_wait_or_abort(&full[s], static_cast<uint32_t>((j / S) & 1), abort_flag);
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) break;
+      // one decision for all epilogue warps (they meet again at barrier 2 below)
+      if (named_barrier_or(2, 32 * L::EPI_WARPS, !ok)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
       float acc[NN];
       const uint32_t dacc = tmem + static_cast<uint32_t>((j & 1) * L::ACC_COLS) +
@@ -425,12 +428,15 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       const float* sg = reinterpret_cast<const float*>(stages + s * L::STAGE_BYTES + 6 * L::QB);
       const int r = 32 * warp + lane;
       const int e = r / 3, c = r - 3 * (r / 3);
-      if (r < L::ROWS && e < nvalid) {
-        // chain-rule combination of the linear part's derivatives for row c
+      const bool row_ok = r < L::ROWS && e < nvalid;
+      // chain-rule combination of the linear part's derivatives for row c;
+      // it reads other rows' vertex values, so every row takes it before
+      // any row is overwritten in place (named barrier over these warps)
+      float lin = 0.f;
+      if (row_ok) {
         const float* qe = sq + e * Np;
         const float* ge = sg + e * kGeo;
         const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
-        float lin;
         if (c < 2) {
           const float z1 = qe[2 * E * Np];
           const float grz = 0.5f * (qe[2 * E * Np + N] - z1);
@@ -441,6 +447,9 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
           lin = 0.5f * (rx * (qe[E * Np + N] - y1) - ry * (qe[N] - x1) +
                         sx * (qe[E * Np + Np - 1] - y1) - sy * (qe[Np - 1] - x1));
         }
+      }
+      named_barrier_or(2, 32 * L::EPI_WARPS, false);
+      if (row_ok) {
         const int off = c * E * Np + e * Np;
         const bool full_block = nvalid == E;
         const int64_t g = static_cast<int64_t>(c) * fs + static_cast<int64_t>(k0 + e) * Np;
