@@ -39,8 +39,9 @@
 //                   results.
 // Hand-offs are mbarriers: stage loaded (full), operand built (xfull),
 // accumulator ready (mma_done, tcgen05.commit), accumulator read
-// (tmem_free), results written (out_ready).  For N <= 5 the operand tiles
-// are double-buffered so that block j+1 is built while block j's MMAs run.
+// (tmem_free), results written (out_ready).  Except at N = 6 (shared memory)
+// the operand tiles are double-buffered so that block j+1 is built while
+// block j's MMAs run.
 // Neighbour traces are gathered one block ahead.  Every wait is bounded; on
 // expiry the CTA sets the status word, drains its copies (bounded), frees
 // its TMEM and returns.
@@ -55,9 +56,14 @@ struct TcLayout {
   static constexpr int Np = Order<N>::Np;
   static constexpr int Nfp = Order<N>::Nfp;
   static constexpr int E = (N == 7) ? 24 : 40;  // 3E <= 128 GEMM rows, E % 4 == 0
-  static constexpr int XBUF = (N <= 5) ? 2 : 1;  // operand tile buffers
-  static constexpr int S = (N <= 5) ? 2 : 3;     // stage buffers
+  static constexpr int XBUF = (N == 6) ? 1 : 2;  // operand tile buffers
+  static constexpr int S = 3;                    // stage buffers
   static constexpr int ROWS = 3 * E;
+  // X tiles hold the ROWS rows in use (rounded to 8); the M = 128 MMA also
+  // reads the following 128 - XROWS rows, which lie inside this CTA's shared
+  // memory (the next tile or the operator tiles) and only feed accumulator
+  // rows that are never read.
+  static constexpr int XROWS = round_up(ROWS, 8);
   static constexpr int KP = tc_kp(N), KG = KP / 4;
   static constexpr int NN = tc_nn(N);
   static constexpr int NPAD = tc_npad(N), FP4 = tc_fp4(N);
@@ -84,7 +90,7 @@ struct TcLayout {
   static constexpr int GB = E * kGeo * 4;
   static constexpr int CB = E * 3 * 4;
   static constexpr int STAGE_BYTES = round_up(6 * QB + GB + CB, 128);
-  static constexpr int XB = 128 * KP * 4;  // one X tile (hi or lo)
+  static constexpr int XB = XROWS * KP * 4;  // one X tile (hi or lo)
   static constexpr int OB = NN * KP * 4;   // one operator tile (hi or lo)
   static constexpr int HEADER = 1024;
   static constexpr int OFF_STAGES = HEADER;
@@ -95,6 +101,8 @@ struct TcLayout {
   static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0 && OB % 16 == 0, "TMA chunks");
   static_assert(ROWS <= 128 && 2 * NN <= 256 && NN % 16 == 0 && KP % 8 == 0, "UMMA shape");
   static_assert(S <= 4 && XBUF <= 2, "header layout");
+  // the rows an MMA reads past the last X tile stay inside the operator tiles
+  static_assert((128 - XROWS) / 8 * KP * 32 <= 2 * OB, "MMA row overrun");
 };
 
 template <int N, int MODE>
@@ -120,7 +128,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
   int* nbr = reinterpret_cast<int*>(smem + 128);      // [6][Nfp] neighbour face-node table
   float* lam = reinterpret_cast<float*>(smem + 384);  // [2][NPAD] vertex-interpolant weights
   unsigned char* stages = smem + L::OFF_STAGES;
-  float* Xs = reinterpret_cast<float*>(smem + L::OFF_X);  // [XBUF][hi, lo][128 x KP] canonical
+  float* Xs = reinterpret_cast<float*>(smem + L::OFF_X);  // [XBUF][hi, lo][XROWS x KP] canonical
 
   const int t = threadIdx.x;
   const int warp = t >> 5, lane = t & 31;
@@ -154,7 +162,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     const int m = t % NPAD;
     lam[t] = m < Np ? __ldg(p.lam + (t / NPAD) * Np + m) : 0.f;
   }
-  {  // zero the X tiles: padding columns and rows beyond 3E stay zero
+  {  // zero the X tiles: padding columns stay zero
     float4* x4 = reinterpret_cast<float4*>(Xs);
     for (int idx = t; idx < XBUF * 2 * L::XB / 16; idx += L::THREADS)
       x4[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
