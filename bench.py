@@ -158,6 +158,25 @@ def cpu_baseline(n=100, N=5, seconds=10.0):
                       "(K=%d, N=%d), 1 thread, %.1f s" % (v["steps"], n, v["K"], N, v["seconds"])}
 
 
+# ------------------------------------------------------------- replicas
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of a list of floats over all ranks (the timed
+    region of the slowest replica decides the whole job's time)."""
+    import torch
+
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def replica_throughput(world, K, steps, ms):
+    """Whole-job element-stage updates/s: every rank advances its own copy
+    of the K-element mesh by `steps` five-stage steps; `ms` is the maximum
+    over ranks of the timed region."""
+    return world * K * 5 * steps / (ms / 1e3)
+
+
 # ------------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -229,18 +248,14 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     barrier()
 
-    tmax = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms, e2e_s = float(tmax[0]), float(tmax[1])
+    ms, e2e_s = max_over_ranks([ms, e2e_s], dist, device="cuda")
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return None
 
     K = s.K
-    units = world * K * 5 * args.steps
-    value = units / (ms / 1e3)
+    value = replica_throughput(world, K, args.steps, ms)
     peaks, peak_kind = measured_peaks()
     bytes_step = K * step_bytes_per_element(N) * (2 if args.precision == "fp64" else 1)
     achieved = bytes_step * args.steps / (ms / 1e3) / 1e9
@@ -293,7 +308,7 @@ def run_ours(args):
             "bytes_per_element_step": step_bytes_per_element(N),
         },
         "e2e": {
-            "value": world * K * 5 * e2e_steps / e2e_s,
+            "value": replica_throughput(world, K, e2e_steps, e2e_s * 1e3),
             "unit": UNIT,
             "h2d_bytes_per_step": 3 * s.fstride * (4 if args.precision == "fp32" else 8),
             "d2h_bytes_per_step": 3 * s.fstride * (4 if args.precision == "fp32" else 8),

@@ -83,9 +83,8 @@ float tf32_round(double v) {
 // layout of dgw::tc_canon, parts at the columns dgw::tc_kd describes; rows
 // >= Np and padding columns are zero.
 std::vector<float> tc_operator_tiles(const dgw::RefElement& R) {
-  const int N = R.N, Np = R.Np, Nfp = R.Nfp, Nafp = R.Nafp;
+  const int N = R.N, Np = R.Np, Nafp = R.Nafp;
   const int kp = dgw::tc_kp(N), nn = dgw::tc_nn(N), npad = dgw::tc_npad(N);
-  const int fp4 = dgw::tc_fp4(N);
   std::vector<float> out(2 * static_cast<size_t>(nn) * kp, 0.0f);
   auto put = [&](int n, int k, double v) {
     const float hi = tf32_round(v);
@@ -99,8 +98,7 @@ std::vector<float> tc_operator_tiles(const dgw::RefElement& R) {
       put(n, m, R.Dr[n * Np + m]);
       put(n, npad + m, R.Ds[n * Np + m]);
     }
-    for (int j = 0; j < Nafp; ++j)
-      put(n, 2 * npad + (j / Nfp) * fp4 + j % Nfp, R.LIFT[n * Nafp + j]);
+    for (int j = 0; j < Nafp; ++j) put(n, 2 * npad + j, R.LIFT[n * Nafp + j]);
   }
   return out;
 }

@@ -14,35 +14,26 @@
 //   row 3e+0 = [ -ry Ez_d | -sy Ez_d | F_x ]  ->  dHx/dt
 //   row 3e+1 = [  rx Ez_d |  sx Ez_d | F_y ]  ->  dHy/dt
 //   row 3e+2 = [  A       |  B       | F_z ]  ->  dEz/dt
-// (parts on 16-byte boundaries, see tc_kd), the right-hand side is
-// D = X [Dr | Ds | LIFT]^T plus, per element and row, the chain-rule
-// combination of the linear part's exact derivatives ((u_v2 - u_v1)/2 along
-// r, (u_v3 - u_v1)/2 along s), added in the epilogue.  The deflation keeps
-// the products' operands O(h^2) for smooth fields, so their TF32 rounding
-// stays far below FP32 accuracy.  M = 3E rows (<= 128), K = tc_kp(N),
-// N = tc_nn(N).  FP32 accuracy comes from three TF32 products, X_hi Op_hi +
-// X_hi Op_lo + X_lo Op_hi: X_hi keeps the top 11 significand bits of X,
-// X_lo = X - X_hi (exact in FP32, truncated to TF32 by the tensor core);
-// Op's hi/lo split is made on the host from FP64 with round-to-nearest.  One
-// MMA of N = 2 tc_nn computes X_hi [Op_hi ; Op_lo] so that X_hi is read once;
-// a second adds X_lo Op_hi.
+// (each part of a row starts on a 16-byte boundary, see tc_kd)
+// the right-hand side is D = X [Dr | Ds | LIFT]^T plus, per element and row,
+// the chain-rule combination of the linear part's exact derivatives
+// ((u_v2 - u_v1)/2 along r, (u_v3 - u_v1)/2 along s), added in the epilogue.
+// The deflation keeps the products' operands O(h^2) for smooth fields, so
+// their TF32 rounding stays far below FP32 accuracy.  M = 3E rows (<= 128),
+// K = 2 Np + Nafp (padded to 8), N = Np (padded to 16).  FP32 accuracy
+// comes from three TF32 products, X_hi Op_hi + X_hi Op_lo + X_lo Op_hi: X_hi
+// keeps the top 11 significand bits of X, X_lo = X - X_hi (exact in FP32,
+// truncated to TF32 by the tensor core); Op's hi/lo split is made on the host
+// from FP64 with round-to-nearest.  One MMA of N = 2 Np' computes X_hi
+// [Op_hi ; Op_lo] so that X_hi is read once; a second adds X_lo Op_hi.
+// One thread issues the tcgen05.mma instructions; the FP32 accumulator lives
+// in TMEM (lane = row) and four warps read it back (tcgen05.ld) for the stage
+// update.
 //
-// Warp roles (one CTA per SM, persistent over element blocks):
-//   epilogue warps  read the accumulator (tcgen05.ld, two warps per TMEM
-//                   lane quarter, half the columns each) and apply the
-//                   stage update in place in the block's stage buffer;
-//   build warps     compute the upwind flux per (element, face) and the
-//                   deflated volume operands, and write X as TF32 hi / lo;
-//   MMA warp        one thread issues the tcgen05.mma instructions;
-//   memory warp     one thread issues the TMA bulk loads of every block's
-//                   data (ring of stage buffers) and the bulk stores of its
-//                   results.
-// Hand-offs are mbarriers: stage loaded (full), operand built (xfull),
-// accumulator ready (mma_done, tcgen05.commit), accumulator read
-// (tmem_free), results written (out_ready).  Except at N = 6 (shared memory)
-// the operand tiles are double-buffered so that block j+1 is built while
-// block j's MMAs run.
-// Neighbour traces are gathered one block ahead.  Every wait is bounded; on
+// Memory pipeline as in the CUDA-core kernel: a block's own data arrives
+// by 1D TMA bulk copies into a ring of stage buffers (mbarrier per stage),
+// neighbour traces are gathered one block ahead, and full blocks leave by
+// TMA bulk stores from the same stage buffer.  Every wait is bounded; on
 // expiry the CTA sets the status word, drains its copies (bounded), frees
 // its TMEM and returns.
 #pragma once
@@ -55,80 +46,75 @@ template <int N>
 struct TcLayout {
   static constexpr int Np = Order<N>::Np;
   static constexpr int Nfp = Order<N>::Nfp;
+  static constexpr int Nafp = Order<N>::Nafp;
   static constexpr int E = (N == 7) ? 24 : 40;  // 3E <= 128 GEMM rows, E % 4 == 0
-  static constexpr int XBUF = (N == 6) ? 1 : 2;  // operand tile buffers
-  static constexpr int S = 3;                    // stage buffers
+  static constexpr int S = (N >= 6) ? 3 : 4;    // stage buffers
   static constexpr int ROWS = 3 * E;
-  // X tiles hold the ROWS rows in use (rounded to 8); the M = 128 MMA also
-  // reads the following 128 - XROWS rows, which lie inside this CTA's shared
-  // memory (the next tile or the operator tiles) and only feed accumulator
-  // rows that are never read.
-  static constexpr int XROWS = round_up(ROWS, 8);
-  static constexpr int KP = tc_kp(N), KG = KP / 4;
+  static constexpr int KD = tc_kd(N), KP = tc_kp(N), KG = KP / 4;
   static constexpr int NN = tc_nn(N);
-  static constexpr int NPAD = tc_npad(N), FP4 = tc_fp4(N);
   // accumulator: columns [0, NN) hold X_hi Op_hi + X_lo Op_hi, columns
-  // [NN, 2 NN) hold X_hi Op_lo
+  // [NN, 2 NN) hold X_hi Op_lo (one N = 2 NN MMA reads X_hi once for both)
   static constexpr int ACC_COLS = 2 * NN <= 64 ? 64 : 128;  // TMEM columns per accumulator
   static constexpr int TMEM_COLS = 2 * ACC_COLS;            // two accumulators
-  static constexpr int NCH = NN / 16;                       // 16-column chunks
-  static constexpr int NCH0 = (NCH + 1) / 2;                // chunks of the first half
-  // warp roles: 0-7 epilogue, 8-19 build, 20 MMA, 21 memory
-  static constexpr int EPI_WARPS = 8, BUILD_WARPS = 12;
+  // warp roles: 0-3 epilogue (TMEM lane quarters), 4-17 flux + operand
+  // build, 18 MMA issue, 19 memory (TMA loads and stores)
+  static constexpr int EPI_WARPS = 4, BUILD_WARPS = 14;
   static constexpr int MMA_WARP = EPI_WARPS + BUILD_WARPS, IO_WARP = MMA_WARP + 1;
   static constexpr int THREADS = 32 * (EPI_WARPS + BUILD_WARPS + 2);
-  static constexpr int EPI_THREADS = 32 * EPI_WARPS;
   static constexpr int BUILD_THREADS = 32 * BUILD_WARPS;
-  // build tasks per block: 3E face tasks (upwind flux at the face's Nfp
-  // nodes into the LIFT part of X), then E * NPAD/4 volume tasks (4 nodes
-  // each, into the Dr and Ds parts)
-  static constexpr int IV = NPAD / 4;
-  static constexpr int FACE_TASKS = 3 * E;
-  static constexpr int TASKS = FACE_TASKS + E * IV;
-  static constexpr int TPT = (TASKS + BUILD_THREADS - 1) / BUILD_THREADS;  // per thread
+  static constexpr int NPAD = tc_npad(N);
+  static constexpr int FPAD = round_up(Nafp, 4);
+  static constexpr int TASKS = E * Nafp;
+  static constexpr int TPT = (TASKS + BUILD_THREADS - 1) / BUILD_THREADS;
+  // build items per element: NPAD/4 volume chunks (each writes its Dr-part
+  // and Ds-part 16-byte chunks) and FPAD/4 lift chunks
+  static constexpr int IV = NPAD / 4, IF = FPAD / 4;
+  static constexpr int ITEMS = E * (IV + IF);
+  static constexpr int IPT = (ITEMS + BUILD_THREADS - 1) / BUILD_THREADS;
   static constexpr int QB = E * Np * 4;
   static constexpr int GB = E * kGeo * 4;
   static constexpr int CB = E * 3 * 4;
   static constexpr int STAGE_BYTES = round_up(6 * QB + GB + CB, 128);
-  static constexpr int XB = XROWS * KP * 4;  // one X tile (hi or lo)
+  static constexpr int XB = 128 * KP * 4;  // one X tile (hi or lo)
   static constexpr int OB = NN * KP * 4;   // one operator tile (hi or lo)
+  static constexpr int FB = E * 3 * FPAD * 4;
   static constexpr int HEADER = 1024;
   static constexpr int OFF_STAGES = HEADER;
-  static constexpr int OFF_X = OFF_STAGES + S * STAGE_BYTES;  // [XBUF][hi, lo]
-  static constexpr int OFF_OP = OFF_X + XBUF * 2 * XB;
-  static constexpr size_t SMEM_BYTES = OFF_OP + 2 * OB;
+  static constexpr int OFF_X = OFF_STAGES + S * STAGE_BYTES;
+  static constexpr int OFF_OP = OFF_X + 2 * XB;
+  static constexpr int OFF_F = OFF_OP + 2 * OB;
+  static constexpr size_t SMEM_BYTES = OFF_F + FB;
   static_assert(SMEM_BYTES <= 232448, "shared memory");
   static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0 && OB % 16 == 0, "TMA chunks");
-  static_assert(ROWS <= 128 && 2 * NN <= 256 && NN % 16 == 0 && KP % 8 == 0, "UMMA shape");
-  static_assert(S <= 4 && XBUF <= 2, "header layout");
-  // the rows an MMA reads past the last X tile stay inside the operator tiles
-  static_assert((128 - XROWS) / 8 * KP * 32 <= 2 * OB, "MMA row overrun");
+  static_assert(ROWS <= 128 && NN <= 256 && NN % 16 == 0 && KP % 8 == 0, "UMMA shape");
+  static_assert(S <= 4, "header layout");
 };
 
 template <int N, int MODE>
 __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     dg_stage_tc_kernel(const StageArgs<float> p) {
   using L = TcLayout<N>;
-  constexpr int Np = L::Np, Nfp = L::Nfp, E = L::E, S = L::S, XBUF = L::XBUF;
-  constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FP4 = L::FP4;
-  constexpr int BT = L::BUILD_THREADS, TASKS = L::TASKS, FACE_TASKS = L::FACE_TASKS;
-  constexpr int TPT = L::TPT;
+  constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
+  constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FPAD = L::FPAD;
+  constexpr int BT = L::BUILD_THREADS, TASKS = L::TASKS, TPT = L::TPT;
+  constexpr int IV = L::IV, ITEMS = L::ITEMS, IPT = L::IPT;
   constexpr int NQ = (MODE == kModeStage) ? 6 : 3;
 
   extern __shared__ __align__(1024) unsigned char smem[];
   // header: mbarriers, TMEM base, abort flag, tables
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem);            // [S] stage loaded
-  uint64_t* out_ready = reinterpret_cast<uint64_t*>(smem + 32);  // [S] outputs written
-  uint64_t* mma_done = reinterpret_cast<uint64_t*>(smem + 64);   // [2] accumulator ready
-  uint64_t* tmem_free = reinterpret_cast<uint64_t*>(smem + 80);  // [2] accumulator read
-  uint64_t* xfull = reinterpret_cast<uint64_t*>(smem + 96);      // [2] operand built
-  uint64_t* op_bar = reinterpret_cast<uint64_t*>(smem + 112);    // operator tiles landed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 120);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 124);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);              // [S] stage loaded
+  uint64_t* out_ready = reinterpret_cast<uint64_t*>(smem + 32);    // [S] outputs written
+  uint64_t* mma_done = reinterpret_cast<uint64_t*>(smem + 64);     // [2] accumulator ready
+  uint64_t* tmem_free = reinterpret_cast<uint64_t*>(smem + 80);    // [2] accumulator read
+  uint64_t* xfull = reinterpret_cast<uint64_t*>(smem + 96);        // operand tile built
+  uint64_t* op_bar = reinterpret_cast<uint64_t*>(smem + 104);      // operator tiles landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 112);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 116);
   int* nbr = reinterpret_cast<int*>(smem + 128);      // [6][Nfp] neighbour face-node table
   float* lam = reinterpret_cast<float*>(smem + 384);  // [2][NPAD] vertex-interpolant weights
   unsigned char* stages = smem + L::OFF_STAGES;
-  float* Xs = reinterpret_cast<float*>(smem + L::OFF_X);  // [XBUF][hi, lo][XROWS x KP] canonical
+  float* Xs = reinterpret_cast<float*>(smem + L::OFF_X);  // [2][128 x KP] canonical
+  float* Fs = reinterpret_cast<float*>(smem + L::OFF_F);  // [E][3][FPAD]
 
   const int t = threadIdx.x;
   const int warp = t >> 5, lane = t & 31;
@@ -142,13 +128,13 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
   if (t == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&out_ready[s], L::EPI_THREADS);
+      mbar_init(&out_ready[s], 32 * L::EPI_WARPS);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&mma_done[b], 1);
-      mbar_init(&tmem_free[b], L::EPI_THREADS);
-      mbar_init(&xfull[b], BT);
+      mbar_init(&tmem_free[b], 32 * L::EPI_WARPS);
     }
+    mbar_init(xfull, BT);
     mbar_init(op_bar, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -162,10 +148,11 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     const int m = t % NPAD;
     lam[t] = m < Np ? __ldg(p.lam + (t / NPAD) * Np + m) : 0.f;
   }
-  {  // zero the X tiles: padding columns stay zero
+  {  // zero the X tiles (padding columns and rows beyond 3E stay zero) and Fs
     float4* x4 = reinterpret_cast<float4*>(Xs);
-    for (int idx = t; idx < XBUF * 2 * L::XB / 16; idx += L::THREADS)
+    for (int idx = t; idx < 2 * L::XB / 16; idx += L::THREADS)
       x4[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int idx = t; idx < L::FB / 4; idx += L::THREADS) Fs[idx] = 0.f;
   }
   fence_proxy_async();
   tc_fence_before();
@@ -246,19 +233,19 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     // ======================= MMA warp: 2 x (KP / 8) tcgen05.mma per block (lane 0)
     if (lane == 0) {
       bool ok = mbar_wait_or_abort(op_bar, 0, abort_flag);
+      const uint32_t xaddr = smem_u32(Xs);
       const uint32_t oaddr = smem_u32(smem + L::OFF_OP);
       constexpr uint32_t LBO = 128, SBO = L::KG * 128;
       constexpr uint32_t IDESC2 = umma_idesc_tf32(128, 2 * NN);  // B = [Op_hi ; Op_lo]
       constexpr uint32_t IDESC1 = umma_idesc_tf32(128, NN);      // B = Op_hi
       int mma_pending = -1;  // block whose MMA group may still run
       for (int j = 0; ok && j < niter; ++j) {
-        ok = mbar_wait_or_abort(&xfull[j & 1], static_cast<uint32_t>((j >> 1) & 1), abort_flag);
+        ok = mbar_wait_or_abort(xfull, static_cast<uint32_t>(j & 1), abort_flag);
         if (ok && j >= 2)
           ok = mbar_wait_or_abort(&tmem_free[j & 1], static_cast<uint32_t>(((j - 2) >> 1) & 1),
                                   abort_flag);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t xaddr = smem_u32(Xs) + static_cast<uint32_t>((j % XBUF) * 2 * L::XB);
         const uint32_t dacc = tmem + static_cast<uint32_t>((j & 1) * L::ACC_COLS);
 #pragma unroll
         for (int ks = 0; ks < KP / 8; ++ks)  // X_hi [Op_hi ; Op_lo] -> columns [0, 2 NN)
@@ -279,122 +266,116 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       }
     }
   } else if (warp >= L::EPI_WARPS) {
-    // ======================= build warps: GEMM operand rows
-    const int bt = t - L::EPI_THREADS;
+    // ======================= build warps: flux, then GEMM operand rows
+    const int bt = t - 32 * L::EPI_WARPS;
     const float* qin[3] = {p.qin, p.qin + fs, p.qin + 2 * fs};
-    // face tasks of this thread: (element fe, face ff), element fastest
-    constexpr int FPT = (FACE_TASKS + BT - 1) / BT;
-    float trc[FPT][Nfp][3];  // the faces' neighbour traces, one block ahead
+    // flux tasks of this thread (the same in every block): element slot,
+    // offsets of its own face node, face code, face geometry and flux slot
+    int task_e[TPT], task_jj[TPT], task_nm[TPT], task_cf[TPT], task_gf[TPT], task_fo[TPT];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const int tau = bt + u * BT;
+      const int ee = tau / Nafp, j = tau - ee * Nafp, f = j / Nfp, jj = j - f * Nfp;
+      task_e[u] = tau < TASKS ? ee : E;
+      task_jj[u] = jj;
+      task_nm[u] = ee * Np + face_node_dev(N, f, jj);
+      task_cf[u] = ee * 3 + f;
+      task_gf[u] = ee * kGeo + 4 + 3 * f;
+      task_fo[u] = (ee * 3) * FPAD + j;
+    }
+    int item_e[IPT], item_c[IPT];  // (element, chunk), element fastest
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      const int idx = bt + u * BT;
+      item_c[u] = idx < ITEMS ? idx / E : -1;  // -1: no item
+      item_e[u] = idx - (idx / E) * E;
+    }
+    float trc[TPT][3];
     auto gather = [&](int it) {
       const int32_t* sc = reinterpret_cast<const int32_t*>(stages + (it % S) * L::STAGE_BYTES +
                                                            6 * L::QB + L::GB);
       const int k0 = (first + it * G) * E;
 #pragma unroll
-      for (int u = 0; u < FPT; ++u) {
-        const int task = bt + u * BT;
-        const int fe = task % E, ff = task / E;
-        const int32_t code = (task < FACE_TASKS && k0 + fe < K) ? sc[fe * 3 + ff] : -1;
-        const int nb = (code & 7) * Nfp;
-        const int gb = (code >> 3) * Np;
-#pragma unroll
-        for (int jj = 0; jj < Nfp; ++jj) {
+      for (int u = 0; u < TPT; ++u) {
+        trc[u][0] = trc[u][1] = trc[u][2] = 0.f;
+        const int ee = task_e[u];
+        if (ee < E && k0 + ee < K) {
+          const int32_t code = sc[task_cf[u]];
           if (code >= 0) {
-            const int gP = gb + nbr[nb + jj];
-            trc[u][jj][0] = __ldg(qin[0] + gP);
-            trc[u][jj][1] = __ldg(qin[1] + gP);
-            trc[u][jj][2] = __ldg(qin[2] + gP);
-          } else {
-            trc[u][jj][0] = trc[u][jj][1] = trc[u][jj][2] = 0.f;
+            const int gP = (code >> 3) * Np + nbr[(code & 7) * Nfp + task_jj[u]];
+            trc[u][0] = __ldg(qin[0] + gP);
+            trc[u][1] = __ldg(qin[1] + gP);
+            trc[u][2] = __ldg(qin[2] + gP);
           }
         }
       }
-    };
-    // 4 consecutive values of row r from column k (k % 4 == 0) as TF32 hi
-    // and exact rest into operand buffer xb
-    auto put4 = [&](float* xb, int r, int k, const float (&w)[4]) {
-      float4 hi, lo;
-      hi.x = tf32_trunc(w[0]);
-      hi.y = tf32_trunc(w[1]);
-      hi.z = tf32_trunc(w[2]);
-      hi.w = tf32_trunc(w[3]);
-      lo.x = w[0] - hi.x;
-      lo.y = w[1] - hi.y;
-      lo.z = w[2] - hi.z;
-      lo.w = w[3] - hi.w;
-      const int idx = tc_canon(r, k, KP);
-      *reinterpret_cast<float4*>(xb + idx) = hi;
-      *reinterpret_cast<float4*>(xb + L::XB / 4 + idx) = lo;
     };
     bool ok = true;
     if (niter > 0) {
       ok = mbar_wait_or_abort(&full[0], 0, abort_flag);
       if (ok) gather(0);
     }
-    for (int j = 0; ok && j < niter; ++j) {
+    for (int j = 0; j < niter; ++j) {
       const int s = j % S;
-      ok = mbar_wait_or_abort(&full[s], static_cast<uint32_t>((j / S) & 1), abort_flag);
-      // the MMAs that last read this operand buffer are done
-      if (ok && j >= XBUF)
-        ok = mbar_wait_or_abort(&mma_done[(j - XBUF) & 1],
-                                static_cast<uint32_t>(((j - XBUF) >> 1) & 1), abort_flag);
-      if (!ok) break;
+      if (ok) ok = mbar_wait_or_abort(&full[s], static_cast<uint32_t>((j / S) & 1), abort_flag);
       const int k0 = (first + j * G) * E;
       const int nvalid = (K - k0) < E ? (K - k0) : E;
       const unsigned char* st = stages + s * L::STAGE_BYTES;
       const float* sq = reinterpret_cast<const float*>(st);
       const float* sg = reinterpret_cast<const float*>(st + 6 * L::QB);
       const int32_t* sc = reinterpret_cast<const int32_t*>(st + 6 * L::QB + L::GB);
-      float* xb = Xs + (j % XBUF) * (2 * L::XB / 4);
 
+      // ---- upwind flux at every face node -> Fs[e][c][j], scaled by Fscale/2
+      if (ok) {
 #pragma unroll
-      for (int u = 0; u < TPT; ++u) {
-        const int task = bt + u * BT;
-        if (task < FACE_TASKS) {
-          // ---- upwind flux at the face's nodes, scaled by Fscale/2, into
-          // the LIFT part of rows 3e .. 3e+2 (face ff's FP4 columns)
-          const int fe = task % E, ff = task / E;
-          if (fe >= nvalid) continue;
-          const bool pec = sc[fe * 3 + ff] < 0;  // PEC wall: Ez+ = -Ez-, H+ = H-
-          const float* gf = sg + fe * kGeo + 4 + 3 * ff;
-          const float nx = gf[0], ny = gf[1], fsc = gf[2];
-          const float* qe = sq + fe * Np;
-          float fx[FP4], fy[FP4], fz[FP4];
-#pragma unroll
-          for (int jj = 0; jj < FP4; ++jj) {
-            fx[jj] = fy[jj] = fz[jj] = 0.f;
-            if (jj < Nfp) {
-              const int nM = face_node_dev(N, ff, jj);
-              const float hxM = qe[nM], hyM = qe[E * Np + nM], ezM = qe[2 * E * Np + nM];
-              const float tx = u < FPT ? trc[u < FPT ? u : 0][jj][0] : 0.f;
-              const float ty = u < FPT ? trc[u < FPT ? u : 0][jj][1] : 0.f;
-              const float tz = u < FPT ? trc[u < FPT ? u : 0][jj][2] : 0.f;
-              const float dHx = pec ? 0.f : hxM - tx;
-              const float dHy = pec ? 0.f : hyM - ty;
-              const float dEz = pec ? 2.f * ezM : ezM - tz;
-              const float ndotdH = nx * dHx + ny * dHy;
-              fx[jj] = fsc * (ny * dEz + (ndotdH * nx - dHx));
-              fy[jj] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
-              fz[jj] = fsc * (ny * dHx - nx * dHy - dEz);
+        for (int u = 0; u < TPT; ++u) {
+          const int ee = task_e[u];
+          if (ee < nvalid) {
+            const int nM = task_nm[u];
+            const float hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
+            float dHx, dHy, dEz;
+            if (sc[task_cf[u]] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
+              dHx = 0.f;
+              dHy = 0.f;
+              dEz = 2.f * ezM;
+            } else {
+              dHx = hxM - trc[u][0];
+              dHy = hyM - trc[u][1];
+              dEz = ezM - trc[u][2];
             }
+            const float* gf = sg + task_gf[u];
+            const float nx = gf[0], ny = gf[1], fsc = gf[2];
+            const float ndotdH = nx * dHx + ny * dHy;
+            float* fo = Fs + task_fo[u];
+            fo[0] = fsc * (ny * dEz + (ndotdH * nx - dHx));
+            fo[FPAD] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
+            fo[2 * FPAD] = fsc * (ny * dHx - nx * dHy - dEz);
           }
+        }
+      }
+      if (ok && j + 1 < niter) {  // next block's traces, one block ahead
+        ok = mbar_wait_or_abort(&full[(j + 1) % S], static_cast<uint32_t>(((j + 1) / S) & 1),
+                                abort_flag);
+        if (ok) gather(j + 1);
+      }
+      // previous MMA has finished reading the operand tiles
+      if (ok && j >= 1)
+        ok = mbar_wait_or_abort(&mma_done[(j - 1) & 1], static_cast<uint32_t>(((j - 1) >> 1) & 1),
+                                abort_flag);
+      if (named_barrier_or(1, BT, !ok)) break;
+
+      // ---- GEMM rows of every element, split into TF32 hi / lo
 #pragma unroll
-          for (int q = 0; q < FP4 / 4; ++q) {
-            const int k = 2 * NPAD + ff * FP4 + 4 * q;
-            const float wx[4] = {fx[4 * q], fx[4 * q + 1], fx[4 * q + 2], fx[4 * q + 3]};
-            const float wy[4] = {fy[4 * q], fy[4 * q + 1], fy[4 * q + 2], fy[4 * q + 3]};
-            const float wz[4] = {fz[4 * q], fz[4 * q + 1], fz[4 * q + 2], fz[4 * q + 3]};
-            put4(xb, 3 * fe + 0, k, wx);
-            put4(xb, 3 * fe + 1, k, wy);
-            put4(xb, 3 * fe + 2, k, wz);
-          }
-        } else if (task < TASKS) {
-          // ---- nodes m0 .. m0+3 minus the vertex-node interpolant, into
-          // the Dr and Ds parts of rows 3e .. 3e+2
-          const int ve = (task - FACE_TASKS) % E, vc = (task - FACE_TASKS) / E;
-          if (ve >= nvalid) continue;
-          const int m0 = 4 * vc;
-          const float* qe = sq + ve * Np;
-          const float* ge = sg + ve * kGeo;
+      for (int u = 0; u < IPT; ++u) {
+        const int ch = item_c[u], e = item_e[u];
+        if (ch < 0 || e >= nvalid) continue;
+        float v[6][4];  // rows 3e+0..2: [0..2] first chunk, [3..5] second chunk
+        int k_a, k_b;   // K column of the first / second chunk (k_b < 0: none)
+        if (ch < IV) {
+          // nodes m0..m0+3 minus the vertex-node interpolant; Dr- and Ds-part chunks
+          const int m0 = 4 * ch;
+          const float* qe = sq + e * Np;
+          const float* ge = sg + e * kGeo;
           const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
           const float x1 = qe[0], x2 = qe[N], x3 = qe[Np - 1];
           const float y1 = qe[E * Np], y2 = qe[E * Np + N], y3 = qe[E * Np + Np - 1];
@@ -403,52 +384,67 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
           const float4 l3v = *reinterpret_cast<const float4*>(lam + NPAD + m0);
           const float l2a[4] = {l2v.x, l2v.y, l2v.z, l2v.w};
           const float l3a[4] = {l3v.x, l3v.y, l3v.z, l3v.w};
-          float ec[4], dhx[4], dhy[4];
 #pragma unroll
           for (int uu = 0; uu < 4; ++uu) {
             const int m = m0 + uu;
-            ec[uu] = dhx[uu] = dhy[uu] = 0.f;
+            float ec = 0.f, dhx = 0.f, dhy = 0.f;
             if (m < Np) {
-              ec[uu] = (qe[2 * E * Np + m] - z1) - ((z2 - z1) * l2a[uu] + (z3 - z1) * l3a[uu]);
-              dhx[uu] = (qe[m] - x1) - ((x2 - x1) * l2a[uu] + (x3 - x1) * l3a[uu]);
-              dhy[uu] = (qe[E * Np + m] - y1) - ((y2 - y1) * l2a[uu] + (y3 - y1) * l3a[uu]);
+              ec = (qe[2 * E * Np + m] - z1) - ((z2 - z1) * l2a[uu] + (z3 - z1) * l3a[uu]);
+              dhx = (qe[m] - x1) - ((x2 - x1) * l2a[uu] + (x3 - x1) * l3a[uu]);
+              dhy = (qe[E * Np + m] - y1) - ((y2 - y1) * l2a[uu] + (y3 - y1) * l3a[uu]);
             }
+            v[0][uu] = -ry * ec;
+            v[1][uu] = rx * ec;
+            v[2][uu] = rx * dhy - ry * dhx;
+            v[3][uu] = -sy * ec;
+            v[4][uu] = sx * ec;
+            v[5][uu] = sx * dhy - sy * dhx;
           }
-          {  // Dr part: -ry Ez_d, rx Ez_d, rx Hy_d - ry Hx_d
-            const float w0[4] = {-ry * ec[0], -ry * ec[1], -ry * ec[2], -ry * ec[3]};
-            const float w1[4] = {rx * ec[0], rx * ec[1], rx * ec[2], rx * ec[3]};
-            const float w2[4] = {rx * dhy[0] - ry * dhx[0], rx * dhy[1] - ry * dhx[1],
-                                 rx * dhy[2] - ry * dhx[2], rx * dhy[3] - ry * dhx[3]};
-            put4(xb, 3 * ve + 0, m0, w0);
-            put4(xb, 3 * ve + 1, m0, w1);
-            put4(xb, 3 * ve + 2, m0, w2);
+          k_a = m0;
+          k_b = NPAD + m0;
+        } else {
+          const int j0 = 4 * (ch - IV);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float4 f4 = *reinterpret_cast<const float4*>(Fs + (e * 3 + c) * FPAD + j0);
+            v[c][0] = f4.x;
+            v[c][1] = f4.y;
+            v[c][2] = f4.z;
+            v[c][3] = f4.w;
           }
-          {  // Ds part: -sy Ez_d, sx Ez_d, sx Hy_d - sy Hx_d
-            const float w0[4] = {-sy * ec[0], -sy * ec[1], -sy * ec[2], -sy * ec[3]};
-            const float w1[4] = {sx * ec[0], sx * ec[1], sx * ec[2], sx * ec[3]};
-            const float w2[4] = {sx * dhy[0] - sy * dhx[0], sx * dhy[1] - sy * dhx[1],
-                                 sx * dhy[2] - sy * dhx[2], sx * dhy[3] - sy * dhx[3]};
-            put4(xb, 3 * ve + 0, NPAD + m0, w0);
-            put4(xb, 3 * ve + 1, NPAD + m0, w1);
-            put4(xb, 3 * ve + 2, NPAD + m0, w2);
+          k_a = 2 * NPAD + j0;
+          k_b = -1;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && k_b < 0) break;
+          const int k = h == 0 ? k_a : k_b;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float* w = v[3 * h + c];
+            float4 hi, lo;  // hi: top 11 significand bits; lo: the exact rest
+            hi.x = tf32_trunc(w[0]);
+            hi.y = tf32_trunc(w[1]);
+            hi.z = tf32_trunc(w[2]);
+            hi.w = tf32_trunc(w[3]);
+            lo.x = w[0] - hi.x;
+            lo.y = w[1] - hi.y;
+            lo.z = w[2] - hi.z;
+            lo.w = w[3] - hi.w;
+            const int idx = tc_canon(3 * e + c, k, KP);
+            *reinterpret_cast<float4*>(Xs + idx) = hi;
+            *reinterpret_cast<float4*>(Xs + L::XB / 4 + idx) = lo;
           }
         }
       }
       fence_proxy_async();
-      mbar_arrive(&xfull[j & 1]);
-      if (j + 1 < niter) {  // next block's traces, one block ahead
-        ok = mbar_wait_or_abort(&full[(j + 1) % S], static_cast<uint32_t>(((j + 1) / S) & 1),
-                                abort_flag);
-        if (ok) gather(j + 1);
-      }
+      mbar_arrive(xfull);
+      // every build thread is done with Fs before the next block's flux
+      if (named_barrier_or(1, BT, false)) break;
     }
     if (!ok) fail();
   } else {
     // ======================= epilogue warps: accumulator -> stage update
-    // warp w: TMEM lanes 32 (w % 4) .. +31 (one GEMM row per thread), column
-    // chunks [0, NCH0) for w < 4, [NCH0, NCH) for w >= 4
-    const int quarter = warp & 3, half = warp >> 2;
-    const int ch0 = half == 0 ? 0 : L::NCH0, ch1 = half == 0 ? L::NCH0 : L::NCH;
     bool ok = true;
     for (int j = 0; j < niter; ++j) {
       const int s = j % S;
@@ -456,23 +452,21 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
                                     abort_flag);
       ok = ok && mbar_wait_or_abort(&full[s], static_cast<uint32_t>((j / S) & 1), abort_flag);
       // one decision for all epilogue warps (they meet again at barrier 2 below)
-      if (named_barrier_or(2, L::EPI_THREADS, !ok)) {
+      if (named_barrier_or(2, 32 * L::EPI_WARPS, !ok)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      float acc[L::NCH0 * 16];
+      float acc[NN];
       const uint32_t dacc = tmem + static_cast<uint32_t>((j & 1) * L::ACC_COLS) +
-                            (static_cast<uint32_t>(32 * quarter) << 16);
+                            (static_cast<uint32_t>(32 * warp) << 16);
 #pragma unroll
-      for (int c = 0; c < L::NCH0; ++c) {
-        if (ch0 + c < ch1) {
-          float va[16], vb[16];
-          tmem_ld16(dacc + 16 * (ch0 + c), va);       // X_hi Op_hi + X_lo Op_hi
-          tmem_ld16(dacc + NN + 16 * (ch0 + c), vb);  // X_hi Op_lo
+      for (int c0 = 0; c0 < NN; c0 += 16) {
+        float va[16], vb[16];
+        tmem_ld16(dacc + c0, va);       // X_hi Op_hi + X_lo Op_hi
+        tmem_ld16(dacc + NN + c0, vb);  // X_hi Op_lo
 #pragma unroll
-          for (int q = 0; q < 16; ++q) acc[16 * c + q] = va[q] + vb[q];
-        }
+        for (int q = 0; q < 16; ++q) acc[c0 + q] = va[q] + vb[q];
       }
       tmem_ld_wait();
       tc_fence_before();
@@ -483,7 +477,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       float* sq = reinterpret_cast<float*>(stages + s * L::STAGE_BYTES);  // q, then outputs
       float* sres = sq + 3 * E * Np;
       const float* sg = reinterpret_cast<const float*>(stages + s * L::STAGE_BYTES + 6 * L::QB);
-      const int r = 32 * quarter + lane;
+      const int r = 32 * warp + lane;
       const int e = r / 3, c = r - 3 * (r / 3);
       const bool row_ok = r < L::ROWS && e < nvalid;
       // chain-rule combination of the linear part's derivatives for row c;
@@ -505,16 +499,14 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
                         sx * (qe[E * Np + Np - 1] - y1) - sy * (qe[Np - 1] - x1));
         }
       }
-      named_barrier_or(2, L::EPI_THREADS, false);
+      named_barrier_or(2, 32 * L::EPI_WARPS, false);
       if (row_ok) {
         const int off = c * E * Np + e * Np;
         const bool full_block = nvalid == E;
         const int64_t g = static_cast<int64_t>(c) * fs + static_cast<int64_t>(k0 + e) * Np;
 #pragma unroll
-        for (int q = 0; q < L::NCH0 * 16; ++q) {
-          const int n = 16 * ch0 + q;
-          if (n >= 16 * ch1 || n >= Np) continue;
-          const float rhs = acc[q] + lin;
+        for (int n = 0; n < Np; ++n) {
+          const float rhs = acc[n] + lin;
           if (MODE == kModeRhs) {
             if (full_block)
               sq[off + n] = rhs;
