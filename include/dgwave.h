@@ -214,6 +214,40 @@ dg_status dg_solve(const dg_op* op, void* d_q, void* d_res, double T, double dt,
 dg_status dg_step_host(const dg_op* op, void* h_q, void* d_q, void* d_res, double t0,
                        double dt, int32_t nsteps, void* stream);
 
+/* Size of the scratch array that dg_step_static uses (per device).        */
+#define DG_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* dg_step_static: dg_step whose second field buffer is a fixed array inside
+ * the library rather than memory owned by the operator.  The paper has no
+ * counterpart; this is a library convenience.
+ *
+ * Which callers need it: callers that may not allocate device memory when
+ * they step, for instance under a fixed device-memory budget that is already
+ * handed out, or in a loop that must not call cudaMalloc/cudaFree, which
+ * synchronise the whole device.  The call allocates nothing: it uses the
+ * caller's d_q and d_res and a DG_STATIC_SCRATCH_BYTES array, one instance
+ * per device, that exists as soon as the library's device code is loaded.
+ *
+ * Result: the same as dg_step with the same arguments (same kernels, same
+ * launch order).  Limit: the fields must fit the array, i.e.
+ * 3 * field_stride * (4 for DG_FP32, 8 for DG_FP64) <= DG_STATIC_SCRATCH_BYTES
+ * (32 MiB: about 133,000 elements at N = 5 in FP32).  Larger operators get
+ * DG_ERR_ARG and a message naming the size; use dg_step for them.
+ *
+ * Nothing in the array has to start at zero.  Each call zeroes the entries
+ * of each field beyond K*Np, which the per-block copies read but no result
+ * uses.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with the operator's device current), which may load
+ * the library's device code.  Make that first call before any stream
+ * capture.  Every call with any operator on one device shares the one array:
+ * calls that overlap on the GPU (other streams, or other threads' calls not
+ * ordered by the caller) race and give wrong results.
+ * Errors: those of dg_step; DG_ERR_ARG for fields larger than the array;
+ * DG_ERR_CUDA if the address lookup fails.                                 */
+dg_status dg_step_static(const dg_op* op, void* d_q, void* d_res, double t0, double dt,
+                         int32_t nsteps, void* stream);
+
 /* dg_check_finite: synchronises `stream`, then scans the first K*Np values
  * of each field of d_q for NaN/Inf.  Returns DG_ERR_NONFINITE if any is
  * found (blow-up detection), DG_OK otherwise.                              */

@@ -25,7 +25,7 @@ __all__ = [
     "dg_mesh_create", "dg_mesh_info", "dg_mesh_connectivity", "dg_mesh_destroy",
     "dg_operator_setup", "dg_get_info", "dg_get_nodes", "dg_get_reference",
     "dg_get_geometry", "dg_get_maps", "dg_cfl_dt", "dg_lsrk_coefficients",
-    "dg_op_destroy", "dg_rhs", "dg_step", "dg_solve", "dg_step_host",
+    "dg_op_destroy", "dg_rhs", "dg_step", "dg_step_static", "dg_solve", "dg_step_host",
     "dg_check_finite", "dg_sync_check", "dg_launch_count", "dg_last_error",
     "Solver", "DGError", "DG_FP32", "DG_FP64",
 ]
@@ -158,6 +158,13 @@ def dg_rhs(op, q, rhs, t=0.0, stream=None):
 def dg_step(op, q, res, t0, dt, nsteps, stream=None):
     _lib.check(_lib.load().dg_step(op, _dptr(q), _dptr(res), t0, dt, nsteps,
                                    _stream_handle(stream)), "dg_step")
+
+
+def dg_step_static(op, q, res, t0, dt, nsteps, stream=None):
+    """dg_step with the library's fixed per-device scratch array instead of
+    the operator's own buffer (allocates nothing)."""
+    _lib.check(_lib.load().dg_step_static(op, _dptr(q), _dptr(res), t0, dt, nsteps,
+                                          _stream_handle(stream)), "dg_step_static")
 
 
 def dg_solve(op, q, res, T, dt=0.0, stream=None):

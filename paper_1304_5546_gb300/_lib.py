@@ -25,6 +25,7 @@ DG_FP64 = 0
 DG_FP32 = 1
 DG_SETUP_HOST_ONLY = 1
 DG_SETUP_SIMT = 2
+DG_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 DG_N_MAX = 7
 
 _STATUS_NAMES = {
@@ -57,6 +58,7 @@ SIGNATURES = [
     ("dg_rhs", c_i32, [c_void_p, c_void_p, c_void_p, c_dbl, c_void_p]),
     ("dg_step", c_i32, [c_void_p, c_void_p, c_void_p, c_dbl, c_dbl, c_i32, c_void_p]),
     ("dg_solve", c_i32, [c_void_p, c_void_p, c_void_p, c_dbl, c_dbl, P(c_i32), P(c_dbl), c_void_p]),
+    ("dg_step_static", c_i32, [c_void_p, c_void_p, c_void_p, c_dbl, c_dbl, c_i32, c_void_p]),
     ("dg_step_host", c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_dbl, c_dbl, c_i32, c_void_p]),
     ("dg_check_finite", c_i32, [c_void_p, c_void_p, c_void_p]),
     ("dg_sync_check", c_i32, [c_void_p, c_void_p]),

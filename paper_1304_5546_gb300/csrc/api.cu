@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -583,3 +584,107 @@ extern "C" int64_t dg_launch_count(const dg_op* op) {
 }
 
 extern "C" const char* dg_last_error(void) { return dgw::last_error_cstr(); }
+
+// ============================================================ static scratch
+// dg_step_static: the second field buffer of the stage ping-pong is this
+// fixed device array (one instance per device, present once the library's
+// device code is loaded) instead of the operator's own buffer.
+static __device__ __align__(256) unsigned char g_step_scratch[DG_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_step_scratch on `device`, looked up once per device
+// with that device current (the caller made it current).
+dg_status static_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices)
+    return fail(DG_ERR_CUDA, "dg_step_static: device %d out of range", device);
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[device]) {
+    void* p = nullptr;
+    cudaError_t err = cudaGetSymbolAddress(&p, g_step_scratch);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_step_static: cudaGetSymbolAddress");
+    g_scratch_addr[device] = p;
+  }
+  *out = g_scratch_addr[device];
+  return DG_OK;
+}
+
+// Same launch sequence as run_steps, with `tmp` as the ping-pong buffer.
+template <typename T>
+dg_status run_steps_static(const dg_op* op, T* q, T* res, double dt, int32_t nsteps, T* tmp,
+                           cudaStream_t s) {
+  dgw::StageArgs<T> a = base_args<T>(op);
+  a.res = res;
+  a.dt = static_cast<T>(dt);
+  T* cur = q;
+  T* other = tmp;
+  for (int32_t n = 0; n < nsteps; ++n) {
+    for (int i = 0; i < 5; ++i) {
+      a.qin = cur;
+      a.qout = other;
+      a.a = static_cast<T>(op->lsrk_a[i]);
+      a.b = static_cast<T>(op->lsrk_b[i]);
+      const int mode = (i == 0) ? dgw::kModeFirstStage : dgw::kModeStage;
+      cudaError_t err = launch_order<T>(op, a, mode, s);
+      if (err != cudaSuccess) return cuda_fail(err, "dg_step_static: kernel launch");
+      op->launches.fetch_add(1, std::memory_order_relaxed);
+      std::swap(cur, other);
+    }
+  }
+  if (cur != q) {
+    cudaError_t err = cudaMemcpyAsync(q, cur, 3 * op->fstride * sizeof(T),
+                                      cudaMemcpyDeviceToDevice, s);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_step_static: copy-back");
+  }
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" dg_status dg_step_static(const dg_op* op, void* d_q, void* d_res, double t0,
+                                    double dt, int32_t nsteps, void* stream) {
+  dgw::clear_error();
+  (void)t0;
+  dg_status st = check_device_op(op, "dg_step_static");  // makes op->device current
+  if (st) return st;
+  if ((st = check_field(op, d_q, "d_q", "dg_step_static"))) return st;
+  if ((st = check_field(op, d_res, "d_res", "dg_step_static"))) return st;
+  if (nsteps < 0) return fail(DG_ERR_ARG, "dg_step_static: nsteps = %d < 0", nsteps);
+  if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dg_step_static: dt is not finite");
+  const size_t bytes = 3 * op->fstride * op->elem_size;
+  if (bytes > static_cast<size_t>(DG_STATIC_SCRATCH_BYTES))
+    return fail(DG_ERR_ARG,
+                "dg_step_static: the fields need %zu bytes of scratch (K = %lld, N = %d), more "
+                "than the %zu-byte static scratch; use dg_step",
+                bytes, static_cast<long long>(op->K), op->N,
+                static_cast<size_t>(DG_STATIC_SCRATCH_BYTES));
+  if (overlaps(d_q, d_res, bytes))
+    return fail(DG_ERR_ARG, "dg_step_static: d_q and d_res overlap");
+  void* scratch = nullptr;
+  if ((st = static_scratch(op->device, &scratch))) return st;
+  if (overlaps(d_q, scratch, bytes) || overlaps(d_res, scratch, bytes))
+    return fail(DG_ERR_ARG, "dg_step_static: buffer overlaps the static scratch");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // The entries of each scratch field beyond K*Np never reach a result, but
+  // the per-block bulk copies read them; zero them so that no value another
+  // operator left there is ever read.
+  const int64_t used = op->K * op->Np;
+  const size_t tail = static_cast<size_t>(op->fstride - used) * op->elem_size;
+  if (tail > 0) {
+    for (int f = 0; f < 3; ++f) {
+      unsigned char* p = static_cast<unsigned char*>(scratch) +
+                         (static_cast<size_t>(f) * op->fstride + used) * op->elem_size;
+      cudaError_t err = cudaMemsetAsync(p, 0, tail, s);
+      if (err != cudaSuccess) return cuda_fail(err, "dg_step_static: cudaMemsetAsync");
+    }
+  }
+  if (op->precision == DG_FP32)
+    return run_steps_static<float>(op, static_cast<float*>(d_q), static_cast<float*>(d_res), dt,
+                                   nsteps, static_cast<float*>(scratch), s);
+  return run_steps_static<double>(op, static_cast<double*>(d_q), static_cast<double*>(d_res), dt,
+                                  nsteps, static_cast<double*>(scratch), s);
+}
