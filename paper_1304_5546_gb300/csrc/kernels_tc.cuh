@@ -11,9 +11,12 @@
 // X rows per element (u_d = u minus its linear interpolant through the
 // element's vertex nodes; A = rx Hy_d - ry Hx_d, B = sx Hy_d - sy Hx_d;
 // F_c = Fscale/2 * flux_c):
-//   row 3e+0 = [ -ry Ez_d | -sy Ez_d | F_x ]  ->  dHx/dt
-//   row 3e+1 = [  rx Ez_d |  sx Ez_d | F_y ]  ->  dHy/dt
-//   row 3e+2 = [  A       |  B       | F_z ]  ->  dEz/dt
+//   row      e = [ -ry Ez_d | -sy Ez_d | F_x ]  ->  dHx/dt
+//   row  E + e = [  rx Ez_d |  sx Ez_d | F_y ]  ->  dHy/dt
+//   row 2E + e = [  A       |  B       | F_z ]  ->  dEz/dt
+// (rows ordered field-major: the lanes of a warp own consecutive elements
+// of one field, so their shared-memory accesses run at a stride of Np words
+// and fall in 32 / gcd(Np, 32) distinct banks -- all 32 for odd Np)
 // (each part of a row starts on a 16-byte boundary, see tc_kd)
 // the right-hand side is D = X [Dr | Ds | LIFT]^T plus, per element and row,
 // the chain-rule combination of the linear part's exact derivatives
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       for (int u = 0; u < IPT; ++u) {
         const int ch = item_c[u], e = item_e[u];
         if (ch < 0 || e >= nvalid) continue;
-        float v[6][4];  // rows 3e+0..2: [0..2] first chunk, [3..5] second chunk
+        float v[6][4];  // rows cE+e, c = 0..2: [0..2] first chunk, [3..5] second chunk
         int k_a, k_b;   // K column of the first / second chunk (k_b < 0: none)
         if (ch < IV) {
           // nodes m0..m0+3 minus the vertex-node interpolant; Dr- and Ds-part chunks
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
             lo.y = w[1] - hi.y;
             lo.z = w[2] - hi.z;
             lo.w = w[3] - hi.w;
-            const int idx = tc_canon(3 * e + c, k, KP);
+            const int idx = tc_canon(c * E + e, k, KP);
             *reinterpret_cast<float4*>(Xs + idx) = hi;
             *reinterpret_cast<float4*>(Xs + L::XB / 4 + idx) = lo;
           }
@@ -478,7 +481,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       float* sres = sq + 3 * E * Np;
       const float* sg = reinterpret_cast<const float*>(stages + s * L::STAGE_BYTES + 6 * L::QB);
       const int r = 32 * warp + lane;
-      const int e = r / 3, c = r - 3 * (r / 3);
+      const int c = r / E, e = r - c * E;
       const bool row_ok = r < L::ROWS && e < nvalid;
       // chain-rule combination of the linear part's derivatives for row c;
       // it reads other rows' vertex values, so every row takes it before
