@@ -79,7 +79,7 @@ float tf32_round(double v) {
   return f;
 }
 
-// [Dr | Ds | LIFT] as the B operand of the tensor-core kernel: hi and lo TF32
+// [Dr | Ds | LIFT | 1] as the B operand of the tensor-core kernel: hi and lo TF32
 // parts (v ~ hi + lo, split in FP64), each an nn x kp tile in the core-matrix
 // layout of dgw::tc_canon, parts at the columns dgw::tc_kd describes; rows
 // >= Np and padding columns are zero.
@@ -100,6 +100,7 @@ std::vector<float> tc_operator_tiles(const dgw::RefElement& R) {
       put(n, npad + m, R.Ds[n * Np + m]);
     }
     for (int j = 0; j < Nafp; ++j) put(n, 2 * npad + j, R.LIFT[n * Nafp + j]);
+    put(n, 2 * npad + Nafp, 1.0);  // carries each row's linear-part term to every node
   }
   return out;
 }

@@ -1,5 +1,5 @@
 // FP32 stage kernel with the element-local products on the 5th-generation
-// tensor cores (tcgen05, TMEM accumulator).
+// tensor cores (tcgen05; operand A and the accumulator in tensor memory).
 //
 // Same result as dg_stage_kernel (kernels.cuh): right-hand side of Eq.
 // dg-strong-explicit -- volume derivative by Dr/Ds and the chain rule of Eq.
@@ -11,34 +11,40 @@
 // X rows per element (u_d = u minus its linear interpolant through the
 // element's vertex nodes; A = rx Hy_d - ry Hx_d, B = sx Hy_d - sy Hx_d;
 // F_c = Fscale/2 * flux_c):
-//   row      e = [ -ry Ez_d | -sy Ez_d | F_x ]  ->  dHx/dt
-//   row  E + e = [  rx Ez_d |  sx Ez_d | F_y ]  ->  dHy/dt
-//   row 2E + e = [  A       |  B       | F_z ]  ->  dEz/dt
-// (rows ordered field-major: the lanes of a warp own consecutive elements
-// of one field, so their shared-memory accesses run at a stride of Np words
-// and fall in 32 / gcd(Np, 32) distinct banks -- all 32 for odd Np)
-// (each part of a row starts on a 16-byte boundary, see tc_kd)
-// the right-hand side is D = X [Dr | Ds | LIFT]^T plus, per element and row,
-// the chain-rule combination of the linear part's exact derivatives
-// ((u_v2 - u_v1)/2 along r, (u_v3 - u_v1)/2 along s), added in the epilogue.
+//   row      e = [ -ry Ez_d | -sy Ez_d | F_x | L_x ]  ->  dHx/dt
+//   row  E + e = [  rx Ez_d |  sx Ez_d | F_y | L_y ]  ->  dHy/dt
+//   row 2E + e = [  A       |  B       | F_z | L_z ]  ->  dEz/dt
+// (each part of a row starts on a 16-byte boundary, see tc_kd; the last
+// column L of a row holds the chain-rule combination of the linear part's
+// exact derivatives, (u_v2 - u_v1)/2 along r and (u_v3 - u_v1)/2 along s,
+// and the operator tile holds 1 there for every node) the right-hand side
+// is the GEMM D = X [Dr | Ds | LIFT | 1]^T, with no further term.
 // The deflation keeps the products' operands O(h^2) for smooth fields, so
 // their TF32 rounding stays far below FP32 accuracy.  M = 3E rows (<= 128),
-// K = 2 Np + Nafp (padded to 8), N = Np (padded to 16).  FP32 accuracy
+// K = 2 Np + Nafp + 1 (padded to 8), N = Np (padded to 16).  FP32 accuracy
 // comes from three TF32 products, X_hi Op_hi + X_hi Op_lo + X_lo Op_hi: X_hi
 // keeps the top 11 significand bits of X, X_lo = X - X_hi (exact in FP32,
 // truncated to TF32 by the tensor core); Op's hi/lo split is made on the host
 // from FP64 with round-to-nearest.  One MMA of N = 2 Np' computes X_hi
 // [Op_hi ; Op_lo] so that X_hi is read once; a second adds X_lo Op_hi.
-// One thread issues the tcgen05.mma instructions; the FP32 accumulator lives
-// in TMEM (lane = row) and four warps read it back (tcgen05.ld) for the stage
-// update.
 //
-// Memory pipeline as in the CUDA-core kernel: a block's own data arrives
-// by 1D TMA bulk copies into a ring of stage buffers (mbarrier per stage),
-// neighbour traces are gathered one block ahead, and full blocks leave by
-// TMA bulk stores from the same stage buffer.  Every wait is bounded; on
-// expiry the CTA sets the status word, drains its copies (bounded), frees
-// its TMEM and returns.
+// X never touches shared memory: the build warps write it straight into
+// tensor memory (tcgen05.st; lane = row, one column per K index), and the
+// MMAs read operand A from there (double-buffered where the 512 columns
+// allow).  Shared memory carries only the stage data, the operator tiles
+// (operand B) and the face fluxes.  Rows are ordered field-major, so the 32
+// rows of a TMEM lane quarter -- the rows one warp may access -- are
+// consecutive elements, whose shared-memory reads at a stride of Np words
+// spread over 32 / gcd(Np, 32) banks.
+//
+// Warp roles: 4 epilogue warps (one per lane quarter: accumulator ->
+// LSRK update in place in the stage buffer), 12 build warps (upwind flux
+// at every face node into shared memory; then per lane quarter two warps
+// write the volume part of their rows' X and one the LIFT part), one MMA
+// warp, one memory warp (1D TMA bulk loads into a ring of stage buffers,
+// bulk stores of full blocks from the same buffers).  Neighbour traces are
+// gathered one block ahead.  Every wait is bounded; on expiry the CTA sets
+// the status word, drains its copies (bounded), frees its TMEM and returns.
 #pragma once
 
 #include "kernels.cuh"
@@ -51,46 +57,52 @@ struct TcLayout {
   static constexpr int Nfp = Order<N>::Nfp;
   static constexpr int Nafp = Order<N>::Nafp;
   static constexpr int E = (N == 7) ? 24 : 40;  // 3E <= 128 GEMM rows, E % 4 == 0
-  static constexpr int S = (N >= 6) ? 3 : 4;    // stage buffers
   static constexpr int ROWS = 3 * E;
   static constexpr int KD = tc_kd(N), KP = tc_kp(N), KG = KP / 4;
   static constexpr int NN = tc_nn(N);
-  // accumulator: columns [0, NN) hold X_hi Op_hi + X_lo Op_hi, columns
-  // [NN, 2 NN) hold X_hi Op_lo (one N = 2 NN MMA reads X_hi once for both)
-  static constexpr int ACC_COLS = 2 * NN <= 64 ? 64 : 128;  // TMEM columns per accumulator
-  static constexpr int TMEM_COLS = 2 * ACC_COLS;            // two accumulators
-  // warp roles: 0-3 epilogue (TMEM lane quarters), 4-17 flux + operand
-  // build, 18 MMA issue, 19 memory (TMA loads and stores)
-  static constexpr int EPI_WARPS = 4, BUILD_WARPS = 14;
+  static constexpr int NPAD = tc_npad(N);
+  static constexpr int IV = NPAD / 4;          // volume chunks of 4 nodes
+  static constexpr int LCOLS = KP - 2 * NPAD;  // LIFT-part columns (zero beyond Nafp)
+  // tensor memory: two accumulators of 2 NN columns (columns [0, NN) hold
+  // X_hi Op_hi + X_lo Op_hi, columns [NN, 2 NN) hold X_hi Op_lo), then XBUF
+  // operand buffers of 2 KP columns (X_hi, then X_lo)
+  static constexpr int ACC_COLS = 2 * NN;
+  static constexpr int XCOLS = 2 * KP;
+  static constexpr int XBUF = (2 * ACC_COLS + 2 * XCOLS <= 512) ? 2 : 1;
+  static constexpr int OFF_XT = 2 * ACC_COLS;
+  static constexpr int TMEM_COLS = 512;
+  // warp roles: 0-3 epilogue, 4-15 build (warp w serves lane quarter w % 4;
+  // role (w - 4) / 4: 0, 1 volume chunks, 2 LIFT part), 16 MMA, 17 memory
+  static constexpr int EPI_WARPS = 4, BUILD_WARPS = 12;
   static constexpr int MMA_WARP = EPI_WARPS + BUILD_WARPS, IO_WARP = MMA_WARP + 1;
   static constexpr int THREADS = 32 * (EPI_WARPS + BUILD_WARPS + 2);
   static constexpr int BUILD_THREADS = 32 * BUILD_WARPS;
-  static constexpr int NPAD = tc_npad(N);
-  static constexpr int FPAD = round_up(Nafp, 4);
   static constexpr int TASKS = E * Nafp;
   static constexpr int TPT = (TASKS + BUILD_THREADS - 1) / BUILD_THREADS;
-  // build items per element: NPAD/4 volume chunks (each writes its Dr-part
-  // and Ds-part 16-byte chunks) and FPAD/4 lift chunks
-  static constexpr int IV = NPAD / 4, IF = FPAD / 4;
-  static constexpr int ITEMS = E * (IV + IF);
-  static constexpr int IPT = (ITEMS + BUILD_THREADS - 1) / BUILD_THREADS;
+  static constexpr int FES = Nafp | 1;  // face-flux row stride, odd: conflict-free row reads
+  static constexpr int FB = 3 * E * FES * 4;  // one face-flux buffer [3][E][FES]
   static constexpr int QB = E * Np * 4;
   static constexpr int GB = E * kGeo * 4;
   static constexpr int CB = E * 3 * 4;
   static constexpr int STAGE_BYTES = round_up(6 * QB + GB + CB, 128);
-  static constexpr int XB = 128 * KP * 4;  // one X tile (hi or lo)
-  static constexpr int OB = NN * KP * 4;   // one operator tile (hi or lo)
-  static constexpr int FB = E * 3 * FPAD * 4;
+  static constexpr int OB = NN * KP * 4;  // one operator tile (hi or lo)
   static constexpr int HEADER = 1024;
-  static constexpr int OFF_STAGES = HEADER;
-  static constexpr int OFF_X = OFF_STAGES + S * STAGE_BYTES;
-  static constexpr int OFF_OP = OFF_X + 2 * XB;
+  static constexpr int OFF_OP = HEADER;
   static constexpr int OFF_F = OFF_OP + 2 * OB;
-  static constexpr size_t SMEM_BYTES = OFF_F + FB;
-  static_assert(SMEM_BYTES <= 232448, "shared memory");
+  static constexpr int OFF_STAGES = round_up(OFF_F + 2 * FB, 128);
+  static constexpr int SMAX = 232448;
+  static constexpr int S_FIT = (SMAX - OFF_STAGES) / STAGE_BYTES;
+  static constexpr int S = S_FIT < 6 ? S_FIT : 6;  // stage buffers
+  // at least half of the SM's shared memory: one CTA per SM, which owns all
+  // 512 TMEM columns (a second resident CTA would wait in tcgen05.alloc)
+  static constexpr size_t SMEM_USED = OFF_STAGES + S * STAGE_BYTES;
+  static constexpr size_t SMEM_BYTES = SMEM_USED > 118784 ? SMEM_USED : 118784;
+  static_assert(S >= 2 && S <= 8, "stage ring / header layout");
+  static_assert(SMEM_BYTES <= SMAX, "shared memory");
   static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0 && OB % 16 == 0, "TMA chunks");
   static_assert(ROWS <= 128 && NN <= 256 && NN % 16 == 0 && KP % 8 == 0, "UMMA shape");
-  static_assert(S <= 4, "header layout");
+  static_assert(LCOLS % 4 == 0 && LCOLS >= Nafp + 1, "LIFT part and linear-part column");
+  static_assert(2 * ACC_COLS + XBUF * XCOLS <= TMEM_COLS, "tensor memory");
 };
 
 template <int N, int MODE>
@@ -98,26 +110,24 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     dg_stage_tc_kernel(const StageArgs<float> p) {
   using L = TcLayout<N>;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
-  constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FPAD = L::FPAD;
-  constexpr int BT = L::BUILD_THREADS, TASKS = L::TASKS, TPT = L::TPT;
-  constexpr int IV = L::IV, ITEMS = L::ITEMS, IPT = L::IPT;
+  constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FES = L::FES, XBUF = L::XBUF;
+  constexpr int BT = L::BUILD_THREADS, TASKS = L::TASKS, TPT = L::TPT, IV = L::IV;
   constexpr int NQ = (MODE == kModeStage) ? 6 : 3;
 
   extern __shared__ __align__(1024) unsigned char smem[];
   // header: mbarriers, TMEM base, abort flag, tables
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);              // [S] stage loaded
-  uint64_t* out_ready = reinterpret_cast<uint64_t*>(smem + 32);    // [S] outputs written
-  uint64_t* mma_done = reinterpret_cast<uint64_t*>(smem + 64);     // [2] accumulator ready
-  uint64_t* tmem_free = reinterpret_cast<uint64_t*>(smem + 80);    // [2] accumulator read
-  uint64_t* xfull = reinterpret_cast<uint64_t*>(smem + 96);        // operand tile built
-  uint64_t* op_bar = reinterpret_cast<uint64_t*>(smem + 104);      // operator tiles landed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 112);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 116);
-  int* nbr = reinterpret_cast<int*>(smem + 128);      // [6][Nfp] neighbour face-node table
+  uint64_t* out_ready = reinterpret_cast<uint64_t*>(smem + 64);    // [S] outputs written
+  uint64_t* mma_done = reinterpret_cast<uint64_t*>(smem + 128);    // [2] accumulator ready
+  uint64_t* tmem_free = reinterpret_cast<uint64_t*>(smem + 144);   // [2] accumulator read
+  uint64_t* xfull = reinterpret_cast<uint64_t*>(smem + 160);       // [2] operand rows written
+  uint64_t* op_bar = reinterpret_cast<uint64_t*>(smem + 176);      // operator tiles landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 184);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 188);
+  int* nbr = reinterpret_cast<int*>(smem + 192);      // [6][Nfp] neighbour face-node table
   float* lam = reinterpret_cast<float*>(smem + 384);  // [2][NPAD] vertex-interpolant weights
   unsigned char* stages = smem + L::OFF_STAGES;
-  float* Xs = reinterpret_cast<float*>(smem + L::OFF_X);  // [2][128 x KP] canonical
-  float* Fs = reinterpret_cast<float*>(smem + L::OFF_F);  // [E][3][FPAD]
+  float* Fs = reinterpret_cast<float*>(smem + L::OFF_F);  // [2][3][E][FES] face fluxes
 
   const int t = threadIdx.x;
   const int warp = t >> 5, lane = t & 31;
@@ -136,8 +146,8 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&mma_done[b], 1);
       mbar_init(&tmem_free[b], 32 * L::EPI_WARPS);
+      mbar_init(&xfull[b], BT);
     }
-    mbar_init(xfull, BT);
     mbar_init(op_bar, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -151,12 +161,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     const int m = t % NPAD;
     lam[t] = m < Np ? __ldg(p.lam + (t / NPAD) * Np + m) : 0.f;
   }
-  {  // zero the X tiles (padding columns and rows beyond 3E stay zero) and Fs
-    float4* x4 = reinterpret_cast<float4*>(Xs);
-    for (int idx = t; idx < 2 * L::XB / 16; idx += L::THREADS)
-      x4[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int idx = t; idx < L::FB / 4; idx += L::THREADS) Fs[idx] = 0.f;
-  }
+  for (int idx = t; idx < 2 * L::FB / 4; idx += L::THREADS) Fs[idx] = 0.f;
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
@@ -236,28 +241,28 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     // ======================= MMA warp: 2 x (KP / 8) tcgen05.mma per block (lane 0)
     if (lane == 0) {
       bool ok = mbar_wait_or_abort(op_bar, 0, abort_flag);
-      const uint32_t xaddr = smem_u32(Xs);
       const uint32_t oaddr = smem_u32(smem + L::OFF_OP);
       constexpr uint32_t LBO = 128, SBO = L::KG * 128;
       constexpr uint32_t IDESC2 = umma_idesc_tf32(128, 2 * NN);  // B = [Op_hi ; Op_lo]
       constexpr uint32_t IDESC1 = umma_idesc_tf32(128, NN);      // B = Op_hi
       int mma_pending = -1;  // block whose MMA group may still run
       for (int j = 0; ok && j < niter; ++j) {
-        ok = mbar_wait_or_abort(xfull, static_cast<uint32_t>(j & 1), abort_flag);
+        const int xb = j % XBUF;
+        ok = mbar_wait_or_abort(&xfull[xb], static_cast<uint32_t>((j / XBUF) & 1), abort_flag);
         if (ok && j >= 2)
           ok = mbar_wait_or_abort(&tmem_free[j & 1], static_cast<uint32_t>(((j - 2) >> 1) & 1),
                                   abort_flag);
         if (!ok) break;
         tc_fence_after();
         const uint32_t dacc = tmem + static_cast<uint32_t>((j & 1) * L::ACC_COLS);
+        const uint32_t xh = tmem + static_cast<uint32_t>(L::OFF_XT + xb * L::XCOLS);
 #pragma unroll
         for (int ks = 0; ks < KP / 8; ++ks)  // X_hi [Op_hi ; Op_lo] -> columns [0, 2 NN)
-          umma_tf32(dacc, umma_desc(xaddr + ks * 256, LBO, SBO),
-                    umma_desc(oaddr + ks * 256, LBO, SBO), IDESC2, ks > 0 ? 1u : 0u);
+          umma_tf32_ta(dacc, xh + 8 * ks, umma_desc(oaddr + ks * 256, LBO, SBO), IDESC2,
+                       ks > 0 ? 1u : 0u);
 #pragma unroll
         for (int ks = 0; ks < KP / 8; ++ks)  // + X_lo Op_hi -> columns [0, NN)
-          umma_tf32(dacc, umma_desc(xaddr + L::XB + ks * 256, LBO, SBO),
-                    umma_desc(oaddr + ks * 256, LBO, SBO), IDESC1, 1u);
+          umma_tf32_ta(dacc, xh + KP + 8 * ks, umma_desc(oaddr + ks * 256, LBO, SBO), IDESC1, 1u);
         umma_commit(&mma_done[j & 1]);
         mma_pending = j;
       }
@@ -269,8 +274,13 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       }
     }
   } else if (warp >= L::EPI_WARPS) {
-    // ======================= build warps: flux, then GEMM operand rows
+    // ======================= build warps: flux, then the GEMM rows into TMEM
     const int bt = t - 32 * L::EPI_WARPS;
+    const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. + 31
+    const int role = (warp - L::EPI_WARPS) >> 2;  // 0, 1: volume chunks; 2: LIFT part
+    const int r = 32 * quarter + lane;            // this thread's X row
+    const int rc = r / E, re = r - rc * E;        // its output field and element
+    const uint32_t lane_base = static_cast<uint32_t>(32 * quarter) << 16;
     const float* qin[3] = {p.qin, p.qin + fs, p.qin + 2 * fs};
     // flux tasks of this thread (the same in every block): element slot,
     // offsets of its own face node, face code, face geometry and flux slot
@@ -284,14 +294,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       task_nm[u] = ee * Np + face_node_dev(N, f, jj);
       task_cf[u] = ee * 3 + f;
       task_gf[u] = ee * kGeo + 4 + 3 * f;
-      task_fo[u] = (ee * 3) * FPAD + j;
-    }
-    int item_e[IPT], item_c[IPT];  // (element, chunk), element fastest
-#pragma unroll
-    for (int u = 0; u < IPT; ++u) {
-      const int idx = bt + u * BT;
-      item_c[u] = idx < ITEMS ? idx / E : -1;  // -1: no item
-      item_e[u] = idx - (idx / E) * E;
+      task_fo[u] = ee * FES + j;
     }
     float trc[TPT][3];
     auto gather = [&](int it) {
@@ -327,8 +330,9 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       const float* sq = reinterpret_cast<const float*>(st);
       const float* sg = reinterpret_cast<const float*>(st + 6 * L::QB);
       const int32_t* sc = reinterpret_cast<const int32_t*>(st + 6 * L::QB + L::GB);
+      float* Fb = Fs + (j & 1) * (L::FB / 4);
 
-      // ---- upwind flux at every face node -> Fs[e][c][j], scaled by Fscale/2
+      // ---- upwind flux at every face node -> Fb[c][e][j], scaled by Fscale/2
       if (ok) {
 #pragma unroll
         for (int u = 0; u < TPT; ++u) {
@@ -349,10 +353,10 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
             const float* gf = sg + task_gf[u];
             const float nx = gf[0], ny = gf[1], fsc = gf[2];
             const float ndotdH = nx * dHx + ny * dHy;
-            float* fo = Fs + task_fo[u];
+            float* fo = Fb + task_fo[u];
             fo[0] = fsc * (ny * dEz + (ndotdH * nx - dHx));
-            fo[FPAD] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
-            fo[2 * FPAD] = fsc * (ny * dHx - nx * dHy - dEz);
+            fo[E * FES] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
+            fo[2 * E * FES] = fsc * (ny * dHx - nx * dHy - dEz);
           }
         }
       }
@@ -361,89 +365,126 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
                                 abort_flag);
         if (ok) gather(j + 1);
       }
-      // previous MMA has finished reading the operand tiles
-      if (ok && j >= 1)
-        ok = mbar_wait_or_abort(&mma_done[(j - 1) & 1], static_cast<uint32_t>(((j - 1) >> 1) & 1),
-                                abort_flag);
+      // the MMAs that last read this operand buffer are done
+      if (ok && j >= XBUF)
+        ok = mbar_wait_or_abort(&mma_done[(j - XBUF) & 1],
+                                static_cast<uint32_t>(((j - XBUF) >> 1) & 1), abort_flag);
+      // every flux of this block is in Fb (double-buffered: the next block's
+      // flux goes to the other buffer, and the one after waits for this barrier)
       if (named_barrier_or(1, BT, !ok)) break;
+      tc_fence_after();
 
-      // ---- GEMM rows of every element, split into TF32 hi / lo
+      // ---- this thread's X row, split into TF32 hi / lo, into tensor memory
+      const bool row_ok = r < L::ROWS && re < nvalid;
+      const uint32_t xh = tmem + lane_base + static_cast<uint32_t>(L::OFF_XT + (j % XBUF) * L::XCOLS);
+      const uint32_t xl = xh + KP;
+      if (role < 2) {
+        // volume chunks ch = role, role + 2, ...: nodes 4ch .. 4ch+3 minus the
+        // vertex-node interpolant, geometric combination for output field rc
+        const float* qe = sq + re * Np;
+        const float* ge = sg + re * kGeo;
+        float rx = 0.f, ry = 0.f, sx = 0.f, sy = 0.f;
+        float a1 = 0.f, a2 = 0.f, a3 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;  // vertex values
+        if (row_ok) {
+          rx = ge[0];
+          ry = ge[1];
+          sx = ge[2];
+          sy = ge[3];
+          if (rc < 2) {
+            a1 = qe[2 * E * Np];
+            a2 = qe[2 * E * Np + N];
+            a3 = qe[2 * E * Np + Np - 1];
+          } else {
+            a1 = qe[0];
+            a2 = qe[N];
+            a3 = qe[Np - 1];
+            b1 = qe[E * Np];
+            b2 = qe[E * Np + N];
+            b3 = qe[E * Np + Np - 1];
+          }
+        }
+        // coefficients of the row: Dr part = cr1 u + cr2 w, Ds part = cs1 u + cs2 w
+        // (u = Ez_d, w = 0 for rc < 2; u = Hx_d, w = Hy_d for rc = 2)
+        const float cr1 = rc == 0 ? -ry : (rc == 1 ? rx : -ry);
+        const float cs1 = rc == 0 ? -sy : (rc == 1 ? sx : -sy);
+        const float cr2 = rc == 2 ? rx : 0.f;
+        const float cs2 = rc == 2 ? sx : 0.f;
+        const int fu = rc < 2 ? 2 * E * Np : 0;  // offset of field u in the stage buffer
 #pragma unroll
-      for (int u = 0; u < IPT; ++u) {
-        const int ch = item_c[u], e = item_e[u];
-        if (ch < 0 || e >= nvalid) continue;
-        float v[6][4];  // rows cE+e, c = 0..2: [0..2] first chunk, [3..5] second chunk
-        int k_a, k_b;   // K column of the first / second chunk (k_b < 0: none)
-        if (ch < IV) {
-          // nodes m0..m0+3 minus the vertex-node interpolant; Dr- and Ds-part chunks
+        for (int u = 0; u < (IV + 1) / 2; ++u) {
+          const int ch = role + 2 * u;
+          if (ch >= IV) break;
           const int m0 = 4 * ch;
-          const float* qe = sq + e * Np;
-          const float* ge = sg + e * kGeo;
-          const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
-          const float x1 = qe[0], x2 = qe[N], x3 = qe[Np - 1];
-          const float y1 = qe[E * Np], y2 = qe[E * Np + N], y3 = qe[E * Np + Np - 1];
-          const float z1 = qe[2 * E * Np], z2 = qe[2 * E * Np + N], z3 = qe[2 * E * Np + Np - 1];
           const float4 l2v = *reinterpret_cast<const float4*>(lam + m0);
           const float4 l3v = *reinterpret_cast<const float4*>(lam + NPAD + m0);
           const float l2a[4] = {l2v.x, l2v.y, l2v.z, l2v.w};
           const float l3a[4] = {l3v.x, l3v.y, l3v.z, l3v.w};
+          float hr[4], lr[4], hs[4], ls[4];
 #pragma unroll
           for (int uu = 0; uu < 4; ++uu) {
             const int m = m0 + uu;
-            float ec = 0.f, dhx = 0.f, dhy = 0.f;
-            if (m < Np) {
-              ec = (qe[2 * E * Np + m] - z1) - ((z2 - z1) * l2a[uu] + (z3 - z1) * l3a[uu]);
-              dhx = (qe[m] - x1) - ((x2 - x1) * l2a[uu] + (x3 - x1) * l3a[uu]);
-              dhy = (qe[E * Np + m] - y1) - ((y2 - y1) * l2a[uu] + (y3 - y1) * l3a[uu]);
+            float vr = 0.f, vs = 0.f;
+            if (row_ok && m < Np) {
+              const float ud = (qe[fu + m] - a1) - ((a2 - a1) * l2a[uu] + (a3 - a1) * l3a[uu]);
+              vr = cr1 * ud;
+              vs = cs1 * ud;
+              if (rc == 2) {
+                const float wd =
+                    (qe[E * Np + m] - b1) - ((b2 - b1) * l2a[uu] + (b3 - b1) * l3a[uu]);
+                vr += cr2 * wd;
+                vs += cs2 * wd;
+              }
             }
-            v[0][uu] = -ry * ec;
-            v[1][uu] = rx * ec;
-            v[2][uu] = rx * dhy - ry * dhx;
-            v[3][uu] = -sy * ec;
-            v[4][uu] = sx * ec;
-            v[5][uu] = sx * dhy - sy * dhx;
+            hr[uu] = tf32_trunc(vr);
+            lr[uu] = vr - hr[uu];
+            hs[uu] = tf32_trunc(vs);
+            ls[uu] = vs - hs[uu];
           }
-          k_a = m0;
-          k_b = NPAD + m0;
-        } else {
-          const int j0 = 4 * (ch - IV);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float4 f4 = *reinterpret_cast<const float4*>(Fs + (e * 3 + c) * FPAD + j0);
-            v[c][0] = f4.x;
-            v[c][1] = f4.y;
-            v[c][2] = f4.z;
-            v[c][3] = f4.w;
+          __syncwarp();
+          tmem_st4(xh + m0, hr);
+          tmem_st4(xh + NPAD + m0, hs);
+          tmem_st4(xl + m0, lr);
+          tmem_st4(xl + NPAD + m0, ls);
+        }
+      } else {
+        // LIFT part: this row's face fluxes, then (column Nafp of the part)
+        // the chain-rule combination of the linear part's exact derivatives,
+        // which the operator tile multiplies by 1 for every node; zero beyond
+        const float* fr = Fb + rc * E * FES + re * FES;
+        float lin = 0.f;
+        if (row_ok) {
+          const float* qe = sq + re * Np;
+          const float* ge = sg + re * kGeo;
+          const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
+          if (rc < 2) {
+            const float z1 = qe[2 * E * Np];
+            const float grz = 0.5f * (qe[2 * E * Np + N] - z1);
+            const float gsz = 0.5f * (qe[2 * E * Np + Np - 1] - z1);
+            lin = (rc == 0) ? -(ry * grz + sy * gsz) : (rx * grz + sx * gsz);
+          } else {
+            const float x1 = qe[0], y1 = qe[E * Np];
+            lin = 0.5f * (rx * (qe[E * Np + N] - y1) - ry * (qe[N] - x1) +
+                          sx * (qe[E * Np + Np - 1] - y1) - sy * (qe[Np - 1] - x1));
           }
-          k_a = 2 * NPAD + j0;
-          k_b = -1;
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h == 1 && k_b < 0) break;
-          const int k = h == 0 ? k_a : k_b;
+        for (int j0 = 0; j0 < L::LCOLS; j0 += 4) {
+          float h4[4], l4[4];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float* w = v[3 * h + c];
-            float4 hi, lo;  // hi: top 11 significand bits; lo: the exact rest
-            hi.x = tf32_trunc(w[0]);
-            hi.y = tf32_trunc(w[1]);
-            hi.z = tf32_trunc(w[2]);
-            hi.w = tf32_trunc(w[3]);
-            lo.x = w[0] - hi.x;
-            lo.y = w[1] - hi.y;
-            lo.z = w[2] - hi.z;
-            lo.w = w[3] - hi.w;
-            const int idx = tc_canon(c * E + e, k, KP);
-            *reinterpret_cast<float4*>(Xs + idx) = hi;
-            *reinterpret_cast<float4*>(Xs + L::XB / 4 + idx) = lo;
+          for (int uu = 0; uu < 4; ++uu) {
+            const int jj = j0 + uu;
+            const float v = !row_ok ? 0.f : (jj < Nafp ? fr[jj] : (jj == Nafp ? lin : 0.f));
+            h4[uu] = tf32_trunc(v);
+            l4[uu] = v - h4[uu];
           }
+          __syncwarp();
+          tmem_st4(xh + 2 * NPAD + j0, h4);
+          tmem_st4(xl + 2 * NPAD + j0, l4);
         }
       }
-      fence_proxy_async();
-      mbar_arrive(xfull);
-      // every build thread is done with Fs before the next block's flux
-      if (named_barrier_or(1, BT, false)) break;
+      tmem_st_wait();
+      tc_fence_before();
+      mbar_arrive(&xfull[j % XBUF]);
     }
     if (!ok) fail();
   } else {
@@ -454,8 +495,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       ok = ok && mbar_wait_or_abort(&mma_done[j & 1], static_cast<uint32_t>((j >> 1) & 1),
                                     abort_flag);
       ok = ok && mbar_wait_or_abort(&full[s], static_cast<uint32_t>((j / S) & 1), abort_flag);
-      // one decision for all epilogue warps (they meet again at barrier 2 below)
-      if (named_barrier_or(2, 32 * L::EPI_WARPS, !ok)) {
+      if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
         break;
       }
@@ -479,37 +519,17 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       const int nvalid = (K - k0) < E ? (K - k0) : E;
       float* sq = reinterpret_cast<float*>(stages + s * L::STAGE_BYTES);  // q, then outputs
       float* sres = sq + 3 * E * Np;
-      const float* sg = reinterpret_cast<const float*>(stages + s * L::STAGE_BYTES + 6 * L::QB);
       const int r = 32 * warp + lane;
       const int c = r / E, e = r - c * E;
+      // each thread updates only its own row: no ordering with other rows
       const bool row_ok = r < L::ROWS && e < nvalid;
-      // chain-rule combination of the linear part's derivatives for row c;
-      // it reads other rows' vertex values, so every row takes it before
-      // any row is overwritten in place (named barrier over these warps)
-      float lin = 0.f;
-      if (row_ok) {
-        const float* qe = sq + e * Np;
-        const float* ge = sg + e * kGeo;
-        const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
-        if (c < 2) {
-          const float z1 = qe[2 * E * Np];
-          const float grz = 0.5f * (qe[2 * E * Np + N] - z1);
-          const float gsz = 0.5f * (qe[2 * E * Np + Np - 1] - z1);
-          lin = (c == 0) ? -(ry * grz + sy * gsz) : (rx * grz + sx * gsz);
-        } else {
-          const float x1 = qe[0], y1 = qe[E * Np];
-          lin = 0.5f * (rx * (qe[E * Np + N] - y1) - ry * (qe[N] - x1) +
-                        sx * (qe[E * Np + Np - 1] - y1) - sy * (qe[Np - 1] - x1));
-        }
-      }
-      named_barrier_or(2, 32 * L::EPI_WARPS, false);
       if (row_ok) {
         const int off = c * E * Np + e * Np;
         const bool full_block = nvalid == E;
         const int64_t g = static_cast<int64_t>(c) * fs + static_cast<int64_t>(k0 + e) * Np;
 #pragma unroll
         for (int n = 0; n < Np; ++n) {
-          const float rhs = acc[n] + lin;
+          const float rhs = acc[n];
           if (MODE == kModeRhs) {
             if (full_block)
               sq[off + n] = rhs;

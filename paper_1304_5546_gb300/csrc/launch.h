@@ -41,14 +41,16 @@ cudaError_t launch_stage(const StageArgs<T>& args, int mode, int num_sms, cudaSt
 
 // Tensor-core path (FP32 fields, 3xTF32 products; see kernels_tc.cuh).  The
 // element-local products of a block of elements form one GEMM
-//   D[3E x Np] = X[3E x KD] [Dr | Ds | LIFT]^T
+//   D[3E x Np] = X[3E x KD] [Dr | Ds | LIFT | 1]^T
 // whose K columns are laid out part by part, each part starting on a
 // 16-byte boundary: Dr columns at [0, NPAD), Ds at [NPAD, 2 NPAD), LIFT at
-// [2 NPAD, 2 NPAD + Nafp) with NPAD = Np rounded up to 4; K is padded to
-// tc_kp(N) (multiple of 8) and N to tc_nn(N) (multiple of 16).
+// [2 NPAD, 2 NPAD + Nafp) with NPAD = Np rounded up to 4, then one column
+// (2 NPAD + Nafp) whose operator entries are 1 for every node and whose X
+// entry is the row's linear-part term; K is padded to tc_kp(N) (multiple
+// of 8) and N to tc_nn(N) (multiple of 16).
 __host__ __device__ constexpr int tc_np(int N) { return (N + 1) * (N + 2) / 2; }
 __host__ __device__ constexpr int tc_npad(int N) { return (tc_np(N) + 3) / 4 * 4; }
-__host__ __device__ constexpr int tc_kd(int N) { return 2 * tc_npad(N) + 3 * (N + 1); }
+__host__ __device__ constexpr int tc_kd(int N) { return 2 * tc_npad(N) + 3 * (N + 1) + 1; }
 __host__ __device__ constexpr int tc_kp(int N) { return (tc_kd(N) + 7) / 8 * 8; }
 __host__ __device__ constexpr int tc_nn(int N) { return (tc_np(N) + 15) / 16 * 16; }
 // Float index of element (row n, column k) of a K-major operand tile with kp
