@@ -39,8 +39,9 @@
 //
 // Warp roles: 4 epilogue warps (one per lane quarter: accumulator ->
 // LSRK update in place in the stage buffer), 12 build warps (upwind flux
-// at every face node into shared memory; then per lane quarter two warps
-// write the volume part of their rows' X and one the LIFT part), one MMA
+// at every face node into shared memory; then the three warps of each lane
+// quarter write their rows of X, each an even share of the volume-part and
+// LIFT-part column chunks, with packed FP32x2 arithmetic), one MMA
 // warp, one memory warp (1D TMA bulk loads into a ring of stage buffers,
 // bulk stores of full blocks from the same buffers).  Neighbour traces are
 // gathered one block ahead.  Every wait is bounded; on expiry the CTA sets
@@ -71,8 +72,8 @@ struct TcLayout {
   static constexpr int XBUF = (2 * ACC_COLS + 2 * XCOLS <= 512) ? 2 : 1;
   static constexpr int OFF_XT = 2 * ACC_COLS;
   static constexpr int TMEM_COLS = 512;
-  // warp roles: 0-3 epilogue, 4-15 build (warp w serves lane quarter w % 4;
-  // role (w - 4) / 4: 0, 1 volume chunks, 2 LIFT part), 16 MMA, 17 memory
+  // warp roles: 0-3 epilogue, 4-15 build (warp w serves lane quarter w % 4
+  // and takes share (w - 4) / 4 of its rows' chunks), 16 MMA, 17 memory
   static constexpr int EPI_WARPS = 4, BUILD_WARPS = 12;
   static constexpr int MMA_WARP = EPI_WARPS + BUILD_WARPS, IO_WARP = MMA_WARP + 1;
   static constexpr int THREADS = 32 * (EPI_WARPS + BUILD_WARPS + 2);
@@ -103,6 +104,7 @@ struct TcLayout {
   static_assert(ROWS <= 128 && NN <= 256 && NN % 16 == 0 && KP % 8 == 0, "UMMA shape");
   static_assert(LCOLS % 4 == 0 && LCOLS >= Nafp + 1, "LIFT part and linear-part column");
   static_assert(2 * ACC_COLS + XBUF * XCOLS <= TMEM_COLS, "tensor memory");
+  static_assert(BUILD_WARPS % 4 == 0, "build warps come in lane-quarter groups");
 };
 
 template <int N, int MODE>
@@ -277,7 +279,10 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     // ======================= build warps: flux, then the GEMM rows into TMEM
     const int bt = t - 32 * L::EPI_WARPS;
     const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. + 31
-    const int role = (warp - L::EPI_WARPS) >> 2;  // 0, 1: volume chunks; 2: LIFT part
+    const int role = (warp - L::EPI_WARPS) >> 2;  // share of the row's chunks
+    constexpr int NR = L::BUILD_WARPS / 4, LC = L::LCOLS / 4;
+    const int vol_lo = role * IV / NR, vol_hi = (role + 1) * IV / NR;
+    const int lift_lo = (NR - 1 - role) * LC / NR, lift_hi = (NR - role) * LC / NR;
     const int r = 32 * quarter + lane;            // this thread's X row
     const int rc = r / E, re = r - rc * E;        // its output field and element
     const uint32_t lane_base = static_cast<uint32_t>(32 * quarter) << 16;
@@ -374,101 +379,96 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       if (named_barrier_or(1, BT, !ok)) break;
       tc_fence_after();
 
-      // ---- this thread's X row, split into TF32 hi / lo, into tensor memory
+      // ---- this thread's X row, split into TF32 hi / lo, into tensor memory.
+      // The NR warps of a lane quarter share the row's chunks of 4 columns
+      // evenly: a contiguous range of volume chunks (Dr and Ds parts) and a
+      // contiguous range of LIFT-part chunks, taken from the other end.
       const bool row_ok = r < L::ROWS && re < nvalid;
       const uint32_t xh = tmem + lane_base + static_cast<uint32_t>(L::OFF_XT + (j % XBUF) * L::XCOLS);
       const uint32_t xl = xh + KP;
-      if (role < 2) {
-        // volume chunks ch = role, role + 2, ...: nodes 4ch .. 4ch+3 minus the
-        // vertex-node interpolant, geometric combination for output field rc
-        const float* qe = sq + re * Np;
+      const float* qe = sq + re * Np;
+      float rx = 0.f, ry = 0.f, sx = 0.f, sy = 0.f;
+      float a1 = 0.f, a2 = 0.f, a3 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;  // vertex values
+      if (row_ok) {
         const float* ge = sg + re * kGeo;
-        float rx = 0.f, ry = 0.f, sx = 0.f, sy = 0.f;
-        float a1 = 0.f, a2 = 0.f, a3 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;  // vertex values
-        if (row_ok) {
-          rx = ge[0];
-          ry = ge[1];
-          sx = ge[2];
-          sy = ge[3];
-          if (rc < 2) {
-            a1 = qe[2 * E * Np];
-            a2 = qe[2 * E * Np + N];
-            a3 = qe[2 * E * Np + Np - 1];
-          } else {
-            a1 = qe[0];
-            a2 = qe[N];
-            a3 = qe[Np - 1];
-            b1 = qe[E * Np];
-            b2 = qe[E * Np + N];
-            b3 = qe[E * Np + Np - 1];
-          }
+        rx = ge[0];
+        ry = ge[1];
+        sx = ge[2];
+        sy = ge[3];
+        if (rc < 2) {  // u = Ez
+          a1 = qe[2 * E * Np];
+          a2 = qe[2 * E * Np + N];
+          a3 = qe[2 * E * Np + Np - 1];
+        } else {  // u = Hx, w = Hy
+          a1 = qe[0];
+          a2 = qe[N];
+          a3 = qe[Np - 1];
+          b1 = qe[E * Np];
+          b2 = qe[E * Np + N];
+          b3 = qe[E * Np + Np - 1];
         }
-        // coefficients of the row: Dr part = cr1 u + cr2 w, Ds part = cs1 u + cs2 w
-        // (u = Ez_d, w = 0 for rc < 2; u = Hx_d, w = Hy_d for rc = 2)
-        const float cr1 = rc == 0 ? -ry : (rc == 1 ? rx : -ry);
-        const float cs1 = rc == 0 ? -sy : (rc == 1 ? sx : -sy);
-        const float cr2 = rc == 2 ? rx : 0.f;
-        const float cs2 = rc == 2 ? sx : 0.f;
-        const int fu = rc < 2 ? 2 * E * Np : 0;  // offset of field u in the stage buffer
+      }
+      for (int ch = vol_lo; ch < vol_hi; ++ch) {
+        // nodes 4ch .. 4ch+3 (two pairs, packed FP32x2 arithmetic): deflated
+        // u (and w), then the row's Dr part cr1 u + cr2 w and Ds part
+        // cs1 u + cs2 w, with (cr1, cs1, cr2, cs2) = (-ry, -sy, 0, 0),
+        // (rx, sx, 0, 0), (-ry, -sy, rx, sx) for output field Hx, Hy, Ez
+        const int m0 = 4 * ch;
+        const float4 l2v = *reinterpret_cast<const float4*>(lam + m0);
+        const float4 l3v = *reinterpret_cast<const float4*>(lam + NPAD + m0);
+        float hr[4], lr[4], hs[4], ls[4];
 #pragma unroll
-        for (int u = 0; u < (IV + 1) / 2; ++u) {
-          const int ch = role + 2 * u;
-          if (ch >= IV) break;
-          const int m0 = 4 * ch;
-          const float4 l2v = *reinterpret_cast<const float4*>(lam + m0);
-          const float4 l3v = *reinterpret_cast<const float4*>(lam + NPAD + m0);
-          const float l2a[4] = {l2v.x, l2v.y, l2v.z, l2v.w};
-          const float l3a[4] = {l3v.x, l3v.y, l3v.z, l3v.w};
-          float hr[4], lr[4], hs[4], ls[4];
-#pragma unroll
-          for (int uu = 0; uu < 4; ++uu) {
-            const int m = m0 + uu;
-            float vr = 0.f, vs = 0.f;
-            if (row_ok && m < Np) {
-              const float ud = (qe[fu + m] - a1) - ((a2 - a1) * l2a[uu] + (a3 - a1) * l3a[uu]);
-              vr = cr1 * ud;
-              vs = cs1 * ud;
-              if (rc == 2) {
-                const float wd =
-                    (qe[E * Np + m] - b1) - ((b2 - b1) * l2a[uu] + (b3 - b1) * l3a[uu]);
-                vr += cr2 * wd;
-                vs += cs2 * wd;
-              }
-            }
-            hr[uu] = tf32_trunc(vr);
-            lr[uu] = vr - hr[uu];
-            hs[uu] = tf32_trunc(vs);
-            ls[uu] = vs - hs[uu];
+        for (int pp = 0; pp < 2; ++pp) {
+          const int m = m0 + 2 * pp;
+          const f32x2 l2 = pp == 0 ? f32x2_pack(l2v.x, l2v.y) : f32x2_pack(l2v.z, l2v.w);
+          const f32x2 l3 = pp == 0 ? f32x2_pack(l3v.x, l3v.y) : f32x2_pack(l3v.z, l3v.w);
+          const bool in0 = row_ok && m < Np, in1 = row_ok && m + 1 < Np;
+          const int fu = rc < 2 ? 2 * E * Np : 0;
+          const f32x2 uq = f32x2_pack(in0 ? qe[fu + m] : a1, in1 ? qe[fu + m + 1] : a1);
+          // (u - u1) - ((u2 - u1) lam2 + (u3 - u1) lam3): zero where out of range
+          f32x2 ud = f32x2_sub(uq, f32x2_dup(a1));
+          ud = f32x2_sub(ud, f32x2_fma(f32x2_dup(a2 - a1), l2, f32x2_mul(f32x2_dup(a3 - a1), l3)));
+          f32x2 vr = f32x2_mul(f32x2_dup(rc == 1 ? rx : -ry), ud);
+          f32x2 vs = f32x2_mul(f32x2_dup(rc == 1 ? sx : -sy), ud);
+          if (rc == 2) {
+            const f32x2 wq = f32x2_pack(in0 ? qe[E * Np + m] : b1, in1 ? qe[E * Np + m + 1] : b1);
+            f32x2 wd = f32x2_sub(wq, f32x2_dup(b1));
+            wd = f32x2_sub(wd, f32x2_fma(f32x2_dup(b2 - b1), l2, f32x2_mul(f32x2_dup(b3 - b1), l3)));
+            vr = f32x2_fma(f32x2_dup(rx), wd, vr);
+            vs = f32x2_fma(f32x2_dup(sx), wd, vs);
           }
-          __syncwarp();
-          tmem_st4(xh + m0, hr);
-          tmem_st4(xh + NPAD + m0, hs);
-          tmem_st4(xl + m0, lr);
-          tmem_st4(xl + NPAD + m0, ls);
+          // out-of-range nodes carry exactly zero (u - u1 - 0 with u = u1
+          // needs lam = 0 there, which the zero-padded table gives for
+          // m >= Np; rows that are not valid have all vertex values 0)
+          const f32x2 hrp = f32x2_tf32_trunc(vr), hsp = f32x2_tf32_trunc(vs);
+          const f32x2 lrp = f32x2_sub(vr, hrp), lsp = f32x2_sub(vs, hsp);
+          f32x2_unpack(hrp, hr[2 * pp], hr[2 * pp + 1]);
+          f32x2_unpack(hsp, hs[2 * pp], hs[2 * pp + 1]);
+          f32x2_unpack(lrp, lr[2 * pp], lr[2 * pp + 1]);
+          f32x2_unpack(lsp, ls[2 * pp], ls[2 * pp + 1]);
         }
-      } else {
+        __syncwarp();
+        tmem_st4(xh + m0, hr);
+        tmem_st4(xh + NPAD + m0, hs);
+        tmem_st4(xl + m0, lr);
+        tmem_st4(xl + NPAD + m0, ls);
+      }
+      if (lift_lo < lift_hi) {
         // LIFT part: this row's face fluxes, then (column Nafp of the part)
         // the chain-rule combination of the linear part's exact derivatives,
         // which the operator tile multiplies by 1 for every node; zero beyond
         const float* fr = Fb + rc * E * FES + re * FES;
         float lin = 0.f;
         if (row_ok) {
-          const float* qe = sq + re * Np;
-          const float* ge = sg + re * kGeo;
-          const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
-          if (rc < 2) {
-            const float z1 = qe[2 * E * Np];
-            const float grz = 0.5f * (qe[2 * E * Np + N] - z1);
-            const float gsz = 0.5f * (qe[2 * E * Np + Np - 1] - z1);
+          if (rc < 2) {  // a = Ez vertex values
+            const float grz = 0.5f * (a2 - a1), gsz = 0.5f * (a3 - a1);
             lin = (rc == 0) ? -(ry * grz + sy * gsz) : (rx * grz + sx * gsz);
-          } else {
-            const float x1 = qe[0], y1 = qe[E * Np];
-            lin = 0.5f * (rx * (qe[E * Np + N] - y1) - ry * (qe[N] - x1) +
-                          sx * (qe[E * Np + Np - 1] - y1) - sy * (qe[Np - 1] - x1));
+          } else {  // a = Hx, b = Hy vertex values
+            lin = 0.5f * (rx * (b2 - b1) - ry * (a2 - a1) + sx * (b3 - b1) - sy * (a3 - a1));
           }
         }
-#pragma unroll
-        for (int j0 = 0; j0 < L::LCOLS; j0 += 4) {
+        for (int lc = lift_lo; lc < lift_hi; ++lc) {
+          const int j0 = 4 * lc;
           float h4[4], l4[4];
 #pragma unroll
           for (int uu = 0; uu < 4; ++uu) {
