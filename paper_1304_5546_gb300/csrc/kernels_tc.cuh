@@ -107,13 +107,121 @@ struct TcLayout {
   static_assert(BUILD_WARPS % 4 == 0, "build warps come in lane-quarter groups");
 };
 
+// The column chunks (4 columns each) of one X row that build warp share
+// ROLE of a lane quarter writes: a contiguous range of volume chunks and a
+// contiguous range of LIFT-part chunks taken from the other end, so that the
+// NR shares are even.
+template <class L, int ROLE>
+struct RowShare {
+  static constexpr int NR = L::BUILD_WARPS / 4, LC = L::LCOLS / 4;
+  static constexpr int VLO = ROLE * L::IV / NR, VHI = (ROLE + 1) * L::IV / NR;
+  static constexpr int LLO = (NR - 1 - ROLE) * LC / NR, LHI = (NR - ROLE) * LC / NR;
+};
+
+// One thread's share of its X row (hi and lo TF32 parts) into tensor memory
+// at xh / xl (this warp's lane quarter).  Every value is computed first and
+// the tcgen05.st follow, so the loads of all chunks can be in flight at once.
+// rc: output field of the row; qe: the element's fields in the stage buffer;
+// fr: the row's face fluxes; (a1, a2, a3) / (b1, b2, b3): vertex values of u
+// (Ez for rc < 2, Hx for rc = 2) / of w (Hy, rc = 2).
+template <int N, class L, int ROLE>
+__device__ __forceinline__ void build_x_share(const float* qe, const float* fr, const float* lam,
+                                              uint32_t xh, uint32_t xl, bool row_ok, int rc,
+                                              float rx, float ry, float sx, float sy, float a1,
+                                              float a2, float a3, float b1, float b2, float b3) {
+  using R = RowShare<L, ROLE>;
+  constexpr int Np = L::Np, E = L::E, NPAD = L::NPAD, Nafp = L::Nafp;
+  constexpr int NV = R::VHI - R::VLO, NL = R::LHI - R::LLO;
+  float hr[NV > 0 ? 4 * NV : 1], lr[NV > 0 ? 4 * NV : 1];
+  float hs[NV > 0 ? 4 * NV : 1], ls[NV > 0 ? 4 * NV : 1];
+  float hl[NL > 0 ? 4 * NL : 1], ll[NL > 0 ? 4 * NL : 1];
+  const int fu = rc < 2 ? 2 * E * Np : 0;  // field u in the stage buffer
+  // volume part: nodes 4ch .. 4ch+3 in pairs (packed FP32x2): deflated u (and
+  // w), then the Dr part cr1 u + cr2 w and the Ds part cs1 u + cs2 w with
+  // (cr1, cs1, cr2, cs2) = (-ry, -sy, 0, 0), (rx, sx, 0, 0), (-ry, -sy, rx, sx)
+  // for output field Hx, Hy, Ez.  Nodes >= Np and rows that are not valid
+  // come out exactly zero (u = u1 there, the zero-padded weights, and zero
+  // vertex values and factors for invalid rows).
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int m0 = 4 * (R::VLO + v);
+    const float4 l2v = *reinterpret_cast<const float4*>(lam + m0);
+    const float4 l3v = *reinterpret_cast<const float4*>(lam + NPAD + m0);
+#pragma unroll
+    for (int pp = 0; pp < 2; ++pp) {
+      const int m = m0 + 2 * pp;
+      const f32x2 l2 = pp == 0 ? f32x2_pack(l2v.x, l2v.y) : f32x2_pack(l2v.z, l2v.w);
+      const f32x2 l3 = pp == 0 ? f32x2_pack(l3v.x, l3v.y) : f32x2_pack(l3v.z, l3v.w);
+      const bool in0 = row_ok && m < Np, in1 = row_ok && m + 1 < Np;
+      const f32x2 uq = f32x2_pack(in0 ? qe[fu + m] : a1, in1 ? qe[fu + m + 1] : a1);
+      f32x2 ud = f32x2_sub(uq, f32x2_dup(a1));
+      ud = f32x2_sub(ud, f32x2_fma(f32x2_dup(a2 - a1), l2, f32x2_mul(f32x2_dup(a3 - a1), l3)));
+      f32x2 vr = f32x2_mul(f32x2_dup(rc == 1 ? rx : -ry), ud);
+      f32x2 vs = f32x2_mul(f32x2_dup(rc == 1 ? sx : -sy), ud);
+      if (rc == 2) {
+        const f32x2 wq = f32x2_pack(in0 ? qe[E * Np + m] : b1, in1 ? qe[E * Np + m + 1] : b1);
+        f32x2 wd = f32x2_sub(wq, f32x2_dup(b1));
+        wd = f32x2_sub(wd, f32x2_fma(f32x2_dup(b2 - b1), l2, f32x2_mul(f32x2_dup(b3 - b1), l3)));
+        vr = f32x2_fma(f32x2_dup(rx), wd, vr);
+        vs = f32x2_fma(f32x2_dup(sx), wd, vs);
+      }
+      const f32x2 hrp = f32x2_tf32_trunc(vr), hsp = f32x2_tf32_trunc(vs);
+      const int i = 4 * v + 2 * pp;
+      f32x2_unpack(hrp, hr[i], hr[i + 1]);
+      f32x2_unpack(hsp, hs[i], hs[i + 1]);
+      f32x2_unpack(f32x2_sub(vr, hrp), lr[i], lr[i + 1]);
+      f32x2_unpack(f32x2_sub(vs, hsp), ls[i], ls[i + 1]);
+    }
+  }
+  // LIFT part: the row's face fluxes, then (column Nafp of the part) the
+  // chain-rule combination of the linear part's exact derivatives, which the
+  // operator tile multiplies by 1 for every node; zero beyond
+  if constexpr (NL > 0) {
+    float lin = 0.f;
+    if (row_ok) {
+      if (rc < 2) {  // a = Ez vertex values
+        const float grz = 0.5f * (a2 - a1), gsz = 0.5f * (a3 - a1);
+        lin = (rc == 0) ? -(ry * grz + sy * gsz) : (rx * grz + sx * gsz);
+      } else {  // a = Hx, b = Hy vertex values
+        lin = 0.5f * (rx * (b2 - b1) - ry * (a2 - a1) + sx * (b3 - b1) - sy * (a3 - a1));
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4 * NL; ++v) {
+      const int jj = 4 * R::LLO + v;
+      float x = 0.f;
+      if (jj < Nafp)
+        x = row_ok ? fr[jj] : 0.f;
+      else if (jj == Nafp)
+        x = lin;
+      hl[v] = tf32_trunc(x);
+      ll[v] = x - hl[v];
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int m0 = 4 * (R::VLO + v);
+    tmem_st4(xh + m0, *reinterpret_cast<const float(*)[4]>(hr + 4 * v));
+    tmem_st4(xh + NPAD + m0, *reinterpret_cast<const float(*)[4]>(hs + 4 * v));
+    tmem_st4(xl + m0, *reinterpret_cast<const float(*)[4]>(lr + 4 * v));
+    tmem_st4(xl + NPAD + m0, *reinterpret_cast<const float(*)[4]>(ls + 4 * v));
+  }
+#pragma unroll
+  for (int v = 0; v < NL; ++v) {
+    const int j0 = 4 * (R::LLO + v);
+    tmem_st4(xh + 2 * NPAD + j0, *reinterpret_cast<const float(*)[4]>(hl + 4 * v));
+    tmem_st4(xl + 2 * NPAD + j0, *reinterpret_cast<const float(*)[4]>(ll + 4 * v));
+  }
+}
+
 template <int N, int MODE>
 __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     dg_stage_tc_kernel(const StageArgs<float> p) {
   using L = TcLayout<N>;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
   constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FES = L::FES, XBUF = L::XBUF;
-  constexpr int BT = L::BUILD_THREADS, TASKS = L::TASKS, TPT = L::TPT, IV = L::IV;
+  constexpr int BT = L::BUILD_THREADS, TASKS = L::TASKS, TPT = L::TPT;
   constexpr int NQ = (MODE == kModeStage) ? 6 : 3;
 
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -280,9 +388,6 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     const int bt = t - 32 * L::EPI_WARPS;
     const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. + 31
     const int role = (warp - L::EPI_WARPS) >> 2;  // share of the row's chunks
-    constexpr int NR = L::BUILD_WARPS / 4, LC = L::LCOLS / 4;
-    const int vol_lo = role * IV / NR, vol_hi = (role + 1) * IV / NR;
-    const int lift_lo = (NR - 1 - role) * LC / NR, lift_hi = (NR - role) * LC / NR;
     const int r = 32 * quarter + lane;            // this thread's X row
     const int rc = r / E, re = r - rc * E;        // its output field and element
     const uint32_t lane_base = static_cast<uint32_t>(32 * quarter) << 16;
@@ -408,79 +513,23 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
           b3 = qe[E * Np + Np - 1];
         }
       }
-      for (int ch = vol_lo; ch < vol_hi; ++ch) {
-        // nodes 4ch .. 4ch+3 (two pairs, packed FP32x2 arithmetic): deflated
-        // u (and w), then the row's Dr part cr1 u + cr2 w and Ds part
-        // cs1 u + cs2 w, with (cr1, cs1, cr2, cs2) = (-ry, -sy, 0, 0),
-        // (rx, sx, 0, 0), (-ry, -sy, rx, sx) for output field Hx, Hy, Ez
-        const int m0 = 4 * ch;
-        const float4 l2v = *reinterpret_cast<const float4*>(lam + m0);
-        const float4 l3v = *reinterpret_cast<const float4*>(lam + NPAD + m0);
-        float hr[4], lr[4], hs[4], ls[4];
-#pragma unroll
-        for (int pp = 0; pp < 2; ++pp) {
-          const int m = m0 + 2 * pp;
-          const f32x2 l2 = pp == 0 ? f32x2_pack(l2v.x, l2v.y) : f32x2_pack(l2v.z, l2v.w);
-          const f32x2 l3 = pp == 0 ? f32x2_pack(l3v.x, l3v.y) : f32x2_pack(l3v.z, l3v.w);
-          const bool in0 = row_ok && m < Np, in1 = row_ok && m + 1 < Np;
-          const int fu = rc < 2 ? 2 * E * Np : 0;
-          const f32x2 uq = f32x2_pack(in0 ? qe[fu + m] : a1, in1 ? qe[fu + m + 1] : a1);
-          // (u - u1) - ((u2 - u1) lam2 + (u3 - u1) lam3): zero where out of range
-          f32x2 ud = f32x2_sub(uq, f32x2_dup(a1));
-          ud = f32x2_sub(ud, f32x2_fma(f32x2_dup(a2 - a1), l2, f32x2_mul(f32x2_dup(a3 - a1), l3)));
-          f32x2 vr = f32x2_mul(f32x2_dup(rc == 1 ? rx : -ry), ud);
-          f32x2 vs = f32x2_mul(f32x2_dup(rc == 1 ? sx : -sy), ud);
-          if (rc == 2) {
-            const f32x2 wq = f32x2_pack(in0 ? qe[E * Np + m] : b1, in1 ? qe[E * Np + m + 1] : b1);
-            f32x2 wd = f32x2_sub(wq, f32x2_dup(b1));
-            wd = f32x2_sub(wd, f32x2_fma(f32x2_dup(b2 - b1), l2, f32x2_mul(f32x2_dup(b3 - b1), l3)));
-            vr = f32x2_fma(f32x2_dup(rx), wd, vr);
-            vs = f32x2_fma(f32x2_dup(sx), wd, vs);
-          }
-          // out-of-range nodes carry exactly zero (u - u1 - 0 with u = u1
-          // needs lam = 0 there, which the zero-padded table gives for
-          // m >= Np; rows that are not valid have all vertex values 0)
-          const f32x2 hrp = f32x2_tf32_trunc(vr), hsp = f32x2_tf32_trunc(vs);
-          const f32x2 lrp = f32x2_sub(vr, hrp), lsp = f32x2_sub(vs, hsp);
-          f32x2_unpack(hrp, hr[2 * pp], hr[2 * pp + 1]);
-          f32x2_unpack(hsp, hs[2 * pp], hs[2 * pp + 1]);
-          f32x2_unpack(lrp, lr[2 * pp], lr[2 * pp + 1]);
-          f32x2_unpack(lsp, ls[2 * pp], ls[2 * pp + 1]);
-        }
-        __syncwarp();
-        tmem_st4(xh + m0, hr);
-        tmem_st4(xh + NPAD + m0, hs);
-        tmem_st4(xl + m0, lr);
-        tmem_st4(xl + NPAD + m0, ls);
-      }
-      if (lift_lo < lift_hi) {
-        // LIFT part: this row's face fluxes, then (column Nafp of the part)
-        // the chain-rule combination of the linear part's exact derivatives,
-        // which the operator tile multiplies by 1 for every node; zero beyond
-        const float* fr = Fb + rc * E * FES + re * FES;
-        float lin = 0.f;
-        if (row_ok) {
-          if (rc < 2) {  // a = Ez vertex values
-            const float grz = 0.5f * (a2 - a1), gsz = 0.5f * (a3 - a1);
-            lin = (rc == 0) ? -(ry * grz + sy * gsz) : (rx * grz + sx * gsz);
-          } else {  // a = Hx, b = Hy vertex values
-            lin = 0.5f * (rx * (b2 - b1) - ry * (a2 - a1) + sx * (b3 - b1) - sy * (a3 - a1));
-          }
-        }
-        for (int lc = lift_lo; lc < lift_hi; ++lc) {
-          const int j0 = 4 * lc;
-          float h4[4], l4[4];
-#pragma unroll
-          for (int uu = 0; uu < 4; ++uu) {
-            const int jj = j0 + uu;
-            const float v = !row_ok ? 0.f : (jj < Nafp ? fr[jj] : (jj == Nafp ? lin : 0.f));
-            h4[uu] = tf32_trunc(v);
-            l4[uu] = v - h4[uu];
-          }
-          __syncwarp();
-          tmem_st4(xh + 2 * NPAD + j0, h4);
-          tmem_st4(xl + 2 * NPAD + j0, l4);
-        }
+      const float* fr = Fb + rc * E * FES + re * FES;
+      switch (role) {  // compile-time chunk ranges: the whole share unrolls
+        case 0:
+          build_x_share<N, L, 0>(qe, fr, lam, xh, xl, row_ok, rc, rx, ry, sx, sy, a1, a2, a3, b1, b2, b3);
+          break;
+        case 1:
+          if constexpr (L::BUILD_WARPS / 4 > 1)
+            build_x_share<N, L, 1>(qe, fr, lam, xh, xl, row_ok, rc, rx, ry, sx, sy, a1, a2, a3, b1, b2, b3);
+          break;
+        case 2:
+          if constexpr (L::BUILD_WARPS / 4 > 2)
+            build_x_share<N, L, 2>(qe, fr, lam, xh, xl, row_ok, rc, rx, ry, sx, sy, a1, a2, a3, b1, b2, b3);
+          break;
+        default:
+          if constexpr (L::BUILD_WARPS / 4 > 3)
+            build_x_share<N, L, 3>(qe, fr, lam, xh, xl, row_ok, rc, rx, ry, sx, sy, a1, a2, a3, b1, b2, b3);
+          break;
       }
       tmem_st_wait();
       tc_fence_before();
