@@ -38,14 +38,15 @@
 // spread over 32 / gcd(Np, 32) banks.
 //
 // Warp roles: 4 epilogue warps (one per lane quarter: accumulator ->
-// LSRK update in place in the stage buffer), 12 build warps (upwind flux
-// at every face node into shared memory; then the three warps of each lane
-// quarter write their rows of X, each an even share of the volume-part and
-// LIFT-part column chunks, with packed FP32x2 arithmetic), one MMA
-// warp, one memory warp (1D TMA bulk loads into a ring of stage buffers,
-// bulk stores of full blocks from the same buffers).  Neighbour traces are
-// gathered one block ahead.  Every wait is bounded; on expiry the CTA sets
-// the status word, drains its copies (bounded), frees its TMEM and returns.
+// LSRK update in place in the stage buffer), 8 flux warps (upwind flux at
+// every face node into a double-buffered shared-memory array, up to two
+// blocks ahead; neighbour traces gathered one block ahead), 8 operand-row
+// warps (two per lane quarter, each an even share of its rows' volume-part
+// and LIFT-part column chunks, with packed FP32x2 arithmetic; the LIFT part
+// waits for the block's fluxes), one MMA warp, one memory warp (1D TMA bulk
+// loads into a ring of stage buffers, bulk stores of full blocks from the
+// same buffers).  Every wait is bounded; on expiry the CTA sets the status
+// word, drains its copies (bounded), frees its TMEM and returns.
 #pragma once
 
 #include "kernels.cuh"
@@ -72,14 +73,16 @@ struct TcLayout {
   static constexpr int XBUF = (2 * ACC_COLS + 2 * XCOLS <= 512) ? 2 : 1;
   static constexpr int OFF_XT = 2 * ACC_COLS;
   static constexpr int TMEM_COLS = 512;
-  // warp roles: 0-3 epilogue, 4-15 build (warp w serves lane quarter w % 4
-  // and takes share (w - 4) / 4 of its rows' chunks), 16 MMA, 17 memory
-  static constexpr int EPI_WARPS = 4, BUILD_WARPS = 12;
-  static constexpr int MMA_WARP = EPI_WARPS + BUILD_WARPS, IO_WARP = MMA_WARP + 1;
-  static constexpr int THREADS = 32 * (EPI_WARPS + BUILD_WARPS + 2);
-  static constexpr int BUILD_THREADS = 32 * BUILD_WARPS;
+  // warp roles: 0-3 epilogue; 4-15 operand rows (warp w serves lane quarter
+  // w % 4 and takes share (w - 4) / 4 of its rows' chunks); 16-19 face flux
+  // and neighbour gathers; 20 MMA; 21 memory
+  static constexpr int EPI_WARPS = 4, X_WARPS = 8, FLUX_WARPS = 8;
+  static constexpr int FLUX_WARP0 = EPI_WARPS + X_WARPS;
+  static constexpr int MMA_WARP = FLUX_WARP0 + FLUX_WARPS, IO_WARP = MMA_WARP + 1;
+  static constexpr int THREADS = 32 * (IO_WARP + 1);
+  static constexpr int X_THREADS = 32 * X_WARPS, FLUX_THREADS = 32 * FLUX_WARPS;
   static constexpr int TASKS = E * Nafp;
-  static constexpr int TPT = (TASKS + BUILD_THREADS - 1) / BUILD_THREADS;
+  static constexpr int TPT = (TASKS + FLUX_THREADS - 1) / FLUX_THREADS;
   static constexpr int FES = Nafp | 1;  // face-flux row stride, odd: conflict-free row reads
   static constexpr int FB = 3 * E * FES * 4;  // one face-flux buffer [3][E][FES]
   static constexpr int QB = E * Np * 4;
@@ -104,7 +107,7 @@ struct TcLayout {
   static_assert(ROWS <= 128 && NN <= 256 && NN % 16 == 0 && KP % 8 == 0, "UMMA shape");
   static_assert(LCOLS % 4 == 0 && LCOLS >= Nafp + 1, "LIFT part and linear-part column");
   static_assert(2 * ACC_COLS + XBUF * XCOLS <= TMEM_COLS, "tensor memory");
-  static_assert(BUILD_WARPS % 4 == 0, "build warps come in lane-quarter groups");
+  static_assert(X_WARPS % 4 == 0, "operand-row warps come in lane-quarter groups");
 };
 
 // The column chunks (4 columns each) of one X row that build warp share
@@ -113,70 +116,93 @@ struct TcLayout {
 // NR shares are even.
 template <class L, int ROLE>
 struct RowShare {
-  static constexpr int NR = L::BUILD_WARPS / 4, LC = L::LCOLS / 4;
+  static constexpr int NR = L::X_WARPS / 4, LC = L::LCOLS / 4;
   static constexpr int VLO = ROLE * L::IV / NR, VHI = (ROLE + 1) * L::IV / NR;
   static constexpr int LLO = (NR - 1 - ROLE) * LC / NR, LHI = (NR - ROLE) * LC / NR;
 };
 
 // One thread's share of its X row (hi and lo TF32 parts) into tensor memory
-// at xh / xl (this warp's lane quarter).  Every value is computed first and
-// the tcgen05.st follow, so the loads of all chunks can be in flight at once.
-// rc: output field of the row; qe: the element's fields in the stage buffer;
-// fr: the row's face fluxes; (a1, a2, a3) / (b1, b2, b3): vertex values of u
-// (Ez for rc < 2, Hx for rc = 2) / of w (Hy, rc = 2).
+// at xh / xl (this warp's lane quarter), in two calls: the volume part, then
+// the LIFT part (which waits for the face fluxes).  Each call computes every
+// value first and then issues its tcgen05.st, so the loads of all its chunks
+// can be in flight at once.  rc: output field of the row; qe: the element's
+// fields in the stage buffer; fr: the row's face fluxes; (a1, a2, a3) /
+// (b1, b2, b3): vertex values of u (Ez for rc < 2, Hx for rc = 2) / of w (Hy,
+// rc = 2).
+//
+// Volume part: nodes 4ch .. 4ch+3 in pairs (packed FP32x2): deflated u (and
+// w), then the Dr part cr1 u + cr2 w and the Ds part cs1 u + cs2 w with
+// (cr1, cs1, cr2, cs2) = (-ry, -sy, 0, 0), (rx, sx, 0, 0), (-ry, -sy, rx, sx)
+// for output field Hx, Hy, Ez.  Nodes >= Np and rows that are not valid come
+// out exactly zero (u = u1 there, the zero-padded weights, and zero vertex
+// values and factors for invalid rows).
 template <int N, class L, int ROLE>
-__device__ __forceinline__ void build_x_share(const float* qe, const float* fr, const float* lam,
-                                              uint32_t xh, uint32_t xl, bool row_ok, int rc,
-                                              float rx, float ry, float sx, float sy, float a1,
-                                              float a2, float a3, float b1, float b2, float b3) {
+__device__ __forceinline__ void build_x_vol(const float* qe, const float* lam, uint32_t xh,
+                                            uint32_t xl, bool row_ok, int rc, float rx, float ry,
+                                            float sx, float sy, float a1, float a2, float a3,
+                                            float b1, float b2, float b3) {
   using R = RowShare<L, ROLE>;
-  constexpr int Np = L::Np, E = L::E, NPAD = L::NPAD, Nafp = L::Nafp;
-  constexpr int NV = R::VHI - R::VLO, NL = R::LHI - R::LLO;
-  float hr[NV > 0 ? 4 * NV : 1], lr[NV > 0 ? 4 * NV : 1];
-  float hs[NV > 0 ? 4 * NV : 1], ls[NV > 0 ? 4 * NV : 1];
-  float hl[NL > 0 ? 4 * NL : 1], ll[NL > 0 ? 4 * NL : 1];
-  const int fu = rc < 2 ? 2 * E * Np : 0;  // field u in the stage buffer
-  // volume part: nodes 4ch .. 4ch+3 in pairs (packed FP32x2): deflated u (and
-  // w), then the Dr part cr1 u + cr2 w and the Ds part cs1 u + cs2 w with
-  // (cr1, cs1, cr2, cs2) = (-ry, -sy, 0, 0), (rx, sx, 0, 0), (-ry, -sy, rx, sx)
-  // for output field Hx, Hy, Ez.  Nodes >= Np and rows that are not valid
-  // come out exactly zero (u = u1 there, the zero-padded weights, and zero
-  // vertex values and factors for invalid rows).
+  constexpr int Np = L::Np, E = L::E, NPAD = L::NPAD;
+  constexpr int NV = R::VHI - R::VLO;
+  if constexpr (NV > 0) {
+    float hr[4 * NV], lr[4 * NV], hs[4 * NV], ls[4 * NV];
+    const int fu = rc < 2 ? 2 * E * Np : 0;  // field u in the stage buffer
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const int m0 = 4 * (R::VLO + v);
-    const float4 l2v = *reinterpret_cast<const float4*>(lam + m0);
-    const float4 l3v = *reinterpret_cast<const float4*>(lam + NPAD + m0);
+    for (int v = 0; v < NV; ++v) {
+      const int m0 = 4 * (R::VLO + v);
+      const float4 l2v = *reinterpret_cast<const float4*>(lam + m0);
+      const float4 l3v = *reinterpret_cast<const float4*>(lam + NPAD + m0);
 #pragma unroll
-    for (int pp = 0; pp < 2; ++pp) {
-      const int m = m0 + 2 * pp;
-      const f32x2 l2 = pp == 0 ? f32x2_pack(l2v.x, l2v.y) : f32x2_pack(l2v.z, l2v.w);
-      const f32x2 l3 = pp == 0 ? f32x2_pack(l3v.x, l3v.y) : f32x2_pack(l3v.z, l3v.w);
-      const bool in0 = row_ok && m < Np, in1 = row_ok && m + 1 < Np;
-      const f32x2 uq = f32x2_pack(in0 ? qe[fu + m] : a1, in1 ? qe[fu + m + 1] : a1);
-      f32x2 ud = f32x2_sub(uq, f32x2_dup(a1));
-      ud = f32x2_sub(ud, f32x2_fma(f32x2_dup(a2 - a1), l2, f32x2_mul(f32x2_dup(a3 - a1), l3)));
-      f32x2 vr = f32x2_mul(f32x2_dup(rc == 1 ? rx : -ry), ud);
-      f32x2 vs = f32x2_mul(f32x2_dup(rc == 1 ? sx : -sy), ud);
-      if (rc == 2) {
-        const f32x2 wq = f32x2_pack(in0 ? qe[E * Np + m] : b1, in1 ? qe[E * Np + m + 1] : b1);
-        f32x2 wd = f32x2_sub(wq, f32x2_dup(b1));
-        wd = f32x2_sub(wd, f32x2_fma(f32x2_dup(b2 - b1), l2, f32x2_mul(f32x2_dup(b3 - b1), l3)));
-        vr = f32x2_fma(f32x2_dup(rx), wd, vr);
-        vs = f32x2_fma(f32x2_dup(sx), wd, vs);
+      for (int pp = 0; pp < 2; ++pp) {
+        const int m = m0 + 2 * pp;
+        const f32x2 l2 = pp == 0 ? f32x2_pack(l2v.x, l2v.y) : f32x2_pack(l2v.z, l2v.w);
+        const f32x2 l3 = pp == 0 ? f32x2_pack(l3v.x, l3v.y) : f32x2_pack(l3v.z, l3v.w);
+        const bool in0 = row_ok && m < Np, in1 = row_ok && m + 1 < Np;
+        const f32x2 uq = f32x2_pack(in0 ? qe[fu + m] : a1, in1 ? qe[fu + m + 1] : a1);
+        f32x2 ud = f32x2_sub(uq, f32x2_dup(a1));
+        ud = f32x2_sub(ud, f32x2_fma(f32x2_dup(a2 - a1), l2, f32x2_mul(f32x2_dup(a3 - a1), l3)));
+        f32x2 vr = f32x2_mul(f32x2_dup(rc == 1 ? rx : -ry), ud);
+        f32x2 vs = f32x2_mul(f32x2_dup(rc == 1 ? sx : -sy), ud);
+        if (rc == 2) {
+          const f32x2 wq = f32x2_pack(in0 ? qe[E * Np + m] : b1, in1 ? qe[E * Np + m + 1] : b1);
+          f32x2 wd = f32x2_sub(wq, f32x2_dup(b1));
+          wd = f32x2_sub(wd, f32x2_fma(f32x2_dup(b2 - b1), l2, f32x2_mul(f32x2_dup(b3 - b1), l3)));
+          vr = f32x2_fma(f32x2_dup(rx), wd, vr);
+          vs = f32x2_fma(f32x2_dup(sx), wd, vs);
+        }
+        const f32x2 hrp = f32x2_tf32_trunc(vr), hsp = f32x2_tf32_trunc(vs);
+        const int i = 4 * v + 2 * pp;
+        f32x2_unpack(hrp, hr[i], hr[i + 1]);
+        f32x2_unpack(hsp, hs[i], hs[i + 1]);
+        f32x2_unpack(f32x2_sub(vr, hrp), lr[i], lr[i + 1]);
+        f32x2_unpack(f32x2_sub(vs, hsp), ls[i], ls[i + 1]);
       }
-      const f32x2 hrp = f32x2_tf32_trunc(vr), hsp = f32x2_tf32_trunc(vs);
-      const int i = 4 * v + 2 * pp;
-      f32x2_unpack(hrp, hr[i], hr[i + 1]);
-      f32x2_unpack(hsp, hs[i], hs[i + 1]);
-      f32x2_unpack(f32x2_sub(vr, hrp), lr[i], lr[i + 1]);
-      f32x2_unpack(f32x2_sub(vs, hsp), ls[i], ls[i + 1]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int m0 = 4 * (R::VLO + v);
+      tmem_st4(xh + m0, *reinterpret_cast<const float(*)[4]>(hr + 4 * v));
+      tmem_st4(xh + NPAD + m0, *reinterpret_cast<const float(*)[4]>(hs + 4 * v));
+      tmem_st4(xl + m0, *reinterpret_cast<const float(*)[4]>(lr + 4 * v));
+      tmem_st4(xl + NPAD + m0, *reinterpret_cast<const float(*)[4]>(ls + 4 * v));
     }
   }
-  // LIFT part: the row's face fluxes, then (column Nafp of the part) the
-  // chain-rule combination of the linear part's exact derivatives, which the
-  // operator tile multiplies by 1 for every node; zero beyond
+}
+
+// LIFT part: the row's face fluxes, then (column Nafp of the part) the
+// chain-rule combination of the linear part's exact derivatives, which the
+// operator tile multiplies by 1 for every node; zero beyond.
+template <int N, class L, int ROLE>
+__device__ __forceinline__ void build_x_lift(const float* fr, uint32_t xh, uint32_t xl,
+                                             bool row_ok, int rc, float rx, float ry, float sx,
+                                             float sy, float a1, float a2, float a3, float b1,
+                                             float b2, float b3) {
+  using R = RowShare<L, ROLE>;
+  constexpr int NPAD = L::NPAD, Nafp = L::Nafp;
+  constexpr int NL = R::LHI - R::LLO;
   if constexpr (NL > 0) {
+    float hl[4 * NL], ll[4 * NL];
     float lin = 0.f;
     if (row_ok) {
       if (rc < 2) {  // a = Ez vertex values
@@ -197,21 +223,13 @@ __device__ __forceinline__ void build_x_share(const float* qe, const float* fr, 
       hl[v] = tf32_trunc(x);
       ll[v] = x - hl[v];
     }
-  }
-  __syncwarp();
+    __syncwarp();
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const int m0 = 4 * (R::VLO + v);
-    tmem_st4(xh + m0, *reinterpret_cast<const float(*)[4]>(hr + 4 * v));
-    tmem_st4(xh + NPAD + m0, *reinterpret_cast<const float(*)[4]>(hs + 4 * v));
-    tmem_st4(xl + m0, *reinterpret_cast<const float(*)[4]>(lr + 4 * v));
-    tmem_st4(xl + NPAD + m0, *reinterpret_cast<const float(*)[4]>(ls + 4 * v));
-  }
-#pragma unroll
-  for (int v = 0; v < NL; ++v) {
-    const int j0 = 4 * (R::LLO + v);
-    tmem_st4(xh + 2 * NPAD + j0, *reinterpret_cast<const float(*)[4]>(hl + 4 * v));
-    tmem_st4(xl + 2 * NPAD + j0, *reinterpret_cast<const float(*)[4]>(ll + 4 * v));
+    for (int v = 0; v < NL; ++v) {
+      const int j0 = 4 * (R::LLO + v);
+      tmem_st4(xh + 2 * NPAD + j0, *reinterpret_cast<const float(*)[4]>(hl + 4 * v));
+      tmem_st4(xl + 2 * NPAD + j0, *reinterpret_cast<const float(*)[4]>(ll + 4 * v));
+    }
   }
 }
 
@@ -221,7 +239,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
   using L = TcLayout<N>;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
   constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FES = L::FES, XBUF = L::XBUF;
-  constexpr int BT = L::BUILD_THREADS, TASKS = L::TASKS, TPT = L::TPT;
+  constexpr int FT = L::FLUX_THREADS, TASKS = L::TASKS, TPT = L::TPT;
   constexpr int NQ = (MODE == kModeStage) ? 6 : 3;
 
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -236,6 +254,8 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 188);
   int* nbr = reinterpret_cast<int*>(smem + 192);      // [6][Nfp] neighbour face-node table
   float* lam = reinterpret_cast<float*>(smem + 384);  // [2][NPAD] vertex-interpolant weights
+  uint64_t* fs_full = reinterpret_cast<uint64_t*>(smem + 704);   // [2] face fluxes written
+  uint64_t* fs_empty = reinterpret_cast<uint64_t*>(smem + 720);  // [2] face fluxes read
   unsigned char* stages = smem + L::OFF_STAGES;
   float* Fs = reinterpret_cast<float*>(smem + L::OFF_F);  // [2][3][E][FES] face fluxes
 
@@ -256,7 +276,9 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&mma_done[b], 1);
       mbar_init(&tmem_free[b], 32 * L::EPI_WARPS);
-      mbar_init(&xfull[b], BT);
+      mbar_init(&xfull[b], L::X_THREADS);
+      mbar_init(&fs_full[b], FT);
+      mbar_init(&fs_empty[b], L::X_THREADS);
     }
     mbar_init(op_bar, 1);
     *abort_flag = 0;
@@ -383,21 +405,18 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
                             static_cast<uint32_t>((mma_pending >> 1) & 1), kWaitLimitNs);
       }
     }
-  } else if (warp >= L::EPI_WARPS) {
-    // ======================= build warps: flux, then the GEMM rows into TMEM
-    const int bt = t - 32 * L::EPI_WARPS;
-    const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. + 31
-    const int role = (warp - L::EPI_WARPS) >> 2;  // share of the row's chunks
-    const int r = 32 * quarter + lane;            // this thread's X row
-    const int rc = r / E, re = r - rc * E;        // its output field and element
-    const uint32_t lane_base = static_cast<uint32_t>(32 * quarter) << 16;
+  } else if (warp >= L::FLUX_WARP0) {
+    // ======================= flux warps: upwind flux at every face node
+    // into the double-buffered face-flux array, up to two blocks ahead of the
+    // operand-row warps; neighbour traces gathered one block ahead
+    const int ft = t - 32 * L::FLUX_WARP0;
     const float* qin[3] = {p.qin, p.qin + fs, p.qin + 2 * fs};
     // flux tasks of this thread (the same in every block): element slot,
     // offsets of its own face node, face code, face geometry and flux slot
     int task_e[TPT], task_jj[TPT], task_nm[TPT], task_cf[TPT], task_gf[TPT], task_fo[TPT];
 #pragma unroll
     for (int u = 0; u < TPT; ++u) {
-      const int tau = bt + u * BT;
+      const int tau = ft + u * FT;
       const int ee = tau / Nafp, j = tau - ee * Nafp, f = j / Nfp, jj = j - f * Nfp;
       task_e[u] = tau < TASKS ? ee : E;
       task_jj[u] = jj;
@@ -431,9 +450,14 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       ok = mbar_wait_or_abort(&full[0], 0, abort_flag);
       if (ok) gather(0);
     }
-    for (int j = 0; j < niter; ++j) {
+    for (int j = 0; ok && j < niter; ++j) {
       const int s = j % S;
-      if (ok) ok = mbar_wait_or_abort(&full[s], static_cast<uint32_t>((j / S) & 1), abort_flag);
+      ok = mbar_wait_or_abort(&full[s], static_cast<uint32_t>((j / S) & 1), abort_flag);
+      // the operand-row warps are done with this flux buffer (block j - 2)
+      if (ok && j >= 2)
+        ok = mbar_wait_or_abort(&fs_empty[j & 1], static_cast<uint32_t>(((j - 2) >> 1) & 1),
+                                abort_flag);
+      if (!ok) break;
       const int k0 = (first + j * G) * E;
       const int nvalid = (K - k0) < E ? (K - k0) : E;
       const unsigned char* st = stages + s * L::STAGE_BYTES;
@@ -441,53 +465,71 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       const float* sg = reinterpret_cast<const float*>(st + 6 * L::QB);
       const int32_t* sc = reinterpret_cast<const int32_t*>(st + 6 * L::QB + L::GB);
       float* Fb = Fs + (j & 1) * (L::FB / 4);
-
       // ---- upwind flux at every face node -> Fb[c][e][j], scaled by Fscale/2
-      if (ok) {
 #pragma unroll
-        for (int u = 0; u < TPT; ++u) {
-          const int ee = task_e[u];
-          if (ee < nvalid) {
-            const int nM = task_nm[u];
-            const float hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
-            float dHx, dHy, dEz;
-            if (sc[task_cf[u]] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
-              dHx = 0.f;
-              dHy = 0.f;
-              dEz = 2.f * ezM;
-            } else {
-              dHx = hxM - trc[u][0];
-              dHy = hyM - trc[u][1];
-              dEz = ezM - trc[u][2];
-            }
-            const float* gf = sg + task_gf[u];
-            const float nx = gf[0], ny = gf[1], fsc = gf[2];
-            const float ndotdH = nx * dHx + ny * dHy;
-            float* fo = Fb + task_fo[u];
-            fo[0] = fsc * (ny * dEz + (ndotdH * nx - dHx));
-            fo[E * FES] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
-            fo[2 * E * FES] = fsc * (ny * dHx - nx * dHy - dEz);
+      for (int u = 0; u < TPT; ++u) {
+        const int ee = task_e[u];
+        if (ee < nvalid) {
+          const int nM = task_nm[u];
+          const float hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
+          float dHx, dHy, dEz;
+          if (sc[task_cf[u]] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
+            dHx = 0.f;
+            dHy = 0.f;
+            dEz = 2.f * ezM;
+          } else {
+            dHx = hxM - trc[u][0];
+            dHy = hyM - trc[u][1];
+            dEz = ezM - trc[u][2];
           }
+          const float* gf = sg + task_gf[u];
+          const float nx = gf[0], ny = gf[1], fsc = gf[2];
+          const float ndotdH = nx * dHx + ny * dHy;
+          float* fo = Fb + task_fo[u];
+          fo[0] = fsc * (ny * dEz + (ndotdH * nx - dHx));
+          fo[E * FES] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
+          fo[2 * E * FES] = fsc * (ny * dHx - nx * dHy - dEz);
         }
       }
-      if (ok && j + 1 < niter) {  // next block's traces, one block ahead
+      mbar_arrive(&fs_full[j & 1]);
+      if (j + 1 < niter) {  // next block's traces, one block ahead
         ok = mbar_wait_or_abort(&full[(j + 1) % S], static_cast<uint32_t>(((j + 1) / S) & 1),
                                 abort_flag);
         if (ok) gather(j + 1);
       }
+    }
+    if (!ok) fail();
+  } else if (warp >= L::EPI_WARPS) {
+    // ======================= operand-row warps: the GEMM rows into TMEM
+    const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. + 31
+    const int role = (warp - L::EPI_WARPS) >> 2;  // share of the row's chunks
+    const int r = 32 * quarter + lane;            // this thread's X row
+    const int rc = r / E, re = r - rc * E;        // its output field and element
+    const uint32_t lane_base = static_cast<uint32_t>(32 * quarter) << 16;
+    bool ok = true;
+    for (int j = 0; j < niter; ++j) {
+      const int s = j % S;
+      ok = ok && mbar_wait_or_abort(&full[s], static_cast<uint32_t>((j / S) & 1), abort_flag);
       // the MMAs that last read this operand buffer are done
       if (ok && j >= XBUF)
         ok = mbar_wait_or_abort(&mma_done[(j - XBUF) & 1],
                                 static_cast<uint32_t>(((j - XBUF) >> 1) & 1), abort_flag);
-      // every flux of this block is in Fb (double-buffered: the next block's
-      // flux goes to the other buffer, and the one after waits for this barrier)
-      if (named_barrier_or(1, BT, !ok)) break;
+      if (!__all_sync(0xffffffffu, ok)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
+      const int k0 = (first + j * G) * E;
+      const int nvalid = (K - k0) < E ? (K - k0) : E;
+      const unsigned char* st = stages + s * L::STAGE_BYTES;
+      const float* sq = reinterpret_cast<const float*>(st);
+      const float* sg = reinterpret_cast<const float*>(st + 6 * L::QB);
+      const float* Fb = Fs + (j & 1) * (L::FB / 4);
 
       // ---- this thread's X row, split into TF32 hi / lo, into tensor memory.
-      // The NR warps of a lane quarter share the row's chunks of 4 columns
-      // evenly: a contiguous range of volume chunks (Dr and Ds parts) and a
-      // contiguous range of LIFT-part chunks, taken from the other end.
+      // The X_WARPS / 4 warps of a lane quarter share the row's chunks of 4
+      // columns evenly: a contiguous range of volume chunks (Dr and Ds parts)
+      // and a contiguous range of LIFT-part chunks, taken from the other end.
       const bool row_ok = r < L::ROWS && re < nvalid;
       const uint32_t xh = tmem + lane_base + static_cast<uint32_t>(L::OFF_XT + (j % XBUF) * L::XCOLS);
       const uint32_t xl = xh + KP;
@@ -514,26 +556,35 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
         }
       }
       const float* fr = Fb + rc * E * FES + re * FES;
-      switch (role) {  // compile-time chunk ranges: the whole share unrolls
+#define DG_BUILD_SHARE(R_)                                                                       \
+  do {                                                                                           \
+    build_x_vol<N, L, R_>(qe, lam, xh, xl, row_ok, rc, rx, ry, sx, sy, a1, a2, a3, b1, b2, b3); \
+    ok = mbar_wait_or_abort(&fs_full[j & 1], static_cast<uint32_t>((j >> 1) & 1), abort_flag);  \
+    if (__all_sync(0xffffffffu, ok))                                                             \
+      build_x_lift<N, L, R_>(fr, xh, xl, row_ok, rc, rx, ry, sx, sy, a1, a2, a3, b1, b2, b3);    \
+    else                                                                                         \
+      ok = false;                                                                                \
+  } while (0)
+      switch (role) {  // compile-time chunk ranges: each share unrolls
         case 0:
-          build_x_share<N, L, 0>(qe, fr, lam, xh, xl, row_ok, rc, rx, ry, sx, sy, a1, a2, a3, b1, b2, b3);
+          DG_BUILD_SHARE(0);
           break;
         case 1:
-          if constexpr (L::BUILD_WARPS / 4 > 1)
-            build_x_share<N, L, 1>(qe, fr, lam, xh, xl, row_ok, rc, rx, ry, sx, sy, a1, a2, a3, b1, b2, b3);
+          if constexpr (L::X_WARPS / 4 > 1) DG_BUILD_SHARE(1);
           break;
         case 2:
-          if constexpr (L::BUILD_WARPS / 4 > 2)
-            build_x_share<N, L, 2>(qe, fr, lam, xh, xl, row_ok, rc, rx, ry, sx, sy, a1, a2, a3, b1, b2, b3);
+          if constexpr (L::X_WARPS / 4 > 2) DG_BUILD_SHARE(2);
           break;
         default:
-          if constexpr (L::BUILD_WARPS / 4 > 3)
-            build_x_share<N, L, 3>(qe, fr, lam, xh, xl, row_ok, rc, rx, ry, sx, sy, a1, a2, a3, b1, b2, b3);
+          if constexpr (L::X_WARPS / 4 > 3) DG_BUILD_SHARE(3);
           break;
       }
+#undef DG_BUILD_SHARE
       tmem_st_wait();
       tc_fence_before();
+      if (!ok) break;
       mbar_arrive(&xfull[j % XBUF]);
+      mbar_arrive(&fs_empty[j & 1]);
     }
     if (!ok) fail();
   } else {
