@@ -609,7 +609,9 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
         tmem_ld16(dacc + c0, va);       // X_hi Op_hi + X_lo Op_hi
         tmem_ld16(dacc + NN + c0, vb);  // X_hi Op_lo
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[c0 + q] = va[q] + vb[q];
+        for (int q = 0; q < 16; q += 2)
+          f32x2_unpack(f32x2_add(f32x2_pack(va[q], va[q + 1]), f32x2_pack(vb[q], vb[q + 1])),
+                       acc[c0 + q], acc[c0 + q + 1]);
       }
       tmem_ld_wait();
       tc_fence_before();
@@ -623,9 +625,40 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       const int c = r / E, e = r - c * E;
       // each thread updates only its own row: no ordering with other rows
       const bool row_ok = r < L::ROWS && e < nvalid;
-      if (row_ok) {
+      if (row_ok && nvalid == E) {
+        // full block: in place in the stage buffer, node pairs in packed
+        // FP32x2 arithmetic (res = a res + dt rhs, q = q + b res)
+        float* rq = sq + c * E * Np + e * Np;
+        float* rr = sres + c * E * Np + e * Np;
+        const f32x2 a2 = f32x2_dup(p.a), b2 = f32x2_dup(p.b), dt2 = f32x2_dup(p.dt);
+#pragma unroll
+        for (int n = 0; n + 1 < Np; n += 2) {
+          if (MODE == kModeRhs) {
+            rq[n] = acc[n];
+            rq[n + 1] = acc[n + 1];
+          } else {
+            f32x2 rn = f32x2_mul(dt2, f32x2_pack(acc[n], acc[n + 1]));
+            if (MODE == kModeStage) rn = f32x2_fma(a2, f32x2_pack(rr[n], rr[n + 1]), rn);
+            const f32x2 qn = f32x2_fma(b2, rn, f32x2_pack(rq[n], rq[n + 1]));
+            f32x2_unpack(qn, rq[n], rq[n + 1]);
+            f32x2_unpack(rn, rr[n], rr[n + 1]);
+          }
+        }
+        if (Np & 1) {
+          constexpr int n = Np - 1;
+          if (MODE == kModeRhs) {
+            rq[n] = acc[n];
+          } else {
+            float rn = p.dt * acc[n];
+            if (MODE == kModeStage) rn = __fmaf_rn(p.a, rr[n], rn);
+            rq[n] = __fmaf_rn(p.b, rn, rq[n]);
+            rr[n] = rn;
+          }
+        }
+      } else if (row_ok) {
+        // ragged last block: straight to global memory
         const int off = c * E * Np + e * Np;
-        const bool full_block = nvalid == E;
+        const bool full_block = false;
         const int64_t g = static_cast<int64_t>(c) * fs + static_cast<int64_t>(k0 + e) * Np;
 #pragma unroll
         for (int n = 0; n < Np; ++n) {
