@@ -33,6 +33,9 @@ UNIT = "element-stage updates/s"
 # the first stage of a step does not read the residual (a_1 = 0).
 STAGE_BYTES = {1: 220, 2: 364, 3: 556, 4: 796, 5: 1084, 6: 1420, 7: 1804}
 
+# element-local products of the FP32-field tensor-core variants
+PRODUCTS = {"fp32": "3xTF32", "tf32": "1xTF32", "bf16": "1xBF16", "bf16x3": "3xBF16"}
+
 
 def rhs_flops_per_element(N):
     Np = (N + 1) * (N + 2) // 2
@@ -281,17 +284,17 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "f64",
+        "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic",
         "config": {
             "workload": "single large mesh: jittered Delaunay unit square n=%d (K=%d), N=%d, "
                         "Gaussian pulse w=0.05, LSRK(5,4) steps" % (args.n, K, N),
             "K": K, "N": N, "Np": s.Np, "precision": args.precision,
             "products": ("CUDA cores" if (args.simt or args.precision == "fp64")
-                         else "tensor cores (tcgen05, 3xTF32)"),
+                         else "tensor cores (tcgen05, %s)" % PRODUCTS[args.precision]),
             "mesh_seed": 2024,
             "l2": "inputs larger than L2 (q, q_tmp, res: %.0f MB)" % (
-                3 * 3 * s.fstride * (4 if args.precision == "fp32" else 8) / 1e6),
+                3 * 3 * s.fstride * (8 if args.precision == "fp64" else 4) / 1e6),
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
         "rhs_gflops": world * K * rhs_flops_per_element(N) * 5 * args.steps / (ms / 1e3) / 1e9,
@@ -310,8 +313,8 @@ def run_ours(args):
         "e2e": {
             "value": replica_throughput(world, K, e2e_steps, e2e_s * 1e3),
             "unit": UNIT,
-            "h2d_bytes_per_step": 3 * s.fstride * (4 if args.precision == "fp32" else 8),
-            "d2h_bytes_per_step": 3 * s.fstride * (4 if args.precision == "fp32" else 8),
+            "h2d_bytes_per_step": 3 * s.fstride * (8 if args.precision == "fp64" else 4),
+            "d2h_bytes_per_step": 3 * s.fstride * (8 if args.precision == "fp64" else 4),
             "steps": e2e_steps,
             "api": "dg_step_host (pinned host buffer -> device, 1 step, device -> host)",
         },
@@ -357,6 +360,54 @@ def run_reference(args):
     }
 
 
+def run_precision_study(args):
+    """Precision path of the element-local contractions: each FP32-field
+    tensor-core variant against an FP64 run of the same solve (jittered
+    unit-square mesh, Gaussian pulse, LSRK(5,4) steps).  One JSON line with
+    max and L2 errors relative to the FP64 run per variant."""
+    import numpy as np
+    import torch
+
+    import paper_1304_5546_gb300 as P
+    from synth import gaussian_pulse, jittered_delaunay_mesh
+
+    torch.cuda.set_device(0)
+    N, n, steps = args.order, args.n, args.study_steps
+
+    mesh = jittered_delaunay_mesh(n, seed=2024)
+    runs = {}
+    for v in ("fp64", "fp32", "bf16x3", "tf32", "bf16"):
+        s = P.Solver(*mesh, N=N, precision=v)
+        x, y = s.nodes()
+        q0 = np.stack(gaussian_pulse(x, y))
+        if v == "fp64":
+            q0 = q0.astype(np.float32).astype(np.float64)  # same start as the FP32 runs
+        q = s.from_numpy(q0)
+        res = s.new_fields()
+        dt = s.cfl_dt()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(q, res, dt, steps)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        P.dg_sync_check(s.op)
+        runs[v] = (s.to_numpy(q), el, s.K)
+        s.close()
+    ref = runs["fp64"][0]
+    scale = np.abs(ref).max()
+    table = {}
+    for v, (qv, el, K) in runs.items():
+        e = qv - ref
+        table[v] = {"max_err": float(np.abs(e).max() / scale),
+                    "l2_err": float(np.sqrt((e ** 2).mean() / (ref ** 2).mean())),
+                    "seconds": el, "element_stage_per_s": K * 5 * steps / el}
+    return {"study": "precision", "N": N, "K": runs["fp64"][2], "steps": steps,
+            "reference": "FP64 run of the same solve (the FP64 path matches the FP64 oracle "
+                         "to 1e-12 in the GPU parity tests)",
+            "errors_relative_to": "max|q| (max_err) and rms(q) (l2_err) of the FP64 run",
+            "variants": table}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,17 +416,27 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--n", type=int, default=707, help="mesh resolution (K = 2 n^2)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32",
+                    choices=["fp32", "fp64", "tf32", "bf16", "bf16x3"],
+                    help="fp32: 3xTF32 tensor-core products; tf32 / bf16 / bf16x3: the "
+                         "precision-path variants (FP32 fields and accumulation)")
     ap.add_argument("--simt", action="store_true", help="FP32 products on CUDA cores")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--_oracle-sample", nargs=3, default=None)
+    ap.add_argument("--study", choices=["precision"], default=None,
+                    help="instead of the benchmark line: the precision-path study "
+                         "(use with --order 7 --n 362 for K = 262,088)")
+    ap.add_argument("--study-steps", type=int, default=500)
     args = ap.parse_args(argv)
     if args._oracle_sample:
         n, N, sec = int(args._oracle_sample[0]), int(args._oracle_sample[1]), float(args._oracle_sample[2])
         v, steps, K, el = oracle_sample_rate(n, N, sec)
         print(json.dumps({"value": v, "steps": steps, "K": K, "seconds": el}))
+        return 0
+    if args.study == "precision":
+        print(json.dumps(run_precision_study(args)), flush=True)
         return 0
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

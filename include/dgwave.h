@@ -79,6 +79,14 @@ typedef int32_t dg_status;
 #define DG_SETUP_HOST_ONLY 1 /* dg_operator_setup flag: skip device upload */
 #define DG_SETUP_SIMT 2      /* FP32: element-local products on the CUDA cores
                                 instead of the tensor cores (3xTF32)         */
+/* FP32 tensor-core product variants (at most one; default: three TF32
+ * products per term, hi/lo split of both operands, FP32 accuracy).  Fields,
+ * accumulation and the LSRK update stay FP32; only the element-local
+ * products (Dr, Ds, LIFT) change precision:                                */
+#define DG_SETUP_TC_TF32 4   /* one product, both operands rounded to TF32   */
+#define DG_SETUP_TC_BF16 8   /* one product, both operands rounded to BF16   */
+#define DG_SETUP_TC_BF16X3 16 /* three BF16 products: hi/lo split of both
+                                 operands (X_hi Op_hi + X_hi Op_lo + X_lo Op_hi) */
 
 #define DG_N_MAX 7
 
@@ -121,13 +129,16 @@ void dg_mesh_destroy(dg_mesh* mesh);
  * Surface Contribution"), and the trace maps.  FP32 operators run the
  * element-local products (Dr, Ds, LIFT) on the tensor cores as three TF32
  * products per term (hi/lo splits of both operands, FP32 accumulation);
- * flags DG_SETUP_SIMT selects the CUDA-core FP32 kernel instead.  FP64
+ * flags DG_SETUP_SIMT selects the CUDA-core FP32 kernel instead, and one
+ * of DG_SETUP_TC_TF32 / _BF16 / _BF16X3 a lower-precision product variant
+ * (the precision path of the element-local contractions).  FP64
  * operators always use the CUDA cores.  Unless flags has
  * DG_SETUP_HOST_ONLY, device-ready copies are uploaded once, cast to the
  * operator's precision (DG_FP32 or DG_FP64), to the current CUDA device.
  * The operator keeps its own copy of the mesh data; the mesh may be
  * destroyed afterwards.
- * Errors: DG_ERR_ARG (also when a field would hold 2^31 or more values:
+ * Errors: DG_ERR_ARG (unknown flags; more than one product variant, or one
+ * with DG_FP64 or DG_SETUP_SIMT; also when a field would hold 2^31 or more values:
  * kernel offsets inside a field are 32-bit), DG_ERR_ORDER (N < 1 or
  * N > DG_N_MAX), DG_ERR_CUDA, DG_ERR_OOM.  *out is written only on success. */
 dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t precision,

@@ -201,18 +201,36 @@ def dg_last_error():
 
 
 # ------------------------------------------------------------ convenience
+# FP32-field variants: name -> dg_operator_setup flags
+_FP32_VARIANTS = {
+    "fp32": 0,                              # 3xTF32 tensor-core products (FP32 accuracy)
+    "fp32simt": _lib.DG_SETUP_SIMT,         # CUDA-core FP32 products
+    "tf32": _lib.DG_SETUP_TC_TF32,          # one TF32 product
+    "bf16": _lib.DG_SETUP_TC_BF16,          # one BF16 product
+    "bf16x3": _lib.DG_SETUP_TC_BF16X3,      # three BF16 products (hi/lo split)
+}
+
+
 class Solver:
     """Owns a mesh + operator pair and the torch tensors that hold fields.
 
     Field tensors have shape (3, field_stride) on the operator's device, in
     the operator's precision; ``view(q)`` gives the (3, K, Np) window.
+    ``precision``: "fp64", or an FP32-field variant: "fp32" (default,
+    tensor cores, 3xTF32), "fp32simt", "tf32", "bf16", "bf16x3".
     """
 
     def __init__(self, VX, VY, EToV, N, precision="fp32", device=None, host_only=False,
                  simt=False):
         import torch
-        if precision == "fp32simt":
-            precision, simt = "fp32", True
+        variant_flags = 0
+        if precision in _FP32_VARIANTS:
+            variant_flags = _FP32_VARIANTS[precision]
+            precision = "fp32"
+        elif precision not in ("fp64", DG_FP64, DG_FP32):
+            raise ValueError("unknown precision %r" % (precision,))
+        if simt:
+            variant_flags |= _lib.DG_SETUP_SIMT
         self.precision = DG_FP32 if precision in ("fp32", DG_FP32) else DG_FP64
         self.dtype = torch.float32 if self.precision == DG_FP32 else torch.float64
         if device is not None and not host_only:
@@ -220,7 +238,7 @@ class Solver:
         self.device = None if host_only else torch.device("cuda", torch.cuda.current_device())
         self.mesh = dg_mesh_create(VX, VY, EToV)
         try:
-            flags = (DG_SETUP_HOST_ONLY if host_only else 0) | (_lib.DG_SETUP_SIMT if simt else 0)
+            flags = (DG_SETUP_HOST_ONLY if host_only else 0) | variant_flags
             self.op = dg_operator_setup(self.mesh, N, self.precision, flags)
         except Exception:
             dg_mesh_destroy(self.mesh)

@@ -25,6 +25,9 @@ DG_FP64 = 0
 DG_FP32 = 1
 DG_SETUP_HOST_ONLY = 1
 DG_SETUP_SIMT = 2
+DG_SETUP_TC_TF32 = 4
+DG_SETUP_TC_BF16 = 8
+DG_SETUP_TC_BF16X3 = 16
 DG_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 DG_N_MAX = 7
 

@@ -27,7 +27,8 @@ def _nvcc():
 
 def sources():
     names = (["host_setup.cpp", "api.cu"] + ["kernels_N%d.cu" % n for n in range(1, 8)]
-             + ["kernels_tc_N%d.cu" % n for n in range(1, 8)])
+             + ["kernels_tc_N%d.cu" % n for n in range(1, 8)]
+             + ["kernels_tcp_N%d.cu" % n for n in range(1, 8)])
     return [os.path.join(CSRC, n) for n in names]
 
 

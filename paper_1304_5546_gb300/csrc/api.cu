@@ -39,8 +39,9 @@ struct dg_op {
   void* d_qtmp = nullptr;  // second field buffer for the stage ping-pong
   int* d_flag = nullptr;   // finiteness scan result
   int* d_status = nullptr; // kernel status word (bounded-wait expiry)
-  float* d_tcop = nullptr; // tensor-core operator tiles (TF32 hi, lo) for FP32
+  void* d_tcop = nullptr;  // tensor-core operator tiles for FP32 (see tc_operator_tiles)
   bool use_tc = false;     // FP32 products on the tensor cores
+  int tc_prec = 0;         // their product variant (dgw::TcPrecision)
   double lsrk_a[5], lsrk_b[5], lsrk_c[5];
   mutable std::atomic<int64_t> launches{0};
 };
@@ -79,20 +80,48 @@ float tf32_round(double v) {
   return f;
 }
 
-// [Dr | Ds | LIFT | 1] as the B operand of the tensor-core kernel: hi and lo TF32
-// parts (v ~ hi + lo, split in FP64), each an nn x kp tile in the core-matrix
-// layout of dgw::tc_canon, parts at the columns dgw::tc_kd describes; rows
-// >= Np and padding columns are zero.
-std::vector<float> tc_operator_tiles(const dgw::RefElement& R) {
+// BF16 value nearest to v (ties to even), as its 16-bit pattern.
+uint16_t bf16_round(double v) {
+  const float f = static_cast<float>(v);
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return static_cast<uint16_t>(u >> 16);
+}
+double bf16_value(uint16_t h) {
+  const uint32_t u = static_cast<uint32_t>(h) << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// [Dr | Ds | LIFT | 1] as the B operand of the tensor-core kernel, in the
+// operand format of product variant `prec`: nsplit tiles (hi, then lo for
+// the split variants, v ~ hi + lo, split in FP64), each nn x kpp elements in
+// the core-matrix layout of dgw::tc_canon (TF32, 4 bytes) or dgw::tc_canon16
+// (BF16, 2 bytes), parts at the columns dgw::tc_kd describes; rows >= Np and
+// padding columns are zero.  Returned as bytes.
+std::vector<unsigned char> tc_operator_tiles(const dgw::RefElement& R, int prec) {
   const int N = R.N, Np = R.Np, Nafp = R.Nafp;
-  const int kp = dgw::tc_kp(N), nn = dgw::tc_nn(N), npad = dgw::tc_npad(N);
-  std::vector<float> out(2 * static_cast<size_t>(nn) * kp, 0.0f);
+  const int kp = dgw::tc_kpp(N, prec), nn = dgw::tc_nn(N), npad = dgw::tc_npad(N);
+  const int ns = dgw::tc_nsplit(prec);
+  const bool bf = dgw::tc_is_bf16(prec);
+  const size_t tile = static_cast<size_t>(nn) * kp;  // elements per tile
+  std::vector<unsigned char> out(ns * tile * (bf ? 2 : 4), 0);
+  float* f32 = reinterpret_cast<float*>(out.data());
+  uint16_t* b16 = reinterpret_cast<uint16_t*>(out.data());
   auto put = [&](int n, int k, double v) {
-    const float hi = tf32_round(v);
-    const float lo = tf32_round(v - static_cast<double>(hi));
-    const int idx = dgw::tc_canon(n, k, kp);
-    out[idx] = hi;
-    out[static_cast<size_t>(nn) * kp + idx] = lo;
+    if (bf) {
+      const int idx = dgw::tc_canon16(n, k, kp);
+      const uint16_t hi = bf16_round(v);
+      b16[idx] = hi;
+      if (ns == 2) b16[tile + idx] = bf16_round(v - bf16_value(hi));
+    } else {
+      const int idx = dgw::tc_canon(n, k, kp);
+      const float hi = tf32_round(v);
+      f32[idx] = hi;
+      if (ns == 2) f32[tile + idx] = tf32_round(v - static_cast<double>(hi));
+    }
   };
   for (int n = 0; n < Np; ++n) {
     for (int m = 0; m < Np; ++m) {
@@ -159,11 +188,10 @@ dg_status upload(dg_op* op) {
   err = cudaMalloc(&op->d_flag, sizeof(int));
   if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(flag)");
   if (op->use_tc) {
-    const std::vector<float> tiles = tc_operator_tiles(op->ref);
-    err = cudaMalloc(&op->d_tcop, tiles.size() * sizeof(float));
+    const std::vector<unsigned char> tiles = tc_operator_tiles(op->ref, op->tc_prec);
+    err = cudaMalloc(&op->d_tcop, tiles.size());
     if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(operator tiles)");
-    err = cudaMemcpy(op->d_tcop, tiles.data(), tiles.size() * sizeof(float),
-                     cudaMemcpyHostToDevice);
+    err = cudaMemcpy(op->d_tcop, tiles.data(), tiles.size(), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMemcpy(operator tiles)");
   }
   err = cudaMalloc(&op->d_status, sizeof(int));
@@ -175,16 +203,28 @@ dg_status upload(dg_op* op) {
   return DG_OK;
 }
 
+template <int N>
+cudaError_t launch_prec_tc(const dg_op* op, const dgw::StageArgs<float>& a, int mode,
+                           cudaStream_t s) {
+  switch (op->tc_prec) {
+    case dgw::kTcTf32x3: return dgw::launch_stage_tc<N, dgw::kTcTf32x3>(a, mode, op->num_sms, s);
+    case dgw::kTcTf32: return dgw::launch_stage_tc<N, dgw::kTcTf32>(a, mode, op->num_sms, s);
+    case dgw::kTcBf16: return dgw::launch_stage_tc<N, dgw::kTcBf16>(a, mode, op->num_sms, s);
+    case dgw::kTcBf16x3: return dgw::launch_stage_tc<N, dgw::kTcBf16x3>(a, mode, op->num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_order_tc(const dg_op* op, const dgw::StageArgs<float>& a, int mode,
                             cudaStream_t s) {
   switch (op->N) {
-    case 1: return dgw::launch_stage_tc<1>(a, mode, op->num_sms, s);
-    case 2: return dgw::launch_stage_tc<2>(a, mode, op->num_sms, s);
-    case 3: return dgw::launch_stage_tc<3>(a, mode, op->num_sms, s);
-    case 4: return dgw::launch_stage_tc<4>(a, mode, op->num_sms, s);
-    case 5: return dgw::launch_stage_tc<5>(a, mode, op->num_sms, s);
-    case 6: return dgw::launch_stage_tc<6>(a, mode, op->num_sms, s);
-    case 7: return dgw::launch_stage_tc<7>(a, mode, op->num_sms, s);
+    case 1: return launch_prec_tc<1>(op, a, mode, s);
+    case 2: return launch_prec_tc<2>(op, a, mode, s);
+    case 3: return launch_prec_tc<3>(op, a, mode, s);
+    case 4: return launch_prec_tc<4>(op, a, mode, s);
+    case 5: return launch_prec_tc<5>(op, a, mode, s);
+    case 6: return launch_prec_tc<6>(op, a, mode, s);
+    case 7: return launch_prec_tc<7>(op, a, mode, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -297,6 +337,14 @@ extern "C" dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t p
     return fail(DG_ERR_ORDER, "dg_operator_setup: N = %d outside 1..%d", N, DG_N_MAX);
   if (precision != DG_FP32 && precision != DG_FP64)
     return fail(DG_ERR_ARG, "dg_operator_setup: unknown precision %d", precision);
+  const int32_t known = DG_SETUP_HOST_ONLY | DG_SETUP_SIMT | DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 |
+                        DG_SETUP_TC_BF16X3;
+  const int32_t variants = flags & (DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 | DG_SETUP_TC_BF16X3);
+  if (flags & ~known) return fail(DG_ERR_ARG, "dg_operator_setup: unknown flags 0x%x", flags);
+  if (variants && ((variants & (variants - 1)) || precision != DG_FP32 || (flags & DG_SETUP_SIMT)))
+    return fail(DG_ERR_ARG,
+                "dg_operator_setup: at most one tensor-core product variant, FP32 only, not with "
+                "DG_SETUP_SIMT");
   dg_op* op = nullptr;
   try {
     op = new dg_op;
@@ -308,6 +356,10 @@ extern "C" dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t p
     op->precision = precision;
     op->flags = flags;
     op->use_tc = (precision == DG_FP32) && !(flags & DG_SETUP_SIMT);
+    op->tc_prec = (flags & DG_SETUP_TC_TF32)    ? dgw::kTcTf32
+                  : (flags & DG_SETUP_TC_BF16)  ? dgw::kTcBf16
+                  : (flags & DG_SETUP_TC_BF16X3) ? dgw::kTcBf16x3
+                                                 : dgw::kTcTf32x3;
     op->elem_size = (precision == DG_FP32) ? 4 : 8;
     op->K = mesh->K;
     op->Kpad = (mesh->K + 1 + kBlockPad - 1) / kBlockPad * kBlockPad;

@@ -53,23 +53,30 @@
 
 namespace dgw {
 
-template <int N>
+template <int N, int PREC_>
 struct TcLayout {
+  static constexpr int PREC = PREC_;
+  static constexpr bool BF = tc_is_bf16(PREC);  // BF16 operands (else TF32)
+  static constexpr int NS = tc_nsplit(PREC);     // X parts and operator tiles (hi, lo)
   static constexpr int Np = Order<N>::Np;
   static constexpr int Nfp = Order<N>::Nfp;
   static constexpr int Nafp = Order<N>::Nafp;
   static constexpr int E = (N == 7) ? 24 : 40;  // 3E <= 128 GEMM rows, E % 4 == 0
   static constexpr int ROWS = 3 * E;
-  static constexpr int KD = tc_kd(N), KP = tc_kp(N), KG = KP / 4;
+  static constexpr int KD = tc_kd(N), KP = tc_kpp(N, PREC);
+  static constexpr int EB = BF ? 2 : 4;         // operand element bytes
+  static constexpr int KG = KP * EB / 16;       // core matrices along K
+  static constexpr int XPART = BF ? KP / 2 : KP;  // TMEM columns of one X part
   static constexpr int NN = tc_nn(N);
   static constexpr int NPAD = tc_npad(N);
   static constexpr int IV = NPAD / 4;          // volume chunks of 4 nodes
   static constexpr int LCOLS = KP - 2 * NPAD;  // LIFT-part columns (zero beyond Nafp)
-  // tensor memory: two accumulators of 2 NN columns (columns [0, NN) hold
-  // X_hi Op_hi + X_lo Op_hi, columns [NN, 2 NN) hold X_hi Op_lo), then XBUF
-  // operand buffers of 2 KP columns (X_hi, then X_lo)
-  static constexpr int ACC_COLS = 2 * NN;
-  static constexpr int XCOLS = 2 * KP;
+  // tensor memory: two accumulators, then XBUF operand buffers of NS parts.
+  // Split variants: an accumulator has 2 NN columns, [0, NN) holding
+  // X_hi Op_hi + X_lo Op_hi and [NN, 2 NN) holding X_hi Op_lo; an operand
+  // buffer holds X_hi, then X_lo.  Single-product variants: NN columns, X.
+  static constexpr int ACC_COLS = NS == 2 ? 2 * NN : NN;
+  static constexpr int XCOLS = NS * XPART;
   static constexpr int XBUF = (2 * ACC_COLS + 2 * XCOLS <= 512) ? 2 : 1;
   static constexpr int OFF_XT = 2 * ACC_COLS;
   static constexpr int TMEM_COLS = 512;
@@ -89,10 +96,10 @@ struct TcLayout {
   static constexpr int GB = E * kGeo * 4;
   static constexpr int CB = E * 3 * 4;
   static constexpr int STAGE_BYTES = round_up(6 * QB + GB + CB, 128);
-  static constexpr int OB = NN * KP * 4;  // one operator tile (hi or lo)
+  static constexpr int OB = NN * KP * EB;  // one operator tile
   static constexpr int HEADER = 1024;
   static constexpr int OFF_OP = HEADER;
-  static constexpr int OFF_F = OFF_OP + 2 * OB;
+  static constexpr int OFF_F = OFF_OP + NS * OB;
   static constexpr int OFF_STAGES = round_up(OFF_F + 2 * FB, 128);
   static constexpr int SMAX = 232448;
   static constexpr int S_FIT = (SMAX - OFF_STAGES) / STAGE_BYTES;
@@ -104,7 +111,7 @@ struct TcLayout {
   static_assert(S >= 2 && S <= 8, "stage ring / header layout");
   static_assert(SMEM_BYTES <= SMAX, "shared memory");
   static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0 && OB % 16 == 0, "TMA chunks");
-  static_assert(ROWS <= 128 && NN <= 256 && NN % 16 == 0 && KP % 8 == 0, "UMMA shape");
+  static_assert(ROWS <= 128 && NN <= 256 && NN % 16 == 0 && KP % (BF ? 16 : 8) == 0, "UMMA shape");
   static_assert(LCOLS % 4 == 0 && LCOLS >= Nafp + 1, "LIFT part and linear-part column");
   static_assert(2 * ACC_COLS + XBUF * XCOLS <= TMEM_COLS, "tensor memory");
   static_assert(X_WARPS % 4 == 0, "operand-row warps come in lane-quarter groups");
@@ -121,14 +128,47 @@ struct RowShare {
   static constexpr int LLO = (NR - 1 - ROLE) * LC / NR, LHI = (NR - ROLE) * LC / NR;
 };
 
-// One thread's share of its X row (hi and lo TF32 parts) into tensor memory
-// at xh / xl (this warp's lane quarter), in two calls: the volume part, then
-// the LIFT part (which waits for the face fluxes).  Each call computes every
-// value first and then issues its tcgen05.st, so the loads of all its chunks
-// can be in flight at once.  rc: output field of the row; qe: the element's
-// fields in the stage buffer; fr: the row's face fluxes; (a1, a2, a3) /
-// (b1, b2, b3): vertex values of u (Ez for rc < 2, Hx for rc = 2) / of w (Hy,
-// rc = 2).
+// Four consecutive K columns (k0, a multiple of 4) of this thread's X row
+// into tensor memory at xh (and xl for the split variants), in the operand
+// format of the launch's product variant:
+//   kTcTf32x3  hi = top 11 significand bits (TF32), lo = the exact rest
+//   kTcTf32    rounded to the nearest TF32
+//   kTcBf16    rounded to the nearest BF16, two per column
+//   kTcBf16x3  hi = nearest BF16, lo = nearest BF16 of the rest
+template <class L>
+__device__ __forceinline__ void x_emit4(uint32_t xh, uint32_t xl, int k0, float v0, float v1,
+                                        float v2, float v3) {
+  if constexpr (L::PREC == kTcTf32x3) {
+    const f32x2 p0 = f32x2_pack(v0, v1), p1 = f32x2_pack(v2, v3);
+    const f32x2 h0 = f32x2_tf32_trunc(p0), h1 = f32x2_tf32_trunc(p1);
+    float h[4], l[4];
+    f32x2_unpack(h0, h[0], h[1]);
+    f32x2_unpack(h1, h[2], h[3]);
+    f32x2_unpack(f32x2_sub(p0, h0), l[0], l[1]);
+    f32x2_unpack(f32x2_sub(p1, h1), l[2], l[3]);
+    tmem_st4(xh + k0, h);
+    tmem_st4(xl + k0, l);
+  } else if constexpr (L::PREC == kTcTf32) {
+    const float h[4] = {tf32_rna(v0), tf32_rna(v1), tf32_rna(v2), tf32_rna(v3)};
+    tmem_st4(xh + k0, h);
+  } else if constexpr (L::PREC == kTcBf16) {
+    tmem_st2(xh + k0 / 2, bf16x2_rn(v0, v1), bf16x2_rn(v2, v3));
+  } else {
+    const uint32_t h01 = bf16x2_rn(v0, v1), h23 = bf16x2_rn(v2, v3);
+    const uint32_t l01 = bf16x2_rn(v0 - bf16_lo_f32(h01), v1 - bf16_hi_f32(h01));
+    const uint32_t l23 = bf16x2_rn(v2 - bf16_lo_f32(h23), v3 - bf16_hi_f32(h23));
+    tmem_st2(xh + k0 / 2, h01, h23);
+    tmem_st2(xl + k0 / 2, l01, l23);
+  }
+}
+
+// One thread's share of its X row into tensor memory at xh / xl (this warp's
+// lane quarter), in two calls: the volume part, then the LIFT part (which
+// waits for the face fluxes).  Each call computes every value first and then
+// converts and stores them (x_emit4), so the loads of all its chunks can be
+// in flight at once.  rc: output field of the row; qe: the element's fields
+// in the stage buffer; fr: the row's face fluxes; (a1, a2, a3) / (b1, b2,
+// b3): vertex values of u (Ez for rc < 2, Hx for rc = 2) / of w (Hy, rc = 2).
 //
 // Volume part: nodes 4ch .. 4ch+3 in pairs (packed FP32x2): deflated u (and
 // w), then the Dr part cr1 u + cr2 w and the Ds part cs1 u + cs2 w with
@@ -145,7 +185,7 @@ __device__ __forceinline__ void build_x_vol(const float* qe, const float* lam, u
   constexpr int Np = L::Np, E = L::E, NPAD = L::NPAD;
   constexpr int NV = R::VHI - R::VLO;
   if constexpr (NV > 0) {
-    float hr[4 * NV], lr[4 * NV], hs[4 * NV], ls[4 * NV];
+    float vr[4 * NV], vs[4 * NV];
     const int fu = rc < 2 ? 2 * E * Np : 0;  // field u in the stage buffer
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -161,31 +201,26 @@ __device__ __forceinline__ void build_x_vol(const float* qe, const float* lam, u
         const f32x2 uq = f32x2_pack(in0 ? qe[fu + m] : a1, in1 ? qe[fu + m + 1] : a1);
         f32x2 ud = f32x2_sub(uq, f32x2_dup(a1));
         ud = f32x2_sub(ud, f32x2_fma(f32x2_dup(a2 - a1), l2, f32x2_mul(f32x2_dup(a3 - a1), l3)));
-        f32x2 vr = f32x2_mul(f32x2_dup(rc == 1 ? rx : -ry), ud);
-        f32x2 vs = f32x2_mul(f32x2_dup(rc == 1 ? sx : -sy), ud);
+        f32x2 pr = f32x2_mul(f32x2_dup(rc == 1 ? rx : -ry), ud);
+        f32x2 ps = f32x2_mul(f32x2_dup(rc == 1 ? sx : -sy), ud);
         if (rc == 2) {
           const f32x2 wq = f32x2_pack(in0 ? qe[E * Np + m] : b1, in1 ? qe[E * Np + m + 1] : b1);
           f32x2 wd = f32x2_sub(wq, f32x2_dup(b1));
           wd = f32x2_sub(wd, f32x2_fma(f32x2_dup(b2 - b1), l2, f32x2_mul(f32x2_dup(b3 - b1), l3)));
-          vr = f32x2_fma(f32x2_dup(rx), wd, vr);
-          vs = f32x2_fma(f32x2_dup(sx), wd, vs);
+          pr = f32x2_fma(f32x2_dup(rx), wd, pr);
+          ps = f32x2_fma(f32x2_dup(sx), wd, ps);
         }
-        const f32x2 hrp = f32x2_tf32_trunc(vr), hsp = f32x2_tf32_trunc(vs);
         const int i = 4 * v + 2 * pp;
-        f32x2_unpack(hrp, hr[i], hr[i + 1]);
-        f32x2_unpack(hsp, hs[i], hs[i + 1]);
-        f32x2_unpack(f32x2_sub(vr, hrp), lr[i], lr[i + 1]);
-        f32x2_unpack(f32x2_sub(vs, hsp), ls[i], ls[i + 1]);
+        f32x2_unpack(pr, vr[i], vr[i + 1]);
+        f32x2_unpack(ps, vs[i], vs[i + 1]);
       }
     }
     __syncwarp();
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const int m0 = 4 * (R::VLO + v);
-      tmem_st4(xh + m0, *reinterpret_cast<const float(*)[4]>(hr + 4 * v));
-      tmem_st4(xh + NPAD + m0, *reinterpret_cast<const float(*)[4]>(hs + 4 * v));
-      tmem_st4(xl + m0, *reinterpret_cast<const float(*)[4]>(lr + 4 * v));
-      tmem_st4(xl + NPAD + m0, *reinterpret_cast<const float(*)[4]>(ls + 4 * v));
+      x_emit4<L>(xh, xl, m0, vr[4 * v], vr[4 * v + 1], vr[4 * v + 2], vr[4 * v + 3]);
+      x_emit4<L>(xh, xl, NPAD + m0, vs[4 * v], vs[4 * v + 1], vs[4 * v + 2], vs[4 * v + 3]);
     }
   }
 }
@@ -202,7 +237,7 @@ __device__ __forceinline__ void build_x_lift(const float* fr, uint32_t xh, uint3
   constexpr int NPAD = L::NPAD, Nafp = L::Nafp;
   constexpr int NL = R::LHI - R::LLO;
   if constexpr (NL > 0) {
-    float hl[4 * NL], ll[4 * NL];
+    float x[4 * NL];
     float lin = 0.f;
     if (row_ok) {
       if (rc < 2) {  // a = Ez vertex values
@@ -215,28 +250,24 @@ __device__ __forceinline__ void build_x_lift(const float* fr, uint32_t xh, uint3
 #pragma unroll
     for (int v = 0; v < 4 * NL; ++v) {
       const int jj = 4 * R::LLO + v;
-      float x = 0.f;
+      x[v] = 0.f;
       if (jj < Nafp)
-        x = row_ok ? fr[jj] : 0.f;
+        x[v] = row_ok ? fr[jj] : 0.f;
       else if (jj == Nafp)
-        x = lin;
-      hl[v] = tf32_trunc(x);
-      ll[v] = x - hl[v];
+        x[v] = lin;
     }
     __syncwarp();
 #pragma unroll
-    for (int v = 0; v < NL; ++v) {
-      const int j0 = 4 * (R::LLO + v);
-      tmem_st4(xh + 2 * NPAD + j0, *reinterpret_cast<const float(*)[4]>(hl + 4 * v));
-      tmem_st4(xl + 2 * NPAD + j0, *reinterpret_cast<const float(*)[4]>(ll + 4 * v));
-    }
+    for (int v = 0; v < NL; ++v)
+      x_emit4<L>(xh, xl, 2 * NPAD + 4 * (R::LLO + v), x[4 * v], x[4 * v + 1], x[4 * v + 2],
+                 x[4 * v + 3]);
   }
 }
 
-template <int N, int MODE>
-__global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
+template <int N, int MODE, int PREC>
+__global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
     dg_stage_tc_kernel(const StageArgs<float> p) {
-  using L = TcLayout<N>;
+  using L = TcLayout<N, PREC>;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
   constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FES = L::FES, XBUF = L::XBUF;
   constexpr int FT = L::FLUX_THREADS, TASKS = L::TASKS, TPT = L::TPT;
@@ -329,8 +360,8 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
         tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * kGeo, gb, &full[s]);
         tma_load_1d(st + 6 * L::QB + L::GB, p.conn + static_cast<int64_t>(k0) * 3, cb, &full[s]);
       };
-      mbar_expect_tx(op_bar, 2 * L::OB);
-      tma_load_1d(smem + L::OFF_OP, p.tc_op, 2 * L::OB, op_bar);
+      mbar_expect_tx(op_bar, L::NS * L::OB);
+      tma_load_1d(smem + L::OFF_OP, p.tc_op, L::NS * L::OB, op_bar);
       for (; issued < niter && issued < S; ++issued) issue(issued);
       bool ok = true;
       // outputs of block jj leave by bulk stores; its stage is then refilled
@@ -375,8 +406,17 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       bool ok = mbar_wait_or_abort(op_bar, 0, abort_flag);
       const uint32_t oaddr = smem_u32(smem + L::OFF_OP);
       constexpr uint32_t LBO = 128, SBO = L::KG * 128;
-      constexpr uint32_t IDESC2 = umma_idesc_tf32(128, 2 * NN);  // B = [Op_hi ; Op_lo]
-      constexpr uint32_t IDESC1 = umma_idesc_tf32(128, NN);      // B = Op_hi
+      constexpr int KS = KP / (L::BF ? 16 : 8);  // MMA K steps (8 TMEM columns each)
+      constexpr uint32_t IDESC2 =                // B = [Op_hi ; Op_lo]
+          L::BF ? umma_idesc_bf16(128, 2 * NN) : umma_idesc_tf32(128, 2 * NN);
+      constexpr uint32_t IDESC1 = L::BF ? umma_idesc_bf16(128, NN) : umma_idesc_tf32(128, NN);
+      auto mma = [&](uint32_t d, uint32_t a, int ks, uint32_t idesc, uint32_t acc) {
+        const uint64_t bd = umma_desc(oaddr + ks * 256, LBO, SBO);
+        if constexpr (L::BF)
+          umma_bf16_ta(d, a, bd, idesc, acc);
+        else
+          umma_tf32_ta(d, a, bd, idesc, acc);
+      };
       int mma_pending = -1;  // block whose MMA group may still run
       for (int j = 0; ok && j < niter; ++j) {
         const int xb = j % XBUF;
@@ -388,13 +428,18 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
         tc_fence_after();
         const uint32_t dacc = tmem + static_cast<uint32_t>((j & 1) * L::ACC_COLS);
         const uint32_t xh = tmem + static_cast<uint32_t>(L::OFF_XT + xb * L::XCOLS);
+        if constexpr (L::NS == 2) {
 #pragma unroll
-        for (int ks = 0; ks < KP / 8; ++ks)  // X_hi [Op_hi ; Op_lo] -> columns [0, 2 NN)
-          umma_tf32_ta(dacc, xh + 8 * ks, umma_desc(oaddr + ks * 256, LBO, SBO), IDESC2,
-                       ks > 0 ? 1u : 0u);
+          for (int ks = 0; ks < KS; ++ks)  // X_hi [Op_hi ; Op_lo] -> columns [0, 2 NN)
+            mma(dacc, xh + 8 * ks, ks, IDESC2, ks > 0 ? 1u : 0u);
 #pragma unroll
-        for (int ks = 0; ks < KP / 8; ++ks)  // + X_lo Op_hi -> columns [0, NN)
-          umma_tf32_ta(dacc, xh + KP + 8 * ks, umma_desc(oaddr + ks * 256, LBO, SBO), IDESC1, 1u);
+          for (int ks = 0; ks < KS; ++ks)  // + X_lo Op_hi -> columns [0, NN)
+            mma(dacc, xh + L::XPART + 8 * ks, ks, IDESC1, 1u);
+        } else {
+#pragma unroll
+          for (int ks = 0; ks < KS; ++ks)  // X Op -> columns [0, NN)
+            mma(dacc, xh + 8 * ks, ks, IDESC1, ks > 0 ? 1u : 0u);
+        }
         umma_commit(&mma_done[j & 1]);
         mma_pending = j;
       }
@@ -532,7 +577,7 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
       // and a contiguous range of LIFT-part chunks, taken from the other end.
       const bool row_ok = r < L::ROWS && re < nvalid;
       const uint32_t xh = tmem + lane_base + static_cast<uint32_t>(L::OFF_XT + (j % XBUF) * L::XCOLS);
-      const uint32_t xl = xh + KP;
+      const uint32_t xl = xh + L::XPART;
       const float* qe = sq + re * Np;
       float rx = 0.f, ry = 0.f, sx = 0.f, sy = 0.f;
       float a1 = 0.f, a2 = 0.f, a3 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;  // vertex values
@@ -605,13 +650,20 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
                             (static_cast<uint32_t>(32 * warp) << 16);
 #pragma unroll
       for (int c0 = 0; c0 < NN; c0 += 16) {
-        float va[16], vb[16];
-        tmem_ld16(dacc + c0, va);       // X_hi Op_hi + X_lo Op_hi
-        tmem_ld16(dacc + NN + c0, vb);  // X_hi Op_lo
+        if constexpr (L::NS == 2) {
+          float va[16], vb[16];
+          tmem_ld16(dacc + c0, va);       // X_hi Op_hi + X_lo Op_hi
+          tmem_ld16(dacc + NN + c0, vb);  // X_hi Op_lo
 #pragma unroll
-        for (int q = 0; q < 16; q += 2)
-          f32x2_unpack(f32x2_add(f32x2_pack(va[q], va[q + 1]), f32x2_pack(vb[q], vb[q + 1])),
-                       acc[c0 + q], acc[c0 + q + 1]);
+          for (int q = 0; q < 16; q += 2)
+            f32x2_unpack(f32x2_add(f32x2_pack(va[q], va[q + 1]), f32x2_pack(vb[q], vb[q + 1])),
+                         acc[c0 + q], acc[c0 + q + 1]);
+        } else {
+          float va[16];
+          tmem_ld16(dacc + c0, va);  // X Op
+#pragma unroll
+          for (int q = 0; q < 16; ++q) acc[c0 + q] = va[q];
+        }
       }
       tmem_ld_wait();
       tc_fence_before();
@@ -694,12 +746,12 @@ __global__ void __launch_bounds__(TcLayout<N>::THREADS, 1)
   if (warp == 0) tmem_dealloc(tmem, L::TMEM_COLS);
 }
 
-template <int N, int MODE>
+template <int N, int MODE, int PREC>
 cudaError_t launch_stage_tc_mode(const StageArgs<float>& args, int num_sms, cudaStream_t stream) {
-  using L = TcLayout<N>;
+  using L = TcLayout<N, PREC>;
   static bool configured = false;
   if (!configured) {
-    cudaError_t err = cudaFuncSetAttribute(dg_stage_tc_kernel<N, MODE>,
+    cudaError_t err = cudaFuncSetAttribute(dg_stage_tc_kernel<N, MODE, PREC>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(L::SMEM_BYTES));
     if (err != cudaSuccess) return err;
@@ -709,17 +761,18 @@ cudaError_t launch_stage_tc_mode(const StageArgs<float>& args, int num_sms, cuda
   int64_t grid = num_sms;  // one CTA per SM (shared memory and TMEM sized for it)
   if (grid > nblk) grid = nblk;
   if (grid < 1) grid = 1;
-  dg_stage_tc_kernel<N, MODE>
+  dg_stage_tc_kernel<N, MODE, PREC>
       <<<static_cast<unsigned>(grid), L::THREADS, L::SMEM_BYTES, stream>>>(args);
   return cudaGetLastError();
 }
 
-template <int N>
+template <int N, int PREC>
 cudaError_t launch_stage_tc(const StageArgs<float>& args, int mode, int num_sms,
                             cudaStream_t stream) {
-  if (mode == kModeRhs) return launch_stage_tc_mode<N, kModeRhs>(args, num_sms, stream);
-  if (mode == kModeFirstStage) return launch_stage_tc_mode<N, kModeFirstStage>(args, num_sms, stream);
-  return launch_stage_tc_mode<N, kModeStage>(args, num_sms, stream);
+  if (mode == kModeRhs) return launch_stage_tc_mode<N, kModeRhs, PREC>(args, num_sms, stream);
+  if (mode == kModeFirstStage)
+    return launch_stage_tc_mode<N, kModeFirstStage, PREC>(args, num_sms, stream);
+  return launch_stage_tc_mode<N, kModeStage, PREC>(args, num_sms, stream);
 }
 
 }  // namespace dgw

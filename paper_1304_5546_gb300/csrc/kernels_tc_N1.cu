@@ -1,6 +1,6 @@
-// Order-1 instantiation of the FP32 tensor-core stage kernel.
+// Order-1 instantiation of the FP32 tensor-core stage kernel, 3xTF32 products.
 #include "kernels_tc.cuh"
 
 namespace dgw {
-template cudaError_t launch_stage_tc<1>(const StageArgs<float>&, int, int, cudaStream_t);
+template cudaError_t launch_stage_tc<1, kTcTf32x3>(const StageArgs<float>&, int, int, cudaStream_t);
 }  // namespace dgw

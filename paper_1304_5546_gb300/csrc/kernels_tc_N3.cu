@@ -1,6 +1,6 @@
-// Order-3 instantiation of the FP32 tensor-core stage kernel.
+// Order-3 instantiation of the FP32 tensor-core stage kernel, 3xTF32 products.
 #include "kernels_tc.cuh"
 
 namespace dgw {
-template cudaError_t launch_stage_tc<3>(const StageArgs<float>&, int, int, cudaStream_t);
+template cudaError_t launch_stage_tc<3, kTcTf32x3>(const StageArgs<float>&, int, int, cudaStream_t);
 }  // namespace dgw

@@ -27,9 +27,11 @@ struct StageArgs {
   const T* lam = nullptr;         // [2][Np]: (1 + r_n) / 2, (1 + s_n) / 2 per node
   T a = 0, b = 0, dt = 0;
   int* status = nullptr;  // set to 1 by a CTA whose bounded wait expired
-  // tensor-core path only: [Dr | Ds | LIFT] as TF32 hi and lo parts, each an
-  // tc_nn(N) x tc_kp(N) tile in the core-matrix layout of tc_canon
-  const float* tc_op = nullptr;
+  // tensor-core path only: [Dr | Ds | LIFT | 1] as the operator tiles of the
+  // launch's product variant (tc_nsplit tiles of tc_nn(N) x tc_kpp(N, prec)
+  // elements, TF32 or BF16, in the core-matrix layout of tc_canon /
+  // tc_canon16)
+  const void* tc_op = nullptr;
 };
 
 enum StageMode : int { kModeRhs = 0, kModeFirstStage = 1, kModeStage = 2 };
@@ -39,15 +41,15 @@ enum StageMode : int { kModeRhs = 0, kModeFirstStage = 1, kModeStage = 2 };
 template <typename T, int N>
 cudaError_t launch_stage(const StageArgs<T>& args, int mode, int num_sms, cudaStream_t stream);
 
-// Tensor-core path (FP32 fields, 3xTF32 products; see kernels_tc.cuh).  The
+// Tensor-core path (FP32 fields, FP32 accumulation; see kernels_tc.cuh).  The
 // element-local products of a block of elements form one GEMM
 //   D[3E x Np] = X[3E x KD] [Dr | Ds | LIFT | 1]^T
 // whose K columns are laid out part by part, each part starting on a
 // 16-byte boundary: Dr columns at [0, NPAD), Ds at [NPAD, 2 NPAD), LIFT at
 // [2 NPAD, 2 NPAD + Nafp) with NPAD = Np rounded up to 4, then one column
 // (2 NPAD + Nafp) whose operator entries are 1 for every node and whose X
-// entry is the row's linear-part term; K is padded to tc_kp(N) (multiple
-// of 8) and N to tc_nn(N) (multiple of 16).
+// entry is the row's linear-part term; K is padded to tc_kpp(N, prec) (one
+// MMA step: 8 TF32 or 16 BF16 elements) and N to tc_nn(N) (multiple of 16).
 __host__ __device__ constexpr int tc_np(int N) { return (N + 1) * (N + 2) / 2; }
 __host__ __device__ constexpr int tc_npad(int N) { return (tc_np(N) + 3) / 4 * 4; }
 __host__ __device__ constexpr int tc_kd(int N) { return 2 * tc_npad(N) + 3 * (N + 1) + 1; }
@@ -60,8 +62,30 @@ __host__ __device__ constexpr int tc_nn(int N) { return (tc_np(N) + 15) / 16 * 1
 __host__ __device__ constexpr int tc_canon(int n, int k, int kp) {
   return ((n / 8) * (kp / 4) + k / 4) * 32 + (n % 8) * 4 + (k % 4);
 }
+// The same for 16-bit elements (8 per 16-byte core-matrix row); index in
+// 16-bit units.
+__host__ __device__ constexpr int tc_canon16(int n, int k, int kp) {
+  return ((n / 8) * (kp / 8) + k / 8) * 64 + (n % 8) * 8 + (k % 8);
+}
 
-template <int N>
+// Product variants of the tensor-core path.  FP32 fields and accumulation
+// in every variant; they differ in the operand types and the number of
+// products per term:
+//   kTcTf32x3  X_hi Op_hi + X_hi Op_lo + X_lo Op_hi in TF32 (FP32 accuracy)
+//   kTcTf32    X Op with both operands rounded to TF32
+//   kTcBf16    X Op with both operands rounded to BF16
+//   kTcBf16x3  X_hi Op_hi + X_hi Op_lo + X_lo Op_hi in BF16
+enum TcPrecision : int { kTcTf32x3 = 0, kTcTf32 = 1, kTcBf16 = 2, kTcBf16x3 = 3 };
+__host__ __device__ constexpr bool tc_is_bf16(int prec) { return prec == kTcBf16 || prec == kTcBf16x3; }
+__host__ __device__ constexpr int tc_nsplit(int prec) {
+  return (prec == kTcTf32x3 || prec == kTcBf16x3) ? 2 : 1;
+}
+// K padded to whole MMA steps: 8 TF32 or 16 BF16 elements
+__host__ __device__ constexpr int tc_kpp(int N, int prec) {
+  return tc_is_bf16(prec) ? (tc_kd(N) + 15) / 16 * 16 : tc_kp(N);
+}
+
+template <int N, int PREC>
 cudaError_t launch_stage_tc(const StageArgs<float>& args, int mode, int num_sms,
                             cudaStream_t stream);
 

@@ -193,6 +193,20 @@ __device__ __forceinline__ void umma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, u
       "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// Instruction descriptor: kind::f16 with BF16 A and B (K-major), D in FP32.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+// D(tmem) (+)= A(tmem) * B(desc)^T with BF16 operands (two per A column)
+__device__ __forceinline__ void umma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc,
+                                             uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // arrive on `bar` when every tcgen05.mma issued so far by this thread is done
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile(
@@ -219,6 +233,12 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, const float (&v)[4]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
                "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
                "r"(__float_as_uint(v[3]))
+               : "memory");
+}
+// 2 consecutive 32-bit columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t v0, uint32_t v1) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(v0),
+               "r"(v1)
                : "memory");
 }
 // this thread's tcgen05.st are complete
@@ -263,6 +283,17 @@ __device__ __forceinline__ f32x2 f32x2_sub(f32x2 a, f32x2 b) {
 }
 // both halves truncated to TF32 (low 13 significand bits cleared)
 __device__ __forceinline__ f32x2 f32x2_tf32_trunc(f32x2 a) { return a & 0xFFFFE000FFFFE000ull; }
+
+// Two FP32 values rounded to nearest-even BF16 and packed, `lo` in the low
+// half (the lower K index of an operand), `hi` in the high half.
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+// the BF16 halves of a packed pair as FP32 (exact)
+__device__ __forceinline__ float bf16_lo_f32(uint32_t p) { return __uint_as_float(p << 16); }
+__device__ __forceinline__ float bf16_hi_f32(uint32_t p) { return __uint_as_float(p & 0xFFFF0000u); }
 
 // TF32 value with the top 11 significand bits of x (low 13 bits cleared)
 __device__ __forceinline__ float tf32_trunc(float x) {
