@@ -506,6 +506,59 @@ def maxwell_rhs(d, q, alpha=1.0, flux=True):
     return np.stack([rhsHx, rhsHy, rhsEz])
 
 
+def maxwell_rhs_media(d, q, eps):
+    """Right-hand side with a piecewise-constant permittivity eps[k] per
+    element (mu = 1), the variable-coefficient form of Eq. tm-maxwells:
+    dHx/dt = -dEz/dy, dHy/dt = dEz/dx, eps dEz/dt = dHy/dx - dHx/dy.
+
+    Upwind flux from the exact Riemann solution along the face normal.
+    With Ht = ny Hx - nx Hy the normal system is dHt/dt + dEz/dxi = 0,
+    eps dEz/dt + dHt/dxi = 0, impedance Z = 1/sqrt(eps); the interface
+    state follows from the outgoing characteristic of each side, and with
+    jumps [u] = u- - u+ the flux differences n.(F- - F*) are
+        Ez:        (Z+ [Ht] - [Ez]) / (Z- + Z+)
+        (Hx, Hy):  (ny, -nx) Z- ([Ez] - Z+ [Ht]) / (Z- + Z+)
+    (the normal H component has no flux).  PEC faces: Ez+ = -Ez-, H+ = H-,
+    Z+ = Z-.  Then rhs = vol + LIFT (Fscale * n.(F - F*)), and the Ez row
+    is divided by eps[k].  With eps = 1 this is maxwell_rhs with alpha = 1
+    (there the flux carries the factor 1/2 as (Z- + Z+) = 2).
+    """
+    R = d.ref
+    eps = np.asarray(eps, dtype=np.float64).reshape(d.K)
+    Z = 1.0 / np.sqrt(eps)
+    vol = maxwell_rhs(d, q, flux=False)
+    Hx, Hy, Ez = q[0], q[1], q[2]
+    vM = d.vmapM.reshape(-1)
+    vP = d.vmapP.reshape(-1)
+    jHx = Hx.reshape(-1)[vM] - Hx.reshape(-1)[vP]
+    jHy = Hy.reshape(-1)[vM] - Hy.reshape(-1)[vP]
+    jEz = Ez.reshape(-1)[vM] - Ez.reshape(-1)[vP]
+    ZM = np.repeat(Z, d.Nafp)                # interior side of every face node
+    ZP = Z[vP // d.Np]                       # the neighbour's element
+    jHx[d.mapB] = 0.0
+    jHy[d.mapB] = 0.0
+    jEz[d.mapB] = 2.0 * Ez.reshape(-1)[d.vmapB]
+    ZP[d.mapB] = ZM[d.mapB]
+    nx, ny = d.nx.reshape(-1), d.ny.reshape(-1)
+    jHt = ny * jHx - nx * jHy
+    fEz = (ZP * jHt - jEz) / (ZM + ZP)
+    g = ZM * (jEz - ZP * jHt) / (ZM + ZP)
+    shape = (d.K, d.Nafp)
+    Fs = d.Fscale
+    rhsHx = vol[0] + (Fs * (ny * g).reshape(shape)) @ R.LIFT.T
+    rhsHy = vol[1] + (Fs * (-nx * g).reshape(shape)) @ R.LIFT.T
+    rhsEz = (vol[2] + (Fs * fEz.reshape(shape)) @ R.LIFT.T) / eps[:, None]
+    return np.stack([rhsHx, rhsHy, rhsEz])
+
+
+def energy_media(d, q, eps):
+    """1/2 sum_k J_k (Hx^T M Hx + Hy^T M Hy + eps_k Ez^T M Ez)."""
+    M = d.ref.M
+    Jk = d.J[:, 0]
+    w = [Jk, Jk, Jk * np.asarray(eps, dtype=np.float64).reshape(d.K)]
+    return 0.5 * sum(np.sum(w[f] * np.einsum("kn,nm,km->k", q[f], M, q[f])) for f in range(3))
+
+
 # ---------------------------------------------------------------------------
 # LSRK(5,4): Carpenter & Kennedy (1994), five-stage fourth-order, 2N storage
 # ---------------------------------------------------------------------------
