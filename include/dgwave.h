@@ -60,6 +60,7 @@ extern "C" {
 
 typedef struct dg_mesh dg_mesh;
 typedef struct dg_op dg_op;
+typedef struct dg_batch dg_batch;
 typedef int32_t dg_status;
 
 #define DG_OK 0
@@ -143,6 +144,28 @@ void dg_mesh_destroy(dg_mesh* mesh);
  * N > DG_N_MAX), DG_ERR_CUDA, DG_ERR_OOM.  *out is written only on success. */
 dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t precision,
                             int32_t flags, dg_op** out);
+
+/* dg_operator_setup_media: dg_operator_setup for a medium with a
+ * piecewise-constant permittivity, eps[k] > 0 on element k (host, K
+ * doubles, copied), and mu = 1: the variable-coefficient form of Eq.
+ * tm-maxwells, eps dEz/dt = dHy/dx - dHx/dy (the H equations unchanged).
+ * The paper treats eps = mu = 1 only; the flux at an interface between
+ * different media is the upwind flux of the exact Riemann solution along the
+ * face normal (impedance Z = 1/sqrt(eps), Z- own, Z+ the neighbour's; at a
+ * PEC face Z+ = Z-).  With jumps [u] = u- - u+ and [Ht] = ny [Hx] - nx [Hy]:
+ *     n.(F - F*) for Ez      = (Z+ [Ht] - [Ez]) / (Z- + Z+)
+ *     n.(F - F*) for (Hx,Hy) = (ny, -nx) Z- ([Ez] - Z+ [Ht]) / (Z- + Z+)
+ * lifted with Fscale (no extra 1/2), and the Ez right-hand side divided by
+ * eps[k].  For eps = 1 this equals the right-hand side of dg_operator_setup
+ * up to rounding.  dg_cfl_dt uses min over elements of inradius *
+ * sqrt(eps[k]) (the wave speed is 1/sqrt(eps)).  The hot-path calls and
+ * their conventions are those of any operator.
+ * Errors: those of dg_operator_setup; DG_ERR_ARG when eps is NULL or an
+ * entry is not a positive finite number, or with the lower-precision
+ * product variants (DG_SETUP_TC_*), which have no per-element-permittivity
+ * kernel.                                                                  */
+dg_status dg_operator_setup_media(const dg_mesh* mesh, int32_t N, const double* eps,
+                                  int32_t precision, int32_t flags, dg_op** out);
 
 /* Np, Nfp = N+1, K and field_stride (see conventions).  NULL outputs are
  * skipped.                                                                 */
@@ -258,6 +281,104 @@ dg_status dg_step_host(const dg_op* op, void* h_q, void* d_q, void* d_res, doubl
  * DG_ERR_CUDA if the address lookup fails.                                 */
 dg_status dg_step_static(const dg_op* op, void* d_q, void* d_res, double t0, double dt,
                          int32_t nsteps, void* stream);
+
+/* ------------------------------------------------------------ batches ---
+ * A batch steps many independent problems of mixed orders together: each
+ * LSRK stage of every problem in the batch is ONE persistent launch (all
+ * orders at once; the launch's CTAs are split among the orders), and a step
+ * (five stages) is replayed from a captured CUDA graph.  Problems join and
+ * leave between steps (continuous batching); each keeps its own time step.
+ * Computation: FP32 fields, tensor-core 3xTF32 products, the per-element
+ * permittivity flux of dg_operator_setup_media (eps = 1 for operators set
+ * up without one).  The paper has no batches: this is the element-blocked,
+ * many-problem form of its right-hand side and time stepping.
+ *
+ * Memory: one pool per order with the element capacity given at creation
+ * (about 36 Np + 92 bytes per element of capacity: two field buffers, the
+ * residual, geometry records, face codes), allocated by dg_batch_create and
+ * freed by dg_batch_destroy.  A problem occupies K elements (rounded up to a
+ * multiple of 4) of its order's pool.
+ * Fields: the batch owns them.  Problem i's fields are copied in and out
+ * with dg_batch_set_fields / dg_batch_get_fields, in the layout of a single
+ * operator (field f, element k, node n at f * stride + k * Np + n) with a
+ * stride the caller chooses.                                               */
+#define DG_BATCH_NO_GRAPH 1 /* dg_batch_create flag: launch the five stage
+                               kernels directly instead of replaying graphs */
+
+/* dg_batch_create: capacity[N-1] = elements of order N the batch can hold
+ * (N = 1..DG_N_MAX, 0 = none), on the current device.
+ * Errors: DG_ERR_ARG (NULL, unknown flags, capacities all zero or one
+ * >= 2^27 or too large for 32-bit field offsets), DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_batch** out);
+
+/* Waits for the device, then frees the batch and its device memory.      */
+void dg_batch_destroy(dg_batch* batch);
+
+/* dg_batch_add: admit the problem of operator `op` (DG_FP32; set up on any
+ * device or host-only: the batch copies what it needs from the operator's
+ * host data, and the operator may be destroyed afterwards) with time step
+ * dt (<= 0: the operator's dg_cfl_dt with cfl = 1).  Its geometry is
+ * uploaded asynchronously on `stream`.  Its fields are unspecified until
+ * dg_batch_set_fields; it is stepped by every later dg_batch_step.  Writes
+ * the problem's slot number.
+ * Errors: DG_ERR_ARG (NULL, not DG_FP32, no capacity for its order),
+ * DG_ERR_OOM (no free range of its size in the pool), DG_ERR_CUDA.        */
+dg_status dg_batch_add(dg_batch* batch, const dg_op* op, double dt, void* stream, int32_t* slot);
+
+/* dg_batch_remove: the problem in `slot` leaves the batch; its range of the
+ * pool and its slot number become free.  Copy its fields out first.       */
+dg_status dg_batch_remove(dg_batch* batch, int32_t slot);
+
+/* Order, K, time step and pool field stride of the problem in `slot`.     */
+dg_status dg_batch_info(const dg_batch* batch, int32_t slot, int32_t* N, int64_t* K, double* dt,
+                        int64_t* field_stride);
+
+/* Copy the problem's three fields in (set) or out (get): src / dst hold
+ * field f, element k, node n at f * stride + k * Np + n (float), stride >=
+ * K * Np, in host (pageable or pinned) or device memory.  Enqueued on
+ * `stream`, ordered with dg_batch_step calls on the same stream.          */
+dg_status dg_batch_set_fields(dg_batch* batch, int32_t slot, const void* src, int64_t src_stride,
+                              void* stream);
+dg_status dg_batch_get_fields(dg_batch* batch, int32_t slot, void* dst, int64_t dst_stride,
+                              void* stream);
+
+/* dg_batch_step: nsteps LSRK(5,4) steps of every problem in the batch, each
+ * with its own dt; per stage one launch over all problems.  The first call
+ * after a problem joined or left uploads the block tables and CTA split
+ * (asynchronously on `stream`).  Calls on one batch must be ordered (one
+ * stream, or the caller's synchronisation).
+ * Errors: DG_ERR_ARG (nsteps < 0; more orders present than SMs),
+ * DG_ERR_OOM, DG_ERR_CUDA.                                                 */
+dg_status dg_batch_step(dg_batch* batch, int32_t nsteps, void* stream);
+
+/* dg_batch_tune: the autotuner.  Times `reps` stage launches of each order
+ * alone on all SMs (cost of one block iteration per CTA), plans the CTA
+ * split from those costs, then tries moving single CTAs between orders and
+ * keeps every move that measures at least 0.5 % faster.  Synchronises
+ * `stream`; leaves the fields unchanged.  Later joins and leaves re-plan with
+ * the measured costs.                                                      */
+dg_status dg_batch_tune(dg_batch* batch, int32_t reps, void* stream);
+
+/* The current plan: CTAs and blocks per order (index N-1) and the per-block
+ * cost the planner used (seconds after dg_batch_tune; before it, the bytes
+ * a block moves).  NULL outputs are skipped.                               */
+dg_status dg_batch_plan(const dg_batch* batch, int32_t* cta, int64_t* nblocks, double* cost);
+
+/* The planner on its own (host only): CTAs per order for block counts
+ * nblocks[7] and per-block costs cost[7] on num_ctas CTAs.  Every order with
+ * blocks gets one CTA; each further CTA goes to the order with the largest
+ * ceil(nblocks / cta) * cost that has fewer CTAs than blocks.
+ * Errors: DG_ERR_ARG (NULL, num_ctas < 1, more orders with blocks than
+ * CTAs).                                                                   */
+dg_status dg_batch_plan_ctas(const int64_t* nblocks, const double* cost, int32_t num_ctas,
+                             int32_t* cta);
+
+/* Synchronises `stream`, reports pending CUDA errors and the kernels'
+ * status word (DG_ERR_TIMEOUT after an expired bounded wait).             */
+dg_status dg_batch_sync_check(dg_batch* batch, void* stream);
+
+/* Stage launches enqueued by the batch (five per step).                   */
+int64_t dg_batch_launch_count(const dg_batch* batch);
 
 /* dg_check_finite: synchronises `stream`, then scans the first K*Np values
  * of each field of d_q for NaN/Inf.  Returns DG_ERR_NONFINITE if any is

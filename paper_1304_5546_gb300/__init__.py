@@ -23,11 +23,14 @@ from ._lib import (  # noqa: F401
 
 __all__ = [
     "dg_mesh_create", "dg_mesh_info", "dg_mesh_connectivity", "dg_mesh_destroy",
-    "dg_operator_setup", "dg_get_info", "dg_get_nodes", "dg_get_reference",
+    "dg_operator_setup", "dg_operator_setup_media", "dg_get_info", "dg_get_nodes", "dg_get_reference",
     "dg_get_geometry", "dg_get_maps", "dg_cfl_dt", "dg_lsrk_coefficients",
     "dg_op_destroy", "dg_rhs", "dg_step", "dg_step_static", "dg_solve", "dg_step_host",
     "dg_check_finite", "dg_sync_check", "dg_launch_count", "dg_last_error",
-    "Solver", "DGError", "DG_FP32", "DG_FP64",
+    "dg_batch_create", "dg_batch_destroy", "dg_batch_add", "dg_batch_remove", "dg_batch_info",
+    "dg_batch_set_fields", "dg_batch_get_fields", "dg_batch_step", "dg_batch_tune",
+    "dg_batch_plan", "dg_batch_plan_ctas", "dg_batch_sync_check", "dg_batch_launch_count",
+    "Solver", "Batch", "DGError", "DG_FP32", "DG_FP64",
 ]
 
 
@@ -86,6 +89,14 @@ def dg_operator_setup(mesh, N, precision=DG_FP32, flags=0):
     h = ctypes.c_void_p()
     _lib.check(_lib.load().dg_operator_setup(mesh, N, precision, flags, ctypes.byref(h)),
                "dg_operator_setup")
+    return h.value
+
+
+def dg_operator_setup_media(mesh, N, eps, precision=DG_FP32, flags=0):
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _lib.check(_lib.load().dg_operator_setup_media(mesh, N, _ptr(e), precision, flags,
+                                                   ctypes.byref(h)), "dg_operator_setup_media")
     return h.value
 
 
@@ -200,6 +211,88 @@ def dg_last_error():
     return m.decode() if m else ""
 
 
+# --------------------------------------------------------------- batches
+def dg_batch_create(capacity, flags=0):
+    """capacity: 7 element counts (orders 1..7)."""
+    c = np.ascontiguousarray(capacity, dtype=np.int64)
+    if c.size != DG_N_MAX:
+        raise ValueError("capacity needs %d entries" % DG_N_MAX)
+    h = ctypes.c_void_p()
+    _lib.check(_lib.load().dg_batch_create(_ptr(c), flags, ctypes.byref(h)), "dg_batch_create")
+    return h.value
+
+
+def dg_batch_destroy(batch):
+    if batch:
+        _lib.load().dg_batch_destroy(batch)
+
+
+def dg_batch_add(batch, op, dt=0.0, stream=None):
+    slot = ctypes.c_int32()
+    _lib.check(_lib.load().dg_batch_add(batch, op, dt, _stream_handle(stream), ctypes.byref(slot)),
+               "dg_batch_add")
+    return slot.value
+
+
+def dg_batch_remove(batch, slot):
+    _lib.check(_lib.load().dg_batch_remove(batch, slot), "dg_batch_remove")
+
+
+def dg_batch_info(batch, slot):
+    N, K, dt, fs = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+    _lib.check(_lib.load().dg_batch_info(batch, slot, ctypes.byref(N), ctypes.byref(K),
+                                         ctypes.byref(dt), ctypes.byref(fs)), "dg_batch_info")
+    return N.value, K.value, dt.value, fs.value
+
+
+def _buf_ptr(a):
+    return ctypes.c_void_p(a.data_ptr()) if hasattr(a, "data_ptr") else _ptr(a)
+
+
+def dg_batch_set_fields(batch, slot, src, stride, stream=None):
+    """src: float32 host array / tensor or device tensor; field f at f * stride."""
+    _lib.check(_lib.load().dg_batch_set_fields(batch, slot, _buf_ptr(src), stride,
+                                               _stream_handle(stream)), "dg_batch_set_fields")
+
+
+def dg_batch_get_fields(batch, slot, dst, stride, stream=None):
+    _lib.check(_lib.load().dg_batch_get_fields(batch, slot, _buf_ptr(dst), stride,
+                                               _stream_handle(stream)), "dg_batch_get_fields")
+
+
+def dg_batch_step(batch, nsteps, stream=None):
+    _lib.check(_lib.load().dg_batch_step(batch, nsteps, _stream_handle(stream)), "dg_batch_step")
+
+
+def dg_batch_tune(batch, reps=5, stream=None):
+    _lib.check(_lib.load().dg_batch_tune(batch, reps, _stream_handle(stream)), "dg_batch_tune")
+
+
+def dg_batch_plan(batch):
+    cta = np.zeros(DG_N_MAX, np.int32)
+    nb = np.zeros(DG_N_MAX, np.int64)
+    cost = np.zeros(DG_N_MAX, np.float64)
+    _lib.check(_lib.load().dg_batch_plan(batch, _ptr(cta), _ptr(nb), _ptr(cost)), "dg_batch_plan")
+    return cta, nb, cost
+
+
+def dg_batch_plan_ctas(nblocks, cost, num_ctas):
+    nb = np.ascontiguousarray(nblocks, dtype=np.int64)
+    c = np.ascontiguousarray(cost, dtype=np.float64)
+    out = np.zeros(DG_N_MAX, np.int32)
+    _lib.check(_lib.load().dg_batch_plan_ctas(_ptr(nb), _ptr(c), num_ctas, _ptr(out)),
+               "dg_batch_plan_ctas")
+    return out
+
+
+def dg_batch_sync_check(batch, stream=None):
+    _lib.check(_lib.load().dg_batch_sync_check(batch, _stream_handle(stream)), "dg_batch_sync_check")
+
+
+def dg_batch_launch_count(batch):
+    return int(_lib.load().dg_batch_launch_count(batch))
+
+
 # ------------------------------------------------------------ convenience
 # FP32-field variants: name -> dg_operator_setup flags
 _FP32_VARIANTS = {
@@ -218,10 +311,11 @@ class Solver:
     the operator's precision; ``view(q)`` gives the (3, K, Np) window.
     ``precision``: "fp64", or an FP32-field variant: "fp32" (default,
     tensor cores, 3xTF32), "fp32simt", "tf32", "bf16", "bf16x3".
+    ``eps``: per-element permittivity (K values; dg_operator_setup_media).
     """
 
     def __init__(self, VX, VY, EToV, N, precision="fp32", device=None, host_only=False,
-                 simt=False):
+                 simt=False, eps=None):
         import torch
         variant_flags = 0
         if precision in _FP32_VARIANTS:
@@ -239,7 +333,10 @@ class Solver:
         self.mesh = dg_mesh_create(VX, VY, EToV)
         try:
             flags = (DG_SETUP_HOST_ONLY if host_only else 0) | variant_flags
-            self.op = dg_operator_setup(self.mesh, N, self.precision, flags)
+            if eps is None:
+                self.op = dg_operator_setup(self.mesh, N, self.precision, flags)
+            else:
+                self.op = dg_operator_setup_media(self.mesh, N, eps, self.precision, flags)
         except Exception:
             dg_mesh_destroy(self.mesh)
             raise
@@ -293,3 +390,73 @@ class Solver:
 
     def nodes(self):
         return dg_get_nodes(self.op)
+
+
+class Batch:
+    """Many problems of mixed orders stepped together (dg_batch_*).
+
+    ``capacity``: dict order -> element capacity, or 7 counts.  ``add``
+    admits a Solver's operator (FP32) with its time step; fields move in and
+    out as (3, K, Np) arrays.
+    """
+
+    def __init__(self, capacity, graph=True, device=None):
+        import torch
+        if device is not None:
+            torch.cuda.set_device(device)
+        if isinstance(capacity, dict):
+            cap = [0] * DG_N_MAX
+            for n, c in capacity.items():
+                cap[n - 1] = int(c)
+            capacity = cap
+        self.batch = dg_batch_create(capacity, 0 if graph else _lib.DG_BATCH_NO_GRAPH)
+
+    def close(self):
+        dg_batch_destroy(getattr(self, "batch", None))
+        self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, solver_or_op, dt=0.0, stream=None):
+        op = solver_or_op.op if hasattr(solver_or_op, "op") else solver_or_op
+        return dg_batch_add(self.batch, op, dt, stream)
+
+    def remove(self, slot):
+        dg_batch_remove(self.batch, slot)
+
+    def info(self, slot):
+        return dg_batch_info(self.batch, slot)
+
+    def set_fields(self, slot, q3, stream=None):
+        import torch
+        q = np.ascontiguousarray(q3, dtype=np.float32)
+        dg_batch_set_fields(self.batch, slot, q, q[0].size, stream)
+        (stream or torch.cuda.current_stream()).synchronize()  # q is pageable and local
+
+    def get_fields(self, slot, stream=None):
+        import torch
+        N, K, _, _ = self.info(slot)
+        Np = (N + 1) * (N + 2) // 2
+        out = np.empty((3, K, Np), np.float32)
+        dg_batch_get_fields(self.batch, slot, out, K * Np, stream)
+        (stream or torch.cuda.current_stream()).synchronize()
+        return out
+
+    def step(self, nsteps=1, stream=None):
+        dg_batch_step(self.batch, nsteps, stream)
+
+    def tune(self, reps=5, stream=None):
+        dg_batch_tune(self.batch, reps, stream)
+
+    def plan(self):
+        return dg_batch_plan(self.batch)
+
+    def sync_check(self, stream=None):
+        dg_batch_sync_check(self.batch, stream)
+
+    def launch_count(self):
+        return dg_batch_launch_count(self.batch)

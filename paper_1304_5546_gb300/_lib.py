@@ -29,6 +29,7 @@ DG_SETUP_TC_TF32 = 4
 DG_SETUP_TC_BF16 = 8
 DG_SETUP_TC_BF16X3 = 16
 DG_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
+DG_BATCH_NO_GRAPH = 1
 DG_N_MAX = 7
 
 _STATUS_NAMES = {
@@ -50,6 +51,7 @@ SIGNATURES = [
     ("dg_mesh_connectivity", c_i32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("dg_mesh_destroy", None, [c_void_p]),
     ("dg_operator_setup", c_i32, [c_void_p, c_i32, c_i32, c_i32, P(c_void_p)]),
+    ("dg_operator_setup_media", c_i32, [c_void_p, c_i32, c_void_p, c_i32, c_i32, P(c_void_p)]),
     ("dg_get_info", c_i32, [c_void_p, P(c_i32), P(c_i32), P(c_i64), P(c_i64)]),
     ("dg_get_nodes", c_i32, [c_void_p, c_void_p, c_void_p]),
     ("dg_get_reference", c_i32, [c_void_p] + [c_void_p] * 6),
@@ -66,6 +68,19 @@ SIGNATURES = [
     ("dg_check_finite", c_i32, [c_void_p, c_void_p, c_void_p]),
     ("dg_sync_check", c_i32, [c_void_p, c_void_p]),
     ("dg_launch_count", c_i64, [c_void_p]),
+    ("dg_batch_create", c_i32, [c_void_p, c_i32, P(c_void_p)]),
+    ("dg_batch_destroy", None, [c_void_p]),
+    ("dg_batch_add", c_i32, [c_void_p, c_void_p, c_dbl, c_void_p, P(c_i32)]),
+    ("dg_batch_remove", c_i32, [c_void_p, c_i32]),
+    ("dg_batch_info", c_i32, [c_void_p, c_i32, P(c_i32), P(c_i64), P(c_dbl), P(c_i64)]),
+    ("dg_batch_set_fields", c_i32, [c_void_p, c_i32, c_void_p, c_i64, c_void_p]),
+    ("dg_batch_get_fields", c_i32, [c_void_p, c_i32, c_void_p, c_i64, c_void_p]),
+    ("dg_batch_step", c_i32, [c_void_p, c_i32, c_void_p]),
+    ("dg_batch_tune", c_i32, [c_void_p, c_i32, c_void_p]),
+    ("dg_batch_plan", c_i32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("dg_batch_plan_ctas", c_i32, [c_void_p, c_void_p, c_i32, c_void_p]),
+    ("dg_batch_sync_check", c_i32, [c_void_p, c_void_p]),
+    ("dg_batch_launch_count", c_i64, [c_void_p]),
     ("dg_last_error", ctypes.c_char_p, []),
 ]
 

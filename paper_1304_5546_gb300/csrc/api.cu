@@ -19,33 +19,6 @@ const char* last_error_cstr();
 
 using dgw::fail;
 
-struct dg_op {
-  int N = 0, Np = 0, Nfp = 0, Nafp = 0;
-  int precision = DG_FP32;
-  int flags = 0;
-  int64_t K = 0, Kpad = 0, fstride = 0;
-  size_t elem_size = 4;
-  dgw::RefElement ref;
-  dgw::Geometry geo;
-  bool has_device = false;
-  int device = 0;
-  int num_sms = 0;
-  void* d_Dr = nullptr;
-  void* d_Ds = nullptr;
-  void* d_LIFT = nullptr;
-  void* d_lam = nullptr;   // vertex-interpolant weights per node
-  void* d_geo = nullptr;
-  void* d_conn = nullptr;
-  void* d_qtmp = nullptr;  // second field buffer for the stage ping-pong
-  int* d_flag = nullptr;   // finiteness scan result
-  int* d_status = nullptr; // kernel status word (bounded-wait expiry)
-  void* d_tcop = nullptr;  // tensor-core operator tiles for FP32 (see tc_operator_tiles)
-  bool use_tc = false;     // FP32 products on the tensor cores
-  int tc_prec = 0;         // their product variant (dgw::TcPrecision)
-  double lsrk_a[5], lsrk_b[5], lsrk_c[5];
-  mutable std::atomic<int64_t> launches{0};
-};
-
 namespace {
 
 // K is padded to whole blocks of <= 64 elements plus at least one spare
@@ -95,6 +68,10 @@ double bf16_value(uint16_t h) {
   return f;
 }
 
+}  // namespace
+
+namespace dgw {
+
 // [Dr | Ds | LIFT | 1] as the B operand of the tensor-core kernel, in the
 // operand format of product variant `prec`: nsplit tiles (hi, then lo for
 // the split variants, v ~ hi + lo, split in FP64), each nn x kpp elements in
@@ -134,6 +111,39 @@ std::vector<unsigned char> tc_operator_tiles(const dgw::RefElement& R, int prec)
   return out;
 }
 
+void media_records(const dg_op& op, double sh, std::vector<double>& out) {
+  const int64_t K = op.K;
+  constexpr int R = kGeoMedia;
+  out.assign(static_cast<size_t>(K) * R, 0.0);
+  auto eps_of = [&](int64_t k) { return op.media() ? op.eps[k] : 1.0; };
+  for (int64_t k = 0; k < K; ++k) {
+    double* g = &out[k * R];
+    g[0] = op.geo.rx[k];
+    g[1] = op.geo.ry[k];
+    g[2] = op.geo.sx[k];
+    g[3] = op.geo.sy[k];
+    const double zM = 1.0 / std::sqrt(eps_of(k));
+    for (int f = 0; f < 3; ++f) {
+      const int32_t code = op.geo.conn[3 * k + f];
+      const double zP = code < 0 ? zM : 1.0 / std::sqrt(eps_of(code >> 3));
+      const double fsc = op.geo.Fscale[3 * k + f];
+      g[4 + 4 * f] = op.geo.nx[3 * k + f];
+      g[5 + 4 * f] = op.geo.ny[3 * k + f];
+      g[6 + 4 * f] = fsc * zP / (zM + zP);
+      g[7 + 4 * f] = fsc / (zM + zP);
+    }
+    g[16] = zM;
+    g[17] = sh;
+    g[18] = sh / eps_of(k);
+  }
+}
+
+}  // namespace dgw
+
+namespace {
+
+using dgw::tc_operator_tiles;
+
 template <typename T>
 dg_status upload(dg_op* op) {
   const int Np = op->Np, Nafp = op->Nafp;
@@ -148,10 +158,18 @@ dg_status upload(dg_op* op) {
     lam[n] = static_cast<T>(0.5 * (1.0 + op->ref.r[n]));
     lam[Np + n] = static_cast<T>(0.5 * (1.0 + op->ref.s[n]));
   }
-  std::vector<T> geo(static_cast<size_t>(Kpad) * dgw::kGeo, T(0));
+  const int rec = op->media() ? dgw::kGeoMedia : dgw::kGeo;
+  std::vector<T> geo(static_cast<size_t>(Kpad) * rec, T(0));
   std::vector<int32_t> conn(static_cast<size_t>(Kpad) * 3, -1);
+  if (op->media()) {
+    std::vector<double> m;
+    dgw::media_records(*op, 1.0, m);
+    for (size_t i = 0; i < m.size(); ++i) geo[i] = static_cast<T>(m[i]);
+  }
   for (int64_t k = 0; k < K; ++k) {
-    T* g = &geo[k * dgw::kGeo];
+    T* g = &geo[k * rec];
+    for (int f = 0; f < 3; ++f) conn[3 * k + f] = op->geo.conn[3 * k + f];
+    if (op->media()) continue;
     g[0] = static_cast<T>(op->geo.rx[k]);
     g[1] = static_cast<T>(op->geo.ry[k]);
     g[2] = static_cast<T>(op->geo.sx[k]);
@@ -160,7 +178,6 @@ dg_status upload(dg_op* op) {
       g[4 + 3 * f] = static_cast<T>(op->geo.nx[3 * k + f]);
       g[5 + 3 * f] = static_cast<T>(op->geo.ny[3 * k + f]);
       g[6 + 3 * f] = static_cast<T>(0.5 * op->geo.Fscale[3 * k + f]);
-      conn[3 * k + f] = op->geo.conn[3 * k + f];
     }
   }
   struct Up {
@@ -229,8 +246,41 @@ cudaError_t launch_order_tc(const dg_op* op, const dgw::StageArgs<float>& a, int
   }
 }
 
+cudaError_t launch_order_tc_media(const dg_op* op, const dgw::StageArgs<float>& a, int mode,
+                                  cudaStream_t s) {
+  switch (op->N) {
+    case 1: return dgw::launch_stage_tc_media<1>(a, mode, op->num_sms, s);
+    case 2: return dgw::launch_stage_tc_media<2>(a, mode, op->num_sms, s);
+    case 3: return dgw::launch_stage_tc_media<3>(a, mode, op->num_sms, s);
+    case 4: return dgw::launch_stage_tc_media<4>(a, mode, op->num_sms, s);
+    case 5: return dgw::launch_stage_tc_media<5>(a, mode, op->num_sms, s);
+    case 6: return dgw::launch_stage_tc_media<6>(a, mode, op->num_sms, s);
+    case 7: return dgw::launch_stage_tc_media<7>(a, mode, op->num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t launch_order_media(const dg_op* op, const dgw::StageArgs<T>& a, int mode,
+                               cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (op->use_tc) return launch_order_tc_media(op, a, mode, s);
+  }
+  switch (op->N) {
+    case 1: return dgw::launch_stage_media<T, 1>(a, mode, op->num_sms, s);
+    case 2: return dgw::launch_stage_media<T, 2>(a, mode, op->num_sms, s);
+    case 3: return dgw::launch_stage_media<T, 3>(a, mode, op->num_sms, s);
+    case 4: return dgw::launch_stage_media<T, 4>(a, mode, op->num_sms, s);
+    case 5: return dgw::launch_stage_media<T, 5>(a, mode, op->num_sms, s);
+    case 6: return dgw::launch_stage_media<T, 6>(a, mode, op->num_sms, s);
+    case 7: return dgw::launch_stage_media<T, 7>(a, mode, op->num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
 cudaError_t launch_order(const dg_op* op, const dgw::StageArgs<T>& a, int mode, cudaStream_t s) {
+  if (op->media()) return launch_order_media<T>(op, a, mode, s);
   if constexpr (sizeof(T) == 4) {
     if (op->use_tc) return launch_order_tc(op, a, mode, s);
   }
@@ -329,9 +379,11 @@ __global__ void finite_scan_kernel(const float* q32, const double* q64, int64_t 
 }  // namespace
 
 // ============================================================ C ABI
-extern "C" dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t precision,
-                                       int32_t flags, dg_op** out) {
-  dgw::clear_error();
+namespace {
+
+// dg_operator_setup and dg_operator_setup_media; eps NULL: eps = 1.
+dg_status operator_setup(const dg_mesh* mesh, int32_t N, const double* eps, int32_t precision,
+                         int32_t flags, dg_op** out) {
   if (!mesh || !out) return fail(DG_ERR_ARG, "dg_operator_setup: NULL argument");
   if (N < 1 || N > DG_N_MAX)
     return fail(DG_ERR_ORDER, "dg_operator_setup: N = %d outside 1..%d", N, DG_N_MAX);
@@ -372,6 +424,22 @@ extern "C" dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t p
                   "dg_operator_setup: K * Np = %lld nodes per field exceeds 2^31 - 1", fsz);
     }
     op->geo = dgw::build_geometry(*mesh, op->ref);
+    op->min_inradius_over_c = op->geo.min_inradius;
+    if (eps) {
+      op->eps.assign(eps, eps + mesh->K);
+      // CFL length scale of a medium: min over elements of inradius * sqrt(eps_k)
+      double m = 1e300;
+      for (int64_t k = 0; k < mesh->K; ++k) {
+        const int32_t* v = &mesh->EToV[3 * k];
+        double per = 0.0;
+        for (int f = 0; f < 3; ++f) {
+          const int32_t a = v[f], b = v[(f + 1) % 3];
+          per += std::hypot(mesh->vx[b] - mesh->vx[a], mesh->vy[b] - mesh->vy[a]);
+        }
+        m = std::min(m, 2.0 * op->geo.J[k] / (0.5 * per) * std::sqrt(op->eps[k]));
+      }
+      op->min_inradius_over_c = m;
+    }
     dgw::lsrk_coefficients(op->lsrk_a, op->lsrk_b, op->lsrk_c);
   } catch (const std::bad_alloc&) {
     delete op;
@@ -401,6 +469,29 @@ extern "C" dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t p
   }
   *out = op;
   return DG_OK;
+}
+
+}  // namespace
+
+extern "C" dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t precision,
+                                       int32_t flags, dg_op** out) {
+  dgw::clear_error();
+  return operator_setup(mesh, N, nullptr, precision, flags, out);
+}
+
+extern "C" dg_status dg_operator_setup_media(const dg_mesh* mesh, int32_t N, const double* eps,
+                                             int32_t precision, int32_t flags, dg_op** out) {
+  dgw::clear_error();
+  if (!mesh || !eps || !out) return fail(DG_ERR_ARG, "dg_operator_setup_media: NULL argument");
+  for (int64_t k = 0; k < mesh->K; ++k)
+    if (!(eps[k] > 0.0) || !std::isfinite(eps[k]))
+      return fail(DG_ERR_ARG, "dg_operator_setup_media: eps[%lld] = %g is not a positive number",
+                  static_cast<long long>(k), eps[k]);
+  if (flags & (DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 | DG_SETUP_TC_BF16X3))
+    return fail(DG_ERR_ARG,
+                "dg_operator_setup_media: the lower-precision product variants are not "
+                "available with a per-element permittivity");
+  return operator_setup(mesh, N, eps, precision, flags, out);
 }
 
 extern "C" dg_status dg_get_info(const dg_op* op, int32_t* Np, int32_t* Nfp, int64_t* K,
@@ -480,7 +571,7 @@ extern "C" dg_status dg_cfl_dt(const dg_op* op, double cfl, double* dt) {
   dgw::clear_error();
   if (!op || !dt) return fail(DG_ERR_ARG, "dg_cfl_dt: NULL argument");
   if (!(cfl > 0) || !std::isfinite(cfl)) return fail(DG_ERR_ARG, "dg_cfl_dt: cfl must be > 0");
-  *dt = cfl * (2.0 / 3.0) * op->geo.min_inradius * op->ref.lgl_gap;
+  *dt = cfl * (2.0 / 3.0) * op->min_inradius_over_c * op->ref.lgl_gap;
   return DG_OK;
 }
 

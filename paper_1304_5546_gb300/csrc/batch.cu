@@ -1,0 +1,747 @@
+// Batched solves: many independent problems of mixed orders stepped by one
+// persistent launch per LSRK stage (dg_batch_* of the C ABI).
+//
+// Each order N has a pool: element capacity fixed at creation, field buffers
+// (two for the stage ping-pong, one residual), geometry records of
+// kGeoMedia values and face codes.  A problem occupies a range of its
+// order's pool (first fit, 4-element aligned so that every block's chunks
+// start on 16 bytes); its face codes point at pool element numbers, so the
+// kernels never look outside the problem.  The problem's own time step is
+// folded into its records' row scales (sH = dt, sE = dt / eps_k) and the
+// launch runs with dt = 1, so problems with different steps share a launch.
+//
+// A launch walks a block table per order (E-element blocks that never span
+// two problems; the last block of a problem may be short).  Tables, block
+// counts and the split of the launch's CTAs among the orders live in device
+// memory and are rewritten when problems join or leave, so the two captured
+// one-step graphs (starting from either ping-pong buffer) stay valid for the
+// batch's lifetime.
+//
+// The CTA split: order N's blocks take ceil(nblk_N / c_N) iterations of
+// tau_N seconds on each of its c_N CTAs; the planner gives every order with
+// blocks one CTA and then hands out the rest one at a time to the order with
+// the largest ceil(nblk_N / c_N) tau_N.  tau_N starts from the bytes a block
+// moves and is replaced by measured values by dg_batch_tune, which also
+// tries moving single CTAs between orders and keeps what measures faster.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "launch.h"
+
+using dgw::fail;
+
+namespace {
+
+constexpr int kOrders = DG_N_MAX;
+constexpr int kPadElems = 8;  // pool tail read by the last block's 16-byte rounding
+
+dg_status cuda_fail(cudaError_t err, const char* where) {
+  return fail(err == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA, "%s: %s (%s)", where,
+              cudaGetErrorName(err), cudaGetErrorString(err));
+}
+
+// Pinned host buffers for asynchronous uploads; a buffer is reused once the
+// event recorded after its copies has completed.
+class Staging {
+ public:
+  ~Staging() { release(); }
+  void* get(size_t bytes, size_t* idx) {
+    for (size_t i = 0; i < bufs_.size(); ++i) {
+      Buf& b = bufs_[i];
+      if (b.busy && cudaEventQuery(b.ev) == cudaSuccess) b.busy = false;
+      if (!b.busy && b.cap >= bytes) {
+        *idx = i;
+        return b.p;
+      }
+    }
+    Buf b;
+    b.cap = std::max<size_t>(bytes, 1 << 16);
+    if (cudaMallocHost(&b.p, b.cap) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaFreeHost(b.p);
+      return nullptr;
+    }
+    bufs_.push_back(b);
+    *idx = bufs_.size() - 1;
+    return b.p;
+  }
+  // the copies from buffer idx are enqueued on `s`
+  cudaError_t mark(size_t idx, cudaStream_t s) {
+    bufs_[idx].busy = true;
+    return cudaEventRecord(bufs_[idx].ev, s);
+  }
+  void release() {
+    for (Buf& b : bufs_) {
+      if (b.busy) cudaEventSynchronize(b.ev);
+      cudaEventDestroy(b.ev);
+      cudaFreeHost(b.p);
+    }
+    bufs_.clear();
+  }
+
+ private:
+  struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+  };
+  std::vector<Buf> bufs_;
+};
+
+struct Pool {
+  int N = 0, Np = 0, E = 0;
+  int64_t cap = 0;      // element capacity
+  int64_t fstride = 0;  // values between fields
+  float* q[2] = {nullptr, nullptr};
+  float* res = nullptr;
+  float* geo = nullptr;
+  int32_t* conn = nullptr;
+  float* lam = nullptr;
+  void* tcop = nullptr;
+  int2* blocks = nullptr;
+  int64_t max_blocks = 0;
+  std::map<int64_t, int64_t> free_ranges;  // start -> length
+  size_t smem = 0;
+};
+
+struct Problem {
+  bool live = false;
+  int N = 0;
+  int64_t K = 0, off = 0, len = 0;
+  double dt = 0.0;
+};
+
+}  // namespace
+
+struct dg_batch {
+  int device = 0;
+  int num_sms = 0;
+  int flags = 0;
+  Pool pools[kOrders];
+  int* d_meta = nullptr;  // [0, 7): block counts per order, [8, 16): CTA split cta0
+  int* d_status = nullptr;
+  std::vector<Problem> probs;
+  int cur = 0;  // ping-pong buffer holding the current fields
+  bool dirty = true;
+  int64_t nblk[kOrders] = {};
+  int cta[kOrders] = {};
+  double cost[kOrders] = {};  // seconds (or model units) per block iteration of one CTA
+  bool measured = false;
+  size_t smem = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaStream_t capture = nullptr;
+  double lsrk_a[5], lsrk_b[5], lsrk_c[5];
+  int64_t launches = 0;
+  Staging staging;
+};
+
+namespace {
+
+// ----------------------------------------------------------- planning
+// CTAs per order for block counts nblk and per-block costs cost: every
+// order with blocks gets one, the rest go one at a time to the order whose
+// ceil(nblk / c) * cost is largest (an order never gets more CTAs than
+// blocks).  Returns false if there are more orders with blocks than CTAs.
+bool plan_ctas(const int64_t* nblk, const double* cost, int num_ctas, int* cta) {
+  int used = 0;
+  for (int g = 0; g < kOrders; ++g) {
+    cta[g] = nblk[g] > 0 ? 1 : 0;
+    used += cta[g];
+  }
+  if (used > num_ctas) return false;
+  auto finish = [&](int g, int c) {
+    return static_cast<double>((nblk[g] + c - 1) / c) * cost[g];
+  };
+  for (; used < num_ctas; ++used) {
+    int best = -1;
+    double worst = -1.0;
+    for (int g = 0; g < kOrders; ++g) {
+      if (cta[g] == 0 || cta[g] >= nblk[g]) continue;
+      const double f = finish(g, cta[g]);
+      if (f > worst) {
+        worst = f;
+        best = g;
+      }
+    }
+    if (best < 0) break;
+    ++cta[best];
+  }
+  return true;
+}
+
+// model cost of one block iteration before measurement: the bytes a full
+// block moves in one fused stage (fields and residual in and out, records,
+// face codes)
+double model_cost(int N, int E) {
+  const int Np = (N + 1) * (N + 2) / 2;
+  return static_cast<double>(E) * (12.0 * Np * 4 + dgw::kGeoMedia * 4 + 12);
+}
+
+void free_pool(Pool& p) {
+  void* ptrs[] = {p.q[0], p.q[1], p.res, p.geo, p.conn, p.lam, p.tcop, p.blocks};
+  for (void* x : ptrs)
+    if (x) cudaFree(x);
+  p.q[0] = p.q[1] = p.res = p.geo = p.lam = nullptr;
+  p.conn = nullptr;
+  p.tcop = nullptr;
+  p.blocks = nullptr;
+}
+
+void destroy_batch(dg_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  for (cudaGraphExec_t& g : b->graph)
+    if (g) cudaGraphExecDestroy(g);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  for (Pool& p : b->pools) free_pool(p);
+  if (b->d_meta) cudaFree(b->d_meta);
+  if (b->d_status) cudaFree(b->d_status);
+  b->staging.release();
+  delete b;
+}
+
+dg_status alloc_pool(dg_batch* b, int N, int64_t cap) {
+  Pool& p = b->pools[N - 1];
+  p.N = N;
+  p.cap = cap;
+  const dgw::RefElement ref = dgw::build_reference(N);
+  p.Np = ref.Np;
+  p.E = dgw::batch_tc_block_elems(N);
+  p.smem = dgw::batch_tc_smem_bytes(N);
+  const int64_t rows = cap + kPadElems;
+  p.fstride = (rows * p.Np + 63) / 64 * 64;
+  if (p.fstride >= (int64_t(1) << 31) || rows * 8 >= (int64_t(1) << 31))
+    return fail(DG_ERR_ARG, "dg_batch_create: capacity %lld at N = %d exceeds 32-bit offsets",
+                static_cast<long long>(cap), N);
+  p.max_blocks = cap / 4 + 1;  // problems are >= 1 element at 4-element alignment
+  const size_t fb = 3 * static_cast<size_t>(p.fstride) * sizeof(float);
+  struct A {
+    void** dst;
+    size_t bytes;
+  } allocs[] = {
+      {reinterpret_cast<void**>(&p.q[0]), fb},
+      {reinterpret_cast<void**>(&p.q[1]), fb},
+      {reinterpret_cast<void**>(&p.res), fb},
+      {reinterpret_cast<void**>(&p.geo), static_cast<size_t>(rows) * dgw::kGeoMedia * 4},
+      {reinterpret_cast<void**>(&p.conn), static_cast<size_t>(rows) * 3 * 4},
+      {reinterpret_cast<void**>(&p.blocks), static_cast<size_t>(p.max_blocks) * sizeof(int2)},
+  };
+  for (const A& a : allocs) {
+    cudaError_t err = cudaMalloc(a.dst, a.bytes);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_batch_create: cudaMalloc");
+    err = cudaMemset(*a.dst, 0, a.bytes);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_batch_create: cudaMemset");
+  }
+  std::vector<float> lam(2 * static_cast<size_t>(p.Np));
+  for (int n = 0; n < p.Np; ++n) {
+    lam[n] = static_cast<float>(0.5 * (1.0 + ref.r[n]));
+    lam[p.Np + n] = static_cast<float>(0.5 * (1.0 + ref.s[n]));
+  }
+  const std::vector<unsigned char> tiles = dgw::tc_operator_tiles(ref, dgw::kTcTf32x3);
+  cudaError_t err = cudaMalloc(reinterpret_cast<void**>(&p.lam), lam.size() * 4);
+  if (err == cudaSuccess) err = cudaMemcpy(p.lam, lam.data(), lam.size() * 4, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMalloc(&p.tcop, tiles.size());
+  if (err == cudaSuccess) err = cudaMemcpy(p.tcop, tiles.data(), tiles.size(), cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_batch_create: operator upload");
+  p.free_ranges[0] = cap;
+  return DG_OK;
+}
+
+// first-fit range of `len` elements; -1 if none
+int64_t take_range(Pool& p, int64_t len) {
+  for (auto it = p.free_ranges.begin(); it != p.free_ranges.end(); ++it) {
+    if (it->second >= len) {
+      const int64_t start = it->first, rest = it->second - len;
+      p.free_ranges.erase(it);
+      if (rest > 0) p.free_ranges[start + len] = rest;
+      return start;
+    }
+  }
+  return -1;
+}
+
+void give_range(Pool& p, int64_t start, int64_t len) {
+  auto next = p.free_ranges.lower_bound(start);
+  if (next != p.free_ranges.end() && next->first == start + len) {
+    len += next->second;
+    next = p.free_ranges.erase(next);
+  }
+  if (next != p.free_ranges.begin()) {
+    auto prev = std::prev(next);
+    if (prev->first + prev->second == start) {
+      prev->second += len;
+      return;
+    }
+  }
+  p.free_ranges[start] = len;
+}
+
+dgw::BatchArgs batch_args(const dg_batch* b, int src, int stage) {
+  dgw::BatchArgs a;
+  for (int g = 0; g < kOrders; ++g) {
+    const Pool& p = b->pools[g];
+    dgw::StageArgs<float>& s = a.g[g];
+    if (p.cap == 0) continue;
+    s.K = p.cap;
+    s.fstride = p.fstride;
+    s.qin = p.q[src];
+    s.qout = p.q[src ^ 1];
+    s.res = p.res;
+    s.geo = p.geo;
+    s.conn = p.conn;
+    s.lam = p.lam;
+    s.tc_op = p.tcop;
+    s.status = b->d_status;
+    s.blocks = p.blocks;
+    s.nblocks = b->d_meta + g;
+    s.a = static_cast<float>(b->lsrk_a[stage]);
+    s.b = static_cast<float>(b->lsrk_b[stage]);
+    s.dt = 1.0f;  // each problem's step is in its row scales
+  }
+  a.cta0 = b->d_meta + 8;
+  return a;
+}
+
+cudaError_t launch_stage(dg_batch* b, int src, int stage, cudaStream_t s) {
+  const dgw::BatchArgs a = batch_args(b, src, stage);
+  cudaError_t err = stage == 0 ? dgw::launch_batch_tc<dgw::kModeFirstStage>(a, b->num_sms, b->smem, s)
+                               : dgw::launch_batch_tc<dgw::kModeStage>(a, b->num_sms, b->smem, s);
+  if (err == cudaSuccess) ++b->launches;
+  return err;
+}
+
+// block tables, counts and CTA split -> device (asynchronously on s)
+dg_status upload_tables(dg_batch* b, cudaStream_t s) {
+  std::vector<int2> tab[kOrders];
+  for (const Problem& pr : b->probs) {
+    if (!pr.live) continue;
+    const int E = b->pools[pr.N - 1].E;
+    for (int64_t k = 0; k < pr.K; k += E)
+      tab[pr.N - 1].push_back(make_int2(static_cast<int>(pr.off + k),
+                                        static_cast<int>(std::min<int64_t>(E, pr.K - k))));
+  }
+  for (int g = 0; g < kOrders; ++g) {
+    // longest problems first inside an order is not needed: blocks are
+    // handed out strided over the CTAs, so neighbours in the table spread
+    std::sort(tab[g].begin(), tab[g].end(), [](const int2& x, const int2& y) { return x.x < y.x; });
+    b->nblk[g] = static_cast<int64_t>(tab[g].size());
+  }
+  if (!plan_ctas(b->nblk, b->cost, b->num_sms, b->cta))
+    return fail(DG_ERR_ARG, "dg_batch_step: more orders with problems than CTAs");
+  size_t total = 0;
+  for (int g = 0; g < kOrders; ++g) total += tab[g].size();
+  const size_t bytes = 16 * sizeof(int) + total * sizeof(int2);
+  size_t idx = 0;
+  unsigned char* h = static_cast<unsigned char*>(b->staging.get(bytes, &idx));
+  if (!h) return fail(DG_ERR_OOM, "dg_batch_step: pinned staging buffer");
+  int* meta = reinterpret_cast<int*>(h);
+  int2* blk = reinterpret_cast<int2*>(h + 16 * sizeof(int));
+  meta[7] = 0;
+  meta[8] = 0;
+  for (int g = 0; g < kOrders; ++g) {
+    meta[g] = static_cast<int>(b->nblk[g]);
+    meta[9 + g] = meta[8 + g] + b->cta[g];
+  }
+  cudaError_t err = cudaMemcpyAsync(b->d_meta, meta, 16 * sizeof(int), cudaMemcpyHostToDevice, s);
+  size_t o = 0;
+  for (int g = 0; g < kOrders && err == cudaSuccess; ++g) {
+    if (tab[g].empty()) continue;
+    std::memcpy(blk + o, tab[g].data(), tab[g].size() * sizeof(int2));
+    err = cudaMemcpyAsync(b->pools[g].blocks, blk + o, tab[g].size() * sizeof(int2),
+                          cudaMemcpyHostToDevice, s);
+    o += tab[g].size();
+  }
+  if (err == cudaSuccess) err = b->staging.mark(idx, s);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: table upload");
+  b->dirty = false;
+  return DG_OK;
+}
+
+dg_status capture_graphs(dg_batch* b) {
+  if (!b->capture) {
+    cudaError_t err = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: stream");
+  }
+  // set the kernels' shared-memory attribute outside the capture (a launch
+  // of zero CTAs only configures)
+  const dgw::BatchArgs a0 = batch_args(b, 0, 0);
+  cudaError_t cerr = dgw::launch_batch_tc<dgw::kModeFirstStage>(a0, 0, 0, b->capture);
+  if (cerr == cudaSuccess) cerr = dgw::launch_batch_tc<dgw::kModeStage>(a0, 0, 0, b->capture);
+  if (cerr != cudaSuccess) return cuda_fail(cerr, "dg_batch_step: kernel attributes");
+  for (int src = 0; src < 2; ++src) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t err = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: begin capture");
+    const int64_t before = b->launches;
+    cudaError_t lerr = cudaSuccess;
+    for (int i = 0; i < 5 && lerr == cudaSuccess; ++i) lerr = launch_stage(b, src ^ (i & 1), i, b->capture);
+    b->launches = before;  // captured, not run
+    err = cudaStreamEndCapture(b->capture, &graph);
+    if (lerr != cudaSuccess) err = lerr;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&b->graph[src], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: graph capture");
+  }
+  return DG_OK;
+}
+
+dg_status check_batch(dg_batch* b, const char* where) {
+  if (!b) return fail(DG_ERR_ARG, "%s: NULL batch", where);
+  cudaError_t err = cudaSetDevice(b->device);
+  if (err != cudaSuccess) return cuda_fail(err, where);
+  return DG_OK;
+}
+
+dg_status check_slot(const dg_batch* b, int32_t slot, const char* where) {
+  if (slot < 0 || slot >= static_cast<int32_t>(b->probs.size()) || !b->probs[slot].live)
+    return fail(DG_ERR_ARG, "%s: no problem in slot %d", where, slot);
+  return DG_OK;
+}
+
+}  // namespace
+
+// ============================================================ C ABI
+extern "C" dg_status dg_batch_plan_ctas(const int64_t* nblocks, const double* cost,
+                                        int32_t num_ctas, int32_t* cta) {
+  dgw::clear_error();
+  if (!nblocks || !cost || !cta || num_ctas < 1)
+    return fail(DG_ERR_ARG, "dg_batch_plan_ctas: bad argument");
+  int c[kOrders];
+  if (!plan_ctas(nblocks, cost, num_ctas, c))
+    return fail(DG_ERR_ARG, "dg_batch_plan_ctas: more orders with blocks than CTAs");
+  for (int g = 0; g < kOrders; ++g) cta[g] = c[g];
+  return DG_OK;
+}
+
+extern "C" dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_batch** out) {
+  dgw::clear_error();
+  if (!capacity || !out) return fail(DG_ERR_ARG, "dg_batch_create: NULL argument");
+  if (flags & ~DG_BATCH_NO_GRAPH) return fail(DG_ERR_ARG, "dg_batch_create: unknown flags 0x%x", flags);
+  bool any = false;
+  for (int g = 0; g < kOrders; ++g) {
+    if (capacity[g] < 0 || capacity[g] >= (int64_t(1) << 27))
+      return fail(DG_ERR_ARG, "dg_batch_create: capacity[%d] = %lld out of range", g,
+                  static_cast<long long>(capacity[g]));
+    any = any || capacity[g] > 0;
+  }
+  if (!any) return fail(DG_ERR_ARG, "dg_batch_create: every capacity is zero");
+  dg_batch* b = new (std::nothrow) dg_batch;
+  if (!b) return fail(DG_ERR_OOM, "dg_batch_create: out of host memory");
+  b->flags = flags;
+  dgw::lsrk_coefficients(b->lsrk_a, b->lsrk_b, b->lsrk_c);
+  cudaError_t err = cudaGetDevice(&b->device);
+  if (err == cudaSuccess)
+    err = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (err != cudaSuccess) {
+    delete b;
+    return cuda_fail(err, "dg_batch_create: device");
+  }
+  for (int g = 0; g < kOrders; ++g) {
+    if (capacity[g] == 0) continue;
+    const dg_status st = alloc_pool(b, g + 1, capacity[g]);
+    if (st != DG_OK) {
+      destroy_batch(b);
+      return st;
+    }
+    b->smem = std::max(b->smem, b->pools[g].smem);
+    b->cost[g] = model_cost(g + 1, b->pools[g].E);
+  }
+  err = cudaMalloc(reinterpret_cast<void**>(&b->d_meta), 16 * sizeof(int));
+  if (err == cudaSuccess) err = cudaMemset(b->d_meta, 0, 16 * sizeof(int));
+  if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(int));
+  if (err == cudaSuccess) err = cudaMemset(b->d_status, 0, sizeof(int));
+  if (err != cudaSuccess) {
+    destroy_batch(b);
+    return cuda_fail(err, "dg_batch_create: cudaMalloc");
+  }
+  *out = b;
+  return DG_OK;
+}
+
+extern "C" void dg_batch_destroy(dg_batch* b) { destroy_batch(b); }
+
+extern "C" dg_status dg_batch_add(dg_batch* b, const dg_op* op, double dt, void* stream,
+                                  int32_t* slot) {
+  dgw::clear_error();
+  dg_status st = check_batch(b, "dg_batch_add");
+  if (st) return st;
+  if (!op || !slot) return fail(DG_ERR_ARG, "dg_batch_add: NULL argument");
+  if (op->precision != DG_FP32)
+    return fail(DG_ERR_ARG, "dg_batch_add: the batch computes in FP32; set the operator up with DG_FP32");
+  Pool& p = b->pools[op->N - 1];
+  if (p.cap == 0)
+    return fail(DG_ERR_ARG, "dg_batch_add: the batch has no capacity for order N = %d", op->N);
+  if (!(dt > 0.0)) dt = (2.0 / 3.0) * op->min_inradius_over_c * op->ref.lgl_gap;
+  if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dg_batch_add: dt is not finite");
+  const int64_t K = op->K, len = (K + 3) / 4 * 4;
+  const int64_t off = take_range(p, len);
+  if (off < 0)
+    return fail(DG_ERR_OOM, "dg_batch_add: no free range of %lld elements in the N = %d pool",
+                static_cast<long long>(len), op->N);
+  // records with this problem's step folded in, face codes in pool numbering
+  std::vector<double> rec;
+  try {
+    dgw::media_records(*op, dt, rec);
+  } catch (const std::bad_alloc&) {
+    give_range(p, off, len);
+    return fail(DG_ERR_OOM, "dg_batch_add: out of host memory");
+  }
+  const size_t rb = static_cast<size_t>(K) * dgw::kGeoMedia * 4, cb = static_cast<size_t>(K) * 12;
+  size_t idx = 0;
+  unsigned char* h = static_cast<unsigned char*>(b->staging.get(rb + cb, &idx));
+  if (!h) {
+    give_range(p, off, len);
+    return fail(DG_ERR_OOM, "dg_batch_add: pinned staging buffer");
+  }
+  float* hg = reinterpret_cast<float*>(h);
+  int32_t* hc = reinterpret_cast<int32_t*>(h + rb);
+  for (size_t i = 0; i < rec.size(); ++i) hg[i] = static_cast<float>(rec[i]);
+  for (int64_t i = 0; i < 3 * K; ++i) {
+    const int32_t code = op->geo.conn[i];
+    hc[i] = code < 0 ? -1 : static_cast<int32_t>(((code >> 3) + off) * 8 + (code & 7));
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t err = cudaMemcpyAsync(p.geo + off * dgw::kGeoMedia, hg, rb, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(p.conn + off * 3, hc, cb, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = b->staging.mark(idx, s);
+  if (err != cudaSuccess) {
+    give_range(p, off, len);
+    return cuda_fail(err, "dg_batch_add: upload");
+  }
+  Problem pr;
+  pr.live = true;
+  pr.N = op->N;
+  pr.K = K;
+  pr.off = off;
+  pr.len = len;
+  pr.dt = dt;
+  int32_t id = -1;
+  for (size_t i = 0; i < b->probs.size(); ++i)
+    if (!b->probs[i].live) {
+      id = static_cast<int32_t>(i);
+      break;
+    }
+  if (id < 0) {
+    id = static_cast<int32_t>(b->probs.size());
+    b->probs.push_back(pr);
+  } else {
+    b->probs[id] = pr;
+  }
+  b->dirty = true;
+  *slot = id;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_batch_remove(dg_batch* b, int32_t slot) {
+  dgw::clear_error();
+  dg_status st = check_batch(b, "dg_batch_remove");
+  if (st) return st;
+  if ((st = check_slot(b, slot, "dg_batch_remove"))) return st;
+  Problem& pr = b->probs[slot];
+  give_range(b->pools[pr.N - 1], pr.off, pr.len);
+  pr.live = false;
+  b->dirty = true;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_batch_info(const dg_batch* b, int32_t slot, int32_t* N, int64_t* K,
+                                   double* dt, int64_t* field_stride) {
+  dgw::clear_error();
+  if (!b) return fail(DG_ERR_ARG, "dg_batch_info: NULL batch");
+  dg_status st = check_slot(b, slot, "dg_batch_info");
+  if (st) return st;
+  const Problem& pr = b->probs[slot];
+  if (N) *N = pr.N;
+  if (K) *K = pr.K;
+  if (dt) *dt = pr.dt;
+  if (field_stride) *field_stride = b->pools[pr.N - 1].fstride;
+  return DG_OK;
+}
+
+namespace {
+
+dg_status copy_fields(dg_batch* b, int32_t slot, void* other, int64_t other_stride, bool to_pool,
+                      void* stream, const char* where) {
+  dg_status st = check_batch(b, where);
+  if (st) return st;
+  if ((st = check_slot(b, slot, where))) return st;
+  const Problem& pr = b->probs[slot];
+  const Pool& p = b->pools[pr.N - 1];
+  const int64_t n = pr.K * p.Np;
+  if (!other) return fail(DG_ERR_ARG, "%s: NULL buffer", where);
+  if (other_stride < n) return fail(DG_ERR_ARG, "%s: field stride %lld < K * Np = %lld", where,
+                                    static_cast<long long>(other_stride), static_cast<long long>(n));
+  float* dev = p.q[b->cur] + pr.off * p.Np;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t width = static_cast<size_t>(n) * 4;
+  const size_t pitch_pool = static_cast<size_t>(p.fstride) * 4;
+  const size_t pitch_other = static_cast<size_t>(other_stride) * 4;
+  cudaError_t err =
+      to_pool ? cudaMemcpy2DAsync(dev, pitch_pool, other, pitch_other, width, 3, cudaMemcpyDefault, s)
+              : cudaMemcpy2DAsync(other, pitch_other, dev, pitch_pool, width, 3, cudaMemcpyDefault, s);
+  if (err != cudaSuccess) return cuda_fail(err, where);
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" dg_status dg_batch_set_fields(dg_batch* b, int32_t slot, const void* src,
+                                         int64_t src_stride, void* stream) {
+  dgw::clear_error();
+  return copy_fields(b, slot, const_cast<void*>(src), src_stride, true, stream,
+                     "dg_batch_set_fields");
+}
+
+extern "C" dg_status dg_batch_get_fields(dg_batch* b, int32_t slot, void* dst,
+                                         int64_t dst_stride, void* stream) {
+  dgw::clear_error();
+  return copy_fields(b, slot, dst, dst_stride, false, stream, "dg_batch_get_fields");
+}
+
+extern "C" dg_status dg_batch_step(dg_batch* b, int32_t nsteps, void* stream) {
+  dgw::clear_error();
+  dg_status st = check_batch(b, "dg_batch_step");
+  if (st) return st;
+  if (nsteps < 0) return fail(DG_ERR_ARG, "dg_batch_step: nsteps = %d < 0", nsteps);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (b->dirty && (st = upload_tables(b, s))) return st;
+  const bool use_graph = !(b->flags & DG_BATCH_NO_GRAPH);
+  if (use_graph && !b->graph[0] && (st = capture_graphs(b))) return st;
+  for (int32_t n = 0; n < nsteps; ++n) {
+    if (use_graph) {
+      cudaError_t err = cudaGraphLaunch(b->graph[b->cur], s);
+      if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: graph launch");
+      b->launches += 5;
+    } else {
+      for (int i = 0; i < 5; ++i) {
+        cudaError_t err = launch_stage(b, b->cur ^ (i & 1), i, s);
+        if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: kernel launch");
+      }
+    }
+    b->cur ^= 1;
+  }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_batch_tune(dg_batch* b, int32_t reps, void* stream) {
+  dgw::clear_error();
+  dg_status st = check_batch(b, "dg_batch_tune");
+  if (st) return st;
+  if (reps < 1) return fail(DG_ERR_ARG, "dg_batch_tune: reps = %d < 1", reps);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = upload_tables(b, s))) return st;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int meta[16];
+  // time `reps` stage launches (stage 2 form: reads q[cur] and the residual,
+  // writes the other buffer and the residual; the fields stay as they are)
+  auto timed = [&](const int* cta, float* ms) -> cudaError_t {
+    meta[7] = 0;
+    meta[8] = 0;
+    for (int g = 0; g < kOrders; ++g) {
+      meta[g] = static_cast<int>(b->nblk[g]);
+      meta[9 + g] = meta[8 + g] + cta[g];
+    }
+    cudaError_t err = cudaStreamSynchronize(s);
+    if (err == cudaSuccess) err = cudaMemcpy(b->d_meta, meta, sizeof(meta), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = launch_stage(b, b->cur, 1, s);  // warm
+    if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && err == cudaSuccess; ++r) err = launch_stage(b, b->cur, 1, s);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
+    return err;
+  };
+  cudaError_t err = cudaSuccess;
+  int alone[kOrders];
+  for (int g = 0; g < kOrders && err == cudaSuccess; ++g) {
+    if (b->nblk[g] == 0) continue;
+    for (int h = 0; h < kOrders; ++h) alone[h] = 0;
+    alone[g] = b->num_sms;
+    float ms = 0.f;
+    err = timed(alone, &ms);
+    const int64_t iters = (b->nblk[g] + b->num_sms - 1) / b->num_sms;
+    b->cost[g] = 1e-3 * ms / reps / static_cast<double>(iters);
+  }
+  // measured costs -> plan, then single-CTA moves between orders that
+  // measure faster
+  int best[kOrders];
+  float best_ms = 0.f;
+  if (err == cudaSuccess) {
+    plan_ctas(b->nblk, b->cost, b->num_sms, best);
+    err = timed(best, &best_ms);
+  }
+  for (int round = 0; round < 3 && err == cudaSuccess; ++round) {
+    bool improved = false;
+    for (int from = 0; from < kOrders && err == cudaSuccess; ++from) {
+      for (int to = 0; to < kOrders && err == cudaSuccess; ++to) {
+        if (from == to || best[from] <= 1 || best[to] == 0 || best[to] >= b->nblk[to]) continue;
+        int trial[kOrders];
+        std::copy(best, best + kOrders, trial);
+        --trial[from];
+        ++trial[to];
+        float ms = 0.f;
+        err = timed(trial, &ms);
+        if (err == cudaSuccess && ms < 0.995f * best_ms) {
+          std::copy(trial, trial + kOrders, best);
+          best_ms = ms;
+          improved = true;
+        }
+      }
+    }
+    if (!improved) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_batch_tune");
+  b->measured = true;
+  std::copy(best, best + kOrders, b->cta);
+  for (int g = 0; g < kOrders; ++g) {
+    meta[g] = static_cast<int>(b->nblk[g]);
+    meta[9 + g] = meta[8 + g] + b->cta[g];
+  }
+  err = cudaMemcpy(b->d_meta, meta, sizeof(meta), cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_batch_tune: plan upload");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_batch_plan(const dg_batch* b, int32_t* cta, int64_t* nblocks,
+                                   double* cost) {
+  dgw::clear_error();
+  if (!b) return fail(DG_ERR_ARG, "dg_batch_plan: NULL batch");
+  for (int g = 0; g < kOrders; ++g) {
+    if (cta) cta[g] = b->cta[g];
+    if (nblocks) nblocks[g] = b->nblk[g];
+    if (cost) cost[g] = b->cost[g];
+  }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_batch_sync_check(dg_batch* b, void* stream) {
+  dgw::clear_error();
+  dg_status st = check_batch(b, "dg_batch_sync_check");
+  if (st) return st;
+  cudaError_t err = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (err == cudaSuccess) err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "dg_batch_sync_check");
+  int status = 0;
+  err = cudaMemcpy(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_batch_sync_check: status read");
+  if (status != 0) {
+    cudaMemset(b->d_status, 0, sizeof(int));
+    return fail(DG_ERR_TIMEOUT, "dg_batch_sync_check: a kernel's bounded wait expired");
+  }
+  return DG_OK;
+}
+
+extern "C" int64_t dg_batch_launch_count(const dg_batch* b) { return b ? b->launches : 0; }

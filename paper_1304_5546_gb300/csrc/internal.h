@@ -2,6 +2,7 @@
 // (api.cu) and the kernels (kernels.cuh).  Not part of the public interface.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -62,5 +63,52 @@ inline int face_node(int N, int f, int j) {
 
 // LSRK(5,4) 2N-storage coefficients and stage times.
 void lsrk_coefficients(double a[5], double b[5], double c[5]);
+
+}  // namespace dgw
+
+// Operator handle (dg_op of the C ABI).
+struct dg_op {
+  int N = 0, Np = 0, Nfp = 0, Nafp = 0;
+  int precision = DG_FP32;
+  int flags = 0;
+  int64_t K = 0, Kpad = 0, fstride = 0;
+  size_t elem_size = 4;
+  dgw::RefElement ref;
+  dgw::Geometry geo;
+  // per-element permittivity (dg_operator_setup_media); empty: eps = 1
+  std::vector<double> eps;
+  // min over elements of inradius / wave speed (wave speed 1 / sqrt(eps))
+  double min_inradius_over_c = 0.0;
+  bool has_device = false;
+  int device = 0;
+  int num_sms = 0;
+  void* d_Dr = nullptr;
+  void* d_Ds = nullptr;
+  void* d_LIFT = nullptr;
+  void* d_lam = nullptr;   // vertex-interpolant weights per node
+  void* d_geo = nullptr;
+  void* d_conn = nullptr;
+  void* d_qtmp = nullptr;  // second field buffer for the stage ping-pong
+  int* d_flag = nullptr;   // finiteness scan result
+  int* d_status = nullptr; // kernel status word (bounded-wait expiry)
+  void* d_tcop = nullptr;  // tensor-core operator tiles for FP32 (see tc_operator_tiles)
+  bool use_tc = false;     // FP32 products on the tensor cores
+  int tc_prec = 0;         // their product variant (dgw::TcPrecision)
+  double lsrk_a[5], lsrk_b[5], lsrk_c[5];
+  mutable std::atomic<int64_t> launches{0};
+
+  bool media() const { return !eps.empty(); }
+};
+
+namespace dgw {
+
+// [Dr | Ds | LIFT | 1] as the B operand of the tensor-core kernel in the
+// operand format of product variant `prec` (see api.cu).
+std::vector<unsigned char> tc_operator_tiles(const RefElement& R, int prec);
+
+// Geometry records of kGeoMedia values (layout in launch.h) for the K
+// elements of `op`, with row scales sH = sh and sE = sh / eps_k, as doubles
+// (out[k * kGeoMedia + i]); eps = 1 where the operator has none.
+void media_records(const dg_op& op, double sh, std::vector<double>& out);
 
 }  // namespace dgw

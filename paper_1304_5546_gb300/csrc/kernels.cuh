@@ -80,8 +80,9 @@ struct Vec16<double> {
 
 constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-template <typename T, int N>
+template <typename T, int N, bool MEDIA = false>
 struct Layout {
+  static constexpr int GEO = MEDIA ? kGeoMedia : kGeo;  // geometry record length
   static constexpr int Np = Order<N>::Np;
   static constexpr int Nfp = Order<N>::Nfp;
   static constexpr int Nafp = Order<N>::Nafp;
@@ -94,7 +95,7 @@ struct Layout {
   static constexpr int TPT = (TASKS + THREADS - 1) / THREADS;  // per thread
   // stage buffer: q[3][E Np], res[3][E Np], geo[E][kGeo], conn[E][3]
   static constexpr int QB = E * Np * static_cast<int>(sizeof(T));
-  static constexpr int GB = E * kGeo * static_cast<int>(sizeof(T));
+  static constexpr int GB = E * GEO * static_cast<int>(sizeof(T));
   static constexpr int CB = E * 3 * 4;
   static constexpr int STAGE_BYTES = round_up(6 * QB + GB + CB, 128);
   // double-buffered work arrays: centred volume operands and lifted fluxes
@@ -122,11 +123,15 @@ __host__ __device__ constexpr uint32_t round16(uint32_t x) { return (x + 15u) & 
 
 // ------------------------------------------------------------ kernel
 // Offsets inside one field are 32-bit (the host guarantees field_stride <
-// 2^31); each field has its own 64-bit base pointer.
-template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(Layout<T, N>::THREADS)
+// 2^31); each field has its own 64-bit base pointer.  MEDIA: geometry
+// records of kGeoMedia values (per-element permittivity, see launch.h): the
+// flux of the exact interface Riemann solution and per-row scales of the
+// right-hand side.
+template <typename T, int N, int MODE, bool MEDIA>
+__global__ void __launch_bounds__(Layout<T, N, MEDIA>::THREADS)
     dg_stage_kernel(const StageArgs<T> p) {
-  using L = Layout<T, N>;
+  using L = Layout<T, N, MEDIA>;
+  constexpr int GEO = L::GEO;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp;
   constexpr int E = L::E, NPAD = L::NPAD, FPAD = L::FPAD, VW = L::VW;
   constexpr int THREADS = L::THREADS, TASKS = L::TASKS, TPT = L::TPT;
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
     const int k0 = (first + it * G) * E;
     const int n = (K - k0) < E ? (K - k0) : E;
     const uint32_t qb = round16(static_cast<uint32_t>(n * Np * sizeof(T)));
-    const uint32_t gb = round16(static_cast<uint32_t>(n * kGeo * sizeof(T)));
+    const uint32_t gb = round16(static_cast<uint32_t>(n * GEO * sizeof(T)));
     const uint32_t cb = round16(static_cast<uint32_t>(n * 3 * 4));
     unsigned char* st = stages + s * L::STAGE_BYTES;
     mbar_expect_tx(&bars[s], NQ * qb + gb + cb);
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
       for (int f = 0; f < 3; ++f)
         tma_load_1d(st + (3 + f) * L::QB, p.res + f * p.fstride + k0 * Np, qb, &bars[s]);
     }
-    tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * kGeo, gb, &bars[s]);
+    tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * GEO, gb, &bars[s]);
     tma_load_1d(st + 6 * L::QB + L::GB, p.conn + static_cast<int64_t>(k0) * 3, cb, &bars[s]);
   };
 
@@ -260,6 +265,7 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
     // their linear part
     T hx = 0, hy = 0, ez = 0, r0 = 0, r1 = 0, r2 = 0, rx = 0, ry = 0, sx = 0, sy = 0;
     T lin0 = 0, lin1 = 0, lin2 = 0;
+    T sH = 1, sE = 1;  // row scales of the right-hand side (media records)
     if (ok) {
       hx = sq[t];
       hy = sq[E * Np + t];
@@ -269,10 +275,14 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
         r1 = sq[4 * E * Np + t];
         r2 = sq[5 * E * Np + t];
       }
-      rx = sg[e * kGeo + 0];
-      ry = sg[e * kGeo + 1];
-      sx = sg[e * kGeo + 2];
-      sy = sg[e * kGeo + 3];
+      rx = sg[e * GEO + 0];
+      ry = sg[e * GEO + 1];
+      sx = sg[e * GEO + 2];
+      sy = sg[e * GEO + 3];
+      if (MEDIA) {
+        sH = sg[e * GEO + 17];
+        sE = sg[e * GEO + 18];
+      }
       const T* qe = sq + e * Np;  // vertex nodes: 0, N, Np - 1
       const T x1 = qe[0], x2 = qe[N], x3 = qe[Np - 1];
       const T y1 = qe[E * Np], y2 = qe[E * Np + N], y3 = qe[E * Np + Np - 1];
@@ -308,12 +318,23 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
           dHy = hyM - trc[u][1];
           dEz = ezM - trc[u][2];
         }
-        const T* gf = sg + ee * kGeo + 4 + 3 * f;
-        const T nx = gf[0], ny = gf[1], fsc = gf[2];
-        const T ndotdH = nx * dHx + ny * dHy;
-        Fb[(0 * E + ee) * FPAD + j] = fsc * (ny * dEz + (ndotdH * nx - dHx));
-        Fb[(1 * E + ee) * FPAD + j] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
-        Fb[(2 * E + ee) * FPAD + j] = fsc * (ny * dHx - nx * dHy - dEz);
+        if constexpr (MEDIA) {
+          // exact interface Riemann solution: fz = cH [Ht] - cE [Ez]
+          const T* gf = sg + ee * GEO + 4 + 4 * f;
+          const T nx = gf[0], ny = gf[1], cH = gf[2], cE = gf[3];
+          const T zM = sg[ee * GEO + 16];
+          const T fz = cH * (ny * dHx - nx * dHy) - cE * dEz;
+          Fb[(0 * E + ee) * FPAD + j] = -zM * ny * fz;
+          Fb[(1 * E + ee) * FPAD + j] = zM * nx * fz;
+          Fb[(2 * E + ee) * FPAD + j] = fz;
+        } else {
+          const T* gf = sg + ee * GEO + 4 + 3 * f;
+          const T nx = gf[0], ny = gf[1], fsc = gf[2];
+          const T ndotdH = nx * dHx + ny * dHy;
+          Fb[(0 * E + ee) * FPAD + j] = fsc * (ny * dEz + (ndotdH * nx - dHx));
+          Fb[(1 * E + ee) * FPAD + j] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
+          Fb[(2 * E + ee) * FPAD + j] = fsc * (ny * dHx - nx * dHy - dEz);
+        }
       }
     }
     // next block's traces: their addresses are in the next stage's codes
@@ -389,9 +410,14 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
         }
       }
     }
-    const T rhsHx = -(ry * dEzdr + sy * dEzds) + lin0 + l0;
-    const T rhsHy = (rx * dEzdr + sx * dEzds) + lin1 + l1;
-    const T rhsEz = (cA + cB) + lin2 + l2;
+    T rhsHx = -(ry * dEzdr + sy * dEzds) + lin0 + l0;
+    T rhsHy = (rx * dEzdr + sx * dEzds) + lin1 + l1;
+    T rhsEz = (cA + cB) + lin2 + l2;
+    if (MEDIA) {
+      rhsHx *= sH;
+      rhsHy *= sH;
+      rhsEz *= sE;
+    }
 
     if (valid) {
       if (MODE == kModeRhs) {
@@ -429,17 +455,17 @@ __global__ void __launch_bounds__(Layout<T, N>::THREADS)
   }
 }
 
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, bool MEDIA>
 cudaError_t launch_stage_mode(const StageArgs<T>& args, int num_sms, cudaStream_t stream) {
-  using L = Layout<T, N>;
-  static int blocks_per_sm = 0;  // per (T, N, MODE), set on the first launch
+  using L = Layout<T, N, MEDIA>;
+  static int blocks_per_sm = 0;  // per (T, N, MODE, MEDIA), set on the first launch
   if (blocks_per_sm == 0) {
-    cudaError_t err = cudaFuncSetAttribute(dg_stage_kernel<T, N, MODE>,
+    cudaError_t err = cudaFuncSetAttribute(dg_stage_kernel<T, N, MODE, MEDIA>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(L::SMEM_BYTES));
     if (err != cudaSuccess) return err;
     int nb = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dg_stage_kernel<T, N, MODE>,
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dg_stage_kernel<T, N, MODE, MEDIA>,
                                                         L::THREADS, L::SMEM_BYTES);
     if (err != cudaSuccess) return err;
     blocks_per_sm = nb > 0 ? nb : 1;
@@ -448,18 +474,30 @@ cudaError_t launch_stage_mode(const StageArgs<T>& args, int num_sms, cudaStream_
   int64_t grid = static_cast<int64_t>(blocks_per_sm) * num_sms;
   if (grid > nblk) grid = nblk;
   if (grid < 1) grid = 1;
-  dg_stage_kernel<T, N, MODE>
+  dg_stage_kernel<T, N, MODE, MEDIA>
       <<<static_cast<unsigned>(grid), L::THREADS, L::SMEM_BYTES, stream>>>(args);
   return cudaGetLastError();
 }
 
-// Definition of the launcher declared in launch.h; explicitly instantiated
+template <typename T, int N, bool MEDIA>
+cudaError_t launch_stage_any(const StageArgs<T>& args, int mode, int num_sms,
+                             cudaStream_t stream) {
+  if (mode == kModeRhs) return launch_stage_mode<T, N, kModeRhs, MEDIA>(args, num_sms, stream);
+  if (mode == kModeFirstStage)
+    return launch_stage_mode<T, N, kModeFirstStage, MEDIA>(args, num_sms, stream);
+  return launch_stage_mode<T, N, kModeStage, MEDIA>(args, num_sms, stream);
+}
+
+// Definitions of the launchers declared in launch.h; explicitly instantiated
 // per order in kernels_N*.cu.
 template <typename T, int N>
 cudaError_t launch_stage(const StageArgs<T>& args, int mode, int num_sms, cudaStream_t stream) {
-  if (mode == kModeRhs) return launch_stage_mode<T, N, kModeRhs>(args, num_sms, stream);
-  if (mode == kModeFirstStage) return launch_stage_mode<T, N, kModeFirstStage>(args, num_sms, stream);
-  return launch_stage_mode<T, N, kModeStage>(args, num_sms, stream);
+  return launch_stage_any<T, N, false>(args, mode, num_sms, stream);
+}
+template <typename T, int N>
+cudaError_t launch_stage_media(const StageArgs<T>& args, int mode, int num_sms,
+                               cudaStream_t stream) {
+  return launch_stage_any<T, N, true>(args, mode, num_sms, stream);
 }
 
 }  // namespace dgw

@@ -53,9 +53,11 @@
 
 namespace dgw {
 
-template <int N, int PREC_>
+template <int N, int PREC_, bool MEDIA_ = false>
 struct TcLayout {
   static constexpr int PREC = PREC_;
+  static constexpr bool MEDIA = MEDIA_;
+  static constexpr int GEO = MEDIA ? kGeoMedia : kGeo;  // geometry record length
   static constexpr bool BF = tc_is_bf16(PREC);  // BF16 operands (else TF32)
   static constexpr int NS = tc_nsplit(PREC);     // X parts and operator tiles (hi, lo)
   static constexpr int Np = Order<N>::Np;
@@ -93,7 +95,7 @@ struct TcLayout {
   static constexpr int FES = Nafp | 1;  // face-flux row stride, odd: conflict-free row reads
   static constexpr int FB = 3 * E * FES * 4;  // one face-flux buffer [3][E][FES]
   static constexpr int QB = E * Np * 4;
-  static constexpr int GB = E * kGeo * 4;
+  static constexpr int GB = E * GEO * 4;
   static constexpr int CB = E * 3 * 4;
   static constexpr int STAGE_BYTES = round_up(6 * QB + GB + CB, 128);
   static constexpr int OB = NN * KP * EB;  // one operator tile
@@ -264,16 +266,20 @@ __device__ __forceinline__ void build_x_lift(const float* fr, uint32_t xh, uint3
   }
 }
 
-template <int N, int MODE, int PREC>
-__global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
-    dg_stage_tc_kernel(const StageArgs<float> p) {
-  using L = TcLayout<N, PREC>;
+// One CTA's share of a stage launch: the blocks first, first + G, ... of
+// the launch (TABLE: from the block table p.blocks; else contiguous blocks of
+// E elements over [0, K)).  smem: the CTA's dynamic shared memory (1024-byte
+// aligned, L::SMEM_BYTES).
+template <int N, int MODE, int PREC, bool MEDIA, bool TABLE>
+__device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const int first,
+                                              const int G, unsigned char* smem) {
+  using L = TcLayout<N, PREC, MEDIA>;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
   constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FES = L::FES, XBUF = L::XBUF;
   constexpr int FT = L::FLUX_THREADS, TASKS = L::TASKS, TPT = L::TPT;
   constexpr int NQ = (MODE == kModeStage) ? 6 : 3;
+  constexpr int GEO = L::GEO;
 
-  extern __shared__ __align__(1024) unsigned char smem[];
   // header: mbarriers, TMEM base, abort flag, tables
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);              // [S] stage loaded
   uint64_t* out_ready = reinterpret_cast<uint64_t*>(smem + 64);    // [S] outputs written
@@ -293,11 +299,21 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
   const int t = threadIdx.x;
   const int warp = t >> 5, lane = t & 31;
   const int K = static_cast<int>(p.K);
-  const int nblk = (K + E - 1) / E;
-  const int G = gridDim.x;
-  const int first = blockIdx.x;
+  const int nblk = TABLE ? __ldg(p.nblocks) : (K + E - 1) / E;
   const int niter = first < nblk ? (nblk - 1 - first) / G + 1 : 0;
   const int64_t fs = p.fstride;
+  // first element and element count of this CTA's block `it`
+  auto block_at = [&](int it, int& k0, int& n) {
+    const int b = first + it * G;
+    if constexpr (TABLE) {
+      const int2 d = __ldg(p.blocks + b);
+      k0 = d.x;
+      n = d.y;
+    } else {
+      k0 = b * E;
+      n = (K - k0) < E ? (K - k0) : E;
+    }
+  };
 
   if (t == 0) {
     for (int s = 0; s < S; ++s) {
@@ -342,10 +358,10 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
       int issued = 0;
       auto issue = [&](int it) {
         const int s = it % S;
-        const int k0 = (first + it * G) * E;
-        const int n = (K - k0) < E ? (K - k0) : E;
+        int k0, n;
+        block_at(it, k0, n);
         const uint32_t qb = round16(static_cast<uint32_t>(n * Np * 4));
-        const uint32_t gb = round16(static_cast<uint32_t>(n * kGeo * 4));
+        const uint32_t gb = round16(static_cast<uint32_t>(n * GEO * 4));
         const uint32_t cb = round16(static_cast<uint32_t>(n * 3 * 4));
         unsigned char* st = stages + s * L::STAGE_BYTES;
         mbar_expect_tx(&full[s], NQ * qb + gb + cb);
@@ -357,7 +373,7 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
           for (int f = 0; f < 3; ++f)
             tma_load_1d(st + (3 + f) * L::QB, p.res + f * fs + k0 * Np, qb, &full[s]);
         }
-        tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * kGeo, gb, &full[s]);
+        tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * GEO, gb, &full[s]);
         tma_load_1d(st + 6 * L::QB + L::GB, p.conn + static_cast<int64_t>(k0) * 3, cb, &full[s]);
       };
       mbar_expect_tx(op_bar, L::NS * L::OB);
@@ -369,8 +385,9 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
         const int s = jj % S;
         ok = mbar_wait_or_abort(&out_ready[s], static_cast<uint32_t>((jj / S) & 1), abort_flag);
         if (!ok) break;
-        const int k0 = (first + jj * G) * E;
-        if (K - k0 >= E) {
+        int k0, nv;
+        block_at(jj, k0, nv);
+        if (nv == E) {
           const float* sq = reinterpret_cast<const float*>(stages + s * L::STAGE_BYTES);
           if (MODE == kModeRhs) {
 #pragma unroll
@@ -467,19 +484,20 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
       task_jj[u] = jj;
       task_nm[u] = ee * Np + face_node_dev(N, f, jj);
       task_cf[u] = ee * 3 + f;
-      task_gf[u] = ee * kGeo + 4 + 3 * f;
+      task_gf[u] = ee * GEO + 4 + (MEDIA ? 4 : 3) * f;
       task_fo[u] = ee * FES + j;
     }
     float trc[TPT][3];
     auto gather = [&](int it) {
       const int32_t* sc = reinterpret_cast<const int32_t*>(stages + (it % S) * L::STAGE_BYTES +
                                                            6 * L::QB + L::GB);
-      const int k0 = (first + it * G) * E;
+      int k0, nv;
+      block_at(it, k0, nv);
 #pragma unroll
       for (int u = 0; u < TPT; ++u) {
         trc[u][0] = trc[u][1] = trc[u][2] = 0.f;
         const int ee = task_e[u];
-        if (ee < E && k0 + ee < K) {
+        if (ee < nv) {
           const int32_t code = sc[task_cf[u]];
           if (code >= 0) {
             const int gP = (code >> 3) * Np + nbr[(code & 7) * Nfp + task_jj[u]];
@@ -503,8 +521,8 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
         ok = mbar_wait_or_abort(&fs_empty[j & 1], static_cast<uint32_t>(((j - 2) >> 1) & 1),
                                 abort_flag);
       if (!ok) break;
-      const int k0 = (first + j * G) * E;
-      const int nvalid = (K - k0) < E ? (K - k0) : E;
+      int k0, nvalid;
+      block_at(j, k0, nvalid);
       const unsigned char* st = stages + s * L::STAGE_BYTES;
       const float* sq = reinterpret_cast<const float*>(st);
       const float* sg = reinterpret_cast<const float*>(st + 6 * L::QB);
@@ -528,12 +546,22 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
             dEz = ezM - trc[u][2];
           }
           const float* gf = sg + task_gf[u];
-          const float nx = gf[0], ny = gf[1], fsc = gf[2];
-          const float ndotdH = nx * dHx + ny * dHy;
           float* fo = Fb + task_fo[u];
-          fo[0] = fsc * (ny * dEz + (ndotdH * nx - dHx));
-          fo[E * FES] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
-          fo[2 * E * FES] = fsc * (ny * dHx - nx * dHy - dEz);
+          if constexpr (MEDIA) {
+            // exact interface Riemann solution: fz = cH [Ht] - cE [Ez]
+            const float nx = gf[0], ny = gf[1], cH = gf[2], cE = gf[3];
+            const float zM = sg[ee * GEO + 16];
+            const float fz = cH * (ny * dHx - nx * dHy) - cE * dEz;
+            fo[0] = -zM * ny * fz;
+            fo[E * FES] = zM * nx * fz;
+            fo[2 * E * FES] = fz;
+          } else {
+            const float nx = gf[0], ny = gf[1], fsc = gf[2];
+            const float ndotdH = nx * dHx + ny * dHy;
+            fo[0] = fsc * (ny * dEz + (ndotdH * nx - dHx));
+            fo[E * FES] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
+            fo[2 * E * FES] = fsc * (ny * dHx - nx * dHy - dEz);
+          }
         }
       }
       mbar_arrive(&fs_full[j & 1]);
@@ -564,8 +592,8 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
         break;
       }
       tc_fence_after();
-      const int k0 = (first + j * G) * E;
-      const int nvalid = (K - k0) < E ? (K - k0) : E;
+      int k0, nvalid;
+      block_at(j, k0, nvalid);
       const unsigned char* st = stages + s * L::STAGE_BYTES;
       const float* sq = reinterpret_cast<const float*>(st);
       const float* sg = reinterpret_cast<const float*>(st + 6 * L::QB);
@@ -582,7 +610,7 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
       float rx = 0.f, ry = 0.f, sx = 0.f, sy = 0.f;
       float a1 = 0.f, a2 = 0.f, a3 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;  // vertex values
       if (row_ok) {
-        const float* ge = sg + re * kGeo;
+        const float* ge = sg + re * GEO;
         rx = ge[0];
         ry = ge[1];
         sx = ge[2];
@@ -669,25 +697,31 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
       tc_fence_before();
       mbar_arrive(&tmem_free[j & 1]);
 
-      const int k0 = (first + j * G) * E;
-      const int nvalid = (K - k0) < E ? (K - k0) : E;
+      int k0, nvalid;
+      block_at(j, k0, nvalid);
       float* sq = reinterpret_cast<float*>(stages + s * L::STAGE_BYTES);  // q, then outputs
       float* sres = sq + 3 * E * Np;
       const int r = 32 * warp + lane;
       const int c = r / E, e = r - c * E;
       // each thread updates only its own row: no ordering with other rows
       const bool row_ok = r < L::ROWS && e < nvalid;
+      // the row's scale of the right-hand side (media records: sH or sE)
+      float srow = 1.f;
+      if constexpr (MEDIA) {
+        if (row_ok) srow = sq[6 * E * Np + e * GEO + (c < 2 ? 17 : 18)];
+      }
+      const float drow = MEDIA ? p.dt * srow : p.dt;
       if (row_ok && nvalid == E) {
         // full block: in place in the stage buffer, node pairs in packed
         // FP32x2 arithmetic (res = a res + dt rhs, q = q + b res)
         float* rq = sq + c * E * Np + e * Np;
         float* rr = sres + c * E * Np + e * Np;
-        const f32x2 a2 = f32x2_dup(p.a), b2 = f32x2_dup(p.b), dt2 = f32x2_dup(p.dt);
+        const f32x2 a2 = f32x2_dup(p.a), b2 = f32x2_dup(p.b), dt2 = f32x2_dup(drow);
 #pragma unroll
         for (int n = 0; n + 1 < Np; n += 2) {
           if (MODE == kModeRhs) {
-            rq[n] = acc[n];
-            rq[n + 1] = acc[n + 1];
+            rq[n] = MEDIA ? srow * acc[n] : acc[n];
+            rq[n + 1] = MEDIA ? srow * acc[n + 1] : acc[n + 1];
           } else {
             f32x2 rn = f32x2_mul(dt2, f32x2_pack(acc[n], acc[n + 1]));
             if (MODE == kModeStage) rn = f32x2_fma(a2, f32x2_pack(rr[n], rr[n + 1]), rn);
@@ -699,9 +733,9 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
         if (Np & 1) {
           constexpr int n = Np - 1;
           if (MODE == kModeRhs) {
-            rq[n] = acc[n];
+            rq[n] = MEDIA ? srow * acc[n] : acc[n];
           } else {
-            float rn = p.dt * acc[n];
+            float rn = drow * acc[n];
             if (MODE == kModeStage) rn = __fmaf_rn(p.a, rr[n], rn);
             rq[n] = __fmaf_rn(p.b, rn, rq[n]);
             rr[n] = rn;
@@ -714,7 +748,7 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
         const int64_t g = static_cast<int64_t>(c) * fs + static_cast<int64_t>(k0 + e) * Np;
 #pragma unroll
         for (int n = 0; n < Np; ++n) {
-          const float rhs = acc[n];
+          const float rhs = MEDIA && MODE == kModeRhs ? srow * acc[n] : acc[n];
           if (MODE == kModeRhs) {
             if (full_block)
               sq[off + n] = rhs;
@@ -722,7 +756,7 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
               p.rhs[g + n] = rhs;
           } else {
             const float rn =
-                (MODE == kModeFirstStage) ? p.dt * rhs : p.a * sres[off + n] + p.dt * rhs;
+                (MODE == kModeFirstStage) ? drow * rhs : p.a * sres[off + n] + drow * rhs;
             const float qn = sq[off + n] + p.b * rn;
             if (full_block) {
               sq[off + n] = qn;
@@ -746,12 +780,19 @@ __global__ void __launch_bounds__(TcLayout<N, PREC>::THREADS, 1)
   if (warp == 0) tmem_dealloc(tmem, L::TMEM_COLS);
 }
 
-template <int N, int MODE, int PREC>
+template <int N, int MODE, int PREC, bool MEDIA>
+__global__ void __launch_bounds__(TcLayout<N, PREC, MEDIA>::THREADS, 1)
+    dg_stage_tc_kernel(const __grid_constant__ StageArgs<float> p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  tc_stage_body<N, MODE, PREC, MEDIA, false>(p, blockIdx.x, gridDim.x, smem);
+}
+
+template <int N, int MODE, int PREC, bool MEDIA>
 cudaError_t launch_stage_tc_mode(const StageArgs<float>& args, int num_sms, cudaStream_t stream) {
-  using L = TcLayout<N, PREC>;
+  using L = TcLayout<N, PREC, MEDIA>;
   static bool configured = false;
   if (!configured) {
-    cudaError_t err = cudaFuncSetAttribute(dg_stage_tc_kernel<N, MODE, PREC>,
+    cudaError_t err = cudaFuncSetAttribute(dg_stage_tc_kernel<N, MODE, PREC, MEDIA>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(L::SMEM_BYTES));
     if (err != cudaSuccess) return err;
@@ -761,18 +802,80 @@ cudaError_t launch_stage_tc_mode(const StageArgs<float>& args, int num_sms, cuda
   int64_t grid = num_sms;  // one CTA per SM (shared memory and TMEM sized for it)
   if (grid > nblk) grid = nblk;
   if (grid < 1) grid = 1;
-  dg_stage_tc_kernel<N, MODE, PREC>
+  dg_stage_tc_kernel<N, MODE, PREC, MEDIA>
       <<<static_cast<unsigned>(grid), L::THREADS, L::SMEM_BYTES, stream>>>(args);
   return cudaGetLastError();
+}
+
+template <int N, int PREC, bool MEDIA>
+cudaError_t launch_stage_tc_any(const StageArgs<float>& args, int mode, int num_sms,
+                                cudaStream_t stream) {
+  if (mode == kModeRhs)
+    return launch_stage_tc_mode<N, kModeRhs, PREC, MEDIA>(args, num_sms, stream);
+  if (mode == kModeFirstStage)
+    return launch_stage_tc_mode<N, kModeFirstStage, PREC, MEDIA>(args, num_sms, stream);
+  return launch_stage_tc_mode<N, kModeStage, PREC, MEDIA>(args, num_sms, stream);
 }
 
 template <int N, int PREC>
 cudaError_t launch_stage_tc(const StageArgs<float>& args, int mode, int num_sms,
                             cudaStream_t stream) {
-  if (mode == kModeRhs) return launch_stage_tc_mode<N, kModeRhs, PREC>(args, num_sms, stream);
-  if (mode == kModeFirstStage)
-    return launch_stage_tc_mode<N, kModeFirstStage, PREC>(args, num_sms, stream);
-  return launch_stage_tc_mode<N, kModeStage, PREC>(args, num_sms, stream);
+  return launch_stage_tc_any<N, PREC, false>(args, mode, num_sms, stream);
+}
+
+template <int N>
+cudaError_t launch_stage_tc_media(const StageArgs<float>& args, int mode, int num_sms,
+                                  cudaStream_t stream) {
+  return launch_stage_tc_any<N, kTcTf32x3, true>(args, mode, num_sms, stream);
+}
+
+// ------------------------------------------------------------ batched launch
+// One persistent launch over every order group of a batch (BatchArgs):
+// CTA b runs the body of the order whose CTA range holds b, over that
+// group's block table.  Every order's CTA has the same warp layout, so the
+// launch has one block size; its dynamic shared memory is the largest any
+// present order needs.
+constexpr int kTcThreads = TcLayout<5, kTcTf32x3, true>::THREADS;
+
+template <int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    dg_batch_tc_kernel(const __grid_constant__ BatchArgs p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int b = blockIdx.x;
+  // CTA ranges of the order groups, from device memory
+  int c0[8];
+#pragma unroll
+  for (int g = 0; g < 8; ++g) c0[g] = __ldg(p.cta0 + g);
+#define DG_BATCH_GROUP(NN_)                                                              \
+  if (b >= c0[NN_ - 1] && b < c0[NN_]) {                                                 \
+    static_assert(TcLayout<NN_, kTcTf32x3, true>::THREADS == kTcThreads, "block size");   \
+    tc_stage_body<NN_, MODE, kTcTf32x3, true, true>(p.g[NN_ - 1], b - c0[NN_ - 1],        \
+                                                    c0[NN_] - c0[NN_ - 1], smem);        \
+    return;                                                                              \
+  }
+  DG_BATCH_GROUP(1)
+  DG_BATCH_GROUP(2)
+  DG_BATCH_GROUP(3)
+  DG_BATCH_GROUP(4)
+  DG_BATCH_GROUP(5)
+  DG_BATCH_GROUP(6)
+  DG_BATCH_GROUP(7)
+#undef DG_BATCH_GROUP
+}
+
+template <int MODE>
+cudaError_t launch_batch_tc(const BatchArgs& args, int grid, size_t smem, cudaStream_t stream) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t err = cudaFuncSetAttribute(dg_batch_tc_kernel<MODE>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           TcLayout<5, kTcTf32x3, true>::SMAX);
+    if (err != cudaSuccess) return err;
+    configured = true;
+  }
+  if (grid < 1) return cudaSuccess;
+  dg_batch_tc_kernel<MODE><<<grid, kTcThreads, smem, stream>>>(args);
+  return cudaGetLastError();
 }
 
 }  // namespace dgw

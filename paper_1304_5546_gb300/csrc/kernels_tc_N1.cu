@@ -1,6 +1,8 @@
-// Order-1 instantiation of the FP32 tensor-core stage kernel, 3xTF32 products.
+// Order-1 instantiations of the FP32 tensor-core stage kernel with 3xTF32
+// products: uniform medium, and per-element permittivity.
 #include "kernels_tc.cuh"
 
 namespace dgw {
 template cudaError_t launch_stage_tc<1, kTcTf32x3>(const StageArgs<float>&, int, int, cudaStream_t);
+template cudaError_t launch_stage_tc_media<1>(const StageArgs<float>&, int, int, cudaStream_t);
 }  // namespace dgw

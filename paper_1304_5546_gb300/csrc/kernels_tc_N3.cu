@@ -1,6 +1,8 @@
-// Order-3 instantiation of the FP32 tensor-core stage kernel, 3xTF32 products.
+// Order-3 instantiations of the FP32 tensor-core stage kernel with 3xTF32
+// products: uniform medium, and per-element permittivity.
 #include "kernels_tc.cuh"
 
 namespace dgw {
 template cudaError_t launch_stage_tc<3, kTcTf32x3>(const StageArgs<float>&, int, int, cudaStream_t);
+template cudaError_t launch_stage_tc_media<3>(const StageArgs<float>&, int, int, cudaStream_t);
 }  // namespace dgw

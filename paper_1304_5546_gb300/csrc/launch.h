@@ -11,6 +11,26 @@ namespace dgw {
 // geometry record per element: rx ry sx sy, then per face nx ny Fscale/2
 constexpr int kGeo = 13;
 
+// Geometry record per element of an operator with a piecewise-constant
+// permittivity eps_k (mu = 1; Eq. tm-maxwells with variable eps), 20 values:
+//   [0, 4)          rx ry sx sy
+//   [4 + 4f, 8 + 4f) face f: nx, ny, cH = Fscale Z+ / (Z- + Z+),
+//                   cE = Fscale / (Z- + Z+)   (Z = 1 / sqrt(eps), '+' the
+//                   neighbour, Z+ = Z- at a PEC face)
+//   16              Z- of the element
+//   17, 18          row scales sH (Hx, Hy rows) and sE (Ez row): the
+//                   update multiplies the right-hand side by dt * s, so
+//                   sH = 1, sE = 1 / eps_k for a single operator, and a
+//                   batch folds each problem's own time step in
+//                   (sH = dt_p, sE = dt_p / eps_k, launch dt = 1)
+//   19              zero (padding to 80 bytes)
+// With these the upwind flux at a face node is, for the jumps
+// [u] = u- - u+ and [Ht] = ny [Hx] - nx [Hy],
+//   fz = cH [Ht] - cE [Ez];  lifted terms (-Z- ny fz, Z- nx fz, fz)
+// which is Fscale n.(F - F*) of the exact interface Riemann solution, and
+// for eps = 1 everywhere the eps = 1 upwind flux times Fscale / 2.
+constexpr int kGeoMedia = 20;
+
 template <typename T>
 struct StageArgs {
   int64_t K = 0;
@@ -27,6 +47,13 @@ struct StageArgs {
   const T* lam = nullptr;         // [2][Np]: (1 + r_n) / 2, (1 + s_n) / 2 per node
   T a = 0, b = 0, dt = 0;
   int* status = nullptr;  // set to 1 by a CTA whose bounded wait expired
+  // block table of the batched launch: block i of the launch covers
+  // elements [blocks[i].x, blocks[i].x + blocks[i].y), 1 <= y <= E, x a
+  // multiple of 4; the count is read from device memory (*nblocks) so that a
+  // captured graph replays with a changed table.  Unused by the
+  // single-operator launches (blocks of E consecutive elements over [0, K)).
+  const int2* blocks = nullptr;
+  const int* nblocks = nullptr;
   // tensor-core path only: [Dr | Ds | LIFT | 1] as the operator tiles of the
   // launch's product variant (tc_nsplit tiles of tc_nn(N) x tc_kpp(N, prec)
   // elements, TF32 or BF16, in the core-matrix layout of tc_canon /
@@ -88,5 +115,32 @@ __host__ __device__ constexpr int tc_kpp(int N, int prec) {
 template <int N, int PREC>
 cudaError_t launch_stage_tc(const StageArgs<float>& args, int mode, int num_sms,
                             cudaStream_t stream);
+
+// Operators with a per-element permittivity (geometry records of kGeoMedia
+// values): CUDA-core kernel (FP32 / FP64) and tensor-core kernel (3xTF32).
+template <typename T, int N>
+cudaError_t launch_stage_media(const StageArgs<T>& args, int mode, int num_sms,
+                               cudaStream_t stream);
+template <int N>
+cudaError_t launch_stage_tc_media(const StageArgs<float>& args, int mode, int num_sms,
+                                  cudaStream_t stream);
+
+// Batched launch: one persistent launch over the problems of a batch, all
+// orders at once.  Group g (order N = g + 1) runs on CTAs
+// [cta0[g], cta0[g + 1]) over its own block table; groups without CTAs are
+// skipped.  Media records, 3xTF32 products, LSRK stage modes only.
+// The CTA ranges are read from device memory (cta0[0..7]) so that a
+// captured graph replays with a changed split.
+struct BatchArgs {
+  StageArgs<float> g[7];
+  const int* cta0 = nullptr;
+};
+// grid: CTAs of the launch (cta0[7]); smem: the largest
+// batch_tc_smem_bytes of an order that may have CTAs
+template <int MODE>
+cudaError_t launch_batch_tc(const BatchArgs& args, int grid, size_t smem, cudaStream_t stream);
+// shared memory and elements per block of order N's CTA in the batched launch
+size_t batch_tc_smem_bytes(int N);
+int batch_tc_block_elems(int N);
 
 }  // namespace dgw

@@ -17,4 +17,5 @@ from .fields import (  # noqa: F401
     gaussian_pulse,
     cavity_mode,
     random_fields,
+    random_permittivity,
 )

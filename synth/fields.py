@@ -39,3 +39,11 @@ def random_fields(K, Np, seed, scale=1.0):
     """Seeded U(-scale, scale) float64 values for (Hx, Hy, Ez), shape (3, K, Np)."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-scale, scale, size=(3, K, Np))
+
+
+def random_permittivity(K, seed, speeds=(0.5, 1.0, 2.0)):
+    """Seeded piecewise-constant medium: each element's wave speed c drawn
+    uniformly from `speeds`; returns eps = 1 / c^2 per element (mu = 1)."""
+    rng = np.random.default_rng(seed)
+    c = rng.choice(np.asarray(speeds, dtype=np.float64), size=K)
+    return 1.0 / c ** 2

@@ -1,0 +1,180 @@
+"""GPU checks of batches (dg_batch_*): many problems of mixed orders, sizes,
+media and time steps stepped by one persistent launch per stage.
+
+* every problem matches the FP64 oracle stepped alone with its own dt and
+  permittivity (FP32 tolerance 1e-5 relative to max |q|, FP32-rounded start);
+* a problem's result is bit-for-bit the same alone in a batch and in a mix
+  (each element's arithmetic depends only on its own problem);
+* graph replay and direct launches agree bit for bit;
+* problems leave and join between steps (continuous batching): the others
+  carry on unchanged and a newcomer in a freed range starts clean;
+* the autotuner leaves the fields alone and produces a valid CTA split.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import gaussian_pulse, jittered_delaunay_mesh, random_permittivity
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1304_5546_gb300 import build as B
+    B.build()
+    import paper_1304_5546_gb300 as P
+    return P
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+# (mesh n, N, seed): K = 2 n^2 = 98 (not a multiple of 4), 72, 128, 50, 162, 32
+SPECS = [(7, 3, 1), (6, 5, 2), (8, 7, 3), (5, 1, 4), (9, 5, 5), (4, 2, 6)]
+
+
+class _Problem:
+    def __init__(self, P, n, N, seed, dt_scale=0.8):
+        self.mesh = jittered_delaunay_mesh(n, seed=seed)
+        self.N = N
+        self.d = O.Discretization(*self.mesh, N)
+        self.eps = random_permittivity(self.d.K, seed=seed + 100)
+        self.solver = P.Solver(*self.mesh, N=N, precision="fp32", eps=self.eps, host_only=True)
+        self.dt = dt_scale * self.solver.cfl_dt()
+        x0, y0 = 0.3 + 0.05 * (seed % 5), 0.6 - 0.04 * (seed % 4)
+        q = np.stack(gaussian_pulse(self.d.x, self.d.y, x0, y0, 0.2))
+        self.q0 = q.astype(np.float32).astype(np.float64)
+
+    def oracle(self, steps):
+        rhs = lambda u, t: O.maxwell_rhs_media(self.d, u, self.eps)  # noqa: E731
+        q = self.q0
+        for n in range(steps):
+            q = O.lsrk_step(self.d, q, n * self.dt, self.dt, rhs=rhs)
+        return q
+
+
+def _capacity(probs, extra=0):
+    cap = [0] * 7
+    for p in probs:
+        cap[p.N - 1] += (p.d.K + 3) // 4 * 4 + extra
+    return cap
+
+
+@pytest.fixture(scope="module")
+def problems(P):
+    return [_Problem(P, *s) for s in SPECS]
+
+
+def _run(P, probs, steps, graph=True, tune=False):
+    b = P.Batch(_capacity(probs), graph=graph)
+    slots = []
+    for p in probs:
+        slot = b.add(p.solver, p.dt)
+        b.set_fields(slot, p.q0)
+        slots.append(slot)
+    if tune:
+        b.tune(reps=2)
+    b.step(steps)
+    b.sync_check()
+    out = [b.get_fields(s) for s in slots]
+    assert b.launch_count() >= 5 * steps
+    b.close()
+    return out
+
+
+def test_batch_matches_oracle(P, problems):
+    steps = 3
+    got = _run(P, problems, steps)
+    for p, g in zip(problems, got):
+        want = p.oracle(steps)
+        assert _rel(g, want) <= TOL, (p.N, p.d.K, _rel(g, want))
+
+
+def test_alone_equals_in_mix_bitwise(P, problems):
+    steps = 2
+    mix = _run(P, problems, steps)
+    for i in (0, 2, 4):
+        alone = _run(P, [problems[i]], steps)[0]
+        assert np.array_equal(alone, mix[i]), i
+
+
+def test_graph_equals_direct_launches(P, problems):
+    a = _run(P, problems[:4], 2, graph=True)
+    b = _run(P, problems[:4], 2, graph=False)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_leave_and_join_between_steps(P, problems):
+    p0, p1, p2 = problems[0], problems[4], problems[1]  # N = 3, 5, 5
+    cap = _capacity([p0, p1], extra=0)
+    cap[4] = max(cap[4], (p2.d.K + 3) // 4 * 4)  # p2 fits where p1 was
+    b = P.Batch(cap)
+    s0 = b.add(p0.solver, p0.dt)
+    b.set_fields(s0, p0.q0)
+    s1 = b.add(p1.solver, p1.dt)
+    b.set_fields(s1, p1.q0)
+    b.step(2)
+    got1 = b.get_fields(s1)
+    b.remove(s1)
+    s2 = b.add(p2.solver, p2.dt)  # reuses the freed range
+    b.set_fields(s2, p2.q0)
+    b.step(1)
+    b.sync_check()
+    got0 = b.get_fields(s0)
+    got2 = b.get_fields(s2)
+    b.close()
+    assert _rel(got1, p1.oracle(2)) <= TOL
+    assert _rel(got0, p0.oracle(3)) <= TOL
+    assert _rel(got2, p2.oracle(1)) <= TOL
+
+
+def test_tune_keeps_fields_and_plans_valid_split(P, problems):
+    import torch
+    b = P.Batch(_capacity(problems))
+    slots = []
+    for p in problems:
+        s = b.add(p.solver, p.dt)
+        b.set_fields(s, p.q0)
+        slots.append(s)
+    b.step(1)
+    before = [b.get_fields(s) for s in slots]
+    b.tune(reps=2)
+    after = [b.get_fields(s) for s in slots]
+    for x, y in zip(before, after):
+        assert np.array_equal(x, y)
+    cta, nblk, cost = b.plan()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert cta.sum() <= sms
+    for g in range(7):
+        assert (cta[g] >= 1) == (nblk[g] > 0)
+        assert cta[g] <= max(nblk[g], 0) or nblk[g] == 0
+        if nblk[g]:
+            assert cost[g] > 0
+    # stepping after the tune still matches the oracle
+    b.step(1)
+    b.sync_check()
+    for p, s in zip(problems, slots):
+        assert _rel(b.get_fields(s), p.oracle(2)) <= TOL
+    b.close()
+
+
+def test_batch_rejects_bad_use(P, problems):
+    from paper_1304_5546_gb300 import DGError
+    p = problems[0]  # N = 3
+    b = P.Batch({5: 64})
+    with pytest.raises(DGError):
+        b.add(p.solver, p.dt)  # no capacity for N = 3
+    small = P.Batch({3: 8})
+    with pytest.raises(DGError):
+        small.add(p.solver, p.dt)  # K = 98 > 8
+    with pytest.raises(DGError):
+        small.remove(0)
+    b.close()
+    small.close()
