@@ -408,6 +408,55 @@ def run_precision_study(args):
             "variants": table}
 
 
+def run_sweep_study(args):
+    """Order sweep of the single-mesh path at about 10M nodal values per
+    field (K ~ 1e7 / Np): for N = 1..7, the FP32 tensor-core kernel and the
+    FP32 CUDA-core kernel, `--study-steps` LSRK steps each timed with CUDA
+    events.  One JSON line: ms/step, element-stage updates/s, RHS GFLOP/s
+    and achieved HBM bandwidth (algorithmic bytes) per order and kernel."""
+    import numpy as np
+    import torch
+
+    import paper_1304_5546_gb300 as P
+    from synth import gaussian_pulse, jittered_delaunay_mesh, n_for_target_elements
+
+    torch.cuda.set_device(0)
+    peaks, peak_kind = measured_peaks()
+    steps = args.study_steps
+    rows = []
+    for N in args.sweep_orders:
+        Np = (N + 1) * (N + 2) // 2
+        n = n_for_target_elements(1e7 / Np)
+        mesh = jittered_delaunay_mesh(n, seed=2024)
+        for simt in (False, True):
+            s = P.Solver(*mesh, N=N, precision="fp32simt" if simt else "fp32tc")
+            x, y = s.nodes()
+            q = s.from_numpy(np.stack(gaussian_pulse(x, y)))
+            res = s.new_fields()
+            dt = s.cfl_dt()
+            s.step(q, res, dt, 3)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            s.step(q, res, dt, steps)
+            b.record()
+            b.synchronize()
+            P.dg_sync_check(s.op)
+            ms = a.elapsed_time(b) / steps
+            K = s.K
+            gbs = K * step_bytes_per_element(N) / (ms / 1e3) / 1e9
+            rows.append({"N": N, "K": K, "kernel": "cuda cores" if simt else "tensor cores (3xTF32)",
+                         "ms_per_step": ms, "element_stage_per_s": K * 5 / (ms / 1e3),
+                         "rhs_gflops": K * rhs_flops_per_element(N) * 5 / (ms / 1e3) / 1e9,
+                         "hbm_gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"]})
+            s.close()
+    return {"study": "order sweep", "nodal_values_per_field": "~1e7", "steps": steps,
+            "peak_hbm_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind,
+            "bytes_per_element_step": {str(N): step_bytes_per_element(N) for N in range(1, 8)},
+            "rows": rows}
+
+
 def batched_workload(n_problems=256, seed=4242, k_lo=500, k_hi=50000, orders=(3, 5, 7),
                      speeds=(0.5, 1.0, 2.0)):
     """Seeded batch of independent problems: K log-uniform in [k_lo, k_hi]
@@ -583,10 +632,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--_oracle-sample", nargs=3, default=None)
-    ap.add_argument("--study", choices=["precision"], default=None,
+    ap.add_argument("--study", choices=["precision", "sweep"], default=None,
                     help="instead of the benchmark line: the precision-path study "
                          "(use with --order 7 --n 362 for K = 262,088)")
     ap.add_argument("--study-steps", type=int, default=500)
+    ap.add_argument("--sweep-orders", type=int, nargs="+", default=list(range(1, 8)))
     ap.add_argument("--workload", choices=["single", "batched"], default="single",
                     help="single: the large-mesh benchmark line (default); batched: many "
                          "mixed-order problems in one launch per stage vs sequential solves")
@@ -601,6 +651,9 @@ def main(argv=None):
         return 0
     if args.study == "precision":
         print(json.dumps(run_precision_study(args)), flush=True)
+        return 0
+    if args.study == "sweep":
+        print(json.dumps(run_sweep_study(args)), flush=True)
         return 0
     if args.workload == "batched" and args.impl == "ours":
         print(json.dumps(run_batched(args)), flush=True)

@@ -88,6 +88,9 @@ typedef int32_t dg_status;
 #define DG_SETUP_TC_BF16 8   /* one product, both operands rounded to BF16   */
 #define DG_SETUP_TC_BF16X3 16 /* three BF16 products: hi/lo split of both
                                  operands (X_hi Op_hi + X_hi Op_lo + X_lo Op_hi) */
+/* Default FP32 products per order: the tensor cores (3xTF32) from N = 3 on,
+ * the CUDA cores at N <= 2, where that kernel measured faster.  Override: */
+#define DG_SETUP_TC 32       /* FP32: tensor cores (3xTF32) at every order   */
 
 #define DG_N_MAX 7
 
@@ -129,8 +132,9 @@ void dg_mesh_destroy(dg_mesh* mesh);
  * Fscale = surface Jacobian / volume Jacobian (Section "Computing the
  * Surface Contribution"), and the trace maps.  FP32 operators run the
  * element-local products (Dr, Ds, LIFT) on the tensor cores as three TF32
- * products per term (hi/lo splits of both operands, FP32 accumulation);
- * flags DG_SETUP_SIMT selects the CUDA-core FP32 kernel instead, and one
+ * products per term (hi/lo splits of both operands, FP32 accumulation) from
+ * N = 3 on and on the CUDA cores at N <= 2 (DG_SETUP_TC: tensor cores at
+ * every order); flags DG_SETUP_SIMT selects the CUDA-core FP32 kernel, and one
  * of DG_SETUP_TC_TF32 / _BF16 / _BF16X3 a lower-precision product variant
  * (the precision path of the element-local contractions).  FP64
  * operators always use the CUDA cores.  Unless flags has
@@ -139,7 +143,8 @@ void dg_mesh_destroy(dg_mesh* mesh);
  * The operator keeps its own copy of the mesh data; the mesh may be
  * destroyed afterwards.
  * Errors: DG_ERR_ARG (unknown flags; more than one product variant, or one
- * with DG_FP64 or DG_SETUP_SIMT; also when a field would hold 2^31 or more values:
+ * with DG_FP64 or DG_SETUP_SIMT; DG_SETUP_TC with DG_FP64 or DG_SETUP_SIMT;
+ * also when a field would hold 2^31 or more values:
  * kernel offsets inside a field are 32-bit), DG_ERR_ORDER (N < 1 or
  * N > DG_N_MAX), DG_ERR_CUDA, DG_ERR_OOM.  *out is written only on success. */
 dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t precision,

@@ -28,6 +28,7 @@ DG_SETUP_SIMT = 2
 DG_SETUP_TC_TF32 = 4
 DG_SETUP_TC_BF16 = 8
 DG_SETUP_TC_BF16X3 = 16
+DG_SETUP_TC = 32
 DG_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 DG_BATCH_NO_GRAPH = 1
 DG_N_MAX = 7

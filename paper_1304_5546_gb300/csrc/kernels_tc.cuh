@@ -63,7 +63,7 @@ struct TcLayout {
   static constexpr int Np = Order<N>::Np;
   static constexpr int Nfp = Order<N>::Nfp;
   static constexpr int Nafp = Order<N>::Nafp;
-  static constexpr int E = (N == 7) ? 24 : 40;  // 3E <= 128 GEMM rows, E % 4 == 0
+  static constexpr int E = 40;  // 3E <= 128 GEMM rows, E % 4 == 0
   static constexpr int ROWS = 3 * E;
   static constexpr int KD = tc_kd(N), KP = tc_kpp(N, PREC);
   static constexpr int EB = BF ? 2 : 4;         // operand element bytes
@@ -74,11 +74,16 @@ struct TcLayout {
   static constexpr int IV = NPAD / 4;          // volume chunks of 4 nodes
   static constexpr int LCOLS = KP - 2 * NPAD;  // LIFT-part columns (zero beyond Nafp)
   // tensor memory: two accumulators, then XBUF operand buffers of NS parts.
-  // Split variants: an accumulator has 2 NN columns, [0, NN) holding
-  // X_hi Op_hi + X_lo Op_hi and [NN, 2 NN) holding X_hi Op_lo; an operand
-  // buffer holds X_hi, then X_lo.  Single-product variants: NN columns, X.
-  static constexpr int ACC_COLS = NS == 2 ? 2 * NN : NN;
+  // Split variants (ACC_SPLIT): an accumulator has 2 NN columns, [0, NN)
+  // holding X_hi Op_hi + X_lo Op_hi and [NN, 2 NN) holding X_hi Op_lo (one
+  // MMA of N = 2 NN reads X_hi once for both operator tiles); where that
+  // leaves no room for two operand buffers (N = 7) all three products go to
+  // the same NN columns instead, so that operand building and MMAs still
+  // overlap.  An operand buffer holds X_hi, then X_lo.  Single-product
+  // variants: NN columns, X.
   static constexpr int XCOLS = NS * XPART;
+  static constexpr bool ACC_SPLIT = NS == 2 && 2 * (2 * NN) + 2 * XCOLS <= 512;
+  static constexpr int ACC_COLS = ACC_SPLIT ? 2 * NN : NN;
   static constexpr int XBUF = (2 * ACC_COLS + 2 * XCOLS <= 512) ? 2 : 1;
   static constexpr int OFF_XT = 2 * ACC_COLS;
   static constexpr int TMEM_COLS = 512;
@@ -427,8 +432,9 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
       constexpr uint32_t IDESC2 =                // B = [Op_hi ; Op_lo]
           L::BF ? umma_idesc_bf16(128, 2 * NN) : umma_idesc_tf32(128, 2 * NN);
       constexpr uint32_t IDESC1 = L::BF ? umma_idesc_bf16(128, NN) : umma_idesc_tf32(128, NN);
-      auto mma = [&](uint32_t d, uint32_t a, int ks, uint32_t idesc, uint32_t acc) {
-        const uint64_t bd = umma_desc(oaddr + ks * 256, LBO, SBO);
+      auto mma = [&](uint32_t d, uint32_t a, int ks, uint32_t idesc, uint32_t acc,
+                     uint32_t b_off = 0) {  // b_off: byte offset of the operator tile
+        const uint64_t bd = umma_desc(oaddr + b_off + ks * 256, LBO, SBO);
         if constexpr (L::BF)
           umma_bf16_ta(d, a, bd, idesc, acc);
         else
@@ -445,12 +451,22 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
         tc_fence_after();
         const uint32_t dacc = tmem + static_cast<uint32_t>((j & 1) * L::ACC_COLS);
         const uint32_t xh = tmem + static_cast<uint32_t>(L::OFF_XT + xb * L::XCOLS);
-        if constexpr (L::NS == 2) {
+        if constexpr (L::NS == 2 && L::ACC_SPLIT) {
 #pragma unroll
           for (int ks = 0; ks < KS; ++ks)  // X_hi [Op_hi ; Op_lo] -> columns [0, 2 NN)
             mma(dacc, xh + 8 * ks, ks, IDESC2, ks > 0 ? 1u : 0u);
 #pragma unroll
           for (int ks = 0; ks < KS; ++ks)  // + X_lo Op_hi -> columns [0, NN)
+            mma(dacc, xh + L::XPART + 8 * ks, ks, IDESC1, 1u);
+        } else if constexpr (L::NS == 2) {
+#pragma unroll
+          for (int ks = 0; ks < KS; ++ks)  // X_hi Op_hi -> columns [0, NN)
+            mma(dacc, xh + 8 * ks, ks, IDESC1, ks > 0 ? 1u : 0u);
+#pragma unroll
+          for (int ks = 0; ks < KS; ++ks)  // + X_hi Op_lo (the lo tile follows the hi tile)
+            mma(dacc, xh + 8 * ks, ks, IDESC1, 1u, L::OB);
+#pragma unroll
+          for (int ks = 0; ks < KS; ++ks)  // + X_lo Op_hi
             mma(dacc, xh + L::XPART + 8 * ks, ks, IDESC1, 1u);
         } else {
 #pragma unroll
@@ -678,7 +694,7 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
                             (static_cast<uint32_t>(32 * warp) << 16);
 #pragma unroll
       for (int c0 = 0; c0 < NN; c0 += 16) {
-        if constexpr (L::NS == 2) {
+        if constexpr (L::NS == 2 && L::ACC_SPLIT) {
           float va[16], vb[16];
           tmem_ld16(dacc + c0, va);       // X_hi Op_hi + X_lo Op_hi
           tmem_ld16(dacc + NN + c0, vb);  // X_hi Op_lo

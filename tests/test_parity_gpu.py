@@ -13,7 +13,7 @@ from synth import (cavity_mode, gaussian_pulse, jittered_delaunay_mesh, random_f
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp32simt": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp32simt": 1e-5, "fp32tc": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +34,7 @@ def _solver(P, mesh, N, prec):
     return P.Solver(*mesh, N=N, precision=prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32simt"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32simt", "fp32tc"])
 @pytest.mark.parametrize("N", list(range(1, 8)))
 def test_rhs_parity_random_fields(P, N, prec):
     # 2 * 9^2 = 162 elements: several CTAs and a ragged last block at every N
@@ -48,7 +48,7 @@ def test_rhs_parity_random_fields(P, N, prec):
     assert _rel(got, want) <= TOL[prec], _rel(got, want)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32simt"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32simt", "fp32tc"])
 @pytest.mark.parametrize("N", [1, 3, 5, 7])
 def test_lsrk_steps_parity(P, N, prec):
     mesh = jittered_delaunay_mesh(8, seed=7 * N)
