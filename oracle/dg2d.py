@@ -551,6 +551,58 @@ def maxwell_rhs_media(d, q, eps):
     return np.stack([rhsHx, rhsHy, rhsEz])
 
 
+def ricker(t, f=10.0, t0=None, amplitude=1.0):
+    """Ricker wavelet s(t) = A (1 - 2 pi^2 f^2 tau^2) exp(-pi^2 f^2 tau^2),
+    tau = t - t0, peak frequency f; t0 defaults to 1.2 / f (reading: the
+    source term f of the problem statement is unspecified there)."""
+    if t0 is None:
+        t0 = 1.2 / f
+    a = (math.pi * f * (np.asarray(t, dtype=np.float64) - t0)) ** 2
+    return amplitude * (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def locate_point(d, xs, ys):
+    """Element k that contains (xs, ys) (barycentric coordinates of its three
+    vertices all >= -1e-12; the lowest such k) and the point's reference
+    coordinates (r, s) under that element's affine map
+    x = (-(r+s) v1 + (1+r) v2 + (1+s) v3) / 2."""
+    x = d.VX[d.EToV]
+    y = d.VY[d.EToV]
+    det = (x[:, 1] - x[:, 0]) * (y[:, 2] - y[:, 0]) - (x[:, 2] - x[:, 0]) * (y[:, 1] - y[:, 0])
+    l2 = ((xs - x[:, 0]) * (y[:, 2] - y[:, 0]) - (x[:, 2] - x[:, 0]) * (ys - y[:, 0])) / det
+    l3 = ((x[:, 1] - x[:, 0]) * (ys - y[:, 0]) - (xs - x[:, 0]) * (y[:, 1] - y[:, 0])) / det
+    l1 = 1.0 - l2 - l3
+    inside = np.nonzero((l1 >= -1e-12) & (l2 >= -1e-12) & (l3 >= -1e-12))[0]
+    if inside.size == 0:
+        raise ValueError("point outside the mesh")
+    k = int(inside[0])
+    return k, 2.0 * l2[k] - 1.0, 2.0 * l3[k] - 1.0
+
+
+def point_source_weights(d, xs, ys):
+    """Projection of the point load delta(x - x_s) onto the nodal basis of
+    the element k that contains x_s: the field w on element k with
+    integral_k w v = v(x_s) for every polynomial v of degree <= N, i.e.
+    w = M^-1 l(x_s) / J_k, where l(x_s) holds the Lagrange basis functions of
+    the element's nodes at x_s (l = V^-T psi(r_s, s_s), psi the orthonormal
+    basis) and M^-1 = V V^T.  Returns (k, w[Np])."""
+    k, r, s = locate_point(d, xs, ys)
+    R = d.ref
+    psi = vandermonde_2d(R.N, np.array([r]), np.array([s]))[0]
+    lag = np.linalg.solve(R.V.T, psi)
+    w = R.V @ (R.V.T @ lag) / d.J[k, 0]
+    return k, w
+
+
+def point_source_rhs(d, k, w, amplitude):
+    """Right-hand-side contribution amplitude * w on the Ez field of element
+    k (reading: the source adds to dEz/dt directly, after any division by
+    eps)."""
+    out = np.zeros((3, d.K, d.Np))
+    out[2, k] = amplitude * np.asarray(w)
+    return out
+
+
 def energy_media(d, q, eps):
     """1/2 sum_k J_k (Hx^T M Hx + Hy^T M Hy + eps_k Ez^T M Ez)."""
     M = d.ref.M

@@ -34,7 +34,12 @@ RHS = _load("test_oracle_rhs")
 ELEM = _load("test_oracle_element")
 MESH = _load("test_oracle_mesh")
 LSRK = _load("test_oracle_lsrk")
+MEDIA = _load("test_oracle_media")
+SRC = _load("test_oracle_source")
 JIT4 = jittered_delaunay_mesh(4, seed=5)
+
+MEDIA_PIN_UNIT = MEDIA.test_unit_permittivity_is_the_homogeneous_upwind_rhs
+MEDIA_PIN_RIEMANN = MEDIA.test_interface_flux_is_the_riemann_solution
 
 # pins, cheapest first; each is a call that raises when the pin fails
 PINS = [
@@ -54,6 +59,11 @@ PINS = [
     ("operator spectrum", lambda: RHS.test_brute_force_operator_spectrum(2)),
     ("permutation invariance", RHS.test_permutation_invariance),
     ("cavity mode", RHS.test_cavity_mode_config_one),
+    ("media: unit eps", MEDIA_PIN_UNIT),
+    ("media: interface Riemann", MEDIA_PIN_RIEMANN),
+    ("media: dissipative weighted operator", lambda: MEDIA.test_weighted_operator_is_dissipative(2)),
+    ("ricker closed forms", SRC.test_ricker_closed_forms),
+    ("point source point values", lambda: SRC.test_point_source_reproduces_point_values(3)),
 ]
 
 
@@ -93,6 +103,15 @@ def _ref(old, new):
                                     _mutated(D.ReferenceElement.__init__, old, new))
 
 
+def _media(old, new):
+    return lambda mp: _patch_function(mp, "maxwell_rhs_media",
+                                      _mutated(D.maxwell_rhs_media, old, new))
+
+
+def _src(fn, old, new):
+    return lambda mp: _patch_function(mp, fn, _mutated(getattr(D, fn), old, new))
+
+
 def _lsrk_b_digit(mp):
     b = D.LSRK_B.copy()
     b[2] *= 1.0 + 1e-9  # one wrong digit in a coefficient
@@ -130,6 +149,15 @@ MUTANTS = [
                                     "self.M = np.linalg.inv(self.V.T @ self.V)")),
     ("LSRK b coefficient digit", _lsrk_b_digit),
     ("LSRK published c4", _lsrk_published_c),
+    ("media: Z+ and Z- swapped", _media("fEz = (ZP * jHt - jEz) / (ZM + ZP)",
+                                        "fEz = (ZM * jHt - jEz) / (ZM + ZP)")),
+    ("media: Ez not divided by eps", _media(") / eps[:, None]", ") / 1.0")),
+    ("source: no 1/J", _src("point_source_weights", "/ d.J[k, 0]", "/ 1.0")),
+    ("source: Lagrange values via V", _src("point_source_weights",
+                                           "np.linalg.solve(R.V.T, psi)", "np.linalg.solve(R.V, psi)")),
+    ("source: wrong reference coordinate", _src("locate_point", "2.0 * l3[k] - 1.0",
+                                                "2.0 * l1[k] - 1.0")),
+    ("ricker: factor 2 dropped", _src("ricker", "(1.0 - 2.0 * a)", "(1.0 - a)")),
 ]
 
 
