@@ -319,16 +319,36 @@ dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_batch** out
 /* Waits for the device, then frees the batch and its device memory.      */
 void dg_batch_destroy(dg_batch* batch);
 
+/* A point source for dg_batch_add: the source term f of the problem
+ * statement (which the paper leaves unspecified), read as
+ *     dEz/dt += s(t) delta(x - (x, y)),
+ *     s(t) = amplitude (1 - 2 a^2) exp(-a^2),  a = pi f (t - t0)
+ * (a Ricker wavelet of peak frequency f), t measured from the problem's
+ * first step.  The delta is projected onto the nodal basis of the element
+ * that contains the point (the lowest-numbered one, barycentric coordinates
+ * >= -1e-12): w = M^-1 l(x_s) / J_k, l the element's Lagrange basis at the
+ * point; the Ez right-hand side of that element gains s(t) w, after the
+ * division by eps.  Stage times are t_n + c_i dt.                           */
+typedef struct dg_point_source {
+  double x, y;       /* location, inside the mesh                          */
+  double f;          /* peak frequency, > 0                                */
+  double t0;         /* time of the peak (1.2 / f is customary)            */
+  double amplitude;  /* peak value of s                                    */
+} dg_point_source;
+
 /* dg_batch_add: admit the problem of operator `op` (DG_FP32; set up on any
  * device or host-only: the batch copies what it needs from the operator's
  * host data, and the operator may be destroyed afterwards) with time step
- * dt (<= 0: the operator's dg_cfl_dt with cfl = 1).  Its geometry is
- * uploaded asynchronously on `stream`.  Its fields are unspecified until
- * dg_batch_set_fields; it is stepped by every later dg_batch_step.  Writes
- * the problem's slot number.
- * Errors: DG_ERR_ARG (NULL, not DG_FP32, no capacity for its order),
- * DG_ERR_OOM (no free range of its size in the pool), DG_ERR_CUDA.        */
-dg_status dg_batch_add(dg_batch* batch, const dg_op* op, double dt, void* stream, int32_t* slot);
+ * dt (<= 0: the operator's dg_cfl_dt with cfl = 1) and an optional point
+ * source (NULL: none; copied).  Its geometry is uploaded asynchronously on
+ * `stream`.  Its fields are unspecified until dg_batch_set_fields; it is
+ * stepped by every later dg_batch_step, its time starting at 0 with the
+ * first of them.  Writes the problem's slot number.
+ * Errors: DG_ERR_ARG (NULL, not DG_FP32, no capacity for its order, bad
+ * source parameters or a source point outside the mesh), DG_ERR_OOM (no
+ * free range of its size in the pool), DG_ERR_CUDA.                       */
+dg_status dg_batch_add(dg_batch* batch, const dg_op* op, double dt, const dg_point_source* src,
+                       void* stream, int32_t* slot);
 
 /* dg_batch_remove: the problem in `slot` leaves the batch; its range of the
  * pool and its slot number become free.  Copy its fields out first.       */
@@ -382,7 +402,9 @@ dg_status dg_batch_plan_ctas(const int64_t* nblocks, const double* cost, int32_t
  * status word (DG_ERR_TIMEOUT after an expired bounded wait).             */
 dg_status dg_batch_sync_check(dg_batch* batch, void* stream);
 
-/* Stage launches enqueued by the batch (five per step).                   */
+/* Kernel launches enqueued by the batch: per step five stage launches and
+ * one single-thread launch that advances the step counter the point sources
+ * read.                                                                   */
 int64_t dg_batch_launch_count(const dg_batch* batch);
 
 /* dg_check_finite: synchronises `stream`, then scans the first K*Np values

@@ -227,10 +227,14 @@ def dg_batch_destroy(batch):
         _lib.load().dg_batch_destroy(batch)
 
 
-def dg_batch_add(batch, op, dt=0.0, stream=None):
+def dg_batch_add(batch, op, dt=0.0, source=None, stream=None):
+    """source: None or (x, y, f, t0, amplitude) of a Ricker point source."""
     slot = ctypes.c_int32()
-    _lib.check(_lib.load().dg_batch_add(batch, op, dt, _stream_handle(stream), ctypes.byref(slot)),
-               "dg_batch_add")
+    src = None
+    if source is not None:
+        src = ctypes.byref(_lib.dg_point_source(*[float(v) for v in source]))
+    _lib.check(_lib.load().dg_batch_add(batch, op, dt, src, _stream_handle(stream),
+                                        ctypes.byref(slot)), "dg_batch_add")
     return slot.value
 
 
@@ -423,9 +427,10 @@ class Batch:
         except Exception:
             pass
 
-    def add(self, solver_or_op, dt=0.0, stream=None):
+    def add(self, solver_or_op, dt=0.0, source=None, stream=None):
+        """source: None or (x, y, f, t0, amplitude) of a Ricker point source."""
         op = solver_or_op.op if hasattr(solver_or_op, "op") else solver_or_op
-        return dg_batch_add(self.batch, op, dt, stream)
+        return dg_batch_add(self.batch, op, dt, source, stream)
 
     def remove(self, slot):
         dg_batch_remove(self.batch, slot)

@@ -40,6 +40,11 @@ _STATUS_NAMES = {
 }
 
 c_void_p = ctypes.c_void_p
+
+
+class dg_point_source(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_double), ("y", ctypes.c_double), ("f", ctypes.c_double),
+                ("t0", ctypes.c_double), ("amplitude", ctypes.c_double)]
 c_i32 = ctypes.c_int32
 c_i64 = ctypes.c_int64
 c_dbl = ctypes.c_double
@@ -71,7 +76,7 @@ SIGNATURES = [
     ("dg_launch_count", c_i64, [c_void_p]),
     ("dg_batch_create", c_i32, [c_void_p, c_i32, P(c_void_p)]),
     ("dg_batch_destroy", None, [c_void_p]),
-    ("dg_batch_add", c_i32, [c_void_p, c_void_p, c_dbl, c_void_p, P(c_i32)]),
+    ("dg_batch_add", c_i32, [c_void_p, c_void_p, c_dbl, c_void_p, c_void_p, P(c_i32)]),
     ("dg_batch_remove", c_i32, [c_void_p, c_i32]),
     ("dg_batch_info", c_i32, [c_void_p, c_i32, P(c_i32), P(c_i64), P(c_dbl), P(c_i64)]),
     ("dg_batch_set_fields", c_i32, [c_void_p, c_i32, c_void_p, c_i64, c_void_p]),

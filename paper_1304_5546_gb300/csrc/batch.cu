@@ -114,6 +114,7 @@ struct Pool {
 
 struct Problem {
   bool live = false;
+  bool source = false;
   int N = 0;
   int64_t K = 0, off = 0, len = 0;
   double dt = 0.0;
@@ -126,8 +127,15 @@ struct dg_batch {
   int num_sms = 0;
   int flags = 0;
   Pool pools[kOrders];
-  int* d_meta = nullptr;  // [0, 7): block counts per order, [8, 16): CTA split cta0
+  int* d_meta = nullptr;  // [0, 7): block counts per order, [8, 16): CTA split cta0,
+                          // [16]: steps completed (stage time of the point sources)
   int* d_status = nullptr;
+  // point sources, indexed by problem slot
+  int64_t max_slots = 0;
+  float* d_src_w = nullptr;      // [slot][kSrcStride]
+  double* d_src_meta = nullptr;  // [slot][4]: dt, t0, pi f, amplitude
+  int* d_src_step = nullptr;     // [slot]: steps enqueued when the problem joined
+  int64_t steps = 0;             // steps enqueued so far
   std::vector<Problem> probs;
   int cur = 0;  // ping-pong buffer holding the current fields
   bool dirty = true;
@@ -205,6 +213,9 @@ void destroy_batch(dg_batch* b) {
   for (Pool& p : b->pools) free_pool(p);
   if (b->d_meta) cudaFree(b->d_meta);
   if (b->d_status) cudaFree(b->d_status);
+  if (b->d_src_w) cudaFree(b->d_src_w);
+  if (b->d_src_meta) cudaFree(b->d_src_meta);
+  if (b->d_src_step) cudaFree(b->d_src_step);
   b->staging.release();
   delete b;
 }
@@ -306,9 +317,26 @@ dgw::BatchArgs batch_args(const dg_batch* b, int src, int stage) {
     s.a = static_cast<float>(b->lsrk_a[stage]);
     s.b = static_cast<float>(b->lsrk_b[stage]);
     s.dt = 1.0f;  // each problem's step is in its row scales
+    s.src_w = b->d_src_w;
+    s.src_meta = b->d_src_meta;
+    s.src_step = b->d_src_step;
+    s.step_ctr = b->d_meta + 16;
+    s.c_stage = b->lsrk_c[stage];
   }
   a.cta0 = b->d_meta + 8;
   return a;
+}
+
+// end of a step: the device step counter that the source times read
+__global__ void batch_tick_kernel(int* ctr) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *ctr += 1;
+}
+
+cudaError_t launch_tick(dg_batch* b, cudaStream_t s) {
+  batch_tick_kernel<<<1, 32, 0, s>>>(b->d_meta + 16);
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess) ++b->launches;
+  return err;
 }
 
 cudaError_t launch_stage(dg_batch* b, int src, int stage, cudaStream_t s) {
@@ -384,6 +412,7 @@ dg_status capture_graphs(dg_batch* b) {
     const int64_t before = b->launches;
     cudaError_t lerr = cudaSuccess;
     for (int i = 0; i < 5 && lerr == cudaSuccess; ++i) lerr = launch_stage(b, src ^ (i & 1), i, b->capture);
+    if (lerr == cudaSuccess) lerr = launch_tick(b, b->capture);
     b->launches = before;  // captured, not run
     err = cudaStreamEndCapture(b->capture, &graph);
     if (lerr != cudaSuccess) err = lerr;
@@ -455,8 +484,15 @@ extern "C" dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_
     b->smem = std::max(b->smem, b->pools[g].smem);
     b->cost[g] = model_cost(g + 1, b->pools[g].E);
   }
-  err = cudaMalloc(reinterpret_cast<void**>(&b->d_meta), 16 * sizeof(int));
-  if (err == cudaSuccess) err = cudaMemset(b->d_meta, 0, 16 * sizeof(int));
+  for (int g = 0; g < kOrders; ++g) b->max_slots += capacity[g] > 0 ? capacity[g] / 4 + 1 : 0;
+  err = cudaMalloc(reinterpret_cast<void**>(&b->d_meta), 17 * sizeof(int));
+  if (err == cudaSuccess) err = cudaMemset(b->d_meta, 0, 17 * sizeof(int));
+  if (err == cudaSuccess)
+    err = cudaMalloc(reinterpret_cast<void**>(&b->d_src_w), b->max_slots * dgw::kSrcStride * 4);
+  if (err == cudaSuccess)
+    err = cudaMalloc(reinterpret_cast<void**>(&b->d_src_meta), b->max_slots * 4 * sizeof(double));
+  if (err == cudaSuccess)
+    err = cudaMalloc(reinterpret_cast<void**>(&b->d_src_step), b->max_slots * sizeof(int));
   if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(b->d_status, 0, sizeof(int));
   if (err != cudaSuccess) {
@@ -469,8 +505,8 @@ extern "C" dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_
 
 extern "C" void dg_batch_destroy(dg_batch* b) { destroy_batch(b); }
 
-extern "C" dg_status dg_batch_add(dg_batch* b, const dg_op* op, double dt, void* stream,
-                                  int32_t* slot) {
+extern "C" dg_status dg_batch_add(dg_batch* b, const dg_op* op, double dt,
+                                  const dg_point_source* src, void* stream, int32_t* slot) {
   dgw::clear_error();
   dg_status st = check_batch(b, "dg_batch_add");
   if (st) return st;
@@ -482,6 +518,26 @@ extern "C" dg_status dg_batch_add(dg_batch* b, const dg_op* op, double dt, void*
     return fail(DG_ERR_ARG, "dg_batch_add: the batch has no capacity for order N = %d", op->N);
   if (!(dt > 0.0)) dt = (2.0 / 3.0) * op->min_inradius_over_c * op->ref.lgl_gap;
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dg_batch_add: dt is not finite");
+  int64_t src_k = -1;
+  std::vector<double> src_wt;
+  if (src) {
+    if (!std::isfinite(src->x) || !std::isfinite(src->y) || !(src->f > 0.0) ||
+        !std::isfinite(src->t0) || !std::isfinite(src->amplitude))
+      return fail(DG_ERR_ARG, "dg_batch_add: bad point source parameters");
+    src_k = dgw::point_source(op->ref, op->geo, op->K, src->x, src->y, src_wt);
+    if (src_k < 0)
+      return fail(DG_ERR_ARG, "dg_batch_add: source point (%g, %g) is outside the mesh", src->x,
+                  src->y);
+  }
+  // slot: the lowest free number (below max_slots: every live problem holds
+  // at least 4 elements of some pool)
+  int32_t id = -1;
+  for (size_t i = 0; i < b->probs.size(); ++i)
+    if (!b->probs[i].live) {
+      id = static_cast<int32_t>(i);
+      break;
+    }
+  if (id < 0) id = static_cast<int32_t>(b->probs.size());
   const int64_t K = op->K, len = (K + 3) / 4 * 4;
   const int64_t off = take_range(p, len);
   if (off < 0)
@@ -495,9 +551,12 @@ extern "C" dg_status dg_batch_add(dg_batch* b, const dg_op* op, double dt, void*
     give_range(p, off, len);
     return fail(DG_ERR_OOM, "dg_batch_add: out of host memory");
   }
+  if (src) rec[src_k * dgw::kGeoMedia + 19] = id + 1.0;
   const size_t rb = static_cast<size_t>(K) * dgw::kGeoMedia * 4, cb = static_cast<size_t>(K) * 12;
+  const size_t sb = dgw::kSrcStride * 4 + 4 * sizeof(double) + sizeof(int);
+  const size_t so = (rb + cb + 15) / 16 * 16;  // source block, 16-byte aligned
   size_t idx = 0;
-  unsigned char* h = static_cast<unsigned char*>(b->staging.get(rb + cb, &idx));
+  unsigned char* h = static_cast<unsigned char*>(b->staging.get(so + sb, &idx));
   if (!h) {
     give_range(p, off, len);
     return fail(DG_ERR_OOM, "dg_batch_add: pinned staging buffer");
@@ -512,6 +571,25 @@ extern "C" dg_status dg_batch_add(dg_batch* b, const dg_op* op, double dt, void*
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t err = cudaMemcpyAsync(p.geo + off * dgw::kGeoMedia, hg, rb, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(p.conn + off * 3, hc, cb, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess && src) {
+    // weights times this problem's dt, wavelet parameters, starting step
+    double* hm = reinterpret_cast<double*>(h + so);
+    float* hw = reinterpret_cast<float*>(h + so + 4 * sizeof(double));
+    int* hs = reinterpret_cast<int*>(h + so + 4 * sizeof(double) + dgw::kSrcStride * 4);
+    hm[0] = dt;
+    hm[1] = src->t0;
+    hm[2] = 3.14159265358979323846 * src->f;
+    hm[3] = src->amplitude;
+    for (int n = 0; n < dgw::kSrcStride; ++n)
+      hw[n] = n < op->Np ? static_cast<float>(dt * src_wt[n]) : 0.0f;
+    *hs = static_cast<int>(b->steps);
+    err = cudaMemcpyAsync(b->d_src_meta + 4 * id, hm, 4 * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(b->d_src_w + dgw::kSrcStride * id, hw, dgw::kSrcStride * 4,
+                            cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(b->d_src_step + id, hs, sizeof(int), cudaMemcpyHostToDevice, s);
+  }
   if (err == cudaSuccess) err = b->staging.mark(idx, s);
   if (err != cudaSuccess) {
     give_range(p, off, len);
@@ -519,23 +597,16 @@ extern "C" dg_status dg_batch_add(dg_batch* b, const dg_op* op, double dt, void*
   }
   Problem pr;
   pr.live = true;
+  pr.source = src != nullptr;
   pr.N = op->N;
   pr.K = K;
   pr.off = off;
   pr.len = len;
   pr.dt = dt;
-  int32_t id = -1;
-  for (size_t i = 0; i < b->probs.size(); ++i)
-    if (!b->probs[i].live) {
-      id = static_cast<int32_t>(i);
-      break;
-    }
-  if (id < 0) {
-    id = static_cast<int32_t>(b->probs.size());
+  if (id == static_cast<int32_t>(b->probs.size()))
     b->probs.push_back(pr);
-  } else {
+  else
     b->probs[id] = pr;
-  }
   b->dirty = true;
   *slot = id;
   return DG_OK;
@@ -620,14 +691,17 @@ extern "C" dg_status dg_batch_step(dg_batch* b, int32_t nsteps, void* stream) {
     if (use_graph) {
       cudaError_t err = cudaGraphLaunch(b->graph[b->cur], s);
       if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: graph launch");
-      b->launches += 5;
+      b->launches += 6;
     } else {
       for (int i = 0; i < 5; ++i) {
         cudaError_t err = launch_stage(b, b->cur ^ (i & 1), i, s);
         if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: kernel launch");
       }
+      cudaError_t err = launch_tick(b, s);
+      if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: kernel launch");
     }
     b->cur ^= 1;
+    ++b->steps;
   }
   return DG_OK;
 }

@@ -407,6 +407,40 @@ Geometry build_geometry(const dg_mesh& mesh, const RefElement& ref) {
   return G;
 }
 
+// ------------------------------------------------------- point source
+int64_t point_source(const RefElement& R, const Geometry& G, int64_t K, double xs, double ys,
+                     std::vector<double>& w) {
+  const int N = R.N, Np = R.Np;
+  for (int64_t k = 0; k < K; ++k) {
+    // vertices are the nodes 0 (v1), N (v2) and Np - 1 (v3)
+    const double x1 = G.x[k * Np], y1 = G.y[k * Np];
+    const double x2 = G.x[k * Np + N], y2 = G.y[k * Np + N];
+    const double x3 = G.x[k * Np + Np - 1], y3 = G.y[k * Np + Np - 1];
+    const double det = (x2 - x1) * (y3 - y1) - (x3 - x1) * (y2 - y1);
+    const double l2 = ((xs - x1) * (y3 - y1) - (x3 - x1) * (ys - y1)) / det;
+    const double l3 = ((x2 - x1) * (ys - y1) - (xs - x1) * (y2 - y1)) / det;
+    const double l1 = 1.0 - l2 - l3;
+    if (l1 < -1e-12 || l2 < -1e-12 || l3 < -1e-12) continue;
+    const double r = 2.0 * l2 - 1.0, s = 2.0 * l3 - 1.0;
+    // M^-1 l(x_s) = V V^T V^-T psi(r, s) = V psi(r, s)
+    std::vector<double> psi(Np);
+    int col = 0;
+    for (int i = 0; i <= N; ++i)
+      for (int j = 0; i + j <= N; ++j, ++col) {
+        double dr, ds;
+        simplex_psi(i, j, r, s, &psi[col], &dr, &ds);
+      }
+    w.assign(Np, 0.0);
+    for (int n = 0; n < Np; ++n) {
+      double acc = 0.0;
+      for (int c = 0; c < Np; ++c) acc += R.V[n * Np + c] * psi[c];
+      w[n] = acc / G.J[k];
+    }
+    return k;
+  }
+  return -1;
+}
+
 // --------------------------------------------------------------- LSRK
 void lsrk_coefficients(double a[5], double b[5], double c[5]) {
   // Carpenter & Kennedy (1994), five-stage fourth-order 2N-storage scheme

@@ -52,6 +52,13 @@ struct Geometry {
 
 Geometry build_geometry(const dg_mesh& mesh, const RefElement& ref);
 
+// Point load delta(x - x_s) projected onto the nodal basis of the element
+// that contains (xs, ys) (the lowest-numbered one whose barycentric
+// coordinates are all >= -1e-12): w = M^-1 l(x_s) / J_k = V psi(r_s, s_s) /
+// J_k.  Returns k, or -1 if no element contains the point.
+int64_t point_source(const RefElement& R, const Geometry& G, int64_t K, double xs, double ys,
+                     std::vector<double>& w);
+
 // Face f's node j in the lattice numbering (same as RefElement::Fmask).
 inline int face_node(int N, int f, int j) {
   // index of lattice point (row, col): rows below hold N+1, N, ... points

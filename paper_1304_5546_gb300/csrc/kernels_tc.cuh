@@ -727,6 +727,20 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
         if (row_ok) srow = sq[6 * E * Np + e * GEO + (c < 2 ? 17 : 18)];
       }
       const float drow = MEDIA ? p.dt * srow : p.dt;
+      // point source on this row (batched launch, Ez row of a source element)
+      float samp = 0.f;
+      const float* sw = nullptr;
+      if constexpr (TABLE && MEDIA && MODE != kModeRhs) {
+        const int sid = row_ok && c == 2 ? static_cast<int>(sq[6 * E * Np + e * GEO + 19]) - 1 : -1;
+        if (sid >= 0) {
+          const double* m = p.src_meta + 4 * sid;
+          const double t =
+              (static_cast<double>(__ldg(p.step_ctr) - __ldg(p.src_step + sid)) + p.c_stage) * m[0];
+          const double aa = (t - m[1]) * m[2];
+          samp = static_cast<float>(m[3] * (1.0 - 2.0 * aa * aa) * exp(-aa * aa));
+          sw = p.src_w + sid * kSrcStride;
+        }
+      }
       if (row_ok && nvalid == E) {
         // full block: in place in the stage buffer, node pairs in packed
         // FP32x2 arithmetic (res = a res + dt rhs, q = q + b res)
@@ -757,6 +771,15 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
             rr[n] = rn;
           }
         }
+        if constexpr (TABLE && MEDIA && MODE != kModeRhs) {
+          if (sw) {  // res += s w, q += b s w
+            for (int n = 0; n < Np; ++n) {
+              const float v = samp * __ldg(sw + n);
+              rr[n] += v;
+              rq[n] = __fmaf_rn(p.b, v, rq[n]);
+            }
+          }
+        }
       } else if (row_ok) {
         // ragged last block: straight to global memory
         const int off = c * E * Np + e * Np;
@@ -771,8 +794,11 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
             else
               p.rhs[g + n] = rhs;
           } else {
-            const float rn =
+            float rn =
                 (MODE == kModeFirstStage) ? drow * rhs : p.a * sres[off + n] + drow * rhs;
+            if constexpr (TABLE && MEDIA) {
+              if (sw) rn += samp * __ldg(sw + n);
+            }
             const float qn = sq[off + n] + p.b * rn;
             if (full_block) {
               sq[off + n] = qn;

@@ -23,13 +23,15 @@ constexpr int kGeo = 13;
 //                   sH = 1, sE = 1 / eps_k for a single operator, and a
 //                   batch folds each problem's own time step in
 //                   (sH = dt_p, sE = dt_p / eps_k, launch dt = 1)
-//   19              zero (padding to 80 bytes)
+//   19              point source of the batched launch: source index + 1
+//                   (0: none; the single-operator launches never read it)
 // With these the upwind flux at a face node is, for the jumps
 // [u] = u- - u+ and [Ht] = ny [Hx] - nx [Hy],
 //   fz = cH [Ht] - cE [Ez];  lifted terms (-Z- ny fz, Z- nx fz, fz)
 // which is Fscale n.(F - F*) of the exact interface Riemann solution, and
 // for eps = 1 everywhere the eps = 1 upwind flux times Fscale / 2.
 constexpr int kGeoMedia = 20;
+constexpr int kSrcStride = 36;  // Np at N = 7
 
 template <typename T>
 struct StageArgs {
@@ -54,6 +56,17 @@ struct StageArgs {
   // single-operator launches (blocks of E consecutive elements over [0, K)).
   const int2* blocks = nullptr;
   const int* nblocks = nullptr;
+  // point sources of the batched launch (record value 19 = index + 1):
+  // the Ez right-hand side of the source element gains s(t) w, with w the
+  // projected point load times the problem's dt (src_w[index][kSrcStride])
+  // and s the Ricker wavelet A (1 - 2 a^2) exp(-a^2), a = pi f (t - t0),
+  // from src_meta[index] = {dt, t0, pi f, A}; the stage time is
+  // t = (step_ctr - src_step[index] + c_stage) dt.
+  const float* src_w = nullptr;
+  const double* src_meta = nullptr;
+  const int* src_step = nullptr;
+  const int* step_ctr = nullptr;
+  double c_stage = 0.0;
   // tensor-core path only: [Dr | Ds | LIFT | 1] as the operator tiles of the
   // launch's product variant (tc_nsplit tiles of tc_nn(N) x tc_kpp(N, prec)
   // elements, TF32 or BF16, in the core-matrix layout of tc_canon /

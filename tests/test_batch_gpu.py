@@ -8,7 +8,10 @@ media and time steps stepped by one persistent launch per stage.
 * graph replay and direct launches agree bit for bit;
 * problems leave and join between steps (continuous batching): the others
   carry on unchanged and a newcomer in a freed range starts clean;
-* the autotuner leaves the fields alone and produces a valid CTA split.
+* the autotuner leaves the fields alone and produces a valid CTA split;
+* Ricker point sources: each problem's wavelet runs on its own clock (time 0
+  at its first step, stage times t_n + c_i dt), also for problems that join a
+  batch that has already stepped.
 """
 import numpy as np
 import pytest
@@ -40,7 +43,7 @@ SPECS = [(7, 3, 1), (6, 5, 2), (8, 7, 3), (5, 1, 4), (9, 5, 5), (4, 2, 6)]
 
 
 class _Problem:
-    def __init__(self, P, n, N, seed, dt_scale=0.8):
+    def __init__(self, P, n, N, seed, dt_scale=0.8, source=False):
         self.mesh = jittered_delaunay_mesh(n, seed=seed)
         self.N = N
         self.d = O.Discretization(*self.mesh, N)
@@ -50,13 +53,37 @@ class _Problem:
         x0, y0 = 0.3 + 0.05 * (seed % 5), 0.6 - 0.04 * (seed % 4)
         q = np.stack(gaussian_pulse(self.d.x, self.d.y, x0, y0, 0.2))
         self.q0 = q.astype(np.float32).astype(np.float64)
+        self.source = None
+        if source:
+            # wavelet peak after 2.5 steps, a = pi f (t - t0) spanning about +-1.3
+            f = 0.15 / self.dt
+            self.source = (0.37 + 0.03 * (seed % 3), 0.52, f, 2.5 * self.dt, 1.7)
 
     def oracle(self, steps):
-        rhs = lambda u, t: O.maxwell_rhs_media(self.d, u, self.eps)  # noqa: E731
+        if self.source is None:
+            rhs = lambda u, t: O.maxwell_rhs_media(self.d, u, self.eps)  # noqa: E731
+        else:
+            xs, ys, f, t0, amp = self.source
+            k, w = O.point_source_weights(self.d, xs, ys)
+
+            def rhs(u, t):
+                return (O.maxwell_rhs_media(self.d, u, self.eps)
+                        + O.point_source_rhs(self.d, k, w, O.ricker(t, f, t0, amp)))
         q = self.q0
         for n in range(steps):
             q = O.lsrk_step(self.d, q, n * self.dt, self.dt, rhs=rhs)
         return q
+
+
+def _oracle_without_source(p, steps):
+    rhs = lambda u, t: O.maxwell_rhs_media(p.d, u, p.eps)  # noqa: E731
+    q = p.q0
+    for n in range(steps):
+        q = O.lsrk_step(p.d, q, n * p.dt, p.dt, rhs=rhs)
+    return q
+
+
+_Problem.oracle_without_source = staticmethod(_oracle_without_source)
 
 
 def _capacity(probs, extra=0):
@@ -75,7 +102,7 @@ def _run(P, probs, steps, graph=True, tune=False):
     b = P.Batch(_capacity(probs), graph=graph)
     slots = []
     for p in probs:
-        slot = b.add(p.solver, p.dt)
+        slot = b.add(p.solver, p.dt, source=p.source)
         b.set_fields(slot, p.q0)
         slots.append(slot)
     if tune:
@@ -178,3 +205,47 @@ def test_batch_rejects_bad_use(P, problems):
         small.remove(0)
     b.close()
     small.close()
+
+
+@pytest.fixture(scope="module")
+def sourced(P):
+    return [_Problem(P, n, N, seed, source=True) for n, N, seed in [(6, 3, 11), (7, 5, 12), (5, 7, 13)]]
+
+
+def test_point_sources_match_oracle(P, sourced):
+    steps = 5
+    got = _run(P, sourced, steps)
+    for p, g in zip(sourced, got):
+        want = p.oracle(steps)
+        # the source term must matter at this tolerance
+        assert _rel(want, _Problem.oracle_without_source(p, steps)) > 1e-3
+        assert _rel(g, want) <= TOL, (p.N, _rel(g, want))
+
+
+def test_point_source_clock_starts_at_join(P, problems, sourced):
+    # a sourced problem joins after the batch has stepped three times
+    early, late = problems[1], sourced[1]
+    b = P.Batch(_capacity([early, late]))
+    s0 = b.add(early.solver, early.dt)
+    b.set_fields(s0, early.q0)
+    b.step(3)
+    s1 = b.add(late.solver, late.dt, source=late.source)
+    b.set_fields(s1, late.q0)
+    b.step(4)
+    b.sync_check()
+    got0, got1 = b.get_fields(s0), b.get_fields(s1)
+    b.close()
+    assert _rel(got0, early.oracle(7)) <= TOL
+    assert _rel(got1, late.oracle(4)) <= TOL
+    # and bit for bit what it gives alone
+    alone = _run(P, [late], 4)[0]
+    assert np.array_equal(alone, got1)
+
+
+def test_point_source_outside_mesh_is_rejected(P, sourced):
+    from paper_1304_5546_gb300 import DGError
+    p = sourced[0]
+    b = P.Batch(_capacity([p]))
+    with pytest.raises(DGError):
+        b.add(p.solver, p.dt, source=(1.5, 0.5, 10.0, 0.12, 1.0))
+    b.close()
