@@ -360,8 +360,12 @@ dg_status dg_batch_info(const dg_batch* batch, int32_t slot, int32_t* N, int64_t
 
 /* Copy the problem's three fields in (set) or out (get): src / dst hold
  * field f, element k, node n at f * stride + k * Np + n (float), stride >=
- * K * Np, in host (pageable or pinned) or device memory.  Enqueued on
- * `stream`, ordered with dg_batch_step calls on the same stream.          */
+ * K * Np, in host (pageable or pinned) or device memory; set with src NULL
+ * zeroes the fields.  Enqueued on `stream`, ordered with dg_batch_step calls
+ * on the same stream.  set copies a pageable host source into a pinned
+ * buffer of the batch first, so it returns without waiting for the device;
+ * get into pageable host memory returns once the copy is done (use pinned
+ * memory, or dg_server, to keep the host ahead of the device).            */
 dg_status dg_batch_set_fields(dg_batch* batch, int32_t slot, const void* src, int64_t src_stride,
                               void* stream);
 dg_status dg_batch_get_fields(dg_batch* batch, int32_t slot, void* dst, int64_t dst_stride,
@@ -406,6 +410,79 @@ dg_status dg_batch_sync_check(dg_batch* batch, void* stream);
  * one single-thread launch that advances the step counter the point sources
  * read.                                                                   */
 int64_t dg_batch_launch_count(const dg_batch* batch);
+
+/* ------------------------------------------------------------ serving ---
+ * A solve server: continuous batching of wave-propagation solves on the
+ * current device.  A worker thread owns a batch (above) and a stream; it
+ * admits submitted requests, oldest first, whenever their order's pool has
+ * room (the memory budget is the pools' capacity), steps every admitted
+ * request together (one dg_batch_step per chunk of up to 4 steps, so
+ * requests that arrive while others run join at the next chunk boundary),
+ * and retires each request at its final time: its fields go to host memory
+ * and its pool range is free for the next admission.  A request's result
+ * does not depend on what else runs with it.  The paper has no server: this
+ * is the serving form of dg_solve with a point source.                    */
+#define DG_SERVER_SEQUENTIAL 1 /* dg_server_create flag: admit a request only
+                                  when none is running (one solve at a time) */
+
+#define DG_REQUEST_QUEUED 0
+#define DG_REQUEST_RUNNING 1
+#define DG_REQUEST_DONE 2
+#define DG_REQUEST_FAILED 3
+
+typedef struct dg_server dg_server;
+
+/* Times in seconds on the library's steady clock (dg_server_clock).       */
+typedef struct dg_request_info {
+  int32_t state;    /* DG_REQUEST_*                                        */
+  int32_t status;   /* why a failed request failed (DG_ERR_OOM: it does not
+                       fit the pool of its order even when empty)          */
+  int32_t N;
+  int64_t K;
+  int64_t nsteps;   /* LSRK steps to the final time                        */
+  double dt;        /* step: T / ceil(T / dg_cfl_dt(op, 1))                */
+  double t_submit, t_admit, t_done;
+} dg_request_info;
+
+/* The steady clock of the request times (seconds).                        */
+double dg_server_clock(void);
+
+/* capacity[N-1]: elements of order N the server's batch can hold.  Starts
+ * the worker thread.  Errors: those of dg_batch_create.                   */
+dg_status dg_server_create(const int64_t* capacity, int32_t flags, dg_server** out);
+
+/* Finishes every submitted request, stops the worker and frees everything. */
+void dg_server_destroy(dg_server* server);
+
+/* dg_server_submit: queue the solve of operator `op` (DG_FP32, host-only is
+ * enough; it must stay alive until the request is released) from t = 0 to
+ * T with the optional point source `src` (copied; NULL: none), starting
+ * from the host fields q0 (3 * K * Np floats in the layout of
+ * dg_batch_set_fields with stride K * Np; NULL: zero fields; read at
+ * admission, so it must stay valid until then) and writing the fields at T
+ * to `out` (same layout; NULL: discard), host memory that must stay valid
+ * until the request is done.  Returns at once with the request id.
+ * Errors: DG_ERR_ARG (NULL, not DG_FP32, T not positive, step count out
+ * of range, server stopping), DG_ERR_OOM.                                  */
+dg_status dg_server_submit(dg_server* server, const dg_op* op, double T,
+                           const dg_point_source* src, const void* q0, void* out,
+                           int64_t* request_id);
+
+/* Waits until the request is done or failed (timeout_s < 0: no limit) and
+ * fills info.  Errors: DG_ERR_ARG (unknown id), DG_ERR_TIMEOUT.            */
+dg_status dg_server_wait(dg_server* server, int64_t request_id, double timeout_s,
+                         dg_request_info* info);
+
+/* The request's current state and times, without waiting.                 */
+dg_status dg_server_info(dg_server* server, int64_t request_id, dg_request_info* info);
+
+/* Forget a finished request (its id becomes unknown).                     */
+dg_status dg_server_release(dg_server* server, int64_t request_id);
+
+/* Requests completed and failed, LSRK steps taken by the batch, and its
+ * kernel launches.  NULL outputs are skipped.                              */
+dg_status dg_server_stats(dg_server* server, int64_t* completed, int64_t* failed, int64_t* steps,
+                          int64_t* launches);
 
 /* dg_check_finite: synchronises `stream`, then scans the first K*Np values
  * of each field of d_q for NaN/Inf.  Returns DG_ERR_NONFINITE if any is

@@ -30,7 +30,9 @@ __all__ = [
     "dg_batch_create", "dg_batch_destroy", "dg_batch_add", "dg_batch_remove", "dg_batch_info",
     "dg_batch_set_fields", "dg_batch_get_fields", "dg_batch_step", "dg_batch_tune",
     "dg_batch_plan", "dg_batch_plan_ctas", "dg_batch_sync_check", "dg_batch_launch_count",
-    "Solver", "Batch", "DGError", "DG_FP32", "DG_FP64",
+    "dg_server_clock", "dg_server_create", "dg_server_destroy", "dg_server_submit",
+    "dg_server_wait", "dg_server_info", "dg_server_release", "dg_server_stats",
+    "Solver", "Batch", "Server", "DGError", "DG_FP32", "DG_FP64",
 ]
 
 
@@ -297,6 +299,69 @@ def dg_batch_launch_count(batch):
     return int(_lib.load().dg_batch_launch_count(batch))
 
 
+# --------------------------------------------------------------- serving
+def dg_server_clock():
+    return float(_lib.load().dg_server_clock())
+
+
+def dg_server_create(capacity, sequential=False):
+    c = np.ascontiguousarray(capacity, dtype=np.int64)
+    if c.size != DG_N_MAX:
+        raise ValueError("capacity needs %d entries" % DG_N_MAX)
+    h = ctypes.c_void_p()
+    _lib.check(_lib.load().dg_server_create(_ptr(c), _lib.DG_SERVER_SEQUENTIAL if sequential else 0,
+                                            ctypes.byref(h)), "dg_server_create")
+    return h.value
+
+
+def dg_server_destroy(server):
+    if server:
+        _lib.load().dg_server_destroy(server)
+
+
+def dg_server_submit(server, op, T, source=None, q0=None, out=None):
+    """q0 / out: contiguous float32 host arrays of 3 * K * Np values (or
+    None); they must stay alive until admission / completion."""
+    rid = ctypes.c_int64()
+    src = None
+    if source is not None:
+        src = ctypes.byref(_lib.dg_point_source(*[float(v) for v in source]))
+    _lib.check(_lib.load().dg_server_submit(server, op, T, src,
+                                            None if q0 is None else _buf_ptr(q0),
+                                            None if out is None else _buf_ptr(out),
+                                            ctypes.byref(rid)), "dg_server_submit")
+    return rid.value
+
+
+def _info_dict(i):
+    return {"state": i.state, "status": i.status, "N": i.N, "K": i.K, "nsteps": i.nsteps,
+            "dt": i.dt, "t_submit": i.t_submit, "t_admit": i.t_admit, "t_done": i.t_done}
+
+
+def dg_server_wait(server, request_id, timeout=-1.0):
+    info = _lib.dg_request_info()
+    _lib.check(_lib.load().dg_server_wait(server, request_id, timeout, ctypes.byref(info)),
+               "dg_server_wait")
+    return _info_dict(info)
+
+
+def dg_server_info(server, request_id):
+    info = _lib.dg_request_info()
+    _lib.check(_lib.load().dg_server_info(server, request_id, ctypes.byref(info)), "dg_server_info")
+    return _info_dict(info)
+
+
+def dg_server_release(server, request_id):
+    _lib.check(_lib.load().dg_server_release(server, request_id), "dg_server_release")
+
+
+def dg_server_stats(server):
+    v = [ctypes.c_int64() for _ in range(4)]
+    _lib.check(_lib.load().dg_server_stats(server, *[ctypes.byref(x) for x in v]), "dg_server_stats")
+    return {"completed": v[0].value, "failed": v[1].value, "steps": v[2].value,
+            "launches": v[3].value}
+
+
 # ------------------------------------------------------------ convenience
 # FP32-field variants: name -> dg_operator_setup flags
 _FP32_VARIANTS = {
@@ -467,3 +532,61 @@ class Batch:
 
     def launch_count(self):
         return dg_batch_launch_count(self.batch)
+
+
+class Server:
+    """Continuous-batching solve server (dg_server_*).
+
+    ``capacity``: dict order -> element capacity, or 7 counts (the memory
+    budget).  ``submit`` returns a request id at once; the result lands in
+    the ``out`` array given to it once ``wait`` reports the request done.
+    Operators, q0 and out arrays are kept alive here until ``release``.
+    """
+
+    def __init__(self, capacity, sequential=False, device=None):
+        import torch
+        if device is not None:
+            torch.cuda.set_device(device)
+        if isinstance(capacity, dict):
+            cap = [0] * DG_N_MAX
+            for n, c in capacity.items():
+                cap[n - 1] = int(c)
+            capacity = cap
+        self.server = dg_server_create(capacity, sequential)
+        self._keep = {}
+
+    def close(self):
+        dg_server_destroy(getattr(self, "server", None))
+        self.server = None
+        self._keep = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, solver_or_op, T, source=None, q0=None, out=None):
+        op = solver_or_op.op if hasattr(solver_or_op, "op") else solver_or_op
+        if q0 is not None:
+            q0 = np.ascontiguousarray(q0, dtype=np.float32)
+        rid = dg_server_submit(self.server, op, T, source, q0, out)
+        self._keep[rid] = (solver_or_op, q0, out)
+        return rid
+
+    def wait(self, rid, timeout=-1.0):
+        return dg_server_wait(self.server, rid, timeout)
+
+    def info(self, rid):
+        return dg_server_info(self.server, rid)
+
+    def release(self, rid):
+        dg_server_release(self.server, rid)
+        self._keep.pop(rid, None)
+
+    def stats(self):
+        return dg_server_stats(self.server)
+
+    @staticmethod
+    def clock():
+        return dg_server_clock()

@@ -31,6 +31,8 @@ DG_SETUP_TC_BF16X3 = 16
 DG_SETUP_TC = 32
 DG_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 DG_BATCH_NO_GRAPH = 1
+DG_SERVER_SEQUENTIAL = 1
+DG_REQUEST_QUEUED, DG_REQUEST_RUNNING, DG_REQUEST_DONE, DG_REQUEST_FAILED = 0, 1, 2, 3
 DG_N_MAX = 7
 
 _STATUS_NAMES = {
@@ -40,6 +42,13 @@ _STATUS_NAMES = {
 }
 
 c_void_p = ctypes.c_void_p
+
+
+class dg_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("K", ctypes.c_int64), ("nsteps", ctypes.c_int64), ("dt", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
 
 
 class dg_point_source(ctypes.Structure):
@@ -87,6 +96,14 @@ SIGNATURES = [
     ("dg_batch_plan_ctas", c_i32, [c_void_p, c_void_p, c_i32, c_void_p]),
     ("dg_batch_sync_check", c_i32, [c_void_p, c_void_p]),
     ("dg_batch_launch_count", c_i64, [c_void_p]),
+    ("dg_server_clock", c_dbl, []),
+    ("dg_server_create", c_i32, [c_void_p, c_i32, P(c_void_p)]),
+    ("dg_server_destroy", None, [c_void_p]),
+    ("dg_server_submit", c_i32, [c_void_p, c_void_p, c_dbl, c_void_p, c_void_p, c_void_p, P(c_i64)]),
+    ("dg_server_wait", c_i32, [c_void_p, c_i64, c_dbl, c_void_p]),
+    ("dg_server_info", c_i32, [c_void_p, c_i64, c_void_p]),
+    ("dg_server_release", c_i32, [c_void_p, c_i64]),
+    ("dg_server_stats", c_i32, [c_void_p, P(c_i64), P(c_i64), P(c_i64), P(c_i64)]),
     ("dg_last_error", ctypes.c_char_p, []),
 ]
 

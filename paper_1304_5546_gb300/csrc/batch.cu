@@ -34,6 +34,7 @@
 
 #include "internal.h"
 #include "launch.h"
+#include "staging.h"
 
 using dgw::fail;
 
@@ -46,55 +47,6 @@ dg_status cuda_fail(cudaError_t err, const char* where) {
   return fail(err == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA, "%s: %s (%s)", where,
               cudaGetErrorName(err), cudaGetErrorString(err));
 }
-
-// Pinned host buffers for asynchronous uploads; a buffer is reused once the
-// event recorded after its copies has completed.
-class Staging {
- public:
-  ~Staging() { release(); }
-  void* get(size_t bytes, size_t* idx) {
-    for (size_t i = 0; i < bufs_.size(); ++i) {
-      Buf& b = bufs_[i];
-      if (b.busy && cudaEventQuery(b.ev) == cudaSuccess) b.busy = false;
-      if (!b.busy && b.cap >= bytes) {
-        *idx = i;
-        return b.p;
-      }
-    }
-    Buf b;
-    b.cap = std::max<size_t>(bytes, 1 << 16);
-    if (cudaMallocHost(&b.p, b.cap) != cudaSuccess) return nullptr;
-    if (cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess) {
-      cudaFreeHost(b.p);
-      return nullptr;
-    }
-    bufs_.push_back(b);
-    *idx = bufs_.size() - 1;
-    return b.p;
-  }
-  // the copies from buffer idx are enqueued on `s`
-  cudaError_t mark(size_t idx, cudaStream_t s) {
-    bufs_[idx].busy = true;
-    return cudaEventRecord(bufs_[idx].ev, s);
-  }
-  void release() {
-    for (Buf& b : bufs_) {
-      if (b.busy) cudaEventSynchronize(b.ev);
-      cudaEventDestroy(b.ev);
-      cudaFreeHost(b.p);
-    }
-    bufs_.clear();
-  }
-
- private:
-  struct Buf {
-    void* p = nullptr;
-    size_t cap = 0;
-    cudaEvent_t ev = nullptr;
-    bool busy = false;
-  };
-  std::vector<Buf> bufs_;
-};
 
 struct Pool {
   int N = 0, Np = 0, E = 0;
@@ -148,7 +100,7 @@ struct dg_batch {
   cudaStream_t capture = nullptr;
   double lsrk_a[5], lsrk_b[5], lsrk_c[5];
   int64_t launches = 0;
-  Staging staging;
+  dgw::Staging staging;
 };
 
 namespace {
@@ -648,17 +600,38 @@ dg_status copy_fields(dg_batch* b, int32_t slot, void* other, int64_t other_stri
   const Problem& pr = b->probs[slot];
   const Pool& p = b->pools[pr.N - 1];
   const int64_t n = pr.K * p.Np;
-  if (!other) return fail(DG_ERR_ARG, "%s: NULL buffer", where);
-  if (other_stride < n) return fail(DG_ERR_ARG, "%s: field stride %lld < K * Np = %lld", where,
-                                    static_cast<long long>(other_stride), static_cast<long long>(n));
   float* dev = p.q[b->cur] + pr.off * p.Np;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t width = static_cast<size_t>(n) * 4;
   const size_t pitch_pool = static_cast<size_t>(p.fstride) * 4;
+  if (!other) {
+    if (!to_pool) return fail(DG_ERR_ARG, "%s: NULL buffer", where);
+    cudaError_t err = cudaMemset2DAsync(dev, pitch_pool, 0, width, 3, s);  // zero fields
+    if (err != cudaSuccess) return cuda_fail(err, where);
+    return DG_OK;
+  }
+  if (other_stride < n) return fail(DG_ERR_ARG, "%s: field stride %lld < K * Np = %lld", where,
+                                    static_cast<long long>(other_stride), static_cast<long long>(n));
   const size_t pitch_other = static_cast<size_t>(other_stride) * 4;
-  cudaError_t err =
-      to_pool ? cudaMemcpy2DAsync(dev, pitch_pool, other, pitch_other, width, 3, cudaMemcpyDefault, s)
+  cudaPointerAttributes attr;
+  const bool pageable = cudaPointerGetAttributes(&attr, other) == cudaSuccess &&
+                        attr.type == cudaMemoryTypeUnregistered;
+  cudaGetLastError();  // clear a failed attribute query
+  cudaError_t err;
+  if (to_pool && pageable) {
+    // through a pinned buffer, so that the call does not wait for the device
+    size_t idx = 0;
+    unsigned char* h = static_cast<unsigned char*>(b->staging.get(3 * width, &idx));
+    if (!h) return fail(DG_ERR_OOM, "%s: pinned staging buffer", where);
+    for (int f = 0; f < 3; ++f)
+      std::memcpy(h + f * width, static_cast<const unsigned char*>(other) + f * pitch_other, width);
+    err = cudaMemcpy2DAsync(dev, pitch_pool, h, width, width, 3, cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess) err = b->staging.mark(idx, s);
+  } else {
+    err = to_pool
+              ? cudaMemcpy2DAsync(dev, pitch_pool, other, pitch_other, width, 3, cudaMemcpyDefault, s)
               : cudaMemcpy2DAsync(other, pitch_other, dev, pitch_pool, width, 3, cudaMemcpyDefault, s);
+  }
   if (err != cudaSuccess) return cuda_fail(err, where);
   return DG_OK;
 }
