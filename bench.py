@@ -505,7 +505,8 @@ def run_batched(args):
 
     torch.cuda.set_device(0)
     steps = args.batch_steps
-    specs = batched_workload(args.batch_problems, seed=args.batch_seed)
+    specs = batched_workload(args.batch_problems, seed=args.batch_seed,
+                             orders=tuple(args.batch_orders))
     solvers, q0s, dts = [], [], []
     for sp in specs:
         s = P.Solver(*sp["mesh"], N=sp["N"], precision="fp32", eps=sp["eps"])
@@ -615,6 +616,121 @@ def run_batched(args):
     }
 
 
+def serving_requests(n_requests=120, seed=777, k_lo=1000, k_hi=200000, orders=(3, 4, 5, 6, 7),
+                     t_lo=0.5, t_hi=2.0, f=10.0, time_scale=0.01):
+    """Seeded solve requests: K log-uniform in [k_lo, k_hi] (jittered
+    Delaunay unit-square meshes), N uniform over `orders`, final time
+    uniform in [t_lo, t_hi], Ricker source of peak frequency f at a seeded
+    location, zero initial fields.  Times are scaled by `time_scale` (final
+    time and wavelet period alike: T -> T s, f -> f / s, t0 = 1.2 / f) so
+    that a solve takes tens to hundreds of steps.  Returns dicts with mesh, N,
+    T and source (x, y, f, t0, amplitude)."""
+    import numpy as np
+
+    from synth import jittered_delaunay_mesh, n_for_target_elements
+
+    rng = np.random.default_rng(seed)
+    out = []
+    fs = f / time_scale
+    for i in range(n_requests):
+        k = float(np.exp(rng.uniform(np.log(k_lo), np.log(k_hi))))
+        N = int(rng.choice(orders))
+        T = float(rng.uniform(t_lo, t_hi)) * time_scale
+        xs, ys = rng.uniform(0.2, 0.8, size=2)
+        mesh = jittered_delaunay_mesh(n_for_target_elements(k), seed=seed + 1 + i)
+        out.append({"mesh": mesh, "N": N, "T": T,
+                    "source": (float(xs), float(ys), fs, 1.2 / fs, 1.0)})
+    return out
+
+
+def _percentile(v, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def run_serving(args):
+    """Serving workload: Poisson arrivals at each rate in --serve-rates of
+    the same seeded requests, served by the continuous-batching server and by
+    the same server admitting one request at a time (sequential plain
+    solves).  Latency = result in host memory - submission.  One JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_1304_5546_gb300 as P
+
+    torch.cuda.set_device(0)
+    reqs = serving_requests(args.serve_requests, seed=args.serve_seed,
+                            time_scale=args.serve_time_scale)
+    solvers = [P.Solver(*r["mesh"], N=r["N"], precision="fp32", host_only=True) for r in reqs]
+    outs = [np.zeros((3, s.K, s.Np), np.float32) for s in solvers]
+    # memory budget -> element capacity per order: 36 Np + 92 bytes per
+    # element (two field buffers and the residual, records, face codes),
+    # split evenly over the orders
+    budget = args.serve_budget_gb * 1e9
+    orders = sorted({r["N"] for r in reqs})
+    cap = [0] * 7
+    for N in orders:
+        Np = (N + 1) * (N + 2) // 2
+        cap[N - 1] = int(budget / len(orders) / (36 * Np + 92))
+    rng = np.random.default_rng(args.serve_seed + 1)
+    clocks = ClockSampler(None) if not args.no_clocks else None
+    if clocks:
+        clocks.start()
+    # warm: one request through each mode (kernels, graphs, staging)
+    for seq in (False, True):
+        srv = P.Server(cap, sequential=seq)
+        srv.wait(srv.submit(solvers[0], reqs[0]["T"], source=reqs[0]["source"], out=outs[0]))
+        srv.close()
+    rows = []
+    for lam in args.serve_rates:
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs)))
+        row = {"rate_per_s": lam}
+        for mode, seq in (("batched", False), ("sequential", True)):
+            srv = P.Server(cap, sequential=seq)
+            t_start = P.Server.clock() + 0.01
+            ids = []
+            for i, (r, s, o) in enumerate(zip(reqs, solvers, outs)):
+                while P.Server.clock() < t_start + arrivals[i]:
+                    pass
+                ids.append(srv.submit(s, r["T"], source=r["source"], out=o))
+            infos = [srv.wait(i) for i in ids]
+            st = srv.stats()
+            srv.close()
+            lat = [i["t_done"] - i["t_submit"] for i in infos if i["state"] == 2]
+            span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+            el_steps = sum(i["K"] * i["nsteps"] for i in infos if i["state"] == 2)
+            row[mode] = {"solves_per_s": len(lat) / span, "p50_ms": 1e3 * _percentile(lat, 50),
+                         "p99_ms": 1e3 * _percentile(lat, 99), "mean_ms": 1e3 * float(np.mean(lat)),
+                         "makespan_s": span, "failed": st["failed"], "gpu_launches": st["launches"],
+                         "batched_steps": st["steps"],
+                         "element_stage_updates_per_s": 5.0 * el_steps / span}
+        row["speedup_solves_per_s"] = row["batched"]["solves_per_s"] / row["sequential"]["solves_per_s"]
+        row["p99_ratio_seq_over_batched"] = row["sequential"]["p99_ms"] / row["batched"]["p99_ms"]
+        rows.append(row)
+    clk = clocks.stop() if clocks else None
+    Ks = np.array([s.K for s in solvers])
+    return {
+        "workload": "serving",
+        "metric": "served solves/s and p50/p99 latency (continuous batching vs sequential)",
+        "unit": "solves/s",
+        "higher_is_better": True,
+        "rates": rows,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"requests_per_rate": len(reqs), "K_min": int(Ks.min()), "K_max": int(Ks.max()),
+                   "K_mean": float(Ks.mean()), "orders": orders,
+                   "T_range": [0.5 * args.serve_time_scale, 2.0 * args.serve_time_scale],
+                   "time_scale": args.serve_time_scale,
+                   "source": "Ricker, peak frequency %g, t0 = 1.2 / f, seeded location"
+                             % (10.0 / args.serve_time_scale),
+                   "initial_fields": "zero", "memory_budget_gb": args.serve_budget_gb,
+                   "capacity_elements": {str(N): cap[N - 1] for N in orders},
+                   "latency": "submission to result in host memory",
+                   "sequential": "same server, one request admitted at a time"},
+        "clocks": clk,
+    }
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -637,12 +753,18 @@ def main(argv=None):
                          "(use with --order 7 --n 362 for K = 262,088)")
     ap.add_argument("--study-steps", type=int, default=500)
     ap.add_argument("--sweep-orders", type=int, nargs="+", default=list(range(1, 8)))
-    ap.add_argument("--workload", choices=["single", "batched"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
                     help="single: the large-mesh benchmark line (default); batched: many "
                          "mixed-order problems in one launch per stage vs sequential solves")
     ap.add_argument("--batch-problems", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--batch-seed", type=int, default=4242)
+    ap.add_argument("--batch-orders", type=int, nargs="+", default=[3, 5, 7])
+    ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000])
+    ap.add_argument("--serve-seed", type=int, default=777)
+    ap.add_argument("--serve-time-scale", type=float, default=0.01)
+    ap.add_argument("--serve-budget-gb", type=float, default=4.0)
     args = ap.parse_args(argv)
     if args._oracle_sample:
         n, N, sec = int(args._oracle_sample[0]), int(args._oracle_sample[1]), float(args._oracle_sample[2])
@@ -654,6 +776,9 @@ def main(argv=None):
         return 0
     if args.study == "sweep":
         print(json.dumps(run_sweep_study(args)), flush=True)
+        return 0
+    if args.workload == "serving" and args.impl == "ours":
+        print(json.dumps(run_serving(args)), flush=True)
         return 0
     if args.workload == "batched" and args.impl == "ours":
         print(json.dumps(run_batched(args)), flush=True)
