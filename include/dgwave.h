@@ -389,8 +389,9 @@ dg_status dg_batch_step(dg_batch* batch, int32_t nsteps, void* stream);
 dg_status dg_batch_tune(dg_batch* batch, int32_t reps, void* stream);
 
 /* The current plan: CTAs and blocks per order (index N-1) and the per-block
- * cost the planner used (seconds after dg_batch_tune; before it, the bytes
- * a block moves).  NULL outputs are skipped.                               */
+ * cost the planner used (seconds per block iteration of one CTA: measured
+ * by dg_batch_tune, before it a table measured on a GB300).  NULL outputs
+ * are skipped.                                                             */
 dg_status dg_batch_plan(const dg_batch* batch, int32_t* cta, int64_t* nblocks, double* cost);
 
 /* The planner on its own (host only): CTAs per order for block counts

@@ -20,9 +20,10 @@
 // The CTA split: order N's blocks take ceil(nblk_N / c_N) iterations of
 // tau_N seconds on each of its c_N CTAs; the planner gives every order with
 // blocks one CTA and then hands out the rest one at a time to the order with
-// the largest ceil(nblk_N / c_N) tau_N.  tau_N starts from the bytes a block
-// moves and is replaced by measured values by dg_batch_tune, which also
-// tries moving single CTAs between orders and keeps what measures faster.
+// the largest ceil(nblk_N / c_N) tau_N.  tau_N starts from a table measured
+// on a GB300 and is replaced by the batch's own measurements by
+// dg_batch_tune, which also tries moving single CTAs between orders and
+// keeps what measures faster.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -137,12 +138,15 @@ bool plan_ctas(const int64_t* nblk, const double* cost, int num_ctas, int* cta) 
   return true;
 }
 
-// model cost of one block iteration before measurement: the bytes a full
-// block moves in one fused stage (fields and residual in and out, records,
-// face codes)
-double model_cost(int N, int E) {
-  const int Np = (N + 1) * (N + 2) / 2;
-  return static_cast<double>(E) * (12.0 * Np * 4 + dgw::kGeoMedia * 4 + 12);
+// cost of one block iteration per CTA before dg_batch_tune measures it:
+// seconds measured by dg_batch_tune on a GB300 (152 CTAs, 40-element blocks,
+// a batch of all seven orders with 1400 to 7000 blocks each).  The bytes a
+// block moves predict these badly (1 : 0.21 for N = 1 against N = 5 where
+// 1 : 0.60 was measured): a block has a fixed cost in hand-offs and
+// instruction issue.
+double model_cost(int N) {
+  static const double us[8] = {0.0, 1.22, 1.51, 1.54, 1.64, 2.02, 2.24, 3.78};
+  return 1e-6 * us[N];
 }
 
 void free_pool(Pool& p) {
@@ -434,7 +438,7 @@ extern "C" dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_
       return st;
     }
     b->smem = std::max(b->smem, b->pools[g].smem);
-    b->cost[g] = model_cost(g + 1, b->pools[g].E);
+    b->cost[g] = model_cost(g + 1);
   }
   for (int g = 0; g < kOrders; ++g) b->max_slots += capacity[g] > 0 ? capacity[g] / 4 + 1 : 0;
   err = cudaMalloc(reinterpret_cast<void**>(&b->d_meta), 17 * sizeof(int));
