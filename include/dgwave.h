@@ -172,6 +172,14 @@ dg_status dg_operator_setup(const dg_mesh* mesh, int32_t N, int32_t precision,
 dg_status dg_operator_setup_media(const dg_mesh* mesh, int32_t N, const double* eps,
                                   int32_t precision, int32_t flags, dg_op** out);
 
+/* dg_operator_set_alpha: the flux parameter alpha of Eq. max2d-numflux for
+ * later calls on the operator: 1 (the default) is the upwind flux, 0 the
+ * central flux n.(F - {F}) of Eq. dg-strong, values between blend the two
+ * (the dissipative alpha-terms scale with alpha).  Not for operators with a
+ * per-element permittivity.  Errors: DG_ERR_ARG (NULL, alpha outside
+ * [0, 1], a media operator).  Calls already enqueued keep their alpha.    */
+dg_status dg_operator_set_alpha(dg_op* op, double alpha);
+
 /* Np, Nfp = N+1, K and field_stride (see conventions).  NULL outputs are
  * skipped.                                                                 */
 dg_status dg_get_info(const dg_op* op, int32_t* Np, int32_t* Nfp, int64_t* K,

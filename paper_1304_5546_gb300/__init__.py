@@ -23,7 +23,7 @@ from ._lib import (  # noqa: F401
 
 __all__ = [
     "dg_mesh_create", "dg_mesh_info", "dg_mesh_connectivity", "dg_mesh_destroy",
-    "dg_operator_setup", "dg_operator_setup_media", "dg_get_info", "dg_get_nodes", "dg_get_reference",
+    "dg_operator_setup", "dg_operator_setup_media", "dg_operator_set_alpha", "dg_get_info", "dg_get_nodes", "dg_get_reference",
     "dg_get_geometry", "dg_get_maps", "dg_cfl_dt", "dg_lsrk_coefficients",
     "dg_op_destroy", "dg_rhs", "dg_step", "dg_step_static", "dg_solve", "dg_step_host",
     "dg_check_finite", "dg_sync_check", "dg_launch_count", "dg_last_error",
@@ -100,6 +100,10 @@ def dg_operator_setup_media(mesh, N, eps, precision=DG_FP32, flags=0):
     _lib.check(_lib.load().dg_operator_setup_media(mesh, N, _ptr(e), precision, flags,
                                                    ctypes.byref(h)), "dg_operator_setup_media")
     return h.value
+
+
+def dg_operator_set_alpha(op, alpha):
+    _lib.check(_lib.load().dg_operator_set_alpha(op, alpha), "dg_operator_set_alpha")
 
 
 def dg_get_info(op):

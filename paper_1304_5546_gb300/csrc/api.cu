@@ -309,6 +309,7 @@ dgw::StageArgs<T> base_args(const dg_op* op) {
   a.lam = static_cast<const T*>(op->d_lam);
   a.status = op->d_status;
   a.tc_op = op->d_tcop;
+  a.alpha = static_cast<T>(op->alpha);
   return a;
 }
 
@@ -498,6 +499,19 @@ extern "C" dg_status dg_operator_setup_media(const dg_mesh* mesh, int32_t N, con
                 "dg_operator_setup_media: the lower-precision product variants are not "
                 "available with a per-element permittivity");
   return operator_setup(mesh, N, eps, precision, flags, out);
+}
+
+extern "C" dg_status dg_operator_set_alpha(dg_op* op, double alpha) {
+  dgw::clear_error();
+  if (!op) return fail(DG_ERR_ARG, "dg_operator_set_alpha: NULL operator");
+  if (!(alpha >= 0.0 && alpha <= 1.0))
+    return fail(DG_ERR_ARG, "dg_operator_set_alpha: alpha = %g outside [0, 1]", alpha);
+  if (op->media())
+    return fail(DG_ERR_ARG,
+                "dg_operator_set_alpha: operators with a per-element permittivity use the upwind "
+                "flux of the interface Riemann solution only");
+  op->alpha = alpha;
+  return DG_OK;
 }
 
 extern "C" dg_status dg_get_info(const dg_op* op, int32_t* Np, int32_t* Nfp, int64_t* K,

@@ -86,6 +86,8 @@ struct dg_op {
   std::vector<double> eps;
   // min over elements of inradius / wave speed (wave speed 1 / sqrt(eps))
   double min_inradius_over_c = 0.0;
+  // flux parameter of Eq. max2d-numflux: 1 upwind (default), 0 central
+  double alpha = 1.0;
   bool has_device = false;
   int device = 0;
   int num_sms = 0;

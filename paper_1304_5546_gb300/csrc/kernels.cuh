@@ -328,12 +328,13 @@ __global__ void __launch_bounds__(Layout<T, N, MEDIA>::THREADS)
           Fb[(1 * E + ee) * FPAD + j] = zM * nx * fz;
           Fb[(2 * E + ee) * FPAD + j] = fz;
         } else {
+          // Eq. max2d-numflux with parameter alpha (1: upwind, 0: central)
           const T* gf = sg + ee * GEO + 4 + 3 * f;
-          const T nx = gf[0], ny = gf[1], fsc = gf[2];
+          const T nx = gf[0], ny = gf[1], fsc = gf[2], fa = fsc * p.alpha;
           const T ndotdH = nx * dHx + ny * dHy;
-          Fb[(0 * E + ee) * FPAD + j] = fsc * (ny * dEz + (ndotdH * nx - dHx));
-          Fb[(1 * E + ee) * FPAD + j] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
-          Fb[(2 * E + ee) * FPAD + j] = fsc * (ny * dHx - nx * dHy - dEz);
+          Fb[(0 * E + ee) * FPAD + j] = fsc * ny * dEz + fa * (ndotdH * nx - dHx);
+          Fb[(1 * E + ee) * FPAD + j] = -fsc * nx * dEz + fa * (ndotdH * ny - dHy);
+          Fb[(2 * E + ee) * FPAD + j] = fsc * (ny * dHx - nx * dHy) - fa * dEz;
         }
       }
     }

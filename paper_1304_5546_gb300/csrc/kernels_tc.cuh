@@ -572,11 +572,12 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
             fo[E * FES] = zM * nx * fz;
             fo[2 * E * FES] = fz;
           } else {
-            const float nx = gf[0], ny = gf[1], fsc = gf[2];
+            // Eq. max2d-numflux with parameter alpha (1: upwind, 0: central)
+            const float nx = gf[0], ny = gf[1], fsc = gf[2], fa = fsc * p.alpha;
             const float ndotdH = nx * dHx + ny * dHy;
-            fo[0] = fsc * (ny * dEz + (ndotdH * nx - dHx));
-            fo[E * FES] = fsc * (-nx * dEz + (ndotdH * ny - dHy));
-            fo[2 * E * FES] = fsc * (ny * dHx - nx * dHy - dEz);
+            fo[0] = fsc * ny * dEz + fa * (ndotdH * nx - dHx);
+            fo[E * FES] = -fsc * nx * dEz + fa * (ndotdH * ny - dHy);
+            fo[2 * E * FES] = fsc * (ny * dHx - nx * dHy) - fa * dEz;
           }
         }
       }

@@ -48,6 +48,7 @@ struct StageArgs {
   const T* LIFT = nullptr;        // Np x Nafp
   const T* lam = nullptr;         // [2][Np]: (1 + r_n) / 2, (1 + s_n) / 2 per node
   T a = 0, b = 0, dt = 0;
+  T alpha = 1;  // flux parameter of Eq. max2d-numflux (uniform medium only)
   int* status = nullptr;  // set to 1 by a CTA whose bounded wait expired
   // block table of the batched launch: block i of the launch covers
   // elements [blocks[i].x, blocks[i].x + blocks[i].y), 1 <= y <= E, x a

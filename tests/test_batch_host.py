@@ -125,3 +125,24 @@ def test_media_setup_rejects_bad_input(dgw):
                                         dgw.DG_SETUP_HOST_ONLY | 4)  # DG_SETUP_TC_TF32
     finally:
         dgw.dg_mesh_destroy(mesh)
+
+
+def test_set_alpha_checks(dgw):
+    from paper_1304_5546_gb300 import DGError
+    VX, VY, EToV = jittered_delaunay_mesh(3, seed=1)
+    mesh = dgw.dg_mesh_create(VX, VY, EToV)
+    op = dgw.dg_operator_setup(mesh, 3, dgw.DG_FP64, dgw.DG_SETUP_HOST_ONLY)
+    media = dgw.dg_operator_setup_media(mesh, 3, np.ones(EToV.shape[0]), dgw.DG_FP32,
+                                        dgw.DG_SETUP_HOST_ONLY)
+    try:
+        dgw.dg_operator_set_alpha(op, 0.0)
+        dgw.dg_operator_set_alpha(op, 0.25)
+        for bad in (-0.1, 1.5, float("nan")):
+            with pytest.raises(DGError):
+                dgw.dg_operator_set_alpha(op, bad)
+        with pytest.raises(DGError):
+            dgw.dg_operator_set_alpha(media, 0.0)
+    finally:
+        dgw.dg_op_destroy(op)
+        dgw.dg_op_destroy(media)
+        dgw.dg_mesh_destroy(mesh)
