@@ -389,11 +389,14 @@ dg_status dg_batch_get_fields(dg_batch* batch, int32_t slot, void* dst, int64_t 
 dg_status dg_batch_step(dg_batch* batch, int32_t nsteps, void* stream);
 
 /* dg_batch_tune: the autotuner.  Times `reps` stage launches of each order
- * alone on all SMs (cost of one block iteration per CTA), plans the CTA
- * split from those costs, then tries moving single CTAs between orders and
- * keeps every move that measures at least 0.5 % faster.  Synchronises
- * `stream`; leaves the fields unchanged.  Later joins and leaves re-plan with
- * the measured costs.                                                      */
+ * alone on all SMs (cost of one block iteration per CTA) and plans the CTA
+ * split from those costs; then, up to six times, runs the mixed launch with
+ * per-CTA clocks, takes each order's cost from its observed finish time
+ * (the orders share HBM and L2 there) and re-plans, until the plan no longer
+ * changes; finally tries moving single CTAs between orders and keeps every
+ * move that measures at least 0.5 % faster.  The fastest measured plan is
+ * kept.  Synchronises `stream`; leaves the fields unchanged.  Later joins
+ * and leaves re-plan with the last costs.                                  */
 dg_status dg_batch_tune(dg_batch* batch, int32_t reps, void* stream);
 
 /* The current plan: CTAs and blocks per order (index N-1) and the per-block

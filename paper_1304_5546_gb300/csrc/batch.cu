@@ -295,8 +295,10 @@ cudaError_t launch_tick(dg_batch* b, cudaStream_t s) {
   return err;
 }
 
-cudaError_t launch_stage(dg_batch* b, int src, int stage, cudaStream_t s) {
-  const dgw::BatchArgs a = batch_args(b, src, stage);
+cudaError_t launch_stage(dg_batch* b, int src, int stage, cudaStream_t s,
+                         unsigned long long* clock = nullptr) {
+  dgw::BatchArgs a = batch_args(b, src, stage);
+  a.cta_clock = clock;
   cudaError_t err = stage == 0 ? dgw::launch_batch_tc<dgw::kModeFirstStage>(a, b->num_sms, b->smem, s)
                                : dgw::launch_batch_tc<dgw::kModeStage>(a, b->num_sms, b->smem, s);
   if (err == cudaSuccess) ++b->launches;
@@ -693,27 +695,61 @@ extern "C" dg_status dg_batch_tune(dg_batch* b, int32_t reps, void* stream) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  unsigned long long* d_clock = nullptr;
+  cudaError_t err = cudaMalloc(reinterpret_cast<void**>(&d_clock),
+                               2 * static_cast<size_t>(b->num_sms) * sizeof(unsigned long long));
+  std::vector<unsigned long long> clk(2 * static_cast<size_t>(b->num_sms));
   int meta[16];
-  // time `reps` stage launches (stage 2 form: reads q[cur] and the residual,
-  // writes the other buffer and the residual; the fields stay as they are)
-  auto timed = [&](const int* cta, float* ms) -> cudaError_t {
+  auto set_plan = [&](const int* cta) -> cudaError_t {
     meta[7] = 0;
     meta[8] = 0;
     for (int g = 0; g < kOrders; ++g) {
       meta[g] = static_cast<int>(b->nblk[g]);
       meta[9 + g] = meta[8 + g] + cta[g];
     }
-    cudaError_t err = cudaStreamSynchronize(s);
-    if (err == cudaSuccess) err = cudaMemcpy(b->d_meta, meta, sizeof(meta), cudaMemcpyHostToDevice);
-    if (err == cudaSuccess) err = launch_stage(b, b->cur, 1, s);  // warm
-    if (err == cudaSuccess) err = cudaEventRecord(e0, s);
-    for (int r = 0; r < reps && err == cudaSuccess; ++r) err = launch_stage(b, b->cur, 1, s);
-    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
-    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-    if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
-    return err;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_meta, meta, sizeof(meta), cudaMemcpyHostToDevice);
+    return e;
   };
-  cudaError_t err = cudaSuccess;
+  // time `reps` stage launches (stage 2 form: reads q[cur] and the residual,
+  // writes the other buffer and the residual; the fields stay as they are)
+  auto timed = [&](const int* cta, float* ms) -> cudaError_t {
+    cudaError_t e = set_plan(cta);
+    if (e == cudaSuccess) e = launch_stage(b, b->cur, 1, s);  // warm
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_stage(b, b->cur, 1, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    return e;
+  };
+  // one launch with per-CTA clocks: each order's finish time after the
+  // launch's first CTA start, divided by its block iterations per CTA
+  auto observed_costs = [&](const int* cta, double* cost) -> cudaError_t {
+    cudaError_t e = set_plan(cta);
+    if (e == cudaSuccess) e = launch_stage(b, b->cur, 1, s, d_clock);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(clk.data(), d_clock, clk.size() * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    unsigned long long t0 = ~0ull;
+    int c = 0;
+    for (int g = 0; g < kOrders; ++g) c += cta[g];
+    for (int i = 0; i < c; ++i) t0 = std::min(t0, clk[2 * i]);
+    int first = 0;
+    for (int g = 0; g < kOrders; ++g) {
+      unsigned long long end = t0;
+      for (int i = first; i < first + cta[g]; ++i) end = std::max(end, clk[2 * i + 1]);
+      first += cta[g];
+      if (cta[g] > 0 && b->nblk[g] > 0) {
+        const int64_t iters = (b->nblk[g] + cta[g] - 1) / cta[g];
+        cost[g] = 1e-9 * static_cast<double>(end - t0) / static_cast<double>(iters);
+      }
+    }
+    return cudaSuccess;
+  };
+  // 1. each order alone on all SMs
   int alone[kOrders];
   for (int g = 0; g < kOrders && err == cudaSuccess; ++g) {
     if (b->nblk[g] == 0) continue;
@@ -724,15 +760,34 @@ extern "C" dg_status dg_batch_tune(dg_batch* b, int32_t reps, void* stream) {
     const int64_t iters = (b->nblk[g] + b->num_sms - 1) / b->num_sms;
     b->cost[g] = 1e-3 * ms / reps / static_cast<double>(iters);
   }
-  // measured costs -> plan, then single-CTA moves between orders that
-  // measure faster
-  int best[kOrders];
+  // 2. plan, then re-plan from the costs observed in the mixed launch (the
+  //    orders share HBM and L2 there) while the plan changes
+  int best[kOrders], plan[kOrders];
   float best_ms = 0.f;
   if (err == cudaSuccess) {
-    plan_ctas(b->nblk, b->cost, b->num_sms, best);
+    plan_ctas(b->nblk, b->cost, b->num_sms, plan);
+    std::copy(plan, plan + kOrders, best);
     err = timed(best, &best_ms);
   }
-  for (int round = 0; round < 3 && err == cudaSuccess; ++round) {
+  for (int it = 0; it < 6 && err == cudaSuccess; ++it) {
+    double cost[kOrders];
+    std::copy(b->cost, b->cost + kOrders, cost);
+    err = observed_costs(plan, cost);
+    if (err != cudaSuccess) break;
+    std::copy(cost, cost + kOrders, b->cost);
+    int next[kOrders];
+    plan_ctas(b->nblk, b->cost, b->num_sms, next);
+    if (std::equal(next, next + kOrders, plan)) break;
+    std::copy(next, next + kOrders, plan);
+    float ms = 0.f;
+    err = timed(plan, &ms);
+    if (err == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      std::copy(plan, plan + kOrders, best);
+    }
+  }
+  // 3. single-CTA moves between orders that measure faster
+  for (int round = 0; round < 2 && err == cudaSuccess; ++round) {
     bool improved = false;
     for (int from = 0; from < kOrders && err == cudaSuccess; ++from) {
       for (int to = 0; to < kOrders && err == cudaSuccess; ++to) {
@@ -754,14 +809,11 @@ extern "C" dg_status dg_batch_tune(dg_batch* b, int32_t reps, void* stream) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (d_clock) cudaFree(d_clock);
   if (err != cudaSuccess) return cuda_fail(err, "dg_batch_tune");
   b->measured = true;
   std::copy(best, best + kOrders, b->cta);
-  for (int g = 0; g < kOrders; ++g) {
-    meta[g] = static_cast<int>(b->nblk[g]);
-    meta[9 + g] = meta[8 + g] + b->cta[g];
-  }
-  err = cudaMemcpy(b->d_meta, meta, sizeof(meta), cudaMemcpyHostToDevice);
+  err = set_plan(b->cta);
   if (err != cudaSuccess) return cuda_fail(err, "dg_batch_tune: plan upload");
   return DG_OK;
 }

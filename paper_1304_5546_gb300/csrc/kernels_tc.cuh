@@ -889,11 +889,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   int c0[8];
 #pragma unroll
   for (int g = 0; g < 8; ++g) c0[g] = __ldg(p.cta0 + g);
+  // tuning launches: each CTA's start and end time (ns)
+  const unsigned long long t_start = p.cta_clock ? global_ns() : 0ull;
 #define DG_BATCH_GROUP(NN_)                                                              \
   if (b >= c0[NN_ - 1] && b < c0[NN_]) {                                                 \
     static_assert(TcLayout<NN_, kTcTf32x3, true>::THREADS == kTcThreads, "block size");   \
     tc_stage_body<NN_, MODE, kTcTf32x3, true, true>(p.g[NN_ - 1], b - c0[NN_ - 1],        \
                                                     c0[NN_] - c0[NN_ - 1], smem);        \
+    if (p.cta_clock && threadIdx.x == 0) {                                               \
+      p.cta_clock[2 * b] = t_start;                                                      \
+      p.cta_clock[2 * b + 1] = global_ns();                                              \
+    }                                                                                    \
     return;                                                                              \
   }
   DG_BATCH_GROUP(1)

@@ -148,6 +148,9 @@ cudaError_t launch_stage_tc_media(const StageArgs<float>& args, int mode, int nu
 struct BatchArgs {
   StageArgs<float> g[7];
   const int* cta0 = nullptr;
+  // tuning launches only: CTA b writes its start and end time (globaltimer,
+  // ns) to cta_clock[2b], cta_clock[2b + 1]; NULL otherwise
+  unsigned long long* cta_clock = nullptr;
 };
 // grid: CTAs of the launch (cta0[7]); smem: the largest
 // batch_tc_smem_bytes of an order that may have CTAs
