@@ -317,12 +317,15 @@ dg_status dg_step_static(const dg_op* op, void* d_q, void* d_res, double t0, dou
  * stride the caller chooses.                                               */
 #define DG_BATCH_NO_GRAPH 1 /* dg_batch_create flag: launch the five stage
                                kernels directly instead of replaying graphs */
+#define DG_BATCH_NO_ADAPT 2 /* dg_batch_create flag: keep the CTA split fixed
+                               between joins and leaves (see dg_batch_step) */
 
 /* dg_batch_create: capacity[N-1] = elements of order N the batch can hold
  * (N = 1..DG_N_MAX, 0 = none), on the current device.
  * Errors: DG_ERR_ARG (NULL, unknown flags, capacities all zero or one
  * >= 2^27 or too large for 32-bit field offsets), DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_batch** out);
+/* flags: DG_BATCH_NO_GRAPH, DG_BATCH_NO_ADAPT (either or both).           */
 
 /* Waits for the device, then frees the batch and its device memory.      */
 void dg_batch_destroy(dg_batch* batch);
@@ -383,7 +386,13 @@ dg_status dg_batch_get_fields(dg_batch* batch, int32_t slot, void* dst, int64_t 
  * with its own dt; per stage one launch over all problems.  The first call
  * after a problem joined or left uploads the block tables and CTA split
  * (asynchronously on `stream`).  Calls on one batch must be ordered (one
- * stream, or the caller's synchronisation).
+ * stream, or the caller's synchronisation).  Unless DG_BATCH_NO_ADAPT, the
+ * split adapts online: every launch records each CTA's start and end time;
+ * every 8 steps a snapshot is copied to host memory, and once it has arrived
+ * (checked at a later call, never waited for) each order's cost moves
+ * halfway to the cost observed in that launch and the split is re-planned,
+ * switching when the predicted makespan is at least 3 % shorter.  The split
+ * changes only which CTA computes a block, never a result.
  * Errors: DG_ERR_ARG (nsteps < 0; more orders present than SMs),
  * DG_ERR_OOM, DG_ERR_CUDA.                                                 */
 dg_status dg_batch_step(dg_batch* batch, int32_t nsteps, void* stream);

@@ -475,7 +475,7 @@ class Batch:
     out as (3, K, Np) arrays.
     """
 
-    def __init__(self, capacity, graph=True, device=None):
+    def __init__(self, capacity, graph=True, adapt=True, device=None):
         import torch
         if device is not None:
             torch.cuda.set_device(device)
@@ -484,7 +484,8 @@ class Batch:
             for n, c in capacity.items():
                 cap[n - 1] = int(c)
             capacity = cap
-        self.batch = dg_batch_create(capacity, 0 if graph else _lib.DG_BATCH_NO_GRAPH)
+        flags = (0 if graph else _lib.DG_BATCH_NO_GRAPH) | (0 if adapt else _lib.DG_BATCH_NO_ADAPT)
+        self.batch = dg_batch_create(capacity, flags)
 
     def close(self):
         dg_batch_destroy(getattr(self, "batch", None))

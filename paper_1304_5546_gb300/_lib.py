@@ -31,6 +31,7 @@ DG_SETUP_TC_BF16X3 = 16
 DG_SETUP_TC = 32
 DG_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 DG_BATCH_NO_GRAPH = 1
+DG_BATCH_NO_ADAPT = 2
 DG_SERVER_SEQUENTIAL = 1
 DG_REQUEST_QUEUED, DG_REQUEST_RUNNING, DG_REQUEST_DONE, DG_REQUEST_FAILED = 0, 1, 2, 3
 DG_N_MAX = 7

@@ -102,6 +102,18 @@ struct dg_batch {
   double lsrk_a[5], lsrk_b[5], lsrk_c[5];
   int64_t launches = 0;
   dgw::Staging staging;
+  // online adaptation of the CTA split: every launch writes each CTA's start
+  // and end time to d_clock; every kAdaptSteps steps a snapshot goes to
+  // pinned host memory, and once it has arrived the per-order costs are
+  // updated from the observed finish times and the split re-planned
+  unsigned long long* d_clock = nullptr;
+  unsigned long long* h_clock = nullptr;
+  cudaEvent_t clock_ev = nullptr;
+  bool clock_pending = false;
+  int clock_cta[kOrders] = {};
+  int64_t clock_nblk[kOrders] = {};
+  int64_t steps_since_snapshot = 0;
+  int64_t replans = 0;
 };
 
 namespace {
@@ -169,6 +181,9 @@ void destroy_batch(dg_batch* b) {
   for (Pool& p : b->pools) free_pool(p);
   if (b->d_meta) cudaFree(b->d_meta);
   if (b->d_status) cudaFree(b->d_status);
+  if (b->d_clock) cudaFree(b->d_clock);
+  if (b->h_clock) cudaFreeHost(b->h_clock);
+  if (b->clock_ev) cudaEventDestroy(b->clock_ev);
   if (b->d_src_w) cudaFree(b->d_src_w);
   if (b->d_src_meta) cudaFree(b->d_src_meta);
   if (b->d_src_step) cudaFree(b->d_src_step);
@@ -295,10 +310,9 @@ cudaError_t launch_tick(dg_batch* b, cudaStream_t s) {
   return err;
 }
 
-cudaError_t launch_stage(dg_batch* b, int src, int stage, cudaStream_t s,
-                         unsigned long long* clock = nullptr) {
+cudaError_t launch_stage(dg_batch* b, int src, int stage, cudaStream_t s) {
   dgw::BatchArgs a = batch_args(b, src, stage);
-  a.cta_clock = clock;
+  a.cta_clock = b->d_clock;
   cudaError_t err = stage == 0 ? dgw::launch_batch_tc<dgw::kModeFirstStage>(a, b->num_sms, b->smem, s)
                                : dgw::launch_batch_tc<dgw::kModeStage>(a, b->num_sms, b->smem, s);
   if (err == cudaSuccess) ++b->launches;
@@ -412,7 +426,8 @@ extern "C" dg_status dg_batch_plan_ctas(const int64_t* nblocks, const double* co
 extern "C" dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_batch** out) {
   dgw::clear_error();
   if (!capacity || !out) return fail(DG_ERR_ARG, "dg_batch_create: NULL argument");
-  if (flags & ~DG_BATCH_NO_GRAPH) return fail(DG_ERR_ARG, "dg_batch_create: unknown flags 0x%x", flags);
+  if (flags & ~(DG_BATCH_NO_GRAPH | DG_BATCH_NO_ADAPT))
+    return fail(DG_ERR_ARG, "dg_batch_create: unknown flags 0x%x", flags);
   bool any = false;
   for (int g = 0; g < kOrders; ++g) {
     if (capacity[g] < 0 || capacity[g] >= (int64_t(1) << 27))
@@ -451,6 +466,11 @@ extern "C" dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_
     err = cudaMalloc(reinterpret_cast<void**>(&b->d_src_meta), b->max_slots * 4 * sizeof(double));
   if (err == cudaSuccess)
     err = cudaMalloc(reinterpret_cast<void**>(&b->d_src_step), b->max_slots * sizeof(int));
+  const size_t clock_bytes = 2 * static_cast<size_t>(b->num_sms) * sizeof(unsigned long long);
+  if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void**>(&b->d_clock), clock_bytes);
+  if (err == cudaSuccess) err = cudaMemset(b->d_clock, 0, clock_bytes);
+  if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void**>(&b->h_clock), clock_bytes);
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->clock_ev, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(b->d_status, 0, sizeof(int));
   if (err != cudaSuccess) {
@@ -657,6 +677,64 @@ extern "C" dg_status dg_batch_get_fields(dg_batch* b, int32_t slot, void* dst,
   return copy_fields(b, slot, dst, dst_stride, false, stream, "dg_batch_get_fields");
 }
 
+namespace {
+
+constexpr int64_t kAdaptSteps = 8;  // steps between clock snapshots
+
+// Per-order cost of one block iteration, from one launch's per-CTA clocks
+// under the split cta[] with block counts nblk[]: the order's finish time
+// after the launch's first CTA start over its block iterations per CTA.
+void observed_costs(const unsigned long long* clk, const int* cta, const int64_t* nblk,
+                    double* cost) {
+  unsigned long long t0 = ~0ull;
+  int c = 0;
+  for (int g = 0; g < kOrders; ++g) c += cta[g];
+  for (int i = 0; i < c; ++i) t0 = std::min(t0, clk[2 * i]);
+  int first = 0;
+  for (int g = 0; g < kOrders; ++g) {
+    unsigned long long end = t0;
+    for (int i = first; i < first + cta[g]; ++i) end = std::max(end, clk[2 * i + 1]);
+    first += cta[g];
+    if (cta[g] > 0 && nblk[g] > 0 && end > t0) {
+      const int64_t iters = (nblk[g] + cta[g] - 1) / cta[g];
+      cost[g] = 1e-9 * static_cast<double>(end - t0) / static_cast<double>(iters);
+    }
+  }
+}
+
+double makespan(const int64_t* nblk, const double* cost, const int* cta) {
+  double m = 0.0;
+  for (int g = 0; g < kOrders; ++g)
+    if (cta[g] > 0) m = std::max(m, static_cast<double>((nblk[g] + cta[g] - 1) / cta[g]) * cost[g]);
+  return m;
+}
+
+// a clock snapshot has arrived: move the costs halfway to the observed ones
+// and switch to a new split when it predicts a makespan at least 3 % shorter
+dg_status adapt_split(dg_batch* b, cudaStream_t s) {
+  double obs[kOrders];
+  std::copy(b->cost, b->cost + kOrders, obs);
+  observed_costs(b->h_clock, b->clock_cta, b->clock_nblk, obs);
+  for (int g = 0; g < kOrders; ++g) b->cost[g] = 0.5 * (b->cost[g] + obs[g]);
+  int next[kOrders];
+  if (!plan_ctas(b->nblk, b->cost, b->num_sms, next)) return DG_OK;
+  if (std::equal(next, next + kOrders, b->cta)) return DG_OK;
+  if (makespan(b->nblk, b->cost, next) > 0.97 * makespan(b->nblk, b->cost, b->cta)) return DG_OK;
+  size_t idx = 0;
+  int* meta = static_cast<int*>(b->staging.get(8 * sizeof(int), &idx));
+  if (!meta) return fail(DG_ERR_OOM, "dg_batch_step: pinned staging buffer");
+  meta[0] = 0;
+  for (int g = 0; g < kOrders; ++g) meta[g + 1] = meta[g] + next[g];
+  cudaError_t err = cudaMemcpyAsync(b->d_meta + 8, meta, 8 * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = b->staging.mark(idx, s);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: split upload");
+  std::copy(next, next + kOrders, b->cta);
+  ++b->replans;
+  return DG_OK;
+}
+
+}  // namespace
+
 extern "C" dg_status dg_batch_step(dg_batch* b, int32_t nsteps, void* stream) {
   dgw::clear_error();
   dg_status st = check_batch(b, "dg_batch_step");
@@ -682,6 +760,24 @@ extern "C" dg_status dg_batch_step(dg_batch* b, int32_t nsteps, void* stream) {
     b->cur ^= 1;
     ++b->steps;
   }
+  if (!(b->flags & DG_BATCH_NO_ADAPT) && nsteps > 0) {
+    if (b->clock_pending && cudaEventQuery(b->clock_ev) == cudaSuccess) {
+      b->clock_pending = false;
+      if (!b->dirty && (st = adapt_split(b, s))) return st;
+    }
+    b->steps_since_snapshot += nsteps;
+    if (!b->clock_pending && b->steps_since_snapshot >= kAdaptSteps) {
+      cudaError_t err = cudaMemcpyAsync(b->h_clock, b->d_clock,
+                                        2 * static_cast<size_t>(b->num_sms) * sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, s);
+      if (err == cudaSuccess) err = cudaEventRecord(b->clock_ev, s);
+      if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: clock snapshot");
+      std::copy(b->cta, b->cta + kOrders, b->clock_cta);
+      std::copy(b->nblk, b->nblk + kOrders, b->clock_nblk);
+      b->clock_pending = true;
+      b->steps_since_snapshot = 0;
+    }
+  }
   return DG_OK;
 }
 
@@ -695,9 +791,7 @@ extern "C" dg_status dg_batch_tune(dg_batch* b, int32_t reps, void* stream) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  unsigned long long* d_clock = nullptr;
-  cudaError_t err = cudaMalloc(reinterpret_cast<void**>(&d_clock),
-                               2 * static_cast<size_t>(b->num_sms) * sizeof(unsigned long long));
+  cudaError_t err = cudaSuccess;
   std::vector<unsigned long long> clk(2 * static_cast<size_t>(b->num_sms));
   int meta[16];
   auto set_plan = [&](const int* cta) -> cudaError_t {
@@ -725,29 +819,15 @@ extern "C" dg_status dg_batch_tune(dg_batch* b, int32_t reps, void* stream) {
   };
   // one launch with per-CTA clocks: each order's finish time after the
   // launch's first CTA start, divided by its block iterations per CTA
-  auto observed_costs = [&](const int* cta, double* cost) -> cudaError_t {
+  auto observed = [&](const int* cta, double* cost) -> cudaError_t {
     cudaError_t e = set_plan(cta);
-    if (e == cudaSuccess) e = launch_stage(b, b->cur, 1, s, d_clock);
+    if (e == cudaSuccess) e = launch_stage(b, b->cur, 1, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess)
-      e = cudaMemcpy(clk.data(), d_clock, clk.size() * sizeof(unsigned long long),
+      e = cudaMemcpy(clk.data(), b->d_clock, clk.size() * sizeof(unsigned long long),
                      cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return e;
-    unsigned long long t0 = ~0ull;
-    int c = 0;
-    for (int g = 0; g < kOrders; ++g) c += cta[g];
-    for (int i = 0; i < c; ++i) t0 = std::min(t0, clk[2 * i]);
-    int first = 0;
-    for (int g = 0; g < kOrders; ++g) {
-      unsigned long long end = t0;
-      for (int i = first; i < first + cta[g]; ++i) end = std::max(end, clk[2 * i + 1]);
-      first += cta[g];
-      if (cta[g] > 0 && b->nblk[g] > 0) {
-        const int64_t iters = (b->nblk[g] + cta[g] - 1) / cta[g];
-        cost[g] = 1e-9 * static_cast<double>(end - t0) / static_cast<double>(iters);
-      }
-    }
-    return cudaSuccess;
+    if (e == cudaSuccess) observed_costs(clk.data(), cta, b->nblk, cost);
+    return e;
   };
   // 1. each order alone on all SMs
   int alone[kOrders];
@@ -772,7 +852,7 @@ extern "C" dg_status dg_batch_tune(dg_batch* b, int32_t reps, void* stream) {
   for (int it = 0; it < 6 && err == cudaSuccess; ++it) {
     double cost[kOrders];
     std::copy(b->cost, b->cost + kOrders, cost);
-    err = observed_costs(plan, cost);
+    err = observed(plan, cost);
     if (err != cudaSuccess) break;
     std::copy(cost, cost + kOrders, b->cost);
     int next[kOrders];
@@ -809,7 +889,6 @@ extern "C" dg_status dg_batch_tune(dg_batch* b, int32_t reps, void* stream) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (d_clock) cudaFree(d_clock);
   if (err != cudaSuccess) return cuda_fail(err, "dg_batch_tune");
   b->measured = true;
   std::copy(best, best + kOrders, b->cta);

@@ -98,8 +98,8 @@ def problems(P):
     return [_Problem(P, *s) for s in SPECS]
 
 
-def _run(P, probs, steps, graph=True, tune=False):
-    b = P.Batch(_capacity(probs), graph=graph)
+def _run(P, probs, steps, graph=True, tune=False, adapt=True):
+    b = P.Batch(_capacity(probs), graph=graph, adapt=adapt)
     slots = []
     for p in probs:
         slot = b.add(p.solver, p.dt, source=p.source)
@@ -249,3 +249,12 @@ def test_point_source_outside_mesh_is_rejected(P, sourced):
     with pytest.raises(DGError):
         b.add(p.solver, p.dt, source=(1.5, 0.5, 10.0, 0.12, 1.0))
     b.close()
+
+
+def test_online_split_adaptation_keeps_results(P, problems):
+    # 20 steps: the split is re-planned from clock snapshots along the way;
+    # which CTA computes a block never changes a result
+    a = _run(P, problems, 20, adapt=True)
+    b = _run(P, problems, 20, adapt=False)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
