@@ -115,7 +115,9 @@ struct TcLayout {
   // 512 TMEM columns (a second resident CTA would wait in tcgen05.alloc)
   static constexpr size_t SMEM_USED = OFF_STAGES + S * STAGE_BYTES;
   static constexpr size_t SMEM_BYTES = SMEM_USED > 118784 ? SMEM_USED : 118784;
-  static_assert(S >= 2 && S <= 8, "stage ring / header layout");
+  // S >= 3: a stage is refilled one block after its stores are issued, and
+  // the flux warps wait for the next block's stage while on this one
+  static_assert(S >= 3 && S <= 8, "stage ring / header layout");
   static_assert(SMEM_BYTES <= SMAX, "shared memory");
   static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0 && OB % 16 == 0, "TMA chunks");
   static_assert(ROWS <= 128 && NN <= 256 && NN % 16 == 0 && KP % (BF ? 16 : 8) == 0, "UMMA shape");
@@ -385,7 +387,10 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
       tma_load_1d(smem + L::OFF_OP, p.tc_op, L::NS * L::OB, op_bar);
       for (; issued < niter && issued < S; ++issued) issue(issued);
       bool ok = true;
-      // outputs of block jj leave by bulk stores; its stage is then refilled
+      // outputs of block jj leave by bulk stores, one bulk group per block
+      // (empty for a short block, whose epilogue writes global memory); the
+      // stage of block jj - 1 is refilled once that block's stores have read
+      // it, so the warp never waits for the stores it has just issued
       for (int jj = 0; ok && jj < niter; ++jj) {
         const int s = jj % S;
         ok = mbar_wait_or_abort(&out_ready[s], static_cast<uint32_t>((jj / S) & 1), abort_flag);
@@ -405,10 +410,10 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
               tma_store_1d(p.res + f * fs + k0 * Np, sq + (3 + f) * E * Np, L::QB);
             }
           }
-          bulk_commit();
         }
-        if (issued < niter) {  // issued == jj + S: the same stage buffer
-          bulk_wait_read_all();
+        bulk_commit();
+        if (jj >= 1 && issued < niter) {  // issued == jj - 1 + S: the stage of block jj - 1
+          bulk_wait_read_but_last();
           fence_proxy_async();
           issue(issued);
           ++issued;
