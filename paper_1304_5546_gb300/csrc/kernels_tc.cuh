@@ -133,8 +133,32 @@ struct TcLayout {
 template <class L, int ROLE>
 struct RowShare {
   static constexpr int NR = L::X_WARPS / 4, LC = L::LCOLS / 4;
-  static constexpr int VLO = ROLE * L::IV / NR, VHI = (ROLE + 1) * L::IV / NR;
-  static constexpr int LLO = (NR - 1 - ROLE) * LC / NR, LHI = (NR - ROLE) * LC / NR;
+  // work model of a chunk (instructions, roughly): a volume chunk converts
+  // and stores two parts (16) and computes 6 per node inside the element; a
+  // LIFT-part chunk loads, converts and stores one part (12)
+  static constexpr int vol_w(int v) {
+    return 16 + 6 * (L::Np - 4 * v >= 4 ? 4 : (L::Np - 4 * v > 0 ? L::Np - 4 * v : 0));
+  }
+  static constexpr int vol_sum(int a, int b) { return a >= b ? 0 : vol_w(a) + vol_sum(a + 1, b); }
+  // two shares: share 0 takes volume chunks [0, k) and LIFT chunks [l, LC),
+  // share 1 the rest; (k, l) minimises the larger share's work
+  static constexpr int cost(int k, int l) {
+    return vol_sum(0, k) + 12 * (LC - l) > vol_sum(k, L::IV) + 12 * l
+               ? vol_sum(0, k) + 12 * (LC - l)
+               : vol_sum(k, L::IV) + 12 * l;
+  }
+  static constexpr int best(int k, int l, int bk, int bl) {
+    return k > L::IV ? bk * 64 + bl
+           : l > LC  ? best(k + 1, 0, bk, bl)
+                     : best(k, l + 1, cost(k, l) < cost(bk, bl) ? k : bk,
+                            cost(k, l) < cost(bk, bl) ? l : bl);
+  }
+  static constexpr int SPLIT = best(0, 0, L::IV / 2, LC / 2);
+  static constexpr int K2 = SPLIT / 64, L2 = SPLIT % 64;
+  static constexpr int VLO = NR == 2 ? (ROLE == 0 ? 0 : K2) : ROLE * L::IV / NR;
+  static constexpr int VHI = NR == 2 ? (ROLE == 0 ? K2 : L::IV) : (ROLE + 1) * L::IV / NR;
+  static constexpr int LLO = NR == 2 ? (ROLE == 0 ? L2 : 0) : (NR - 1 - ROLE) * LC / NR;
+  static constexpr int LHI = NR == 2 ? (ROLE == 0 ? LC : L2) : (NR - ROLE) * LC / NR;
 };
 
 // Four consecutive K columns (k0, a multiple of 4) of this thread's X row
