@@ -459,20 +459,24 @@ __global__ void __launch_bounds__(Layout<T, N, MEDIA>::THREADS)
 template <typename T, int N, int MODE, bool MEDIA>
 cudaError_t launch_stage_mode(const StageArgs<T>& args, int num_sms, cudaStream_t stream) {
   using L = Layout<T, N, MEDIA>;
-  static int blocks_per_sm = 0;  // per (T, N, MODE, MEDIA), set on the first launch
-  if (blocks_per_sm == 0) {
-    cudaError_t err = cudaFuncSetAttribute(dg_stage_kernel<T, N, MODE, MEDIA>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(L::SMEM_BYTES));
-    if (err != cudaSuccess) return err;
+  // per (T, N, MODE, MEDIA): shared-memory attribute and resident CTAs per
+  // SM, set on the first launch on each device
+  static std::atomic<uint64_t> configured{0};
+  static std::atomic<int> blocks_per_sm{1};
+  cudaError_t err = configure_once_per_device(configured, [] {
+    cudaError_t e = cudaFuncSetAttribute(dg_stage_kernel<T, N, MODE, MEDIA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(L::SMEM_BYTES));
     int nb = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dg_stage_kernel<T, N, MODE, MEDIA>,
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dg_stage_kernel<T, N, MODE, MEDIA>,
                                                         L::THREADS, L::SMEM_BYTES);
-    if (err != cudaSuccess) return err;
-    blocks_per_sm = nb > 0 ? nb : 1;
-  }
+    if (e == cudaSuccess) blocks_per_sm.store(nb > 0 ? nb : 1);
+    return e;
+  });
+  if (err != cudaSuccess) return err;
   const int64_t nblk = (args.K + L::E - 1) / L::E;
-  int64_t grid = static_cast<int64_t>(blocks_per_sm) * num_sms;
+  int64_t grid = static_cast<int64_t>(blocks_per_sm.load()) * num_sms;
   if (grid > nblk) grid = nblk;
   if (grid < 1) grid = 1;
   dg_stage_kernel<T, N, MODE, MEDIA>

@@ -862,14 +862,13 @@ __global__ void __launch_bounds__(TcLayout<N, PREC, MEDIA>::THREADS, 1)
 template <int N, int MODE, int PREC, bool MEDIA>
 cudaError_t launch_stage_tc_mode(const StageArgs<float>& args, int num_sms, cudaStream_t stream) {
   using L = TcLayout<N, PREC, MEDIA>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t err = cudaFuncSetAttribute(dg_stage_tc_kernel<N, MODE, PREC, MEDIA>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(L::SMEM_BYTES));
-    if (err != cudaSuccess) return err;
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  cudaError_t err = configure_once_per_device(configured, [] {
+    return cudaFuncSetAttribute(dg_stage_tc_kernel<N, MODE, PREC, MEDIA>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(L::SMEM_BYTES));
+  });
+  if (err != cudaSuccess) return err;
   const int64_t nblk = (args.K + L::E - 1) / L::E;
   int64_t grid = num_sms;  // one CTA per SM (shared memory and TMEM sized for it)
   if (grid > nblk) grid = nblk;
@@ -943,14 +942,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 template <int MODE>
 cudaError_t launch_batch_tc(const BatchArgs& args, int grid, size_t smem, cudaStream_t stream) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t err = cudaFuncSetAttribute(dg_batch_tc_kernel<MODE>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           TcLayout<5, kTcTf32x3, true>::SMAX);
-    if (err != cudaSuccess) return err;
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  cudaError_t err = configure_once_per_device(configured, [] {
+    return cudaFuncSetAttribute(dg_batch_tc_kernel<MODE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcLayout<5, kTcTf32x3, true>::SMAX);
+  });
+  if (err != cudaSuccess) return err;
   if (grid < 1) return cudaSuccess;
   dg_batch_tc_kernel<MODE><<<grid, kTcThreads, smem, stream>>>(args);
   return cudaGetLastError();

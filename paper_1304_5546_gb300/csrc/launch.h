@@ -4,9 +4,27 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 namespace dgw {
+
+// Per-device, per-kernel configuration: kernel attributes such as the
+// dynamic shared-memory limit are set in each device's context, so each
+// launcher keeps one bit per device (ids 0..63; larger ids configure on
+// every launch).  Returns cudaSuccess once configure() has succeeded on the
+// current device.
+template <class F>
+cudaError_t configure_once_per_device(std::atomic<uint64_t>& done, F configure) {
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  err = configure();
+  if (err == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return err;
+}
 
 // geometry record per element: rx ry sx sy, then per face nx ny Fscale/2
 constexpr int kGeo = 13;
