@@ -88,8 +88,8 @@ typedef int32_t dg_status;
 #define DG_SETUP_TC_BF16 8   /* one product, both operands rounded to BF16   */
 #define DG_SETUP_TC_BF16X3 16 /* three BF16 products: hi/lo split of both
                                  operands (X_hi Op_hi + X_hi Op_lo + X_lo Op_hi) */
-/* Default FP32 products per order: the tensor cores (3xTF32) from N = 3 on,
- * the CUDA cores at N <= 2, where that kernel measured faster.  Override: */
+/* Default FP32 products per order: the tensor cores (3xTF32) from N = 2 on,
+ * the CUDA cores at N = 1, where that kernel measured faster.  Override:  */
 #define DG_SETUP_TC 32       /* FP32: tensor cores (3xTF32) at every order   */
 
 #define DG_N_MAX 7
@@ -133,7 +133,7 @@ void dg_mesh_destroy(dg_mesh* mesh);
  * Surface Contribution"), and the trace maps.  FP32 operators run the
  * element-local products (Dr, Ds, LIFT) on the tensor cores as three TF32
  * products per term (hi/lo splits of both operands, FP32 accumulation) from
- * N = 3 on and on the CUDA cores at N <= 2 (DG_SETUP_TC: tensor cores at
+ * N = 2 on and on the CUDA cores at N = 1 (DG_SETUP_TC: tensor cores at
  * every order); flags DG_SETUP_SIMT selects the CUDA-core FP32 kernel, and one
  * of DG_SETUP_TC_TF32 / _BF16 / _BF16X3 a lower-precision product variant
  * (the precision path of the element-local contractions).  FP64

@@ -410,11 +410,11 @@ dg_status operator_setup(const dg_mesh* mesh, int32_t N, const double* eps, int3
     op->Nafp = op->ref.Nafp;
     op->precision = precision;
     op->flags = flags;
-    // FP32 default: tensor cores from N = 3 on; at N <= 2 the CUDA-core
+    // FP32 default: tensor cores from N = 2 on; at N = 1 the CUDA-core
     // kernel measured faster (order sweep at ~1e7 nodal values per field:
-    // 0.85 vs 2.46 ms/step at N = 1, 0.97 vs 1.31 at N = 2)
+    // 0.87 vs 1.39 ms/step at N = 1; 0.98 vs 0.83 at N = 2)
     op->use_tc = (precision == DG_FP32) && !(flags & DG_SETUP_SIMT) &&
-                 (N >= 3 || variants != 0 || (flags & DG_SETUP_TC));
+                 (N >= 2 || variants != 0 || (flags & DG_SETUP_TC));
     op->tc_prec = (flags & DG_SETUP_TC_TF32)    ? dgw::kTcTf32
                   : (flags & DG_SETUP_TC_BF16)  ? dgw::kTcBf16
                   : (flags & DG_SETUP_TC_BF16X3) ? dgw::kTcBf16x3

@@ -151,13 +151,12 @@ bool plan_ctas(const int64_t* nblk, const double* cost, int num_ctas, int* cta) 
 }
 
 // cost of one block iteration per CTA before dg_batch_tune measures it:
-// seconds measured by dg_batch_tune on a GB300 (152 CTAs, 40-element blocks,
-// a batch of all seven orders with 1400 to 7000 blocks each).  The bytes a
-// block moves predict these badly (1 : 0.21 for N = 1 against N = 5 where
-// 1 : 0.60 was measured): a block has a fixed cost in hand-offs and
-// instruction issue.
+// seconds, rounded from dg_batch_tune on a GB300 (152 CTAs, a batch of all
+// seven orders with 1300 to 6200 blocks each; blocks of 80 elements at N <= 3,
+// 40 above).  The bytes a block moves predict these badly: a block has a
+// fixed cost in hand-offs and instruction issue.
 double model_cost(int N) {
-  static const double us[8] = {0.0, 1.22, 1.51, 1.54, 1.64, 2.02, 2.24, 3.78};
+  static const double us[8] = {0.0, 1.27, 2.47, 2.67, 1.40, 1.75, 2.10, 3.00};
   return 1e-6 * us[N];
 }
 

@@ -63,13 +63,23 @@ struct TcLayout {
   static constexpr int Np = Order<N>::Np;
   static constexpr int Nfp = Order<N>::Nfp;
   static constexpr int Nafp = Order<N>::Nafp;
-  static constexpr int E = 40;  // 3E <= 128 GEMM rows, E % 4 == 0
-  static constexpr int ROWS = 3 * E;
   static constexpr int KD = tc_kd(N), KP = tc_kpp(N, PREC);
   static constexpr int EB = BF ? 2 : 4;         // operand element bytes
   static constexpr int KG = KP * EB / 16;       // core matrices along K
   static constexpr int XPART = BF ? KP / 2 : KP;  // TMEM columns of one X part
   static constexpr int NN = tc_nn(N);
+  // GEMM row tiles of 128 TMEM lanes per block: two at N <= 3, where two
+  // tiles' double-buffered operands and (split) accumulators fit the 512
+  // columns and the stage ring still fits shared memory, so that a block of
+  // 80 elements shares the per-block hand-offs (measured: N = 3 0.86 ->
+  // 0.65 ms/step, N = 2 1.31 -> 0.83; N = 4, which also fits, 0.65 -> 0.68)
+  static constexpr int TILES =
+      (N <= 3 &&
+       2 * 2 * (tc_nsplit(PREC) == 2 ? 2 * NN : NN) + 2 * 2 * tc_nsplit(PREC) * XPART <= 512)
+          ? 2
+          : 1;
+  static constexpr int E = 40 * TILES;  // 3E <= 128 TILES GEMM rows, E % 4 == 0
+  static constexpr int ROWS = 3 * E;
   static constexpr int NPAD = tc_npad(N);
   static constexpr int IV = NPAD / 4;          // volume chunks of 4 nodes
   static constexpr int LCOLS = KP - 2 * NPAD;  // LIFT-part columns (zero beyond Nafp)
@@ -81,11 +91,14 @@ struct TcLayout {
   // the same NN columns instead, so that operand building and MMAs still
   // overlap.  An operand buffer holds X_hi, then X_lo.  Single-product
   // variants: NN columns, X.
+  // With TILES = 2 every buffer holds one such part per tile (accumulator
+  // buffer b, tile t at (b TILES + t) ACC_COLS; operand buffer x, tile t at
+  // OFF_XT + (x TILES + t) XCOLS).
   static constexpr int XCOLS = NS * XPART;
-  static constexpr bool ACC_SPLIT = NS == 2 && 2 * (2 * NN) + 2 * XCOLS <= 512;
+  static constexpr bool ACC_SPLIT = NS == 2 && TILES * (2 * (2 * NN) + 2 * XCOLS) <= 512;
   static constexpr int ACC_COLS = ACC_SPLIT ? 2 * NN : NN;
-  static constexpr int XBUF = (2 * ACC_COLS + 2 * XCOLS <= 512) ? 2 : 1;
-  static constexpr int OFF_XT = 2 * ACC_COLS;
+  static constexpr int XBUF = TILES * (2 * ACC_COLS + 2 * XCOLS) <= 512 ? 2 : 1;
+  static constexpr int OFF_XT = 2 * TILES * ACC_COLS;
   static constexpr int TMEM_COLS = 512;
   // warp roles: 0-3 epilogue; 4-15 operand rows (warp w serves lane quarter
   // w % 4 and takes share (w - 4) / 4 of its rows' chunks); 16-19 face flux
@@ -120,9 +133,10 @@ struct TcLayout {
   static_assert(S >= 3 && S <= 8, "stage ring / header layout");
   static_assert(SMEM_BYTES <= SMAX, "shared memory");
   static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0 && OB % 16 == 0, "TMA chunks");
-  static_assert(ROWS <= 128 && NN <= 256 && NN % 16 == 0 && KP % (BF ? 16 : 8) == 0, "UMMA shape");
+  static_assert(ROWS <= 128 * TILES && NN <= 256 && NN % 16 == 0 && KP % (BF ? 16 : 8) == 0,
+                "UMMA shape");
   static_assert(LCOLS % 4 == 0 && LCOLS >= Nafp + 1, "LIFT part and linear-part column");
-  static_assert(2 * ACC_COLS + XBUF * XCOLS <= TMEM_COLS, "tensor memory");
+  static_assert(TILES * (2 * ACC_COLS + XBUF * XCOLS) <= TMEM_COLS, "tensor memory");
   static_assert(X_WARPS % 4 == 0, "operand-row warps come in lane-quarter groups");
 };
 
@@ -478,8 +492,12 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
                                   abort_flag);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t dacc = tmem + static_cast<uint32_t>((j & 1) * L::ACC_COLS);
-        const uint32_t xh = tmem + static_cast<uint32_t>(L::OFF_XT + xb * L::XCOLS);
+#pragma unroll
+        for (int tile = 0; tile < L::TILES; ++tile) {
+        const uint32_t dacc =
+            tmem + static_cast<uint32_t>(((j & 1) * L::TILES + tile) * L::ACC_COLS);
+        const uint32_t xh =
+            tmem + static_cast<uint32_t>(L::OFF_XT + (xb * L::TILES + tile) * L::XCOLS);
         if constexpr (L::NS == 2 && L::ACC_SPLIT) {
 #pragma unroll
           for (int ks = 0; ks < KS; ++ks)  // X_hi [Op_hi ; Op_lo] -> columns [0, 2 NN)
@@ -502,6 +520,7 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
           for (int ks = 0; ks < KS; ++ks)  // X Op -> columns [0, NN)
             mma(dacc, xh + 8 * ks, ks, IDESC1, ks > 0 ? 1u : 0u);
         }
+        }  // tile
         umma_commit(&mma_done[j & 1]);
         mma_pending = j;
       }
@@ -622,8 +641,6 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
     // ======================= operand-row warps: the GEMM rows into TMEM
     const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. + 31
     const int role = (warp - L::EPI_WARPS) >> 2;  // share of the row's chunks
-    const int r = 32 * quarter + lane;            // this thread's X row
-    const int rc = r / E, re = r - rc * E;        // its output field and element
     const uint32_t lane_base = static_cast<uint32_t>(32 * quarter) << 16;
     bool ok = true;
     for (int j = 0; j < niter; ++j) {
@@ -645,44 +662,67 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
       const float* sg = reinterpret_cast<const float*>(st + 6 * L::QB);
       const float* Fb = Fs + (j & 1) * (L::FB / 4);
 
-      // ---- this thread's X row, split into TF32 hi / lo, into tensor memory.
-      // The X_WARPS / 4 warps of a lane quarter share the row's chunks of 4
-      // columns evenly: a contiguous range of volume chunks (Dr and Ds parts)
-      // and a contiguous range of LIFT-part chunks, taken from the other end.
-      const bool row_ok = r < L::ROWS && re < nvalid;
-      const uint32_t xh = tmem + lane_base + static_cast<uint32_t>(L::OFF_XT + (j % XBUF) * L::XCOLS);
-      const uint32_t xl = xh + L::XPART;
-      const float* qe = sq + re * Np;
-      float rx = 0.f, ry = 0.f, sx = 0.f, sy = 0.f;
-      float a1 = 0.f, a2 = 0.f, a3 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;  // vertex values
-      if (row_ok) {
-        const float* ge = sg + re * GEO;
-        rx = ge[0];
-        ry = ge[1];
-        sx = ge[2];
-        sy = ge[3];
-        if (rc < 2) {  // u = Ez
-          a1 = qe[2 * E * Np];
-          a2 = qe[2 * E * Np + N];
-          a3 = qe[2 * E * Np + Np - 1];
-        } else {  // u = Hx, w = Hy
-          a1 = qe[0];
-          a2 = qe[N];
-          a3 = qe[Np - 1];
-          b1 = qe[E * Np];
-          b2 = qe[E * Np + N];
-          b3 = qe[E * Np + Np - 1];
+      // ---- this thread's X rows (one per row tile), split into TF32 hi /
+      // lo, into tensor memory.  The X_WARPS / 4 warps of a lane quarter share
+      // a row's chunks of 4 columns: a contiguous range of volume chunks (Dr
+      // and Ds parts) and a contiguous range of LIFT-part chunks, taken from
+      // the other end.
+      bool row_ok[L::TILES];
+      int rc[L::TILES];
+      const float* qe[L::TILES];
+      const float* fr[L::TILES];
+      uint32_t xh[L::TILES], xl[L::TILES];
+      float rx[L::TILES], ry[L::TILES], sx[L::TILES], sy[L::TILES];
+      float a1[L::TILES], a2[L::TILES], a3[L::TILES], b1[L::TILES], b2[L::TILES], b3[L::TILES];
+#pragma unroll
+      for (int tile = 0; tile < L::TILES; ++tile) {
+        const int r = 128 * tile + 32 * quarter + lane;  // this thread's X row of the tile
+        const int c = r / E, re = r - c * E;              // its output field and element
+        rc[tile] = c;
+        row_ok[tile] = r < L::ROWS && re < nvalid;
+        xh[tile] = tmem + lane_base +
+                   static_cast<uint32_t>(L::OFF_XT + ((j % XBUF) * L::TILES + tile) * L::XCOLS);
+        xl[tile] = xh[tile] + L::XPART;
+        qe[tile] = sq + re * Np;
+        fr[tile] = Fb + c * E * FES + re * FES;
+        rx[tile] = ry[tile] = sx[tile] = sy[tile] = 0.f;
+        a1[tile] = a2[tile] = a3[tile] = b1[tile] = b2[tile] = b3[tile] = 0.f;  // vertex values
+        if (row_ok[tile]) {
+          const float* ge = sg + re * GEO;
+          const float* q = qe[tile];
+          rx[tile] = ge[0];
+          ry[tile] = ge[1];
+          sx[tile] = ge[2];
+          sy[tile] = ge[3];
+          if (c < 2) {  // u = Ez
+            a1[tile] = q[2 * E * Np];
+            a2[tile] = q[2 * E * Np + N];
+            a3[tile] = q[2 * E * Np + Np - 1];
+          } else {  // u = Hx, w = Hy
+            a1[tile] = q[0];
+            a2[tile] = q[N];
+            a3[tile] = q[Np - 1];
+            b1[tile] = q[E * Np];
+            b2[tile] = q[E * Np + N];
+            b3[tile] = q[E * Np + Np - 1];
+          }
         }
       }
-      const float* fr = Fb + rc * E * FES + re * FES;
-#define DG_BUILD_SHARE(R_)                                                                       \
-  do {                                                                                           \
-    build_x_vol<N, L, R_>(qe, lam, xh, xl, row_ok, rc, rx, ry, sx, sy, a1, a2, a3, b1, b2, b3); \
-    ok = mbar_wait_or_abort(&fs_full[j & 1], static_cast<uint32_t>((j >> 1) & 1), abort_flag);  \
-    if (__all_sync(0xffffffffu, ok))                                                             \
-      build_x_lift<N, L, R_>(fr, xh, xl, row_ok, rc, rx, ry, sx, sy, a1, a2, a3, b1, b2, b3);    \
-    else                                                                                         \
-      ok = false;                                                                                \
+#define DG_BUILD_SHARE(R_)                                                                     \
+  do {                                                                                         \
+    _Pragma("unroll") for (int tile = 0; tile < L::TILES; ++tile)                              \
+      build_x_vol<N, L, R_>(qe[tile], lam, xh[tile], xl[tile], row_ok[tile], rc[tile],         \
+                            rx[tile], ry[tile], sx[tile], sy[tile], a1[tile], a2[tile],         \
+                            a3[tile], b1[tile], b2[tile], b3[tile]);                           \
+    ok = mbar_wait_or_abort(&fs_full[j & 1], static_cast<uint32_t>((j >> 1) & 1), abort_flag); \
+    if (__all_sync(0xffffffffu, ok)) {                                                         \
+      _Pragma("unroll") for (int tile = 0; tile < L::TILES; ++tile)                            \
+        build_x_lift<N, L, R_>(fr[tile], xh[tile], xl[tile], row_ok[tile], rc[tile],           \
+                               rx[tile], ry[tile], sx[tile], sy[tile], a1[tile], a2[tile],      \
+                               a3[tile], b1[tile], b2[tile], b3[tile]);                        \
+    } else {                                                                                   \
+      ok = false;                                                                              \
+    }                                                                                          \
   } while (0)
       switch (role) {  // compile-time chunk ranges: each share unrolls
         case 0:
@@ -719,24 +759,29 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
         break;
       }
       tc_fence_after();
-      float acc[NN];
-      const uint32_t dacc = tmem + static_cast<uint32_t>((j & 1) * L::ACC_COLS) +
-                            (static_cast<uint32_t>(32 * warp) << 16);
+      float acc_t[L::TILES][NN];  // this thread's accumulator row of each tile
 #pragma unroll
-      for (int c0 = 0; c0 < NN; c0 += 16) {
-        if constexpr (L::NS == 2 && L::ACC_SPLIT) {
-          float va[16], vb[16];
-          tmem_ld16(dacc + c0, va);       // X_hi Op_hi + X_lo Op_hi
-          tmem_ld16(dacc + NN + c0, vb);  // X_hi Op_lo
+      for (int tile = 0; tile < L::TILES; ++tile) {
+        float* acc = acc_t[tile];
+        const uint32_t dacc = tmem +
+                              static_cast<uint32_t>(((j & 1) * L::TILES + tile) * L::ACC_COLS) +
+                              (static_cast<uint32_t>(32 * warp) << 16);
 #pragma unroll
-          for (int q = 0; q < 16; q += 2)
-            f32x2_unpack(f32x2_add(f32x2_pack(va[q], va[q + 1]), f32x2_pack(vb[q], vb[q + 1])),
-                         acc[c0 + q], acc[c0 + q + 1]);
-        } else {
-          float va[16];
-          tmem_ld16(dacc + c0, va);  // X Op
+        for (int c0 = 0; c0 < NN; c0 += 16) {
+          if constexpr (L::NS == 2 && L::ACC_SPLIT) {
+            float va[16], vb[16];
+            tmem_ld16(dacc + c0, va);       // X_hi Op_hi + X_lo Op_hi
+            tmem_ld16(dacc + NN + c0, vb);  // X_hi Op_lo
 #pragma unroll
-          for (int q = 0; q < 16; ++q) acc[c0 + q] = va[q];
+            for (int q = 0; q < 16; q += 2)
+              f32x2_unpack(f32x2_add(f32x2_pack(va[q], va[q + 1]), f32x2_pack(vb[q], vb[q + 1])),
+                           acc[c0 + q], acc[c0 + q + 1]);
+          } else {
+            float va[16];
+            tmem_ld16(dacc + c0, va);  // X Op
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[c0 + q] = va[q];
+          }
         }
       }
       tmem_ld_wait();
@@ -747,99 +792,104 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
       block_at(j, k0, nvalid);
       float* sq = reinterpret_cast<float*>(stages + s * L::STAGE_BYTES);  // q, then outputs
       float* sres = sq + 3 * E * Np;
-      const int r = 32 * warp + lane;
-      const int c = r / E, e = r - c * E;
-      // each thread updates only its own row: no ordering with other rows
-      const bool row_ok = r < L::ROWS && e < nvalid;
-      // the row's scale of the right-hand side (media records: sH or sE)
-      float srow = 1.f;
-      if constexpr (MEDIA) {
-        if (row_ok) srow = sq[6 * E * Np + e * GEO + (c < 2 ? 17 : 18)];
-      }
-      const float drow = MEDIA ? p.dt * srow : p.dt;
-      // point source on this row (batched launch, Ez row of a source element)
-      float samp = 0.f;
-      const float* sw = nullptr;
-      if constexpr (TABLE && MEDIA && MODE != kModeRhs) {
-        const int sid = row_ok && c == 2 ? static_cast<int>(sq[6 * E * Np + e * GEO + 19]) - 1 : -1;
-        if (sid >= 0) {
-          const double* m = p.src_meta + 4 * sid;
-          const double t =
-              (static_cast<double>(__ldg(p.step_ctr) - __ldg(p.src_step + sid)) + p.c_stage) * m[0];
-          const double aa = (t - m[1]) * m[2];
-          samp = static_cast<float>(m[3] * (1.0 - 2.0 * aa * aa) * exp(-aa * aa));
-          sw = p.src_w + sid * kSrcStride;
-        }
-      }
-      if (row_ok && nvalid == E) {
-        // full block: in place in the stage buffer, node pairs in packed
-        // FP32x2 arithmetic (res = a res + dt rhs, q = q + b res)
-        float* rq = sq + c * E * Np + e * Np;
-        float* rr = sres + c * E * Np + e * Np;
-        const f32x2 a2 = f32x2_dup(p.a), b2 = f32x2_dup(p.b), dt2 = f32x2_dup(drow);
+      // each thread updates its own row of every tile: no ordering with other rows
 #pragma unroll
-        for (int n = 0; n + 1 < Np; n += 2) {
-          if (MODE == kModeRhs) {
-            rq[n] = MEDIA ? srow * acc[n] : acc[n];
-            rq[n + 1] = MEDIA ? srow * acc[n + 1] : acc[n + 1];
-          } else {
-            f32x2 rn = f32x2_mul(dt2, f32x2_pack(acc[n], acc[n + 1]));
-            if (MODE == kModeStage) rn = f32x2_fma(a2, f32x2_pack(rr[n], rr[n + 1]), rn);
-            const f32x2 qn = f32x2_fma(b2, rn, f32x2_pack(rq[n], rq[n + 1]));
-            f32x2_unpack(qn, rq[n], rq[n + 1]);
-            f32x2_unpack(rn, rr[n], rr[n + 1]);
-          }
+      for (int tile = 0; tile < L::TILES; ++tile) {
+        const int r = 128 * tile + 32 * warp + lane;
+        const float* acc = acc_t[tile];
+        const int c = r / E, e = r - c * E;
+        // each thread updates only its own row: no ordering with other rows
+        const bool row_ok = r < L::ROWS && e < nvalid;
+        // the row's scale of the right-hand side (media records: sH or sE)
+        float srow = 1.f;
+        if constexpr (MEDIA) {
+          if (row_ok) srow = sq[6 * E * Np + e * GEO + (c < 2 ? 17 : 18)];
         }
-        if (Np & 1) {
-          constexpr int n = Np - 1;
-          if (MODE == kModeRhs) {
-            rq[n] = MEDIA ? srow * acc[n] : acc[n];
-          } else {
-            float rn = drow * acc[n];
-            if (MODE == kModeStage) rn = __fmaf_rn(p.a, rr[n], rn);
-            rq[n] = __fmaf_rn(p.b, rn, rq[n]);
-            rr[n] = rn;
-          }
-        }
+        const float drow = MEDIA ? p.dt * srow : p.dt;
+        // point source on this row (batched launch, Ez row of a source element)
+        float samp = 0.f;
+        const float* sw = nullptr;
         if constexpr (TABLE && MEDIA && MODE != kModeRhs) {
-          if (sw) {  // res += s w, q += b s w
-            for (int n = 0; n < Np; ++n) {
-              const float v = samp * __ldg(sw + n);
-              rr[n] += v;
-              rq[n] = __fmaf_rn(p.b, v, rq[n]);
-            }
+          const int sid = row_ok && c == 2 ? static_cast<int>(sq[6 * E * Np + e * GEO + 19]) - 1 : -1;
+          if (sid >= 0) {
+            const double* m = p.src_meta + 4 * sid;
+            const double t =
+                (static_cast<double>(__ldg(p.step_ctr) - __ldg(p.src_step + sid)) + p.c_stage) * m[0];
+            const double aa = (t - m[1]) * m[2];
+            samp = static_cast<float>(m[3] * (1.0 - 2.0 * aa * aa) * exp(-aa * aa));
+            sw = p.src_w + sid * kSrcStride;
           }
         }
-      } else if (row_ok) {
-        // ragged last block: straight to global memory
-        const int off = c * E * Np + e * Np;
-        const bool full_block = false;
-        const int64_t g = static_cast<int64_t>(c) * fs + static_cast<int64_t>(k0 + e) * Np;
-#pragma unroll
-        for (int n = 0; n < Np; ++n) {
-          const float rhs = MEDIA && MODE == kModeRhs ? srow * acc[n] : acc[n];
-          if (MODE == kModeRhs) {
-            if (full_block)
-              sq[off + n] = rhs;
-            else
-              p.rhs[g + n] = rhs;
-          } else {
-            float rn =
-                (MODE == kModeFirstStage) ? drow * rhs : p.a * sres[off + n] + drow * rhs;
-            if constexpr (TABLE && MEDIA) {
-              if (sw) rn += samp * __ldg(sw + n);
-            }
-            const float qn = sq[off + n] + p.b * rn;
-            if (full_block) {
-              sq[off + n] = qn;
-              sres[off + n] = rn;
+        if (row_ok && nvalid == E) {
+          // full block: in place in the stage buffer, node pairs in packed
+          // FP32x2 arithmetic (res = a res + dt rhs, q = q + b res)
+          float* rq = sq + c * E * Np + e * Np;
+          float* rr = sres + c * E * Np + e * Np;
+          const f32x2 a2 = f32x2_dup(p.a), b2 = f32x2_dup(p.b), dt2 = f32x2_dup(drow);
+  #pragma unroll
+          for (int n = 0; n + 1 < Np; n += 2) {
+            if (MODE == kModeRhs) {
+              rq[n] = MEDIA ? srow * acc[n] : acc[n];
+              rq[n + 1] = MEDIA ? srow * acc[n + 1] : acc[n + 1];
             } else {
-              p.qout[g + n] = qn;
-              p.res[g + n] = rn;
+              f32x2 rn = f32x2_mul(dt2, f32x2_pack(acc[n], acc[n + 1]));
+              if (MODE == kModeStage) rn = f32x2_fma(a2, f32x2_pack(rr[n], rr[n + 1]), rn);
+              const f32x2 qn = f32x2_fma(b2, rn, f32x2_pack(rq[n], rq[n + 1]));
+              f32x2_unpack(qn, rq[n], rq[n + 1]);
+              f32x2_unpack(rn, rr[n], rr[n + 1]);
+            }
+          }
+          if (Np & 1) {
+            constexpr int n = Np - 1;
+            if (MODE == kModeRhs) {
+              rq[n] = MEDIA ? srow * acc[n] : acc[n];
+            } else {
+              float rn = drow * acc[n];
+              if (MODE == kModeStage) rn = __fmaf_rn(p.a, rr[n], rn);
+              rq[n] = __fmaf_rn(p.b, rn, rq[n]);
+              rr[n] = rn;
+            }
+          }
+          if constexpr (TABLE && MEDIA && MODE != kModeRhs) {
+            if (sw) {  // res += s w, q += b s w
+              for (int n = 0; n < Np; ++n) {
+                const float v = samp * __ldg(sw + n);
+                rr[n] += v;
+                rq[n] = __fmaf_rn(p.b, v, rq[n]);
+              }
+            }
+          }
+        } else if (row_ok) {
+          // ragged last block: straight to global memory
+          const int off = c * E * Np + e * Np;
+          const bool full_block = false;
+          const int64_t g = static_cast<int64_t>(c) * fs + static_cast<int64_t>(k0 + e) * Np;
+  #pragma unroll
+          for (int n = 0; n < Np; ++n) {
+            const float rhs = MEDIA && MODE == kModeRhs ? srow * acc[n] : acc[n];
+            if (MODE == kModeRhs) {
+              if (full_block)
+                sq[off + n] = rhs;
+              else
+                p.rhs[g + n] = rhs;
+            } else {
+              float rn =
+                  (MODE == kModeFirstStage) ? drow * rhs : p.a * sres[off + n] + drow * rhs;
+              if constexpr (TABLE && MEDIA) {
+                if (sw) rn += samp * __ldg(sw + n);
+              }
+              const float qn = sq[off + n] + p.b * rn;
+              if (full_block) {
+                sq[off + n] = qn;
+                sres[off + n] = rn;
+              } else {
+                p.qout[g + n] = qn;
+                p.res[g + n] = rn;
+              }
             }
           }
         }
-      }
+      }  // tile
       fence_proxy_async();
       mbar_arrive(&out_ready[s]);
     }
