@@ -152,11 +152,11 @@ bool plan_ctas(const int64_t* nblk, const double* cost, int num_ctas, int* cta) 
 
 // cost of one block iteration per CTA before dg_batch_tune measures it:
 // seconds, rounded from dg_batch_tune on a GB300 (152 CTAs, a batch of all
-// seven orders with 1300 to 6200 blocks each; blocks of 80 elements at N <= 3,
-// 40 above).  The bytes a block moves predict these badly: a block has a
-// fixed cost in hand-offs and instruction issue.
+// seven orders with 1400 to 7000 blocks of 40 elements each, costs observed
+// in the mixed launch).  The bytes a block moves predict these badly: a block
+// has a fixed cost in hand-offs and instruction issue.
 double model_cost(int N) {
-  static const double us[8] = {0.0, 1.27, 2.47, 2.67, 1.40, 1.75, 2.10, 3.00};
+  static const double us[8] = {0.0, 1.16, 1.30, 1.36, 1.41, 2.64, 3.06, 4.38};
   return 1e-6 * us[N];
 }
 

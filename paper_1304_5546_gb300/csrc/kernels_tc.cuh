@@ -53,7 +53,10 @@
 
 namespace dgw {
 
-template <int N, int PREC_, bool MEDIA_ = false>
+// ONE_TILE: one 128-row tile at every order (the batched launch, whose
+// seven inlined order bodies share one register budget; two-tile bodies
+// there measured slower through spills).
+template <int N, int PREC_, bool MEDIA_ = false, bool ONE_TILE = false>
 struct TcLayout {
   static constexpr int PREC = PREC_;
   static constexpr bool MEDIA = MEDIA_;
@@ -74,7 +77,7 @@ struct TcLayout {
   // 80 elements shares the per-block hand-offs (measured: N = 3 0.86 ->
   // 0.65 ms/step, N = 2 1.31 -> 0.83; N = 4, which also fits, 0.65 -> 0.68)
   static constexpr int TILES =
-      (N <= 3 &&
+      (!ONE_TILE && N <= 3 &&
        2 * 2 * (tc_nsplit(PREC) == 2 ? 2 * NN : NN) + 2 * 2 * tc_nsplit(PREC) * XPART <= 512)
           ? 2
           : 1;
@@ -318,7 +321,7 @@ __device__ __forceinline__ void build_x_lift(const float* fr, uint32_t xh, uint3
 template <int N, int MODE, int PREC, bool MEDIA, bool TABLE>
 __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const int first,
                                               const int G, unsigned char* smem) {
-  using L = TcLayout<N, PREC, MEDIA>;
+  using L = TcLayout<N, PREC, MEDIA, TABLE>;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
   constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FES = L::FES, XBUF = L::XBUF;
   constexpr int FT = L::FLUX_THREADS, TASKS = L::TASKS, TPT = L::TPT;
@@ -971,7 +974,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const unsigned long long t_start = p.cta_clock ? global_ns() : 0ull;
 #define DG_BATCH_GROUP(NN_)                                                              \
   if (b >= c0[NN_ - 1] && b < c0[NN_]) {                                                 \
-    static_assert(TcLayout<NN_, kTcTf32x3, true>::THREADS == kTcThreads, "block size");   \
+    static_assert(TcLayout<NN_, kTcTf32x3, true, true>::THREADS == kTcThreads, "block size"); \
     tc_stage_body<NN_, MODE, kTcTf32x3, true, true>(p.g[NN_ - 1], b - c0[NN_ - 1],        \
                                                     c0[NN_] - c0[NN_ - 1], smem);        \
     if (p.cta_clock && threadIdx.x == 0) {                                               \
