@@ -154,3 +154,33 @@ def test_memory_budget_admission(P, reqs):
     assert inf_b["t_admit"] >= inf_a["t_admit"]
     assert inf_c["state"] == 3 and inf_c["status"] == 6  # DG_ERR_OOM
     assert np.array_equal(ob, b.alone(P, inf_b["dt"], inf_b["nsteps"]))
+
+
+def test_concurrent_submitters(P, reqs):
+    # four host threads submit and wait at once; every result equals the
+    # request's solve alone
+    import threading
+    srv = P.Server(_capacity(reqs))
+    outs = {}
+    errors = []
+
+    def client(k):
+        try:
+            for r in reqs[k::2]:
+                o = r.out()
+                rid = srv.submit(r.solver, r.T, source=r.source, q0=r.q0, out=o)
+                info = srv.wait(rid, timeout=60.0)
+                outs[(k, id(r))] = (r, o, info)
+        except Exception as ex:  # noqa: BLE001 (reported below)
+            errors.append(ex)
+
+    threads = [threading.Thread(target=client, args=(k % 2,)) for k in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    srv.close()
+    assert not errors, errors
+    for r, o, info in outs.values():
+        assert info["state"] == 2
+        assert np.array_equal(o, r.alone(P, info["dt"], info["nsteps"]))
