@@ -161,26 +161,27 @@ def test_concurrent_submitters(P, reqs):
     # request's solve alone
     import threading
     srv = P.Server(_capacity(reqs))
-    outs = {}
+    outs = []  # (request, result, info) of every submission
     errors = []
 
     def client(k):
         try:
-            for r in reqs[k::2]:
+            for r in reqs[k % 2::2]:
                 o = r.out()
                 rid = srv.submit(r.solver, r.T, source=r.source, q0=r.q0, out=o)
                 info = srv.wait(rid, timeout=60.0)
-                outs[(k, id(r))] = (r, o, info)
+                outs.append((r, o, info))
         except Exception as ex:  # noqa: BLE001 (reported below)
             errors.append(ex)
 
-    threads = [threading.Thread(target=client, args=(k % 2,)) for k in range(4)]
+    threads = [threading.Thread(target=client, args=(k,)) for k in range(4)]
     for t in threads:
         t.start()
     for t in threads:
         t.join()
     srv.close()
     assert not errors, errors
-    for r, o, info in outs.values():
+    assert len(outs) == 2 * len(reqs)
+    for r, o, info in outs:
         assert info["state"] == 2
         assert np.array_equal(o, r.alone(P, info["dt"], info["nsteps"]))
