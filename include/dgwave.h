@@ -208,6 +208,19 @@ dg_status dg_get_geometry(const dg_op* op, double* rx, double* ry, double* sx,
  * face node; boundary face nodes have vmapP = vmapM).                     */
 dg_status dg_get_maps(const dg_op* op, int64_t* vmapM, int64_t* vmapP);
 
+/* dg_operator_tune: the kernel choice of an FP32 operator, by measurement.
+ * Times `reps` stage launches of the tensor-core kernel and of the
+ * CUDA-core kernel on the operator's own mesh (scratch fields, allocated
+ * and freed here; synchronises `stream`) and keeps the faster for later
+ * calls; writes the milliseconds per launch of each (NULL outputs skipped).
+ * Operators whose set-up fixed the kernel (FP64, DG_SETUP_SIMT,
+ * DG_SETUP_TC, DG_SETUP_TC_*) are left as they are and get -1.  Call it
+ * before stepping, not while calls on the operator are in flight.
+ * Errors: DG_ERR_ARG (NULL, reps < 1), DG_ERR_NO_DEVICE, DG_ERR_OOM,
+ * DG_ERR_CUDA.                                                             */
+dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, double* ms_tc,
+                           double* ms_cuda_cores);
+
 /* CFL time step: cfl * (2/3) * min over elements of the inradius *
  * (spacing of the first two Gauss-Lobatto points of order N).             */
 dg_status dg_cfl_dt(const dg_op* op, double cfl, double* dt);
@@ -517,7 +530,8 @@ dg_status dg_check_finite(const dg_op* op, const void* d_q, void* stream);
 dg_status dg_sync_check(const dg_op* op, void* stream);
 
 /* Number of kernel launches enqueued by this operator since setup (one per
- * dg_rhs, five per step, plus one per dg_check_finite).                   */
+ * dg_rhs, five per step, one per dg_check_finite, and 2 (reps + 1) per
+ * dg_operator_tune that measured).                                         */
 int64_t dg_launch_count(const dg_op* op);
 
 /* Thread-local message of the last failing call on this thread ("" if

@@ -23,7 +23,8 @@ from ._lib import (  # noqa: F401
 
 __all__ = [
     "dg_mesh_create", "dg_mesh_info", "dg_mesh_connectivity", "dg_mesh_destroy",
-    "dg_operator_setup", "dg_operator_setup_media", "dg_operator_set_alpha", "dg_get_info", "dg_get_nodes", "dg_get_reference",
+    "dg_operator_setup", "dg_operator_setup_media", "dg_operator_set_alpha", "dg_operator_tune",
+    "dg_get_info", "dg_get_nodes", "dg_get_reference",
     "dg_get_geometry", "dg_get_maps", "dg_cfl_dt", "dg_lsrk_coefficients",
     "dg_op_destroy", "dg_rhs", "dg_step", "dg_step_static", "dg_solve", "dg_step_host",
     "dg_check_finite", "dg_sync_check", "dg_launch_count", "dg_last_error",
@@ -104,6 +105,15 @@ def dg_operator_setup_media(mesh, N, eps, precision=DG_FP32, flags=0):
 
 def dg_operator_set_alpha(op, alpha):
     _lib.check(_lib.load().dg_operator_set_alpha(op, alpha), "dg_operator_set_alpha")
+
+
+def dg_operator_tune(op, reps=5, stream=None):
+    """Returns (ms per launch on the tensor cores, on the CUDA cores); -1
+    for operators whose kernel the set-up fixed."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _lib.check(_lib.load().dg_operator_tune(op, reps, _stream_handle(stream), ctypes.byref(a),
+                                            ctypes.byref(b)), "dg_operator_tune")
+    return a.value, b.value
 
 
 def dg_get_info(op):
@@ -462,6 +472,10 @@ class Solver:
 
     def cfl_dt(self, cfl=1.0):
         return dg_cfl_dt(self.op, cfl)
+
+    def tune(self, reps=5, stream=None):
+        """Pick the faster FP32 kernel for this mesh (dg_operator_tune)."""
+        return dg_operator_tune(self.op, reps, stream)
 
     def nodes(self):
         return dg_get_nodes(self.op)

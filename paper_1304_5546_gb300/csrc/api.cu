@@ -587,6 +587,71 @@ extern "C" dg_status dg_get_maps(const dg_op* op, int64_t* vmapM, int64_t* vmapP
   return DG_OK;
 }
 
+extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, double* ms_tc,
+                                      double* ms_cuda_cores) {
+  dgw::clear_error();
+  dg_status st = check_device_op(op, "dg_operator_tune");
+  if (st) return st;
+  if (reps < 1) return fail(DG_ERR_ARG, "dg_operator_tune: reps = %d < 1", reps);
+  if (ms_tc) *ms_tc = -1.0;
+  if (ms_cuda_cores) *ms_cuda_cores = -1.0;
+  const int32_t forced = DG_SETUP_SIMT | DG_SETUP_TC | DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 |
+                         DG_SETUP_TC_BF16X3;
+  if (op->precision != DG_FP32 || (op->flags & forced)) return DG_OK;  // nothing to choose
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t err = cudaSuccess;
+  if (!op->d_tcop) {  // the tensor-core kernel's operator tiles
+    const std::vector<unsigned char> tiles = tc_operator_tiles(op->ref, dgw::kTcTf32x3);
+    err = cudaMalloc(&op->d_tcop, tiles.size());
+    if (err == cudaSuccess)
+      err = cudaMemcpy(op->d_tcop, tiles.data(), tiles.size(), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_operator_tune: operator tiles");
+  }
+  // scratch fields q, q_out and res (zero), stage-2 launches of each kernel
+  const size_t fb = 3 * static_cast<size_t>(op->fstride) * sizeof(float);
+  float* buf = nullptr;
+  err = cudaMalloc(reinterpret_cast<void**>(&buf), 3 * fb);
+  if (err == cudaSuccess) err = cudaMemsetAsync(buf, 0, 3 * fb, s);
+  if (err != cudaSuccess) {
+    if (buf) cudaFree(buf);
+    return cuda_fail(err, "dg_operator_tune: scratch fields");
+  }
+  dgw::StageArgs<float> a = base_args<float>(op);
+  a.qin = buf;
+  a.qout = buf + 3 * op->fstride;
+  a.res = buf + 6 * op->fstride;
+  a.a = static_cast<float>(op->lsrk_a[1]);
+  a.b = static_cast<float>(op->lsrk_b[1]);
+  a.dt = 1e-6f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bool was_tc = op->use_tc;
+  float ms[2] = {0.f, 0.f};
+  for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+    op->use_tc = (v == 0);
+    err = launch_order<float>(op, a, dgw::kModeStage, s);  // warm
+    if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && err == cudaSuccess; ++r)
+      err = launch_order<float>(op, a, dgw::kModeStage, s);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms[v], e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  op->launches.fetch_add(2 * (reps + 1), std::memory_order_relaxed);
+  if (err != cudaSuccess) {
+    op->use_tc = was_tc;
+    return cuda_fail(err, "dg_operator_tune");
+  }
+  op->use_tc = ms[0] <= ms[1];
+  if (ms_tc) *ms_tc = ms[0] / reps;
+  if (ms_cuda_cores) *ms_cuda_cores = ms[1] / reps;
+  return DG_OK;
+}
+
 extern "C" dg_status dg_cfl_dt(const dg_op* op, double cfl, double* dt) {
   dgw::clear_error();
   if (!op || !dt) return fail(DG_ERR_ARG, "dg_cfl_dt: NULL argument");

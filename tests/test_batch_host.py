@@ -146,3 +146,16 @@ def test_set_alpha_checks(dgw):
         dgw.dg_op_destroy(op)
         dgw.dg_op_destroy(media)
         dgw.dg_mesh_destroy(mesh)
+
+
+def test_tune_needs_a_device_operator(dgw):
+    from paper_1304_5546_gb300 import DGError
+    VX, VY, EToV = jittered_delaunay_mesh(3, seed=1)
+    mesh = dgw.dg_mesh_create(VX, VY, EToV)
+    op = dgw.dg_operator_setup(mesh, 3, dgw.DG_FP32, dgw.DG_SETUP_HOST_ONLY)
+    try:
+        with pytest.raises(DGError):
+            dgw.dg_operator_tune(op, 2, stream=0)
+    finally:
+        dgw.dg_op_destroy(op)
+        dgw.dg_mesh_destroy(mesh)
