@@ -77,14 +77,18 @@ def build(force=False, verbose=False, extra_flags=()):
 
 
 def kernel_source_hash():
-    """Short hash of the kernel sources; profiles record it so that stale
+    """Short hash of the kernel sources (code only: // comments, trailing
+    blanks and empty lines are left out); profiles record it so that stale
     counter captures are not reported for a changed kernel."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in sorted(os.listdir(CSRC)):
         if name.startswith("kernels") or name in ("launch.h", "ptx.cuh"):
-            with open(os.path.join(CSRC, name), "rb") as f:
-                h.update(name.encode() + f.read())
+            with open(os.path.join(CSRC, name), encoding="utf-8") as f:
+                lines = (re.sub(r"//.*$", "", line).rstrip() for line in f)
+                code = "\n".join(line for line in lines if line)
+            h.update(name.encode() + code.encode())
     return h.hexdigest()[:16]
 
 

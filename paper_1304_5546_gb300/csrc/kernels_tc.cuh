@@ -20,13 +20,17 @@
 // and the operator tile holds 1 there for every node) the right-hand side
 // is the GEMM D = X [Dr | Ds | LIFT | 1]^T, with no further term.
 // The deflation keeps the products' operands O(h^2) for smooth fields, so
-// their TF32 rounding stays far below FP32 accuracy.  M = 3E rows (<= 128),
-// K = 2 Np + Nafp + 1 (padded to 8), N = Np (padded to 16).  FP32 accuracy
+// their TF32 rounding stays far below FP32 accuracy.  M = 3E rows in one
+// 128-row tile (E = 40), or in two tiles at N <= 3 (E = 80: each tile is its
+// own MMA group and each operand-row and epilogue thread owns one row per
+// tile), K = 2 Np + Nafp + 1 (padded to 8), N = Np (padded to 16).  FP32 accuracy
 // comes from three TF32 products, X_hi Op_hi + X_hi Op_lo + X_lo Op_hi: X_hi
 // keeps the top 11 significand bits of X, X_lo = X - X_hi (exact in FP32,
 // truncated to TF32 by the tensor core); Op's hi/lo split is made on the host
 // from FP64 with round-to-nearest.  One MMA of N = 2 Np' computes X_hi
-// [Op_hi ; Op_lo] so that X_hi is read once; a second adds X_lo Op_hi.
+// [Op_hi ; Op_lo] so that X_hi is read once; a second adds X_lo Op_hi (at
+// N = 7 all three products go to one accumulator of Np' columns, see
+// TcLayout).
 //
 // X never touches shared memory: the build warps write it straight into
 // tensor memory (tcgen05.st; lane = row, one column per K index), and the
@@ -41,12 +45,14 @@
 // LSRK update in place in the stage buffer), 8 flux warps (upwind flux at
 // every face node into a double-buffered shared-memory array, up to two
 // blocks ahead; neighbour traces gathered one block ahead), 8 operand-row
-// warps (two per lane quarter, each an even share of its rows' volume-part
-// and LIFT-part column chunks, with packed FP32x2 arithmetic; the LIFT part
-// waits for the block's fluxes), one MMA warp, one memory warp (1D TMA bulk
-// loads into a ring of stage buffers, bulk stores of full blocks from the
-// same buffers).  Every wait is bounded; on expiry the CTA sets the status
-// word, drains its copies (bounded), frees its TMEM and returns.
+// warps (two per lane quarter, each a share of its rows' volume-part and
+// LIFT-part column chunks balanced by a work model, with packed FP32x2
+// arithmetic; the LIFT part waits for the block's fluxes), one MMA warp, one
+// memory warp (1D TMA bulk loads into a ring of stage buffers, bulk stores
+// of full blocks from the same buffers, a stage refilled once the stores of
+// the block after it are issued).  Every wait is bounded; on expiry the CTA
+// sets the status word, drains its copies (bounded), frees its TMEM and
+// returns.
 #pragma once
 
 #include "kernels.cuh"
