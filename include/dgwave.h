@@ -73,6 +73,8 @@ typedef int32_t dg_status;
 #define DG_ERR_NONFINITE 7          /* NaN or Inf found in a field           */
 #define DG_ERR_NO_DEVICE 8          /* operator was set up host-only         */
 #define DG_ERR_TIMEOUT 9            /* a kernel's bounded wait expired       */
+#define DG_ERR_IO 10                /* a checkpoint file could not be read or
+                                       written                               */
 
 #define DG_FP64 0
 #define DG_FP32 1
@@ -463,6 +465,7 @@ int64_t dg_batch_launch_count(const dg_batch* batch);
 #define DG_REQUEST_RUNNING 1
 #define DG_REQUEST_DONE 2
 #define DG_REQUEST_FAILED 3
+#define DG_REQUEST_CANCELLED 4
 
 typedef struct dg_server dg_server;
 
@@ -510,6 +513,14 @@ dg_status dg_server_wait(dg_server* server, int64_t request_id, double timeout_s
 /* The request's current state and times, without waiting.                 */
 dg_status dg_server_info(dg_server* server, int64_t request_id, dg_request_info* info);
 
+/* dg_server_cancel: a queued request is dropped at the worker's next
+ * admission pass, a running one leaves the batch at the next chunk boundary
+ * without its result (`out` is not written); either then reports
+ * DG_REQUEST_CANCELLED.  A request whose result is already on its way to
+ * host memory completes normally.
+ * Errors: DG_ERR_ARG (unknown id, or the request already finished).       */
+dg_status dg_server_cancel(dg_server* server, int64_t request_id);
+
 /* Forget a finished request (its id becomes unknown).                     */
 dg_status dg_server_release(dg_server* server, int64_t request_id);
 
@@ -517,6 +528,31 @@ dg_status dg_server_release(dg_server* server, int64_t request_id);
  * kernel launches.  NULL outputs are skipped.                              */
 dg_status dg_server_stats(dg_server* server, int64_t* completed, int64_t* failed, int64_t* steps,
                           int64_t* launches);
+
+/* ---------------------------------------------------------- checkpoints ---
+ * The state of a solve between steps is its three fields, its time and its
+ * step count (the LSRK residual needs no saving: the first stage of a step
+ * overwrites it).  dg_checkpoint_save writes q's first K * Np values of each
+ * field (field f at f * q_stride) to the file `path`, with t and step, in
+ * the operator's precision.  The header records the operator (N, K,
+ * precision, medium) and a hash of its node coordinates and permittivities.
+ * The file is written under a temporary name and then renamed.
+ * dg_checkpoint_load refuses a file written for another operator or mesh,
+ * or whose field data no longer match their hash, and otherwise fills q (the
+ * entries beyond K * Np are left alone) and returns t and step.  Resuming
+ * from a checkpoint gives bit for bit what running on would have given.
+ * q is device memory of the operator's device, or host memory with
+ * DG_CKPT_HOST.  Both calls are synchronous.
+ * Errors: DG_ERR_ARG (NULL, unknown flags, q_stride < K * Np, a file for
+ * another operator or mesh, damaged data), DG_ERR_NO_DEVICE (device fields
+ * with a host-only operator), DG_ERR_IO (open, read, write, rename),
+ * DG_ERR_OOM, DG_ERR_CUDA.                                                 */
+#define DG_CKPT_HOST 1 /* the fields are in host memory */
+
+dg_status dg_checkpoint_save(const dg_op* op, const void* q, int64_t q_stride, int32_t flags,
+                             double t, int64_t step, const char* path);
+dg_status dg_checkpoint_load(const dg_op* op, const char* path, void* q, int64_t q_stride,
+                             int32_t flags, double* t, int64_t* step);
 
 /* dg_check_finite: synchronises `stream`, then scans the first K*Np values
  * of each field of d_q for NaN/Inf.  Returns DG_ERR_NONFINITE if any is
@@ -528,6 +564,19 @@ dg_status dg_check_finite(const dg_op* op, const void* d_q, void* stream);
  * the operator's kernel status word: DG_ERR_TIMEOUT if a stage kernel gave
  * up waiting for its own shared-memory copies (bounded waits, ~2 s).       */
 dg_status dg_sync_check(const dg_op* op, void* stream);
+
+/* dg_test_wait_timeout: the timeout path, exercised without any fault.
+ * Launches one right-hand-side pass of a tensor-core operator whose memory
+ * warp first waits, bounded by 0.1 s, for a device flag that nothing sets.
+ * The wait runs out, the CTAs set the operator's status word, stop their
+ * other warps through their shared abort flag, free their tensor memory and
+ * return, having read and written no field.  Synchronises `stream`.  A
+ * following dg_sync_check returns DG_ERR_TIMEOUT (and clears the word); the
+ * operator stays usable.  The paper has no counterpart: this tests the
+ * failure detection of the bounded waits.
+ * Errors: DG_ERR_ARG (NULL, not a tensor-core operator), DG_ERR_NO_DEVICE,
+ * DG_ERR_CUDA.                                                             */
+dg_status dg_test_wait_timeout(const dg_op* op, void* stream);
 
 /* Number of kernel launches enqueued by this operator since setup (one per
  * dg_rhs, five per step, one per dg_check_finite, and 2 (reps + 1) per

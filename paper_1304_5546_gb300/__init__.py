@@ -27,12 +27,13 @@ __all__ = [
     "dg_get_info", "dg_get_nodes", "dg_get_reference",
     "dg_get_geometry", "dg_get_maps", "dg_cfl_dt", "dg_lsrk_coefficients",
     "dg_op_destroy", "dg_rhs", "dg_step", "dg_step_static", "dg_solve", "dg_step_host",
-    "dg_check_finite", "dg_sync_check", "dg_launch_count", "dg_last_error",
+    "dg_check_finite", "dg_sync_check", "dg_launch_count", "dg_last_error", "dg_test_wait_timeout",
+    "dg_checkpoint_save", "dg_checkpoint_load",
     "dg_batch_create", "dg_batch_destroy", "dg_batch_add", "dg_batch_remove", "dg_batch_info",
     "dg_batch_set_fields", "dg_batch_get_fields", "dg_batch_step", "dg_batch_tune",
     "dg_batch_plan", "dg_batch_plan_ctas", "dg_batch_sync_check", "dg_batch_launch_count",
     "dg_server_clock", "dg_server_create", "dg_server_destroy", "dg_server_submit",
-    "dg_server_wait", "dg_server_info", "dg_server_release", "dg_server_stats",
+    "dg_server_wait", "dg_server_info", "dg_server_release", "dg_server_cancel", "dg_server_stats",
     "Solver", "Batch", "Server", "DGError", "DG_FP32", "DG_FP64",
 ]
 
@@ -218,6 +219,29 @@ def dg_sync_check(op, stream=None):
     _lib.check(_lib.load().dg_sync_check(op, _stream_handle(stream)), "dg_sync_check")
 
 
+def dg_test_wait_timeout(op, stream=None):
+    _lib.check(_lib.load().dg_test_wait_timeout(op, _stream_handle(stream)), "dg_test_wait_timeout")
+
+
+def dg_checkpoint_save(op, q, q_stride, t, step, path):
+    """q: device tensor (field stride q_stride) or host numpy array / CPU
+    tensor (DG_CKPT_HOST)."""
+    host = not (hasattr(q, "is_cuda") and q.is_cuda)
+    _lib.check(_lib.load().dg_checkpoint_save(op, _buf_ptr(q), q_stride,
+                                              _lib.DG_CKPT_HOST if host else 0, t, step,
+                                              str(path).encode()), "dg_checkpoint_save")
+
+
+def dg_checkpoint_load(op, path, q, q_stride):
+    """Fills q (device tensor or host array); returns (t, step)."""
+    host = not (hasattr(q, "is_cuda") and q.is_cuda)
+    t, step = ctypes.c_double(), ctypes.c_int64()
+    _lib.check(_lib.load().dg_checkpoint_load(op, str(path).encode(), _buf_ptr(q), q_stride,
+                                              _lib.DG_CKPT_HOST if host else 0, ctypes.byref(t),
+                                              ctypes.byref(step)), "dg_checkpoint_load")
+    return t.value, step.value
+
+
 def dg_launch_count(op):
     return int(_lib.load().dg_launch_count(op))
 
@@ -365,6 +389,10 @@ def dg_server_info(server, request_id):
     return _info_dict(info)
 
 
+def dg_server_cancel(server, request_id):
+    _lib.check(_lib.load().dg_server_cancel(server, request_id), "dg_server_cancel")
+
+
 def dg_server_release(server, request_id):
     _lib.check(_lib.load().dg_server_release(server, request_id), "dg_server_release")
 
@@ -472,6 +500,14 @@ class Solver:
 
     def cfl_dt(self, cfl=1.0):
         return dg_cfl_dt(self.op, cfl)
+
+    def save(self, q, path, t=0.0, step=0):
+        """Checkpoint the fields q (a field tensor of this solver) with t, step."""
+        dg_checkpoint_save(self.op, q, self.fstride, t, step, path)
+
+    def load(self, path, q):
+        """Resume: fill q from a checkpoint of this solver's mesh; returns (t, step)."""
+        return dg_checkpoint_load(self.op, path, q, self.fstride)
 
     def tune(self, reps=5, stream=None):
         """Pick the faster FP32 kernel for this mesh (dg_operator_tune)."""
@@ -602,6 +638,9 @@ class Server:
     def release(self, rid):
         dg_server_release(self.server, rid)
         self._keep.pop(rid, None)
+
+    def cancel(self, rid):
+        dg_server_cancel(self.server, rid)
 
     def stats(self):
         return dg_server_stats(self.server)

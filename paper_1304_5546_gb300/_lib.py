@@ -21,6 +21,8 @@ DG_ERR_OOM = 6
 DG_ERR_NONFINITE = 7
 DG_ERR_NO_DEVICE = 8
 DG_ERR_TIMEOUT = 9
+DG_ERR_IO = 10
+DG_CKPT_HOST = 1
 DG_FP64 = 0
 DG_FP32 = 1
 DG_SETUP_HOST_ONLY = 1
@@ -34,12 +36,13 @@ DG_BATCH_NO_GRAPH = 1
 DG_BATCH_NO_ADAPT = 2
 DG_SERVER_SEQUENTIAL = 1
 DG_REQUEST_QUEUED, DG_REQUEST_RUNNING, DG_REQUEST_DONE, DG_REQUEST_FAILED = 0, 1, 2, 3
+DG_REQUEST_CANCELLED = 4
 DG_N_MAX = 7
 
 _STATUS_NAMES = {
     0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_MESH_DEGENERATE", 3: "DG_ERR_MESH_NONCONFORMING",
     4: "DG_ERR_ORDER", 5: "DG_ERR_CUDA", 6: "DG_ERR_OOM", 7: "DG_ERR_NONFINITE",
-    8: "DG_ERR_NO_DEVICE", 9: "DG_ERR_TIMEOUT",
+    8: "DG_ERR_NO_DEVICE", 9: "DG_ERR_TIMEOUT", 10: "DG_ERR_IO",
 }
 
 c_void_p = ctypes.c_void_p
@@ -86,6 +89,10 @@ SIGNATURES = [
     ("dg_check_finite", c_i32, [c_void_p, c_void_p, c_void_p]),
     ("dg_sync_check", c_i32, [c_void_p, c_void_p]),
     ("dg_launch_count", c_i64, [c_void_p]),
+    ("dg_test_wait_timeout", c_i32, [c_void_p, c_void_p]),
+    ("dg_checkpoint_save", c_i32, [c_void_p, c_void_p, c_i64, c_i32, c_dbl, c_i64, ctypes.c_char_p]),
+    ("dg_checkpoint_load", c_i32, [c_void_p, ctypes.c_char_p, c_void_p, c_i64, c_i32, P(c_dbl),
+                                   P(c_i64)]),
     ("dg_batch_create", c_i32, [c_void_p, c_i32, P(c_void_p)]),
     ("dg_batch_destroy", None, [c_void_p]),
     ("dg_batch_add", c_i32, [c_void_p, c_void_p, c_dbl, c_void_p, c_void_p, P(c_i32)]),
@@ -106,6 +113,7 @@ SIGNATURES = [
     ("dg_server_wait", c_i32, [c_void_p, c_i64, c_dbl, c_void_p]),
     ("dg_server_info", c_i32, [c_void_p, c_i64, c_void_p]),
     ("dg_server_release", c_i32, [c_void_p, c_i64]),
+    ("dg_server_cancel", c_i32, [c_void_p, c_i64]),
     ("dg_server_stats", c_i32, [c_void_p, P(c_i64), P(c_i64), P(c_i64), P(c_i64)]),
     ("dg_last_error", ctypes.c_char_p, []),
 ]

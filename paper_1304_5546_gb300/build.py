@@ -29,12 +29,13 @@ def sources():
     names = (["host_setup.cpp", "api.cu"] + ["kernels_N%d.cu" % n for n in range(1, 8)]
              + ["kernels_tc_N%d.cu" % n for n in range(1, 8)]
              + ["kernels_tcp_N%d.cu" % n for n in range(1, 8)]
-             + ["kernels_batch_s1.cu", "kernels_batch_s2.cu", "batch.cu", "server.cu"])
+             + ["kernels_batch_s1.cu", "kernels_batch_s2.cu", "batch.cu", "server.cu", "checkpoint.cu"])
     return [os.path.join(CSRC, n) for n in names]
 
 
 def _deps():
-    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "dgwave.h")]
+    return ([os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+            + [os.path.join(INCLUDE, "dgwave.h"), os.path.abspath(__file__)])
 
 
 def up_to_date():

@@ -808,6 +808,30 @@ extern "C" dg_status dg_sync_check(const dg_op* op, void* stream) {
   return DG_OK;
 }
 
+extern "C" dg_status dg_test_wait_timeout(const dg_op* op, void* stream) {
+  dgw::clear_error();
+  dg_status st = check_device_op(op, "dg_test_wait_timeout");
+  if (st) return st;
+  if (!op->use_tc)
+    return fail(DG_ERR_ARG, "dg_test_wait_timeout: needs an operator on the tensor-core kernel");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* gate = nullptr;
+  cudaError_t err = cudaMalloc(reinterpret_cast<void**>(&gate), sizeof(int));
+  if (err == cudaSuccess) err = cudaMemsetAsync(gate, 0, sizeof(int), s);
+  if (err == cudaSuccess) {
+    dgw::StageArgs<float> a = base_args<float>(op);
+    a.qin = static_cast<const float*>(op->d_qtmp);  // never read: the wait runs out first
+    a.rhs = static_cast<float*>(op->d_qtmp);
+    a.stall_gate = gate;
+    err = launch_order<float>(op, a, dgw::kModeRhs, s);
+    if (err == cudaSuccess) op->launches.fetch_add(1, std::memory_order_relaxed);
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (gate) cudaFree(gate);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_test_wait_timeout");
+  return DG_OK;
+}
+
 extern "C" int64_t dg_launch_count(const dg_op* op) {
   return op ? op->launches.load(std::memory_order_relaxed) : 0;
 }

@@ -430,10 +430,22 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
         tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * GEO, gb, &full[s]);
         tma_load_1d(st + 6 * L::QB + L::GB, p.conn + static_cast<int64_t>(k0) * 3, cb, &full[s]);
       };
-      mbar_expect_tx(op_bar, L::NS * L::OB);
-      tma_load_1d(smem + L::OFF_OP, p.tc_op, L::NS * L::OB, op_bar);
-      for (; issued < niter && issued < S; ++issued) issue(issued);
       bool ok = true;
+      if (p.stall_gate) {  // timeout test: a flag that nothing sets, bounded wait
+        const unsigned long long t0 = global_ns();
+        while (*reinterpret_cast<const volatile int*>(p.stall_gate) == 0) {
+          if (global_ns() - t0 > kGateLimitNs) {
+            ok = false;
+            break;
+          }
+          __nanosleep(1000);
+        }
+      }
+      if (ok) {
+        mbar_expect_tx(op_bar, L::NS * L::OB);
+        tma_load_1d(smem + L::OFF_OP, p.tc_op, L::NS * L::OB, op_bar);
+        for (; issued < niter && issued < S; ++issued) issue(issued);
+      }
       // outputs of block jj leave by bulk stores, one bulk group per block
       // (empty for a short block, whose epilogue writes global memory); the
       // stage of block jj - 1 is refilled once that block's stores have read

@@ -68,6 +68,10 @@ struct StageArgs {
   T a = 0, b = 0, dt = 0;
   T alpha = 1;  // flux parameter of Eq. max2d-numflux (uniform medium only)
   int* status = nullptr;  // set to 1 by a CTA whose bounded wait expired
+  // timeout test only (tensor-core kernel): the memory warp first waits,
+  // bounded by kGateLimitNs, for *stall_gate to become non-zero; NULL
+  // otherwise
+  const int* stall_gate = nullptr;
   // block table of the batched launch: block i of the launch covers
   // elements [blocks[i].x, blocks[i].x + blocks[i].y), 1 <= y <= E, x a
   // multiple of 4; the count is read from device memory (*nblocks) so that a

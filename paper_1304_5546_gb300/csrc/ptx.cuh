@@ -10,6 +10,7 @@
 namespace dgw {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // ~2 s per bounded wait
+constexpr unsigned long long kGateLimitNs = 100000000ull;   // 0.1 s: timeout-test gate
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

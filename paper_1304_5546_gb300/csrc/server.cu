@@ -65,6 +65,7 @@ struct Request {
   double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
   size_t staging_idx = 0;  // pinned buffer holding the result on its way out
   bool staged = false;     // staging_idx is held for this request
+  bool cancel = false;     // dg_server_cancel asked for it (under the server lock)
   cudaEvent_t out_ev = nullptr;
 };
 
@@ -89,7 +90,7 @@ struct dg_server {
   std::vector<Request*> finishing;
   std::deque<cudaEvent_t> inflight;
   std::vector<cudaEvent_t> spare_events;
-  int64_t completed = 0, failed = 0;
+  int64_t completed = 0, failed = 0, cancelled = 0;
   std::atomic<int64_t> steps{0}, launches{0};
 };
 
@@ -113,8 +114,10 @@ void finish(dg_server* s, Request* r, int32_t state, dg_status status) {
   r->t_done = now_s();
   if (state == DG_REQUEST_DONE)
     ++s->completed;
-  else
+  else if (state == DG_REQUEST_FAILED)
     ++s->failed;
+  else
+    ++s->cancelled;
   s->cv_done.notify_all();
 }
 
@@ -150,6 +153,22 @@ void admit(dg_server* s) {
   }
   const bool seq = (s->flags & DG_SERVER_SEQUENTIAL) != 0;
   for (Request* r : cand) {
+    bool cancelled = false;
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      if (r->cancel) {
+        for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+          if (*it == r) {
+            s->queue.erase(it);
+            break;
+          }
+        cancelled = true;
+      }
+    }
+    if (cancelled) {
+      finish(s, r, DG_REQUEST_CANCELLED, DG_OK);
+      continue;
+    }
     if (seq && (!s->running.empty() || !s->finishing.empty())) break;
     int32_t slot = -1;
     dg_status st = dg_batch_add(s->batch, r->op, r->dt, r->has_src ? &r->src : nullptr, s->stream,
@@ -183,6 +202,26 @@ void admit(dg_server* s) {
     }
     s->running.push_back(r);
     if (seq) break;
+  }
+}
+
+// running requests that were cancelled leave the batch, without results
+void drop_cancelled(dg_server* s) {
+  for (size_t i = 0; i < s->running.size();) {
+    Request* r = s->running[i];
+    bool cancel;
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      cancel = r->cancel;
+    }
+    if (!cancel) {
+      ++i;
+      continue;
+    }
+    dg_batch_remove(s->batch, r->slot);
+    s->running[i] = s->running.back();
+    s->running.pop_back();
+    finish(s, r, DG_REQUEST_CANCELLED, DG_OK);
   }
 }
 
@@ -231,6 +270,7 @@ void worker_loop(dg_server* s) {
   cudaSetDevice(s->device);
   for (;;) {
     poll_finishing(s);
+    drop_cancelled(s);
     admit(s);
     if (!s->running.empty()) {
       if (static_cast<int>(s->inflight.size()) >= kAhead) {
@@ -415,7 +455,10 @@ extern "C" dg_status dg_server_wait(dg_server* s, int64_t request_id, double tim
   if (it == s->requests.end())
     return fail(DG_ERR_ARG, "dg_server_wait: unknown request %lld", static_cast<long long>(request_id));
   Request* r = it->second;
-  auto done = [&] { return r->state == DG_REQUEST_DONE || r->state == DG_REQUEST_FAILED; };
+  auto done = [&] {
+    return r->state == DG_REQUEST_DONE || r->state == DG_REQUEST_FAILED ||
+           r->state == DG_REQUEST_CANCELLED;
+  };
   if (timeout_s < 0)
     s->cv_done.wait(lock, done);
   else if (!s->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), done))
@@ -444,11 +487,31 @@ extern "C" dg_status dg_server_release(dg_server* s, int64_t request_id) {
   if (it == s->requests.end())
     return fail(DG_ERR_ARG, "dg_server_release: unknown request %lld", static_cast<long long>(request_id));
   Request* r = it->second;
-  if (r->state != DG_REQUEST_DONE && r->state != DG_REQUEST_FAILED)
+  if (r->state != DG_REQUEST_DONE && r->state != DG_REQUEST_FAILED &&
+      r->state != DG_REQUEST_CANCELLED)
     return fail(DG_ERR_ARG, "dg_server_release: request %lld has not finished",
                 static_cast<long long>(request_id));
   s->requests.erase(it);
   delete r;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_server_cancel(dg_server* s, int64_t request_id) {
+  dgw::clear_error();
+  if (!s) return fail(DG_ERR_ARG, "dg_server_cancel: NULL server");
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->requests.find(request_id);
+    if (it == s->requests.end())
+      return fail(DG_ERR_ARG, "dg_server_cancel: unknown request %lld",
+                  static_cast<long long>(request_id));
+    Request* r = it->second;
+    if (r->state != DG_REQUEST_QUEUED && r->state != DG_REQUEST_RUNNING)
+      return fail(DG_ERR_ARG, "dg_server_cancel: request %lld has already finished",
+                  static_cast<long long>(request_id));
+    r->cancel = true;
+  }
+  s->cv_work.notify_one();
   return DG_OK;
 }
 

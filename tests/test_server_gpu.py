@@ -185,3 +185,27 @@ def test_concurrent_submitters(P, reqs):
     for r, o, info in outs:
         assert info["state"] == 2
         assert np.array_equal(o, r.alone(P, info["dt"], info["nsteps"]))
+
+
+def test_cancel_queued_and_running(P, reqs):
+    long = _Req(P, 9, 6, 22, nsteps=3000, source=True)
+    cap = [0] * 7
+    cap[5] = (long.K + 3) // 4 * 4  # room for one of the two N = 6 requests
+    short = reqs[0]                 # N = 3
+    cap[2] = (short.K + 3) // 4 * 4
+    srv = P.Server(cap)
+    out_long = long.out()
+    lid = srv.submit(long.solver, long.T, source=long.source, q0=long.q0, out=out_long)
+    t0 = time.time()
+    while srv.info(lid)["state"] == 0 and time.time() - t0 < 10:
+        time.sleep(0.001)
+    qid = srv.submit(long.solver, long.T, source=long.source, q0=long.q0, out=long.out())
+    assert srv.info(qid)["state"] == 0  # no room: queued
+    srv.cancel(qid)
+    srv.cancel(lid)
+    sid = srv.submit(short.solver, short.T, source=short.source, q0=short.q0, out=short.out())
+    qi, li, si = srv.wait(qid, 60.0), srv.wait(lid, 60.0), srv.wait(sid, 60.0)
+    srv.close()
+    assert qi["state"] == 4 and qi["t_admit"] == 0.0   # cancelled before admission
+    assert li["state"] == 4 and np.all(out_long == 0)  # cancelled while running, no result
+    assert si["state"] == 2
