@@ -457,6 +457,68 @@ def run_sweep_study(args):
             "rows": rows}
 
 
+def run_partition_study(args):
+    """The mesh-partition path on one device (dg_partition_*): the default
+    workload (order `--order`, K = 2 n^2) split into P parts by recursive
+    coordinate bisection and stepped with one halo exchange per LSRK stage,
+    for P in `--partition-parts`.  Per P: ms/step against the unpartitioned
+    operator, the exchange alone (pack, transfer, unpack) per stage, the traces exchanged per stage, and whether the
+    result equals the unpartitioned one bit for bit.  One JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_1304_5546_gb300 as P
+    from synth import gaussian_pulse, jittered_delaunay_mesh
+
+    torch.cuda.set_device(0)
+    N, n, steps = args.order, args.n, args.study_steps
+    s = P.Solver(*jittered_delaunay_mesh(n, seed=2024), N=N, precision=args.precision)
+    x, y = s.nodes()
+    q0 = s.from_numpy(np.stack(gaussian_pulse(x, y)))
+    dt = s.cfl_dt()
+
+    def timed(fn, reps):
+        fn(3)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn(reps)
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    q, res = q0.clone(), s.new_fields()
+    ms_single = timed(lambda k: s.step(q, res, dt, k), steps)
+    want, wres = q0.clone(), s.new_fields()
+    s.step(want, wres, dt, 10)
+    rows = []
+    for nparts in args.partition_parts:
+        part = P.Partition(s, nparts)
+        part.set_fields(q0)
+        ms = timed(lambda k: part.step(dt, k), steps)
+        ms_x = timed(lambda k: [part.exchange() for _ in range(k)], 200)
+        part.set_fields(q0)
+        part.step(dt, 10)
+        got = s.new_fields()
+        part.get_fields(got)
+        part.sync_check()
+        torch.cuda.synchronize()
+        info = [part.info(p) for p in range(nparts)]
+        values = sum(i[4] for i in info)  # node values per field per exchange
+        pairs = sum(i[2] for i in info)
+        rows.append({"parts": nparts, "ms_per_step": ms, "vs_unpartitioned": ms / ms_single,
+                     "exchange_ms_per_stage": ms_x, "part_pairs": pairs,
+                     "trace_values_per_stage": 3 * values,
+                     "trace_bytes_per_stage": 3 * values * s.view(q).element_size(),
+                     "elements_per_part": [i[0] for i in info],
+                     "ghosts_per_part": [i[1] for i in info],
+                     "bitwise_equal_after_10_steps": bool(torch.equal(s.view(got), s.view(want)))})
+        part.close()
+    return {"study": "partition", "N": N, "K": s.K, "precision": args.precision, "steps": steps,
+            "ms_per_step_unpartitioned": ms_single, "rows": rows}
+
+
 def batched_workload(n_problems=256, seed=4242, k_lo=500, k_hi=50000, orders=(3, 5, 7),
                      speeds=(0.5, 1.0, 2.0)):
     """Seeded batch of independent problems: K log-uniform in [k_lo, k_hi]
@@ -748,11 +810,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--_oracle-sample", nargs=3, default=None)
-    ap.add_argument("--study", choices=["precision", "sweep"], default=None,
+    ap.add_argument("--study", choices=["precision", "sweep", "partition"], default=None,
                     help="instead of the benchmark line: the precision-path study "
                          "(use with --order 7 --n 362 for K = 262,088)")
     ap.add_argument("--study-steps", type=int, default=500)
     ap.add_argument("--sweep-orders", type=int, nargs="+", default=list(range(1, 8)))
+    ap.add_argument("--partition-parts", type=int, nargs="+", default=[1, 2, 4, 8])
     ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
                     help="single: the large-mesh benchmark line (default); batched: many "
                          "mixed-order problems in one launch per stage vs sequential solves")
@@ -776,6 +839,9 @@ def main(argv=None):
         return 0
     if args.study == "sweep":
         print(json.dumps(run_sweep_study(args)), flush=True)
+        return 0
+    if args.study == "partition":
+        print(json.dumps(run_partition_study(args)), flush=True)
         return 0
     if args.workload == "serving" and args.impl == "ours":
         print(json.dumps(run_serving(args)), flush=True)

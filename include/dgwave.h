@@ -554,6 +554,70 @@ dg_status dg_checkpoint_save(const dg_op* op, const void* q, int64_t q_stride, i
 dg_status dg_checkpoint_load(const dg_op* op, const char* path, void* q, int64_t q_stride,
                              int32_t flags, double* t, int64_t* step);
 
+/* ----------------------------------------------------------- partitions ---
+ * A mesh partition of one operator into P parts, each with its own element
+ * tables and field buffers, stepped with one halo exchange per LSRK stage:
+ * the multi-GPU decomposition of Section "Further Tuning Opportunities"
+ * (only the face traces that the flux needs cross a cut), emulated on one
+ * device.  Parts are recursive coordinate bisections of the element
+ * centroids (sizes within one element of K / P); each part keeps its
+ * elements in increasing global order.  Every element whose face meets a
+ * cut gets, in each part across that face, a ghost slot whose face nodes
+ * receive its traces.  A stage is: pack (one kernel: every part's outgoing
+ * traces into a send buffer, one contiguous message per (sender, receiver)
+ * pair), the transfer (between GPUs one send / receive per pair; on one
+ * device a single copy of all messages into the receive buffer), unpack
+ * (one kernel into the ghost slots), then one stage launch per part.  The
+ * result equals, bit for bit, the unpartitioned operator's.
+ *
+ * dg_partition_create: partitions `op` (not owned; it must outlive the
+ * partition) into P parts, 1 <= P <= min(K, 64).  With a device operator it
+ * builds the parts' device tables and buffers on op's device; with a
+ * host-only operator only the plan (parts, ghosts, exchange lists).
+ * dg_partition_info: part p's element count, ghost count, the number of
+ * parts it receives from and sends to, and the node values (per field) it
+ * receives and sends per exchange.
+ * dg_partition_elements / dg_partition_ghosts: global element ids of part
+ * p's elements (K_p) and of its ghost slots (G_p), host int64 arrays.
+ * dg_partition_conn: part p's face connection codes (3 K_p, int32): -1 on a
+ * boundary face, otherwise e * 8 + f * 2 + rev with e the neighbour's slot in
+ * part p (an element index below K_p, or ghost slot g at index Kpad_p + g).
+ * dg_partition_exchange_plan: what part p sends and receives per exchange,
+ * as node offsets into one field of its local layout (element slot * Np +
+ * node): send_peer[i] gets send_count[i] values at the next send_count[i]
+ * entries of send_off, in that order; recv_peer[i] sends recv_count[i]
+ * values, stored at the next recv_count[i] entries of recv_off.  The lists
+ * of a sender and its receiver match entry for entry.  Any pointer may be
+ * NULL; arrays are sized by dg_partition_info.
+ * dg_partition_set_fields / dg_partition_get_fields: scatter the global
+ * fields q (device, the operator's precision, field f at f * q_stride) into
+ * the parts, or gather them back.  Asynchronous on `stream`.
+ * dg_partition_exchange: one halo exchange on the parts' current fields.
+ * dg_partition_step: nsteps LSRK(5,4) steps of size dt of every part.
+ * dg_partition_sync_check: dg_sync_check of every part.
+ * Errors: DG_ERR_ARG (NULL, P out of range, p out of range, q_stride <
+ * K * Np, nsteps < 0, dt not finite), DG_ERR_NO_DEVICE (a device call on a
+ * plan-only partition), DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_TIMEOUT.          */
+typedef struct dg_partition dg_partition;
+
+dg_status dg_partition_create(const dg_op* op, int32_t P, dg_partition** out);
+void dg_partition_destroy(dg_partition* part);
+dg_status dg_partition_info(const dg_partition* part, int32_t p, int64_t* K_p, int64_t* G_p,
+                            int32_t* n_recv_peers, int32_t* n_send_peers, int64_t* n_recv,
+                            int64_t* n_send);
+dg_status dg_partition_elements(const dg_partition* part, int32_t p, int64_t* gid);
+dg_status dg_partition_ghosts(const dg_partition* part, int32_t p, int64_t* gid);
+dg_status dg_partition_conn(const dg_partition* part, int32_t p, int32_t* conn);
+dg_status dg_partition_exchange_plan(const dg_partition* part, int32_t p, int32_t* send_peer,
+                                     int64_t* send_count, int32_t* send_off, int32_t* recv_peer,
+                                     int64_t* recv_count, int32_t* recv_off);
+dg_status dg_partition_set_fields(dg_partition* part, const void* q, int64_t q_stride,
+                                  void* stream);
+dg_status dg_partition_get_fields(dg_partition* part, void* q, int64_t q_stride, void* stream);
+dg_status dg_partition_exchange(dg_partition* part, void* stream);
+dg_status dg_partition_step(dg_partition* part, double dt, int32_t nsteps, void* stream);
+dg_status dg_partition_sync_check(dg_partition* part, void* stream);
+
 /* dg_check_finite: synchronises `stream`, then scans the first K*Np values
  * of each field of d_q for NaN/Inf.  Returns DG_ERR_NONFINITE if any is
  * found (blow-up detection), DG_OK otherwise.                              */

@@ -34,7 +34,11 @@ __all__ = [
     "dg_batch_plan", "dg_batch_plan_ctas", "dg_batch_sync_check", "dg_batch_launch_count",
     "dg_server_clock", "dg_server_create", "dg_server_destroy", "dg_server_submit",
     "dg_server_wait", "dg_server_info", "dg_server_release", "dg_server_cancel", "dg_server_stats",
-    "Solver", "Batch", "Server", "DGError", "DG_FP32", "DG_FP64",
+    "dg_partition_create", "dg_partition_destroy", "dg_partition_info", "dg_partition_elements",
+    "dg_partition_ghosts", "dg_partition_conn", "dg_partition_exchange_plan",
+    "dg_partition_set_fields", "dg_partition_get_fields", "dg_partition_exchange",
+    "dg_partition_step", "dg_partition_sync_check",
+    "Solver", "Batch", "Server", "Partition", "DGError", "DG_FP32", "DG_FP64",
 ]
 
 
@@ -416,6 +420,97 @@ _FP32_VARIANTS = {
 }
 
 
+# ------------------------------------------------------------ partitions
+def dg_partition_create(op, P):
+    h = ctypes.c_void_p()
+    _lib.check(_lib.load().dg_partition_create(op, P, ctypes.byref(h)), "dg_partition_create")
+    return h
+
+
+def dg_partition_destroy(part):
+    if part:
+        _lib.load().dg_partition_destroy(part)
+
+
+def dg_partition_info(part, p):
+    """(K_p, G_p, n_recv_peers, n_send_peers, n_recv, n_send) of part p."""
+    K, G, n_sends, n_recvs = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    rp, sp = ctypes.c_int32(), ctypes.c_int32()
+    _lib.check(_lib.load().dg_partition_info(part, p, ctypes.byref(K), ctypes.byref(G),
+                                             ctypes.byref(rp), ctypes.byref(sp),
+                                             ctypes.byref(n_recvs), ctypes.byref(n_sends)),
+               "dg_partition_info")
+    return K.value, G.value, rp.value, sp.value, n_recvs.value, n_sends.value
+
+
+def dg_partition_elements(part, p):
+    K = dg_partition_info(part, p)[0]
+    out = np.empty(K, np.int64)
+    _lib.check(_lib.load().dg_partition_elements(part, p, _ptr(out)), "dg_partition_elements")
+    return out
+
+
+def dg_partition_ghosts(part, p):
+    G = dg_partition_info(part, p)[1]
+    out = np.empty(max(G, 1), np.int64)
+    _lib.check(_lib.load().dg_partition_ghosts(part, p, _ptr(out)), "dg_partition_ghosts")
+    return out[:G]
+
+
+def dg_partition_conn(part, p):
+    K = dg_partition_info(part, p)[0]
+    out = np.empty((K, 3), np.int32)
+    _lib.check(_lib.load().dg_partition_conn(part, p, _ptr(out)), "dg_partition_conn")
+    return out
+
+
+def dg_partition_exchange_plan(part, p):
+    """{"send": [(peer, offsets)], "recv": [(peer, offsets)]} of part p."""
+    _, _, rp, sp, nr, ns = dg_partition_info(part, p)
+    send_peer, recv_peer = np.empty(max(sp, 1), np.int32), np.empty(max(rp, 1), np.int32)
+    send_cnt, recv_cnt = np.empty(max(sp, 1), np.int64), np.empty(max(rp, 1), np.int64)
+    send_off, recv_off = np.empty(max(ns, 1), np.int32), np.empty(max(nr, 1), np.int32)
+    _lib.check(_lib.load().dg_partition_exchange_plan(
+        part, p, _ptr(send_peer), _ptr(send_cnt), _ptr(send_off), _ptr(recv_peer),
+        _ptr(recv_cnt), _ptr(recv_off)), "dg_partition_exchange_plan")
+
+    def split(peers, counts, offs, n):
+        out, o = [], 0
+        for i in range(n):
+            out.append((int(peers[i]), offs[o:o + counts[i]].copy()))
+            o += counts[i]
+        return out
+    return {"send": split(send_peer, send_cnt, send_off, sp),
+            "recv": split(recv_peer, recv_cnt, recv_off, rp)}
+
+
+def dg_partition_set_fields(part, q, q_stride, stream=None):
+    _lib.check(_lib.load().dg_partition_set_fields(part, _dptr(q), q_stride,
+                                                   _stream_handle(stream)),
+               "dg_partition_set_fields")
+
+
+def dg_partition_get_fields(part, q, q_stride, stream=None):
+    _lib.check(_lib.load().dg_partition_get_fields(part, _dptr(q), q_stride,
+                                                   _stream_handle(stream)),
+               "dg_partition_get_fields")
+
+
+def dg_partition_exchange(part, stream=None):
+    _lib.check(_lib.load().dg_partition_exchange(part, _stream_handle(stream)),
+               "dg_partition_exchange")
+
+
+def dg_partition_step(part, dt, nsteps, stream=None):
+    _lib.check(_lib.load().dg_partition_step(part, dt, nsteps, _stream_handle(stream)),
+               "dg_partition_step")
+
+
+def dg_partition_sync_check(part, stream=None):
+    _lib.check(_lib.load().dg_partition_sync_check(part, _stream_handle(stream)),
+               "dg_partition_sync_check")
+
+
 class Solver:
     """Owns a mesh + operator pair and the torch tensors that hold fields.
 
@@ -648,3 +743,54 @@ class Server:
     @staticmethod
     def clock():
         return dg_server_clock()
+
+
+class Partition:
+    """A Solver's mesh split into P parts stepped with one halo exchange per
+    LSRK stage (dg_partition_*).  Fields move in and out as the Solver's
+    (3, field_stride) tensors; ``plan(p)`` is part p's exchange lists."""
+
+    def __init__(self, solver, P):
+        self.solver = solver  # the operator must outlive the partition
+        self.P = P
+        self.part = dg_partition_create(solver.op, P)
+
+    def close(self):
+        dg_partition_destroy(getattr(self, "part", None))
+        self.part = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self, p):
+        return dg_partition_info(self.part, p)
+
+    def elements(self, p):
+        return dg_partition_elements(self.part, p)
+
+    def ghosts(self, p):
+        return dg_partition_ghosts(self.part, p)
+
+    def conn(self, p):
+        return dg_partition_conn(self.part, p)
+
+    def plan(self, p):
+        return dg_partition_exchange_plan(self.part, p)
+
+    def set_fields(self, q, stream=None):
+        dg_partition_set_fields(self.part, q, self.solver.fstride, stream)
+
+    def get_fields(self, q, stream=None):
+        dg_partition_get_fields(self.part, q, self.solver.fstride, stream)
+
+    def exchange(self, stream=None):
+        dg_partition_exchange(self.part, stream)
+
+    def step(self, dt, nsteps=1, stream=None):
+        dg_partition_step(self.part, dt, nsteps, stream)
+
+    def sync_check(self, stream=None):
+        dg_partition_sync_check(self.part, stream)

@@ -115,6 +115,19 @@ SIGNATURES = [
     ("dg_server_release", c_i32, [c_void_p, c_i64]),
     ("dg_server_cancel", c_i32, [c_void_p, c_i64]),
     ("dg_server_stats", c_i32, [c_void_p, P(c_i64), P(c_i64), P(c_i64), P(c_i64)]),
+    ("dg_partition_create", c_i32, [c_void_p, c_i32, P(c_void_p)]),
+    ("dg_partition_destroy", None, [c_void_p]),
+    ("dg_partition_info", c_i32, [c_void_p, c_i32, P(c_i64), P(c_i64), P(c_i32), P(c_i32),
+                                  P(c_i64), P(c_i64)]),
+    ("dg_partition_elements", c_i32, [c_void_p, c_i32, c_void_p]),
+    ("dg_partition_ghosts", c_i32, [c_void_p, c_i32, c_void_p]),
+    ("dg_partition_conn", c_i32, [c_void_p, c_i32, c_void_p]),
+    ("dg_partition_exchange_plan", c_i32, [c_void_p, c_i32] + [c_void_p] * 6),
+    ("dg_partition_set_fields", c_i32, [c_void_p, c_void_p, c_i64, c_void_p]),
+    ("dg_partition_get_fields", c_i32, [c_void_p, c_void_p, c_i64, c_void_p]),
+    ("dg_partition_exchange", c_i32, [c_void_p, c_void_p]),
+    ("dg_partition_step", c_i32, [c_void_p, c_dbl, c_i32, c_void_p]),
+    ("dg_partition_sync_check", c_i32, [c_void_p, c_void_p]),
     ("dg_last_error", ctypes.c_char_p, []),
 ]
 

@@ -140,12 +140,39 @@ void media_records(const dg_op& op, double sh, std::vector<double>& out) {
 
 }  // namespace dgw
 
+namespace dgw {
+
+void operator_records(const dg_op& op, std::vector<double>& rec, std::vector<int32_t>& conn) {
+  const int64_t K = op.K;
+  if (op.media()) {
+    media_records(op, 1.0, rec);
+  } else {
+    rec.assign(static_cast<size_t>(K) * kGeo, 0.0);
+    for (int64_t k = 0; k < K; ++k) {
+      double* g = &rec[k * kGeo];
+      g[0] = op.geo.rx[k];
+      g[1] = op.geo.ry[k];
+      g[2] = op.geo.sx[k];
+      g[3] = op.geo.sy[k];
+      for (int f = 0; f < 3; ++f) {
+        g[4 + 3 * f] = op.geo.nx[3 * k + f];
+        g[5 + 3 * f] = op.geo.ny[3 * k + f];
+        g[6 + 3 * f] = 0.5 * op.geo.Fscale[3 * k + f];
+      }
+    }
+  }
+  conn.assign(op.geo.conn.begin(), op.geo.conn.begin() + 3 * K);
+}
+
+}  // namespace dgw
+
 namespace {
 
 using dgw::tc_operator_tiles;
 
 template <typename T>
-dg_status upload(dg_op* op) {
+dg_status upload(dg_op* op, const std::vector<double>& rec_in,
+                 const std::vector<int32_t>& conn_in) {
   const int Np = op->Np, Nafp = op->Nafp;
   const int64_t K = op->K, Kpad = op->Kpad;
   std::vector<T> Dr(op->ref.Dr.begin(), op->ref.Dr.end());
@@ -158,28 +185,12 @@ dg_status upload(dg_op* op) {
     lam[n] = static_cast<T>(0.5 * (1.0 + op->ref.r[n]));
     lam[Np + n] = static_cast<T>(0.5 * (1.0 + op->ref.s[n]));
   }
+  // records padded to Kpad elements: zero geometry, boundary faces
   const int rec = op->media() ? dgw::kGeoMedia : dgw::kGeo;
   std::vector<T> geo(static_cast<size_t>(Kpad) * rec, T(0));
   std::vector<int32_t> conn(static_cast<size_t>(Kpad) * 3, -1);
-  if (op->media()) {
-    std::vector<double> m;
-    dgw::media_records(*op, 1.0, m);
-    for (size_t i = 0; i < m.size(); ++i) geo[i] = static_cast<T>(m[i]);
-  }
-  for (int64_t k = 0; k < K; ++k) {
-    T* g = &geo[k * rec];
-    for (int f = 0; f < 3; ++f) conn[3 * k + f] = op->geo.conn[3 * k + f];
-    if (op->media()) continue;
-    g[0] = static_cast<T>(op->geo.rx[k]);
-    g[1] = static_cast<T>(op->geo.ry[k]);
-    g[2] = static_cast<T>(op->geo.sx[k]);
-    g[3] = static_cast<T>(op->geo.sy[k]);
-    for (int f = 0; f < 3; ++f) {
-      g[4 + 3 * f] = static_cast<T>(op->geo.nx[3 * k + f]);
-      g[5 + 3 * f] = static_cast<T>(op->geo.ny[3 * k + f]);
-      g[6 + 3 * f] = static_cast<T>(0.5 * op->geo.Fscale[3 * k + f]);
-    }
-  }
+  for (size_t i = 0; i < static_cast<size_t>(K) * rec; ++i) geo[i] = static_cast<T>(rec_in[i]);
+  std::copy(conn_in.begin(), conn_in.begin() + 3 * K, conn.begin());
   struct Up {
     void** dst;
     const void* src;
@@ -466,7 +477,15 @@ dg_status operator_setup(const dg_mesh* mesh, int32_t N, const double* eps, int3
       delete op;
       return cuda_fail(err, "dg_operator_setup: device attribute");
     }
-    const dg_status st = (precision == DG_FP32) ? upload<float>(op) : upload<double>(op);
+    dg_status st = DG_OK;
+    try {
+      std::vector<double> rec;
+      std::vector<int32_t> conn;
+      dgw::operator_records(*op, rec, conn);
+      st = (precision == DG_FP32) ? upload<float>(op, rec, conn) : upload<double>(op, rec, conn);
+    } catch (const std::bad_alloc&) {
+      st = fail(DG_ERR_OOM, "dg_operator_setup: out of host memory");
+    }
     if (st != DG_OK) {
       free_device(op);
       delete op;
@@ -941,3 +960,38 @@ extern "C" dg_status dg_step_static(const dg_op* op, void* d_q, void* d_res, dou
   return run_steps_static<double>(op, static_cast<double*>(d_q), static_cast<double*>(d_res), dt,
                                   nsteps, static_cast<double*>(scratch), s);
 }
+
+namespace dgw {
+
+dg_status upload_operator(dg_op* op, const std::vector<double>& rec,
+                          const std::vector<int32_t>& conn) {
+  const dg_status st =
+      (op->precision == DG_FP32) ? upload<float>(op, rec, conn) : upload<double>(op, rec, conn);
+  if (st != DG_OK) free_device(op);
+  return st;
+}
+
+cudaError_t op_stage(const dg_op* op, const void* qin, void* qout, void* res, int stage,
+                     double dt, cudaStream_t s) {
+  const int mode = (stage == 0) ? kModeFirstStage : kModeStage;
+  if (op->precision == DG_FP32) {
+    StageArgs<float> a = base_args<float>(op);
+    a.qin = static_cast<const float*>(qin);
+    a.qout = static_cast<float*>(qout);
+    a.res = static_cast<float*>(res);
+    a.a = static_cast<float>(op->lsrk_a[stage]);
+    a.b = static_cast<float>(op->lsrk_b[stage]);
+    a.dt = static_cast<float>(dt);
+    return launch_order<float>(op, a, mode, s);
+  }
+  StageArgs<double> a = base_args<double>(op);
+  a.qin = static_cast<const double*>(qin);
+  a.qout = static_cast<double*>(qout);
+  a.res = static_cast<double*>(res);
+  a.a = op->lsrk_a[stage];
+  a.b = op->lsrk_b[stage];
+  a.dt = dt;
+  return launch_order<double>(op, a, mode, s);
+}
+
+}  // namespace dgw

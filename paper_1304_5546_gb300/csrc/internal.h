@@ -2,6 +2,8 @@
 // (api.cu) and the kernels (kernels.cuh).  Not part of the public interface.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <atomic>
 #include <cstdint>
 #include <string>
@@ -119,5 +121,24 @@ std::vector<unsigned char> tc_operator_tiles(const RefElement& R, int prec);
 // elements of `op`, with row scales sH = sh and sE = sh / eps_k, as doubles
 // (out[k * kGeoMedia + i]); eps = 1 where the operator has none.
 void media_records(const dg_op& op, double sh, std::vector<double>& out);
+
+// Per-element records of `op` in the kernels' layout (kGeo values, or
+// kGeoMedia for an operator with a permittivity) and its face connection
+// codes (3 per element), K elements, as doubles.
+void operator_records(const dg_op& op, std::vector<double>& rec, std::vector<int32_t>& conn);
+
+// Uploads the reference-element tables of `op` and the given K element
+// records and connection codes (padded to Kpad), and allocates its ping-pong
+// field buffer (3 * fstride values), flag and status words.  `op` must have
+// N, Np, Nafp, ref, precision, use_tc, tc_prec, elem_size, K, Kpad, fstride
+// and eps (for media()) set.  On failure the partial device state is freed.
+dg_status upload_operator(dg_op* op, const std::vector<double>& rec,
+                          const std::vector<int32_t>& conn);
+
+// One fused LSRK(5,4) stage (stage 0..4) of operator `op`: reads the fields
+// qin and the residual res, writes the updated fields to qout and the new
+// residual to res, asynchronously on stream s.
+cudaError_t op_stage(const dg_op* op, const void* qin, void* qout, void* res, int stage,
+                     double dt, cudaStream_t s);
 
 }  // namespace dgw

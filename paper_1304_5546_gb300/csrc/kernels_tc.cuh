@@ -865,7 +865,7 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
             if (MODE == kModeRhs) {
               rq[n] = MEDIA ? srow * acc[n] : acc[n];
             } else {
-              float rn = drow * acc[n];
+              float rn = __fmul_rn(drow, acc[n]);
               if (MODE == kModeStage) rn = __fmaf_rn(p.a, rr[n], rn);
               rq[n] = __fmaf_rn(p.b, rn, rq[n]);
               rr[n] = rn;
@@ -874,39 +874,35 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
           if constexpr (TABLE && MEDIA && MODE != kModeRhs) {
             if (sw) {  // res += s w, q += b s w
               for (int n = 0; n < Np; ++n) {
-                const float v = samp * __ldg(sw + n);
-                rr[n] += v;
+                const float v = __fmul_rn(samp, __ldg(sw + n));
+                rr[n] = __fadd_rn(rr[n], v);
                 rq[n] = __fmaf_rn(p.b, v, rq[n]);
               }
             }
           }
         } else if (row_ok) {
-          // ragged last block: straight to global memory
+          // ragged last block: straight to global memory, with the same
+          // rounded operations as a full block, so that an element's result
+          // does not depend on the block it falls in
           const int off = c * E * Np + e * Np;
-          const bool full_block = false;
           const int64_t g = static_cast<int64_t>(c) * fs + static_cast<int64_t>(k0 + e) * Np;
   #pragma unroll
           for (int n = 0; n < Np; ++n) {
-            const float rhs = MEDIA && MODE == kModeRhs ? srow * acc[n] : acc[n];
             if (MODE == kModeRhs) {
-              if (full_block)
-                sq[off + n] = rhs;
-              else
-                p.rhs[g + n] = rhs;
+              p.rhs[g + n] = MEDIA ? srow * acc[n] : acc[n];
             } else {
-              float rn =
-                  (MODE == kModeFirstStage) ? drow * rhs : p.a * sres[off + n] + drow * rhs;
+              float rn = __fmul_rn(drow, acc[n]);
+              if (MODE == kModeStage) rn = __fmaf_rn(p.a, sres[off + n], rn);
+              float qn = __fmaf_rn(p.b, rn, sq[off + n]);
               if constexpr (TABLE && MEDIA) {
-                if (sw) rn += samp * __ldg(sw + n);
+                if (sw) {
+                  const float v = __fmul_rn(samp, __ldg(sw + n));
+                  rn = __fadd_rn(rn, v);
+                  qn = __fmaf_rn(p.b, v, qn);
+                }
               }
-              const float qn = sq[off + n] + p.b * rn;
-              if (full_block) {
-                sq[off + n] = qn;
-                sres[off + n] = rn;
-              } else {
-                p.qout[g + n] = qn;
-                p.res[g + n] = rn;
-              }
+              p.qout[g + n] = qn;
+              p.res[g + n] = rn;
             }
           }
         }
