@@ -712,9 +712,11 @@ def _percentile(v, q):
 
 def run_serving(args):
     """Serving workload: Poisson arrivals at each rate in --serve-rates of
-    the same seeded requests, served by the continuous-batching server and by
-    the same server admitting one request at a time (sequential plain
-    solves).  Latency = result in host memory - submission.  One JSON line."""
+    the same seeded requests, served by the continuous-batching server, by
+    the same server with each work limit of --serve-work-limits (nodal values
+    per field stepped together, first come first served), and by the server
+    admitting one request at a time (sequential plain solves).  Latency =
+    result in host memory - submission.  One JSON line."""
     import numpy as np
     import torch
 
@@ -747,8 +749,11 @@ def run_serving(args):
     for lam in args.serve_rates:
         arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs)))
         row = {"rate_per_s": lam}
-        for mode, seq in (("batched", False), ("sequential", True)):
-            srv = P.Server(cap, sequential=seq)
+        modes = ([("batched", False, 0)]
+                 + [("limited_%g" % w, False, int(w)) for w in args.serve_work_limits]
+                 + [("sequential", True, 0)])
+        for mode, seq, limit in modes:
+            srv = P.Server(cap, sequential=seq, work_limit=limit)
             t_start = P.Server.clock() + 0.01
             ids = []
             for i, (r, s, o) in enumerate(zip(reqs, solvers, outs)):
@@ -768,6 +773,12 @@ def run_serving(args):
                          "element_stage_updates_per_s": 5.0 * el_steps / span}
         row["speedup_solves_per_s"] = row["batched"]["solves_per_s"] / row["sequential"]["solves_per_s"]
         row["p99_ratio_seq_over_batched"] = row["sequential"]["p99_ms"] / row["batched"]["p99_ms"]
+        for mode, _, limit in modes:
+            if limit:
+                row[mode]["speedup_solves_per_s"] = (row[mode]["solves_per_s"]
+                                                     / row["sequential"]["solves_per_s"])
+                row[mode]["p99_ratio_seq_over_this"] = (row["sequential"]["p99_ms"]
+                                                        / row[mode]["p99_ms"])
         rows.append(row)
     clk = clocks.stop() if clocks else None
     Ks = np.array([s.K for s in solvers])
@@ -828,6 +839,8 @@ def main(argv=None):
     ap.add_argument("--serve-seed", type=int, default=777)
     ap.add_argument("--serve-time-scale", type=float, default=0.01)
     ap.add_argument("--serve-budget-gb", type=float, default=4.0)
+    ap.add_argument("--serve-work-limits", type=float, nargs="*", default=[3e6, 1e7],
+                    help="work limits (nodal values per field stepped together) to serve with")
     args = ap.parse_args(argv)
     if args._oracle_sample:
         n, N, sec = int(args._oracle_sample[0]), int(args._oracle_sample[1]), float(args._oracle_sample[2])

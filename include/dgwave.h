@@ -479,6 +479,8 @@ typedef struct dg_request_info {
   int64_t nsteps;   /* LSRK steps to the final time                        */
   double dt;        /* step: T / ceil(T / dg_cfl_dt(op, 1))                */
   double t_submit, t_admit, t_done;
+  double t_retired; /* left the batch: its last step enqueued (0 if it never
+                       ran to its final time)                              */
 } dg_request_info;
 
 /* The steady clock of the request times (seconds).                        */
@@ -490,6 +492,18 @@ dg_status dg_server_create(const int64_t* capacity, int32_t flags, dg_server** o
 
 /* Finishes every submitted request, stops the worker and frees everything. */
 void dg_server_destroy(dg_server* server);
+
+/* dg_server_set_work_limit: bound on the work stepped together.  While
+ * requests run, the oldest queued request is admitted only if the running
+ * requests' K * Np (nodal values per field) plus its own stay within
+ * max_nodes; otherwise it, and every request behind it, waits (first come,
+ * first served: a large request is not passed by later small ones).  A
+ * request is always admitted when none runs, so one larger than the limit
+ * runs alone.  This caps the processor sharing that stretches long solves;
+ * 0 (the default) means no limit beyond the memory budget.  Takes effect at
+ * the worker's next admission pass.  Errors: DG_ERR_ARG (NULL,
+ * max_nodes < 0).                                                          */
+dg_status dg_server_set_work_limit(dg_server* server, int64_t max_nodes);
 
 /* dg_server_submit: queue the solve of operator `op` (DG_FP32, host-only is
  * enough; it must stay alive until the request is released) from t = 0 to

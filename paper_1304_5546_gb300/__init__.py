@@ -34,6 +34,7 @@ __all__ = [
     "dg_batch_plan", "dg_batch_plan_ctas", "dg_batch_sync_check", "dg_batch_launch_count",
     "dg_server_clock", "dg_server_create", "dg_server_destroy", "dg_server_submit",
     "dg_server_wait", "dg_server_info", "dg_server_release", "dg_server_cancel", "dg_server_stats",
+    "dg_server_set_work_limit",
     "dg_partition_create", "dg_partition_destroy", "dg_partition_info", "dg_partition_elements",
     "dg_partition_ghosts", "dg_partition_conn", "dg_partition_exchange_plan",
     "dg_partition_set_fields", "dg_partition_get_fields", "dg_partition_exchange",
@@ -377,7 +378,8 @@ def dg_server_submit(server, op, T, source=None, q0=None, out=None):
 
 def _info_dict(i):
     return {"state": i.state, "status": i.status, "N": i.N, "K": i.K, "nsteps": i.nsteps,
-            "dt": i.dt, "t_submit": i.t_submit, "t_admit": i.t_admit, "t_done": i.t_done}
+            "dt": i.dt, "t_submit": i.t_submit, "t_admit": i.t_admit, "t_done": i.t_done,
+            "t_retired": i.t_retired}
 
 
 def dg_server_wait(server, request_id, timeout=-1.0):
@@ -395,6 +397,11 @@ def dg_server_info(server, request_id):
 
 def dg_server_cancel(server, request_id):
     _lib.check(_lib.load().dg_server_cancel(server, request_id), "dg_server_cancel")
+
+
+def dg_server_set_work_limit(server, max_nodes):
+    _lib.check(_lib.load().dg_server_set_work_limit(server, int(max_nodes)),
+               "dg_server_set_work_limit")
 
 
 def dg_server_release(server, request_id):
@@ -691,9 +698,11 @@ class Server:
     budget).  ``submit`` returns a request id at once; the result lands in
     the ``out`` array given to it once ``wait`` reports the request done.
     Operators, q0 and out arrays are kept alive here until ``release``.
+    ``work_limit``: at most this many nodal values per field (sum of K * Np)
+    stepped together, first come first served (dg_server_set_work_limit).
     """
 
-    def __init__(self, capacity, sequential=False, device=None):
+    def __init__(self, capacity, sequential=False, device=None, work_limit=0):
         import torch
         if device is not None:
             torch.cuda.set_device(device)
@@ -704,6 +713,11 @@ class Server:
             capacity = cap
         self.server = dg_server_create(capacity, sequential)
         self._keep = {}
+        if work_limit:
+            dg_server_set_work_limit(self.server, work_limit)
+
+    def set_work_limit(self, max_nodes):
+        dg_server_set_work_limit(self.server, max_nodes)
 
     def close(self):
         dg_server_destroy(getattr(self, "server", None))

@@ -52,7 +52,7 @@ class dg_request_info(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("N", ctypes.c_int32),
                 ("K", ctypes.c_int64), ("nsteps", ctypes.c_int64), ("dt", ctypes.c_double),
                 ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("t_done", ctypes.c_double), ("t_retired", ctypes.c_double)]
 
 
 class dg_point_source(ctypes.Structure):
@@ -114,6 +114,7 @@ SIGNATURES = [
     ("dg_server_info", c_i32, [c_void_p, c_i64, c_void_p]),
     ("dg_server_release", c_i32, [c_void_p, c_i64]),
     ("dg_server_cancel", c_i32, [c_void_p, c_i64]),
+    ("dg_server_set_work_limit", c_i32, [c_void_p, c_i64]),
     ("dg_server_stats", c_i32, [c_void_p, P(c_i64), P(c_i64), P(c_i64), P(c_i64)]),
     ("dg_partition_create", c_i32, [c_void_p, c_i32, P(c_void_p)]),
     ("dg_partition_destroy", None, [c_void_p]),

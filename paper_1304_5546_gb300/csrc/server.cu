@@ -8,7 +8,8 @@
 //   2. admits queued requests, oldest first, into the batch while their
 //      order's pool has a free range (the memory budget is the pools'
 //      capacity; a request that does not fit waits, later smaller ones may
-//      pass it);
+//      pass it) and, with a work limit, while the running requests' nodal
+//      values stay within it (there the queue is first come, first served);
 //   3. advances every admitted request by a chunk of LSRK steps (the
 //      smallest number of steps any of them has left, at most kChunk) with
 //      one dg_batch_step, so requests that arrive while others run join at
@@ -62,7 +63,7 @@ struct Request {
   int32_t slot = -1;
   int32_t state = DG_REQUEST_QUEUED;
   dg_status status = DG_OK;
-  double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+  double t_submit = 0.0, t_admit = 0.0, t_done = 0.0, t_retired = 0.0;
   size_t staging_idx = 0;  // pinned buffer holding the result on its way out
   bool staged = false;     // staging_idx is held for this request
   bool cancel = false;     // dg_server_cancel asked for it (under the server lock)
@@ -92,6 +93,7 @@ struct dg_server {
   std::vector<cudaEvent_t> spare_events;
   int64_t completed = 0, failed = 0, cancelled = 0;
   std::atomic<int64_t> steps{0}, launches{0};
+  std::atomic<int64_t> max_nodes{0};  // work limit (dg_server_set_work_limit); 0: none
 };
 
 namespace {
@@ -152,6 +154,9 @@ void admit(dg_server* s) {
     cand.assign(s->queue.begin(), s->queue.end());
   }
   const bool seq = (s->flags & DG_SERVER_SEQUENTIAL) != 0;
+  const int64_t limit = s->max_nodes.load(std::memory_order_relaxed);
+  int64_t nodes = 0;  // K * Np of the running requests
+  for (const Request* r : s->running) nodes += r->op->K * r->op->Np;
   for (Request* r : cand) {
     bool cancelled = false;
     {
@@ -170,6 +175,8 @@ void admit(dg_server* s) {
       continue;
     }
     if (seq && (!s->running.empty() || !s->finishing.empty())) break;
+    const int64_t r_nodes = r->op->K * r->op->Np;
+    if (limit > 0 && !s->running.empty() && nodes + r_nodes > limit) break;
     int32_t slot = -1;
     dg_status st = dg_batch_add(s->batch, r->op, r->dt, r->has_src ? &r->src : nullptr, s->stream,
                                 &slot);
@@ -201,6 +208,7 @@ void admit(dg_server* s) {
       r->state = DG_REQUEST_RUNNING;
     }
     s->running.push_back(r);
+    nodes += r_nodes;
     if (seq) break;
   }
 }
@@ -253,6 +261,10 @@ dg_status retire(dg_server* s) {
     dg_batch_remove(s->batch, r->slot);
     s->running[i] = s->running.back();
     s->running.pop_back();
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      r->t_retired = now_s();
+    }
     if (st != DG_OK) {
       if (r->staged) s->out_staging.unhold(r->staging_idx);
       r->staged = false;
@@ -442,6 +454,7 @@ void fill_info(const Request* r, dg_request_info* info) {
   info->t_submit = r->t_submit;
   info->t_admit = r->t_admit;
   info->t_done = r->t_done;
+  info->t_retired = r->t_retired;
 }
 
 }  // namespace
@@ -524,5 +537,15 @@ extern "C" dg_status dg_server_stats(dg_server* s, int64_t* completed, int64_t* 
   if (failed) *failed = s->failed;
   if (steps) *steps = s->steps.load();
   if (launches) *launches = s->launches.load();
+  return DG_OK;
+}
+
+extern "C" dg_status dg_server_set_work_limit(dg_server* server, int64_t max_nodes) {
+  dgw::clear_error();
+  if (!server) return fail(DG_ERR_ARG, "dg_server_set_work_limit: NULL server");
+  if (max_nodes < 0)
+    return fail(DG_ERR_ARG, "dg_server_set_work_limit: max_nodes = %lld < 0",
+                static_cast<long long>(max_nodes));
+  server->max_nodes.store(max_nodes, std::memory_order_relaxed);
   return DG_OK;
 }

@@ -209,3 +209,27 @@ def test_cancel_queued_and_running(P, reqs):
     assert qi["state"] == 4 and qi["t_admit"] == 0.0   # cancelled before admission
     assert li["state"] == 4 and np.all(out_long == 0)  # cancelled while running, no result
     assert si["state"] == 2
+
+
+def test_work_limit_bounds_work_stepped_together(P, reqs):
+    # limit = the largest request's nodal values: it runs alone, smaller ones
+    # share the limit; admissions stay first come, first served
+    nodes = [r.K * r.Np for r in reqs]
+    limit = max(nodes)
+    srv = P.Server(_capacity(reqs), work_limit=limit)
+    with pytest.raises(P.DGError):
+        srv.set_work_limit(-1)
+    outs = [r.out() for r in reqs]
+    ids = [srv.submit(r.solver, r.T, source=r.source, q0=r.q0, out=o) for r, o in zip(reqs, outs)]
+    infos = [srv.wait(i, timeout=60.0) for i in ids]
+    srv.close()
+    assert all(i["state"] == 2 for i in infos)
+    admits = [i["t_admit"] for i in infos]
+    assert admits == sorted(admits)
+    for a, (ia, na) in enumerate(zip(infos, nodes)):
+        t = ia["t_admit"]
+        others = [nb for b, (ib, nb) in enumerate(zip(infos, nodes))
+                  if b != a and ib["t_admit"] <= t < ib["t_retired"]]
+        assert not others or sum(others) + na <= limit, (a, others, na, limit)
+    for r, o, info in zip(reqs, outs, infos):
+        assert np.array_equal(o, r.alone(P, info["dt"], info["nsteps"]))
