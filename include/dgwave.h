@@ -276,6 +276,24 @@ dg_status dg_solve(const dg_op* op, void* d_q, void* d_res, double T, double dt,
 dg_status dg_step_host(const dg_op* op, void* h_q, void* d_q, void* d_res, double t0,
                        double dt, int32_t nsteps, void* stream);
 
+/* dg_step_host_jobs: many independent host-resident field sets, each
+ * copied to the device, advanced by nsteps steps and copied back into its
+ * own host buffer, with the copies of one job overlapping the steps of the
+ * next: job j's copy in runs on one internal stream while job j - 1 steps on
+ * `stream`, and job j - 2 is copied out on another.  h_q[j] (j < njobs) are
+ * host buffers of 3 * field_stride values each (pinned memory, or the
+ * copies do not overlap); a buffer may be listed more than once, and a job
+ * then reads it after every earlier job's result has been written there.
+ * d_work is caller-owned device memory of dg_step_host_jobs_work_bytes(op)
+ * bytes (16-byte aligned): three job slots of two field buffers each and
+ * one shared residual buffer.  Every job's stage launches run in order on
+ * `stream`, so each result equals that of dg_step_host on the same fields.
+ * Returns after every result is in host memory.  Errors: those of
+ * dg_step_host, DG_ERR_ARG (njobs < 0, a NULL buffer).                     */
+dg_status dg_step_host_jobs(const dg_op* op, int32_t njobs, void* const* h_q, void* d_work,
+                            double t0, double dt, int32_t nsteps, void* stream);
+int64_t dg_step_host_jobs_work_bytes(const dg_op* op);
+
 /* Size of the scratch array that dg_step_static uses (per device).        */
 #define DG_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 

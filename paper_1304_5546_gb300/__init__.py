@@ -27,6 +27,7 @@ __all__ = [
     "dg_get_info", "dg_get_nodes", "dg_get_reference",
     "dg_get_geometry", "dg_get_maps", "dg_cfl_dt", "dg_lsrk_coefficients",
     "dg_op_destroy", "dg_rhs", "dg_step", "dg_step_static", "dg_solve", "dg_step_host",
+    "dg_step_host_jobs", "dg_step_host_jobs_work_bytes",
     "dg_check_finite", "dg_sync_check", "dg_launch_count", "dg_last_error", "dg_test_wait_timeout",
     "dg_checkpoint_save", "dg_checkpoint_load",
     "dg_batch_create", "dg_batch_destroy", "dg_batch_add", "dg_batch_remove", "dg_batch_info",
@@ -214,6 +215,20 @@ def dg_step_host(op, h_q, d_q, d_res, t0, dt, nsteps, stream=None):
     hp = ctypes.c_void_p(h_q.data_ptr()) if hasattr(h_q, "data_ptr") else _ptr(h_q)
     _lib.check(_lib.load().dg_step_host(op, hp, _dptr(d_q), _dptr(d_res), t0, dt, nsteps,
                                         _stream_handle(stream)), "dg_step_host")
+
+
+def dg_step_host_jobs_work_bytes(op):
+    return int(_lib.load().dg_step_host_jobs_work_bytes(op))
+
+
+def dg_step_host_jobs(op, h_qs, d_work, t0, dt, nsteps, stream=None):
+    """h_qs: list of host tensors (pinned) or contiguous numpy arrays of
+    3 * field_stride values each, one per job; d_work: device tensor of at
+    least dg_step_host_jobs_work_bytes(op) bytes."""
+    ptrs = (ctypes.c_void_p * max(len(h_qs), 1))(
+        *[h.data_ptr() if hasattr(h, "data_ptr") else h.ctypes.data for h in h_qs])
+    _lib.check(_lib.load().dg_step_host_jobs(op, len(h_qs), ptrs, _dptr(d_work), t0, dt, nsteps,
+                                             _stream_handle(stream)), "dg_step_host_jobs")
 
 
 def dg_check_finite(op, q, stream=None):

@@ -86,6 +86,9 @@ SIGNATURES = [
     ("dg_solve", c_i32, [c_void_p, c_void_p, c_void_p, c_dbl, c_dbl, P(c_i32), P(c_dbl), c_void_p]),
     ("dg_step_static", c_i32, [c_void_p, c_void_p, c_void_p, c_dbl, c_dbl, c_i32, c_void_p]),
     ("dg_step_host", c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_dbl, c_dbl, c_i32, c_void_p]),
+    ("dg_step_host_jobs", c_i32, [c_void_p, c_i32, c_void_p, c_void_p, c_dbl, c_dbl, c_i32,
+                                  c_void_p]),
+    ("dg_step_host_jobs_work_bytes", c_i64, [c_void_p]),
     ("dg_check_finite", c_i32, [c_void_p, c_void_p, c_void_p]),
     ("dg_sync_check", c_i32, [c_void_p, c_void_p]),
     ("dg_launch_count", c_i64, [c_void_p]),

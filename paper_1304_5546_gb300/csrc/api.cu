@@ -780,6 +780,158 @@ extern "C" dg_status dg_step_host(const dg_op* op, void* h_q, void* d_q, void* d
   return DG_OK;
 }
 
+namespace {
+
+// nsteps LSRK steps ping-ponging between q and tmp (no copy back); returns
+// the buffer that holds the result
+template <typename T>
+dg_status run_stages(const dg_op* op, T* q, T* tmp, T* res, double dt, int32_t nsteps,
+                     cudaStream_t s, T** result) {
+  dgw::StageArgs<T> a = base_args<T>(op);
+  a.res = res;
+  a.dt = static_cast<T>(dt);
+  T* cur = q;
+  T* other = tmp;
+  for (int32_t n = 0; n < nsteps; ++n) {
+    for (int i = 0; i < 5; ++i) {
+      a.qin = cur;
+      a.qout = other;
+      a.a = static_cast<T>(op->lsrk_a[i]);
+      a.b = static_cast<T>(op->lsrk_b[i]);
+      const int mode = (i == 0) ? dgw::kModeFirstStage : dgw::kModeStage;
+      cudaError_t err = launch_order<T>(op, a, mode, s);
+      if (err != cudaSuccess) return cuda_fail(err, "dg_step_host_jobs: kernel launch");
+      op->launches.fetch_add(1, std::memory_order_relaxed);
+      std::swap(cur, other);
+    }
+  }
+  *result = cur;
+  return DG_OK;
+}
+
+// Pipeline of dg_step_host_jobs: slot j % kJobSlots of the work buffer holds
+// job j's fields (q, tmp); the residual is shared (the first stage of a step
+// overwrites it, and the stage launches of all jobs run in order on one
+// stream).
+constexpr int kJobSlots = 3;
+
+struct JobPipe {
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t start = nullptr;
+  cudaEvent_t in_done[kJobSlots] = {}, comp_done[kJobSlots] = {}, free_slot[kJobSlots] = {};
+  bool used[kJobSlots] = {};
+
+  cudaError_t create() {
+    cudaError_t err = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+    for (int i = 0; i < kJobSlots && err == cudaSuccess; ++i) {
+      err = cudaEventCreateWithFlags(&in_done[i], cudaEventDisableTiming);
+      if (err == cudaSuccess) err = cudaEventCreateWithFlags(&comp_done[i], cudaEventDisableTiming);
+      if (err == cudaSuccess) err = cudaEventCreateWithFlags(&free_slot[i], cudaEventDisableTiming);
+    }
+    return err;
+  }
+  ~JobPipe() {
+    if (h2d) cudaStreamSynchronize(h2d);
+    if (d2h) cudaStreamSynchronize(d2h);
+    for (int i = 0; i < kJobSlots; ++i) {
+      if (in_done[i]) cudaEventDestroy(in_done[i]);
+      if (comp_done[i]) cudaEventDestroy(comp_done[i]);
+      if (free_slot[i]) cudaEventDestroy(free_slot[i]);
+    }
+    if (start) cudaEventDestroy(start);
+    if (h2d) cudaStreamDestroy(h2d);
+    if (d2h) cudaStreamDestroy(d2h);
+  }
+};
+
+template <typename T>
+dg_status run_jobs(const dg_op* op, int32_t njobs, void* const* h_q, T* work, double dt,
+                   int32_t nsteps, cudaStream_t s) {
+  const char* where = "dg_step_host_jobs";
+  const size_t fvals = 3 * static_cast<size_t>(op->fstride);
+  const size_t bytes = fvals * sizeof(T);
+  T* res = work + 2 * kJobSlots * fvals;
+  JobPipe pipe;
+  cudaError_t err = pipe.create();
+  if (err != cudaSuccess) return cuda_fail(err, where);
+  // the entries of each field beyond K * Np never reach a result, but the
+  // per-block bulk copies read them; zero them in the buffers the host does
+  // not fill, so that no value left in the work memory is ever read
+  const size_t used = static_cast<size_t>(op->K) * op->Np;
+  const size_t tail = (static_cast<size_t>(op->fstride) - used) * sizeof(T);
+  for (int b = 0; b <= 2 * kJobSlots && tail > 0 && err == cudaSuccess; ++b) {
+    if (b < 2 * kJobSlots && b % 2 == 0) continue;  // a slot's q comes from the host
+    for (int f = 0; f < 3 && err == cudaSuccess; ++f)
+      err = cudaMemsetAsync(work + b * fvals + f * static_cast<size_t>(op->fstride) + used, 0,
+                            tail, s);
+  }
+  if (err != cudaSuccess) return cuda_fail(err, where);
+  // the copies start after whatever the caller queued on `stream` before
+  err = cudaEventRecord(pipe.start, s);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(pipe.h2d, pipe.start, 0);
+  if (err != cudaSuccess) return cuda_fail(err, where);
+  for (int32_t j = 0; j < njobs; ++j) {
+    const int slot = j % kJobSlots;
+    T* q = work + 2 * slot * fvals;
+    T* tmp = q + fvals;
+    // copy in once the slot's previous job has been copied out, and once any
+    // earlier job still in flight that shares this host buffer has written
+    // its result there (jobs j - 1 and j - 2; job j - 3 is the slot's own)
+    if (pipe.used[slot]) err = cudaStreamWaitEvent(pipe.h2d, pipe.free_slot[slot], 0);
+    for (int back = 1; back < kJobSlots && back <= j && err == cudaSuccess; ++back)
+      if (h_q[j - back] == h_q[j])
+        err = cudaStreamWaitEvent(pipe.h2d, pipe.free_slot[(j - back) % kJobSlots], 0);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(q, h_q[j], bytes, cudaMemcpyHostToDevice, pipe.h2d);
+    if (err == cudaSuccess) err = cudaEventRecord(pipe.in_done[slot], pipe.h2d);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(s, pipe.in_done[slot], 0);
+    if (err != cudaSuccess) return cuda_fail(err, where);
+    T* out = nullptr;
+    dg_status st = run_stages<T>(op, q, tmp, res, dt, nsteps, s, &out);
+    if (st) return st;
+    err = cudaEventRecord(pipe.comp_done[slot], s);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(pipe.d2h, pipe.comp_done[slot], 0);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(h_q[j], out, bytes, cudaMemcpyDeviceToHost, pipe.d2h);
+    if (err == cudaSuccess) err = cudaEventRecord(pipe.free_slot[slot], pipe.d2h);
+    if (err != cudaSuccess) return cuda_fail(err, where);
+    pipe.used[slot] = true;
+  }
+  err = cudaStreamSynchronize(pipe.d2h);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_step_host_jobs: synchronize");
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" int64_t dg_step_host_jobs_work_bytes(const dg_op* op) {
+  if (!op) return 0;
+  return static_cast<int64_t>(2 * kJobSlots + 1) * 3 * op->fstride *
+         static_cast<int64_t>(op->elem_size);
+}
+
+extern "C" dg_status dg_step_host_jobs(const dg_op* op, int32_t njobs, void* const* h_q,
+                                       void* d_work, double t0, double dt, int32_t nsteps,
+                                       void* stream) {
+  dgw::clear_error();
+  (void)t0;
+  const char* where = "dg_step_host_jobs";
+  dg_status st = check_device_op(op, where);
+  if (st) return st;
+  if (njobs < 0 || nsteps < 0 || !std::isfinite(dt))
+    return fail(DG_ERR_ARG, "%s: bad njobs/nsteps/dt", where);
+  if (njobs == 0) return DG_OK;
+  if (!h_q) return fail(DG_ERR_ARG, "%s: h_q is NULL", where);
+  for (int32_t j = 0; j < njobs; ++j)
+    if (!h_q[j]) return fail(DG_ERR_ARG, "%s: h_q[%d] is NULL", where, j);
+  if ((st = check_field(op, d_work, "d_work", where))) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (op->precision == DG_FP32)
+    return run_jobs<float>(op, njobs, h_q, static_cast<float*>(d_work), dt, nsteps, s);
+  return run_jobs<double>(op, njobs, h_q, static_cast<double*>(d_work), dt, nsteps, s);
+}
+
 extern "C" dg_status dg_check_finite(const dg_op* op, const void* d_q, void* stream) {
   dgw::clear_error();
   dg_status st = check_device_op(op, "dg_check_finite");
