@@ -599,8 +599,10 @@ dg_status dg_checkpoint_load(const dg_op* op, const char* path, void* q, int64_t
  * traces into a send buffer, one contiguous message per (sender, receiver)
  * pair), the transfer (between GPUs one send / receive per pair; on one
  * device a single copy of all messages into the receive buffer), unpack
- * (one kernel into the ghost slots), then one stage launch per part.  The
- * result equals, bit for bit, the unpartitioned operator's.
+ * (one kernel into the ghost slots), then one stage launch per part, each
+ * on a stream of the partition's own (the parts' launches of a stage are
+ * independent), which `stream` waits for.  The result equals, bit for bit,
+ * the unpartitioned operator's.
  *
  * dg_partition_create: partitions `op` (not owned; it must outlive the
  * partition) into P parts, 1 <= P <= min(K, 64).  With a device operator it

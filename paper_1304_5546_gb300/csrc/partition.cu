@@ -157,8 +157,20 @@ struct dg_partition {
   void* d_send = nullptr;
   void* d_recv = nullptr;
   int cur = 0;  // parity of the buffers holding the current fields
+  // one stream per part: the parts' stage launches of one stage are
+  // independent, so a part's CTAs start on the SMs that the previous part's
+  // tail leaves idle
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> part_done;
+  cudaEvent_t exchanged = nullptr;
 
   ~dg_partition() {
+    for (cudaStream_t st : streams) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+    for (cudaEvent_t e : part_done) cudaEventDestroy(e);
+    if (exchanged) cudaEventDestroy(exchanged);
     for (dg_op* s : sub) dg_op_destroy(s);
     for (void* p : d_q) cudaFree(p);
     for (void* p : d_res) cudaFree(p);
@@ -350,6 +362,16 @@ dg_status build_device(dg_partition& pt) {
                        cudaMemcpyHostToDevice);
   }
   if (err != cudaSuccess) return cuda_fail(err, "dg_partition_create: exchange tables");
+  err = cudaEventCreateWithFlags(&pt.exchanged, cudaEventDisableTiming);
+  for (int p = 0; p < P && err == cudaSuccess; ++p) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (err == cudaSuccess) pt.streams.push_back(st);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (err == cudaSuccess) pt.part_done.push_back(ev);
+  }
+  if (err != cudaSuccess) return cuda_fail(err, "dg_partition_create: streams");
   return DG_OK;
 }
 
@@ -594,16 +616,22 @@ extern "C" dg_status dg_partition_step(dg_partition* part, double dt, int32_t ns
   if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "%s: dt is not finite", where);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool fp32 = part->op->precision == DG_FP32;
+  // per stage: the exchange on `stream`, then every part's stage launch on
+  // its own stream once the exchange is done, and `stream` waits for them all
   for (int32_t n = 0; n < nsteps; ++n) {
     for (int i = 0; i < 5; ++i) {
       cudaError_t err = fp32 ? exchange<float>(*part, s) : exchange<double>(*part, s);
+      if (err == cudaSuccess) err = cudaEventRecord(part->exchanged, s);
       if (err != cudaSuccess) return cuda_fail(err, "dg_partition_step: exchange");
       for (int p = 0; p < part->P; ++p) {
         dg_op* sub = part->sub[p];
-        if (sub->K == 0) continue;
+        cudaStream_t ps = part->streams[p];
         void* qin = part->cur ? sub->d_qtmp : part->d_q[p];
         void* qout = part->cur ? part->d_q[p] : sub->d_qtmp;
-        err = dgw::op_stage(sub, qin, qout, part->d_res[p], i, dt, s);
+        err = cudaStreamWaitEvent(ps, part->exchanged, 0);
+        if (err == cudaSuccess) err = dgw::op_stage(sub, qin, qout, part->d_res[p], i, dt, ps);
+        if (err == cudaSuccess) err = cudaEventRecord(part->part_done[p], ps);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(s, part->part_done[p], 0);
         if (err != cudaSuccess) return cuda_fail(err, "dg_partition_step: stage launch");
         sub->launches.fetch_add(1, std::memory_order_relaxed);
       }
