@@ -152,6 +152,13 @@ def test_error_codes(dgw):
             st = lib.dg_step(op, ctypes.c_void_p(16), ctypes.c_void_p(4096), 0.0, 0.1, 1, None)
             assert st == _lib.DG_ERR_NO_DEVICE
             assert lib.dg_launch_count(op) == 0
+            # pipelined host jobs: three slots of two field buffers and one
+            # shared residual; refused without a device
+            Np, _, K, fstride = dgw.dg_get_info(op)
+            assert lib.dg_step_host_jobs_work_bytes(op) == 7 * 3 * fstride * 4
+            bufs = (ctypes.c_void_p * 1)(ctypes.c_void_p(4096))
+            st = lib.dg_step_host_jobs(op, 1, bufs, ctypes.c_void_p(4096), 0.0, 0.1, 1, None)
+            assert st == _lib.DG_ERR_NO_DEVICE
             st = lib.dg_cfl_dt(op, -1.0, ctypes.byref(ctypes.c_double()))
             assert st == _lib.DG_ERR_ARG
         finally:
