@@ -147,6 +147,64 @@ def oracle_sample_rate(n, N, seconds, steps=None, warmup=0):
     return d.K * 5 * done / el, done, d.K, el
 
 
+def oracle_timings():
+    """The oracle's own timings on this host, in the calling process: per
+    right-hand side and per LSRK(5,4) step on the three configurations
+    (bounded samples of the two large ones), and the whole cavity solve of
+    the small one.  Returns a dict (seconds and element-stage updates/s)."""
+    import numpy as np
+
+    import oracle as O
+    from synth import cavity_mode, gaussian_pulse, jittered_delaunay_mesh, square_grid_mesh
+
+    def per_call(fn, min_s=2.0):
+        fn()
+        t0, k = time.perf_counter(), 0
+        while True:
+            fn()
+            k += 1
+            el = time.perf_counter() - t0
+            if el >= min_s:
+                return el / k, k
+
+    out = {}
+    # cavity: [-1,1]^2, 8x8 squares x 2, N = 4, T = 1 at the CFL step
+    d = O.Discretization(*square_grid_mesh(8, 8), 4)
+    q0 = np.stack(cavity_mode(d.x, d.y, 0.0))
+    rhs_s, _ = per_call(lambda: O.maxwell_rhs(d, q0))
+    t0 = time.perf_counter()
+    qT, t = O.solve(d, q0, 1.0, O.cfl_dt(d))
+    solve_s = time.perf_counter() - t0
+    nsteps = int(np.ceil(1.0 / O.cfl_dt(d) - 1e-12))
+    out["cavity_N4_K128"] = {"K": d.K, "N": 4, "rhs_s": rhs_s, "solve_s": solve_s,
+                             "steps": nsteps, "max_error_vs_exact": float(
+                                 np.abs(qT - np.stack(cavity_mode(d.x, d.y, t))).max()),
+                             "element_stage_per_s": d.K * 5 * nsteps / solve_s}
+    # samples of the large configurations
+    for name, n, N in (("jittered_N5_sample", 100, 5), ("jittered_N7_sample", 50, 7)):
+        d = O.Discretization(*jittered_delaunay_mesh(n, seed=2024), N)
+        q = np.stack(gaussian_pulse(d.x, d.y))
+        dt = O.cfl_dt(d)
+        rhs_s, _ = per_call(lambda: O.maxwell_rhs(d, q))
+        step_s, k = per_call(lambda: O.lsrk_step(d, q, 0.0, dt))
+        out[name] = {"K": d.K, "N": N, "n": n, "rhs_s": rhs_s, "step_s": step_s, "steps_timed": k,
+                     "element_stage_per_s": d.K * 5 / step_s}
+    return out
+
+
+def run_oracle_study(args):
+    """The oracle timed on the host cores, one thread (child process with
+    the BLAS / OpenMP thread counts pinned to 1) and the default threads.
+    One JSON line."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle-timings"]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1200)
+    one = json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else {
+        "error": r.stderr[-500:]}
+    return {"study": "oracle timings", "kind": "oracle", "host_cores": os.cpu_count(),
+            "one_thread": one, "default_threads": oracle_timings()}
+
+
 def cpu_baseline(n=100, N=5, seconds=10.0):
     """The oracle on one host core (BLAS/OpenMP threads pinned to 1), in a
     child process so the thread limit applies before numpy loads."""
@@ -837,7 +895,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--_oracle-sample", nargs=3, default=None)
-    ap.add_argument("--study", choices=["precision", "sweep", "partition"], default=None,
+    ap.add_argument("--_oracle-timings", action="store_true")
+    ap.add_argument("--study", choices=["precision", "sweep", "partition", "oracle"], default=None,
                     help="instead of the benchmark line: the precision-path study "
                          "(use with --order 7 --n 362 for K = 262,088)")
     ap.add_argument("--study-steps", type=int, default=500)
@@ -871,6 +930,12 @@ def main(argv=None):
         return 0
     if args.study == "partition":
         print(json.dumps(run_partition_study(args)), flush=True)
+        return 0
+    if args._oracle_timings:
+        print(json.dumps(oracle_timings()), flush=True)
+        return 0
+    if args.study == "oracle":
+        print(json.dumps(run_oracle_study(args)), flush=True)
         return 0
     if args.workload == "serving" and args.impl == "ours":
         print(json.dumps(run_serving(args)), flush=True)
