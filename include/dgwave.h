@@ -75,6 +75,9 @@ typedef int32_t dg_status;
 #define DG_ERR_TIMEOUT 9            /* a kernel's bounded wait expired       */
 #define DG_ERR_IO 10                /* a checkpoint file could not be read or
                                        written                               */
+#define DG_ERR_INDEX 11             /* a checked build (libdgwave_checked.so)
+                                       found an index in device tables out of
+                                       range and skipped the access          */
 
 #define DG_FP64 0
 #define DG_FP32 1
@@ -660,7 +663,12 @@ dg_status dg_check_finite(const dg_op* op, const void* d_q, void* stream);
 /* dg_sync_check: synchronises `stream` and reports any pending CUDA error
  * (DG_ERR_CUDA with its message in dg_last_error()), then reads and clears
  * the operator's kernel status word: DG_ERR_TIMEOUT if a stage kernel gave
- * up waiting for its own shared-memory copies (bounded waits, ~2 s).       */
+ * up waiting for its own shared-memory copies (bounded waits, ~2 s), and
+ * DG_ERR_INDEX if a checked build's kernel found a face connection code or
+ * a block-table entry out of range (the access is skipped, the result is
+ * not valid).  The checked build is the same library compiled with
+ * DGW_DEVICE_CHECKS into libdgwave_checked.so; the Python binding loads it
+ * when DGWAVE_CHECKED=1.                                                    */
 dg_status dg_sync_check(const dg_op* op, void* stream);
 
 /* dg_test_wait_timeout: the timeout path, exercised without any fault.

@@ -9,7 +9,10 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libdgwave.so")
+# DGWAVE_CHECKED=1: the checked build (device-side index checks that report
+# DG_ERR_INDEX instead of faulting), built by build(checked=True)
+CHECKED = os.environ.get("DGWAVE_CHECKED", "") == "1"
+LIB_PATH = os.path.join(_PKG, "libdgwave_checked.so" if CHECKED else "libdgwave.so")
 
 DG_OK = 0
 DG_ERR_ARG = 1
@@ -22,6 +25,7 @@ DG_ERR_NONFINITE = 7
 DG_ERR_NO_DEVICE = 8
 DG_ERR_TIMEOUT = 9
 DG_ERR_IO = 10
+DG_ERR_INDEX = 11
 DG_CKPT_HOST = 1
 DG_FP64 = 0
 DG_FP32 = 1
@@ -42,7 +46,7 @@ DG_N_MAX = 7
 _STATUS_NAMES = {
     0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_MESH_DEGENERATE", 3: "DG_ERR_MESH_NONCONFORMING",
     4: "DG_ERR_ORDER", 5: "DG_ERR_CUDA", 6: "DG_ERR_OOM", 7: "DG_ERR_NONFINITE",
-    8: "DG_ERR_NO_DEVICE", 9: "DG_ERR_TIMEOUT", 10: "DG_ERR_IO",
+    8: "DG_ERR_NO_DEVICE", 9: "DG_ERR_TIMEOUT", 10: "DG_ERR_IO", 11: "DG_ERR_INDEX",
 }
 
 c_void_p = ctypes.c_void_p

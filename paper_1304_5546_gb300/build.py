@@ -1,6 +1,10 @@
 """Build the in-tree shared library ``libdgwave.so`` (C ABI of include/dgwave.h)
 for sm_103a with nvcc.  Translation units compile in parallel; the link step
-produces ``paper_1304_5546_gb300/libdgwave.so``."""
+produces ``paper_1304_5546_gb300/libdgwave.so``.  ``build(checked=True)``
+builds the same sources with DGW_DEVICE_CHECKS into ``libdgwave_checked.so``:
+the stage kernels then test the face connection codes and block-table
+entries they read before using them, and report DG_ERR_INDEX instead of
+faulting."""
 import concurrent.futures as cf
 import os
 import shutil
@@ -12,6 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdgwave.so")
+LIB_CHECKED = os.path.join(PKG, "libdgwave_checked.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,22 +45,26 @@ def _deps():
             + [os.path.join(INCLUDE, "dgwave.h"), os.path.abspath(__file__)])
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    """Compile and link the library; returns its path."""
-    if not force and up_to_date():
-        return LIB
+def build(force=False, verbose=False, extra_flags=(), checked=False):
+    """Compile and link the library (the checked build with checked=True);
+    returns its path."""
+    lib, bdir = (LIB_CHECKED, BUILD_CHECKED) if checked else (LIB, BUILD)
+    if checked:
+        extra_flags = tuple(extra_flags) + ("-DDGW_DEVICE_CHECKS",)
+    if not force and up_to_date(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(bdir, exist_ok=True)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         cmd = [nvcc, *COMMON, *ARCH, *extra_flags, "-c", src, "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc, "-x", "c++", *COMMON, *extra_flags, "-c", src, "-o", obj]
@@ -68,13 +78,13 @@ def build(force=False, verbose=False, extra_flags=()):
     workers = min(len(sources()), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 

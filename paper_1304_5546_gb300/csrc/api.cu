@@ -974,6 +974,8 @@ extern "C" dg_status dg_sync_check(const dg_op* op, void* stream) {
   if (err != cudaSuccess) return cuda_fail(err, "dg_sync_check: status read");
   if (status != 0) {
     cudaMemset(op->d_status, 0, sizeof(int));
+    if (status & dgw::kStatusIndex)
+      return fail(DG_ERR_INDEX, "dg_sync_check: a checked kernel found an index out of range");
     return fail(DG_ERR_TIMEOUT, "dg_sync_check: a kernel's bounded wait expired");
   }
   return DG_OK;

@@ -920,6 +920,9 @@ extern "C" dg_status dg_batch_sync_check(dg_batch* b, void* stream) {
   if (err != cudaSuccess) return cuda_fail(err, "dg_batch_sync_check: status read");
   if (status != 0) {
     cudaMemset(b->d_status, 0, sizeof(int));
+    if (status & dgw::kStatusIndex)
+      return fail(DG_ERR_INDEX,
+                  "dg_batch_sync_check: a checked kernel found an index out of range");
     return fail(DG_ERR_TIMEOUT, "dg_batch_sync_check: a kernel's bounded wait expired");
   }
   return DG_OK;

@@ -230,6 +230,12 @@ __global__ void __launch_bounds__(Layout<T, N, MEDIA>::THREADS)
       const int ee = task_e[u];
       if (ee < E && k0 + ee < K) {
         const int32_t code = sc[ee * 3 + task_f[u]];
+#ifdef DGW_DEVICE_CHECKS
+        if (!nbr_code_ok(code, p.fstride, Np)) {
+          atomicOr(p.status, kStatusIndex);
+          continue;
+        }
+#endif
         if (code >= 0) {
           const int gP = (code >> 3) * Np + nbr[(code & 7) * Nfp + task_jj[u]];
           trc[u][0] = __ldg(qin[0] + gP);
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(Layout<T, N, MEDIA>::THREADS)
   if (it < niter && t == 0) {
     // a wait expired: report, then let this CTA's copies in flight land
     // (each wait bounded) before the CTA's shared memory is released
-    atomicExch(p.status, 1);
+    atomicOr(p.status, kStatusTimeout);
     for (int j = it; j < issued; ++j)
       mbar_wait_bounded(&bars[j % kStages], static_cast<uint32_t>((j / kStages) & 1),
                         kWaitLimitNs);

@@ -363,6 +363,14 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
       const int2 d = __ldg(p.blocks + b);
       k0 = d.x;
       n = d.y;
+#ifdef DGW_DEVICE_CHECKS
+      if (!block_ok(k0, n, E, fs, Np)) {  // no access to the block; the CTA stops
+        atomicOr(p.status, kStatusIndex);
+        *abort_flag = 1;
+        k0 = 0;
+        n = 0;
+      }
+#endif
     } else {
       k0 = b * E;
       n = (K - k0) < E ? (K - k0) : E;
@@ -403,7 +411,7 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
 
   auto fail = [&]() {
     *abort_flag = 1;
-    atomicExch(p.status, 1);
+    atomicOr(p.status, kStatusTimeout);
   };
 
   if (warp == L::IO_WARP) {
@@ -414,6 +422,9 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
         const int s = it % S;
         int k0, n;
         block_at(it, k0, n);
+#ifdef DGW_DEVICE_CHECKS
+        if (n == 0) return;  // rejected block: the abort flag ends every wait
+#endif
         const uint32_t qb = round16(static_cast<uint32_t>(n * Np * 4));
         const uint32_t gb = round16(static_cast<uint32_t>(n * GEO * 4));
         const uint32_t cb = round16(static_cast<uint32_t>(n * 3 * 4));
@@ -584,6 +595,12 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
         const int ee = task_e[u];
         if (ee < nv) {
           const int32_t code = sc[task_cf[u]];
+#ifdef DGW_DEVICE_CHECKS
+          if (!nbr_code_ok(code, fs, Np)) {
+            atomicOr(p.status, kStatusIndex);
+            continue;
+          }
+#endif
           if (code >= 0) {
             const int gP = (code >> 3) * Np + nbr[(code & 7) * Nfp + task_jj[u]];
             trc[u][0] = __ldg(qin[0] + gP);

@@ -26,6 +26,26 @@ cudaError_t configure_once_per_device(std::atomic<uint64_t>& done, F configure) 
   return err;
 }
 
+// Bits of a launch's status word (dg_sync_check): a bounded wait expired;
+// a checked build (DGW_DEVICE_CHECKS) found an index it read from device
+// memory out of range and skipped the access instead of making it.
+constexpr int kStatusTimeout = 1, kStatusIndex = 2;
+
+// Checked builds: a face connection code (-1, or neighbour * 8 + face * 2 +
+// reversed) names a face 0..2 of an element whose Np values lie inside a
+// field of fstride values.
+__host__ __device__ constexpr bool nbr_code_ok(int32_t code, int64_t fstride, int Np) {
+  return code < 0 || (((code >> 1) & 3) < 3 &&
+                      (static_cast<int64_t>(code >> 3) + 1) * Np <= fstride);
+}
+
+// Checked builds: a block-table entry (first element k0, count n) of a
+// launch with blocks of at most E elements lies inside a field of fstride
+// values.
+__host__ __device__ constexpr bool block_ok(int k0, int n, int E, int64_t fstride, int Np) {
+  return k0 >= 0 && n >= 1 && n <= E && (static_cast<int64_t>(k0) + n) * Np <= fstride;
+}
+
 // geometry record per element: rx ry sx sy, then per face nx ny Fscale/2
 constexpr int kGeo = 13;
 
