@@ -671,6 +671,16 @@ dg_status dg_check_finite(const dg_op* op, const void* d_q, void* stream);
  * when DGWAVE_CHECKED=1.                                                    */
 dg_status dg_sync_check(const dg_op* op, void* stream);
 
+/* dg_test_fail_alloc: allocation failures made on the host.  The n-th
+ * device allocation the library makes from now on (n >= 1) fails with
+ * DG_ERR_OOM without allocating; n = 0 switches this off.  Each set-up call
+ * must then return DG_ERR_OOM, free what it had allocated and leave the
+ * library usable.  dg_test_fail_alloc_pending: allocations left before the
+ * planted failure (0: it happened, or none is planted).  Process-wide; for
+ * tests only.  Errors: DG_ERR_ARG (n < 0).                                 */
+dg_status dg_test_fail_alloc(int32_t n);
+int32_t dg_test_fail_alloc_pending(void);
+
 /* dg_test_wait_timeout: the timeout path, exercised without any fault.
  * Launches one right-hand-side pass of a tensor-core operator whose memory
  * warp first waits, bounded by 0.1 s, for a device flag that nothing sets.

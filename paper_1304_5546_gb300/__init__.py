@@ -27,7 +27,8 @@ __all__ = [
     "dg_get_info", "dg_get_nodes", "dg_get_reference",
     "dg_get_geometry", "dg_get_maps", "dg_cfl_dt", "dg_lsrk_coefficients",
     "dg_op_destroy", "dg_rhs", "dg_step", "dg_step_static", "dg_solve", "dg_step_host",
-    "dg_step_host_jobs", "dg_step_host_jobs_work_bytes",
+    "dg_step_host_jobs", "dg_step_host_jobs_work_bytes", "dg_test_fail_alloc",
+    "dg_test_fail_alloc_pending",
     "dg_check_finite", "dg_sync_check", "dg_launch_count", "dg_last_error", "dg_test_wait_timeout",
     "dg_checkpoint_save", "dg_checkpoint_load",
     "dg_batch_create", "dg_batch_destroy", "dg_batch_add", "dg_batch_remove", "dg_batch_info",
@@ -229,6 +230,14 @@ def dg_step_host_jobs(op, h_qs, d_work, t0, dt, nsteps, stream=None):
         *[h.data_ptr() if hasattr(h, "data_ptr") else h.ctypes.data for h in h_qs])
     _lib.check(_lib.load().dg_step_host_jobs(op, len(h_qs), ptrs, _dptr(d_work), t0, dt, nsteps,
                                              _stream_handle(stream)), "dg_step_host_jobs")
+
+
+def dg_test_fail_alloc(n):
+    _lib.check(_lib.load().dg_test_fail_alloc(int(n)), "dg_test_fail_alloc")
+
+
+def dg_test_fail_alloc_pending():
+    return int(_lib.load().dg_test_fail_alloc_pending())
 
 
 def dg_check_finite(op, q, stream=None):

@@ -97,6 +97,8 @@ SIGNATURES = [
     ("dg_sync_check", c_i32, [c_void_p, c_void_p]),
     ("dg_launch_count", c_i64, [c_void_p]),
     ("dg_test_wait_timeout", c_i32, [c_void_p, c_void_p]),
+    ("dg_test_fail_alloc", c_i32, [c_i32]),
+    ("dg_test_fail_alloc_pending", c_i32, []),
     ("dg_checkpoint_save", c_i32, [c_void_p, c_void_p, c_i64, c_i32, c_dbl, c_i64, ctypes.c_char_p]),
     ("dg_checkpoint_load", c_i32, [c_void_p, ctypes.c_char_p, c_void_p, c_i64, c_i32, P(c_dbl),
                                    P(c_i64)]),

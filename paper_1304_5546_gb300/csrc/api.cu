@@ -15,6 +15,7 @@
 
 namespace dgw {
 const char* last_error_cstr();
+std::atomic<int> g_fail_alloc{0};
 }
 
 using dgw::fail;
@@ -204,25 +205,25 @@ dg_status upload(dg_op* op, const std::vector<double>& rec_in,
       {&op->d_conn, conn.data(), conn.size() * sizeof(int32_t)},
   };
   for (const Up& u : ups) {
-    cudaError_t err = cudaMalloc(u.dst, u.bytes);
+    cudaError_t err = dgw::dev_malloc(u.dst, u.bytes);
     if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc");
     err = cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMemcpy");
   }
-  cudaError_t err = cudaMalloc(&op->d_qtmp, 3 * op->fstride * sizeof(T));
+  cudaError_t err = dgw::dev_malloc(&op->d_qtmp, 3 * op->fstride * sizeof(T));
   if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(field buffer)");
   err = cudaMemset(op->d_qtmp, 0, 3 * op->fstride * sizeof(T));
   if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMemset");
-  err = cudaMalloc(&op->d_flag, sizeof(int));
+  err = dgw::dev_malloc(&op->d_flag, sizeof(int));
   if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(flag)");
   if (op->use_tc) {
     const std::vector<unsigned char> tiles = tc_operator_tiles(op->ref, op->tc_prec);
-    err = cudaMalloc(&op->d_tcop, tiles.size());
+    err = dgw::dev_malloc(&op->d_tcop, tiles.size());
     if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(operator tiles)");
     err = cudaMemcpy(op->d_tcop, tiles.data(), tiles.size(), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMemcpy(operator tiles)");
   }
-  err = cudaMalloc(&op->d_status, sizeof(int));
+  err = dgw::dev_malloc(&op->d_status, sizeof(int));
   if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMalloc(status)");
   err = cudaMemset(op->d_status, 0, sizeof(int));
   if (err != cudaSuccess) return cuda_fail(err, "dg_operator_setup: cudaMemset(status)");
@@ -621,7 +622,7 @@ extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, dou
   cudaError_t err = cudaSuccess;
   if (!op->d_tcop) {  // the tensor-core kernel's operator tiles
     const std::vector<unsigned char> tiles = tc_operator_tiles(op->ref, dgw::kTcTf32x3);
-    err = cudaMalloc(&op->d_tcop, tiles.size());
+    err = dgw::dev_malloc(&op->d_tcop, tiles.size());
     if (err == cudaSuccess)
       err = cudaMemcpy(op->d_tcop, tiles.data(), tiles.size(), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return cuda_fail(err, "dg_operator_tune: operator tiles");
@@ -629,7 +630,7 @@ extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, dou
   // scratch fields q, q_out and res (zero), stage-2 launches of each kernel
   const size_t fb = 3 * static_cast<size_t>(op->fstride) * sizeof(float);
   float* buf = nullptr;
-  err = cudaMalloc(reinterpret_cast<void**>(&buf), 3 * fb);
+  err = dgw::dev_malloc(reinterpret_cast<void**>(&buf), 3 * fb);
   if (err == cudaSuccess) err = cudaMemsetAsync(buf, 0, 3 * fb, s);
   if (err != cudaSuccess) {
     if (buf) cudaFree(buf);
@@ -989,7 +990,7 @@ extern "C" dg_status dg_test_wait_timeout(const dg_op* op, void* stream) {
     return fail(DG_ERR_ARG, "dg_test_wait_timeout: needs an operator on the tensor-core kernel");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* gate = nullptr;
-  cudaError_t err = cudaMalloc(reinterpret_cast<void**>(&gate), sizeof(int));
+  cudaError_t err = dgw::dev_malloc(reinterpret_cast<void**>(&gate), sizeof(int));
   if (err == cudaSuccess) err = cudaMemsetAsync(gate, 0, sizeof(int), s);
   if (err == cudaSuccess) {
     dgw::StageArgs<float> a = base_args<float>(op);
@@ -1149,3 +1150,14 @@ cudaError_t op_stage(const dg_op* op, const void* qin, void* qout, void* res, in
 }
 
 }  // namespace dgw
+
+extern "C" dg_status dg_test_fail_alloc(int32_t n) {
+  dgw::clear_error();
+  if (n < 0) return fail(DG_ERR_ARG, "dg_test_fail_alloc: n = %d < 0", n);
+  dgw::g_fail_alloc.store(n, std::memory_order_relaxed);
+  return DG_OK;
+}
+
+extern "C" int32_t dg_test_fail_alloc_pending(void) {
+  return dgw::g_fail_alloc.load(std::memory_order_relaxed);
+}

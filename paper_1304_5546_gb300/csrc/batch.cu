@@ -217,7 +217,7 @@ dg_status alloc_pool(dg_batch* b, int N, int64_t cap) {
       {reinterpret_cast<void**>(&p.blocks), static_cast<size_t>(p.max_blocks) * sizeof(int2)},
   };
   for (const A& a : allocs) {
-    cudaError_t err = cudaMalloc(a.dst, a.bytes);
+    cudaError_t err = dgw::dev_malloc(a.dst, a.bytes);
     if (err != cudaSuccess) return cuda_fail(err, "dg_batch_create: cudaMalloc");
     err = cudaMemset(*a.dst, 0, a.bytes);
     if (err != cudaSuccess) return cuda_fail(err, "dg_batch_create: cudaMemset");
@@ -228,9 +228,9 @@ dg_status alloc_pool(dg_batch* b, int N, int64_t cap) {
     lam[p.Np + n] = static_cast<float>(0.5 * (1.0 + ref.s[n]));
   }
   const std::vector<unsigned char> tiles = dgw::tc_operator_tiles(ref, dgw::kTcTf32x3);
-  cudaError_t err = cudaMalloc(reinterpret_cast<void**>(&p.lam), lam.size() * 4);
+  cudaError_t err = dgw::dev_malloc(reinterpret_cast<void**>(&p.lam), lam.size() * 4);
   if (err == cudaSuccess) err = cudaMemcpy(p.lam, lam.data(), lam.size() * 4, cudaMemcpyHostToDevice);
-  if (err == cudaSuccess) err = cudaMalloc(&p.tcop, tiles.size());
+  if (err == cudaSuccess) err = dgw::dev_malloc(&p.tcop, tiles.size());
   if (err == cudaSuccess) err = cudaMemcpy(p.tcop, tiles.data(), tiles.size(), cudaMemcpyHostToDevice);
   if (err != cudaSuccess) return cuda_fail(err, "dg_batch_create: operator upload");
   p.free_ranges[0] = cap;
@@ -457,20 +457,20 @@ extern "C" dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_
     b->cost[g] = model_cost(g + 1);
   }
   for (int g = 0; g < kOrders; ++g) b->max_slots += capacity[g] > 0 ? capacity[g] / 4 + 1 : 0;
-  err = cudaMalloc(reinterpret_cast<void**>(&b->d_meta), 17 * sizeof(int));
+  err = dgw::dev_malloc(reinterpret_cast<void**>(&b->d_meta), 17 * sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(b->d_meta, 0, 17 * sizeof(int));
   if (err == cudaSuccess)
-    err = cudaMalloc(reinterpret_cast<void**>(&b->d_src_w), b->max_slots * dgw::kSrcStride * 4);
+    err = dgw::dev_malloc(reinterpret_cast<void**>(&b->d_src_w), b->max_slots * dgw::kSrcStride * 4);
   if (err == cudaSuccess)
-    err = cudaMalloc(reinterpret_cast<void**>(&b->d_src_meta), b->max_slots * 4 * sizeof(double));
+    err = dgw::dev_malloc(reinterpret_cast<void**>(&b->d_src_meta), b->max_slots * 4 * sizeof(double));
   if (err == cudaSuccess)
-    err = cudaMalloc(reinterpret_cast<void**>(&b->d_src_step), b->max_slots * sizeof(int));
+    err = dgw::dev_malloc(reinterpret_cast<void**>(&b->d_src_step), b->max_slots * sizeof(int));
   const size_t clock_bytes = 2 * static_cast<size_t>(b->num_sms) * sizeof(unsigned long long);
-  if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void**>(&b->d_clock), clock_bytes);
+  if (err == cudaSuccess) err = dgw::dev_malloc(reinterpret_cast<void**>(&b->d_clock), clock_bytes);
   if (err == cudaSuccess) err = cudaMemset(b->d_clock, 0, clock_bytes);
   if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void**>(&b->h_clock), clock_bytes);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->clock_ev, cudaEventDisableTiming);
-  if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(int));
+  if (err == cudaSuccess) err = dgw::dev_malloc(reinterpret_cast<void**>(&b->d_status), sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(b->d_status, 0, sizeof(int));
   if (err != cudaSuccess) {
     destroy_batch(b);

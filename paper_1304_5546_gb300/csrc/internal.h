@@ -73,6 +73,24 @@ inline int face_node(int N, int f, int j) {
 // LSRK(5,4) 2N-storage coefficients and stage times.
 void lsrk_coefficients(double a[5], double b[5], double c[5]);
 
+// Device allocations of the library go through dev_malloc.  Test hook
+// (dg_test_fail_alloc): while g_fail_alloc = n > 0, each allocation counts
+// it down, and the one that takes it from 1 to 0 fails with
+// cudaErrorMemoryAllocation without allocating.
+extern std::atomic<int> g_fail_alloc;
+
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  int n = g_fail_alloc.load(std::memory_order_relaxed);
+  while (n > 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 1) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
 }  // namespace dgw
 
 // Operator handle (dg_op of the C ABI).

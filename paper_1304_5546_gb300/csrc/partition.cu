@@ -316,11 +316,11 @@ dg_status build_device(dg_partition& pt) {
     void* q = nullptr;
     void* r = nullptr;
     int64_t* g = nullptr;
-    cudaError_t err = cudaMalloc(&q, fb);
+    cudaError_t err = dgw::dev_malloc(&q, fb);
     if (err == cudaSuccess) pt.d_q.push_back(q);
-    if (err == cudaSuccess) err = cudaMalloc(&r, fb);
+    if (err == cudaSuccess) err = dgw::dev_malloc(&r, fb);
     if (err == cudaSuccess) pt.d_res.push_back(r);
-    if (err == cudaSuccess) err = cudaMalloc(&g, std::max<size_t>(el.size(), 1) * 8);
+    if (err == cudaSuccess) err = dgw::dev_malloc(&g, std::max<size_t>(el.size(), 1) * 8);
     if (err == cudaSuccess) pt.d_gid.push_back(g);
     if (err == cudaSuccess) err = cudaMemset(q, 0, fb);
     if (err == cudaSuccess) err = cudaMemset(r, 0, fb);
@@ -345,12 +345,12 @@ dg_status build_device(dg_partition& pt) {
   }
   const size_t nb = std::max<size_t>(3 * static_cast<size_t>(pt.n_entries), 1) * sizeof(T);
   const size_t eb = std::max<size_t>(static_cast<size_t>(pt.n_entries), 1) * sizeof(Entry);
-  cudaError_t err = cudaMalloc(&pt.d_base, base.size() * sizeof(void*));
-  if (err == cudaSuccess) err = cudaMalloc(&pt.d_fs, P * sizeof(int64_t));
-  if (err == cudaSuccess) err = cudaMalloc(&pt.d_pack, eb);
-  if (err == cudaSuccess) err = cudaMalloc(&pt.d_unpack, eb);
-  if (err == cudaSuccess) err = cudaMalloc(&pt.d_send, nb);
-  if (err == cudaSuccess) err = cudaMalloc(&pt.d_recv, nb);
+  cudaError_t err = dgw::dev_malloc(&pt.d_base, base.size() * sizeof(void*));
+  if (err == cudaSuccess) err = dgw::dev_malloc(&pt.d_fs, P * sizeof(int64_t));
+  if (err == cudaSuccess) err = dgw::dev_malloc(&pt.d_pack, eb);
+  if (err == cudaSuccess) err = dgw::dev_malloc(&pt.d_unpack, eb);
+  if (err == cudaSuccess) err = dgw::dev_malloc(&pt.d_send, nb);
+  if (err == cudaSuccess) err = dgw::dev_malloc(&pt.d_recv, nb);
   if (err == cudaSuccess)
     err = cudaMemcpy(pt.d_base, base.data(), base.size() * sizeof(void*), cudaMemcpyHostToDevice);
   if (err == cudaSuccess)
