@@ -59,10 +59,7 @@
 
 namespace dgw {
 
-// ONE_TILE: one 128-row tile at every order (the batched launch, whose
-// seven inlined order bodies share one register budget; two-tile bodies
-// there measured slower through spills).
-template <int N, int PREC_, bool MEDIA_ = false, bool ONE_TILE = false>
+template <int N, int PREC_, bool MEDIA_ = false>
 struct TcLayout {
   static constexpr int PREC = PREC_;
   static constexpr bool MEDIA = MEDIA_;
@@ -83,7 +80,7 @@ struct TcLayout {
   // 80 elements shares the per-block hand-offs (measured: N = 3 0.86 ->
   // 0.65 ms/step, N = 2 1.31 -> 0.83; N = 4, which also fits, 0.65 -> 0.68)
   static constexpr int TILES =
-      (!ONE_TILE && N <= 3 &&
+      (N <= 3 &&
        2 * 2 * (tc_nsplit(PREC) == 2 ? 2 * NN : NN) + 2 * 2 * tc_nsplit(PREC) * XPART <= 512)
           ? 2
           : 1;
@@ -327,7 +324,7 @@ __device__ __forceinline__ void build_x_lift(const float* fr, uint32_t xh, uint3
 template <int N, int MODE, int PREC, bool MEDIA, bool TABLE>
 __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const int first,
                                               const int G, unsigned char* smem) {
-  using L = TcLayout<N, PREC, MEDIA, TABLE>;
+  using L = TcLayout<N, PREC, MEDIA>;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
   constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FES = L::FES, XBUF = L::XBUF;
   constexpr int FT = L::FLUX_THREADS, TASKS = L::TASKS, TPT = L::TPT;
@@ -992,6 +989,16 @@ cudaError_t launch_stage_tc_media(const StageArgs<float>& args, int mode, int nu
 // present order needs.
 constexpr int kTcThreads = TcLayout<5, kTcTf32x3, true>::THREADS;
 
+// one order's share of a batched launch, compiled as a function of its own:
+// its registers are allocated for that order alone, so the two-tile bodies
+// at N <= 3 fit as in the single-operator kernel (inlined into one kernel,
+// the seven bodies spilled, and the launch kept one tile at every order)
+template <int N, int MODE>
+__device__ __noinline__ void batch_order_body(const StageArgs<float>& g, int first, int G,
+                                              unsigned char* smem) {
+  tc_stage_body<N, MODE, kTcTf32x3, true, true>(g, first, G, smem);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1)
     dg_batch_tc_kernel(const __grid_constant__ BatchArgs p) {
@@ -1005,9 +1012,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const unsigned long long t_start = p.cta_clock ? global_ns() : 0ull;
 #define DG_BATCH_GROUP(NN_)                                                              \
   if (b >= c0[NN_ - 1] && b < c0[NN_]) {                                                 \
-    static_assert(TcLayout<NN_, kTcTf32x3, true, true>::THREADS == kTcThreads, "block size"); \
-    tc_stage_body<NN_, MODE, kTcTf32x3, true, true>(p.g[NN_ - 1], b - c0[NN_ - 1],        \
-                                                    c0[NN_] - c0[NN_ - 1], smem);        \
+    static_assert(TcLayout<NN_, kTcTf32x3, true>::THREADS == kTcThreads, "block size");   \
+    batch_order_body<NN_, MODE>(p.g[NN_ - 1], b - c0[NN_ - 1], c0[NN_] - c0[NN_ - 1], smem); \
     if (p.cta_clock && threadIdx.x == 0) {                                               \
       p.cta_clock[2 * b] = t_start;                                                      \
       p.cta_clock[2 * b + 1] = global_ns();                                              \
