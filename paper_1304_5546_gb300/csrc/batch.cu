@@ -151,12 +151,13 @@ bool plan_ctas(const int64_t* nblk, const double* cost, int num_ctas, int* cta) 
 }
 
 // cost of one block iteration per CTA before dg_batch_tune measures it:
-// seconds, rounded from dg_batch_tune on a GB300 (152 CTAs, a batch of all
-// seven orders with 1400 to 7000 blocks of 40 elements each, costs observed
-// in the mixed launch).  The bytes a block moves predict these badly: a block
-// has a fixed cost in hand-offs and instruction issue.
+// seconds, the medians of four dg_batch_tune runs on a GB300 (152 CTAs, a
+// batch of all seven orders with about 3000 blocks each, of 80 elements at
+// N <= 3 and 40 above; costs observed in the mixed launch).  The bytes a
+// block moves predict these badly: a block has a fixed cost in hand-offs
+// and instruction issue.
 double model_cost(int N) {
-  static const double us[8] = {0.0, 1.16, 1.30, 1.36, 1.41, 2.64, 3.06, 4.38};
+  static const double us[8] = {0.0, 1.55, 1.98, 2.22, 2.18, 2.68, 2.92, 2.93};
   return 1e-6 * us[N];
 }
 
