@@ -323,7 +323,9 @@ int64_t dg_step_host_jobs_work_bytes(const dg_op* op);
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with the operator's device current), which may load
  * the library's device code.  Make that first call before any stream
- * capture.  Every call with any operator on one device shares the one array:
+ * capture.  The address is kept per device and per context: after the
+ * device's context is destroyed and created again (cudaDeviceReset), the
+ * next call looks it up afresh, so make that call before any capture too.  Every call with any operator on one device shares the one array:
  * calls that overlap on the GPU (other streams, or other threads' calls not
  * ordered by the caller) race and give wrong results.
  * Errors: those of dg_step; DG_ERR_ARG for fields larger than the array;

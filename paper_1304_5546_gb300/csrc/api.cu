@@ -1,5 +1,6 @@
 // C ABI of the nodal DG wave solver: operator set-up and upload, and the
 // hot-path entry points dg_rhs / dg_step / dg_solve / dg_step_host.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1022,19 +1023,60 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
+// per device: the context the address was looked up in (its process-unique
+// id, 0 = none yet) and g_step_scratch's device address in that context
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_step_scratch on `device`, looked up once per device
-// with that device current (the caller made it current).
+// Driver calls reached through the runtime's entry-point table, so that the
+// library links no driver library (types from cuda.h, plain function
+// pointers).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Process-unique id of the calling thread's current context.  A context that
+// is destroyed and created again (cudaDeviceReset, then any CUDA call) gets a
+// new id, and loads the library's device code afresh, possibly at another
+// address.  Called with g_scratch_mutex held.
+dg_status current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    cudaError_t err = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                       cudaEnableDefault, &q1);
+    if (err == cudaSuccess)
+      err = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (err != cudaSuccess) return cuda_fail(err, "dg_step_static: driver entry points");
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return fail(DG_ERR_CUDA, "dg_step_static: cuCtxGetCurrent / cuCtxGetId not available");
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, id) != CUDA_SUCCESS || *id == 0)
+    return fail(DG_ERR_CUDA, "dg_step_static: no current CUDA context");
+  return DG_OK;
+}
+
+// Device address of g_step_scratch on `device` (the caller made it
+// current), looked up with cudaGetSymbolAddress once per device and context:
+// again after the context was destroyed and re-created.
 dg_status static_scratch(int device, void** out) {
   if (device < 0 || device >= kMaxDevices)
     return fail(DG_ERR_CUDA, "dg_step_static: device %d out of range", device);
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[device]) {
+  unsigned long long ctx = 0;
+  dg_status st = current_context_id(&ctx);
+  if (st) return st;
+  if (!g_scratch_addr[device] || g_scratch_ctx[device] != ctx) {
     void* p = nullptr;
     cudaError_t err = cudaGetSymbolAddress(&p, g_step_scratch);
     if (err != cudaSuccess) return cuda_fail(err, "dg_step_static: cudaGetSymbolAddress");
     g_scratch_addr[device] = p;
+    g_scratch_ctx[device] = ctx;
   }
   *out = g_scratch_addr[device];
   return DG_OK;

@@ -166,24 +166,38 @@ def test_permutation_invariance():
 
 
 def test_cavity_mode_config_one():
-    # [-1,1]^2, 8x8 squares x 2, N = 4, T = 1, CFL dt: recorded oracle error
-    # 1.53e-4 (max nodal); pin it against the exact PEC eigenmode.
-    VX, VY, EToV = square_grid_mesh(8, 8)
-    d = O.Discretization(VX, VY, EToV, 4)
-    q0 = np.stack(cavity_mode(d.x, d.y, 0.0))
-    qT, t = O.solve(d, q0, 1.0, O.cfl_dt(d))
-    assert abs(t - 1.0) < 1e-12
-    err = np.abs(qT - np.stack(cavity_mode(d.x, d.y, t))).max()
-    assert err < 2.0e-4
+    # [-1,1]^2, 8x8 squares x 2, N = 4, T = 1, CFL dt: the oracle's max nodal
+    # error against the exact PEC eigenmode is 1.53e-4.  That figure is
+    # backed by convergence, not by itself: refining to 16x16 (same T, CFL
+    # dt) must cut the error by at least 2^(N + 0.5) in the max and the L2
+    # norm, as the method's rate N + 1 predicts; so the 8x8 error is the
+    # discretisation error of a correct scheme and the bound below follows
+    # from the 16x16 error times 2^(N + 1).
+    N = 4
+    ref = O.ReferenceElement(N)
+    errs = {}
+    for n in (8, 16):
+        VX, VY, EToV = square_grid_mesh(n, n)
+        d = O.Discretization(VX, VY, EToV, N, ref=ref)
+        q0 = np.stack(cavity_mode(d.x, d.y, 0.0))
+        qT, t = O.solve(d, q0, 1.0, O.cfl_dt(d))
+        assert abs(t - 1.0) < 1e-12
+        e = qT - np.stack(cavity_mode(d.x, d.y, t))
+        errs[n] = (np.abs(e).max(), np.sqrt(2 * O.energy(d, e)))
+    for i in range(2):
+        assert errs[8][i] / errs[16][i] >= 2.0 ** (N + 0.5), errs
+    assert errs[8][0] < 1.3 * 2.0 ** (N + 1) * errs[16][0]
+    assert errs[8][0] < 2.0e-4
 
 
 def test_h_convergence_rate():
-    # L2 error of the cavity mode at T = 0.25 on 4x4, 8x8, 16x16 grids:
-    # rate ~ N + 1 (accept >= N + 0.5)
-    for N in (1, 2, 3, 4):
+    # L2 error of the cavity mode at T = 0.25 (dt = CFL / 2, small enough that
+    # the fourth-order time error stays below the spatial one) on 4x4 ... 32x32
+    # grids: rate ~ N + 1; the last two refinements must reach N + 0.5
+    for N in (1, 2, 3, 4, 5):
         ref = O.ReferenceElement(N)
         errs = []
-        for n in (4, 8, 16):
+        for n in (4, 8, 16, 32):
             VX, VY, EToV = square_grid_mesh(n, n)
             d = O.Discretization(VX, VY, EToV, N, ref=ref)
             q0 = np.stack(cavity_mode(d.x, d.y, 0.0))
@@ -191,7 +205,7 @@ def test_h_convergence_rate():
             e = qT - np.stack(cavity_mode(d.x, d.y, t))
             errs.append(np.sqrt(2 * O.energy(d, e)))
         rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
-        assert rates[-1] >= N + 0.5, (N, errs, rates)
+        assert rates[-1] >= N + 0.5 and rates[-2] >= N + 0.5, (N, errs, rates)
 
 
 def test_energy_does_not_increase_under_lsrk():
