@@ -484,10 +484,13 @@ def run_precision_study(args):
 
 def run_sweep_study(args):
     """Order sweep of the single-mesh path at about 10M nodal values per
-    field (K ~ 1e7 / Np): for N = 1..7, the FP32 tensor-core kernel and the
-    FP32 CUDA-core kernel, `--study-steps` LSRK steps each timed with CUDA
-    events.  One JSON line: ms/step, element-stage updates/s, RHS GFLOP/s
-    and achieved HBM bandwidth (algorithmic bytes) per order and kernel."""
+    field (K ~ 1e7 / Np): for N = 1..7, the FP32 tensor-core kernel (face
+    pairs off and on: dg_operator_set_face_pairs) and the FP32 CUDA-core
+    kernel, `--study-steps` LSRK steps each timed with CUDA events (the two
+    tensor-core settings alternate three times on one operator; medians).
+    One JSON line: ms/step, element-stage updates/s, RHS GFLOP/s and
+    achieved HBM bandwidth (algorithmic bytes) per order and kernel, and the
+    share of interior faces whose two elements lie in one tensor-core block."""
     import numpy as np
     import torch
 
@@ -498,6 +501,26 @@ def run_sweep_study(args):
     peaks, peak_kind = measured_peaks()
     steps = args.study_steps
     rows = []
+
+    def timed(s, q, res, dt):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        s.step(q, res, dt, steps)
+        b.record()
+        b.synchronize()
+        P.dg_sync_check(s.op)
+        return a.elapsed_time(b) / steps
+
+    def row(N, K, kernel, ms, **extra):
+        gbs = K * step_bytes_per_element(N) / (ms / 1e3) / 1e9
+        r = {"N": N, "K": K, "kernel": kernel, "ms_per_step": ms,
+             "element_stage_per_s": K * 5 / (ms / 1e3),
+             "rhs_gflops": K * rhs_flops_per_element(N) * 5 / (ms / 1e3) / 1e9,
+             "hbm_gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"]}
+        r.update(extra)
+        return r
+
     for N in args.sweep_orders:
         Np = (N + 1) * (N + 2) // 2
         n = n_for_target_elements(1e7 / Np)
@@ -510,20 +533,23 @@ def run_sweep_study(args):
             dt = s.cfl_dt()
             s.step(q, res, dt, 3)
             torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            s.step(q, res, dt, steps)
-            b.record()
-            b.synchronize()
-            P.dg_sync_check(s.op)
-            ms = a.elapsed_time(b) / steps
-            K = s.K
-            gbs = K * step_bytes_per_element(N) / (ms / 1e3) / 1e9
-            rows.append({"N": N, "K": K, "kernel": "cuda cores" if simt else "tensor cores (3xTF32)",
-                         "ms_per_step": ms, "element_stage_per_s": K * 5 / (ms / 1e3),
-                         "rhs_gflops": K * rhs_flops_per_element(N) * 5 / (ms / 1e3) / 1e9,
-                         "hbm_gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"]})
+            if simt:
+                rows.append(row(N, s.K, "cuda cores", timed(s, q, res, dt)))
+            else:
+                times = {0: [], 1: []}
+                for _ in range(3):
+                    for pairs in (0, 1):
+                        P.dg_operator_set_face_pairs(s.op, pairs)
+                        times[pairs].append(timed(s, q, res, dt))
+                E = 80 if N <= 3 else 40
+                EToE = P.dg_mesh_connectivity(s.mesh)[0]
+                k = np.arange(s.K)[:, None]
+                interior = EToE != k
+                same = interior & (EToE // E == k // E)
+                share = float(same.sum() / max(interior.sum(), 1))
+                rows.append(row(N, s.K, "tensor cores (3xTF32)", float(np.median(times[0]))))
+                rows.append(row(N, s.K, "tensor cores (3xTF32), face pairs",
+                                float(np.median(times[1])), faces_in_block=share))
             s.close()
     return {"study": "order sweep", "nodal_values_per_field": "~1e7", "steps": steps,
             "peak_hbm_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind,

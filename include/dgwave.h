@@ -185,6 +185,24 @@ dg_status dg_operator_setup_media(const dg_mesh* mesh, int32_t N, const double* 
  * [0, 1], a media operator).  Calls already enqueued keep their alpha.    */
 dg_status dg_operator_set_alpha(dg_op* op, double alpha);
 
+/* dg_operator_set_face_pairs: with enable = 1, later calls on the operator
+ * compute the numerical flux of a face whose two elements lie in the same
+ * element block of the tensor-core stage kernel once, for both sides, with
+ * the neighbour's traces read from the block's shared-memory copy instead
+ * of being gathered again (Section "Further Tuning Opportunities": each
+ * face pair is otherwise fetched twice, once by each side).  Faces across
+ * blocks and PEC faces are computed per side as before.  Each side keeps
+ * its own normal and Fscale, and every flux operation is explicitly
+ * rounded, so an element's result does not depend on which task computed
+ * its faces (partitions, whose blocks differ, agree bit for bit); it
+ * differs from enable = 0 by rounding only (the default kernel lets the
+ * compiler contract multiply-adds).  It applies to the default 3xTF32
+ * products; the other product variants, operators on the CUDA-core kernel
+ * (FP64, DG_SETUP_SIMT, FP32 at N = 1 by default) and batches ignore it.
+ * Measured slower than the default on GB300 at every order, so off by
+ * default.  Errors: DG_ERR_ARG (NULL, enable not 0 or 1).                  */
+dg_status dg_operator_set_face_pairs(dg_op* op, int32_t enable);
+
 /* Np, Nfp = N+1, K and field_stride (see conventions).  NULL outputs are
  * skipped.                                                                 */
 dg_status dg_get_info(const dg_op* op, int32_t* Np, int32_t* Nfp, int64_t* K,

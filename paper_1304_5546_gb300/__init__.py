@@ -23,7 +23,8 @@ from ._lib import (  # noqa: F401
 
 __all__ = [
     "dg_mesh_create", "dg_mesh_info", "dg_mesh_connectivity", "dg_mesh_destroy",
-    "dg_operator_setup", "dg_operator_setup_media", "dg_operator_set_alpha", "dg_operator_tune",
+    "dg_operator_setup", "dg_operator_setup_media", "dg_operator_set_alpha",
+    "dg_operator_set_face_pairs", "dg_operator_tune",
     "dg_get_info", "dg_get_nodes", "dg_get_reference",
     "dg_get_geometry", "dg_get_maps", "dg_cfl_dt", "dg_lsrk_coefficients",
     "dg_op_destroy", "dg_rhs", "dg_step", "dg_step_static", "dg_solve", "dg_step_host",
@@ -113,6 +114,11 @@ def dg_operator_setup_media(mesh, N, eps, precision=DG_FP32, flags=0):
 
 def dg_operator_set_alpha(op, alpha):
     _lib.check(_lib.load().dg_operator_set_alpha(op, alpha), "dg_operator_set_alpha")
+
+
+def dg_operator_set_face_pairs(op, enable):
+    _lib.check(_lib.load().dg_operator_set_face_pairs(op, int(bool(enable))),
+               "dg_operator_set_face_pairs")
 
 
 def dg_operator_tune(op, reps=5, stream=None):

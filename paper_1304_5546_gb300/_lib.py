@@ -76,6 +76,7 @@ SIGNATURES = [
     ("dg_operator_setup", c_i32, [c_void_p, c_i32, c_i32, c_i32, P(c_void_p)]),
     ("dg_operator_setup_media", c_i32, [c_void_p, c_i32, c_void_p, c_i32, c_i32, P(c_void_p)]),
     ("dg_operator_set_alpha", c_i32, [c_void_p, c_dbl]),
+    ("dg_operator_set_face_pairs", c_i32, [c_void_p, c_i32]),
     ("dg_operator_tune", c_i32, [c_void_p, c_i32, c_void_p, P(c_dbl), P(c_dbl)]),
     ("dg_get_info", c_i32, [c_void_p, P(c_i32), P(c_i32), P(c_i64), P(c_i64)]),
     ("dg_get_nodes", c_i32, [c_void_p, c_void_p, c_void_p]),

@@ -323,6 +323,7 @@ dgw::StageArgs<T> base_args(const dg_op* op) {
   a.status = op->d_status;
   a.tc_op = op->d_tcop;
   a.alpha = static_cast<T>(op->alpha);
+  a.face_pairs = op->face_pairs;
   return a;
 }
 
@@ -532,6 +533,15 @@ extern "C" dg_status dg_operator_set_alpha(dg_op* op, double alpha) {
                 "dg_operator_set_alpha: operators with a per-element permittivity use the upwind "
                 "flux of the interface Riemann solution only");
   op->alpha = alpha;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_operator_set_face_pairs(dg_op* op, int32_t enable) {
+  dgw::clear_error();
+  if (!op) return fail(DG_ERR_ARG, "dg_operator_set_face_pairs: NULL operator");
+  if (enable != 0 && enable != 1)
+    return fail(DG_ERR_ARG, "dg_operator_set_face_pairs: enable = %d is not 0 or 1", enable);
+  op->face_pairs = enable;
   return DG_OK;
 }
 

@@ -108,6 +108,7 @@ struct dg_op {
   double min_inradius_over_c = 0.0;
   // flux parameter of Eq. max2d-numflux: 1 upwind (default), 0 central
   double alpha = 1.0;
+  int face_pairs = 0;  // dg_operator_set_face_pairs
   bool has_device = false;
   int device = 0;
   int num_sms = 0;

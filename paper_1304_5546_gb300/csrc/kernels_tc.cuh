@@ -317,11 +317,40 @@ __device__ __forceinline__ void build_x_lift(const float* fr, uint32_t xh, uint3
   }
 }
 
+// Upwind flux of Eq. max2d-numflux with parameter alpha at one face node,
+// times Fscale/2 (fsc), for the jumps dH = q- - q+ (at a PEC face dH = 0,
+// dEz = 2 Ez-).  Every operation is explicitly rounded: the two sides of a
+// face computed in one task (face pairs) then round exactly as when each
+// side's own task computes it.
+__device__ __forceinline__ void upwind_flux(float nx, float ny, float fsc, float alpha, float dHx,
+                                            float dHy, float dEz, float& fx, float& fy,
+                                            float& fz) {
+  const float fa = __fmul_rn(fsc, alpha);
+  const float ndotdH = __fmaf_rn(nx, dHx, __fmul_rn(ny, dHy));
+  fx = __fmaf_rn(fa, __fmaf_rn(ndotdH, nx, -dHx), __fmul_rn(__fmul_rn(fsc, ny), dEz));
+  fy = __fmaf_rn(fa, __fmaf_rn(ndotdH, ny, -dHy), -__fmul_rn(__fmul_rn(fsc, nx), dEz));
+  fz = __fmaf_rn(-fa, dEz, __fmul_rn(fsc, __fmaf_rn(ny, dHx, -__fmul_rn(nx, dHy))));
+}
+// The same for a per-element permittivity: the exact interface Riemann
+// solution fz = cH [Ht] - cE [Ez], lifted as (-Z- ny fz, Z- nx fz, fz).
+__device__ __forceinline__ void media_flux(float nx, float ny, float cH, float cE, float zM,
+                                           float dHx, float dHy, float dEz, float& fx, float& fy,
+                                           float& fz) {
+  const float f = __fmaf_rn(cH, __fmaf_rn(ny, dHx, -__fmul_rn(nx, dHy)), -__fmul_rn(cE, dEz));
+  fx = -__fmul_rn(__fmul_rn(zM, ny), f);
+  fy = __fmul_rn(__fmul_rn(zM, nx), f);
+  fz = f;
+}
+
 // One CTA's share of a stage launch: the blocks first, first + G, ... of
 // the launch (TABLE: from the block table p.blocks; else contiguous blocks of
 // E elements over [0, K)).  smem: the CTA's dynamic shared memory (1024-byte
-// aligned, L::SMEM_BYTES).
-template <int N, int MODE, int PREC, bool MEDIA, bool TABLE>
+// aligned, L::SMEM_BYTES).  PAIRS: face pairs (a face whose two elements are
+// both in the block is done once, by the lower-numbered element's task, for
+// both sides, with every flux operation explicitly rounded so that an
+// element's result does not depend on whether its neighbour shares its
+// block); otherwise each side's task computes its own face nodes.
+template <int N, int MODE, int PREC, bool MEDIA, bool TABLE, bool PAIRS = false>
 __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const int first,
                                               const int G, unsigned char* smem) {
   using L = TcLayout<N, PREC, MEDIA>;
@@ -598,7 +627,9 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
             continue;
           }
 #endif
-          if (code >= 0) {
+          // face pairs: a neighbour inside the block is read from the stage
+          if (code >= 0 && !(PAIRS && static_cast<unsigned>((code >> 3) - k0) <
+                                           static_cast<unsigned>(nv))) {
             const int gP = (code >> 3) * Np + nbr[(code & 7) * Nfp + task_jj[u]];
             trc[u][0] = __ldg(qin[0] + gP);
             trc[u][1] = __ldg(qin[1] + gP);
@@ -628,39 +659,108 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
       const int32_t* sc = reinterpret_cast<const int32_t*>(st + 6 * L::QB + L::GB);
       float* Fb = Fs + (j & 1) * (L::FB / 4);
       // ---- upwind flux at every face node -> Fb[c][e][j], scaled by Fscale/2
-#pragma unroll
-      for (int u = 0; u < TPT; ++u) {
-        const int ee = task_e[u];
-        if (ee < nvalid) {
-          const int nM = task_nm[u];
-          const float hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
-          float dHx, dHy, dEz;
-          if (sc[task_cf[u]] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
-            dHx = 0.f;
-            dHy = 0.f;
-            dEz = 2.f * ezM;
-          } else {
-            dHx = hxM - trc[u][0];
-            dHy = hyM - trc[u][1];
-            dEz = ezM - trc[u][2];
-          }
-          const float* gf = sg + task_gf[u];
-          float* fo = Fb + task_fo[u];
-          if constexpr (MEDIA) {
-            // exact interface Riemann solution: fz = cH [Ht] - cE [Ez]
-            const float nx = gf[0], ny = gf[1], cH = gf[2], cE = gf[3];
-            const float zM = sg[ee * GEO + 16];
-            const float fz = cH * (ny * dHx - nx * dHy) - cE * dEz;
-            fo[0] = -zM * ny * fz;
-            fo[E * FES] = zM * nx * fz;
+      if constexpr (PAIRS) {
+  #pragma unroll
+        for (int u = 0; u < TPT; ++u) {
+          const int ee = task_e[u];
+          if (ee < nvalid) {
+            const int nM = task_nm[u];
+            const int32_t code = sc[task_cf[u]];
+            // face pairs: a face whose neighbour eP lies in this block is done
+            // once, by the task of the lower-numbered element, for both sides
+            // (each side with its own geometry and its own flux slot)
+            const int eP = code >= 0 ? (code >> 3) - k0 : -1;
+            bool pair = eP >= 0 && eP < nvalid && eP != ee;
+  #ifdef DGW_DEVICE_CHECKS
+            pair = pair && nbr_code_ok(code, fs, Np);  // the gather flagged a bad code
+  #endif
+            if (pair && eP < ee) continue;  // the neighbour's task writes this slot
+            const float hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
+            float hxP, hyP, ezP;
+            if (pair) {
+              const int nP = eP * Np + nbr[(code & 7) * Nfp + task_jj[u]];
+              hxP = sq[nP];
+              hyP = sq[E * Np + nP];
+              ezP = sq[2 * E * Np + nP];
+            } else {
+              hxP = trc[u][0];
+              hyP = trc[u][1];
+              ezP = trc[u][2];
+            }
+            float dHx, dHy, dEz;
+            if (code < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
+              dHx = 0.f;
+              dHy = 0.f;
+              dEz = 2.f * ezM;
+            } else {
+              dHx = hxM - hxP;
+              dHy = hyM - hyP;
+              dEz = ezM - ezP;
+            }
+            const float* gf = sg + task_gf[u];
+            float* fo = Fb + task_fo[u];
+            float fx, fy, fz;
+            if constexpr (MEDIA) {
+              media_flux(gf[0], gf[1], gf[2], gf[3], sg[ee * GEO + 16], dHx, dHy, dEz, fx, fy, fz);
+            } else {
+              upwind_flux(gf[0], gf[1], gf[2], p.alpha, dHx, dHy, dEz, fx, fy, fz);
+            }
+            fo[0] = fx;
+            fo[E * FES] = fy;
             fo[2 * E * FES] = fz;
-          } else {
-            // Eq. max2d-numflux with parameter alpha (1: upwind, 0: central)
-            const float nx = gf[0], ny = gf[1], fsc = gf[2], fa = fsc * p.alpha;
-            const float ndotdH = nx * dHx + ny * dHy;
-            fo[0] = fsc * ny * dEz + fa * (ndotdH * nx - dHx);
-            fo[E * FES] = -fsc * nx * dEz + fa * (ndotdH * ny - dHy);
-            fo[2 * E * FES] = fsc * (ny * dHx - nx * dHy) - fa * dEz;
+            if (pair) {  // the neighbour's side: its jumps are the negated ones
+              const int fP = (code >> 1) & 3;
+              const int jjP = (code & 1) ? N - task_jj[u] : task_jj[u];
+              const float* gP = sg + eP * GEO + 4 + (MEDIA ? 4 : 3) * fP;
+              float* foP = Fb + eP * FES + fP * Nfp + jjP;
+              if constexpr (MEDIA) {
+                media_flux(gP[0], gP[1], gP[2], gP[3], sg[eP * GEO + 16], hxP - hxM, hyP - hyM,
+                           ezP - ezM, fx, fy, fz);
+              } else {
+                upwind_flux(gP[0], gP[1], gP[2], p.alpha, hxP - hxM, hyP - hyM, ezP - ezM, fx, fy,
+                            fz);
+              }
+              foP[0] = fx;
+              foP[E * FES] = fy;
+              foP[2 * E * FES] = fz;
+            }
+          }
+        }
+      } else {
+  #pragma unroll
+        for (int u = 0; u < TPT; ++u) {
+          const int ee = task_e[u];
+          if (ee < nvalid) {
+            const int nM = task_nm[u];
+            const float hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
+            float dHx, dHy, dEz;
+            if (sc[task_cf[u]] < 0) {  // PEC wall: Ez+ = -Ez-, H+ = H-
+              dHx = 0.f;
+              dHy = 0.f;
+              dEz = 2.f * ezM;
+            } else {
+              dHx = hxM - trc[u][0];
+              dHy = hyM - trc[u][1];
+              dEz = ezM - trc[u][2];
+            }
+            const float* gf = sg + task_gf[u];
+            float* fo = Fb + task_fo[u];
+            if constexpr (MEDIA) {
+              // exact interface Riemann solution: fz = cH [Ht] - cE [Ez]
+              const float nx = gf[0], ny = gf[1], cH = gf[2], cE = gf[3];
+              const float zM = sg[ee * GEO + 16];
+              const float fz = cH * (ny * dHx - nx * dHy) - cE * dEz;
+              fo[0] = -zM * ny * fz;
+              fo[E * FES] = zM * nx * fz;
+              fo[2 * E * FES] = fz;
+            } else {
+              // Eq. max2d-numflux with parameter alpha (1: upwind, 0: central)
+              const float nx = gf[0], ny = gf[1], fsc = gf[2], fa = fsc * p.alpha;
+              const float ndotdH = nx * dHx + ny * dHy;
+              fo[0] = fsc * ny * dEz + fa * (ndotdH * nx - dHx);
+              fo[E * FES] = -fsc * nx * dEz + fa * (ndotdH * ny - dHy);
+              fo[2 * E * FES] = fsc * (ny * dHx - nx * dHy) - fa * dEz;
+            }
           }
         }
       }
@@ -933,19 +1033,19 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
   if (warp == 0) tmem_dealloc(tmem, L::TMEM_COLS);
 }
 
-template <int N, int MODE, int PREC, bool MEDIA>
+template <int N, int MODE, int PREC, bool MEDIA, bool PAIRS>
 __global__ void __launch_bounds__(TcLayout<N, PREC, MEDIA>::THREADS, 1)
     dg_stage_tc_kernel(const __grid_constant__ StageArgs<float> p) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  tc_stage_body<N, MODE, PREC, MEDIA, false>(p, blockIdx.x, gridDim.x, smem);
+  tc_stage_body<N, MODE, PREC, MEDIA, false, PAIRS>(p, blockIdx.x, gridDim.x, smem);
 }
 
-template <int N, int MODE, int PREC, bool MEDIA>
+template <int N, int MODE, int PREC, bool MEDIA, bool PAIRS>
 cudaError_t launch_stage_tc_mode(const StageArgs<float>& args, int num_sms, cudaStream_t stream) {
   using L = TcLayout<N, PREC, MEDIA>;
   static std::atomic<uint64_t> configured{0};
   cudaError_t err = configure_once_per_device(configured, [] {
-    return cudaFuncSetAttribute(dg_stage_tc_kernel<N, MODE, PREC, MEDIA>,
+    return cudaFuncSetAttribute(dg_stage_tc_kernel<N, MODE, PREC, MEDIA, PAIRS>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(L::SMEM_BYTES));
   });
@@ -954,19 +1054,31 @@ cudaError_t launch_stage_tc_mode(const StageArgs<float>& args, int num_sms, cuda
   int64_t grid = num_sms;  // one CTA per SM (shared memory and TMEM sized for it)
   if (grid > nblk) grid = nblk;
   if (grid < 1) grid = 1;
-  dg_stage_tc_kernel<N, MODE, PREC, MEDIA>
+  dg_stage_tc_kernel<N, MODE, PREC, MEDIA, PAIRS>
       <<<static_cast<unsigned>(grid), L::THREADS, L::SMEM_BYTES, stream>>>(args);
   return cudaGetLastError();
 }
 
+template <int N, int PREC, bool MEDIA, bool PAIRS>
+cudaError_t launch_stage_tc_modes(const StageArgs<float>& args, int mode, int num_sms,
+                                  cudaStream_t stream) {
+  if (mode == kModeRhs)
+    return launch_stage_tc_mode<N, kModeRhs, PREC, MEDIA, PAIRS>(args, num_sms, stream);
+  if (mode == kModeFirstStage)
+    return launch_stage_tc_mode<N, kModeFirstStage, PREC, MEDIA, PAIRS>(args, num_sms, stream);
+  return launch_stage_tc_mode<N, kModeStage, PREC, MEDIA, PAIRS>(args, num_sms, stream);
+}
+
+// face pairs (args.face_pairs) exist for the 3xTF32 products, the FP32 path's
+// default; the other product variants compute every face node per side
 template <int N, int PREC, bool MEDIA>
 cudaError_t launch_stage_tc_any(const StageArgs<float>& args, int mode, int num_sms,
                                 cudaStream_t stream) {
-  if (mode == kModeRhs)
-    return launch_stage_tc_mode<N, kModeRhs, PREC, MEDIA>(args, num_sms, stream);
-  if (mode == kModeFirstStage)
-    return launch_stage_tc_mode<N, kModeFirstStage, PREC, MEDIA>(args, num_sms, stream);
-  return launch_stage_tc_mode<N, kModeStage, PREC, MEDIA>(args, num_sms, stream);
+  if constexpr (PREC == kTcTf32x3) {
+    if (args.face_pairs)
+      return launch_stage_tc_modes<N, PREC, MEDIA, true>(args, mode, num_sms, stream);
+  }
+  return launch_stage_tc_modes<N, PREC, MEDIA, false>(args, mode, num_sms, stream);
 }
 
 template <int N, int PREC>

@@ -87,6 +87,9 @@ struct StageArgs {
   const T* lam = nullptr;         // [2][Np]: (1 + r_n) / 2, (1 + s_n) / 2 per node
   T a = 0, b = 0, dt = 0;
   T alpha = 1;  // flux parameter of Eq. max2d-numflux (uniform medium only)
+  // tensor-core kernel: compute the flux of a face whose two elements lie in
+  // the same block once, for both sides (0: every face node per side)
+  int face_pairs = 0;
   int* status = nullptr;  // set to 1 by a CTA whose bounded wait expired
   // timeout test only (tensor-core kernel): the memory warp first waits,
   // bounded by kGateLimitNs, for *stall_gate to become non-zero; NULL

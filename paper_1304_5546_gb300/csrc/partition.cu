@@ -291,6 +291,7 @@ dg_status build_device(dg_partition& pt) {
     s->flags = op.flags;
     s->ref = op.ref;
     s->alpha = op.alpha;
+    s->face_pairs = op.face_pairs;
     s->use_tc = op.use_tc;
     s->tc_prec = op.tc_prec;
     s->elem_size = op.elem_size;

@@ -38,7 +38,7 @@ from synth import jittered_delaunay_mesh, random_fields, random_permittivity
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp32tc": 1e-5, "fp32simt": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp32tc": 1e-5, "fp32simt": 1e-5, "fp32pairs": 1e-5}
 U = {"tf32": 2.0 ** -11, "bf16": 2.0 ** -8, "bf16x3": 2.0 ** -16}
 
 
@@ -82,9 +82,13 @@ class _Case:
         return O.maxwell_rhs_media(self.d, u, self.eps)
 
     def solver(self, P, prec):
-        s = P.Solver(*self.mesh, N=self.N, precision=prec, eps=self.eps)
+        # "fp32pairs": the tensor-core kernel with face pairs on
+        pairs = prec == "fp32pairs"
+        s = P.Solver(*self.mesh, N=self.N, precision="fp32tc" if pairs else prec, eps=self.eps)
         if self.alpha != 1.0:
             P.dg_operator_set_alpha(s.op, self.alpha)
+        if pairs:
+            P.dg_operator_set_face_pairs(s.op, 1)
         return s
 
     def want(self, dt):
@@ -136,11 +140,13 @@ def test_mesh_sizes_walk_many_blocks_per_cta():
 
 
 # the CUDA-core kernel serves every FP32 order with "fp32simt", N = 1 by
-# default ("fp32"); "fp32tc" forces the tensor cores at every order; FP64
+# default ("fp32"); "fp32tc" forces the tensor cores at every order
+# ("fp32pairs": with face pairs, dg_operator_set_face_pairs); FP64
 # (CUDA cores) at N = 3, 5, 7.  Ordered by N so that one oracle case serves
 # all of an order's runs.
 _UNIFORM = [(N, prec) for N in range(1, 8)
-            for prec in ("fp32", "fp32tc", "fp32simt") + (("fp64",) if N in (3, 5, 7) else ())]
+            for prec in ("fp32", "fp32tc", "fp32pairs", "fp32simt")
+            + (("fp64",) if N in (3, 5, 7) else ())]
 
 
 @pytest.mark.parametrize("N,prec", _UNIFORM)
@@ -152,7 +158,7 @@ def test_large_uniform_rhs_and_two_steps(P, N, prec):
     assert _rel(got, want_q) <= TOL[prec], ("2 steps", _rel(got, want_q))
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp32simt", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp32pairs", "fp32simt", "fp64"])
 @pytest.mark.parametrize("N", [3, 7])
 def test_large_media_rhs_and_two_steps(P, N, prec):
     case = _case(("media", N), N, seed=600 + N, eps_seed=700 + N)
