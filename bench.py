@@ -397,6 +397,17 @@ def run_ours(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
+    if world == 1 and not args.no_workloads:
+        # the metric's other half: batched solves and served solves/s + p99
+        # (their own seeded workloads, timed after the main measurement)
+        s.close()
+        del q, res, hs, h, dq, dres
+        torch.cuda.empty_cache()
+        out["batched"] = run_batched(args)
+        sargs = argparse.Namespace(**vars(args))
+        sargs.serve_rates = [300.0]
+        sargs.serve_requests = 60
+        out["serving"] = run_serving(sargs)
     if dist is not None:
         dist.destroy_process_group()
     return out
@@ -699,6 +710,36 @@ def run_batched(args):
     seq_launches = sum(P.dg_launch_count(s.op) for s in solvers) - launches0
     seq_out = [s.to_numpy(q) for s, q in zip(solvers, qs)]
 
+    # ---- sequential plain solves replayed from CUDA graphs: each problem's
+    # `steps` steps captured once into a graph of its own (outside the timed
+    # region), the graphs replayed one after another: no launch overhead
+    graph = {"how": "dg_step per problem, its %d steps captured into one CUDA graph, "
+                    "graphs replayed one after another" % steps}
+    try:
+        qg = [s.from_numpy(q) for s, q in zip(solvers, q0s)]
+        rg = [s.new_fields() for s in solvers]
+        side = torch.cuda.Stream()
+        graphs = []
+        for s, q, r, dt in zip(solvers, qg, rg, dts):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=side):
+                s.step(q, r, dt, steps)  # recorded, not run
+            graphs.append(g)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        for g in graphs:
+            g.replay()
+        b.record(stream)
+        b.synchronize()
+        graph_ms = a.elapsed_time(b)
+        same = all(np.array_equal(s.to_numpy(q), ref) for s, q, ref in zip(solvers, qg, seq_out))
+        graph.update({"value": len(solvers) / (graph_ms / 1e3), "unit": "solves/s",
+                      "ms": graph_ms, "bit_equal_to_sequential": bool(same)})
+        del graphs, qg, rg
+    except Exception as e:  # capture refused: report it, keep the rest of the line
+        graph["unavailable"] = repr(e)[:200]
+
     # ---- batched
     cap = [0] * 7
     for K, N in zip(Ks, Ns):
@@ -756,6 +797,8 @@ def run_batched(args):
                        "gpu_launches": seq_launches,
                        "how": "dg_step per problem, one problem after another, one stream"},
         "speedup_vs_sequential": seq_ms / bat_ms,
+        "sequential_graphs": graph,
+        "speedup_vs_sequential_graphs": (graph["ms"] / bat_ms) if "ms" in graph else None,
         "max_rel_diff_vs_sequential": diff,
         "gpu_launches": bat_launches,
         "dtype": "f32",
@@ -810,6 +853,43 @@ def _percentile(v, q):
     return float(np.percentile(np.asarray(v), q)) if len(v) else None
 
 
+def serve_plain_sequential(P, reqs, dev_solvers, arrivals):
+    """Requests served one at a time, in arrival order, by plain dg_solve on
+    each request's own device operator (operator resident in HBM beforehand,
+    its point source attached with dg_operator_set_source, fields and
+    residual allocated beforehand): per request, zero the fields, solve to
+    T, copy the result into pinned host memory, wait for it.  Latency runs
+    from the arrival time to the result in host memory."""
+    import numpy as np
+    import torch
+
+    stream = torch.cuda.current_stream()
+    bufs = [(s.new_fields(), s.new_fields(), torch.empty((3, s.fstride), pin_memory=True))
+            for s in dev_solvers]
+    t_start = P.Server.clock() + 0.01
+    rec = []
+    launches0 = sum(P.dg_launch_count(s.op) for s in dev_solvers)
+    for i, (r, s) in enumerate(zip(reqs, dev_solvers)):
+        t_arr = t_start + arrivals[i]
+        while P.Server.clock() < t_arr:
+            pass
+        q, res, h = bufs[i]
+        q.zero_()
+        nsteps, _ = s.solve(q, res, r["T"])
+        h.copy_(q, non_blocking=True)
+        stream.synchronize()
+        rec.append((t_arr, P.Server.clock(), s.K, nsteps))
+    lat = [d - a for a, d, _, _ in rec]
+    span = rec[-1][1] - rec[0][0]
+    out = {"solves_per_s": len(rec) / span, "p50_ms": 1e3 * _percentile(lat, 50),
+           "p99_ms": 1e3 * _percentile(lat, 99), "mean_ms": 1e3 * float(np.mean(lat)),
+           "makespan_s": span, "failed": 0,
+           "gpu_launches": sum(P.dg_launch_count(s.op) for s in dev_solvers) - launches0,
+           "element_stage_updates_per_s": 5.0 * sum(K * n for _, _, K, n in rec) / span}
+    results = [s.to_numpy(b[0]) for s, b in zip(dev_solvers, bufs)]
+    return out, results
+
+
 def run_serving(args):
     """Serving workload: Poisson arrivals at each rate in --serve-rates of
     the same seeded requests, served by the continuous-batching server, by
@@ -837,6 +917,16 @@ def run_serving(args):
         Np = (N + 1) * (N + 2) // 2
         cap[N - 1] = int(budget / len(orders) / (36 * Np + 92))
     rng = np.random.default_rng(args.serve_seed + 1)
+    # plain sequential solves: device operators with the request's source
+    dev = []
+    if not args.serve_no_plain:
+        for r in reqs:
+            d = P.Solver(*r["mesh"], N=r["N"], precision="fp32")
+            P.dg_operator_set_source(d.op, r["source"])
+            dev.append(d)
+        warm = dev[0].new_fields()
+        dev[0].solve(warm, dev[0].new_fields(), reqs[0]["T"])  # warm the kernels
+        torch.cuda.synchronize()
     clocks = ClockSampler(None) if not args.no_clocks else None
     if clocks:
         clocks.start()
@@ -848,6 +938,7 @@ def run_serving(args):
     rows = []
     for lam in args.serve_rates:
         arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs)))
+        arrivals -= arrivals[0]
         row = {"rate_per_s": lam}
         modes = ([("batched", False, 0)]
                  + [("limited_%g" % w, False, int(w)) for w in args.serve_work_limits]
@@ -871,8 +962,21 @@ def run_serving(args):
                          "makespan_s": span, "failed": st["failed"], "gpu_launches": st["launches"],
                          "batched_steps": st["steps"],
                          "element_stage_updates_per_s": 5.0 * el_steps / span}
+        if dev:
+            row["plain_sequential"], plain_out = serve_plain_sequential(P, reqs, dev, arrivals)
+            # the served results against the plain solves of the same requests
+            row["max_rel_diff_served_vs_plain"] = max(
+                float(np.abs(o - p).max() / max(np.abs(p).max(), 1e-30))
+                for o, p in zip(outs, plain_out))
         row["speedup_solves_per_s"] = row["batched"]["solves_per_s"] / row["sequential"]["solves_per_s"]
         row["p99_ratio_seq_over_batched"] = row["sequential"]["p99_ms"] / row["batched"]["p99_ms"]
+        if dev:
+            base = row["plain_sequential"]
+            for mode, _, _ in modes:
+                row[mode]["vs_plain_sequential"] = {
+                    "solves_per_s": row[mode]["solves_per_s"] / base["solves_per_s"],
+                    "p50": row[mode]["p50_ms"] / base["p50_ms"],
+                    "p99": row[mode]["p99_ms"] / base["p99_ms"]}
         for mode, _, limit in modes:
             if limit:
                 row[mode]["speedup_solves_per_s"] = (row[mode]["solves_per_s"]
@@ -881,6 +985,8 @@ def run_serving(args):
                                                         / row[mode]["p99_ms"])
         rows.append(row)
     clk = clocks.stop() if clocks else None
+    for d in dev:
+        d.close()
     Ks = np.array([s.K for s in solvers])
     return {
         "workload": "serving",
@@ -899,7 +1005,10 @@ def run_serving(args):
                    "initial_fields": "zero", "memory_budget_gb": args.serve_budget_gb,
                    "capacity_elements": {str(N): cap[N - 1] for N in orders},
                    "latency": "submission to result in host memory",
-                   "sequential": "same server, one request admitted at a time"},
+                   "sequential": "same server, one request admitted at a time",
+                   "plain_sequential": "dg_solve per request in arrival order on its own "
+                                       "resident device operator (point source attached), "
+                                       "result copied to pinned host memory"},
         "clocks": clk,
     }
 
@@ -942,6 +1051,10 @@ def main(argv=None):
     ap.add_argument("--serve-budget-gb", type=float, default=4.0)
     ap.add_argument("--serve-work-limits", type=float, nargs="*", default=[3e6, 1e7],
                     help="work limits (nodal values per field stepped together) to serve with")
+    ap.add_argument("--serve-no-plain", action="store_true",
+                    help="leave out the plain sequential dg_solve baseline")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="main line only: without its batched and serving objects")
     args = ap.parse_args(argv)
     if args._oracle_sample:
         n, N, sec = int(args._oracle_sample[0]), int(args._oracle_sample[1]), float(args._oracle_sample[2])

@@ -63,6 +63,26 @@ typedef struct dg_op dg_op;
 typedef struct dg_batch dg_batch;
 typedef int32_t dg_status;
 
+/* A point source (dg_operator_set_source, dg_batch_add, dg_server_submit):
+ * the source term f of the problem statement (which the paper leaves
+ * unspecified), read as
+ *     dEz/dt += s(t) delta(x - (x, y)),
+ *     s(t) = amplitude (1 - 2 a^2) exp(-a^2),  a = pi f (t - t0)
+ * (a Ricker wavelet of peak frequency f).  For an operator, t is the time
+ * dg_step and dg_rhs are given (dg_solve starts at 0); in a batch or a
+ * server it is measured from the problem's first step.  The delta is
+ * projected onto the nodal basis of the element that contains the point
+ * (the lowest-numbered one, barycentric coordinates >= -1e-12):
+ * w = M^-1 l(x_s) / J_k, l the element's Lagrange basis at the point; the
+ * Ez right-hand side of that element gains s(t) w, after the division by
+ * eps.  Stage times are t_n + c_i dt.                                      */
+typedef struct dg_point_source {
+  double x, y;       /* location, inside the mesh                          */
+  double f;          /* peak frequency, > 0                                */
+  double t0;         /* time of the peak (1.2 / f is customary)            */
+  double amplitude;  /* peak value of s                                    */
+} dg_point_source;
+
 #define DG_OK 0
 #define DG_ERR_ARG 1                /* bad pointer, size or value            */
 #define DG_ERR_MESH_DEGENERATE 2    /* zero-area triangle                    */
@@ -203,6 +223,21 @@ dg_status dg_operator_set_alpha(dg_op* op, double alpha);
  * default.  Errors: DG_ERR_ARG (NULL, enable not 0 or 1).                  */
 dg_status dg_operator_set_face_pairs(dg_op* op, int32_t enable);
 
+/* dg_operator_set_source: attach a point source (dg_point_source, copied)
+ * to the operator, or remove it (src = NULL).  Later dg_rhs, dg_step,
+ * dg_solve, dg_step_host, dg_step_host_jobs and dg_step_static calls add
+ * s(t) w to the Ez right-hand side of the element that contains the point:
+ * after each stage launch one small kernel adds dt s(t) w to that element's
+ * residual and b_i dt s(t) w to its fields (t: the stage time t0 + (n + c_i)
+ * dt), which is the stage update with the source in the right-hand side.
+ * The projected load w is computed on the host in FP64 and uploaded once
+ * (an allocation of Np values, made here, not by the stepping calls).
+ * Batches and servers take their own sources and ignore this one;
+ * dg_partition_create refuses an operator with a source.
+ * Errors: DG_ERR_ARG (NULL operator, parameters not finite or f <= 0, the
+ * point outside the mesh), DG_ERR_CUDA, DG_ERR_OOM.                       */
+dg_status dg_operator_set_source(dg_op* op, const dg_point_source* src);
+
 /* Np, Nfp = N+1, K and field_stride (see conventions).  NULL outputs are
  * skipped.                                                                 */
 dg_status dg_get_info(const dg_op* op, int32_t* Np, int32_t* Nfp, int64_t* K,
@@ -261,8 +296,9 @@ void dg_op_destroy(dg_op* op);
  * apply with the factor Fscale/2.  d_q and d_rhs are device field buffers
  * of the operator's precision (3 * field_stride values each, 16-byte
  * aligned; the kernels read whole per-block chunks with bulk copies) and
- * must not overlap.  t is accepted for interface symmetry (the system is
- * autonomous).  Enqueued on `stream`.
+ * must not overlap.  t is the time of the evaluation: it only matters with
+ * a point source (dg_operator_set_source), whose s(t) w is added; without
+ * one the system is autonomous.  Enqueued on `stream`.
  * Errors: DG_ERR_ARG (NULL / overlapping / misaligned buffers),
  * DG_ERR_NO_DEVICE, DG_ERR_CUDA (launch failure).                          */
 dg_status dg_rhs(const dg_op* op, const void* d_q, void* d_rhs, double t, void* stream);
@@ -278,7 +314,8 @@ dg_status dg_rhs(const dg_op* op, const void* d_q, void* d_rhs, double t, void* 
  * result is copied back into d_q with one device-to-device copy.  Enqueued
  * on `stream`.  Calls on one operator must not overlap in time (they share
  * that buffer).
- * Errors: DG_ERR_ARG (NULL/overlapping buffers, nsteps < 0, dt not
+ * With a point source, stage i of step n is at time t0 + (n + c_i) dt.
+ * Errors: DG_ERR_ARG (NULL/overlapping buffers, nsteps < 0, dt or t0 not
  * finite), DG_ERR_NO_DEVICE, DG_ERR_CUDA.                                  */
 dg_status dg_step(const dg_op* op, void* d_q, void* d_res, double t0, double dt,
                   int32_t nsteps, void* stream);
@@ -375,7 +412,16 @@ dg_status dg_step_static(const dg_op* op, void* d_q, void* d_res, double t0, dou
                                kernels directly instead of replaying graphs */
 #define DG_BATCH_NO_ADAPT 2 /* dg_batch_create flag: keep the CTA split fixed
                                between joins and leaves (see dg_batch_step) */
+#define DG_BATCH_SPLIT 4    /* dg_batch_create flag: the split launch mode
+                               only (see below)                            */
 
+/* Launch modes.  Concurrent (the default): each order's share of a stage
+ * is a kernel of its own with one CTA per SM over that order's blocks; the
+ * orders' kernels run side by side on streams of the batch, joined once per
+ * step, and the hardware hands SMs to whichever order has CTAs waiting, so
+ * orders do not wait for each other at every stage.  Split (DG_BATCH_SPLIT,
+ * or when dg_batch_tune measures it faster): one launch per stage over all
+ * orders, its CTAs split among the orders by the planner.                  */
 /* dg_batch_create: capacity[N-1] = elements of order N the batch can hold
  * (N = 1..DG_N_MAX, 0 = none), on the current device.
  * Errors: DG_ERR_ARG (NULL, unknown flags, capacities all zero or one
@@ -386,22 +432,6 @@ dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_batch** out
 /* Waits for the device, then frees the batch and its device memory.      */
 void dg_batch_destroy(dg_batch* batch);
 
-/* A point source for dg_batch_add: the source term f of the problem
- * statement (which the paper leaves unspecified), read as
- *     dEz/dt += s(t) delta(x - (x, y)),
- *     s(t) = amplitude (1 - 2 a^2) exp(-a^2),  a = pi f (t - t0)
- * (a Ricker wavelet of peak frequency f), t measured from the problem's
- * first step.  The delta is projected onto the nodal basis of the element
- * that contains the point (the lowest-numbered one, barycentric coordinates
- * >= -1e-12): w = M^-1 l(x_s) / J_k, l the element's Lagrange basis at the
- * point; the Ez right-hand side of that element gains s(t) w, after the
- * division by eps.  Stage times are t_n + c_i dt.                           */
-typedef struct dg_point_source {
-  double x, y;       /* location, inside the mesh                          */
-  double f;          /* peak frequency, > 0                                */
-  double t0;         /* time of the peak (1.2 / f is customary)            */
-  double amplitude;  /* peak value of s                                    */
-} dg_point_source;
 
 /* dg_batch_add: admit the problem of operator `op` (DG_FP32; set up on any
  * device or host-only: the batch copies what it needs from the operator's

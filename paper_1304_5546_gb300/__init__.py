@@ -24,7 +24,7 @@ from ._lib import (  # noqa: F401
 __all__ = [
     "dg_mesh_create", "dg_mesh_info", "dg_mesh_connectivity", "dg_mesh_destroy",
     "dg_operator_setup", "dg_operator_setup_media", "dg_operator_set_alpha",
-    "dg_operator_set_face_pairs", "dg_operator_tune",
+    "dg_operator_set_face_pairs", "dg_operator_set_source", "dg_operator_tune",
     "dg_get_info", "dg_get_nodes", "dg_get_reference",
     "dg_get_geometry", "dg_get_maps", "dg_cfl_dt", "dg_lsrk_coefficients",
     "dg_op_destroy", "dg_rhs", "dg_step", "dg_step_static", "dg_solve", "dg_step_host",
@@ -119,6 +119,12 @@ def dg_operator_set_alpha(op, alpha):
 def dg_operator_set_face_pairs(op, enable):
     _lib.check(_lib.load().dg_operator_set_face_pairs(op, int(bool(enable))),
                "dg_operator_set_face_pairs")
+
+
+def dg_operator_set_source(op, source):
+    """source: None (remove) or (x, y, f, t0, amplitude) of a Ricker point source."""
+    src = None if source is None else ctypes.byref(_lib.dg_point_source(*[float(v) for v in source]))
+    _lib.check(_lib.load().dg_operator_set_source(op, src), "dg_operator_set_source")
 
 
 def dg_operator_tune(op, reps=5, stream=None):
@@ -654,10 +660,11 @@ class Batch:
 
     ``capacity``: dict order -> element capacity, or 7 counts.  ``add``
     admits a Solver's operator (FP32) with its time step; fields move in and
-    out as (3, K, Np) arrays.
+    out as (3, K, Np) arrays.  ``split``: the split launch mode only
+    (DG_BATCH_SPLIT); by default the orders' kernels run side by side.
     """
 
-    def __init__(self, capacity, graph=True, adapt=True, device=None):
+    def __init__(self, capacity, graph=True, adapt=True, device=None, split=False):
         import torch
         if device is not None:
             torch.cuda.set_device(device)
@@ -666,7 +673,8 @@ class Batch:
             for n, c in capacity.items():
                 cap[n - 1] = int(c)
             capacity = cap
-        flags = (0 if graph else _lib.DG_BATCH_NO_GRAPH) | (0 if adapt else _lib.DG_BATCH_NO_ADAPT)
+        flags = ((0 if graph else _lib.DG_BATCH_NO_GRAPH) | (0 if adapt else _lib.DG_BATCH_NO_ADAPT)
+                 | (_lib.DG_BATCH_SPLIT if split else 0))
         self.batch = dg_batch_create(capacity, flags)
 
     def close(self):

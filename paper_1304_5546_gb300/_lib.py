@@ -38,6 +38,7 @@ DG_SETUP_TC = 32
 DG_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 DG_BATCH_NO_GRAPH = 1
 DG_BATCH_NO_ADAPT = 2
+DG_BATCH_SPLIT = 4
 DG_SERVER_SEQUENTIAL = 1
 DG_REQUEST_QUEUED, DG_REQUEST_RUNNING, DG_REQUEST_DONE, DG_REQUEST_FAILED = 0, 1, 2, 3
 DG_REQUEST_CANCELLED = 4
@@ -77,6 +78,7 @@ SIGNATURES = [
     ("dg_operator_setup_media", c_i32, [c_void_p, c_i32, c_void_p, c_i32, c_i32, P(c_void_p)]),
     ("dg_operator_set_alpha", c_i32, [c_void_p, c_dbl]),
     ("dg_operator_set_face_pairs", c_i32, [c_void_p, c_i32]),
+    ("dg_operator_set_source", c_i32, [c_void_p, c_void_p]),
     ("dg_operator_tune", c_i32, [c_void_p, c_i32, c_void_p, P(c_dbl), P(c_dbl)]),
     ("dg_get_info", c_i32, [c_void_p, P(c_i32), P(c_i32), P(c_i64), P(c_i64)]),
     ("dg_get_nodes", c_i32, [c_void_p, c_void_p, c_void_p]),

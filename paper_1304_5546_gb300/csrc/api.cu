@@ -33,10 +33,11 @@ dg_status cuda_fail(cudaError_t err, const char* where) {
 }
 
 void free_device(dg_op* op) {
-  void* ptrs[] = {op->d_Dr,   op->d_Ds,   op->d_LIFT,   op->d_geo,  op->d_conn,
-                  op->d_qtmp, op->d_flag, op->d_status, op->d_tcop, op->d_lam};
+  void* ptrs[] = {op->d_Dr,   op->d_Ds,     op->d_LIFT, op->d_geo, op->d_conn,    op->d_qtmp,
+                  op->d_flag, op->d_status, op->d_tcop, op->d_lam, op->d_src_w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  op->d_src_w = nullptr;
   op->d_Dr = op->d_Ds = op->d_LIFT = op->d_geo = op->d_conn = op->d_qtmp = nullptr;
   op->d_flag = nullptr;
   op->d_status = nullptr;
@@ -349,8 +350,46 @@ dg_status check_field(const dg_op* op, const void* p, const char* name, const ch
   return DG_OK;
 }
 
+// Ricker point source of an operator (dg_operator_set_source), applied after
+// a stage launch: the source element's Ez residual gains dt s(t) w and its
+// Ez values b times that.  This is the LSRK stage update with s(t) w added
+// to the right-hand side of Eq. dg-strong-explicit (w = M^-1 l(x_s) / J_k,
+// the projected point load).  rhs_only: q is a right-hand side, which gains
+// s(t) w.  s(t) = A (1 - 2 a^2) exp(-a^2), a = pi f (t - t0).
 template <typename T>
-dg_status run_steps(const dg_op* op, T* q, T* res, double dt, int32_t nsteps, cudaStream_t s) {
+__global__ void point_source_kernel(T* q, T* res, const T* w, int Np, double t, double pif,
+                                    double t0, double amp, double dt, double b, int rhs_only) {
+  const int n = threadIdx.x;
+  if (n >= Np) return;
+  const double a = (t - t0) * pif;
+  const double s = amp * (1.0 - 2.0 * a * a) * exp(-a * a);
+  if (rhs_only) {
+    q[n] += static_cast<T>(s) * w[n];
+    return;
+  }
+  const T v = static_cast<T>(dt * s) * w[n];
+  res[n] += v;
+  q[n] += static_cast<T>(b) * v;
+}
+
+// The point source after stage i of a step that starts at t (stage time
+// t + c_i dt), on the stage's output fields q and residual res; nothing
+// without a source.
+template <typename T>
+cudaError_t stage_source(const dg_op* op, T* q, T* res, double t, double dt, int i,
+                         cudaStream_t s) {
+  if (!op->has_src) return cudaSuccess;
+  const int64_t off = 2 * op->fstride + op->src_k * op->Np;
+  point_source_kernel<T><<<1, 64, 0, s>>>(q + off, res + off, static_cast<const T*>(op->d_src_w),
+                                          op->Np, t + op->lsrk_c[i] * dt, M_PI * op->src.f,
+                                          op->src.t0, op->src.amplitude, dt, op->lsrk_b[i], 0);
+  op->launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+template <typename T>
+dg_status run_steps(const dg_op* op, T* q, T* res, double t0, double dt, int32_t nsteps,
+                    cudaStream_t s) {
   dgw::StageArgs<T> a = base_args<T>(op);
   a.res = res;
   a.dt = static_cast<T>(dt);
@@ -366,6 +405,8 @@ dg_status run_steps(const dg_op* op, T* q, T* res, double dt, int32_t nsteps, cu
       cudaError_t err = launch_order<T>(op, a, mode, s);
       if (err != cudaSuccess) return cuda_fail(err, "dg_step: kernel launch");
       op->launches.fetch_add(1, std::memory_order_relaxed);
+      err = stage_source<T>(op, other, res, t0 + n * dt, dt, i, s);
+      if (err != cudaSuccess) return cuda_fail(err, "dg_step: point-source launch");
       std::swap(cur, other);
     }
   }
@@ -545,6 +586,43 @@ extern "C" dg_status dg_operator_set_face_pairs(dg_op* op, int32_t enable) {
   return DG_OK;
 }
 
+extern "C" dg_status dg_operator_set_source(dg_op* op, const dg_point_source* src) {
+  dgw::clear_error();
+  const char* where = "dg_operator_set_source";
+  if (!op) return fail(DG_ERR_ARG, "%s: NULL operator", where);
+  if (!src) {
+    op->has_src = false;
+    op->src_k = -1;
+    return DG_OK;
+  }
+  if (!std::isfinite(src->x) || !std::isfinite(src->y) || !(src->f > 0.0) ||
+      !std::isfinite(src->f) || !std::isfinite(src->t0) || !std::isfinite(src->amplitude))
+    return fail(DG_ERR_ARG, "%s: bad point source parameters", where);
+  std::vector<double> w;
+  const int64_t k = dgw::point_source(op->ref, op->geo, op->K, src->x, src->y, w);
+  if (k < 0)
+    return fail(DG_ERR_ARG, "%s: source point (%g, %g) is outside the mesh", where, src->x, src->y);
+  if (op->has_device) {
+    dg_status st = check_device_op(op, where);
+    if (st) return st;
+    cudaError_t err = cudaSuccess;
+    if (!op->d_src_w) err = dgw::dev_malloc(&op->d_src_w, static_cast<size_t>(op->Np) * 8);
+    if (err == cudaSuccess) {
+      if (op->precision == DG_FP32) {
+        std::vector<float> wf(w.begin(), w.end());
+        err = cudaMemcpy(op->d_src_w, wf.data(), wf.size() * 4, cudaMemcpyHostToDevice);
+      } else {
+        err = cudaMemcpy(op->d_src_w, w.data(), w.size() * 8, cudaMemcpyHostToDevice);
+      }
+    }
+    if (err != cudaSuccess) return cuda_fail(err, where);
+  }
+  op->src = *src;
+  op->src_k = k;
+  op->has_src = true;
+  return DG_OK;
+}
+
 extern "C" dg_status dg_get_info(const dg_op* op, int32_t* Np, int32_t* Nfp, int64_t* K,
                                  int64_t* field_stride) {
   dgw::clear_error();
@@ -703,7 +781,7 @@ extern "C" void dg_op_destroy(dg_op* op) {
 extern "C" dg_status dg_rhs(const dg_op* op, const void* d_q, void* d_rhs, double t,
                             void* stream) {
   dgw::clear_error();
-  (void)t;
+  if (!std::isfinite(t)) return fail(DG_ERR_ARG, "dg_rhs: t is not finite");
   dg_status st = check_device_op(op, "dg_rhs");
   if (st) return st;
   if ((st = check_field(op, d_q, "d_q", "dg_rhs"))) return st;
@@ -725,29 +803,44 @@ extern "C" dg_status dg_rhs(const dg_op* op, const void* d_q, void* d_rhs, doubl
   }
   if (err != cudaSuccess) return cuda_fail(err, "dg_rhs: kernel launch");
   op->launches.fetch_add(1, std::memory_order_relaxed);
+  if (op->has_src) {
+    const int64_t off = 2 * op->fstride + op->src_k * op->Np;
+    const double pif = M_PI * op->src.f;
+    if (op->precision == DG_FP32)
+      point_source_kernel<float><<<1, 64, 0, s>>>(
+          static_cast<float*>(d_rhs) + off, nullptr, static_cast<const float*>(op->d_src_w),
+          op->Np, t, pif, op->src.t0, op->src.amplitude, 0.0, 0.0, 1);
+    else
+      point_source_kernel<double><<<1, 64, 0, s>>>(
+          static_cast<double*>(d_rhs) + off, nullptr, static_cast<const double*>(op->d_src_w),
+          op->Np, t, pif, op->src.t0, op->src.amplitude, 0.0, 0.0, 1);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "dg_rhs: point-source launch");
+    op->launches.fetch_add(1, std::memory_order_relaxed);
+  }
   return DG_OK;
 }
 
 extern "C" dg_status dg_step(const dg_op* op, void* d_q, void* d_res, double t0, double dt,
                              int32_t nsteps, void* stream) {
   dgw::clear_error();
-  (void)t0;
   dg_status st = check_device_op(op, "dg_step");
   if (st) return st;
   if ((st = check_field(op, d_q, "d_q", "dg_step"))) return st;
   if ((st = check_field(op, d_res, "d_res", "dg_step"))) return st;
   if (nsteps < 0) return fail(DG_ERR_ARG, "dg_step: nsteps = %d < 0", nsteps);
-  if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dg_step: dt is not finite");
+  if (!std::isfinite(dt) || !std::isfinite(t0))
+    return fail(DG_ERR_ARG, "dg_step: dt or t0 is not finite");
   const size_t bytes = 3 * op->fstride * op->elem_size;
   if (overlaps(d_q, d_res, bytes)) return fail(DG_ERR_ARG, "dg_step: d_q and d_res overlap");
   if (overlaps(d_q, op->d_qtmp, bytes) || overlaps(d_res, op->d_qtmp, bytes))
     return fail(DG_ERR_ARG, "dg_step: buffer overlaps the operator's internal buffer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (op->precision == DG_FP32)
-    return run_steps<float>(op, static_cast<float*>(d_q), static_cast<float*>(d_res), dt, nsteps,
-                            s);
-  return run_steps<double>(op, static_cast<double*>(d_q), static_cast<double*>(d_res), dt, nsteps,
-                           s);
+    return run_steps<float>(op, static_cast<float*>(d_q), static_cast<float*>(d_res), t0, dt,
+                            nsteps, s);
+  return run_steps<double>(op, static_cast<double*>(d_q), static_cast<double*>(d_res), t0, dt,
+                           nsteps, s);
 }
 
 extern "C" dg_status dg_solve(const dg_op* op, void* d_q, void* d_res, double T, double dt,
@@ -797,8 +890,8 @@ namespace {
 // nsteps LSRK steps ping-ponging between q and tmp (no copy back); returns
 // the buffer that holds the result
 template <typename T>
-dg_status run_stages(const dg_op* op, T* q, T* tmp, T* res, double dt, int32_t nsteps,
-                     cudaStream_t s, T** result) {
+dg_status run_stages(const dg_op* op, T* q, T* tmp, T* res, double t0, double dt,
+                     int32_t nsteps, cudaStream_t s, T** result) {
   dgw::StageArgs<T> a = base_args<T>(op);
   a.res = res;
   a.dt = static_cast<T>(dt);
@@ -814,6 +907,8 @@ dg_status run_stages(const dg_op* op, T* q, T* tmp, T* res, double dt, int32_t n
       cudaError_t err = launch_order<T>(op, a, mode, s);
       if (err != cudaSuccess) return cuda_fail(err, "dg_step_host_jobs: kernel launch");
       op->launches.fetch_add(1, std::memory_order_relaxed);
+      err = stage_source<T>(op, other, res, t0 + n * dt, dt, i, s);
+      if (err != cudaSuccess) return cuda_fail(err, "dg_step_host_jobs: point-source launch");
       std::swap(cur, other);
     }
   }
@@ -859,8 +954,8 @@ struct JobPipe {
 };
 
 template <typename T>
-dg_status run_jobs(const dg_op* op, int32_t njobs, void* const* h_q, T* work, double dt,
-                   int32_t nsteps, cudaStream_t s) {
+dg_status run_jobs(const dg_op* op, int32_t njobs, void* const* h_q, T* work, double t0,
+                   double dt, int32_t nsteps, cudaStream_t s) {
   const char* where = "dg_step_host_jobs";
   const size_t fvals = 3 * static_cast<size_t>(op->fstride);
   const size_t bytes = fvals * sizeof(T);
@@ -900,7 +995,7 @@ dg_status run_jobs(const dg_op* op, int32_t njobs, void* const* h_q, T* work, do
     if (err == cudaSuccess) err = cudaStreamWaitEvent(s, pipe.in_done[slot], 0);
     if (err != cudaSuccess) return cuda_fail(err, where);
     T* out = nullptr;
-    dg_status st = run_stages<T>(op, q, tmp, res, dt, nsteps, s, &out);
+    dg_status st = run_stages<T>(op, q, tmp, res, t0, dt, nsteps, s, &out);
     if (st) return st;
     err = cudaEventRecord(pipe.comp_done[slot], s);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(pipe.d2h, pipe.comp_done[slot], 0);
@@ -927,7 +1022,6 @@ extern "C" dg_status dg_step_host_jobs(const dg_op* op, int32_t njobs, void* con
                                        void* d_work, double t0, double dt, int32_t nsteps,
                                        void* stream) {
   dgw::clear_error();
-  (void)t0;
   const char* where = "dg_step_host_jobs";
   dg_status st = check_device_op(op, where);
   if (st) return st;
@@ -940,8 +1034,8 @@ extern "C" dg_status dg_step_host_jobs(const dg_op* op, int32_t njobs, void* con
   if ((st = check_field(op, d_work, "d_work", where))) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (op->precision == DG_FP32)
-    return run_jobs<float>(op, njobs, h_q, static_cast<float*>(d_work), dt, nsteps, s);
-  return run_jobs<double>(op, njobs, h_q, static_cast<double*>(d_work), dt, nsteps, s);
+    return run_jobs<float>(op, njobs, h_q, static_cast<float*>(d_work), t0, dt, nsteps, s);
+  return run_jobs<double>(op, njobs, h_q, static_cast<double*>(d_work), t0, dt, nsteps, s);
 }
 
 extern "C" dg_status dg_check_finite(const dg_op* op, const void* d_q, void* stream) {
@@ -1094,8 +1188,8 @@ dg_status static_scratch(int device, void** out) {
 
 // Same launch sequence as run_steps, with `tmp` as the ping-pong buffer.
 template <typename T>
-dg_status run_steps_static(const dg_op* op, T* q, T* res, double dt, int32_t nsteps, T* tmp,
-                           cudaStream_t s) {
+dg_status run_steps_static(const dg_op* op, T* q, T* res, double t0, double dt, int32_t nsteps,
+                           T* tmp, cudaStream_t s) {
   dgw::StageArgs<T> a = base_args<T>(op);
   a.res = res;
   a.dt = static_cast<T>(dt);
@@ -1111,6 +1205,8 @@ dg_status run_steps_static(const dg_op* op, T* q, T* res, double dt, int32_t nst
       cudaError_t err = launch_order<T>(op, a, mode, s);
       if (err != cudaSuccess) return cuda_fail(err, "dg_step_static: kernel launch");
       op->launches.fetch_add(1, std::memory_order_relaxed);
+      err = stage_source<T>(op, other, res, t0 + n * dt, dt, i, s);
+      if (err != cudaSuccess) return cuda_fail(err, "dg_step_static: point-source launch");
       std::swap(cur, other);
     }
   }
@@ -1127,13 +1223,13 @@ dg_status run_steps_static(const dg_op* op, T* q, T* res, double dt, int32_t nst
 extern "C" dg_status dg_step_static(const dg_op* op, void* d_q, void* d_res, double t0,
                                     double dt, int32_t nsteps, void* stream) {
   dgw::clear_error();
-  (void)t0;
   dg_status st = check_device_op(op, "dg_step_static");  // makes op->device current
   if (st) return st;
   if ((st = check_field(op, d_q, "d_q", "dg_step_static"))) return st;
   if ((st = check_field(op, d_res, "d_res", "dg_step_static"))) return st;
   if (nsteps < 0) return fail(DG_ERR_ARG, "dg_step_static: nsteps = %d < 0", nsteps);
-  if (!std::isfinite(dt)) return fail(DG_ERR_ARG, "dg_step_static: dt is not finite");
+  if (!std::isfinite(dt) || !std::isfinite(t0))
+    return fail(DG_ERR_ARG, "dg_step_static: dt or t0 is not finite");
   const size_t bytes = 3 * op->fstride * op->elem_size;
   if (bytes > static_cast<size_t>(DG_STATIC_SCRATCH_BYTES))
     return fail(DG_ERR_ARG,
@@ -1162,10 +1258,10 @@ extern "C" dg_status dg_step_static(const dg_op* op, void* d_q, void* d_res, dou
     }
   }
   if (op->precision == DG_FP32)
-    return run_steps_static<float>(op, static_cast<float*>(d_q), static_cast<float*>(d_res), dt,
-                                   nsteps, static_cast<float*>(scratch), s);
-  return run_steps_static<double>(op, static_cast<double*>(d_q), static_cast<double*>(d_res), dt,
-                                  nsteps, static_cast<double*>(scratch), s);
+    return run_steps_static<float>(op, static_cast<float*>(d_q), static_cast<float*>(d_res), t0,
+                                   dt, nsteps, static_cast<float*>(scratch), s);
+  return run_steps_static<double>(op, static_cast<double*>(d_q), static_cast<double*>(d_res), t0,
+                                  dt, nsteps, static_cast<double*>(scratch), s);
 }
 
 namespace dgw {

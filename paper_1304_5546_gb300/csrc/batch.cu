@@ -99,6 +99,15 @@ struct dg_batch {
   size_t smem = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t capture = nullptr;
+  // launch mode: concurrent (each order's stage a kernel of its own, the
+  // orders side by side on streams of their own, joined once per step) or,
+  // with DG_BATCH_SPLIT or when dg_batch_tune measures it faster, split (one
+  // launch per stage, its CTAs split among the orders)
+  bool concurrent = true;
+  float tuned_split_ms = 0.f, tuned_concurrent_ms = 0.f;  // dg_batch_tune's last timings
+  cudaStream_t ostream[kOrders] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kOrders] = {};
   double lsrk_a[5], lsrk_b[5], lsrk_c[5];
   int64_t launches = 0;
   dgw::Staging staging;
@@ -178,6 +187,11 @@ void destroy_batch(dg_batch* b) {
   for (cudaGraphExec_t& g : b->graph)
     if (g) cudaGraphExecDestroy(g);
   if (b->capture) cudaStreamDestroy(b->capture);
+  for (int g = 0; g < kOrders; ++g) {
+    if (b->ostream[g]) cudaStreamDestroy(b->ostream[g]);
+    if (b->join_ev[g]) cudaEventDestroy(b->join_ev[g]);
+  }
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   for (Pool& p : b->pools) free_pool(p);
   if (b->d_meta) cudaFree(b->d_meta);
   if (b->d_status) cudaFree(b->d_status);
@@ -319,6 +333,68 @@ cudaError_t launch_stage(dg_batch* b, int src, int stage, cudaStream_t s) {
   return err;
 }
 
+// Order g's kernel of the concurrent mode for stage `stage`, reading field
+// buffer src; grid 0 only configures the kernel.
+cudaError_t launch_order_stage(dg_batch* b, int g, int src, int stage, int grid, cudaStream_t s) {
+  const dgw::BatchArgs a = batch_args(b, src, stage);
+  const dgw::StageArgs<float>& ga = a.g[g];
+  const bool first = stage == 0;
+  cudaError_t err = cudaErrorInvalidValue;
+#define DG_ORDER_CASE(NN_)                                                                 \
+  case NN_:                                                                                \
+    err = first ? dgw::launch_batch_order<NN_, dgw::kModeFirstStage>(ga, grid, s)          \
+                : dgw::launch_batch_order<NN_, dgw::kModeStage>(ga, grid, s);              \
+    break;
+  switch (g + 1) {
+    DG_ORDER_CASE(1)
+    DG_ORDER_CASE(2)
+    DG_ORDER_CASE(3)
+    DG_ORDER_CASE(4)
+    DG_ORDER_CASE(5)
+    DG_ORDER_CASE(6)
+    DG_ORDER_CASE(7)
+    default:
+      break;
+  }
+#undef DG_ORDER_CASE
+  if (err == cudaSuccess && grid > 0) ++b->launches;
+  return err;
+}
+
+// `reps` launches of stage `stage` (reading buffer src) of every order with
+// a pool, each order on its own stream, forked from and joined back into s.
+cudaError_t launch_concurrent(dg_batch* b, int src, int stage, int reps, bool whole_step,
+                              cudaStream_t s) {
+  cudaError_t err = cudaEventRecord(b->fork_ev, s);
+  for (int g = 0; g < kOrders && err == cudaSuccess; ++g) {
+    if (b->pools[g].cap == 0) continue;
+    err = cudaStreamWaitEvent(b->ostream[g], b->fork_ev, 0);
+    if (whole_step) {
+      for (int i = 0; i < 5 && err == cudaSuccess; ++i)
+        err = launch_order_stage(b, g, src ^ (i & 1), i, b->num_sms, b->ostream[g]);
+    } else {
+      for (int r = 0; r < reps && err == cudaSuccess; ++r)
+        err = launch_order_stage(b, g, src, stage, b->num_sms, b->ostream[g]);
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(b->join_ev[g], b->ostream[g]);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(s, b->join_ev[g], 0);
+  }
+  return err;
+}
+
+// One LSRK step of every problem, from field buffer src, in the batch's
+// launch mode, followed by the step-counter tick.
+cudaError_t launch_step(dg_batch* b, int src, cudaStream_t s) {
+  cudaError_t err = cudaSuccess;
+  if (b->concurrent) {
+    err = launch_concurrent(b, src, 0, 1, true, s);
+  } else {
+    for (int i = 0; i < 5 && err == cudaSuccess; ++i) err = launch_stage(b, src ^ (i & 1), i, s);
+  }
+  if (err == cudaSuccess) err = launch_tick(b, s);
+  return err;
+}
+
 // block tables, counts and CTA split -> device (asynchronously on s)
 dg_status upload_tables(dg_batch* b, cudaStream_t s) {
   std::vector<int2> tab[kOrders];
@@ -376,15 +452,18 @@ dg_status capture_graphs(dg_batch* b) {
   const dgw::BatchArgs a0 = batch_args(b, 0, 0);
   cudaError_t cerr = dgw::launch_batch_tc<dgw::kModeFirstStage>(a0, 0, 0, b->capture);
   if (cerr == cudaSuccess) cerr = dgw::launch_batch_tc<dgw::kModeStage>(a0, 0, 0, b->capture);
+  for (int g = 0; g < kOrders && cerr == cudaSuccess; ++g) {
+    if (b->pools[g].cap == 0) continue;
+    cerr = launch_order_stage(b, g, 0, 0, 0, b->capture);
+    if (cerr == cudaSuccess) cerr = launch_order_stage(b, g, 0, 1, 0, b->capture);
+  }
   if (cerr != cudaSuccess) return cuda_fail(cerr, "dg_batch_step: kernel attributes");
   for (int src = 0; src < 2; ++src) {
     cudaGraph_t graph = nullptr;
     cudaError_t err = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
     if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: begin capture");
     const int64_t before = b->launches;
-    cudaError_t lerr = cudaSuccess;
-    for (int i = 0; i < 5 && lerr == cudaSuccess; ++i) lerr = launch_stage(b, src ^ (i & 1), i, b->capture);
-    if (lerr == cudaSuccess) lerr = launch_tick(b, b->capture);
+    const cudaError_t lerr = launch_step(b, src, b->capture);
     b->launches = before;  // captured, not run
     err = cudaStreamEndCapture(b->capture, &graph);
     if (lerr != cudaSuccess) err = lerr;
@@ -393,6 +472,14 @@ dg_status capture_graphs(dg_batch* b) {
     if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: graph capture");
   }
   return DG_OK;
+}
+
+// kernel launches of one step in the batch's mode (stages and the tick)
+int64_t launches_per_step(const dg_batch* b) {
+  if (!b->concurrent) return 6;
+  int64_t n = 1;
+  for (int g = 0; g < kOrders; ++g) n += b->pools[g].cap > 0 ? 5 : 0;
+  return n;
 }
 
 dg_status check_batch(dg_batch* b, const char* where) {
@@ -426,7 +513,7 @@ extern "C" dg_status dg_batch_plan_ctas(const int64_t* nblocks, const double* co
 extern "C" dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_batch** out) {
   dgw::clear_error();
   if (!capacity || !out) return fail(DG_ERR_ARG, "dg_batch_create: NULL argument");
-  if (flags & ~(DG_BATCH_NO_GRAPH | DG_BATCH_NO_ADAPT))
+  if (flags & ~(DG_BATCH_NO_GRAPH | DG_BATCH_NO_ADAPT | DG_BATCH_SPLIT))
     return fail(DG_ERR_ARG, "dg_batch_create: unknown flags 0x%x", flags);
   bool any = false;
   for (int g = 0; g < kOrders; ++g) {
@@ -439,6 +526,7 @@ extern "C" dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_
   dg_batch* b = new (std::nothrow) dg_batch;
   if (!b) return fail(DG_ERR_OOM, "dg_batch_create: out of host memory");
   b->flags = flags;
+  b->concurrent = !(flags & DG_BATCH_SPLIT);
   dgw::lsrk_coefficients(b->lsrk_a, b->lsrk_b, b->lsrk_c);
   cudaError_t err = cudaGetDevice(&b->device);
   if (err == cudaSuccess)
@@ -473,6 +561,12 @@ extern "C" dg_status dg_batch_create(const int64_t* capacity, int32_t flags, dg_
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->clock_ev, cudaEventDisableTiming);
   if (err == cudaSuccess) err = dgw::dev_malloc(reinterpret_cast<void**>(&b->d_status), sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(b->d_status, 0, sizeof(int));
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+  for (int g = 0; g < kOrders && err == cudaSuccess; ++g) {
+    if (capacity[g] == 0) continue;
+    err = cudaStreamCreateWithFlags(&b->ostream[g], cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->join_ev[g], cudaEventDisableTiming);
+  }
   if (err != cudaSuccess) {
     destroy_batch(b);
     return cuda_fail(err, "dg_batch_create: cudaMalloc");
@@ -748,19 +842,15 @@ extern "C" dg_status dg_batch_step(dg_batch* b, int32_t nsteps, void* stream) {
     if (use_graph) {
       cudaError_t err = cudaGraphLaunch(b->graph[b->cur], s);
       if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: graph launch");
-      b->launches += 6;
+      b->launches += launches_per_step(b);
     } else {
-      for (int i = 0; i < 5; ++i) {
-        cudaError_t err = launch_stage(b, b->cur ^ (i & 1), i, s);
-        if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: kernel launch");
-      }
-      cudaError_t err = launch_tick(b, s);
+      cudaError_t err = launch_step(b, b->cur, s);
       if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: kernel launch");
     }
     b->cur ^= 1;
     ++b->steps;
   }
-  if (!(b->flags & DG_BATCH_NO_ADAPT) && nsteps > 0) {
+  if (!(b->flags & DG_BATCH_NO_ADAPT) && !b->concurrent && nsteps > 0) {
     if (b->clock_pending && cudaEventQuery(b->clock_ev) == cudaSuccess) {
       b->clock_pending = false;
       if (!b->dirty && (st = adapt_split(b, s))) return st;
@@ -887,13 +977,41 @@ extern "C" dg_status dg_batch_tune(dg_batch* b, int32_t reps, void* stream) {
     }
     if (!improved) break;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (err != cudaSuccess) return cuda_fail(err, "dg_batch_tune");
+  if (err != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cuda_fail(err, "dg_batch_tune");
+  }
   b->measured = true;
   std::copy(best, best + kOrders, b->cta);
   err = set_plan(b->cta);
-  if (err != cudaSuccess) return cuda_fail(err, "dg_batch_tune: plan upload");
+  // 4. launch mode: the tuned split against the orders' own kernels side by
+  //    side (same stage, same reps); the faster one is kept (DG_BATCH_SPLIT
+  //    keeps the split)
+  if (err == cudaSuccess && !(b->flags & DG_BATCH_SPLIT)) {
+    float conc_ms = 0.f;
+    err = launch_concurrent(b, b->cur, 1, 1, false, s);  // warm
+    if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+    if (err == cudaSuccess) err = launch_concurrent(b, b->cur, 1, reps, false, s);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&conc_ms, e0, e1);
+    if (err == cudaSuccess) {
+      const bool conc = conc_ms <= best_ms;
+      if (conc != b->concurrent) {
+        for (cudaGraphExec_t& g : b->graph) {
+          if (g) cudaGraphExecDestroy(g);
+          g = nullptr;
+        }
+      }
+      b->concurrent = conc;
+      b->tuned_split_ms = best_ms;
+      b->tuned_concurrent_ms = conc_ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(err, "dg_batch_tune: plan upload / launch mode");
   return DG_OK;
 }
 
@@ -902,7 +1020,11 @@ extern "C" dg_status dg_batch_plan(const dg_batch* b, int32_t* cta, int64_t* nbl
   dgw::clear_error();
   if (!b) return fail(DG_ERR_ARG, "dg_batch_plan: NULL batch");
   for (int g = 0; g < kOrders; ++g) {
-    if (cta) cta[g] = b->cta[g];
+    // concurrent mode: each order's kernel has one CTA per SM, of which as
+    // many as it has blocks do work
+    if (cta)
+      cta[g] = b->concurrent ? static_cast<int32_t>(std::min<int64_t>(b->num_sms, b->nblk[g]))
+                             : b->cta[g];
     if (nblocks) nblocks[g] = b->nblk[g];
     if (cost) cost[g] = b->cost[g];
   }

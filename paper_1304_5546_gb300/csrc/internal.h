@@ -109,6 +109,12 @@ struct dg_op {
   // flux parameter of Eq. max2d-numflux: 1 upwind (default), 0 central
   double alpha = 1.0;
   int face_pairs = 0;  // dg_operator_set_face_pairs
+  // Ricker point source (dg_operator_set_source): element src_k, projected
+  // point load in d_src_w (Np values of the field precision)
+  bool has_src = false;
+  int64_t src_k = -1;
+  dg_point_source src{};
+  void* d_src_w = nullptr;
   bool has_device = false;
   int device = 0;
   int num_sms = 0;

@@ -1142,6 +1142,37 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #undef DG_BATCH_GROUP
 }
 
+// The concurrent launch mode of a batch: each order's share of a stage is a
+// kernel of its own (the body inlined, so the stage arguments are kernel
+// parameters rather than data reached through a pointer), with one CTA per
+// SM striding over the order's block table; the orders' kernels run side by
+// side and the hardware gives SMs to whichever has CTAs waiting.  CTAs past
+// the order's block count (read from device memory, so that a captured
+// graph replays unchanged when problems join or leave) return at once.
+template <int N, int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    dg_batch_order_kernel(const __grid_constant__ StageArgs<float> g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  if (static_cast<int>(blockIdx.x) >= __ldg(g.nblocks)) return;
+  static_assert(TcLayout<N, kTcTf32x3, true>::THREADS == kTcThreads, "block size");
+  tc_stage_body<N, MODE, kTcTf32x3, true, true>(g, blockIdx.x, gridDim.x, smem);
+}
+
+template <int N, int MODE>
+cudaError_t launch_batch_order(const StageArgs<float>& g, int grid, cudaStream_t stream) {
+  using L = TcLayout<N, kTcTf32x3, true>;
+  static std::atomic<uint64_t> configured{0};
+  cudaError_t err = configure_once_per_device(configured, [] {
+    return cudaFuncSetAttribute(dg_batch_order_kernel<N, MODE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(L::SMEM_BYTES));
+  });
+  if (err != cudaSuccess) return err;
+  if (grid < 1) return cudaSuccess;
+  dg_batch_order_kernel<N, MODE><<<grid, kTcThreads, L::SMEM_BYTES, stream>>>(g);
+  return cudaGetLastError();
+}
+
 template <int MODE>
 cudaError_t launch_batch_tc(const BatchArgs& args, int grid, size_t smem, cudaStream_t stream) {
   static std::atomic<uint64_t> configured{0};

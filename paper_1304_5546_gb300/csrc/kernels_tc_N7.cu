@@ -1,8 +1,11 @@
 // Order-7 instantiations of the FP32 tensor-core stage kernel with 3xTF32
-// products: uniform medium, and per-element permittivity.
+// products: uniform medium, per-element permittivity, and the order's kernel
+// of the concurrent batched launch.
 #include "kernels_tc.cuh"
 
 namespace dgw {
 template cudaError_t launch_stage_tc<7, kTcTf32x3>(const StageArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_stage_tc_media<7>(const StageArgs<float>&, int, int, cudaStream_t);
+template cudaError_t launch_batch_order<7, kModeFirstStage>(const StageArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_batch_order<7, kModeStage>(const StageArgs<float>&, int, cudaStream_t);
 }  // namespace dgw

@@ -201,6 +201,11 @@ struct BatchArgs {
 // batch_tc_smem_bytes of an order that may have CTAs
 template <int MODE>
 cudaError_t launch_batch_tc(const BatchArgs& args, int grid, size_t smem, cudaStream_t stream);
+// The concurrent mode of the batched launch: order N's share of a stage as a
+// kernel of its own, `grid` CTAs (one per SM) over its block table
+// (g.blocks, g.nblocks); grid 0 only configures the kernel.
+template <int N, int MODE>
+cudaError_t launch_batch_order(const StageArgs<float>& g, int grid, cudaStream_t stream);
 // shared memory and elements per block of order N's CTA in the batched launch
 size_t batch_tc_smem_bytes(int N);
 int batch_tc_block_elems(int N);

@@ -440,6 +440,9 @@ extern "C" dg_status dg_partition_create(const dg_op* op, int32_t P, dg_partitio
   const char* where = "dg_partition_create";
   if (!op || !out) return fail(DG_ERR_ARG, "%s: NULL argument", where);
   *out = nullptr;
+  if (op->has_src)
+    return fail(DG_ERR_ARG, "%s: the operator has a point source; partitions step without one",
+                where);
   if (P < 1 || P > kMaxParts || P > op->K)
     return fail(DG_ERR_ARG, "%s: P = %d outside [1, min(K = %lld, %d)]", where, P,
                 static_cast<long long>(op->K), kMaxParts);

@@ -5,7 +5,10 @@ media and time steps stepped by one persistent launch per stage.
   permittivity (FP32 tolerance 1e-5 relative to max |q|, FP32-rounded start);
 * a problem's result is bit-for-bit the same alone in a batch and in a mix
   (each element's arithmetic depends only on its own problem);
-* graph replay and direct launches agree bit for bit;
+* graph replay and direct launches agree bit for bit, in both launch modes
+  (concurrent: each order's kernel of its own, side by side; split: one
+  launch per stage with the CTAs split among the orders), and the two modes
+  agree with each other and the oracle;
 * problems leave and join between steps (continuous batching): the others
   carry on unchanged and a newcomer in a freed range starts clean;
 * the autotuner leaves the fields alone and produces a valid CTA split;
@@ -98,8 +101,8 @@ def problems(P):
     return [_Problem(P, *s) for s in SPECS]
 
 
-def _run(P, probs, steps, graph=True, tune=False, adapt=True):
-    b = P.Batch(_capacity(probs), graph=graph, adapt=adapt)
+def _run(P, probs, steps, graph=True, tune=False, adapt=True, split=False):
+    b = P.Batch(_capacity(probs), graph=graph, adapt=adapt, split=split)
     slots = []
     for p in probs:
         slot = b.add(p.solver, p.dt, source=p.source)
@@ -131,11 +134,24 @@ def test_alone_equals_in_mix_bitwise(P, problems):
         assert np.array_equal(alone, mix[i]), i
 
 
-def test_graph_equals_direct_launches(P, problems):
-    a = _run(P, problems[:4], 2, graph=True)
-    b = _run(P, problems[:4], 2, graph=False)
+@pytest.mark.parametrize("split", [False, True])
+def test_graph_equals_direct_launches(P, problems, split):
+    a = _run(P, problems[:4], 2, graph=True, split=split)
+    b = _run(P, problems[:4], 2, graph=False, split=split)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+def test_launch_modes_agree_and_match_oracle(P, problems):
+    # concurrent (each order's kernel of its own, side by side) and split (one
+    # launch per stage, CTAs split among the orders) run the same stage body
+    steps = 3
+    conc = _run(P, problems, steps, split=False)
+    spl = _run(P, problems, steps, split=True)
+    for p, x, y in zip(problems, conc, spl):
+        want = p.oracle(steps)
+        assert _rel(x, want) <= TOL and _rel(y, want) <= TOL
+        assert _rel(x, y.astype(np.float64)) <= TOL
 
 
 def test_leave_and_join_between_steps(P, problems):
@@ -164,7 +180,7 @@ def test_leave_and_join_between_steps(P, problems):
 
 def test_tune_keeps_fields_and_plans_valid_split(P, problems):
     import torch
-    b = P.Batch(_capacity(problems))
+    b = P.Batch(_capacity(problems), split=True)
     slots = []
     for p in problems:
         s = b.add(p.solver, p.dt)
@@ -251,10 +267,27 @@ def test_point_source_outside_mesh_is_rejected(P, sourced):
     b.close()
 
 
+def test_tune_picks_a_launch_mode_and_keeps_results(P, problems):
+    # the tuner times the tuned split against the concurrent mode and keeps
+    # the faster; either way the fields stay and the results match
+    b = P.Batch(_capacity(problems))
+    slots = []
+    for p in problems:
+        s = b.add(p.solver, p.dt)
+        b.set_fields(s, p.q0)
+        slots.append(s)
+    b.tune(reps=2)
+    b.step(2)
+    b.sync_check()
+    for p, s in zip(problems, slots):
+        assert _rel(b.get_fields(s), p.oracle(2)) <= TOL
+    b.close()
+
+
 def test_online_split_adaptation_keeps_results(P, problems):
-    # 20 steps: the split is re-planned from clock snapshots along the way;
-    # which CTA computes a block never changes a result
-    a = _run(P, problems, 20, adapt=True)
-    b = _run(P, problems, 20, adapt=False)
+    # split mode, 20 steps: the split is re-planned from clock snapshots along
+    # the way; which CTA computes a block never changes a result
+    a = _run(P, problems, 20, adapt=True, split=True)
+    b = _run(P, problems, 20, adapt=False, split=True)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)

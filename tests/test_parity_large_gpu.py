@@ -225,16 +225,20 @@ class _Problem:
         return q
 
 
-def test_large_batch_of_three_orders(P):
-    # n = 123: K = 30,258 per problem (ragged at E = 40 and 80); the planner
-    # splits the 152 CTAs over N = 3, 5, 7, so each CTA still walks about
-    # ten blocks of its order
-    probs = [_Problem(P, 123, 3, 11), _Problem(P, 123, 5, 12, source=True),
-             _Problem(P, 123, 7, 13)]
+@pytest.mark.parametrize("split", [True, False])
+def test_large_batch_of_three_orders(P, split):
+    # split mode: n = 123, K = 30,258 per problem (ragged at E = 40 and 80);
+    # the planner splits the 152 CTAs over N = 3, 5, 7, so each CTA walks
+    # about ten blocks of its order.  Concurrent mode: every order's kernel
+    # has 152 CTAs, so the problems are larger (n = 221: K = 97,682 at N = 3;
+    # n = 156: K = 48,672 at N = 5, 7), again eight or more blocks per CTA
+    sizes = (123, 123, 123) if split else (221, 156, 156)
+    probs = [_Problem(P, sizes[0], 3, 11), _Problem(P, sizes[1], 5, 12, source=True),
+             _Problem(P, sizes[2], 7, 13)]
     cap = [0] * 7
     for p in probs:
         cap[p.N - 1] += (p.d.K + 3) // 4 * 4
-    b = P.Batch(cap)
+    b = P.Batch(cap, split=split)
     slots = []
     for p in probs:
         slot = b.add(p.solver, p.dt, source=p.source)
