@@ -568,6 +568,139 @@ def run_sweep_study(args):
             "rows": rows}
 
 
+def _longrun_oracle_worker(name, n, N, steps, snaps, conn, threads):
+    """Spawned process (no CUDA): the FP64 oracle's run of one long-run
+    configuration.  Makes the FP32-rounded Gaussian start on the oracle's
+    nodes, hands it over, takes the time step from the parent, steps, and
+    hands over the fields at the snapshot steps (as .npy files in /tmp)."""
+    import os as _os
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        _os.environ[v] = str(threads)
+    import time as _time
+
+    import numpy as np
+
+    import oracle as O
+    from synth import gaussian_pulse, jittered_delaunay_mesh
+
+    t0 = _time.perf_counter()
+    d = O.Discretization(*jittered_delaunay_mesh(n, seed=2024), N)
+    q = np.stack(gaussian_pulse(d.x, d.y)).astype(np.float32).astype(np.float64)
+    path = "/tmp/longrun_%s_q0.npy" % name
+    np.save(path, q)
+    conn.send(("q0", path))
+    dt = conn.recv()
+    for k in range(steps):
+        q = O.lsrk_step(d, q, k * dt, dt)
+        if k + 1 in snaps:
+            path = "/tmp/longrun_%s_oracle_%d.npy" % (name, k + 1)
+            np.save(path, q)
+            conn.send(("snap", k + 1, path, _time.perf_counter() - t0))
+    conn.send(("done", _time.perf_counter() - t0))
+
+
+def run_longrun_study(args):
+    """Long-run accuracy against the FP64 oracle at the configured sizes:
+    the single large mesh (K = 999,698, N = 5) for 100 LSRK steps and the
+    precision-path mesh (K = 262,088, N = 7) for 500 steps, from the
+    FP32-rounded Gaussian pulse (width 0.05 at (0.5, 0.5)) and the library's
+    CFL time step.  The oracle runs in spawned processes on the host cores
+    (started before any CUDA call); every FP32 variant runs on the GPU from
+    the same start.  At each snapshot step: max nodal error relative to
+    max |q| of the oracle, and L2 (rms) error relative to the oracle's rms.
+    One JSON line; writes gpurun_out/longrun_gpu_done once the GPU part is
+    over (the oracle may still be running)."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    configs = [
+        {"name": "large_N5", "n": 707, "N": 5, "steps": 100, "snaps": [1, 10, 100],
+         "variants": ["fp32", "fp32simt"]},
+        {"name": "precision_N7", "n": 362, "N": 7, "steps": 500, "snaps": [1, 10, 100, 500],
+         "variants": ["fp32", "bf16x3", "tf32", "bf16", "fp32simt"]},
+    ]
+    if args.longrun_quick:  # small sizes, for a check of the machinery
+        configs = [dict(c, n=c["n"] // 8, steps=c["steps"] // 10,
+                        snaps=[x for x in c["snaps"] if x <= c["steps"] // 10]) for c in configs]
+    ctx = mp.get_context("spawn")
+    workers = []
+    for c in configs:
+        a, b = ctx.Pipe()
+        pr = ctx.Process(target=_longrun_oracle_worker,
+                         args=(c["name"], c["n"], c["N"], c["steps"], set(c["snaps"]), b,
+                               args.longrun_threads))
+        pr.start()
+        workers.append((pr, a))
+
+    import torch
+
+    import paper_1304_5546_gb300 as P
+    from synth import jittered_delaunay_mesh
+
+    torch.cuda.set_device(0)
+    results = []
+    for c, (pr, conn) in zip(configs, workers):
+        tag, q0_path = conn.recv()
+        q0 = np.load(q0_path)
+        mesh = jittered_delaunay_mesh(c["n"], seed=2024)
+        gpu = {}
+        dt = None
+        for v in c["variants"]:
+            s = P.Solver(*mesh, N=c["N"], precision=v)
+            if dt is None:
+                dt = s.cfl_dt()
+                conn.send(dt)
+            q, res = s.from_numpy(q0), s.new_fields()
+            snaps, done, ms = {}, 0, 0.0
+            for k in c["snaps"]:
+                a_ev = torch.cuda.Event(enable_timing=True)
+                b_ev = torch.cuda.Event(enable_timing=True)
+                a_ev.record()
+                s.step(q, res, dt, nsteps=k - done, t0=done * dt)
+                b_ev.record()
+                b_ev.synchronize()
+                ms += a_ev.elapsed_time(b_ev)
+                done = k
+                snaps[k] = s.to_numpy(q)
+            P.dg_sync_check(s.op)
+            gpu[v] = (snaps, ms / c["steps"])
+            s.close()
+        results.append((c, gpu, dt))
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    open(os.path.join(ROOT, "gpurun_out", "longrun_gpu_done"), "w").write("done\n")
+    out = []
+    for (c, gpu, dt), (pr, conn) in zip(results, workers):
+        rows = {v: {"steps": [], "max_rel": [], "l2_rel": []} for v in c["variants"]}
+        oracle_s = None
+        while True:
+            msg = conn.recv()
+            if msg[0] == "done":
+                oracle_s = msg[1]
+                break
+            _, k, path, _el = msg
+            ref = np.load(path)
+            scale_max = np.abs(ref).max()
+            scale_l2 = np.sqrt(np.mean(ref ** 2))
+            for v in c["variants"]:
+                e = gpu[v][0][k] - ref
+                rows[v]["steps"].append(k)
+                rows[v]["max_rel"].append(float(np.abs(e).max() / scale_max))
+                rows[v]["l2_rel"].append(float(np.sqrt(np.mean(e ** 2)) / scale_l2))
+            os.remove(path)
+        pr.join()
+        for v in c["variants"]:
+            rows[v]["gpu_ms_per_step"] = gpu[v][1]
+        out.append({"config": c["name"], "K": 2 * c["n"] ** 2, "N": c["N"], "steps": c["steps"],
+                    "dt": dt, "oracle_seconds": oracle_s,
+                    "oracle_threads": args.longrun_threads, "variants": rows})
+    return {"study": "long-run error against the FP64 oracle",
+            "start": "FP32-rounded Gaussian pulse w=0.05 at (0.5, 0.5), H = 0",
+            "error": "max |gpu - oracle| / max |oracle| and rms(gpu - oracle) / rms(oracle) "
+                     "over all nodal values of the three fields",
+            "configs": out}
+
+
 def run_partition_study(args):
     """The mesh-partition path on one device (dg_partition_*): the default
     workload (order `--order`, K = 2 n^2) split into P parts by recursive
@@ -1031,10 +1164,15 @@ def main(argv=None):
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--_oracle-sample", nargs=3, default=None)
     ap.add_argument("--_oracle-timings", action="store_true")
-    ap.add_argument("--study", choices=["precision", "sweep", "partition", "oracle"], default=None,
+    ap.add_argument("--study", choices=["precision", "sweep", "partition", "oracle", "longrun"],
+                    default=None,
                     help="instead of the benchmark line: the precision-path study "
                          "(use with --order 7 --n 362 for K = 262,088)")
     ap.add_argument("--study-steps", type=int, default=500)
+    ap.add_argument("--longrun-threads", type=int, default=4,
+                    help="numpy threads of each oracle process of --study longrun")
+    ap.add_argument("--longrun-quick", action="store_true",
+                    help="--study longrun on small meshes and few steps")
     ap.add_argument("--sweep-orders", type=int, nargs="+", default=list(range(1, 8)))
     ap.add_argument("--partition-parts", type=int, nargs="+", default=[1, 2, 4, 8])
     ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
@@ -1069,6 +1207,9 @@ def main(argv=None):
         return 0
     if args.study == "partition":
         print(json.dumps(run_partition_study(args)), flush=True)
+        return 0
+    if args.study == "longrun":
+        print(json.dumps(run_longrun_study(args)), flush=True)
         return 0
     if args._oracle_timings:
         print(json.dumps(oracle_timings()), flush=True)

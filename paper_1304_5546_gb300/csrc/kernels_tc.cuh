@@ -110,6 +110,11 @@ struct TcLayout {
   // w % 4 and takes share (w - 4) / 4 of its rows' chunks); 16-19 face flux
   // and neighbour gathers; 20 MMA; 21 memory
   static constexpr int EPI_WARPS = 4, X_WARPS = 8, FLUX_WARPS = 8;
+  // memory warp: the bulk copies of a block issued by several lanes at once
+  // at N = 3 and N >= 5 (measured 2-6 % faster there on GB300), by lane 0
+  // alone at N = 1, 2 and 4 (where several issuing lanes measured 4-6 %
+  // slower)
+  static constexpr bool IO_LANES = N == 3 || N >= 5;
   static constexpr int FLUX_WARP0 = EPI_WARPS + X_WARPS;
   static constexpr int MMA_WARP = FLUX_WARP0 + FLUX_WARPS, IO_WARP = MMA_WARP + 1;
   static constexpr int THREADS = 32 * (IO_WARP + 1);
@@ -441,8 +446,12 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
   };
 
   if (warp == L::IO_WARP) {
-    // ======================= memory warp: TMA loads, bulk stores (lane 0)
-    if (lane == 0) {
+    if constexpr (L::IO_LANES) {
+      // ======================= memory warp: TMA loads, bulk stores.  The copies
+      // of a block are issued by several lanes in one instruction (lane f: q
+      // field f, 3 + f: res field f, 6: geometry, 7: face codes; stores: lane
+      // f field f of q, 3 + f of res); lane 0 alone arms the mbarriers.  Bulk
+      // async-groups are per thread, so every lane commits and waits on its own.
       int issued = 0;
       auto issue = [&](int it) {
         const int s = it % S;
@@ -455,73 +464,159 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
         const uint32_t gb = round16(static_cast<uint32_t>(n * GEO * 4));
         const uint32_t cb = round16(static_cast<uint32_t>(n * 3 * 4));
         unsigned char* st = stages + s * L::STAGE_BYTES;
-        mbar_expect_tx(&full[s], NQ * qb + gb + cb);
-#pragma unroll
-        for (int f = 0; f < 3; ++f)
-          tma_load_1d(st + f * L::QB, p.qin + f * fs + k0 * Np, qb, &full[s]);
-        if (MODE == kModeStage) {
-#pragma unroll
-          for (int f = 0; f < 3; ++f)
-            tma_load_1d(st + (3 + f) * L::QB, p.res + f * fs + k0 * Np, qb, &full[s]);
+        if (lane == 0) mbar_expect_tx(&full[s], NQ * qb + gb + cb);
+        __syncwarp();
+        if (lane < 3) {
+          tma_load_1d(st + lane * L::QB, p.qin + lane * fs + k0 * Np, qb, &full[s]);
+        } else if (lane < 6) {
+          if (MODE == kModeStage)
+            tma_load_1d(st + lane * L::QB, p.res + (lane - 3) * fs + k0 * Np, qb, &full[s]);
+        } else if (lane == 6) {
+          tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * GEO, gb, &full[s]);
+        } else if (lane == 7) {
+          tma_load_1d(st + 6 * L::QB + L::GB, p.conn + static_cast<int64_t>(k0) * 3, cb, &full[s]);
         }
-        tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * GEO, gb, &full[s]);
-        tma_load_1d(st + 6 * L::QB + L::GB, p.conn + static_cast<int64_t>(k0) * 3, cb, &full[s]);
       };
       bool ok = true;
       if (p.stall_gate) {  // timeout test: a flag that nothing sets, bounded wait
-        const unsigned long long t0 = global_ns();
-        while (*reinterpret_cast<const volatile int*>(p.stall_gate) == 0) {
-          if (global_ns() - t0 > kGateLimitNs) {
-            ok = false;
-            break;
+        if (lane == 0) {
+          const unsigned long long t0 = global_ns();
+          while (*reinterpret_cast<const volatile int*>(p.stall_gate) == 0) {
+            if (global_ns() - t0 > kGateLimitNs) {
+              ok = false;
+              break;
+            }
+            __nanosleep(1000);
           }
-          __nanosleep(1000);
         }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
       }
       if (ok) {
-        mbar_expect_tx(op_bar, L::NS * L::OB);
-        tma_load_1d(smem + L::OFF_OP, p.tc_op, L::NS * L::OB, op_bar);
+        if (lane == 0) {
+          mbar_expect_tx(op_bar, L::NS * L::OB);
+          tma_load_1d(smem + L::OFF_OP, p.tc_op, L::NS * L::OB, op_bar);
+        }
         for (; issued < niter && issued < S; ++issued) issue(issued);
       }
-      // outputs of block jj leave by bulk stores, one bulk group per block
-      // (empty for a short block, whose epilogue writes global memory); the
-      // stage of block jj - 1 is refilled once that block's stores have read
-      // it, so the warp never waits for the stores it has just issued
       for (int jj = 0; ok && jj < niter; ++jj) {
         const int s = jj % S;
-        ok = mbar_wait_or_abort(&out_ready[s], static_cast<uint32_t>((jj / S) & 1), abort_flag);
+        ok = __all_sync(0xffffffffu, mbar_wait_or_abort(&out_ready[s],
+                                                        static_cast<uint32_t>((jj / S) & 1),
+                                                        abort_flag));
         if (!ok) break;
         int k0, nv;
         block_at(jj, k0, nv);
-        if (nv == E) {
+        if (nv == E && lane < 6) {
           const float* sq = reinterpret_cast<const float*>(stages + s * L::STAGE_BYTES);
           if (MODE == kModeRhs) {
-#pragma unroll
-            for (int f = 0; f < 3; ++f)
-              tma_store_1d(p.rhs + f * fs + k0 * Np, sq + f * E * Np, L::QB);
+            if (lane < 3) tma_store_1d(p.rhs + lane * fs + k0 * Np, sq + lane * E * Np, L::QB);
+          } else if (lane < 3) {
+            tma_store_1d(p.qout + lane * fs + k0 * Np, sq + lane * E * Np, L::QB);
           } else {
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-              tma_store_1d(p.qout + f * fs + k0 * Np, sq + f * E * Np, L::QB);
-              tma_store_1d(p.res + f * fs + k0 * Np, sq + (3 + f) * E * Np, L::QB);
-            }
+            tma_store_1d(p.res + (lane - 3) * fs + k0 * Np, sq + lane * E * Np, L::QB);
           }
         }
         bulk_commit();
         if (jj >= 1 && issued < niter) {  // issued == jj - 1 + S: the stage of block jj - 1
           bulk_wait_read_but_last();
+          __syncwarp();
           fence_proxy_async();
           issue(issued);
           ++issued;
         }
       }
       if (!ok) {
-        fail();
-        // let this CTA's loads in flight land (each wait bounded)
-        for (int jj = (issued > S ? issued - S : 0); jj < issued; ++jj)
-          mbar_wait_bounded(&full[jj % S], static_cast<uint32_t>((jj / S) & 1), kWaitLimitNs);
+        if (lane == 0) {
+          fail();
+          // let this CTA's loads in flight land (each wait bounded)
+          for (int jj = (issued > S ? issued - S : 0); jj < issued; ++jj)
+            mbar_wait_bounded(&full[jj % S], static_cast<uint32_t>((jj / S) & 1), kWaitLimitNs);
+        }
       }
       bulk_wait_all();
+    } else {
+      // ======================= memory warp: TMA loads, bulk stores (lane 0)
+      if (lane == 0) {
+        int issued = 0;
+        auto issue = [&](int it) {
+          const int s = it % S;
+          int k0, n;
+          block_at(it, k0, n);
+#ifdef DGW_DEVICE_CHECKS
+          if (n == 0) return;  // rejected block: the abort flag ends every wait
+#endif
+          const uint32_t qb = round16(static_cast<uint32_t>(n * Np * 4));
+          const uint32_t gb = round16(static_cast<uint32_t>(n * GEO * 4));
+          const uint32_t cb = round16(static_cast<uint32_t>(n * 3 * 4));
+          unsigned char* st = stages + s * L::STAGE_BYTES;
+          mbar_expect_tx(&full[s], NQ * qb + gb + cb);
+#pragma unroll
+          for (int f = 0; f < 3; ++f)
+            tma_load_1d(st + f * L::QB, p.qin + f * fs + k0 * Np, qb, &full[s]);
+          if (MODE == kModeStage) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+              tma_load_1d(st + (3 + f) * L::QB, p.res + f * fs + k0 * Np, qb, &full[s]);
+          }
+          tma_load_1d(st + 6 * L::QB, p.geo + static_cast<int64_t>(k0) * GEO, gb, &full[s]);
+          tma_load_1d(st + 6 * L::QB + L::GB, p.conn + static_cast<int64_t>(k0) * 3, cb, &full[s]);
+        };
+        bool ok = true;
+        if (p.stall_gate) {  // timeout test: a flag that nothing sets, bounded wait
+          const unsigned long long t0 = global_ns();
+          while (*reinterpret_cast<const volatile int*>(p.stall_gate) == 0) {
+            if (global_ns() - t0 > kGateLimitNs) {
+              ok = false;
+              break;
+            }
+            __nanosleep(1000);
+          }
+        }
+        if (ok) {
+          mbar_expect_tx(op_bar, L::NS * L::OB);
+          tma_load_1d(smem + L::OFF_OP, p.tc_op, L::NS * L::OB, op_bar);
+          for (; issued < niter && issued < S; ++issued) issue(issued);
+        }
+        // outputs of block jj leave by bulk stores, one bulk group per block
+        // (empty for a short block, whose epilogue writes global memory); the
+        // stage of block jj - 1 is refilled once that block's stores have read
+        // it, so the warp never waits for the stores it has just issued
+        for (int jj = 0; ok && jj < niter; ++jj) {
+          const int s = jj % S;
+          ok = mbar_wait_or_abort(&out_ready[s], static_cast<uint32_t>((jj / S) & 1), abort_flag);
+          if (!ok) break;
+          int k0, nv;
+          block_at(jj, k0, nv);
+          if (nv == E) {
+            const float* sq = reinterpret_cast<const float*>(stages + s * L::STAGE_BYTES);
+            if (MODE == kModeRhs) {
+#pragma unroll
+              for (int f = 0; f < 3; ++f)
+                tma_store_1d(p.rhs + f * fs + k0 * Np, sq + f * E * Np, L::QB);
+            } else {
+#pragma unroll
+              for (int f = 0; f < 3; ++f) {
+                tma_store_1d(p.qout + f * fs + k0 * Np, sq + f * E * Np, L::QB);
+                tma_store_1d(p.res + f * fs + k0 * Np, sq + (3 + f) * E * Np, L::QB);
+              }
+            }
+          }
+          bulk_commit();
+          if (jj >= 1 && issued < niter) {  // issued == jj - 1 + S: the stage of block jj - 1
+            bulk_wait_read_but_last();
+            fence_proxy_async();
+            issue(issued);
+            ++issued;
+          }
+        }
+        if (!ok) {
+          fail();
+          // let this CTA's loads in flight land (each wait bounded)
+          for (int jj = (issued > S ? issued - S : 0); jj < issued; ++jj)
+            mbar_wait_bounded(&full[jj % S], static_cast<uint32_t>((jj / S) & 1), kWaitLimitNs);
+        }
+        bulk_wait_all();
+      }
     }
   } else if (warp == L::MMA_WARP) {
     // ======================= MMA warp: 2 x (KP / 8) tcgen05.mma per block (lane 0)
@@ -660,7 +755,7 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
       float* Fb = Fs + (j & 1) * (L::FB / 4);
       // ---- upwind flux at every face node -> Fb[c][e][j], scaled by Fscale/2
       if constexpr (PAIRS) {
-  #pragma unroll
+#pragma unroll
         for (int u = 0; u < TPT; ++u) {
           const int ee = task_e[u];
           if (ee < nvalid) {
@@ -671,9 +766,9 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
             // (each side with its own geometry and its own flux slot)
             const int eP = code >= 0 ? (code >> 3) - k0 : -1;
             bool pair = eP >= 0 && eP < nvalid && eP != ee;
-  #ifdef DGW_DEVICE_CHECKS
+#ifdef DGW_DEVICE_CHECKS
             pair = pair && nbr_code_ok(code, fs, Np);  // the gather flagged a bad code
-  #endif
+#endif
             if (pair && eP < ee) continue;  // the neighbour's task writes this slot
             const float hxM = sq[nM], hyM = sq[E * Np + nM], ezM = sq[2 * E * Np + nM];
             float hxP, hyP, ezP;
@@ -727,7 +822,7 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
           }
         }
       } else {
-  #pragma unroll
+#pragma unroll
         for (int u = 0; u < TPT; ++u) {
           const int ee = task_e[u];
           if (ee < nvalid) {
@@ -961,7 +1056,7 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
           float* rq = sq + c * E * Np + e * Np;
           float* rr = sres + c * E * Np + e * Np;
           const f32x2 a2 = f32x2_dup(p.a), b2 = f32x2_dup(p.b), dt2 = f32x2_dup(drow);
-  #pragma unroll
+#pragma unroll
           for (int n = 0; n + 1 < Np; n += 2) {
             if (MODE == kModeRhs) {
               rq[n] = MEDIA ? srow * acc[n] : acc[n];
@@ -1000,7 +1095,7 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
           // does not depend on the block it falls in
           const int off = c * E * Np + e * Np;
           const int64_t g = static_cast<int64_t>(c) * fs + static_cast<int64_t>(k0 + e) * Np;
-  #pragma unroll
+#pragma unroll
           for (int n = 0; n < Np; ++n) {
             if (MODE == kModeRhs) {
               p.rhs[g + n] = MEDIA ? srow * acc[n] : acc[n];
