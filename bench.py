@@ -908,6 +908,7 @@ def run_batched(args):
         got = B.get_fields(slot).astype(np.float64)
         diff = max(diff, float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-30)))
     cta, nblk, cost = B.plan()
+    mode, tuned_split_ms, tuned_conc_ms = B.launch_mode()
     B.close()
     for s in solvers:
         s.close()
@@ -941,7 +942,12 @@ def run_batched(args):
                    "per_order_K": {str(N): int(Ks[Ns == N].sum()) for N in sorted(set(Ns.tolist()))},
                    "orders": sorted(set(Ns.tolist())), "wave_speeds": [0.5, 1.0, 2.0],
                    "seed": args.batch_seed, "products": "tensor cores (tcgen05, 3xTF32)",
-                   "graph": "one-step CUDA graphs (5 stage launches)"},
+                   "graph": "one-step CUDA graphs (concurrent mode: each order's 5 stage "
+                            "launches on its own branch, then the step counter; split mode: 5 "
+                            "stage launches over all orders, then the step counter)"},
+        "launch_mode": {"chosen": mode, "tuned_split_ms": tuned_split_ms,
+                        "tuned_concurrent_ms": tuned_conc_ms,
+                        "how": "dg_batch_tune: 3 stage launches in each mode, the faster kept"},
         "plan": {"cta_per_order": {str(g + 1): int(cta[g]) for g in range(7) if nblk[g]},
                  "blocks_per_order": {str(g + 1): int(nblk[g]) for g in range(7) if nblk[g]},
                  "cost_us_per_block_iter": {str(g + 1): float(cost[g]) * 1e6 for g in range(7)

@@ -500,6 +500,14 @@ dg_status dg_batch_tune(dg_batch* batch, int32_t reps, void* stream);
  * are skipped.                                                             */
 dg_status dg_batch_plan(const dg_batch* batch, int32_t* cta, int64_t* nblocks, double* cost);
 
+/* dg_batch_launch_mode: the batch's current launch mode (DG_BATCH_MODE_*)
+ * and the last dg_batch_tune timings of `reps` stage launches in each mode
+ * (0 before any tuning; the split time is that of the tuned split).      */
+#define DG_BATCH_MODE_CONCURRENT 0
+#define DG_BATCH_MODE_SPLIT 1
+dg_status dg_batch_launch_mode(const dg_batch* batch, int32_t* mode, double* split_ms,
+                               double* concurrent_ms);
+
 /* The planner on its own (host only): CTAs per order for block counts
  * nblocks[7] and per-block costs cost[7] on num_ctas CTAs.  Every order with
  * blocks gets one CTA; each further CTA goes to the order with the largest

@@ -34,7 +34,8 @@ __all__ = [
     "dg_checkpoint_save", "dg_checkpoint_load",
     "dg_batch_create", "dg_batch_destroy", "dg_batch_add", "dg_batch_remove", "dg_batch_info",
     "dg_batch_set_fields", "dg_batch_get_fields", "dg_batch_step", "dg_batch_tune",
-    "dg_batch_plan", "dg_batch_plan_ctas", "dg_batch_sync_check", "dg_batch_launch_count",
+    "dg_batch_plan", "dg_batch_plan_ctas", "dg_batch_launch_mode", "dg_batch_sync_check",
+    "dg_batch_launch_count",
     "dg_server_clock", "dg_server_create", "dg_server_destroy", "dg_server_submit",
     "dg_server_wait", "dg_server_info", "dg_server_release", "dg_server_cancel", "dg_server_stats",
     "dg_server_set_work_limit",
@@ -368,6 +369,14 @@ def dg_batch_plan_ctas(nblocks, cost, num_ctas):
     _lib.check(_lib.load().dg_batch_plan_ctas(_ptr(nb), _ptr(c), num_ctas, _ptr(out)),
                "dg_batch_plan_ctas")
     return out
+
+
+def dg_batch_launch_mode(batch):
+    """("concurrent" | "split", tuned split ms, tuned concurrent ms)."""
+    m, a, c = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+    _lib.check(_lib.load().dg_batch_launch_mode(batch, ctypes.byref(m), ctypes.byref(a),
+                                                ctypes.byref(c)), "dg_batch_launch_mode")
+    return ("split" if m.value == _lib.DG_BATCH_MODE_SPLIT else "concurrent", a.value, c.value)
 
 
 def dg_batch_sync_check(batch, stream=None):
@@ -721,6 +730,9 @@ class Batch:
 
     def plan(self):
         return dg_batch_plan(self.batch)
+
+    def launch_mode(self):
+        return dg_batch_launch_mode(self.batch)
 
     def sync_check(self, stream=None):
         dg_batch_sync_check(self.batch, stream)

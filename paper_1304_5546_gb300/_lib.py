@@ -39,6 +39,7 @@ DG_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 DG_BATCH_NO_GRAPH = 1
 DG_BATCH_NO_ADAPT = 2
 DG_BATCH_SPLIT = 4
+DG_BATCH_MODE_CONCURRENT, DG_BATCH_MODE_SPLIT = 0, 1
 DG_SERVER_SEQUENTIAL = 1
 DG_REQUEST_QUEUED, DG_REQUEST_RUNNING, DG_REQUEST_DONE, DG_REQUEST_FAILED = 0, 1, 2, 3
 DG_REQUEST_CANCELLED = 4
@@ -116,6 +117,7 @@ SIGNATURES = [
     ("dg_batch_tune", c_i32, [c_void_p, c_i32, c_void_p]),
     ("dg_batch_plan", c_i32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("dg_batch_plan_ctas", c_i32, [c_void_p, c_void_p, c_i32, c_void_p]),
+    ("dg_batch_launch_mode", c_i32, [c_void_p, P(c_i32), P(c_dbl), P(c_dbl)]),
     ("dg_batch_sync_check", c_i32, [c_void_p, c_void_p]),
     ("dg_batch_launch_count", c_i64, [c_void_p]),
     ("dg_server_clock", c_dbl, []),

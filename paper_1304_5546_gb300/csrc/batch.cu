@@ -1031,6 +1031,16 @@ extern "C" dg_status dg_batch_plan(const dg_batch* b, int32_t* cta, int64_t* nbl
   return DG_OK;
 }
 
+extern "C" dg_status dg_batch_launch_mode(const dg_batch* b, int32_t* mode, double* split_ms,
+                                          double* concurrent_ms) {
+  dgw::clear_error();
+  if (!b) return fail(DG_ERR_ARG, "dg_batch_launch_mode: NULL batch");
+  if (mode) *mode = b->concurrent ? DG_BATCH_MODE_CONCURRENT : DG_BATCH_MODE_SPLIT;
+  if (split_ms) *split_ms = b->tuned_split_ms;
+  if (concurrent_ms) *concurrent_ms = b->tuned_concurrent_ms;
+  return DG_OK;
+}
+
 extern "C" dg_status dg_batch_sync_check(dg_batch* b, void* stream) {
   dgw::clear_error();
   dg_status st = check_batch(b, "dg_batch_sync_check");

@@ -276,12 +276,19 @@ def test_tune_picks_a_launch_mode_and_keeps_results(P, problems):
         s = b.add(p.solver, p.dt)
         b.set_fields(s, p.q0)
         slots.append(s)
+    assert b.launch_mode() == ("concurrent", 0.0, 0.0)  # the default, untuned
     b.tune(reps=2)
+    mode, split_ms, conc_ms = b.launch_mode()
+    assert split_ms > 0 and conc_ms > 0
+    assert mode == ("concurrent" if conc_ms <= split_ms else "split")
     b.step(2)
     b.sync_check()
     for p, s in zip(problems, slots):
         assert _rel(b.get_fields(s), p.oracle(2)) <= TOL
     b.close()
+    forced = P.Batch(_capacity(problems), split=True)
+    assert forced.launch_mode()[0] == "split"
+    forced.close()
 
 
 def test_online_split_adaptation_keeps_results(P, problems):
