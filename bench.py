@@ -909,6 +909,7 @@ def run_batched(args):
         diff = max(diff, float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-30)))
     cta, nblk, cost = B.plan()
     mode, tuned_split_ms, tuned_conc_ms = B.launch_mode()
+    elems, ms_def, ms_alt = B.block_elems()
     B.close()
     for s in solvers:
         s.close()
@@ -948,6 +949,9 @@ def run_batched(args):
         "launch_mode": {"chosen": mode, "tuned_split_ms": tuned_split_ms,
                         "tuned_concurrent_ms": tuned_conc_ms,
                         "how": "dg_batch_tune: 3 stage launches in each mode, the faster kept"},
+        "block_elems": {str(g + 1): {"elems": int(elems[g]), "tuned_ms_default": float(ms_def[g]),
+                                     "tuned_ms_alternative": float(ms_alt[g])}
+                        for g in range(7) if nblk[g]},
         "plan": {"cta_per_order": {str(g + 1): int(cta[g]) for g in range(7) if nblk[g]},
                  "blocks_per_order": {str(g + 1): int(nblk[g]) for g in range(7) if nblk[g]},
                  "cost_us_per_block_iter": {str(g + 1): float(cost[g]) * 1e6 for g in range(7)

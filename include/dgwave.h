@@ -266,18 +266,40 @@ dg_status dg_get_geometry(const dg_op* op, double* rx, double* ry, double* sx,
  * face node; boundary face nodes have vmapP = vmapM).                     */
 dg_status dg_get_maps(const dg_op* op, int64_t* vmapM, int64_t* vmapP);
 
-/* dg_operator_tune: the kernel choice of an FP32 operator, by measurement.
- * Times `reps` stage launches of the tensor-core kernel and of the
- * CUDA-core kernel on the operator's own mesh (scratch fields, allocated
- * and freed here; synchronises `stream`) and keeps the faster for later
- * calls; writes the milliseconds per launch of each (NULL outputs skipped).
- * Operators whose set-up fixed the kernel (FP64, DG_SETUP_SIMT,
- * DG_SETUP_TC, DG_SETUP_TC_*) are left as they are and get -1.  Call it
- * before stepping, not while calls on the operator are in flight.
+/* dg_operator_tune: the kernel and element-block size of an FP32 operator,
+ * by measurement.  Times `reps` stage launches of each candidate on the
+ * operator's own mesh (scratch fields, allocated and freed here; synchronises
+ * `stream`) and keeps the fastest for later calls.  The candidates are:
+ *   - the tensor-core kernel (3xTF32) in its default element-block size;
+ *   - the same in its alternative size where there is one (40 elements at
+ *     N = 1..3, where the default is 80; 80 at N = 4, where it is 40);
+ *   - the CUDA-core kernel, unless DG_SETUP_TC.
+ * Writes the milliseconds per launch of the fastest tensor-core candidate
+ * and of the CUDA-core kernel (NULL outputs skipped; -1 where not timed).
+ * Operators whose set-up fixed the kernel and products (FP64,
+ * DG_SETUP_SIMT, DG_SETUP_TC_*) are left as they are.  dg_operator_kernel
+ * reports the choice.  Call it before stepping, not while calls on the
+ * operator are in flight.
  * Errors: DG_ERR_ARG (NULL, reps < 1), DG_ERR_NO_DEVICE, DG_ERR_OOM,
  * DG_ERR_CUDA.                                                             */
 dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, double* ms_tc,
                            double* ms_cuda_cores);
+
+/* dg_operator_set_block_elems: the element-block size of the operator's
+ * kernel for later calls: 0 or the default size, or the tensor-core
+ * kernel's alternative size where it has one (3xTF32 products; see
+ * dg_operator_tune).  The blocks are a kernel's unit of work: each CTA of
+ * the persistent launch walks blocks of this many consecutive elements.
+ * Results do not depend on the size beyond rounding.  With face pairs on,
+ * the default size is used.
+ * Errors: DG_ERR_ARG (NULL, a size the operator's kernel does not have). */
+dg_status dg_operator_set_block_elems(dg_op* op, int32_t elems);
+
+/* dg_operator_kernel: the kernel the operator's hot-path calls run
+ * (DG_KERNEL_*) and its elements per block.  Errors: DG_ERR_ARG (NULL).  */
+#define DG_KERNEL_TENSOR_CORES 0
+#define DG_KERNEL_CUDA_CORES 1
+dg_status dg_operator_kernel(const dg_op* op, int32_t* kernel, int32_t* elems);
 
 /* CFL time step: cfl * (2/3) * min over elements of the inradius *
  * (spacing of the first two Gauss-Lobatto points of order N).             */
@@ -507,6 +529,23 @@ dg_status dg_batch_plan(const dg_batch* batch, int32_t* cta, int64_t* nblocks, d
 #define DG_BATCH_MODE_SPLIT 1
 dg_status dg_batch_launch_mode(const dg_batch* batch, int32_t* mode, double* split_ms,
                                double* concurrent_ms);
+
+/* dg_batch_set_block_elems: the element-block size of order N's kernel in
+ * the concurrent launch mode: 0 or the default, or the alternative where
+ * the order has one (40 at N = 1..3, where the default is 80; 80 at N = 4,
+ * where it is 40).  The block tables are rebuilt and the step graphs
+ * captured again before the next dg_batch_step.  dg_batch_tune chooses the
+ * size per order by measurement (in the concurrent mode).
+ * Errors: DG_ERR_ARG (no pool for N, a size order N does not have, the
+ * alternative in the split mode).                                          */
+dg_status dg_batch_set_block_elems(dg_batch* batch, int32_t N, int32_t elems);
+
+/* dg_batch_block_elems: elems[N-1] = order N's elements per block (0 where
+ * the batch has no pool), and the last dg_batch_tune timings of `reps`
+ * stage launches of the order alone in its default and alternative size
+ * (ms_default / ms_alt, 7 values each, may be NULL; 0 where not timed).   */
+dg_status dg_batch_block_elems(const dg_batch* batch, int32_t* elems, double* ms_default,
+                               double* ms_alt);
 
 /* The planner on its own (host only): CTAs per order for block counts
  * nblocks[7] and per-block costs cost[7] on num_ctas CTAs.  Every order with

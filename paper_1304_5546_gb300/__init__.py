@@ -24,7 +24,8 @@ from ._lib import (  # noqa: F401
 __all__ = [
     "dg_mesh_create", "dg_mesh_info", "dg_mesh_connectivity", "dg_mesh_destroy",
     "dg_operator_setup", "dg_operator_setup_media", "dg_operator_set_alpha",
-    "dg_operator_set_face_pairs", "dg_operator_set_source", "dg_operator_tune",
+    "dg_operator_set_face_pairs", "dg_operator_set_source", "dg_operator_set_block_elems",
+    "dg_operator_kernel", "dg_operator_tune",
     "dg_get_info", "dg_get_nodes", "dg_get_reference",
     "dg_get_geometry", "dg_get_maps", "dg_cfl_dt", "dg_lsrk_coefficients",
     "dg_op_destroy", "dg_rhs", "dg_step", "dg_step_static", "dg_solve", "dg_step_host",
@@ -34,7 +35,8 @@ __all__ = [
     "dg_checkpoint_save", "dg_checkpoint_load",
     "dg_batch_create", "dg_batch_destroy", "dg_batch_add", "dg_batch_remove", "dg_batch_info",
     "dg_batch_set_fields", "dg_batch_get_fields", "dg_batch_step", "dg_batch_tune",
-    "dg_batch_plan", "dg_batch_plan_ctas", "dg_batch_launch_mode", "dg_batch_sync_check",
+    "dg_batch_plan", "dg_batch_plan_ctas", "dg_batch_launch_mode", "dg_batch_set_block_elems",
+    "dg_batch_block_elems", "dg_batch_sync_check",
     "dg_batch_launch_count",
     "dg_server_clock", "dg_server_create", "dg_server_destroy", "dg_server_submit",
     "dg_server_wait", "dg_server_info", "dg_server_release", "dg_server_cancel", "dg_server_stats",
@@ -126,6 +128,19 @@ def dg_operator_set_source(op, source):
     """source: None (remove) or (x, y, f, t0, amplitude) of a Ricker point source."""
     src = None if source is None else ctypes.byref(_lib.dg_point_source(*[float(v) for v in source]))
     _lib.check(_lib.load().dg_operator_set_source(op, src), "dg_operator_set_source")
+
+
+def dg_operator_set_block_elems(op, elems):
+    _lib.check(_lib.load().dg_operator_set_block_elems(op, int(elems)),
+               "dg_operator_set_block_elems")
+
+
+def dg_operator_kernel(op):
+    """("tensor cores" | "cuda cores", elements per block)."""
+    k, e = ctypes.c_int32(), ctypes.c_int32()
+    _lib.check(_lib.load().dg_operator_kernel(op, ctypes.byref(k), ctypes.byref(e)),
+               "dg_operator_kernel")
+    return ("cuda cores" if k.value == _lib.DG_KERNEL_CUDA_CORES else "tensor cores", e.value)
 
 
 def dg_operator_tune(op, reps=5, stream=None):
@@ -377,6 +392,21 @@ def dg_batch_launch_mode(batch):
     _lib.check(_lib.load().dg_batch_launch_mode(batch, ctypes.byref(m), ctypes.byref(a),
                                                 ctypes.byref(c)), "dg_batch_launch_mode")
     return ("split" if m.value == _lib.DG_BATCH_MODE_SPLIT else "concurrent", a.value, c.value)
+
+
+def dg_batch_set_block_elems(batch, N, elems):
+    _lib.check(_lib.load().dg_batch_set_block_elems(batch, int(N), int(elems)),
+               "dg_batch_set_block_elems")
+
+
+def dg_batch_block_elems(batch):
+    """(elements per block, tuned ms default, tuned ms alternative), 7 each."""
+    e = np.zeros(DG_N_MAX, np.int32)
+    md = np.zeros(DG_N_MAX, np.float64)
+    ma = np.zeros(DG_N_MAX, np.float64)
+    _lib.check(_lib.load().dg_batch_block_elems(batch, _ptr(e), _ptr(md), _ptr(ma)),
+               "dg_batch_block_elems")
+    return e, md, ma
 
 
 def dg_batch_sync_check(batch, stream=None):
@@ -657,8 +687,12 @@ class Solver:
         return dg_checkpoint_load(self.op, path, q, self.fstride)
 
     def tune(self, reps=5, stream=None):
-        """Pick the faster FP32 kernel for this mesh (dg_operator_tune)."""
+        """Pick the fastest FP32 kernel and block size for this mesh (dg_operator_tune)."""
         return dg_operator_tune(self.op, reps, stream)
+
+    def kernel(self):
+        """(kernel, elements per block) the hot-path calls run."""
+        return dg_operator_kernel(self.op)
 
     def nodes(self):
         return dg_get_nodes(self.op)
@@ -733,6 +767,12 @@ class Batch:
 
     def launch_mode(self):
         return dg_batch_launch_mode(self.batch)
+
+    def set_block_elems(self, N, elems):
+        dg_batch_set_block_elems(self.batch, N, elems)
+
+    def block_elems(self):
+        return dg_batch_block_elems(self.batch)
 
     def sync_check(self, stream=None):
         dg_batch_sync_check(self.batch, stream)

@@ -40,6 +40,7 @@ DG_BATCH_NO_GRAPH = 1
 DG_BATCH_NO_ADAPT = 2
 DG_BATCH_SPLIT = 4
 DG_BATCH_MODE_CONCURRENT, DG_BATCH_MODE_SPLIT = 0, 1
+DG_KERNEL_TENSOR_CORES, DG_KERNEL_CUDA_CORES = 0, 1
 DG_SERVER_SEQUENTIAL = 1
 DG_REQUEST_QUEUED, DG_REQUEST_RUNNING, DG_REQUEST_DONE, DG_REQUEST_FAILED = 0, 1, 2, 3
 DG_REQUEST_CANCELLED = 4
@@ -80,6 +81,8 @@ SIGNATURES = [
     ("dg_operator_set_alpha", c_i32, [c_void_p, c_dbl]),
     ("dg_operator_set_face_pairs", c_i32, [c_void_p, c_i32]),
     ("dg_operator_set_source", c_i32, [c_void_p, c_void_p]),
+    ("dg_operator_set_block_elems", c_i32, [c_void_p, c_i32]),
+    ("dg_operator_kernel", c_i32, [c_void_p, P(c_i32), P(c_i32)]),
     ("dg_operator_tune", c_i32, [c_void_p, c_i32, c_void_p, P(c_dbl), P(c_dbl)]),
     ("dg_get_info", c_i32, [c_void_p, P(c_i32), P(c_i32), P(c_i64), P(c_i64)]),
     ("dg_get_nodes", c_i32, [c_void_p, c_void_p, c_void_p]),
@@ -118,6 +121,8 @@ SIGNATURES = [
     ("dg_batch_plan", c_i32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("dg_batch_plan_ctas", c_i32, [c_void_p, c_void_p, c_i32, c_void_p]),
     ("dg_batch_launch_mode", c_i32, [c_void_p, P(c_i32), P(c_dbl), P(c_dbl)]),
+    ("dg_batch_set_block_elems", c_i32, [c_void_p, c_i32, c_i32]),
+    ("dg_batch_block_elems", c_i32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("dg_batch_sync_check", c_i32, [c_void_p, c_void_p]),
     ("dg_batch_launch_count", c_i64, [c_void_p]),
     ("dg_server_clock", c_dbl, []),

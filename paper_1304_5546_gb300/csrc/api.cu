@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -325,7 +326,31 @@ dgw::StageArgs<T> base_args(const dg_op* op) {
   a.tc_op = op->d_tcop;
   a.alpha = static_cast<T>(op->alpha);
   a.face_pairs = op->face_pairs;
+  a.tc_alt = op->tc_alt;
   return a;
+}
+
+// The 3xTF32 tensor-core kernel of order N has an alternative element-block
+// size (tc_tiles, launch.h).
+bool tc_has_alt_n(int N) {
+  switch (N) {
+    case 1: return dgw::tc_has_alt(1, dgw::kTcTf32x3);
+    case 2: return dgw::tc_has_alt(2, dgw::kTcTf32x3);
+    case 3: return dgw::tc_has_alt(3, dgw::kTcTf32x3);
+    case 4: return dgw::tc_has_alt(4, dgw::kTcTf32x3);
+    case 5: return dgw::tc_has_alt(5, dgw::kTcTf32x3);
+    case 6: return dgw::tc_has_alt(6, dgw::kTcTf32x3);
+    case 7: return dgw::tc_has_alt(7, dgw::kTcTf32x3);
+    default: return false;
+  }
+}
+
+// Elements per block of the kernel the operator runs (alt: the alternative
+// size of the tensor-core kernel).
+int block_elems(const dg_op* op, int alt) {
+  if (op->precision == DG_FP32 && op->use_tc)
+    return 40 * dgw::tc_tiles(op->N, op->tc_prec, alt != 0 && op->tc_prec == dgw::kTcTf32x3);
+  return dgw::simt_block_elems(op->N, op->precision == DG_FP64);
 }
 
 dg_status check_device_op(const dg_op* op, const char* where) {
@@ -704,9 +729,19 @@ extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, dou
   if (reps < 1) return fail(DG_ERR_ARG, "dg_operator_tune: reps = %d < 1", reps);
   if (ms_tc) *ms_tc = -1.0;
   if (ms_cuda_cores) *ms_cuda_cores = -1.0;
-  const int32_t forced = DG_SETUP_SIMT | DG_SETUP_TC | DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 |
-                         DG_SETUP_TC_BF16X3;
-  if (op->precision != DG_FP32 || (op->flags & forced)) return DG_OK;  // nothing to choose
+  const int32_t fixed = DG_SETUP_SIMT | DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 | DG_SETUP_TC_BF16X3;
+  if (op->precision != DG_FP32 || (op->flags & fixed)) return DG_OK;  // nothing to choose
+  // candidates: tensor cores (3xTF32) in the default and, where there is one,
+  // the alternative element-block size; the CUDA cores unless DG_SETUP_TC
+  struct Cand {
+    bool tc;
+    int alt;
+  } cand[3];
+  int nc = 0;
+  cand[nc++] = {true, 0};
+  if (tc_has_alt_n(op->N)) cand[nc++] = {true, 1};
+  if (!(op->flags & DG_SETUP_TC)) cand[nc++] = {false, 0};
+  if (nc < 2) return DG_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t err = cudaSuccess;
   if (!op->d_tcop) {  // the tensor-core kernel's operator tiles
@@ -716,7 +751,7 @@ extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, dou
       err = cudaMemcpy(op->d_tcop, tiles.data(), tiles.size(), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return cuda_fail(err, "dg_operator_tune: operator tiles");
   }
-  // scratch fields q, q_out and res (zero), stage-2 launches of each kernel
+  // scratch fields q, q_out and res (zero), stage-2 launches of each candidate
   const size_t fb = 3 * static_cast<size_t>(op->fstride) * sizeof(float);
   float* buf = nullptr;
   err = dgw::dev_malloc(reinterpret_cast<void**>(&buf), 3 * fb);
@@ -725,20 +760,22 @@ extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, dou
     if (buf) cudaFree(buf);
     return cuda_fail(err, "dg_operator_tune: scratch fields");
   }
-  dgw::StageArgs<float> a = base_args<float>(op);
-  a.qin = buf;
-  a.qout = buf + 3 * op->fstride;
-  a.res = buf + 6 * op->fstride;
-  a.a = static_cast<float>(op->lsrk_a[1]);
-  a.b = static_cast<float>(op->lsrk_b[1]);
-  a.dt = 1e-6f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const bool was_tc = op->use_tc;
-  float ms[2] = {0.f, 0.f};
-  for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
-    op->use_tc = (v == 0);
+  const int was_alt = op->tc_alt;
+  float ms[3] = {0.f, 0.f, 0.f};
+  for (int v = 0; v < nc && err == cudaSuccess; ++v) {
+    op->use_tc = cand[v].tc;
+    op->tc_alt = cand[v].alt;
+    dgw::StageArgs<float> a = base_args<float>(op);
+    a.qin = buf;
+    a.qout = buf + 3 * op->fstride;
+    a.res = buf + 6 * op->fstride;
+    a.a = static_cast<float>(op->lsrk_a[1]);
+    a.b = static_cast<float>(op->lsrk_b[1]);
+    a.dt = 1e-6f;
     err = launch_order<float>(op, a, dgw::kModeStage, s);  // warm
     if (err == cudaSuccess) err = cudaEventRecord(e0, s);
     for (int r = 0; r < reps && err == cudaSuccess; ++r)
@@ -750,14 +787,51 @@ extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, dou
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(buf);
-  op->launches.fetch_add(2 * (reps + 1), std::memory_order_relaxed);
+  op->launches.fetch_add(nc * (reps + 1), std::memory_order_relaxed);
   if (err != cudaSuccess) {
     op->use_tc = was_tc;
+    op->tc_alt = was_alt;
     return cuda_fail(err, "dg_operator_tune");
   }
-  op->use_tc = ms[0] <= ms[1];
-  if (ms_tc) *ms_tc = ms[0] / reps;
-  if (ms_cuda_cores) *ms_cuda_cores = ms[1] / reps;
+  int best = 0;
+  for (int v = 1; v < nc; ++v)
+    if (ms[v] < ms[best]) best = v;
+  op->use_tc = cand[best].tc;
+  op->tc_alt = cand[best].alt;
+  double best_tc = -1.0;
+  for (int v = 0; v < nc; ++v) {
+    if (cand[v].tc && (best_tc < 0 || ms[v] < best_tc)) best_tc = ms[v];
+    if (!cand[v].tc && ms_cuda_cores) *ms_cuda_cores = ms[v] / reps;
+  }
+  if (ms_tc) *ms_tc = best_tc / reps;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_operator_set_block_elems(dg_op* op, int32_t elems) {
+  dgw::clear_error();
+  const char* where = "dg_operator_set_block_elems";
+  if (!op) return fail(DG_ERR_ARG, "%s: NULL operator", where);
+  const bool alt_ok = op->precision == DG_FP32 && op->use_tc && op->tc_prec == dgw::kTcTf32x3 &&
+                      tc_has_alt_n(op->N);
+  const int def = block_elems(op, 0), alt = alt_ok ? block_elems(op, 1) : def;
+  if (elems == 0 || elems == def) {
+    op->tc_alt = 0;
+  } else if (alt_ok && elems == alt) {
+    op->tc_alt = 1;
+  } else {
+    return fail(DG_ERR_ARG, "%s: %d elements per block is not a size of this operator's kernel "
+                "(%d%s%s)", where, elems, def, alt_ok ? " or " : "",
+                alt_ok ? std::to_string(alt).c_str() : "");
+  }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_operator_kernel(const dg_op* op, int32_t* kernel, int32_t* elems) {
+  dgw::clear_error();
+  if (!op) return fail(DG_ERR_ARG, "dg_operator_kernel: NULL operator");
+  const bool tc = op->precision == DG_FP32 && op->use_tc;
+  if (kernel) *kernel = tc ? DG_KERNEL_TENSOR_CORES : DG_KERNEL_CUDA_CORES;
+  if (elems) *elems = block_elems(op, op->tc_alt && !op->face_pairs);
   return DG_OK;
 }
 

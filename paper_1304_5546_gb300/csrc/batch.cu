@@ -31,6 +31,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -51,6 +52,7 @@ dg_status cuda_fail(cudaError_t err, const char* where) {
 
 struct Pool {
   int N = 0, Np = 0, E = 0;
+  bool alt = false;  // concurrent mode: the order's alternative block size (E follows)
   int64_t cap = 0;      // element capacity
   int64_t fstride = 0;  // values between fields
   float* q[2] = {nullptr, nullptr};
@@ -105,6 +107,7 @@ struct dg_batch {
   // launch per stage, its CTAs split among the orders)
   bool concurrent = true;
   float tuned_split_ms = 0.f, tuned_concurrent_ms = 0.f;  // dg_batch_tune's last timings
+  float tuned_order_ms[kOrders][2] = {};  // per order: default, alternative block size
   cudaStream_t ostream[kOrders] = {};
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[kOrders] = {};
@@ -340,10 +343,15 @@ cudaError_t launch_order_stage(dg_batch* b, int g, int src, int stage, int grid,
   const dgw::StageArgs<float>& ga = a.g[g];
   const bool first = stage == 0;
   cudaError_t err = cudaErrorInvalidValue;
+  const bool alt = b->pools[g].alt;
 #define DG_ORDER_CASE(NN_)                                                                 \
   case NN_:                                                                                \
-    err = first ? dgw::launch_batch_order<NN_, dgw::kModeFirstStage>(ga, grid, s)          \
-                : dgw::launch_batch_order<NN_, dgw::kModeStage>(ga, grid, s);              \
+    if (alt)                                                                               \
+      err = first ? dgw::launch_batch_order<NN_, dgw::kModeFirstStage, true>(ga, grid, s)  \
+                  : dgw::launch_batch_order<NN_, dgw::kModeStage, true>(ga, grid, s);      \
+    else                                                                                   \
+      err = first ? dgw::launch_batch_order<NN_, dgw::kModeFirstStage>(ga, grid, s)        \
+                  : dgw::launch_batch_order<NN_, dgw::kModeStage>(ga, grid, s);            \
     break;
   switch (g + 1) {
     DG_ORDER_CASE(1)
@@ -472,6 +480,21 @@ dg_status capture_graphs(dg_batch* b) {
     if (err != cudaSuccess) return cuda_fail(err, "dg_batch_step: graph capture");
   }
   return DG_OK;
+}
+
+// Order g's block size: the default, or (alt) its alternative.  The block
+// tables are rebuilt before the next launch, and the step graphs, which hold
+// the order's kernel, are captured again.
+void set_order_alt(dg_batch* b, int g, bool alt) {
+  Pool& p = b->pools[g];
+  if (p.alt == alt) return;
+  p.alt = alt;
+  p.E = dgw::batch_tc_block_elems(g + 1, alt);
+  b->dirty = true;
+  for (cudaGraphExec_t& ge : b->graph) {
+    if (ge) cudaGraphExecDestroy(ge);
+    ge = nullptr;
+  }
 }
 
 // kernel launches of one step in the batch's mode (stages and the tick)
@@ -1009,6 +1032,38 @@ extern "C" dg_status dg_batch_tune(dg_batch* b, int32_t reps, void* stream) {
       b->tuned_concurrent_ms = conc_ms;
     }
   }
+  if (err == cudaSuccess && !b->concurrent) {  // the split mode runs the default block sizes
+    for (int g = 0; g < kOrders; ++g) set_order_alt(b, g, false);
+    if (b->dirty && upload_tables(b, s) != DG_OK) err = cudaErrorUnknown;
+  }
+  // 5. concurrent mode: each order's element-block size, the default against
+  //    the alternative where there is one, each timed alone on all SMs over
+  //    the order's own blocks (tables rebuilt for each size); the faster kept
+  for (int g = 0; g < kOrders && err == cudaSuccess && b->concurrent; ++g) {
+    if (b->nblk[g] == 0 || dgw::batch_tc_block_elems(g + 1, true) == dgw::batch_tc_block_elems(g + 1, false))
+      continue;
+    float t[2] = {0.f, 0.f};
+    for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+      set_order_alt(b, g, v == 1);
+      if (upload_tables(b, s) != DG_OK) {
+        err = cudaErrorUnknown;
+        break;
+      }
+      err = launch_order_stage(b, g, b->cur, 1, b->num_sms, s);  // warm
+      if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+      for (int r = 0; r < reps && err == cudaSuccess; ++r)
+        err = launch_order_stage(b, g, b->cur, 1, b->num_sms, s);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&t[v], e0, e1);
+    }
+    if (err == cudaSuccess) {
+      set_order_alt(b, g, t[1] < t[0]);
+      b->tuned_order_ms[g][0] = t[0];
+      b->tuned_order_ms[g][1] = t[1];
+      if (b->dirty && upload_tables(b, s) != DG_OK) err = cudaErrorUnknown;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err != cudaSuccess) return cuda_fail(err, "dg_batch_tune: plan upload / launch mode");
@@ -1038,6 +1093,39 @@ extern "C" dg_status dg_batch_launch_mode(const dg_batch* b, int32_t* mode, doub
   if (mode) *mode = b->concurrent ? DG_BATCH_MODE_CONCURRENT : DG_BATCH_MODE_SPLIT;
   if (split_ms) *split_ms = b->tuned_split_ms;
   if (concurrent_ms) *concurrent_ms = b->tuned_concurrent_ms;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_batch_set_block_elems(dg_batch* b, int32_t N, int32_t elems) {
+  dgw::clear_error();
+  const char* where = "dg_batch_set_block_elems";
+  dg_status st = check_batch(b, where);
+  if (st) return st;
+  if (N < 1 || N > kOrders || b->pools[N - 1].cap == 0)
+    return fail(DG_ERR_ARG, "%s: the batch has no pool for order N = %d", where, N);
+  const int def = dgw::batch_tc_block_elems(N, false), alt = dgw::batch_tc_block_elems(N, true);
+  if (elems == 0 || elems == def) {
+    set_order_alt(b, N - 1, false);
+  } else if (elems == alt && alt != def) {
+    if (!b->concurrent)
+      return fail(DG_ERR_ARG, "%s: the split launch mode runs the default size (%d)", where, def);
+    set_order_alt(b, N - 1, true);
+  } else {
+    return fail(DG_ERR_ARG, "%s: %d elements per block is not a size of order %d (%d%s)", where,
+                elems, N, def, alt != def ? (" or " + std::to_string(alt)).c_str() : "");
+  }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_batch_block_elems(const dg_batch* b, int32_t* elems, double* ms_default,
+                                          double* ms_alt) {
+  dgw::clear_error();
+  if (!b || !elems) return fail(DG_ERR_ARG, "dg_batch_block_elems: NULL argument");
+  for (int g = 0; g < kOrders; ++g) {
+    elems[g] = b->pools[g].cap > 0 ? b->pools[g].E : 0;
+    if (ms_default) ms_default[g] = b->tuned_order_ms[g][0];
+    if (ms_alt) ms_alt[g] = b->tuned_order_ms[g][1];
+  }
   return DG_OK;
 }
 

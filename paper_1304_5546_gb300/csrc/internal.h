@@ -109,6 +109,7 @@ struct dg_op {
   // flux parameter of Eq. max2d-numflux: 1 upwind (default), 0 central
   double alpha = 1.0;
   int face_pairs = 0;  // dg_operator_set_face_pairs
+  int tc_alt = 0;      // the tensor-core kernel's alternative block size (dg_operator_set_block_elems)
   // Ricker point source (dg_operator_set_source): element src_k, projected
   // point load in d_src_w (Np values of the field precision)
   bool has_src = false;

@@ -51,16 +51,10 @@ struct Order {
   static constexpr int Nafp = 3 * (N + 1);
 };
 
-// Elements per block.  A multiple of 4, so every per-block chunk (E Np
-// values, E geometry records, E face-code triples) is a whole number of
-// 16-byte units as TMA requires; E Np <= 512 from N = 4 on, because ptxas
-// budgets registers for the CTA rounded up to 4 warps and each thread needs
-// 2 Np + Nafp registers for its matrix rows.
+// Elements per block: simt_block_elems (launch.h, with the reasons).
 template <typename T, int N>
 constexpr int elems_per_block() {
-  constexpr int e32[8] = {0, 64, 32, 32, 32, 24, 16, 12};
-  constexpr int e64[8] = {0, 32, 16, 16, 16, 12, 8, 8};
-  return sizeof(T) == 8 ? e64[N] : e32[N];
+  return simt_block_elems(N, sizeof(T) == 8);
 }
 
 constexpr int kStages = 3;

@@ -5,30 +5,41 @@
 
 namespace dgw {
 
-size_t batch_tc_smem_bytes(int N) {
+size_t batch_tc_smem_bytes(int N, bool alt) {
+#define DG_SMEM_CASE(NN_)                                                           \
+  case NN_:                                                                         \
+    return alt ? TcLayout<NN_, kTcTf32x3, true, true>::SMEM_BYTES                   \
+               : TcLayout<NN_, kTcTf32x3, true>::SMEM_BYTES;
   switch (N) {
-    case 1: return TcLayout<1, kTcTf32x3, true>::SMEM_BYTES;
-    case 2: return TcLayout<2, kTcTf32x3, true>::SMEM_BYTES;
-    case 3: return TcLayout<3, kTcTf32x3, true>::SMEM_BYTES;
-    case 4: return TcLayout<4, kTcTf32x3, true>::SMEM_BYTES;
-    case 5: return TcLayout<5, kTcTf32x3, true>::SMEM_BYTES;
-    case 6: return TcLayout<6, kTcTf32x3, true>::SMEM_BYTES;
-    case 7: return TcLayout<7, kTcTf32x3, true>::SMEM_BYTES;
+    DG_SMEM_CASE(1)
+    DG_SMEM_CASE(2)
+    DG_SMEM_CASE(3)
+    DG_SMEM_CASE(4)
+    DG_SMEM_CASE(5)
+    DG_SMEM_CASE(6)
+    DG_SMEM_CASE(7)
     default: return 0;
   }
+#undef DG_SMEM_CASE
 }
 
-int batch_tc_block_elems(int N) {
+// elements per block; alt: the alternative size (the default where an order
+// has none)
+int batch_tc_block_elems(int N, bool alt) {
+#define DG_ELEMS_CASE(NN_)                                                          \
+  case NN_:                                                                         \
+    return alt ? TcLayout<NN_, kTcTf32x3, true, true>::E : TcLayout<NN_, kTcTf32x3, true>::E;
   switch (N) {
-    case 1: return TcLayout<1, kTcTf32x3, true>::E;
-    case 2: return TcLayout<2, kTcTf32x3, true>::E;
-    case 3: return TcLayout<3, kTcTf32x3, true>::E;
-    case 4: return TcLayout<4, kTcTf32x3, true>::E;
-    case 5: return TcLayout<5, kTcTf32x3, true>::E;
-    case 6: return TcLayout<6, kTcTf32x3, true>::E;
-    case 7: return TcLayout<7, kTcTf32x3, true>::E;
+    DG_ELEMS_CASE(1)
+    DG_ELEMS_CASE(2)
+    DG_ELEMS_CASE(3)
+    DG_ELEMS_CASE(4)
+    DG_ELEMS_CASE(5)
+    DG_ELEMS_CASE(6)
+    DG_ELEMS_CASE(7)
     default: return 0;
   }
+#undef DG_ELEMS_CASE
 }
 
 template cudaError_t launch_batch_tc<kModeFirstStage>(const BatchArgs&, int, size_t, cudaStream_t);

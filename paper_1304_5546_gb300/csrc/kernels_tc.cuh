@@ -59,7 +59,7 @@
 
 namespace dgw {
 
-template <int N, int PREC_, bool MEDIA_ = false>
+template <int N, int PREC_, bool MEDIA_ = false, bool ALT_ = false>
 struct TcLayout {
   static constexpr int PREC = PREC_;
   static constexpr bool MEDIA = MEDIA_;
@@ -74,16 +74,11 @@ struct TcLayout {
   static constexpr int KG = KP * EB / 16;       // core matrices along K
   static constexpr int XPART = BF ? KP / 2 : KP;  // TMEM columns of one X part
   static constexpr int NN = tc_nn(N);
-  // GEMM row tiles of 128 TMEM lanes per block: two at N <= 3, where two
-  // tiles' double-buffered operands and (split) accumulators fit the 512
-  // columns and the stage ring still fits shared memory, so that a block of
-  // 80 elements shares the per-block hand-offs (measured: N = 3 0.86 ->
-  // 0.65 ms/step, N = 2 1.31 -> 0.83; N = 4, which also fits, 0.65 -> 0.68)
-  static constexpr int TILES =
-      (N <= 3 &&
-       2 * 2 * (tc_nsplit(PREC) == 2 ? 2 * NN : NN) + 2 * 2 * tc_nsplit(PREC) * XPART <= 512)
-          ? 2
-          : 1;
+  // GEMM row tiles of 128 TMEM lanes per block (tc_tiles: two at N <= 3,
+  // where two tiles' double-buffered operands and (split) accumulators fit
+  // the 512 columns, one above; ALT_: the other count where both fit).  A
+  // block of 80 elements shares the per-block hand-offs.
+  static constexpr int TILES = tc_tiles(N, PREC_, ALT_);
   static constexpr int E = 40 * TILES;  // 3E <= 128 TILES GEMM rows, E % 4 == 0
   static constexpr int ROWS = 3 * E;
   static constexpr int NPAD = tc_npad(N);
@@ -355,10 +350,10 @@ __device__ __forceinline__ void media_flux(float nx, float ny, float cH, float c
 // both sides, with every flux operation explicitly rounded so that an
 // element's result does not depend on whether its neighbour shares its
 // block); otherwise each side's task computes its own face nodes.
-template <int N, int MODE, int PREC, bool MEDIA, bool TABLE, bool PAIRS = false>
+template <int N, int MODE, int PREC, bool MEDIA, bool TABLE, bool PAIRS = false, bool ALT = false>
 __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const int first,
                                               const int G, unsigned char* smem) {
-  using L = TcLayout<N, PREC, MEDIA>;
+  using L = TcLayout<N, PREC, MEDIA, ALT>;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, E = L::E, S = L::S;
   constexpr int KP = L::KP, NN = L::NN, NPAD = L::NPAD, FES = L::FES, XBUF = L::XBUF;
   constexpr int FT = L::FLUX_THREADS, TASKS = L::TASKS, TPT = L::TPT;
@@ -1128,19 +1123,19 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs<float>& p, const i
   if (warp == 0) tmem_dealloc(tmem, L::TMEM_COLS);
 }
 
-template <int N, int MODE, int PREC, bool MEDIA, bool PAIRS>
-__global__ void __launch_bounds__(TcLayout<N, PREC, MEDIA>::THREADS, 1)
+template <int N, int MODE, int PREC, bool MEDIA, bool PAIRS, bool ALT>
+__global__ void __launch_bounds__(TcLayout<N, PREC, MEDIA, ALT>::THREADS, 1)
     dg_stage_tc_kernel(const __grid_constant__ StageArgs<float> p) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  tc_stage_body<N, MODE, PREC, MEDIA, false, PAIRS>(p, blockIdx.x, gridDim.x, smem);
+  tc_stage_body<N, MODE, PREC, MEDIA, false, PAIRS, ALT>(p, blockIdx.x, gridDim.x, smem);
 }
 
-template <int N, int MODE, int PREC, bool MEDIA, bool PAIRS>
+template <int N, int MODE, int PREC, bool MEDIA, bool PAIRS, bool ALT>
 cudaError_t launch_stage_tc_mode(const StageArgs<float>& args, int num_sms, cudaStream_t stream) {
-  using L = TcLayout<N, PREC, MEDIA>;
+  using L = TcLayout<N, PREC, MEDIA, ALT>;
   static std::atomic<uint64_t> configured{0};
   cudaError_t err = configure_once_per_device(configured, [] {
-    return cudaFuncSetAttribute(dg_stage_tc_kernel<N, MODE, PREC, MEDIA, PAIRS>,
+    return cudaFuncSetAttribute(dg_stage_tc_kernel<N, MODE, PREC, MEDIA, PAIRS, ALT>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(L::SMEM_BYTES));
   });
@@ -1149,29 +1144,35 @@ cudaError_t launch_stage_tc_mode(const StageArgs<float>& args, int num_sms, cuda
   int64_t grid = num_sms;  // one CTA per SM (shared memory and TMEM sized for it)
   if (grid > nblk) grid = nblk;
   if (grid < 1) grid = 1;
-  dg_stage_tc_kernel<N, MODE, PREC, MEDIA, PAIRS>
+  dg_stage_tc_kernel<N, MODE, PREC, MEDIA, PAIRS, ALT>
       <<<static_cast<unsigned>(grid), L::THREADS, L::SMEM_BYTES, stream>>>(args);
   return cudaGetLastError();
 }
 
-template <int N, int PREC, bool MEDIA, bool PAIRS>
+template <int N, int PREC, bool MEDIA, bool PAIRS, bool ALT = false>
 cudaError_t launch_stage_tc_modes(const StageArgs<float>& args, int mode, int num_sms,
                                   cudaStream_t stream) {
   if (mode == kModeRhs)
-    return launch_stage_tc_mode<N, kModeRhs, PREC, MEDIA, PAIRS>(args, num_sms, stream);
+    return launch_stage_tc_mode<N, kModeRhs, PREC, MEDIA, PAIRS, ALT>(args, num_sms, stream);
   if (mode == kModeFirstStage)
-    return launch_stage_tc_mode<N, kModeFirstStage, PREC, MEDIA, PAIRS>(args, num_sms, stream);
-  return launch_stage_tc_mode<N, kModeStage, PREC, MEDIA, PAIRS>(args, num_sms, stream);
+    return launch_stage_tc_mode<N, kModeFirstStage, PREC, MEDIA, PAIRS, ALT>(args, num_sms, stream);
+  return launch_stage_tc_mode<N, kModeStage, PREC, MEDIA, PAIRS, ALT>(args, num_sms, stream);
 }
 
-// face pairs (args.face_pairs) exist for the 3xTF32 products, the FP32 path's
-// default; the other product variants compute every face node per side
+// face pairs (args.face_pairs) and the alternative block size (args.tc_alt)
+// exist for the 3xTF32 products, the FP32 path's default; the other product
+// variants compute every face node per side in blocks of the default size.
+// With both set, face pairs run with the default block size.
 template <int N, int PREC, bool MEDIA>
 cudaError_t launch_stage_tc_any(const StageArgs<float>& args, int mode, int num_sms,
                                 cudaStream_t stream) {
   if constexpr (PREC == kTcTf32x3) {
     if (args.face_pairs)
       return launch_stage_tc_modes<N, PREC, MEDIA, true>(args, mode, num_sms, stream);
+    if constexpr (tc_has_alt(N, PREC)) {
+      if (args.tc_alt)
+        return launch_stage_tc_modes<N, PREC, MEDIA, false, true>(args, mode, num_sms, stream);
+    }
   }
   return launch_stage_tc_modes<N, PREC, MEDIA, false>(args, mode, num_sms, stream);
 }
@@ -1244,28 +1245,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // side and the hardware gives SMs to whichever has CTAs waiting.  CTAs past
 // the order's block count (read from device memory, so that a captured
 // graph replays unchanged when problems join or leave) return at once.
-template <int N, int MODE>
+template <int N, int MODE, bool ALT>
 __global__ void __launch_bounds__(kTcThreads, 1)
     dg_batch_order_kernel(const __grid_constant__ StageArgs<float> g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   if (static_cast<int>(blockIdx.x) >= __ldg(g.nblocks)) return;
-  static_assert(TcLayout<N, kTcTf32x3, true>::THREADS == kTcThreads, "block size");
-  tc_stage_body<N, MODE, kTcTf32x3, true, true>(g, blockIdx.x, gridDim.x, smem);
+  static_assert(TcLayout<N, kTcTf32x3, true, ALT>::THREADS == kTcThreads, "block size");
+  tc_stage_body<N, MODE, kTcTf32x3, true, true, false, ALT>(g, blockIdx.x, gridDim.x, smem);
 }
 
-template <int N, int MODE>
+// ALT: the order's alternative block size (tc_tiles(N, prec, true)); the
+// block table must hold blocks of at most that many elements
+template <int N, int MODE, bool ALT>
 cudaError_t launch_batch_order(const StageArgs<float>& g, int grid, cudaStream_t stream) {
-  using L = TcLayout<N, kTcTf32x3, true>;
-  static std::atomic<uint64_t> configured{0};
-  cudaError_t err = configure_once_per_device(configured, [] {
-    return cudaFuncSetAttribute(dg_batch_order_kernel<N, MODE>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(L::SMEM_BYTES));
-  });
-  if (err != cudaSuccess) return err;
-  if (grid < 1) return cudaSuccess;
-  dg_batch_order_kernel<N, MODE><<<grid, kTcThreads, L::SMEM_BYTES, stream>>>(g);
-  return cudaGetLastError();
+  if constexpr (ALT && !tc_has_alt(N, kTcTf32x3)) {
+    return cudaErrorInvalidValue;
+  } else {
+    using L = TcLayout<N, kTcTf32x3, true, ALT>;
+    static std::atomic<uint64_t> configured{0};
+    cudaError_t err = configure_once_per_device(configured, [] {
+      return cudaFuncSetAttribute(dg_batch_order_kernel<N, MODE, ALT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(L::SMEM_BYTES));
+    });
+    if (err != cudaSuccess) return err;
+    if (grid < 1) return cudaSuccess;
+    dg_batch_order_kernel<N, MODE, ALT><<<grid, kTcThreads, L::SMEM_BYTES, stream>>>(g);
+    return cudaGetLastError();
+  }
 }
 
 template <int MODE>

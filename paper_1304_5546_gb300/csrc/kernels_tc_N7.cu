@@ -1,6 +1,7 @@
 // Order-7 instantiations of the FP32 tensor-core stage kernel with 3xTF32
-// products: uniform medium, per-element permittivity, and the order's kernel
-// of the concurrent batched launch.
+// products: uniform medium, per-element permittivity (each with its
+// alternative element-block size where there is one), and the order's
+// kernels of the concurrent batched launch.
 #include "kernels_tc.cuh"
 
 namespace dgw {
@@ -8,4 +9,8 @@ template cudaError_t launch_stage_tc<7, kTcTf32x3>(const StageArgs<float>&, int,
 template cudaError_t launch_stage_tc_media<7>(const StageArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_batch_order<7, kModeFirstStage>(const StageArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_batch_order<7, kModeStage>(const StageArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_batch_order<7, kModeFirstStage, true>(const StageArgs<float>&, int,
+                                                                   cudaStream_t);
+template cudaError_t launch_batch_order<7, kModeStage, true>(const StageArgs<float>&, int,
+                                                              cudaStream_t);
 }  // namespace dgw

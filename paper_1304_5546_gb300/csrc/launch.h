@@ -46,6 +46,17 @@ __host__ __device__ constexpr bool block_ok(int k0, int n, int E, int64_t fstrid
   return k0 >= 0 && n >= 1 && n <= E && (static_cast<int64_t>(k0) + n) * Np <= fstride;
 }
 
+// Elements per block of the CUDA-core stage kernel (kernels.cuh): a multiple
+// of 4, so every per-block chunk (E Np values, E geometry records, E
+// face-code triples) is a whole number of 16-byte units as TMA requires;
+// E Np <= 512 from N = 4 on, because ptxas budgets registers for the CTA
+// rounded up to 4 warps and each thread needs 2 Np + Nafp registers for its
+// matrix rows.
+__host__ __device__ constexpr int simt_block_elems(int N, bool fp64) {
+  return fp64 ? (N == 1 ? 32 : N <= 4 ? 16 : N == 5 ? 12 : 8)
+              : (N == 1 ? 64 : N <= 4 ? 32 : N == 5 ? 24 : N == 6 ? 16 : 12);
+}
+
 // geometry record per element: rx ry sx sy, then per face nx ny Fscale/2
 constexpr int kGeo = 13;
 
@@ -90,6 +101,9 @@ struct StageArgs {
   // tensor-core kernel: compute the flux of a face whose two elements lie in
   // the same block once, for both sides (0: every face node per side)
   int face_pairs = 0;
+  // tensor-core kernel with 3xTF32 products: the alternative element-block
+  // size (tc_tiles(N, prec, true)) instead of the default; chosen on the host
+  int tc_alt = 0;
   int* status = nullptr;  // set to 1 by a CTA whose bounded wait expired
   // timeout test only (tensor-core kernel): the memory warp first waits,
   // bounded by kGateLimitNs, for *stall_gate to become non-zero; NULL
@@ -170,6 +184,26 @@ __host__ __device__ constexpr int tc_nsplit(int prec) {
 __host__ __device__ constexpr int tc_kpp(int N, int prec) {
   return tc_is_bf16(prec) ? (tc_kd(N) + 15) / 16 * 16 : tc_kp(N);
 }
+// Two 128-row GEMM tiles per element block fit the 512 tensor-memory
+// columns: both tiles' double-buffered accumulators (split: two operator
+// tiles' columns) and double-buffered operands (the X parts of the variant).
+__host__ __device__ constexpr bool tc_two_tiles_fit(int N, int prec) {
+  return 2 * 2 * (tc_nsplit(prec) == 2 ? 2 * tc_nn(N) : tc_nn(N)) +
+             2 * 2 * tc_nsplit(prec) * (tc_is_bf16(prec) ? tc_kpp(N, prec) / 2 : tc_kpp(N, prec)) <=
+         512;
+}
+// Row tiles of an element block (40 elements per tile).  The default is two
+// tiles at N <= 3 where they fit (measured faster there: N = 3 0.86 -> 0.65
+// ms/step, N = 2 1.31 -> 0.83) and one above (N = 4, which also fits two,
+// measured 0.65 -> 0.68 with two).  alt: the other count where both fit,
+// for the autotuner (dg_operator_tune, dg_batch_tune) to try on a live mesh.
+__host__ __device__ constexpr int tc_tiles(int N, int prec, bool alt) {
+  return (N <= 3 && tc_two_tiles_fit(N, prec)) ? (alt ? 1 : 2)
+                                               : ((alt && tc_two_tiles_fit(N, prec)) ? 2 : 1);
+}
+__host__ __device__ constexpr bool tc_has_alt(int N, int prec) {
+  return tc_tiles(N, prec, true) != tc_tiles(N, prec, false);
+}
 
 template <int N, int PREC>
 cudaError_t launch_stage_tc(const StageArgs<float>& args, int mode, int num_sms,
@@ -204,10 +238,11 @@ cudaError_t launch_batch_tc(const BatchArgs& args, int grid, size_t smem, cudaSt
 // The concurrent mode of the batched launch: order N's share of a stage as a
 // kernel of its own, `grid` CTAs (one per SM) over its block table
 // (g.blocks, g.nblocks); grid 0 only configures the kernel.
-template <int N, int MODE>
+template <int N, int MODE, bool ALT = false>
 cudaError_t launch_batch_order(const StageArgs<float>& g, int grid, cudaStream_t stream);
 // shared memory and elements per block of order N's CTA in the batched launch
-size_t batch_tc_smem_bytes(int N);
-int batch_tc_block_elems(int N);
+// (alt: the alternative block size of the concurrent mode's kernels)
+size_t batch_tc_smem_bytes(int N, bool alt = false);
+int batch_tc_block_elems(int N, bool alt = false);
 
 }  // namespace dgw

@@ -291,6 +291,61 @@ def test_tune_picks_a_launch_mode_and_keeps_results(P, problems):
     forced.close()
 
 
+def test_alternative_block_sizes_match_oracle(P, problems):
+    # concurrent mode: N = 3 in 40-element blocks (default 80); the other
+    # orders keep theirs; N = 5 has one size only
+    steps = 3
+    b = P.Batch(_capacity(problems))
+    slots = []
+    for p in problems:
+        s = b.add(p.solver, p.dt)
+        b.set_fields(s, p.q0)
+        slots.append(s)
+    b.set_block_elems(3, 40)
+    with pytest.raises(P.DGError):
+        b.set_block_elems(5, 80)
+    e = b.block_elems()[0]
+    assert e[2] == 40 and e[4] == 40 and e[6] == 40 and e[0] == 80
+    b.step(steps)
+    b.sync_check()
+    for p, s in zip(problems, slots):
+        assert _rel(b.get_fields(s), p.oracle(steps)) <= TOL, p.N
+    b.set_block_elems(3, 0)
+    assert b.block_elems()[0][2] == 80
+    b.close()
+    split = P.Batch(_capacity(problems), split=True)
+    with pytest.raises(P.DGError):
+        split.set_block_elems(3, 40)
+    split.close()
+
+
+def test_tune_records_block_sizes(P, problems):
+    b = P.Batch(_capacity(problems))
+    slots = []
+    for p in problems:
+        s = b.add(p.solver, p.dt)
+        b.set_fields(s, p.q0)
+        slots.append(s)
+    b.tune(reps=2)
+    elems, ms_def, ms_alt = b.block_elems()
+    mode = b.launch_mode()[0]
+    for N in range(1, 8):
+        if elems[N - 1] == 0:
+            continue
+        sizes = {1: (80, 40), 2: (80, 40), 3: (80, 40), 4: (40, 80)}.get(N, (40,))
+        assert elems[N - 1] in sizes
+        if mode == "concurrent" and len(sizes) == 2:
+            assert ms_def[N - 1] > 0 and ms_alt[N - 1] > 0
+            assert elems[N - 1] == (sizes[1] if ms_alt[N - 1] < ms_def[N - 1] else sizes[0])
+        if mode == "split":
+            assert elems[N - 1] == sizes[0]
+    b.step(2)
+    b.sync_check()
+    for p, s in zip(problems, slots):
+        assert _rel(b.get_fields(s), p.oracle(2)) <= TOL
+    b.close()
+
+
 def test_online_split_adaptation_keeps_results(P, problems):
     # split mode, 20 steps: the split is re-planned from clock snapshots along
     # the way; which CTA computes a block never changes a result

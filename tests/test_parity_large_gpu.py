@@ -38,7 +38,8 @@ from synth import jittered_delaunay_mesh, random_fields, random_permittivity
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp32tc": 1e-5, "fp32simt": 1e-5, "fp32pairs": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp32tc": 1e-5, "fp32simt": 1e-5, "fp32pairs": 1e-5,
+       "fp32alt": 1e-5}
 U = {"tf32": 2.0 ** -11, "bf16": 2.0 ** -8, "bf16x3": 2.0 ** -16}
 
 
@@ -82,13 +83,18 @@ class _Case:
         return O.maxwell_rhs_media(self.d, u, self.eps)
 
     def solver(self, P, prec):
-        # "fp32pairs": the tensor-core kernel with face pairs on
-        pairs = prec == "fp32pairs"
-        s = P.Solver(*self.mesh, N=self.N, precision="fp32tc" if pairs else prec, eps=self.eps)
+        # "fp32pairs": the tensor-core kernel with face pairs on; "fp32alt":
+        # the tensor-core kernel in its alternative element-block size
+        special = prec in ("fp32pairs", "fp32alt")
+        s = P.Solver(*self.mesh, N=self.N, precision="fp32tc" if special else prec, eps=self.eps)
         if self.alpha != 1.0:
             P.dg_operator_set_alpha(s.op, self.alpha)
-        if pairs:
+        if prec == "fp32pairs":
             P.dg_operator_set_face_pairs(s.op, 1)
+        if prec == "fp32alt":
+            alt = 40 if self.N <= 3 else 80
+            P.dg_operator_set_block_elems(s.op, alt)
+            assert s.kernel() == ("tensor cores", alt)
         return s
 
     def want(self, dt):
@@ -141,12 +147,13 @@ def test_mesh_sizes_walk_many_blocks_per_cta():
 
 # the CUDA-core kernel serves every FP32 order with "fp32simt", N = 1 by
 # default ("fp32"); "fp32tc" forces the tensor cores at every order
-# ("fp32pairs": with face pairs, dg_operator_set_face_pairs); FP64
+# ("fp32pairs": with face pairs, dg_operator_set_face_pairs; "fp32alt": in
+# the alternative block size at N <= 4, dg_operator_set_block_elems); FP64
 # (CUDA cores) at N = 3, 5, 7.  Ordered by N so that one oracle case serves
 # all of an order's runs.
 _UNIFORM = [(N, prec) for N in range(1, 8)
             for prec in ("fp32", "fp32tc", "fp32pairs", "fp32simt")
-            + (("fp64",) if N in (3, 5, 7) else ())]
+            + (("fp32alt",) if N <= 4 else ()) + (("fp64",) if N in (3, 5, 7) else ())]
 
 
 @pytest.mark.parametrize("N,prec", _UNIFORM)
@@ -158,8 +165,12 @@ def test_large_uniform_rhs_and_two_steps(P, N, prec):
     assert _rel(got, want_q) <= TOL[prec], ("2 steps", _rel(got, want_q))
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp32pairs", "fp32simt", "fp64"])
-@pytest.mark.parametrize("N", [3, 7])
+_MEDIA = [(N, prec) for N in (3, 7)
+          for prec in ("fp32", "fp32pairs") + (("fp32alt",) if N <= 4 else ())
+          + ("fp32simt", "fp64")]
+
+
+@pytest.mark.parametrize("N,prec", _MEDIA)
 def test_large_media_rhs_and_two_steps(P, N, prec):
     case = _case(("media", N), N, seed=600 + N, eps_seed=700 + N)
     rhs, got, dt = _run(P, case, prec)
@@ -225,8 +236,8 @@ class _Problem:
         return q
 
 
-@pytest.mark.parametrize("split", [True, False])
-def test_large_batch_of_three_orders(P, split):
+@pytest.mark.parametrize("split,alt3", [(True, False), (False, False), (False, True)])
+def test_large_batch_of_three_orders(P, split, alt3):
     # split mode: n = 123, K = 30,258 per problem (ragged at E = 40 and 80);
     # the planner splits the 152 CTAs over N = 3, 5, 7, so each CTA walks
     # about ten blocks of its order.  Concurrent mode: every order's kernel
@@ -239,6 +250,8 @@ def test_large_batch_of_three_orders(P, split):
     for p in probs:
         cap[p.N - 1] += (p.d.K + 3) // 4 * 4
     b = P.Batch(cap, split=split)
+    if alt3:  # N = 3 in 40-element blocks: 2,443 blocks, 16 per CTA
+        b.set_block_elems(3, 40)
     slots = []
     for p in probs:
         slot = b.add(p.solver, p.dt, source=p.source)
