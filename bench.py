@@ -239,6 +239,48 @@ def replica_throughput(world, K, steps, ms):
 
 
 # ------------------------------------------------------------- our arm
+def measure_host_link(nbytes, dev, reps=5, rounds=4):
+    """Host <-> device copy bandwidth of pinned memory through torch copies
+    (copy engines): host to device alone, device to host alone, and both at
+    once on two streams; `rounds` copies of `nbytes` per direction, GB/s of
+    the bytes moved, best of `reps`."""
+    import torch
+    h_in = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d_in = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d_out = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
+    main = torch.cuda.current_stream(dev)
+    sa, sb = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def timed(h2d, d2h):
+        best = float("inf")
+        for r in range(reps + 1):
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(main)
+            sa.wait_stream(main)
+            sb.wait_stream(main)
+            for _ in range(rounds):
+                if h2d:
+                    with torch.cuda.stream(sa):
+                        d_in.copy_(h_in, non_blocking=True)
+                if d2h:
+                    with torch.cuda.stream(sb):
+                        h_out.copy_(d_out, non_blocking=True)
+            main.wait_stream(sa)
+            main.wait_stream(sb)
+            e1.record(main)
+            e1.synchronize()
+            if r > 0:
+                best = min(best, e0.elapsed_time(e1))
+        return rounds * (h2d + d2h) * nbytes / (best / 1e3) / 1e9
+
+    out = {"h2d_gbs": timed(1, 0), "d2h_gbs": timed(0, 1), "both_gbs": timed(1, 1)}
+    del h_in, h_out, d_in, d_out
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -321,6 +363,8 @@ def run_ours(args):
         P.dg_step_host(s.op, h, dq, dres, 0.0, dt, 1)
     e2e_serial_s = time.perf_counter() - t0
     barrier()
+    field_bytes = 3 * s.fstride * (8 if args.precision == "fp64" else 4)
+    link = measure_host_link(field_bytes, dev)
 
     ms, e2e_s, e2e_serial_s = max_over_ranks([ms, e2e_s, e2e_serial_s], dist, device="cuda")
     if rank != 0:
@@ -391,10 +435,21 @@ def run_ours(args):
                    "device -> host; one job's copies overlap the neighbouring jobs' steps",
             "serial": {"value": replica_throughput(world, K, e2e_steps, e2e_serial_s * 1e3),
                        "api": "dg_step_host, one job at a time (copy in, step, copy out)"},
+            # the end-to-end bound: a step cannot take less than its copies
+            # at the host link's two-way rate, nor less than the device step
+            "host_link": dict(link, **{
+                "bound_value": replica_throughput(
+                    world, K, 1, 1e3 * max(2 * field_bytes / (link["both_gbs"] * 1e9),
+                                           ms / args.steps / 1e3)),
+                "how": "pinned torch copies of one job's fields (copy engines), 4 per direction, best of 5; "
+                       "bound = K * 5 / max(copy-in + copy-out bytes / two-way GB/s, "
+                       "device ms per step)"}),
         },
         "gpu_launches": launches,
         "clocks": clk,
     }
+    hl = out["e2e"]["host_link"]
+    hl["frac"] = out["e2e"]["value"] / hl["bound_value"]
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     if world == 1 and not args.no_workloads:
