@@ -110,6 +110,10 @@ struct TcLayout {
   // alone at N = 1, 2 and 4 (where several issuing lanes measured 4-6 %
   // slower)
   static constexpr bool IO_LANES = N == 3 || N >= 5;
+  // widest tcgen05.st of an operand-row run (columns): 8 (1-4 % faster than
+  // 4 at every order on GB300), 16 at N = 7 (where it measured faster
+  // still; at N = 6 it was slower than 8)
+  static constexpr int ST_W = N == 7 ? 16 : 8;
   static constexpr int FLUX_WARP0 = EPI_WARPS + X_WARPS;
   static constexpr int MMA_WARP = FLUX_WARP0 + FLUX_WARPS, IO_WARP = MMA_WARP + 1;
   static constexpr int THREADS = 32 * (IO_WARP + 1);
@@ -215,6 +219,62 @@ __device__ __forceinline__ void x_emit4(uint32_t xh, uint32_t xl, int k0, float 
   }
 }
 
+// Eight (sixteen) consecutive K columns from k0 as in x_emit4, in one
+// tcgen05.st per part.
+template <class L>
+__device__ __forceinline__ void x_emit8(uint32_t xh, uint32_t xl, int k0, const float* v) {
+  if constexpr (L::PREC == kTcTf32x3) {
+    float h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+      const f32x2 p = f32x2_pack(v[i], v[i + 1]);
+      const f32x2 hh = f32x2_tf32_trunc(p);
+      f32x2_unpack(hh, h[i], h[i + 1]);
+      f32x2_unpack(f32x2_sub(p, hh), l[i], l[i + 1]);
+    }
+    tmem_st8(xh + k0, h);
+    tmem_st8(xl + k0, l);
+  } else {
+    x_emit4<L>(xh, xl, k0, v[0], v[1], v[2], v[3]);
+    x_emit4<L>(xh, xl, k0 + 4, v[4], v[5], v[6], v[7]);
+  }
+}
+
+template <class L>
+__device__ __forceinline__ void x_emit16(uint32_t xh, uint32_t xl, int k0, const float* v) {
+  if constexpr (L::PREC == kTcTf32x3) {
+    float h[16], l[16];
+#pragma unroll
+    for (int i = 0; i < 16; i += 2) {
+      const f32x2 p = f32x2_pack(v[i], v[i + 1]);
+      const f32x2 hh = f32x2_tf32_trunc(p);
+      f32x2_unpack(hh, h[i], h[i + 1]);
+      f32x2_unpack(f32x2_sub(p, hh), l[i], l[i + 1]);
+    }
+    tmem_st16(xh + k0, h);
+    tmem_st16(xl + k0, l);
+  } else {
+    x_emit8<L>(xh, xl, k0, v);
+    x_emit8<L>(xh, xl, k0 + 8, v + 8);
+  }
+}
+
+// A run of NC chunks of 4 columns (values v[0 .. 4 NC)) from column k0, in
+// stores of at most L::ST_W columns.
+template <class L, int NC>
+__device__ __forceinline__ void x_emit_run(uint32_t xh, uint32_t xl, int k0, const float* v) {
+  constexpr int N16 = L::ST_W >= 16 ? NC / 4 : 0;
+  constexpr int R = NC - 4 * N16, N8 = R / 2, N4 = R % 2;
+#pragma unroll
+  for (int c = 0; c < N16; ++c) x_emit16<L>(xh, xl, k0 + 16 * c, v + 16 * c);
+#pragma unroll
+  for (int c = 0; c < N8; ++c) x_emit8<L>(xh, xl, k0 + 16 * N16 + 8 * c, v + 16 * N16 + 8 * c);
+  if constexpr (N4) {
+    constexpr int o = 16 * N16 + 8 * N8;
+    x_emit4<L>(xh, xl, k0 + o, v[o], v[o + 1], v[o + 2], v[o + 3]);
+  }
+}
+
 // One thread's share of its X row into tensor memory at xh / xl (this warp's
 // lane quarter), in two calls: the volume part, then the LIFT part (which
 // waits for the face fluxes).  Each call computes every value first and then
@@ -269,12 +329,8 @@ __device__ __forceinline__ void build_x_vol(const float* qe, const float* lam, u
       }
     }
     __syncwarp();
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int m0 = 4 * (R::VLO + v);
-      x_emit4<L>(xh, xl, m0, vr[4 * v], vr[4 * v + 1], vr[4 * v + 2], vr[4 * v + 3]);
-      x_emit4<L>(xh, xl, NPAD + m0, vs[4 * v], vs[4 * v + 1], vs[4 * v + 2], vs[4 * v + 3]);
-    }
+    x_emit_run<L, NV>(xh, xl, 4 * R::VLO, vr);
+    x_emit_run<L, NV>(xh, xl, NPAD + 4 * R::VLO, vs);
   }
 }
 
@@ -310,10 +366,7 @@ __device__ __forceinline__ void build_x_lift(const float* fr, uint32_t xh, uint3
         x[v] = lin;
     }
     __syncwarp();
-#pragma unroll
-    for (int v = 0; v < NL; ++v)
-      x_emit4<L>(xh, xl, 2 * NPAD + 4 * (R::LLO + v), x[4 * v], x[4 * v + 1], x[4 * v + 2],
-                 x[4 * v + 3]);
+    x_emit_run<L, NL>(xh, xl, 2 * NPAD + 4 * R::LLO, x);
   }
 }
 
