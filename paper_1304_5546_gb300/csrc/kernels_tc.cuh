@@ -120,7 +120,19 @@ struct TcLayout {
   static constexpr int X_THREADS = 32 * X_WARPS, FLUX_THREADS = 32 * FLUX_WARPS;
   static constexpr int TASKS = E * Nafp;
   static constexpr int TPT = (TASKS + FLUX_THREADS - 1) / FLUX_THREADS;
-  static constexpr int FES = Nafp | 1;  // face-flux row stride, odd: conflict-free row reads
+  // LIFT-part chunks read with one 16-byte load each (N = 3 and 5, where
+  // that measured 0.4-1.5 % faster on GB300; about even elsewhere).  The
+  // face-flux row stride is then 4 x odd words, so that the 16-byte loads of
+  // 8 consecutive rows by a quarter warp fall on distinct banks; otherwise it
+  // is odd, for conflict-free 4-byte row reads.
+  static constexpr bool LIFT_V4 = N == 3 || N == 5;
+  static constexpr int FES = !LIFT_V4                         ? (Nafp | 1)
+                             : ((Nafp + 3) / 4) % 2 == 1      ? (Nafp + 3) / 4 * 4
+                                                              : (Nafp + 3) / 4 * 4 + 4;
+  // deflation of a node pair as one subtraction and two FMAs instead of two
+  // subtractions, a product and an FMA (N = 5 and 6, where that measured
+  // 0.4 % and 5 % faster; 2 % slower at N = 7, even at N <= 4)
+  static constexpr bool DEFL_FMA = N == 5 || N == 6;
   static constexpr int FB = 3 * E * FES * 4;  // one face-flux buffer [3][E][FES]
   static constexpr int QB = E * Np * 4;
   static constexpr int GB = E * GEO * 4;
@@ -143,6 +155,9 @@ struct TcLayout {
   static_assert(S >= 3 && S <= 8, "stage ring / header layout");
   static_assert(SMEM_BYTES <= SMAX, "shared memory");
   static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0 && OB % 16 == 0, "TMA chunks");
+  static_assert(!LIFT_V4 || (FES % 4 == 0 && FES >= (Nafp + 3) / 4 * 4 && OFF_F % 16 == 0 &&
+                             FB % 16 == 0),
+                "16-byte face-flux loads: aligned rows, chunks inside a row");
   static_assert(ROWS <= 128 * TILES && NN <= 256 && NN % 16 == 0 && KP % (BF ? 16 : 8) == 0,
                 "UMMA shape");
   static_assert(LCOLS % 4 == 0 && LCOLS >= Nafp + 1, "LIFT part and linear-part column");
@@ -313,13 +328,23 @@ __device__ __forceinline__ void build_x_vol(const float* qe, const float* lam, u
         const bool in0 = row_ok && m < Np, in1 = row_ok && m + 1 < Np;
         const f32x2 uq = f32x2_pack(in0 ? qe[fu + m] : a1, in1 ? qe[fu + m + 1] : a1);
         f32x2 ud = f32x2_sub(uq, f32x2_dup(a1));
-        ud = f32x2_sub(ud, f32x2_fma(f32x2_dup(a2 - a1), l2, f32x2_mul(f32x2_dup(a3 - a1), l3)));
+        if constexpr (L::DEFL_FMA) {
+          ud = f32x2_fma(f32x2_dup(a1 - a2), l2, ud);
+          ud = f32x2_fma(f32x2_dup(a1 - a3), l3, ud);
+        } else {
+          ud = f32x2_sub(ud, f32x2_fma(f32x2_dup(a2 - a1), l2, f32x2_mul(f32x2_dup(a3 - a1), l3)));
+        }
         f32x2 pr = f32x2_mul(f32x2_dup(rc == 1 ? rx : -ry), ud);
         f32x2 ps = f32x2_mul(f32x2_dup(rc == 1 ? sx : -sy), ud);
         if (rc == 2) {
           const f32x2 wq = f32x2_pack(in0 ? qe[E * Np + m] : b1, in1 ? qe[E * Np + m + 1] : b1);
           f32x2 wd = f32x2_sub(wq, f32x2_dup(b1));
-          wd = f32x2_sub(wd, f32x2_fma(f32x2_dup(b2 - b1), l2, f32x2_mul(f32x2_dup(b3 - b1), l3)));
+          if constexpr (L::DEFL_FMA) {
+            wd = f32x2_fma(f32x2_dup(b1 - b2), l2, wd);
+            wd = f32x2_fma(f32x2_dup(b1 - b3), l3, wd);
+          } else {
+            wd = f32x2_sub(wd, f32x2_fma(f32x2_dup(b2 - b1), l2, f32x2_mul(f32x2_dup(b3 - b1), l3)));
+          }
           pr = f32x2_fma(f32x2_dup(rx), wd, pr);
           ps = f32x2_fma(f32x2_dup(sx), wd, ps);
         }
@@ -356,14 +381,31 @@ __device__ __forceinline__ void build_x_lift(const float* fr, uint32_t xh, uint3
         lin = 0.5f * (rx * (b2 - b1) - ry * (a2 - a1) + sx * (b3 - b1) - sy * (a3 - a1));
       }
     }
+    if constexpr (L::LIFT_V4) {
+      // fr is 16-byte aligned (FES a multiple of 4) and a chunk that starts
+      // below Nafp ends inside the row's FES entries
 #pragma unroll
-    for (int v = 0; v < 4 * NL; ++v) {
-      const int jj = 4 * R::LLO + v;
-      x[v] = 0.f;
-      if (jj < Nafp)
-        x[v] = row_ok ? fr[jj] : 0.f;
-      else if (jj == Nafp)
-        x[v] = lin;
+      for (int c = 0; c < NL; ++c) {
+        const int j0 = 4 * (R::LLO + c);
+        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j0 < Nafp && row_ok) f = *reinterpret_cast<const float4*>(fr + j0);
+        const float fv[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int jj = j0 + i;
+          x[4 * c + i] = jj < Nafp ? fv[i] : (jj == Nafp ? lin : 0.f);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4 * NL; ++v) {
+        const int jj = 4 * R::LLO + v;
+        x[v] = 0.f;
+        if (jj < Nafp)
+          x[v] = row_ok ? fr[jj] : 0.f;
+        else if (jj == Nafp)
+          x[v] = lin;
+      }
     }
     __syncwarp();
     x_emit_run<L, NL>(xh, xl, 2 * NPAD + 4 * R::LLO, x);
