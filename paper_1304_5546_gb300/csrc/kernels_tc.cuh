@@ -133,6 +133,11 @@ struct TcLayout {
   // subtractions, a product and an FMA (N = 5 and 6, where that measured
   // 0.4 % and 5 % faster; 2 % slower at N = 7, even at N <= 4)
   static constexpr bool DEFL_FMA = N == 5 || N == 6;
+  // operand-row field loads without the row-validity predicate (N <= 5,
+  // 0.2-1.3 % faster there; 1 % and 10 % slower at N = 6 and 7): a row that
+  // is not valid reads an address inside the stage buffer, and its values
+  // reach only its own GEMM row, which the epilogue never writes back
+  static constexpr bool ROW_LOADS_UNPRED = N <= 5;
   static constexpr int FB = 3 * E * FES * 4;  // one face-flux buffer [3][E][FES]
   static constexpr int QB = E * Np * 4;
   static constexpr int GB = E * GEO * 4;
@@ -301,9 +306,10 @@ __device__ __forceinline__ void x_emit_run(uint32_t xh, uint32_t xl, int k0, con
 // Volume part: nodes 4ch .. 4ch+3 in pairs (packed FP32x2): deflated u (and
 // w), then the Dr part cr1 u + cr2 w and the Ds part cs1 u + cs2 w with
 // (cr1, cs1, cr2, cs2) = (-ry, -sy, 0, 0), (rx, sx, 0, 0), (-ry, -sy, rx, sx)
-// for output field Hx, Hy, Ez.  Nodes >= Np and rows that are not valid come
-// out exactly zero (u = u1 there, the zero-padded weights, and zero vertex
-// values and factors for invalid rows).
+// for output field Hx, Hy, Ez.  Nodes >= Np come out exactly zero (u = u1
+// there, and the zero-padded weights).  Rows that are not valid have zero
+// vertex values and factors; with L::ROW_LOADS_UNPRED they still read their
+// stage entries, which may hold anything (their GEMM rows are discarded).
 template <int N, class L, int ROLE>
 __device__ __forceinline__ void build_x_vol(const float* qe, const float* lam, uint32_t xh,
                                             uint32_t xl, bool row_ok, int rc, float rx, float ry,
@@ -325,7 +331,8 @@ __device__ __forceinline__ void build_x_vol(const float* qe, const float* lam, u
         const int m = m0 + 2 * pp;
         const f32x2 l2 = pp == 0 ? f32x2_pack(l2v.x, l2v.y) : f32x2_pack(l2v.z, l2v.w);
         const f32x2 l3 = pp == 0 ? f32x2_pack(l3v.x, l3v.y) : f32x2_pack(l3v.z, l3v.w);
-        const bool in0 = row_ok && m < Np, in1 = row_ok && m + 1 < Np;
+        const bool in0 = (L::ROW_LOADS_UNPRED || row_ok) && m < Np;
+        const bool in1 = (L::ROW_LOADS_UNPRED || row_ok) && m + 1 < Np;
         const f32x2 uq = f32x2_pack(in0 ? qe[fu + m] : a1, in1 ? qe[fu + m + 1] : a1);
         f32x2 ud = f32x2_sub(uq, f32x2_dup(a1));
         if constexpr (L::DEFL_FMA) {
