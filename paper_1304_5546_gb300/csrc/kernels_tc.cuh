@@ -101,15 +101,14 @@ struct TcLayout {
   static constexpr int XBUF = TILES * (2 * ACC_COLS + 2 * XCOLS) <= 512 ? 2 : 1;
   static constexpr int OFF_XT = 2 * TILES * ACC_COLS;
   static constexpr int TMEM_COLS = 512;
-  // warp roles: 0-3 epilogue; 4-15 operand rows (warp w serves lane quarter
-  // w % 4 and takes share (w - 4) / 4 of its rows' chunks); 16-19 face flux
+  // warp roles: 0-3 epilogue; 4-11 operand rows (warp w serves lane quarter
+  // w % 4 and takes share (w - 4) / 4 of its rows' chunks); 12-19 face flux
   // and neighbour gathers; 20 MMA; 21 memory
   static constexpr int EPI_WARPS = 4, X_WARPS = 8, FLUX_WARPS = 8;
   // memory warp: the bulk copies of a block issued by several lanes at once
-  // at N = 3 and N >= 5 (measured 2-6 % faster there on GB300), by lane 0
-  // alone at N = 1, 2 and 4 (where several issuing lanes measured 4-6 %
-  // slower)
-  static constexpr bool IO_LANES = N == 3 || N >= 5;
+  // at N >= 5 (2-9 % faster there on GB300), by lane 0 alone at N <= 4
+  // (where several issuing lanes measured 2-6 % slower)
+  static constexpr bool IO_LANES = N >= 5;
   // widest tcgen05.st of an operand-row run (columns): 8 (1-4 % faster than
   // 4 at every order on GB300), 16 at N = 7 (where it measured faster
   // still; at N = 6 it was slower than 8)
