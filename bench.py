@@ -551,8 +551,9 @@ def run_precision_study(args):
 def run_sweep_study(args):
     """Order sweep of the single-mesh path at about 10M nodal values per
     field (K ~ 1e7 / Np): for N = 1..7, the FP32 tensor-core kernel (face
-    pairs off and on: dg_operator_set_face_pairs) and the FP32 CUDA-core
-    kernel, `--study-steps` LSRK steps each timed with CUDA events (the two
+    pairs off and on: dg_operator_set_face_pairs), the FP32 CUDA-core kernel
+    and, at N <= 5, the element-thread kernel (median of three runs),
+    `--study-steps` LSRK steps each timed with CUDA events (the two
     tensor-core settings alternate three times on one operator; medians).
     One JSON line: ms/step, element-stage updates/s, RHS GFLOP/s and
     achieved HBM bandwidth (algorithmic bytes) per order and kernel, and the
@@ -591,16 +592,20 @@ def run_sweep_study(args):
         Np = (N + 1) * (N + 2) // 2
         n = n_for_target_elements(1e7 / Np)
         mesh = jittered_delaunay_mesh(n, seed=2024)
-        for simt in (False, True):
-            s = P.Solver(*mesh, N=N, precision="fp32simt" if simt else "fp32tc")
+        kinds = ("fp32tc", "fp32simt") + (("fp32ept",) if N <= 5 else ())
+        for kind in kinds:
+            s = P.Solver(*mesh, N=N, precision=kind)
             x, y = s.nodes()
             q = s.from_numpy(np.stack(gaussian_pulse(x, y)))
             res = s.new_fields()
             dt = s.cfl_dt()
             s.step(q, res, dt, 3)
             torch.cuda.synchronize()
-            if simt:
+            if kind == "fp32simt":
                 rows.append(row(N, s.K, "cuda cores", timed(s, q, res, dt)))
+            elif kind == "fp32ept":
+                rows.append(row(N, s.K, "element threads",
+                                float(np.median([timed(s, q, res, dt) for _ in range(3)]))))
             else:
                 times = {0: [], 1: []}
                 for _ in range(3):

@@ -113,9 +113,14 @@ typedef struct dg_point_source {
 #define DG_SETUP_TC_BF16 8   /* one product, both operands rounded to BF16   */
 #define DG_SETUP_TC_BF16X3 16 /* three BF16 products: hi/lo split of both
                                  operands (X_hi Op_hi + X_hi Op_lo + X_lo Op_hi) */
-/* Default FP32 products per order: the tensor cores (3xTF32) from N = 2 on,
- * the CUDA cores at N = 1, where that kernel measured faster.  Override:  */
+/* Default FP32 products per order: the element-thread kernel at N <= 2 in a
+ * uniform medium, the tensor cores (3xTF32) otherwise from N = 2 on, the
+ * node-thread CUDA-core kernel at N = 1 with a permittivity -- the fastest
+ * measured at each order.  Overrides:                                     */
 #define DG_SETUP_TC 32       /* FP32: tensor cores (3xTF32) at every order   */
+#define DG_SETUP_ELEMENT_THREADS 64 /* FP32, N <= 5, uniform medium: the CUDA
+                                cores with one thread per element, the
+                                reference matrices as constant operands     */
 
 #define DG_N_MAX 7
 
@@ -158,10 +163,14 @@ void dg_mesh_destroy(dg_mesh* mesh);
  * Surface Contribution"), and the trace maps.  FP32 operators run the
  * element-local products (Dr, Ds, LIFT) on the tensor cores as three TF32
  * products per term (hi/lo splits of both operands, FP32 accumulation) from
- * N = 2 on and on the CUDA cores at N = 1 (DG_SETUP_TC: tensor cores at
- * every order); flags DG_SETUP_SIMT selects the CUDA-core FP32 kernel, and one
- * of DG_SETUP_TC_TF32 / _BF16 / _BF16X3 a lower-precision product variant
- * (the precision path of the element-local contractions).  FP64
+ * N = 3 on (N = 2 with a permittivity), and on the CUDA cores below: one
+ * thread per element in a uniform medium (the element-thread kernel), one
+ * thread per node with a permittivity at N = 1.  DG_SETUP_TC selects the
+ * tensor cores at every order, DG_SETUP_SIMT the node-thread CUDA-core FP32
+ * kernel, DG_SETUP_ELEMENT_THREADS the element-thread kernel (N <= 5,
+ * uniform medium), and one of DG_SETUP_TC_TF32 / _BF16 / _BF16X3 a
+ * lower-precision product variant (the precision path of the element-local
+ * contractions).  FP64
  * operators always use the CUDA cores.  Unless flags has
  * DG_SETUP_HOST_ONLY, device-ready copies are uploaded once, cast to the
  * operator's precision (DG_FP32 or DG_FP64), to the current CUDA device.
@@ -169,6 +178,8 @@ void dg_mesh_destroy(dg_mesh* mesh);
  * destroyed afterwards.
  * Errors: DG_ERR_ARG (unknown flags; more than one product variant, or one
  * with DG_FP64 or DG_SETUP_SIMT; DG_SETUP_TC with DG_FP64 or DG_SETUP_SIMT;
+ * DG_SETUP_ELEMENT_THREADS with DG_FP64, N > 5, a permittivity or another
+ * kernel or product flag;
  * also when a field would hold 2^31 or more values:
  * kernel offsets inside a field are 32-bit), DG_ERR_ORDER (N < 1 or
  * N > DG_N_MAX), DG_ERR_CUDA, DG_ERR_OOM.  *out is written only on success. */
@@ -273,11 +284,13 @@ dg_status dg_get_maps(const dg_op* op, int64_t* vmapM, int64_t* vmapP);
  *   - the tensor-core kernel (3xTF32) in its default element-block size;
  *   - the same in its alternative size where there is one (40 elements at
  *     N = 1..3, where the default is 80; 80 at N = 4, where it is 40);
- *   - the CUDA-core kernel, unless DG_SETUP_TC.
+ *   - unless DG_SETUP_TC, the CUDA cores: the node-thread kernel, and the
+ *     element-thread kernel at N <= 5 in a uniform medium.
  * Writes the milliseconds per launch of the fastest tensor-core candidate
- * and of the CUDA-core kernel (NULL outputs skipped; -1 where not timed).
- * Operators whose set-up fixed the kernel and products (FP64,
- * DG_SETUP_SIMT, DG_SETUP_TC_*) are left as they are.  dg_operator_kernel
+ * and of the fastest CUDA-core candidate (NULL outputs skipped; -1 where not
+ * timed).  Operators whose set-up fixed the kernel and products (FP64,
+ * DG_SETUP_SIMT, DG_SETUP_ELEMENT_THREADS, DG_SETUP_TC_*) are left as they
+ * are.  dg_operator_kernel
  * reports the choice.  Call it before stepping, not while calls on the
  * operator are in flight.
  * Errors: DG_ERR_ARG (NULL, reps < 1), DG_ERR_NO_DEVICE, DG_ERR_OOM,
@@ -296,9 +309,11 @@ dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, double* ms_tc,
 dg_status dg_operator_set_block_elems(dg_op* op, int32_t elems);
 
 /* dg_operator_kernel: the kernel the operator's hot-path calls run
- * (DG_KERNEL_*) and its elements per block.  Errors: DG_ERR_ARG (NULL).  */
+ * (DG_KERNEL_*) and its elements per block (the element-thread kernel: 32,
+ * one per lane of a warp).  Errors: DG_ERR_ARG (NULL).                    */
 #define DG_KERNEL_TENSOR_CORES 0
 #define DG_KERNEL_CUDA_CORES 1
+#define DG_KERNEL_ELEMENT_THREADS 2
 dg_status dg_operator_kernel(const dg_op* op, int32_t* kernel, int32_t* elems);
 
 /* CFL time step: cfl * (2/3) * min over elements of the inradius *

@@ -136,11 +136,13 @@ def dg_operator_set_block_elems(op, elems):
 
 
 def dg_operator_kernel(op):
-    """("tensor cores" | "cuda cores", elements per block)."""
+    """("tensor cores" | "cuda cores" | "element threads", elements per block)."""
     k, e = ctypes.c_int32(), ctypes.c_int32()
     _lib.check(_lib.load().dg_operator_kernel(op, ctypes.byref(k), ctypes.byref(e)),
                "dg_operator_kernel")
-    return ("cuda cores" if k.value == _lib.DG_KERNEL_CUDA_CORES else "tensor cores", e.value)
+    names = {_lib.DG_KERNEL_CUDA_CORES: "cuda cores",
+             _lib.DG_KERNEL_ELEMENT_THREADS: "element threads"}
+    return (names.get(k.value, "tensor cores"), e.value)
 
 
 def dg_operator_tune(op, reps=5, stream=None):
@@ -496,6 +498,7 @@ _FP32_VARIANTS = {
     "fp32": 0,                              # per order: CUDA cores at N = 1, else 3xTF32
     "fp32tc": _lib.DG_SETUP_TC,             # 3xTF32 tensor-core products at every order
     "fp32simt": _lib.DG_SETUP_SIMT,         # CUDA-core FP32 products
+    "fp32ept": _lib.DG_SETUP_ELEMENT_THREADS,  # CUDA cores, one thread per element (N <= 5)
     "tf32": _lib.DG_SETUP_TC_TF32,          # one TF32 product
     "bf16": _lib.DG_SETUP_TC_BF16,          # one BF16 product
     "bf16x3": _lib.DG_SETUP_TC_BF16X3,      # three BF16 products (hi/lo split)
@@ -600,7 +603,8 @@ class Solver:
     the operator's precision; ``view(q)`` gives the (3, K, Np) window.
     ``precision``: "fp64", or an FP32-field variant: "fp32" (default:
     tensor cores, 3xTF32, from N = 2 on; CUDA cores at N = 1), "fp32tc"
-    (tensor cores at every order), "fp32simt", "tf32", "bf16", "bf16x3".
+    (tensor cores at every order), "fp32simt", "fp32ept" (one thread per
+    element on the CUDA cores, N <= 5), "tf32", "bf16", "bf16x3".
     ``eps``: per-element permittivity (K values; dg_operator_setup_media).
     """
 

@@ -35,12 +35,13 @@ DG_SETUP_TC_TF32 = 4
 DG_SETUP_TC_BF16 = 8
 DG_SETUP_TC_BF16X3 = 16
 DG_SETUP_TC = 32
+DG_SETUP_ELEMENT_THREADS = 64
 DG_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 DG_BATCH_NO_GRAPH = 1
 DG_BATCH_NO_ADAPT = 2
 DG_BATCH_SPLIT = 4
 DG_BATCH_MODE_CONCURRENT, DG_BATCH_MODE_SPLIT = 0, 1
-DG_KERNEL_TENSOR_CORES, DG_KERNEL_CUDA_CORES = 0, 1
+DG_KERNEL_TENSOR_CORES, DG_KERNEL_CUDA_CORES, DG_KERNEL_ELEMENT_THREADS = 0, 1, 2
 DG_SERVER_SEQUENTIAL = 1
 DG_REQUEST_QUEUED, DG_REQUEST_RUNNING, DG_REQUEST_DONE, DG_REQUEST_FAILED = 0, 1, 2, 3
 DG_REQUEST_CANCELLED = 4

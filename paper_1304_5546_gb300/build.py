@@ -35,6 +35,7 @@ def sources():
     names = (["host_setup.cpp", "api.cu"] + ["kernels_N%d.cu" % n for n in range(1, 8)]
              + ["kernels_tc_N%d.cu" % n for n in range(1, 8)]
              + ["kernels_tcp_N%d.cu" % n for n in range(1, 8)]
+             + ["kernels_ept_N%d.cu" % n for n in range(1, 6)]
              + ["kernels_batch_s1.cu", "kernels_batch_s2.cu", "batch.cu", "server.cu", "checkpoint.cu",
                   "partition.cu"])
     return [os.path.join(CSRC, n) for n in names]

@@ -189,6 +189,15 @@ dg_status upload(dg_op* op, const std::vector<double>& rec_in,
     lam[n] = static_cast<T>(0.5 * (1.0 + op->ref.r[n]));
     lam[Np + n] = static_cast<T>(0.5 * (1.0 + op->ref.s[n]));
   }
+  // the element-thread kernel's reference tables, FP32 (launch.h,
+  // ept_ops_floats): the same roundings as the device copies above
+  op->ept_ops.clear();
+  if (sizeof(T) == 4 && op->N <= dgw::kEptMaxN) {
+    for (double v : op->ref.Dr) op->ept_ops.push_back(static_cast<float>(v));
+    for (double v : op->ref.Ds) op->ept_ops.push_back(static_cast<float>(v));
+    for (double v : op->ref.LIFT) op->ept_ops.push_back(static_cast<float>(v));
+    for (int n = 0; n < 2 * Np; ++n) op->ept_ops.push_back(static_cast<float>(lam[n]));
+  }
   // records padded to Kpad elements: zero geometry, boundary faces
   const int rec = op->media() ? dgw::kGeoMedia : dgw::kGeo;
   std::vector<T> geo(static_cast<size_t>(Kpad) * rec, T(0));
@@ -293,10 +302,26 @@ cudaError_t launch_order_media(const dg_op* op, const dgw::StageArgs<T>& a, int 
   }
 }
 
+cudaError_t launch_order_ept(const dg_op* op, const dgw::StageArgs<float>& a, int mode,
+                             cudaStream_t s) {
+  if (op->ept_ops.size() != static_cast<size_t>(dgw::ept_ops_floats(op->N)))
+    return cudaErrorInvalidValue;
+  const float* t = op->ept_ops.data();
+  switch (op->N) {
+    case 1: return dgw::launch_stage_ept<1>(a, t, mode, op->num_sms, s);
+    case 2: return dgw::launch_stage_ept<2>(a, t, mode, op->num_sms, s);
+    case 3: return dgw::launch_stage_ept<3>(a, t, mode, op->num_sms, s);
+    case 4: return dgw::launch_stage_ept<4>(a, t, mode, op->num_sms, s);
+    case 5: return dgw::launch_stage_ept<5>(a, t, mode, op->num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
 cudaError_t launch_order(const dg_op* op, const dgw::StageArgs<T>& a, int mode, cudaStream_t s) {
   if (op->media()) return launch_order_media<T>(op, a, mode, s);
   if constexpr (sizeof(T) == 4) {
+    if (op->use_ept) return launch_order_ept(op, a, mode, s);
     if (op->use_tc) return launch_order_tc(op, a, mode, s);
   }
   switch (op->N) {
@@ -348,6 +373,7 @@ bool tc_has_alt_n(int N) {
 // Elements per block of the kernel the operator runs (alt: the alternative
 // size of the tensor-core kernel).
 int block_elems(const dg_op* op, int alt) {
+  if (op->precision == DG_FP32 && op->use_ept && !op->media()) return 32;
   if (op->precision == DG_FP32 && op->use_tc)
     return 40 * dgw::tc_tiles(op->N, op->tc_prec, alt != 0 && op->tc_prec == dgw::kTcTf32x3);
   return dgw::simt_block_elems(op->N, op->precision == DG_FP64);
@@ -471,7 +497,7 @@ dg_status operator_setup(const dg_mesh* mesh, int32_t N, const double* eps, int3
   if (precision != DG_FP32 && precision != DG_FP64)
     return fail(DG_ERR_ARG, "dg_operator_setup: unknown precision %d", precision);
   const int32_t known = DG_SETUP_HOST_ONLY | DG_SETUP_SIMT | DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 |
-                        DG_SETUP_TC_BF16X3 | DG_SETUP_TC;
+                        DG_SETUP_TC_BF16X3 | DG_SETUP_TC | DG_SETUP_ELEMENT_THREADS;
   const int32_t variants = flags & (DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 | DG_SETUP_TC_BF16X3);
   if (flags & ~known) return fail(DG_ERR_ARG, "dg_operator_setup: unknown flags 0x%x", flags);
   if ((flags & DG_SETUP_TC) && ((flags & DG_SETUP_SIMT) || precision != DG_FP32))
@@ -480,6 +506,14 @@ dg_status operator_setup(const dg_mesh* mesh, int32_t N, const double* eps, int3
     return fail(DG_ERR_ARG,
                 "dg_operator_setup: at most one tensor-core product variant, FP32 only, not with "
                 "DG_SETUP_SIMT");
+  if ((flags & DG_SETUP_ELEMENT_THREADS) &&
+      (precision != DG_FP32 || N > dgw::kEptMaxN || eps ||
+       (flags & (DG_SETUP_SIMT | DG_SETUP_TC | DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 |
+                 DG_SETUP_TC_BF16X3))))
+    return fail(DG_ERR_ARG,
+                "dg_operator_setup: DG_SETUP_ELEMENT_THREADS is for FP32 at N <= %d in a uniform "
+                "medium, without another kernel or product flag",
+                dgw::kEptMaxN);
   dg_op* op = nullptr;
   try {
     op = new dg_op;
@@ -490,11 +524,17 @@ dg_status operator_setup(const dg_mesh* mesh, int32_t N, const double* eps, int3
     op->Nafp = op->ref.Nafp;
     op->precision = precision;
     op->flags = flags;
-    // FP32 default: tensor cores from N = 2 on; at N = 1 the CUDA-core
-    // kernel measured faster (order sweep at ~1e7 nodal values per field:
-    // 0.87 vs 1.39 ms/step at N = 1; 0.98 vs 0.83 at N = 2)
+    // FP32 default: the element-thread kernel at N <= 2 in a uniform medium,
+    // the tensor cores otherwise from N = 2 on, the node-thread CUDA-core
+    // kernel at N = 1 with a permittivity (order sweep at ~1e7 nodal values
+    // per field, ms/step: N = 1 element threads 0.65, node threads 0.87,
+    // tensor cores 1.39; N = 2 0.63, 0.98, 0.83; N = 3 0.70, 0.90, 0.60)
     op->use_tc = (precision == DG_FP32) && !(flags & DG_SETUP_SIMT) &&
                  (N >= 2 || variants != 0 || (flags & DG_SETUP_TC));
+    const int32_t chosen = DG_SETUP_SIMT | DG_SETUP_TC | DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 |
+                           DG_SETUP_TC_BF16X3;
+    op->use_ept = (flags & DG_SETUP_ELEMENT_THREADS) ||
+                  (precision == DG_FP32 && !eps && !(flags & chosen) && N <= 2);
     op->tc_prec = (flags & DG_SETUP_TC_TF32)    ? dgw::kTcTf32
                   : (flags & DG_SETUP_TC_BF16)  ? dgw::kTcBf16
                   : (flags & DG_SETUP_TC_BF16X3) ? dgw::kTcBf16x3
@@ -729,18 +769,26 @@ extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, dou
   if (reps < 1) return fail(DG_ERR_ARG, "dg_operator_tune: reps = %d < 1", reps);
   if (ms_tc) *ms_tc = -1.0;
   if (ms_cuda_cores) *ms_cuda_cores = -1.0;
-  const int32_t fixed = DG_SETUP_SIMT | DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 | DG_SETUP_TC_BF16X3;
+  const int32_t fixed = DG_SETUP_SIMT | DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 | DG_SETUP_TC_BF16X3 |
+                        DG_SETUP_ELEMENT_THREADS;
   if (op->precision != DG_FP32 || (op->flags & fixed)) return DG_OK;  // nothing to choose
   // candidates: tensor cores (3xTF32) in the default and, where there is one,
-  // the alternative element-block size; the CUDA cores unless DG_SETUP_TC
+  // the alternative element-block size; unless DG_SETUP_TC, the CUDA cores:
+  // the node-per-thread kernel, and the element-thread kernel where the
+  // operator has its tables (N <= kEptMaxN, uniform medium)
   struct Cand {
     bool tc;
     int alt;
-  } cand[3];
+    bool ept;
+  } cand[4];
   int nc = 0;
-  cand[nc++] = {true, 0};
-  if (tc_has_alt_n(op->N)) cand[nc++] = {true, 1};
-  if (!(op->flags & DG_SETUP_TC)) cand[nc++] = {false, 0};
+  cand[nc++] = {true, 0, false};
+  if (tc_has_alt_n(op->N)) cand[nc++] = {true, 1, false};
+  if (!(op->flags & DG_SETUP_TC)) {
+    cand[nc++] = {false, 0, false};
+    if (!op->media() && op->ept_ops.size() == static_cast<size_t>(dgw::ept_ops_floats(op->N)))
+      cand[nc++] = {false, 0, true};
+  }
   if (nc < 2) return DG_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t err = cudaSuccess;
@@ -763,12 +811,13 @@ extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, dou
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const bool was_tc = op->use_tc;
+  const bool was_tc = op->use_tc, was_ept = op->use_ept;
   const int was_alt = op->tc_alt;
-  float ms[3] = {0.f, 0.f, 0.f};
+  float ms[4] = {0.f, 0.f, 0.f, 0.f};
   for (int v = 0; v < nc && err == cudaSuccess; ++v) {
     op->use_tc = cand[v].tc;
     op->tc_alt = cand[v].alt;
+    op->use_ept = cand[v].ept;
     dgw::StageArgs<float> a = base_args<float>(op);
     a.qin = buf;
     a.qout = buf + 3 * op->fstride;
@@ -791,6 +840,7 @@ extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, dou
   if (err != cudaSuccess) {
     op->use_tc = was_tc;
     op->tc_alt = was_alt;
+    op->use_ept = was_ept;
     return cuda_fail(err, "dg_operator_tune");
   }
   int best = 0;
@@ -798,12 +848,14 @@ extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, dou
     if (ms[v] < ms[best]) best = v;
   op->use_tc = cand[best].tc;
   op->tc_alt = cand[best].alt;
-  double best_tc = -1.0;
+  op->use_ept = cand[best].ept;
+  double best_tc = -1.0, best_cc = -1.0;
   for (int v = 0; v < nc; ++v) {
-    if (cand[v].tc && (best_tc < 0 || ms[v] < best_tc)) best_tc = ms[v];
-    if (!cand[v].tc && ms_cuda_cores) *ms_cuda_cores = ms[v] / reps;
+    double& b = cand[v].tc ? best_tc : best_cc;
+    if (b < 0 || ms[v] < b) b = ms[v];
   }
   if (ms_tc) *ms_tc = best_tc / reps;
+  if (ms_cuda_cores && best_cc >= 0) *ms_cuda_cores = best_cc / reps;
   return DG_OK;
 }
 
@@ -811,8 +863,8 @@ extern "C" dg_status dg_operator_set_block_elems(dg_op* op, int32_t elems) {
   dgw::clear_error();
   const char* where = "dg_operator_set_block_elems";
   if (!op) return fail(DG_ERR_ARG, "%s: NULL operator", where);
-  const bool alt_ok = op->precision == DG_FP32 && op->use_tc && op->tc_prec == dgw::kTcTf32x3 &&
-                      tc_has_alt_n(op->N);
+  const bool alt_ok = op->precision == DG_FP32 && op->use_tc && !op->use_ept &&
+                      op->tc_prec == dgw::kTcTf32x3 && tc_has_alt_n(op->N);
   const int def = block_elems(op, 0), alt = alt_ok ? block_elems(op, 1) : def;
   if (elems == 0 || elems == def) {
     op->tc_alt = 0;
@@ -829,8 +881,10 @@ extern "C" dg_status dg_operator_set_block_elems(dg_op* op, int32_t elems) {
 extern "C" dg_status dg_operator_kernel(const dg_op* op, int32_t* kernel, int32_t* elems) {
   dgw::clear_error();
   if (!op) return fail(DG_ERR_ARG, "dg_operator_kernel: NULL operator");
-  const bool tc = op->precision == DG_FP32 && op->use_tc;
-  if (kernel) *kernel = tc ? DG_KERNEL_TENSOR_CORES : DG_KERNEL_CUDA_CORES;
+  const bool ept = op->precision == DG_FP32 && op->use_ept && !op->media();
+  const bool tc = op->precision == DG_FP32 && op->use_tc && !ept;
+  if (kernel)
+    *kernel = ept ? DG_KERNEL_ELEMENT_THREADS : tc ? DG_KERNEL_TENSOR_CORES : DG_KERNEL_CUDA_CORES;
   if (elems) *elems = block_elems(op, op->tc_alt && !op->face_pairs);
   return DG_OK;
 }
@@ -1165,7 +1219,7 @@ extern "C" dg_status dg_test_wait_timeout(const dg_op* op, void* stream) {
   dgw::clear_error();
   dg_status st = check_device_op(op, "dg_test_wait_timeout");
   if (st) return st;
-  if (!op->use_tc)
+  if (!op->use_tc || op->use_ept || op->precision != DG_FP32)
     return fail(DG_ERR_ARG, "dg_test_wait_timeout: needs an operator on the tensor-core kernel");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* gate = nullptr;

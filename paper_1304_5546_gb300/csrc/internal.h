@@ -130,6 +130,10 @@ struct dg_op {
   int* d_status = nullptr; // kernel status word (bounded-wait expiry)
   void* d_tcop = nullptr;  // tensor-core operator tiles for FP32 (see tc_operator_tiles)
   bool use_tc = false;     // FP32 products on the tensor cores
+  bool use_ept = false;    // FP32: the element-thread kernel (takes precedence over use_tc)
+  // FP32 operators of order <= kEptMaxN: the element-thread kernel's
+  // reference tables (launch.h, ept_ops_floats)
+  std::vector<float> ept_ops;
   int tc_prec = 0;         // their product variant (dgw::TcPrecision)
   double lsrk_a[5], lsrk_b[5], lsrk_c[5];
   mutable std::atomic<int64_t> launches{0};

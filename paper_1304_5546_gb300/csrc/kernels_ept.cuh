@@ -1,0 +1,529 @@
+// FP32 stage kernel with one thread per element ("element threads"), for the
+// low orders.
+//
+// Same result as dg_stage_kernel (kernels.cuh): right-hand side of Eq.
+// dg-strong-explicit -- volume derivative by Dr/Ds and the chain rule of Eq.
+// dg-diff-local-to-global, upwind flux of Eq. max2d-numflux (parameter
+// alpha; PEC by the mirror state Ez+ = -Ez-, H+ = H-) at every face node,
+// LIFT of Eq. dg-lift scaled by Fscale/2 -- followed by one 2N-storage
+// LSRK(5,4) stage update, or written out as the right-hand side.  The
+// products take the same deflated operands (fields minus their linear
+// interpolant through the vertex nodes, whose exact derivatives are added
+// back per element) and the same four-product form of the volume term,
+//   dEz/dt = Dr (rx Hy - ry Hx) + Ds (sx Hy - sy Hx).
+//
+// At low order the element-local matrices are small (Np = 3 .. 21 nodes), so
+// each product is a short dot product whose matrix operand is the same for
+// every element.  Here one thread evaluates one element: its nodal values,
+// deflated operands and face fluxes stay in registers, and Dr, Ds, LIFT and
+// the vertex-interpolant weights are a by-value kernel parameter.  With every
+// loop unrolled each matrix entry is a compile-time offset into the
+// parameter (constant) bank, which an FMA takes as an operand directly: a
+// product term costs one FMA and no load, where the tensor-core kernel
+// spends most of its instructions building operand rows and hand-offs.
+//
+// Work decomposition.  A CTA is one warp (residency is then set warp by warp
+// by shared memory).  The warp walks blocks of 32 consecutive elements, block
+// blockIdx.x + it * gridDim.x, lane e owning element 32 block + e.  All a
+// block owns is contiguous in HBM (its q and residual values per field, its
+// geometry records and face codes) and is fetched by the warp's lanes with
+// 16-byte cp.async copies into a ring of S stage buffers, S - 1 blocks ahead,
+// one commit group per block.  A lane reads its element's values from the
+// stage buffer (a stride of Np words: conflict-free for odd Np, 8-byte loads
+// for even Np), gathers its neighbours' face-node traces from global memory
+// (L2) into registers one block ahead, writes its updated values back into
+// its own stage slots, and the warp stores the block with coalesced 16-byte
+// stores.  No wait spins on a flag: cp.async.wait_group returns when the
+// warp's own copies have landed.
+#pragma once
+
+#include <atomic>
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace dgw {
+
+template <int N>
+struct EptOps {
+  static constexpr int Np = Order<N>::Np, Nafp = Order<N>::Nafp;
+  float dr[Np * Np];    // Dr, row-major
+  float ds[Np * Np];    // Ds, row-major
+  float lf[Np * Nafp];  // LIFT, row-major (face-node columns, face by face)
+  float l2[Np];         // (1 + r_n) / 2: weight of vertex 2 in the linear interpolant
+  float l3[Np];         // (1 + s_n) / 2: weight of vertex 3
+};
+
+// Stage buffers per warp: as many as keep several warps resident per SM
+// (the shared memory of a stage grows with Np).
+__host__ __device__ constexpr int ept_stages(int N) { return N == 1 ? 4 : N == 2 ? 3 : 2; }
+
+// Where the products read the reference matrices: false -- the by-value
+// parameter, every output node unrolled, each entry an FMA's constant
+// operand; true -- a table in shared memory (one row per output node:
+// [Dr | Ds over the interior nodes | LIFT], each part padded to 4), read
+// with 16-byte broadcast loads in a loop over the output nodes, which keeps
+// the code and the constant working set small at the higher orders.
+__host__ __device__ constexpr bool ept_table(int N) { return N >= 4; }
+
+// c-th node of an element that is not a vertex node (0, N, Np - 1): the
+// deflated operands are zero at the vertex nodes
+__host__ __device__ constexpr int ept_interior_node(int N, int c) {
+  return c < N - 1 ? c + 1 : c + 2;
+}
+
+template <int N>
+struct EptLayout {
+  static constexpr int Np = Order<N>::Np, Nfp = Order<N>::Nfp, Nafp = Order<N>::Nafp;
+  static constexpr int E = 32;             // elements per block: one per lane
+  static constexpr int S = ept_stages(N);  // stage buffers of the warp's ring
+  static constexpr int FQ = E * Np;        // floats of one field of a block
+  // stage buffer: q[3][E Np], res[3][E Np], geo[E][kGeo], conn[E][3]
+  static constexpr int QB = FQ * 4;
+  static constexpr int GB = E * kGeo * 4;
+  static constexpr int CB = E * 3 * 4;
+  static constexpr int STAGE_BYTES = 6 * QB + GB + CB;
+  // operator table (ept_table): row width RS floats, Dr and Ds parts DW
+  // wide (Np - 3 interior nodes, padded to 4), LIFT part LW wide
+  static constexpr bool TBL = ept_table(N);
+  static constexpr int DW = (Np - 3 + 3) / 4 * 4, LW = (Nafp + 3) / 4 * 4;
+  static constexpr int RS = 2 * DW + LW;
+  static constexpr int TBL_BYTES = TBL ? Np * RS * 4 : 0;
+  static constexpr int SMEM_BYTES = S * STAGE_BYTES + TBL_BYTES;
+  static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0, "16-byte copies");
+  static_assert(sizeof(EptOps<N>) == 4 * ept_ops_floats(N), "parameter layout");
+};
+
+// Neighbour node for own face-node slot jj, for each value sel = fP * 2 + rev
+// of a face connection code's low bits: 5 bits per sel (Np <= 32).
+template <int N>
+__host__ __device__ constexpr uint32_t ept_nbr_nodes(int jj) {
+  uint32_t v = 0;
+  for (int sel = 0; sel < 6; ++sel)
+    v |= static_cast<uint32_t>(face_node_dev(N, sel >> 1, (sel & 1) ? (N - jj) : jj)) << (5 * sel);
+  return v;
+}
+
+template <int Np>
+__device__ __forceinline__ void ept_ld_row(float (&v)[Np], const float* s) {
+  if constexpr (Np % 2 == 0) {  // 8-byte aligned: lane * Np words, Np even
+#pragma unroll
+    for (int j = 0; j < Np; j += 2) {
+      const float2 t = *reinterpret_cast<const float2*>(s + j);
+      v[j] = t.x;
+      v[j + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < Np; ++j) v[j] = s[j];
+  }
+}
+
+// the warp copies PIECES 16-byte pieces global -> shared
+template <int PIECES>
+__device__ __forceinline__ void ept_fetch(void* dst, const void* src, int lane) {
+#pragma unroll
+  for (int c = lane; c < PIECES; c += 32)
+    cp_async16(static_cast<char*>(dst) + 16 * c, static_cast<const char*>(src) + 16 * c);
+}
+
+// the warp stores the first n elements' values of one field of a block
+// (FQ = 32 Np floats in shared memory) to global memory
+template <int Np>
+__device__ __forceinline__ void ept_store(float* dst, const float* src, int n, int lane) {
+  constexpr int P = 8 * Np;  // 16-byte pieces of a whole block
+  if (n == 32) {
+#pragma unroll
+    for (int c = lane; c < P; c += 32)
+      *reinterpret_cast<float4*>(dst + 4 * c) = *reinterpret_cast<const float4*>(src + 4 * c);
+  } else {
+    const int nv = n * Np;
+    for (int c = lane; 4 * c < nv; c += 32) {
+      if (4 * c + 4 <= nv) {
+        *reinterpret_cast<float4*>(dst + 4 * c) = *reinterpret_cast<const float4*>(src + 4 * c);
+      } else {
+        for (int v = 4 * c; v < nv; ++v) dst[v] = src[v];
+      }
+    }
+  }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float> p,
+                                                          const EptOps<N> ops) {
+  using L = EptLayout<N>;
+  constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, S = L::S, FQ = L::FQ;
+  extern __shared__ __align__(128) unsigned char smem[];
+
+  const int lane = threadIdx.x;
+  const int K = static_cast<int>(p.K);
+  const int nblk = (K + 31) >> 5;
+  const int G = gridDim.x;
+  const int b0 = blockIdx.x;
+  const int niter = b0 < nblk ? (nblk - 1 - b0) / G + 1 : 0;
+  if (niter == 0) return;
+  const float* q0 = p.qin;
+  const float* q1 = p.qin + p.fstride;
+  const float* q2 = p.qin + 2 * p.fstride;
+
+  auto stage = [&](int it) {
+    return reinterpret_cast<float*>(smem + (it % S) * L::STAGE_BYTES);
+  };
+  // the warp fetches everything block `it` owns into its stage buffer; the
+  // first stage of a step does not read the residual (a_1 = 0), nor does the
+  // right-hand-side mode.  A block never reaches past the records' padding
+  // (Kpad, a multiple of 64) nor past a field (fstride >= Kpad Np).
+  auto issue = [&](int it) {
+    float* st = stage(it);
+    const int64_t k0 = static_cast<int64_t>(b0 + it * G) * 32;
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+      ept_fetch<L::QB / 16>(st + f * FQ, p.qin + f * p.fstride + k0 * Np, lane);
+    if (MODE == kModeStage) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+        ept_fetch<L::QB / 16>(st + (3 + f) * FQ, p.res + f * p.fstride + k0 * Np, lane);
+    }
+    ept_fetch<L::GB / 16>(st + 6 * FQ, p.geo + k0 * kGeo, lane);
+    ept_fetch<L::CB / 16>(st + 6 * FQ + 32 * kGeo, p.conn + k0 * 3, lane);
+  };
+
+  // neighbour traces (Hx, Hy, Ez) of this lane's element at its Nafp face
+  // nodes, for block `it` (its face codes are in its stage buffer); zero at
+  // PEC faces (code -1), whose flux takes the mirror state instead
+  float trc[3][Nafp];
+  auto gather = [&](int it) {
+    const int* sc = reinterpret_cast<const int*>(stage(it) + 6 * FQ + 32 * kGeo);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      const int code = sc[lane * 3 + f];
+      bool ok = code >= 0;
+#ifdef DGW_DEVICE_CHECKS
+      if (!nbr_code_ok(code, p.fstride, Np)) {
+        atomicOr(p.status, kStatusIndex);
+        ok = false;
+      }
+#endif
+      const int base = (code >> 3) * Np;
+      const uint32_t sh = 5u * static_cast<uint32_t>(code & 7);
+#pragma unroll
+      for (int jj = 0; jj < Nfp; ++jj) {
+        const int j = f * Nfp + jj;
+        trc[0][j] = trc[1][j] = trc[2][j] = 0.f;
+        if (ok) {
+          const int g = base + static_cast<int>((ept_nbr_nodes<N>(jj) >> sh) & 31u);
+          trc[0][j] = __ldg(q0 + g);
+          trc[1][j] = __ldg(q1 + g);
+          trc[2][j] = __ldg(q2 + g);
+        }
+      }
+    }
+  };
+
+  float* tbl = reinterpret_cast<float*>(smem + S * L::STAGE_BYTES);
+  if constexpr (L::TBL) {
+    // the operator table, from the operator's device copies of Dr, Ds, LIFT
+    for (int idx = lane; idx < Np * L::RS; idx += 32) {
+      const int i = idx / L::RS, c = idx - i * L::RS;
+      float v = 0.f;
+      if (c < L::DW) {
+        if (c < Np - 3) v = __ldg(p.Dr + i * Np + ept_interior_node(N, c));
+      } else if (c < 2 * L::DW) {
+        if (c - L::DW < Np - 3) v = __ldg(p.Ds + i * Np + ept_interior_node(N, c - L::DW));
+      } else if (c - 2 * L::DW < Nafp) {
+        v = __ldg(p.LIFT + i * Nafp + (c - 2 * L::DW));
+      }
+      tbl[idx] = v;
+    }
+  }
+
+#pragma unroll
+  for (int j = 0; j < S - 1; ++j) {
+    if (j < niter) issue(j);
+    cp_async_commit();
+  }
+  cp_async_wait<S - 2>();  // block 0 has landed
+  __syncwarp();
+  gather(0);
+
+  for (int it = 0; it < niter; ++it) {
+    // refill the stage the previous block released
+    if (it + S - 1 < niter) issue(it + S - 1);
+    cp_async_commit();
+
+    float* sq = stage(it);
+    const float* sg = sq + 6 * FQ;
+    const int* sc = reinterpret_cast<const int*>(sg + 32 * kGeo);
+    const int k0 = (b0 + it * G) * 32;
+    float* own = sq + lane * Np;  // this lane's slot in field 0 (fields FQ apart)
+
+    float hx[Np], hy[Np], ez[Np];
+    ept_ld_row<Np>(hx, own);
+    ept_ld_row<Np>(hy, own + FQ);
+    ept_ld_row<Np>(ez, own + 2 * FQ);
+    const float* ge = sg + lane * kGeo;
+    const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
+
+    // ---- upwind flux (Eq. max2d-numflux) times Fscale/2 at every face node
+    float F0[Nafp], F1[Nafp], F2[Nafp];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      const bool pec = sc[lane * 3 + f] < 0;
+      const float nx = ge[4 + 3 * f], ny = ge[5 + 3 * f], fsc = ge[6 + 3 * f];
+      const float fa = fsc * p.alpha, fnx = fsc * nx, fny = fsc * ny;
+#pragma unroll
+      for (int jj = 0; jj < Nfp; ++jj) {
+        const int n = face_node_dev(N, f, jj);
+        const int j = f * Nfp + jj;
+        const float dHx = pec ? 0.f : hx[n] - trc[0][j];
+        const float dHy = pec ? 0.f : hy[n] - trc[1][j];
+        const float dEz = pec ? 2.f * ez[n] : ez[n] - trc[2][j];
+        const float ndH = nx * dHx + ny * dHy;
+        F0[j] = fny * dEz + fa * (ndH * nx - dHx);
+        F1[j] = -fnx * dEz + fa * (ndH * ny - dHy);
+        F2[j] = fny * dHx - fnx * dHy - fa * dEz;
+      }
+    }
+
+    // ---- the next block has landed: gather its traces (their L2 latency
+    // hides behind this block's products)
+    cp_async_wait<S - 2>();
+    __syncwarp();
+    if (it + 1 < niter) gather(it + 1);
+
+    // ---- volume operands minus their linear part (exactly zero at the
+    // vertex nodes 0, N, Np - 1), and the linear part's derivatives
+    const float x1 = hx[0], x2 = hx[N], x3 = hx[Np - 1];
+    const float y1 = hy[0], y2 = hy[N], y3 = hy[Np - 1];
+    const float z1 = ez[0], z2 = ez[N], z3 = ez[Np - 1];
+    float zd[Np], A[Np], B[Np];
+#pragma unroll
+    for (int j = 0; j < Np; ++j) {
+      if (j == 0 || j == N || j == Np - 1) {
+        zd[j] = A[j] = B[j] = 0.f;
+      } else {
+        const float dhx = (hx[j] - x1) - ((x2 - x1) * ops.l2[j] + (x3 - x1) * ops.l3[j]);
+        const float dhy = (hy[j] - y1) - ((y2 - y1) * ops.l2[j] + (y3 - y1) * ops.l3[j]);
+        zd[j] = (ez[j] - z1) - ((z2 - z1) * ops.l2[j] + (z3 - z1) * ops.l3[j]);
+        A[j] = rx * dhy - ry * dhx;
+        B[j] = sx * dhy - sy * dhx;
+      }
+    }
+    const float grz = 0.5f * (z2 - z1), gsz = 0.5f * (z3 - z1);
+    const float lin0 = -(ry * grz + sy * gsz);
+    const float lin1 = rx * grz + sx * gsz;
+    const float lin2 = 0.5f * (rx * (y2 - y1) - ry * (x2 - x1) + sx * (y3 - y1) - sy * (x3 - x1));
+
+    // right-hand side at node i: volume products, chain rule, lift
+    auto rhs_at = [&](int i, float& rHx, float& rHy, float& rEz) {
+      float dzr = 0.f, dzs = 0.f, ca = 0.f, cb = 0.f;
+#pragma unroll
+      for (int j = 0; j < Np; ++j) {
+        if (j == 0 || j == N || j == Np - 1) continue;
+        dzr = fmaf(ops.dr[i * Np + j], zd[j], dzr);
+        dzs = fmaf(ops.ds[i * Np + j], zd[j], dzs);
+        ca = fmaf(ops.dr[i * Np + j], A[j], ca);
+        cb = fmaf(ops.ds[i * Np + j], B[j], cb);
+      }
+      float l0 = lin0, l1 = lin1, l2 = lin2;
+#pragma unroll
+      for (int k = 0; k < Nafp; ++k) {
+        l0 = fmaf(ops.lf[i * Nafp + k], F0[k], l0);
+        l1 = fmaf(ops.lf[i * Nafp + k], F1[k], l1);
+        l2 = fmaf(ops.lf[i * Nafp + k], F2[k], l2);
+      }
+      rHx = l0 - (ry * dzr + sy * dzs);
+      rHy = l1 + (rx * dzr + sx * dzs);
+      rEz = l2 + (ca + cb);
+    };
+
+    // ---- stage update (or the right-hand side) into this lane's own slots
+    auto update = [&](int i, float rHx, float rHy, float rEz, float& o0, float& o1, float& o2,
+                      float& n0, float& n1, float& n2, float r0, float r1, float r2) {
+      if (MODE == kModeFirstStage) {
+        n0 = p.dt * rHx;
+        n1 = p.dt * rHy;
+        n2 = p.dt * rEz;
+      } else {
+        n0 = fmaf(p.a, r0, p.dt * rHx);
+        n1 = fmaf(p.a, r1, p.dt * rHy);
+        n2 = fmaf(p.a, r2, p.dt * rEz);
+      }
+      o0 = fmaf(p.b, n0, hx[i]);
+      o1 = fmaf(p.b, n1, hy[i]);
+      o2 = fmaf(p.b, n2, ez[i]);
+    };
+    if constexpr (L::TBL) {
+      // one output node per trip; own values re-read from the stage slots
+#pragma unroll 1
+      for (int i = 0; i < Np; ++i) {
+        const float* row = tbl + i * L::RS;
+        float dzr = 0.f, dzs = 0.f, ca = 0.f, cb = 0.f;
+#pragma unroll
+        for (int c4 = 0; c4 < L::DW; c4 += 4) {
+          const float4 d4 = *reinterpret_cast<const float4*>(row + c4);
+          const float4 e4 = *reinterpret_cast<const float4*>(row + L::DW + c4);
+          const float dv[4] = {d4.x, d4.y, d4.z, d4.w}, ev[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (c4 + u < Np - 3) {
+              const int j = ept_interior_node(N, c4 + u);
+              dzr = fmaf(dv[u], zd[j], dzr);
+              dzs = fmaf(ev[u], zd[j], dzs);
+              ca = fmaf(dv[u], A[j], ca);
+              cb = fmaf(ev[u], B[j], cb);
+            }
+          }
+        }
+        float l0 = lin0, l1 = lin1, l2 = lin2;
+#pragma unroll
+        for (int c4 = 0; c4 < L::LW; c4 += 4) {
+          const float4 f4 = *reinterpret_cast<const float4*>(row + 2 * L::DW + c4);
+          const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (c4 + u < Nafp) {
+              l0 = fmaf(fv[u], F0[c4 + u], l0);
+              l1 = fmaf(fv[u], F1[c4 + u], l1);
+              l2 = fmaf(fv[u], F2[c4 + u], l2);
+            }
+          }
+        }
+        const float rHx = l0 - (ry * dzr + sy * dzs);
+        const float rHy = l1 + (rx * dzr + sx * dzs);
+        const float rEz = l2 + (ca + cb);
+        if (MODE == kModeRhs) {
+          own[i] = rHx;
+          own[FQ + i] = rHy;
+          own[2 * FQ + i] = rEz;
+        } else {
+          float n0 = p.dt * rHx, n1 = p.dt * rHy, n2 = p.dt * rEz;
+          if (MODE == kModeStage) {
+            n0 = fmaf(p.a, own[3 * FQ + i], n0);
+            n1 = fmaf(p.a, own[4 * FQ + i], n1);
+            n2 = fmaf(p.a, own[5 * FQ + i], n2);
+          }
+          own[i] = fmaf(p.b, n0, own[i]);
+          own[FQ + i] = fmaf(p.b, n1, own[FQ + i]);
+          own[2 * FQ + i] = fmaf(p.b, n2, own[2 * FQ + i]);
+          own[3 * FQ + i] = n0;
+          own[4 * FQ + i] = n1;
+          own[5 * FQ + i] = n2;
+        }
+      }
+    } else if constexpr (Np % 2 == 0) {
+#pragma unroll
+      for (int i = 0; i < Np; i += 2) {
+        float a0, a1, a2, b0_, b1, b2;
+        rhs_at(i, a0, a1, a2);
+        rhs_at(i + 1, b0_, b1, b2);
+        if (MODE == kModeRhs) {
+          *reinterpret_cast<float2*>(own + i) = make_float2(a0, b0_);
+          *reinterpret_cast<float2*>(own + FQ + i) = make_float2(a1, b1);
+          *reinterpret_cast<float2*>(own + 2 * FQ + i) = make_float2(a2, b2);
+        } else {
+          float2 r0 = make_float2(0.f, 0.f), r1 = r0, r2 = r0;
+          if (MODE == kModeStage) {
+            r0 = *reinterpret_cast<const float2*>(own + 3 * FQ + i);
+            r1 = *reinterpret_cast<const float2*>(own + 4 * FQ + i);
+            r2 = *reinterpret_cast<const float2*>(own + 5 * FQ + i);
+          }
+          float oa0, oa1, oa2, na0, na1, na2, ob0, ob1, ob2, nb0, nb1, nb2;
+          update(i, a0, a1, a2, oa0, oa1, oa2, na0, na1, na2, r0.x, r1.x, r2.x);
+          update(i + 1, b0_, b1, b2, ob0, ob1, ob2, nb0, nb1, nb2, r0.y, r1.y, r2.y);
+          *reinterpret_cast<float2*>(own + i) = make_float2(oa0, ob0);
+          *reinterpret_cast<float2*>(own + FQ + i) = make_float2(oa1, ob1);
+          *reinterpret_cast<float2*>(own + 2 * FQ + i) = make_float2(oa2, ob2);
+          *reinterpret_cast<float2*>(own + 3 * FQ + i) = make_float2(na0, nb0);
+          *reinterpret_cast<float2*>(own + 4 * FQ + i) = make_float2(na1, nb1);
+          *reinterpret_cast<float2*>(own + 5 * FQ + i) = make_float2(na2, nb2);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < Np; ++i) {
+        float a0, a1, a2;
+        rhs_at(i, a0, a1, a2);
+        if (MODE == kModeRhs) {
+          own[i] = a0;
+          own[FQ + i] = a1;
+          own[2 * FQ + i] = a2;
+        } else {
+          float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+          if (MODE == kModeStage) {
+            r0 = own[3 * FQ + i];
+            r1 = own[4 * FQ + i];
+            r2 = own[5 * FQ + i];
+          }
+          float o0, o1, o2, n0, n1, n2;
+          update(i, a0, a1, a2, o0, o1, o2, n0, n1, n2, r0, r1, r2);
+          own[i] = o0;
+          own[FQ + i] = o1;
+          own[2 * FQ + i] = o2;
+          own[3 * FQ + i] = n0;
+          own[4 * FQ + i] = n1;
+          own[5 * FQ + i] = n2;
+        }
+      }
+    }
+
+    // ---- the warp stores the block's valid elements
+    __syncwarp();
+    const int n = (K - k0) < 32 ? (K - k0) : 32;
+    const int64_t g0 = static_cast<int64_t>(k0) * Np;
+    if (MODE == kModeRhs) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) ept_store<Np>(p.rhs + f * p.fstride + g0, sq + f * FQ, n, lane);
+    } else {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        ept_store<Np>(p.qout + f * p.fstride + g0, sq + f * FQ, n, lane);
+        ept_store<Np>(p.res + f * p.fstride + g0, sq + (3 + f) * FQ, n, lane);
+      }
+    }
+    __syncwarp();  // the stage is free for the next refill
+  }
+}
+
+template <int N, int MODE>
+cudaError_t launch_stage_ept_mode(const StageArgs<float>& args, const EptOps<N>& ops, int num_sms,
+                                  cudaStream_t stream) {
+  using L = EptLayout<N>;
+  // per (N, MODE): shared-memory attribute and resident CTAs per SM, set on
+  // the first launch on each device
+  static std::atomic<uint64_t> configured{0};
+  static std::atomic<int> blocks_per_sm{1};
+  cudaError_t err = configure_once_per_device(configured, [] {
+    cudaError_t e = cudaFuncSetAttribute(dg_stage_ept_kernel<N, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         L::SMEM_BYTES);
+    int nb = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dg_stage_ept_kernel<N, MODE>, 32,
+                                                        L::SMEM_BYTES);
+    if (e == cudaSuccess) blocks_per_sm.store(nb > 0 ? nb : 1);
+    return e;
+  });
+  if (err != cudaSuccess) return err;
+  const int64_t nblk = (args.K + 31) / 32;
+  int64_t grid = static_cast<int64_t>(blocks_per_sm.load()) * num_sms;
+  if (grid > nblk) grid = nblk;
+  if (grid < 1) grid = 1;
+  dg_stage_ept_kernel<N, MODE><<<static_cast<unsigned>(grid), 32, L::SMEM_BYTES, stream>>>(args, ops);
+  return cudaGetLastError();
+}
+
+// Definition of the launcher declared in launch.h; explicitly instantiated
+// per order in kernels_ept_N*.cu.
+template <int N>
+cudaError_t launch_stage_ept(const StageArgs<float>& args, const float* ops_host, int mode,
+                             int num_sms, cudaStream_t stream) {
+  EptOps<N> ops;
+  std::memcpy(&ops, ops_host, sizeof(ops));
+  if (mode == kModeRhs) return launch_stage_ept_mode<N, kModeRhs>(args, ops, num_sms, stream);
+  if (mode == kModeFirstStage)
+    return launch_stage_ept_mode<N, kModeFirstStage>(args, ops, num_sms, stream);
+  return launch_stage_ept_mode<N, kModeStage>(args, ops, num_sms, stream);
+}
+
+}  // namespace dgw

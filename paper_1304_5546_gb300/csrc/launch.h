@@ -209,6 +209,19 @@ template <int N, int PREC>
 cudaError_t launch_stage_tc(const StageArgs<float>& args, int mode, int num_sms,
                             cudaStream_t stream);
 
+// Element-thread path (FP32, CUDA cores, one thread per element; see
+// kernels_ept.cuh), orders 1..kEptMaxN, uniform medium.  Its reference
+// tables travel as a kernel parameter: `ops` points to host memory holding
+// ept_ops_floats(N) floats, [Dr (Np x Np, row-major) | Ds | LIFT (Np x
+// Nafp) | (1 + r_n) / 2 | (1 + s_n) / 2].
+constexpr int kEptMaxN = 5;
+__host__ __device__ constexpr int ept_ops_floats(int N) {
+  return 2 * tc_np(N) * tc_np(N) + tc_np(N) * 3 * (N + 1) + 2 * tc_np(N);
+}
+template <int N>
+cudaError_t launch_stage_ept(const StageArgs<float>& args, const float* ops, int mode,
+                             int num_sms, cudaStream_t stream);
+
 // Operators with a per-element permittivity (geometry records of kGeoMedia
 // values): CUDA-core kernel (FP32 / FP64) and tensor-core kernel (3xTF32).
 template <typename T, int N>

@@ -293,6 +293,7 @@ dg_status build_device(dg_partition& pt) {
     s->alpha = op.alpha;
     s->face_pairs = op.face_pairs;
     s->use_tc = op.use_tc;
+    s->use_ept = op.use_ept;
     s->tc_prec = op.tc_prec;
     s->elem_size = op.elem_size;
     s->device = op.device;

@@ -145,6 +145,23 @@ __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
+// Per-thread asynchronous copy of 16 bytes global -> shared (L2 only, not
+// cached in L1); both addresses 16-byte aligned.  Completion is tracked per
+// thread in commit groups.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// wait until at most `pending` of this thread's most recent commit groups are
+// still in flight (the copies of every older group have landed)
+template <int pending>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(pending) : "memory");
+}
+
 // ---------------------------------------------------------------- tcgen05
 // Shared-memory matrix descriptor: K-major, no swizzle.  lbo = byte distance
 // between K-adjacent core matrices, sbo = between 8-row groups.

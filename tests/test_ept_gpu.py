@@ -1,0 +1,152 @@
+"""GPU parity of the element-thread stage kernel (DG_SETUP_ELEMENT_THREADS,
+precision "fp32ept": FP32 on the CUDA cores, one thread per element, the
+reference matrices as constant operands; N = 1..5, uniform medium) against
+the FP64 oracle on the same seeded inputs.
+
+Each warp of that kernel walks blocks of 32 elements through its own ring
+of S stage buffers (S = 4 at N = 1, 3 at N = 2, 2 above).  Besides small
+meshes, every order runs on a mesh large enough that each warp of the
+launch handles at least S + 2 blocks, so the ring wraps, the one-block-ahead
+neighbour gather crosses blocks many times, and the last block is ragged.
+The bound on the number of warps comes from shared memory alone (other
+limits only shrink the grid, which gives each warp more blocks).
+
+Tolerance: max nodal error <= 1e-5 relative to max |value| (FP32 fields).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import gaussian_pulse, jittered_delaunay_mesh, random_fields
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+ORDERS = [1, 2, 3, 4, 5]
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1304_5546_gb300 import build as B
+    B.build()
+    import paper_1304_5546_gb300 as P
+    return P
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _warps_bound(N, sms=152, smem_per_sm=233472, reserved=1024, max_ctas=32):
+    # one warp per CTA; its shared memory is S stage buffers of 32 elements:
+    # q and residual (6 Np values), 13 geometry values, 3 face codes
+    Np = (N + 1) * (N + 2) // 2
+    S = {1: 4, 2: 3}.get(N, 2)
+    smem = S * 128 * (6 * Np + 16)
+    return sms * min(max_ctas, smem_per_sm // (smem + reserved)), S
+
+
+def _n_for(N):
+    # smallest jittered grid n (K = 2 n^2) with >= S + 2 blocks per warp and
+    # a ragged last block
+    warps, S = _warps_bound(N)
+    n = int(np.ceil(np.sqrt((S + 2) * warps * 32 / 2)))
+    while (2 * n * n) % 32 == 0:
+        n += 1
+    return n
+
+
+def test_large_sizes_walk_the_ring():
+    for N in ORDERS:
+        warps, S = _warps_bound(N)
+        K = 2 * _n_for(N) ** 2
+        assert -(-K // 32) / warps >= S + 2 and K % 32 != 0, (N, K)
+
+
+@pytest.mark.parametrize("N", ORDERS)
+def test_kernel_report(P, N):
+    s = P.Solver(*jittered_delaunay_mesh(5, seed=N), N=N, precision="fp32ept")
+    assert s.kernel() == ("element threads", 32)
+    s.close()
+
+
+@pytest.mark.parametrize("N", ORDERS)
+def test_rhs_parity_small(P, N):
+    # 162 elements: several warps, a ragged last block
+    mesh = jittered_delaunay_mesh(9, seed=100 + N)
+    d = O.Discretization(*mesh, N)
+    q = random_fields(d.K, d.Np, seed=N)
+    s = P.Solver(*mesh, N=N, precision="fp32ept")
+    got = s.to_numpy(s.rhs(s.from_numpy(q)))
+    P.dg_sync_check(s.op)
+    s.close()
+    assert _rel(got, O.maxwell_rhs(d, q)) <= TOL
+
+
+@pytest.mark.parametrize("N", ORDERS)
+def test_lsrk_steps_parity_small(P, N):
+    mesh = jittered_delaunay_mesh(8, seed=7 * N)
+    d = O.Discretization(*mesh, N)
+    q0 = np.stack(gaussian_pulse(d.x, d.y, 0.5, 0.5, 0.15))
+    dt = O.cfl_dt(d)
+    want = q0
+    for n in range(3):
+        want = O.lsrk_step(d, want, n * dt, dt)
+    s = P.Solver(*mesh, N=N, precision="fp32ept")
+    q = s.from_numpy(q0)
+    res = s.new_fields()
+    s.step(q, res, dt, nsteps=3)
+    got = s.to_numpy(q)
+    P.dg_sync_check(s.op)
+    s.close()
+    assert _rel(got, want) <= TOL
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.5])
+def test_flux_parameter(P, alpha):
+    mesh = jittered_delaunay_mesh(10, seed=31)
+    d = O.Discretization(*mesh, 3)
+    q = random_fields(d.K, d.Np, seed=3)
+    s = P.Solver(*mesh, N=3, precision="fp32ept")
+    P.dg_operator_set_alpha(s.op, alpha)
+    got = s.to_numpy(s.rhs(s.from_numpy(q)))
+    s.close()
+    assert _rel(got, O.maxwell_rhs(d, q, alpha=alpha)) <= TOL
+
+
+@pytest.mark.parametrize("N", ORDERS)
+def test_large_rhs_and_two_steps(P, N):
+    mesh = jittered_delaunay_mesh(_n_for(N), seed=900 + N)
+    d = O.Discretization(*mesh, N)
+    q0 = random_fields(d.K, d.Np, seed=N + 1).astype(np.float32).astype(np.float64)
+    s = P.Solver(*mesh, N=N, precision="fp32ept")
+    try:
+        dt = s.cfl_dt()
+        q = s.from_numpy(q0)
+        rhs = s.to_numpy(s.rhs(q))
+        res = s.new_fields()
+        s.step(q, res, dt, nsteps=2)
+        got = s.to_numpy(q)
+        P.dg_sync_check(s.op)
+    finally:
+        s.close()
+    assert _rel(rhs, O.maxwell_rhs(d, q0)) <= TOL, ("rhs", _rel(rhs, O.maxwell_rhs(d, q0)))
+    want = q0
+    for n in range(2):
+        want = O.lsrk_step(d, want, n * dt, dt)
+    assert _rel(got, want) <= TOL, ("2 steps", _rel(got, want))
+
+
+def test_same_result_as_node_thread_kernel_up_to_rounding(P):
+    # same inputs through the element-thread and the node-thread CUDA-core
+    # kernels: equal within FP32 rounding of the same arithmetic
+    mesh = jittered_delaunay_mesh(40, seed=17)
+    q = random_fields(2 * 40 * 40, 10, seed=5)
+    out = []
+    for prec in ("fp32ept", "fp32simt"):
+        s = P.Solver(*mesh, N=3, precision=prec)
+        out.append(s.to_numpy(s.rhs(s.from_numpy(q))))
+        s.close()
+    assert _rel(out[0], out[1]) <= 1e-6

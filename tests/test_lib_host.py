@@ -166,3 +166,58 @@ def test_error_codes(dgw):
     finally:
         dgw.dg_mesh_destroy(mesh)
     assert _lib.load().dg_mesh_create(None, None, 0, None, 0, ctypes.byref(ctypes.c_void_p())) == _lib.DG_ERR_ARG
+
+
+def test_element_thread_flag_checks(dgw):
+    # DG_SETUP_ELEMENT_THREADS: FP32, N <= 5, uniform medium, no other kernel
+    # or product flag; the kernel report of a host-only operator (no GPU work)
+    from paper_1304_5546_gb300 import _lib
+    VX, VY, EToV = square_grid_mesh(3, 3)
+    mesh = dgw.dg_mesh_create(VX, VY, EToV)
+    E, H = _lib.DG_SETUP_ELEMENT_THREADS, dgw.DG_SETUP_HOST_ONLY
+    try:
+        for N in range(1, 6):
+            op = dgw.dg_operator_setup(mesh, N, dgw.DG_FP32, E | H)
+            try:
+                assert dgw.dg_operator_kernel(op) == ("element threads", 32)
+                # 32 elements per block is the kernel's only size
+                dgw.dg_operator_set_block_elems(op, 32)
+                with pytest.raises(dgw.DGError) as ei:
+                    dgw.dg_operator_set_block_elems(op, 40)
+                assert ei.value.status == _lib.DG_ERR_ARG
+            finally:
+                dgw.dg_op_destroy(op)
+        bad = [(6, dgw.DG_FP32, E), (7, dgw.DG_FP32, E), (3, dgw.DG_FP64, E),
+               (3, dgw.DG_FP32, E | _lib.DG_SETUP_SIMT), (3, dgw.DG_FP32, E | _lib.DG_SETUP_TC),
+               (3, dgw.DG_FP32, E | _lib.DG_SETUP_TC_BF16)]
+        for N, prec, flags in bad:
+            with pytest.raises(dgw.DGError) as ei:
+                dgw.dg_operator_setup(mesh, N, prec, flags | H)
+            assert ei.value.status == _lib.DG_ERR_ARG, (N, prec, flags)
+        with pytest.raises(dgw.DGError) as ei:
+            dgw.dg_operator_setup_media(mesh, 3, np.ones(EToV.shape[0]), dgw.DG_FP32, E | H)
+        assert ei.value.status == _lib.DG_ERR_ARG
+    finally:
+        dgw.dg_mesh_destroy(mesh)
+
+
+def test_default_fp32_kernel_per_order(dgw):
+    # element threads at N <= 2 in a uniform medium, tensor cores above; with
+    # a permittivity: node threads at N = 1, tensor cores from N = 2 on
+    VX, VY, EToV = square_grid_mesh(3, 3)
+    mesh = dgw.dg_mesh_create(VX, VY, EToV)
+    eps = np.full(EToV.shape[0], 2.0)
+    try:
+        for N, want, want_media in ((1, "element threads", "cuda cores"),
+                                    (2, "element threads", "tensor cores"),
+                                    (3, "tensor cores", "tensor cores"),
+                                    (5, "tensor cores", "tensor cores")):
+            for media, w in ((False, want), (True, want_media)):
+                op = (dgw.dg_operator_setup_media(mesh, N, eps, dgw.DG_FP32, dgw.DG_SETUP_HOST_ONLY)
+                      if media else dgw.dg_operator_setup(mesh, N, dgw.DG_FP32, dgw.DG_SETUP_HOST_ONLY))
+                try:
+                    assert dgw.dg_operator_kernel(op)[0] == w, (N, media)
+                finally:
+                    dgw.dg_op_destroy(op)
+    finally:
+        dgw.dg_mesh_destroy(mesh)

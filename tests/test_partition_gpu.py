@@ -55,6 +55,8 @@ CASES = [
     (9, 1, "fp32", 4, 3),       # CUDA cores (default at N = 1)
     (8, 3, "fp64", 7, 3),
     (10, 7, "bf16x3", 2, 2),
+    (13, 2, "fp32ept", 3, 3),   # CUDA cores, one thread per element
+    (12, 5, "fp32ept", 2, 2),
 ]
 
 

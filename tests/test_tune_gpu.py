@@ -37,11 +37,14 @@ def test_tune_times_both_kernels_and_keeps_parity(P, N):
     ms_tc, ms_cc = s.tune(reps=3)
     assert ms_tc > 0 and ms_cc > 0
     # candidates: tensor cores in each block size (two at N <= 4), CUDA cores
-    ncand = 3 if N <= 4 else 2
+    # with a thread per node, CUDA cores with a thread per element (N <= 5)
+    ncand = (3 if N <= 4 else 2) + 1
     assert P.dg_launch_count(s.op) - n0 == ncand * 4
     kernel, elems = s.kernel()
     if kernel == "tensor cores":
         assert elems in ((40, 80) if N <= 4 else (40,))
+    elif kernel == "element threads":
+        assert elems == 32
     else:
         assert elems == {1: 64, 3: 32, 5: 24}[N]
     got = s.to_numpy(s.rhs(s.from_numpy(q)))
@@ -50,7 +53,7 @@ def test_tune_times_both_kernels_and_keeps_parity(P, N):
     assert _rel(got, O.maxwell_rhs(d, q)) <= 1e-5
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32simt", "tf32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32simt", "tf32", "fp32ept"])
 def test_tune_leaves_fixed_kernels_alone(P, prec):
     s = P.Solver(*jittered_delaunay_mesh(4, seed=1), N=3, precision=prec)
     before = s.kernel()
@@ -70,7 +73,8 @@ def test_tune_with_tensor_cores_forced_chooses_the_block_size(P):
 
 @pytest.mark.parametrize("N,prec,sizes", [(3, "fp32tc", (80, 40)), (4, "fp32tc", (40, 80)),
                                           (5, "fp32tc", (40,)), (3, "fp32simt", (32,)),
-                                          (2, "fp64", (16,)), (3, "bf16x3", (80,))])
+                                          (2, "fp64", (16,)), (3, "bf16x3", (80,)),
+                                          (2, "fp32ept", (32,))])
 def test_block_elems_selection(P, N, prec, sizes):
     s = P.Solver(*jittered_delaunay_mesh(6, seed=3), N=N, precision=prec)
     assert s.kernel()[1] == sizes[0]
