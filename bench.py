@@ -373,6 +373,7 @@ def run_ours(args):
         return None
 
     K = s.K
+    kernel_kind = s.kernel()[0]
     value = replica_throughput(world, K, args.steps, ms)
     peaks, peak_kind = measured_peaks()
     bytes_step = K * step_bytes_per_element(N) * (2 if args.precision == "fp64" else 1)
@@ -405,8 +406,10 @@ def run_ours(args):
             "workload": "single large mesh: jittered Delaunay unit square n=%d (K=%d), N=%d, "
                         "Gaussian pulse w=0.05, LSRK(5,4) steps" % (args.n, K, N),
             "K": K, "N": N, "Np": s.Np, "precision": args.precision,
-            "products": ("CUDA cores" if (args.simt or args.precision == "fp64")
-                         else "tensor cores (tcgen05, %s)" % PRODUCTS[args.precision]),
+            "products": {"tensor cores": "tensor cores (tcgen05, %s)" % PRODUCTS.get(
+                             args.precision, "3xTF32"),
+                         "cuda cores": "CUDA cores, one thread per node",
+                         "element threads": "CUDA cores, one thread per element"}[kernel_kind],
             "mesh_seed": 2024,
             "l2": "inputs larger than L2 (q, q_tmp, res: %.0f MB)" % (
                 3 * 3 * s.fstride * (8 if args.precision == "fp64" else 4) / 1e6),
@@ -421,8 +424,9 @@ def run_ours(args):
             "frac": achieved / peaks["hbm_gbs"],
             "traffic": traffic,
             "peak_kind": peak_kind,
-            "kernel": ("dg_stage_kernel" if (args.simt or args.precision == "fp64")
-                       else "dg_stage_tc_kernel") + " (fused RHS + LSRK stage)",
+            "kernel": {"tensor cores": "dg_stage_tc_kernel", "cuda cores": "dg_stage_kernel",
+                       "element threads": "dg_stage_ept_kernel"}[kernel_kind]
+                      + " (fused RHS + LSRK stage)",
             "bytes_per_element_step": step_bytes_per_element(N),
         },
         "e2e": {
@@ -1225,9 +1229,11 @@ def main(argv=None):
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--n", type=int, default=707, help="mesh resolution (K = 2 n^2)")
     ap.add_argument("--precision", default="fp32",
-                    choices=["fp32", "fp64", "tf32", "bf16", "bf16x3"],
-                    help="fp32: 3xTF32 tensor-core products; tf32 / bf16 / bf16x3: the "
-                         "precision-path variants (FP32 fields and accumulation)")
+                    choices=["fp32", "fp64", "tf32", "bf16", "bf16x3", "fp32tc", "fp32ept"],
+                    help="fp32: the default FP32 kernel of the order (3xTF32 tensor-core "
+                         "products at N = 5); fp32tc / fp32ept: the tensor-core / "
+                         "element-thread kernel; tf32 / bf16 / bf16x3: the precision-path "
+                         "variants (FP32 fields and accumulation)")
     ap.add_argument("--simt", action="store_true", help="FP32 products on CUDA cores")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -27,8 +27,8 @@
 // blockIdx.x + it * gridDim.x, lane e owning element 32 block + e.  All a
 // block owns is contiguous in HBM (its q and residual values per field, its
 // geometry records and face codes) and is fetched by the warp's lanes with
-// 16-byte cp.async copies into a ring of S stage buffers, S - 1 blocks ahead,
-// one commit group per block.  A lane reads its element's values from the
+// 16-byte cp.async copies into a ring of S = 2 stage buffers, one block
+// ahead, one commit group per block.  A lane reads its element's values from the
 // stage buffer (a stride of Np words: conflict-free for odd Np, 8-byte loads
 // for even Np), gathers its neighbours' face-node traces from global memory
 // (L2) into registers one block ahead, writes its updated values back into
@@ -54,9 +54,13 @@ struct EptOps {
   float l3[Np];         // (1 + s_n) / 2: weight of vertex 3
 };
 
-// Stage buffers per warp: as many as keep several warps resident per SM
-// (the shared memory of a stage grows with Np).
-__host__ __device__ constexpr int ept_stages(int N) { return N == 1 ? 4 : N == 2 ? 3 : 2; }
+// Stage buffers per warp: two at every order -- one block computed while
+// the next one lands.  Deeper rings measured slower on GB300 (N = 1, ms per
+// step on the order-sweep mesh: 0.542 with two, 0.598 with three, 0.620 with
+// four; N = 2: 0.666 with two, 0.673 with three), because the shared memory
+// they take leaves fewer warps resident per SM, and more warps hide more of
+// the latency of a block's loads and gathers.
+__host__ __device__ constexpr int ept_stages(int) { return 2; }
 
 // Where the products read the reference matrices: false -- the by-value
 // parameter, every output node unrolled, each entry an FMA's constant

@@ -4,7 +4,7 @@ reference matrices as constant operands; N = 1..5, uniform medium) against
 the FP64 oracle on the same seeded inputs.
 
 Each warp of that kernel walks blocks of 32 elements through its own ring
-of S stage buffers (S = 4 at N = 1, 3 at N = 2, 2 above).  Besides small
+of S = 2 stage buffers.  Besides small
 meshes, every order runs on a mesh large enough that each warp of the
 launch handles at least S + 2 blocks, so the ring wraps, the one-block-ahead
 neighbour gather crosses blocks many times, and the last block is ragged.
@@ -43,7 +43,7 @@ def _warps_bound(N, sms=152, smem_per_sm=233472, reserved=1024, max_ctas=32):
     # one warp per CTA; its shared memory is S stage buffers of 32 elements:
     # q and residual (6 Np values), 13 geometry values, 3 face codes
     Np = (N + 1) * (N + 2) // 2
-    S = {1: 4, 2: 3}.get(N, 2)
+    S = 2
     smem = S * 128 * (6 * Np + 16)
     return sms * min(max_ctas, smem_per_sm // (smem + reserved)), S
 
