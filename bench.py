@@ -385,7 +385,8 @@ def run_ours(args):
             from paper_1304_5546_gb300.build import kernel_source_hash
             t = json.load(open(tpath))
             key = "N%d_%s" % (N, args.precision)
-            if t.get("kernel_hash") == kernel_source_hash() and key in t.get("per_element", {}):
+            fam = t.get("kernel_family")
+            if t.get("kernel_hash") == kernel_source_hash(fam) and key in t.get("per_element", {}):
                 traffic = t["per_element"][key] * K * 5 * args.steps / launches
         except Exception:
             traffic = None

@@ -89,15 +89,29 @@ def build(force=False, verbose=False, extra_flags=(), checked=False):
 
 
 
-def kernel_source_hash():
+# Source files that define each stage-kernel family (kernel_source_hash)
+KERNEL_FAMILIES = {
+    "tc": lambda n: (n.startswith("kernels_tc") or n == "kernels.cuh"
+                     or n in ("launch.h", "ptx.cuh")),
+    "ept": lambda n: (n.startswith("kernels_ept") or n == "kernels.cuh"
+                      or n in ("launch.h", "ptx.cuh")),
+}
+
+
+def kernel_source_hash(family=None):
     """Short hash of the kernel sources (code only: // comments, trailing
     blanks and empty lines are left out); profiles record it so that stale
-    counter captures are not reported for a changed kernel."""
+    counter captures are not reported for a changed kernel.  family: only
+    the files of one stage-kernel family (KERNEL_FAMILIES: the tensor-core
+    kernel "tc", the element-thread kernel "ept"); None: every kernel
+    source."""
     import hashlib
     import re
     h = hashlib.sha256()
+    pick = KERNEL_FAMILIES[family] if family else (
+        lambda n: n.startswith("kernels") or n in ("launch.h", "ptx.cuh"))
     for name in sorted(os.listdir(CSRC)):
-        if name.startswith("kernels") or name in ("launch.h", "ptx.cuh"):
+        if pick(name):
             with open(os.path.join(CSRC, name), encoding="utf-8") as f:
                 lines = (re.sub(r"//.*$", "", line).rstrip() for line in f)
                 code = "\n".join(line for line in lines if line)

@@ -27,8 +27,11 @@
 // blockIdx.x + it * gridDim.x, lane e owning element 32 block + e.  All a
 // block owns is contiguous in HBM (its q and residual values per field, its
 // geometry records and face codes) and is fetched by the warp's lanes with
-// 16-byte cp.async copies into a ring of S = 2 stage buffers, one block
-// ahead, one commit group per block.  A lane reads its element's values from the
+// 16-byte cp.async copies, one commit group per block, one block ahead: the
+// values, residual and geometry into a ring of S = 2 stage buffers, the face
+// codes -- all the neighbour gather needs -- one block earlier still, into a
+// ring of three.  So the gather of block it + 1 is issued as block it starts
+// and has that whole block to land, and so do block it + 1's bulk copies.  A lane reads its element's values from the
 // stage buffer (a stride of Np words: conflict-free for odd Np, 8-byte loads
 // for even Np), gathers its neighbours' face-node traces from global memory
 // (L2) into registers one block ahead, writes its updated values back into
@@ -82,18 +85,22 @@ struct EptLayout {
   static constexpr int E = 32;             // elements per block: one per lane
   static constexpr int S = ept_stages(N);  // stage buffers of the warp's ring
   static constexpr int FQ = E * Np;        // floats of one field of a block
-  // stage buffer: q[3][E Np], res[3][E Np], geo[E][kGeo], conn[E][3]
+  // stage buffer: q[3][E Np], res[3][E Np], geo[E][kGeo]
   static constexpr int QB = FQ * 4;
   static constexpr int GB = E * kGeo * 4;
   static constexpr int CB = E * 3 * 4;
-  static constexpr int STAGE_BYTES = 6 * QB + GB + CB;
+  static constexpr int STAGE_BYTES = 6 * QB + GB;
+  // face codes: a ring of three blocks' codes, one block ahead of the stages
+  static constexpr int CONN_OFF = S * STAGE_BYTES, CONN_BYTES = 3 * CB;
   // operator table (ept_table): row width RS floats, Dr and Ds parts DW
   // wide (Np - 3 interior nodes, padded to 4), LIFT part LW wide
   static constexpr bool TBL = ept_table(N);
   static constexpr int DW = (Np - 3 + 3) / 4 * 4, LW = (Nafp + 3) / 4 * 4;
   static constexpr int RS = 2 * DW + LW;
   static constexpr int TBL_BYTES = TBL ? Np * RS * 4 : 0;
-  static constexpr int SMEM_BYTES = S * STAGE_BYTES + TBL_BYTES;
+  static constexpr int TBL_OFF = CONN_OFF + CONN_BYTES;
+  static constexpr int SMEM_BYTES = TBL_OFF + TBL_BYTES;
+  static_assert(S == 2, "the pipeline below waits for one group per block");
   static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0, "16-byte copies");
   static_assert(sizeof(EptOps<N>) == 4 * ept_ops_floats(N), "parameter layout");
 };
@@ -173,10 +180,20 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
   auto stage = [&](int it) {
     return reinterpret_cast<float*>(smem + (it % S) * L::STAGE_BYTES);
   };
-  // the warp fetches everything block `it` owns into its stage buffer; the
-  // first stage of a step does not read the residual (a_1 = 0), nor does the
-  // right-hand-side mode.  A block never reaches past the records' padding
-  // (Kpad, a multiple of 64) nor past a field (fstride >= Kpad Np).
+  auto codes = [&](int it) {
+    return reinterpret_cast<int*>(smem + L::CONN_OFF + (it % 3) * L::CB);
+  };
+  // one commit group per block: the warp fetches block `it`'s values,
+  // residual and geometry into its stage buffer, and the face codes of block
+  // it + 1 into the code ring (the next block's neighbour gather needs only
+  // those).  The first stage of a step does not read the residual (a_1 = 0),
+  // nor does the right-hand-side mode.  A block never reaches past the
+  // records' padding (Kpad, a multiple of 64) nor past a field (fstride >=
+  // Kpad Np).
+  auto fetch_codes = [&](int it) {
+    const int64_t k0 = static_cast<int64_t>(b0 + it * G) * 32;
+    ept_fetch<L::CB / 16>(codes(it), p.conn + k0 * 3, lane);
+  };
   auto issue = [&](int it) {
     float* st = stage(it);
     const int64_t k0 = static_cast<int64_t>(b0 + it * G) * 32;
@@ -189,15 +206,15 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
         ept_fetch<L::QB / 16>(st + (3 + f) * FQ, p.res + f * p.fstride + k0 * Np, lane);
     }
     ept_fetch<L::GB / 16>(st + 6 * FQ, p.geo + k0 * kGeo, lane);
-    ept_fetch<L::CB / 16>(st + 6 * FQ + 32 * kGeo, p.conn + k0 * 3, lane);
+    if (it + 1 < niter) fetch_codes(it + 1);
   };
 
   // neighbour traces (Hx, Hy, Ez) of this lane's element at its Nafp face
-  // nodes, for block `it` (its face codes are in its stage buffer); zero at
+  // nodes, for block `it` (its face codes are in the code ring); zero at
   // PEC faces (code -1), whose flux takes the mirror state instead
   float trc[3][Nafp];
   auto gather = [&](int it) {
-    const int* sc = reinterpret_cast<const int*>(stage(it) + 6 * FQ + 32 * kGeo);
+    const int* sc = codes(it);
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
       const int code = sc[lane * 3 + f];
@@ -224,7 +241,7 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
     }
   };
 
-  float* tbl = reinterpret_cast<float*>(smem + S * L::STAGE_BYTES);
+  float* tbl = reinterpret_cast<float*>(smem + L::TBL_OFF);
   if constexpr (L::TBL) {
     // the operator table, from the operator's device copies of Dr, Ds, LIFT
     for (int idx = lane; idx < Np * L::RS; idx += 32) {
@@ -241,23 +258,26 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
     }
   }
 
-#pragma unroll
-  for (int j = 0; j < S - 1; ++j) {
-    if (j < niter) issue(j);
-    cp_async_commit();
-  }
-  cp_async_wait<S - 2>();  // block 0 has landed
+  // prologue: block 0's codes and group 0, then block 0's gather
+  fetch_codes(0);
+  issue(0);
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncwarp();
   gather(0);
 
   for (int it = 0; it < niter; ++it) {
-    // refill the stage the previous block released
-    if (it + S - 1 < niter) issue(it + S - 1);
+    // refill the stage the previous block released; then block it has
+    // landed (its group was committed one block ago), and so have the codes
+    // of block it + 1
+    if (it + 1 < niter) issue(it + 1);
     cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
 
     float* sq = stage(it);
     const float* sg = sq + 6 * FQ;
-    const int* sc = reinterpret_cast<const int*>(sg + 32 * kGeo);
+    const int* sc = codes(it);
     const int k0 = (b0 + it * G) * 32;
     float* own = sq + lane * Np;  // this lane's slot in field 0 (fields FQ apart)
 
@@ -289,10 +309,8 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
       }
     }
 
-    // ---- the next block has landed: gather its traces (their L2 latency
-    // hides behind this block's products)
-    cp_async_wait<S - 2>();
-    __syncwarp();
+    // ---- the next block's neighbour traces (their L2 latency hides behind
+    // this block's products and stores)
     if (it + 1 < niter) gather(it + 1);
 
     // ---- volume operands minus their linear part (exactly zero at the
