@@ -1,8 +1,9 @@
 """GPU check of the checked build (libdgwave_checked.so, DGW_DEVICE_CHECKS):
 its stage kernels test every face connection code and block-table entry
 they read before using it.  On valid input the checks must change nothing:
-the same solves (tensor cores and CUDA cores, FP32 and FP64, a batch with
-media and a point source, a partition) give bit for bit the results of the
+the same solves (tensor cores, node-thread and element-thread CUDA cores,
+FP32 and FP64, a batch with media and a point source, a partition) give bit
+for bit the results of the
 normal library, and every status check stays DG_OK.  The checked library
 runs in a child process (DGWAVE_CHECKED=1 selects it at import)."""
 import os
@@ -27,7 +28,7 @@ from synth import gaussian_pulse, jittered_delaunay_mesh, random_permittivity
 out = {"lib": P._lib.LIB_PATH}
 mesh = jittered_delaunay_mesh(12, seed=3)
 for name, N, prec in (("tc5", 5, "fp32"), ("tc3", 3, "fp32"), ("simt4", 4, "fp32simt"),
-                      ("fp64", 3, "fp64")):
+                      ("fp64", 3, "fp64"), ("ept2", 2, "fp32"), ("ept1", 1, "fp32")):
     s = P.Solver(*mesh, N=N, precision=prec)
     x, y = s.nodes()
     q = s.from_numpy(np.stack(gaussian_pulse(x, y, 0.4, 0.6, 0.15)))
@@ -75,6 +76,6 @@ def test_checked_build_matches_normal_build(tmp_path):
     checked = _run(str(tmp_path / "checked.npz"), True)
     assert str(checked["lib"]).endswith("libdgwave_checked.so")
     assert str(normal["lib"]).endswith("libdgwave.so")
-    for key in ("tc5", "tc3", "simt4", "fp64", "part", "batch"):
+    for key in ("tc5", "tc3", "simt4", "fp64", "ept2", "ept1", "part", "batch"):
         assert np.array_equal(normal[key], checked[key]), key
     assert np.array_equal(normal["part"], normal["tc5"])
