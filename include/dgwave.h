@@ -229,7 +229,9 @@ dg_status dg_operator_set_alpha(dg_op* op, double alpha);
  * differs from enable = 0 by rounding only (the default kernel lets the
  * compiler contract multiply-adds).  It applies to the default 3xTF32
  * products; the other product variants, operators on the CUDA-core kernel
- * (FP64, DG_SETUP_SIMT, FP32 at N = 1 by default) and batches ignore it.
+ * (FP64, DG_SETUP_SIMT, FP32 media at N = 1 by default), the element-thread
+ * kernel (FP32 at N <= 2 by default, DG_SETUP_ELEMENT_THREADS) and batches
+ * ignore it.
  * Measured slower than the default on GB300 at every order, so off by
  * default.  Errors: DG_ERR_ARG (NULL, enable not 0 or 1).                  */
 dg_status dg_operator_set_face_pairs(dg_op* op, int32_t enable);

@@ -495,7 +495,7 @@ def dg_server_stats(server):
 # ------------------------------------------------------------ convenience
 # FP32-field variants: name -> dg_operator_setup flags
 _FP32_VARIANTS = {
-    "fp32": 0,                              # per order: CUDA cores at N = 1, else 3xTF32
+    "fp32": 0,                              # per order: element threads at N <= 2, else 3xTF32
     "fp32tc": _lib.DG_SETUP_TC,             # 3xTF32 tensor-core products at every order
     "fp32simt": _lib.DG_SETUP_SIMT,         # CUDA-core FP32 products
     "fp32ept": _lib.DG_SETUP_ELEMENT_THREADS,  # CUDA cores, one thread per element (N <= 5)
@@ -602,7 +602,7 @@ class Solver:
     Field tensors have shape (3, field_stride) on the operator's device, in
     the operator's precision; ``view(q)`` gives the (3, K, Np) window.
     ``precision``: "fp64", or an FP32-field variant: "fp32" (default:
-    tensor cores, 3xTF32, from N = 2 on; CUDA cores at N = 1), "fp32tc"
+    element threads at N <= 2, tensor cores (3xTF32) above), "fp32tc"
     (tensor cores at every order), "fp32simt", "fp32ept" (one thread per
     element on the CUDA cores, N <= 5), "tf32", "bf16", "bf16x3".
     ``eps``: per-element permittivity (K values; dg_operator_setup_media).
