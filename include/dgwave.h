@@ -113,14 +113,13 @@ typedef struct dg_point_source {
 #define DG_SETUP_TC_BF16 8   /* one product, both operands rounded to BF16   */
 #define DG_SETUP_TC_BF16X3 16 /* three BF16 products: hi/lo split of both
                                  operands (X_hi Op_hi + X_hi Op_lo + X_lo Op_hi) */
-/* Default FP32 products per order: the element-thread kernel at N <= 2 in a
- * uniform medium, the tensor cores (3xTF32) otherwise from N = 2 on, the
- * node-thread CUDA-core kernel at N = 1 with a permittivity -- the fastest
- * measured at each order.  Overrides:                                     */
+/* Default FP32 products per order: the element-thread kernel at N <= 2,
+ * the tensor cores (3xTF32) from N = 3 on -- the fastest measured at each
+ * order, with or without a permittivity.  Overrides:                      */
 #define DG_SETUP_TC 32       /* FP32: tensor cores (3xTF32) at every order   */
-#define DG_SETUP_ELEMENT_THREADS 64 /* FP32, N <= 5, uniform medium: the CUDA
-                                cores with one thread per element, the
-                                reference matrices as constant operands     */
+#define DG_SETUP_ELEMENT_THREADS 64 /* FP32, N <= 5: the CUDA cores with one
+                                thread per element, the reference matrices
+                                as constant operands                        */
 
 #define DG_N_MAX 7
 
@@ -163,12 +162,11 @@ void dg_mesh_destroy(dg_mesh* mesh);
  * Surface Contribution"), and the trace maps.  FP32 operators run the
  * element-local products (Dr, Ds, LIFT) on the tensor cores as three TF32
  * products per term (hi/lo splits of both operands, FP32 accumulation) from
- * N = 3 on (N = 2 with a permittivity), and on the CUDA cores below: one
- * thread per element in a uniform medium (the element-thread kernel), one
- * thread per node with a permittivity at N = 1.  DG_SETUP_TC selects the
+ * N = 3 on, and on the CUDA cores below, one thread per element (the
+ * element-thread kernel).  DG_SETUP_TC selects the
  * tensor cores at every order, DG_SETUP_SIMT the node-thread CUDA-core FP32
- * kernel, DG_SETUP_ELEMENT_THREADS the element-thread kernel (N <= 5,
- * uniform medium), and one of DG_SETUP_TC_TF32 / _BF16 / _BF16X3 a
+ * kernel, DG_SETUP_ELEMENT_THREADS the element-thread kernel (N <= 5), and
+ * one of DG_SETUP_TC_TF32 / _BF16 / _BF16X3 a
  * lower-precision product variant (the precision path of the element-local
  * contractions).  FP64
  * operators always use the CUDA cores.  Unless flags has
@@ -178,8 +176,8 @@ void dg_mesh_destroy(dg_mesh* mesh);
  * destroyed afterwards.
  * Errors: DG_ERR_ARG (unknown flags; more than one product variant, or one
  * with DG_FP64 or DG_SETUP_SIMT; DG_SETUP_TC with DG_FP64 or DG_SETUP_SIMT;
- * DG_SETUP_ELEMENT_THREADS with DG_FP64, N > 5, a permittivity or another
- * kernel or product flag;
+ * DG_SETUP_ELEMENT_THREADS with DG_FP64, N > 5 or another kernel or product
+ * flag;
  * also when a field would hold 2^31 or more values:
  * kernel offsets inside a field are 32-bit), DG_ERR_ORDER (N < 1 or
  * N > DG_N_MAX), DG_ERR_CUDA, DG_ERR_OOM.  *out is written only on success. */
@@ -229,9 +227,8 @@ dg_status dg_operator_set_alpha(dg_op* op, double alpha);
  * differs from enable = 0 by rounding only (the default kernel lets the
  * compiler contract multiply-adds).  It applies to the default 3xTF32
  * products; the other product variants, operators on the CUDA-core kernel
- * (FP64, DG_SETUP_SIMT, FP32 media at N = 1 by default), the element-thread
- * kernel (FP32 at N <= 2 by default, DG_SETUP_ELEMENT_THREADS) and batches
- * ignore it.
+ * (FP64, DG_SETUP_SIMT), the element-thread kernel (FP32 at N <= 2 by
+ * default, DG_SETUP_ELEMENT_THREADS) and batches ignore it.
  * Measured slower than the default on GB300 at every order, so off by
  * default.  Errors: DG_ERR_ARG (NULL, enable not 0 or 1).                  */
 dg_status dg_operator_set_face_pairs(dg_op* op, int32_t enable);
@@ -287,7 +284,7 @@ dg_status dg_get_maps(const dg_op* op, int64_t* vmapM, int64_t* vmapP);
  *   - the same in its alternative size where there is one (40 elements at
  *     N = 1..3, where the default is 80; 80 at N = 4, where it is 40);
  *   - unless DG_SETUP_TC, the CUDA cores: the node-thread kernel, and the
- *     element-thread kernel at N <= 5 in a uniform medium.
+ *     element-thread kernel at N <= 5.
  * Writes the milliseconds per launch of the fastest tensor-core candidate
  * and of the fastest CUDA-core candidate (NULL outputs skipped; -1 where not
  * timed).  Operators whose set-up fixed the kernel and products (FP64,

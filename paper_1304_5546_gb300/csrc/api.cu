@@ -284,10 +284,26 @@ cudaError_t launch_order_tc_media(const dg_op* op, const dgw::StageArgs<float>& 
   }
 }
 
+cudaError_t launch_order_ept_media(const dg_op* op, const dgw::StageArgs<float>& a, int mode,
+                                   cudaStream_t s) {
+  if (op->ept_ops.size() != static_cast<size_t>(dgw::ept_ops_floats(op->N)))
+    return cudaErrorInvalidValue;
+  const float* t = op->ept_ops.data();
+  switch (op->N) {
+    case 1: return dgw::launch_stage_ept_media<1>(a, t, mode, op->num_sms, s);
+    case 2: return dgw::launch_stage_ept_media<2>(a, t, mode, op->num_sms, s);
+    case 3: return dgw::launch_stage_ept_media<3>(a, t, mode, op->num_sms, s);
+    case 4: return dgw::launch_stage_ept_media<4>(a, t, mode, op->num_sms, s);
+    case 5: return dgw::launch_stage_ept_media<5>(a, t, mode, op->num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
 cudaError_t launch_order_media(const dg_op* op, const dgw::StageArgs<T>& a, int mode,
                                cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
+    if (op->use_ept) return launch_order_ept_media(op, a, mode, s);
     if (op->use_tc) return launch_order_tc_media(op, a, mode, s);
   }
   switch (op->N) {
@@ -373,7 +389,7 @@ bool tc_has_alt_n(int N) {
 // Elements per block of the kernel the operator runs (alt: the alternative
 // size of the tensor-core kernel).
 int block_elems(const dg_op* op, int alt) {
-  if (op->precision == DG_FP32 && op->use_ept && !op->media()) return 32;
+  if (op->precision == DG_FP32 && op->use_ept) return 32;
   if (op->precision == DG_FP32 && op->use_tc)
     return 40 * dgw::tc_tiles(op->N, op->tc_prec, alt != 0 && op->tc_prec == dgw::kTcTf32x3);
   return dgw::simt_block_elems(op->N, op->precision == DG_FP64);
@@ -507,12 +523,12 @@ dg_status operator_setup(const dg_mesh* mesh, int32_t N, const double* eps, int3
                 "dg_operator_setup: at most one tensor-core product variant, FP32 only, not with "
                 "DG_SETUP_SIMT");
   if ((flags & DG_SETUP_ELEMENT_THREADS) &&
-      (precision != DG_FP32 || N > dgw::kEptMaxN || eps ||
+      (precision != DG_FP32 || N > dgw::kEptMaxN ||
        (flags & (DG_SETUP_SIMT | DG_SETUP_TC | DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 |
                  DG_SETUP_TC_BF16X3))))
     return fail(DG_ERR_ARG,
-                "dg_operator_setup: DG_SETUP_ELEMENT_THREADS is for FP32 at N <= %d in a uniform "
-                "medium, without another kernel or product flag",
+                "dg_operator_setup: DG_SETUP_ELEMENT_THREADS is for FP32 at N <= %d, without "
+                "another kernel or product flag",
                 dgw::kEptMaxN);
   dg_op* op = nullptr;
   try {
@@ -524,17 +540,17 @@ dg_status operator_setup(const dg_mesh* mesh, int32_t N, const double* eps, int3
     op->Nafp = op->ref.Nafp;
     op->precision = precision;
     op->flags = flags;
-    // FP32 default: the element-thread kernel at N <= 2 in a uniform medium,
-    // the tensor cores otherwise from N = 2 on, the node-thread CUDA-core
-    // kernel at N = 1 with a permittivity (order sweep at ~1e7 nodal values
-    // per field, ms/step: N = 1 element threads 0.65, node threads 0.87,
-    // tensor cores 1.39; N = 2 0.63, 0.98, 0.83; N = 3 0.70, 0.90, 0.60)
+    // FP32 default: the element-thread kernel at N <= 2, the tensor cores
+    // above (order sweep at ~1e7 nodal values per field, ms/step, element
+    // threads / node threads / tensor cores: N = 1 0.68, 0.87, 1.40; N = 2
+    // 0.64, 0.98, 0.83; N = 3 0.64, 0.90, 0.60; with a permittivity: N = 1
+    // 0.70, 0.86, 1.37; N = 2 0.70, -, 0.82; N = 3 0.64, -, 0.61)
     op->use_tc = (precision == DG_FP32) && !(flags & DG_SETUP_SIMT) &&
                  (N >= 2 || variants != 0 || (flags & DG_SETUP_TC));
     const int32_t chosen = DG_SETUP_SIMT | DG_SETUP_TC | DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 |
                            DG_SETUP_TC_BF16X3;
     op->use_ept = (flags & DG_SETUP_ELEMENT_THREADS) ||
-                  (precision == DG_FP32 && !eps && !(flags & chosen) && N <= 2);
+                  (precision == DG_FP32 && !(flags & chosen) && N <= 2);
     op->tc_prec = (flags & DG_SETUP_TC_TF32)    ? dgw::kTcTf32
                   : (flags & DG_SETUP_TC_BF16)  ? dgw::kTcBf16
                   : (flags & DG_SETUP_TC_BF16X3) ? dgw::kTcBf16x3
@@ -775,7 +791,7 @@ extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, dou
   // candidates: tensor cores (3xTF32) in the default and, where there is one,
   // the alternative element-block size; unless DG_SETUP_TC, the CUDA cores:
   // the node-per-thread kernel, and the element-thread kernel where the
-  // operator has its tables (N <= kEptMaxN, uniform medium)
+  // operator has its tables (N <= kEptMaxN)
   struct Cand {
     bool tc;
     int alt;
@@ -786,7 +802,7 @@ extern "C" dg_status dg_operator_tune(dg_op* op, int32_t reps, void* stream, dou
   if (tc_has_alt_n(op->N)) cand[nc++] = {true, 1, false};
   if (!(op->flags & DG_SETUP_TC)) {
     cand[nc++] = {false, 0, false};
-    if (!op->media() && op->ept_ops.size() == static_cast<size_t>(dgw::ept_ops_floats(op->N)))
+    if (op->ept_ops.size() == static_cast<size_t>(dgw::ept_ops_floats(op->N)))
       cand[nc++] = {false, 0, true};
   }
   if (nc < 2) return DG_OK;
@@ -881,7 +897,7 @@ extern "C" dg_status dg_operator_set_block_elems(dg_op* op, int32_t elems) {
 extern "C" dg_status dg_operator_kernel(const dg_op* op, int32_t* kernel, int32_t* elems) {
   dgw::clear_error();
   if (!op) return fail(DG_ERR_ARG, "dg_operator_kernel: NULL operator");
-  const bool ept = op->precision == DG_FP32 && op->use_ept && !op->media();
+  const bool ept = op->precision == DG_FP32 && op->use_ept;
   const bool tc = op->precision == DG_FP32 && op->use_tc && !ept;
   if (kernel)
     *kernel = ept ? DG_KERNEL_ELEMENT_THREADS : tc ? DG_KERNEL_TENSOR_CORES : DG_KERNEL_CUDA_CORES;

@@ -79,15 +79,17 @@ __host__ __device__ constexpr int ept_interior_node(int N, int c) {
   return c < N - 1 ? c + 1 : c + 2;
 }
 
-template <int N>
+template <int N, bool MEDIA = false>
 struct EptLayout {
   static constexpr int Np = Order<N>::Np, Nfp = Order<N>::Nfp, Nafp = Order<N>::Nafp;
   static constexpr int E = 32;             // elements per block: one per lane
   static constexpr int S = ept_stages(N);  // stage buffers of the warp's ring
   static constexpr int FQ = E * Np;        // floats of one field of a block
-  // stage buffer: q[3][E Np], res[3][E Np], geo[E][kGeo]
+  // stage buffer: q[3][E Np], res[3][E Np], geo[E][GEO] (MEDIA: the
+  // per-element-permittivity records, launch.h)
+  static constexpr int GEO = MEDIA ? kGeoMedia : kGeo;
   static constexpr int QB = FQ * 4;
-  static constexpr int GB = E * kGeo * 4;
+  static constexpr int GB = E * GEO * 4;
   static constexpr int CB = E * 3 * 4;
   static constexpr int STAGE_BYTES = 6 * QB + GB;
   // face codes: a ring of three blocks' codes, one block ahead of the stages
@@ -159,10 +161,11 @@ __device__ __forceinline__ void ept_store(float* dst, const float* src, int n, i
   }
 }
 
-template <int N, int MODE>
+template <int N, int MODE, bool MEDIA>
 __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float> p,
                                                           const EptOps<N> ops) {
-  using L = EptLayout<N>;
+  using L = EptLayout<N, MEDIA>;
+  constexpr int GEO = L::GEO;
   constexpr int Np = L::Np, Nfp = L::Nfp, Nafp = L::Nafp, S = L::S, FQ = L::FQ;
   extern __shared__ __align__(128) unsigned char smem[];
 
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
       for (int f = 0; f < 3; ++f)
         ept_fetch<L::QB / 16>(st + (3 + f) * FQ, p.res + f * p.fstride + k0 * Np, lane);
     }
-    ept_fetch<L::GB / 16>(st + 6 * FQ, p.geo + k0 * kGeo, lane);
+    ept_fetch<L::GB / 16>(st + 6 * FQ, p.geo + k0 * GEO, lane);
     if (it + 1 < niter) fetch_codes(it + 1);
   };
 
@@ -285,27 +288,48 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
     ept_ld_row<Np>(hx, own);
     ept_ld_row<Np>(hy, own + FQ);
     ept_ld_row<Np>(ez, own + 2 * FQ);
-    const float* ge = sg + lane * kGeo;
+    const float* ge = sg + lane * GEO;
     const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
+    // row scales of the right-hand side (media records; 1 otherwise)
+    const float sH = MEDIA ? ge[17] : 1.f, sE = MEDIA ? ge[18] : 1.f;
 
     // ---- upwind flux (Eq. max2d-numflux) times Fscale/2 at every face node
     float F0[Nafp], F1[Nafp], F2[Nafp];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
       const bool pec = sc[lane * 3 + f] < 0;
-      const float nx = ge[4 + 3 * f], ny = ge[5 + 3 * f], fsc = ge[6 + 3 * f];
-      const float fa = fsc * p.alpha, fnx = fsc * nx, fny = fsc * ny;
+      if constexpr (MEDIA) {
+        // the exact interface Riemann solution: fz = cH [Ht] - cE [Ez],
+        // lifted terms (-Z- ny fz, Z- nx fz, fz)
+        const float nx = ge[4 + 4 * f], ny = ge[5 + 4 * f], cH = ge[6 + 4 * f],
+                    cE = ge[7 + 4 * f], zM = ge[16];
 #pragma unroll
-      for (int jj = 0; jj < Nfp; ++jj) {
-        const int n = face_node_dev(N, f, jj);
-        const int j = f * Nfp + jj;
-        const float dHx = pec ? 0.f : hx[n] - trc[0][j];
-        const float dHy = pec ? 0.f : hy[n] - trc[1][j];
-        const float dEz = pec ? 2.f * ez[n] : ez[n] - trc[2][j];
-        const float ndH = nx * dHx + ny * dHy;
-        F0[j] = fny * dEz + fa * (ndH * nx - dHx);
-        F1[j] = -fnx * dEz + fa * (ndH * ny - dHy);
-        F2[j] = fny * dHx - fnx * dHy - fa * dEz;
+        for (int jj = 0; jj < Nfp; ++jj) {
+          const int n = face_node_dev(N, f, jj);
+          const int j = f * Nfp + jj;
+          const float dHx = pec ? 0.f : hx[n] - trc[0][j];
+          const float dHy = pec ? 0.f : hy[n] - trc[1][j];
+          const float dEz = pec ? 2.f * ez[n] : ez[n] - trc[2][j];
+          const float fz = cH * (ny * dHx - nx * dHy) - cE * dEz;
+          F0[j] = -zM * ny * fz;
+          F1[j] = zM * nx * fz;
+          F2[j] = fz;
+        }
+      } else {
+        const float nx = ge[4 + 3 * f], ny = ge[5 + 3 * f], fsc = ge[6 + 3 * f];
+        const float fa = fsc * p.alpha, fnx = fsc * nx, fny = fsc * ny;
+#pragma unroll
+        for (int jj = 0; jj < Nfp; ++jj) {
+          const int n = face_node_dev(N, f, jj);
+          const int j = f * Nfp + jj;
+          const float dHx = pec ? 0.f : hx[n] - trc[0][j];
+          const float dHy = pec ? 0.f : hy[n] - trc[1][j];
+          const float dEz = pec ? 2.f * ez[n] : ez[n] - trc[2][j];
+          const float ndH = nx * dHx + ny * dHy;
+          F0[j] = fny * dEz + fa * (ndH * nx - dHx);
+          F1[j] = -fnx * dEz + fa * (ndH * ny - dHy);
+          F2[j] = fny * dHx - fnx * dHy - fa * dEz;
+        }
       }
     }
 
@@ -357,6 +381,11 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
       rHx = l0 - (ry * dzr + sy * dzs);
       rHy = l1 + (rx * dzr + sx * dzs);
       rEz = l2 + (ca + cb);
+      if (MEDIA) {
+        rHx *= sH;
+        rHy *= sH;
+        rEz *= sE;
+      }
     };
 
     // ---- stage update (or the right-hand side) into this lane's own slots
@@ -411,9 +440,14 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
             }
           }
         }
-        const float rHx = l0 - (ry * dzr + sy * dzs);
-        const float rHy = l1 + (rx * dzr + sx * dzs);
-        const float rEz = l2 + (ca + cb);
+        float rHx = l0 - (ry * dzr + sy * dzs);
+        float rHy = l1 + (rx * dzr + sx * dzs);
+        float rEz = l2 + (ca + cb);
+        if (MEDIA) {
+          rHx *= sH;
+          rHy *= sH;
+          rEz *= sE;
+        }
         if (MODE == kModeRhs) {
           own[i] = rHx;
           own[FQ + i] = rHy;
@@ -507,22 +541,22 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
   }
 }
 
-template <int N, int MODE>
+template <int N, int MODE, bool MEDIA>
 cudaError_t launch_stage_ept_mode(const StageArgs<float>& args, const EptOps<N>& ops, int num_sms,
                                   cudaStream_t stream) {
-  using L = EptLayout<N>;
-  // per (N, MODE): shared-memory attribute and resident CTAs per SM, set on
-  // the first launch on each device
+  using L = EptLayout<N, MEDIA>;
+  // per (N, MODE, MEDIA): shared-memory attribute and resident CTAs per SM,
+  // set on the first launch on each device
   static std::atomic<uint64_t> configured{0};
   static std::atomic<int> blocks_per_sm{1};
   cudaError_t err = configure_once_per_device(configured, [] {
-    cudaError_t e = cudaFuncSetAttribute(dg_stage_ept_kernel<N, MODE>,
+    cudaError_t e = cudaFuncSetAttribute(dg_stage_ept_kernel<N, MODE, MEDIA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          L::SMEM_BYTES);
     int nb = 0;
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dg_stage_ept_kernel<N, MODE>, 32,
-                                                        L::SMEM_BYTES);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dg_stage_ept_kernel<N, MODE, MEDIA>,
+                                                        32, L::SMEM_BYTES);
     if (e == cudaSuccess) blocks_per_sm.store(nb > 0 ? nb : 1);
     return e;
   });
@@ -531,21 +565,34 @@ cudaError_t launch_stage_ept_mode(const StageArgs<float>& args, const EptOps<N>&
   int64_t grid = static_cast<int64_t>(blocks_per_sm.load()) * num_sms;
   if (grid > nblk) grid = nblk;
   if (grid < 1) grid = 1;
-  dg_stage_ept_kernel<N, MODE><<<static_cast<unsigned>(grid), 32, L::SMEM_BYTES, stream>>>(args, ops);
+  dg_stage_ept_kernel<N, MODE, MEDIA>
+      <<<static_cast<unsigned>(grid), 32, L::SMEM_BYTES, stream>>>(args, ops);
   return cudaGetLastError();
 }
 
-// Definition of the launcher declared in launch.h; explicitly instantiated
+template <int N, bool MEDIA>
+cudaError_t launch_stage_ept_any(const StageArgs<float>& args, const float* ops_host, int mode,
+                                 int num_sms, cudaStream_t stream) {
+  EptOps<N> ops;
+  std::memcpy(&ops, ops_host, sizeof(ops));
+  if (mode == kModeRhs)
+    return launch_stage_ept_mode<N, kModeRhs, MEDIA>(args, ops, num_sms, stream);
+  if (mode == kModeFirstStage)
+    return launch_stage_ept_mode<N, kModeFirstStage, MEDIA>(args, ops, num_sms, stream);
+  return launch_stage_ept_mode<N, kModeStage, MEDIA>(args, ops, num_sms, stream);
+}
+
+// Definitions of the launchers declared in launch.h; explicitly instantiated
 // per order in kernels_ept_N*.cu.
 template <int N>
 cudaError_t launch_stage_ept(const StageArgs<float>& args, const float* ops_host, int mode,
                              int num_sms, cudaStream_t stream) {
-  EptOps<N> ops;
-  std::memcpy(&ops, ops_host, sizeof(ops));
-  if (mode == kModeRhs) return launch_stage_ept_mode<N, kModeRhs>(args, ops, num_sms, stream);
-  if (mode == kModeFirstStage)
-    return launch_stage_ept_mode<N, kModeFirstStage>(args, ops, num_sms, stream);
-  return launch_stage_ept_mode<N, kModeStage>(args, ops, num_sms, stream);
+  return launch_stage_ept_any<N, false>(args, ops_host, mode, num_sms, stream);
+}
+template <int N>
+cudaError_t launch_stage_ept_media(const StageArgs<float>& args, const float* ops_host, int mode,
+                                   int num_sms, cudaStream_t stream) {
+  return launch_stage_ept_any<N, true>(args, ops_host, mode, num_sms, stream);
 }
 
 }  // namespace dgw

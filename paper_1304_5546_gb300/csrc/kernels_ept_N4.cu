@@ -1,7 +1,10 @@
-// Order-4 instantiation of the FP32 element-thread stage kernel.
+// Order-4 instantiations of the FP32 element-thread stage kernel (uniform
+// medium and per-element permittivity).
 #include "kernels_ept.cuh"
 
 namespace dgw {
 template cudaError_t launch_stage_ept<4>(const StageArgs<float>&, const float*, int, int,
                                         cudaStream_t);
+template cudaError_t launch_stage_ept_media<4>(const StageArgs<float>&, const float*, int, int,
+                                              cudaStream_t);
 }  // namespace dgw

@@ -210,7 +210,8 @@ cudaError_t launch_stage_tc(const StageArgs<float>& args, int mode, int num_sms,
                             cudaStream_t stream);
 
 // Element-thread path (FP32, CUDA cores, one thread per element; see
-// kernels_ept.cuh), orders 1..kEptMaxN, uniform medium.  Its reference
+// kernels_ept.cuh), orders 1..kEptMaxN; the _media launcher takes
+// per-element-permittivity records (kGeoMedia values).  Its reference
 // tables travel as a kernel parameter: `ops` points to host memory holding
 // ept_ops_floats(N) floats, [Dr (Np x Np, row-major) | Ds | LIFT (Np x
 // Nafp) | (1 + r_n) / 2 | (1 + s_n) / 2].
@@ -221,6 +222,9 @@ __host__ __device__ constexpr int ept_ops_floats(int N) {
 template <int N>
 cudaError_t launch_stage_ept(const StageArgs<float>& args, const float* ops, int mode,
                              int num_sms, cudaStream_t stream);
+template <int N>
+cudaError_t launch_stage_ept_media(const StageArgs<float>& args, const float* ops, int mode,
+                                   int num_sms, cudaStream_t stream);
 
 // Operators with a per-element permittivity (geometry records of kGeoMedia
 // values): CUDA-core kernel (FP32 / FP64) and tensor-core kernel (3xTF32).

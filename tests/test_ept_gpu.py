@@ -1,7 +1,7 @@
 """GPU parity of the element-thread stage kernel (DG_SETUP_ELEMENT_THREADS,
 precision "fp32ept": FP32 on the CUDA cores, one thread per element, the
-reference matrices as constant operands; N = 1..5, uniform medium) against
-the FP64 oracle on the same seeded inputs.
+reference matrices as constant operands; N = 1..5, uniform medium and
+per-element permittivity) against the FP64 oracle on the same seeded inputs.
 
 Each warp of that kernel walks blocks of 32 elements through its own ring
 of S = 2 stage buffers.  Besides small
@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from synth import gaussian_pulse, jittered_delaunay_mesh, random_fields
+from synth import gaussian_pulse, jittered_delaunay_mesh, random_fields, random_permittivity
 
 pytestmark = pytest.mark.gpu
 
@@ -40,11 +40,13 @@ def _rel(a, b):
 
 
 def _warps_bound(N, sms=152, smem_per_sm=233472, reserved=1024, max_ctas=32):
-    # one warp per CTA; its shared memory is S stage buffers of 32 elements:
-    # q and residual (6 Np values), 13 geometry values, 3 face codes
+    # one warp per CTA; its shared memory is S = 2 stage buffers of 32
+    # elements (q and residual: 6 Np values; 13 geometry values) and three
+    # blocks' face codes (3 each); more with media records or the operator
+    # table, which only lowers the bound
     Np = (N + 1) * (N + 2) // 2
     S = 2
-    smem = S * 128 * (6 * Np + 16)
+    smem = S * 128 * (6 * Np + 13) + 3 * 384
     return sms * min(max_ctas, smem_per_sm // (smem + reserved)), S
 
 
@@ -147,6 +149,72 @@ def test_same_result_as_node_thread_kernel_up_to_rounding(P):
     out = []
     for prec in ("fp32ept", "fp32simt"):
         s = P.Solver(*mesh, N=3, precision=prec)
+        out.append(s.to_numpy(s.rhs(s.from_numpy(q))))
+        s.close()
+    assert _rel(out[0], out[1]) <= 1e-6
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_media_rhs_and_steps_small(P, N):
+    # per-element permittivity: the flux of the exact interface Riemann
+    # solution and the 1/eps row scale of the Ez right-hand side
+    mesh = jittered_delaunay_mesh(9, seed=300 + N)
+    d = O.Discretization(*mesh, N)
+    eps = random_permittivity(d.K, seed=N)
+    q = random_fields(d.K, d.Np, seed=N + 7)
+    s = P.Solver(*mesh, N=N, precision="fp32ept", eps=eps)
+    assert s.kernel() == ("element threads", 32)
+    got = s.to_numpy(s.rhs(s.from_numpy(q)))
+    q0 = np.stack(gaussian_pulse(d.x, d.y, 0.5, 0.5, 0.15))
+    dt = s.cfl_dt()
+    qq = s.from_numpy(q0)
+    res = s.new_fields()
+    s.step(qq, res, dt, nsteps=3)
+    stepped = s.to_numpy(qq)
+    P.dg_sync_check(s.op)
+    s.close()
+    assert _rel(got, O.maxwell_rhs_media(d, q, eps)) <= TOL
+    want = q0
+    for n in range(3):
+        want = O.lsrk_step(d, want, n * dt, dt, rhs=lambda u, t: O.maxwell_rhs_media(d, u, eps))
+    assert _rel(stepped, want) <= TOL
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_media_large_rhs_and_two_steps(P, N):
+    mesh = jittered_delaunay_mesh(_n_for(N), seed=950 + N)
+    d = O.Discretization(*mesh, N)
+    eps = random_permittivity(d.K, seed=960 + N)
+    q0 = random_fields(d.K, d.Np, seed=N + 3).astype(np.float32).astype(np.float64)
+    s = P.Solver(*mesh, N=N, precision="fp32ept", eps=eps)
+    try:
+        dt = s.cfl_dt()
+        q = s.from_numpy(q0)
+        rhs = s.to_numpy(s.rhs(q))
+        res = s.new_fields()
+        s.step(q, res, dt, nsteps=2)
+        got = s.to_numpy(q)
+        P.dg_sync_check(s.op)
+    finally:
+        s.close()
+
+    def f(u, t):
+        return O.maxwell_rhs_media(d, u, eps)
+    assert _rel(rhs, f(q0, 0.0)) <= TOL, ("rhs", _rel(rhs, f(q0, 0.0)))
+    want = q0
+    for n in range(2):
+        want = O.lsrk_step(d, want, n * dt, dt, rhs=f)
+    assert _rel(got, want) <= TOL, ("2 steps", _rel(got, want))
+
+
+def test_media_same_result_as_node_thread_kernel_up_to_rounding(P):
+    mesh = jittered_delaunay_mesh(40, seed=19)
+    K = 2 * 40 * 40
+    eps = random_permittivity(K, seed=4)
+    q = random_fields(K, 6, seed=6)
+    out = []
+    for prec in ("fp32ept", "fp32simt"):
+        s = P.Solver(*mesh, N=2, precision=prec, eps=eps)
         out.append(s.to_numpy(s.rhs(s.from_numpy(q))))
         s.close()
     assert _rel(out[0], out[1]) <= 1e-6

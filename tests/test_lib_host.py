@@ -169,8 +169,8 @@ def test_error_codes(dgw):
 
 
 def test_element_thread_flag_checks(dgw):
-    # DG_SETUP_ELEMENT_THREADS: FP32, N <= 5, uniform medium, no other kernel
-    # or product flag; the kernel report of a host-only operator (no GPU work)
+    # DG_SETUP_ELEMENT_THREADS: FP32, N <= 5, no other kernel or product
+    # flag; the kernel report of a host-only operator (no GPU work)
     from paper_1304_5546_gb300 import _lib
     VX, VY, EToV = square_grid_mesh(3, 3)
     mesh = dgw.dg_mesh_create(VX, VY, EToV)
@@ -194,22 +194,28 @@ def test_element_thread_flag_checks(dgw):
             with pytest.raises(dgw.DGError) as ei:
                 dgw.dg_operator_setup(mesh, N, prec, flags | H)
             assert ei.value.status == _lib.DG_ERR_ARG, (N, prec, flags)
+        # a permittivity is allowed (the kernel's media variant)
+        op = dgw.dg_operator_setup_media(mesh, 3, np.ones(EToV.shape[0]), dgw.DG_FP32, E | H)
+        try:
+            assert dgw.dg_operator_kernel(op) == ("element threads", 32)
+        finally:
+            dgw.dg_op_destroy(op)
         with pytest.raises(dgw.DGError) as ei:
-            dgw.dg_operator_setup_media(mesh, 3, np.ones(EToV.shape[0]), dgw.DG_FP32, E | H)
+            dgw.dg_operator_setup_media(mesh, 6, np.ones(EToV.shape[0]), dgw.DG_FP32, E | H)
         assert ei.value.status == _lib.DG_ERR_ARG
     finally:
         dgw.dg_mesh_destroy(mesh)
 
 
 def test_default_fp32_kernel_per_order(dgw):
-    # element threads at N <= 2 in a uniform medium, tensor cores above; with
-    # a permittivity: node threads at N = 1, tensor cores from N = 2 on
+    # element threads at N <= 2, tensor cores above, with or without a
+    # permittivity
     VX, VY, EToV = square_grid_mesh(3, 3)
     mesh = dgw.dg_mesh_create(VX, VY, EToV)
     eps = np.full(EToV.shape[0], 2.0)
     try:
-        for N, want, want_media in ((1, "element threads", "cuda cores"),
-                                    (2, "element threads", "tensor cores"),
+        for N, want, want_media in ((1, "element threads", "element threads"),
+                                    (2, "element threads", "element threads"),
                                     (3, "tensor cores", "tensor cores"),
                                     (5, "tensor cores", "tensor cores")):
             for media, w in ((False, want), (True, want_media)):
