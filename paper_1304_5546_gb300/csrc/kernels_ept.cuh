@@ -20,7 +20,12 @@
 // loop unrolled each matrix entry is a compile-time offset into the
 // parameter (constant) bank, which an FMA takes as an operand directly: a
 // product term costs one FMA and no load, where the tensor-core kernel
-// spends most of its instructions building operand rows and hand-offs.
+// spends most of its instructions building operand rows and hand-offs.  At
+// N = 4, 5 the matrices outgrow the fast constant cache and the unrolled code
+// grows large; there they are read from a table in shared memory instead
+// (ept_table).  MEDIA: per-element-permittivity records (launch.h), the flux
+// of the exact interface Riemann solution and the row scales of the
+// right-hand side.
 //
 // Work decomposition.  A CTA is one warp (residency is then set warp by warp
 // by shared memory).  The warp walks blocks of 32 consecutive elements, block
@@ -31,13 +36,13 @@
 // values, residual and geometry into a ring of S = 2 stage buffers, the face
 // codes -- all the neighbour gather needs -- one block earlier still, into a
 // ring of three.  So the gather of block it + 1 is issued as block it starts
-// and has that whole block to land, and so do block it + 1's bulk copies.  A lane reads its element's values from the
-// stage buffer (a stride of Np words: conflict-free for odd Np, 8-byte loads
-// for even Np), gathers its neighbours' face-node traces from global memory
-// (L2) into registers one block ahead, writes its updated values back into
-// its own stage slots, and the warp stores the block with coalesced 16-byte
-// stores.  No wait spins on a flag: cp.async.wait_group returns when the
-// warp's own copies have landed.
+// and has that whole block to land, and so do block it + 1's bulk copies.
+// A lane reads its element's values from the stage buffer (a stride of Np
+// words: conflict-free for odd Np, 8-byte loads for even Np), gathers its
+// neighbours' face-node traces from global memory (L2) into registers, writes
+// its updated values back into its own stage slots, and the warp stores the
+// block's valid elements with coalesced 16-byte stores.  No wait spins on a
+// flag: cp.async.wait_group returns when the warp's own copies have landed.
 #pragma once
 
 #include <atomic>
@@ -103,6 +108,7 @@ struct EptLayout {
   static constexpr int TBL_OFF = CONN_OFF + CONN_BYTES;
   static constexpr int SMEM_BYTES = TBL_OFF + TBL_BYTES;
   static_assert(S == 2, "the pipeline below waits for one group per block");
+  static_assert(Np <= 32, "neighbour node numbers are packed in 5 bits (ept_nbr_nodes)");
   static_assert(QB % 16 == 0 && GB % 16 == 0 && CB % 16 == 0, "16-byte copies");
   static_assert(sizeof(EptOps<N>) == 4 * ept_ops_floats(N), "parameter layout");
 };
