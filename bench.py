@@ -560,18 +560,24 @@ def run_sweep_study(args):
     and, at N <= 5, the element-thread kernel (median of three runs),
     `--study-steps` LSRK steps each timed with CUDA events (the two
     tensor-core settings alternate three times on one operator; medians).
-    One JSON line: ms/step, element-stage updates/s, RHS GFLOP/s and
-    achieved HBM bandwidth (algorithmic bytes) per order and kernel, and the
-    share of interior faces whose two elements lie in one tensor-core block."""
+    With --sweep-media every operator has a seeded per-element permittivity
+    (wave speeds drawn from {0.5, 1, 2}) and the algorithmic bytes are those
+    of its 20-value records (media_step_bytes_per_element).  One JSON line: ms/step, element-stage updates/s, RHS
+    GFLOP/s and achieved HBM bandwidth (algorithmic bytes) per order and
+    kernel, and the share of interior faces whose two elements lie in one
+    tensor-core block."""
     import numpy as np
     import torch
 
     import paper_1304_5546_gb300 as P
     from synth import gaussian_pulse, jittered_delaunay_mesh, n_for_target_elements
+    from synth import random_permittivity
 
     torch.cuda.set_device(0)
     peaks, peak_kind = measured_peaks()
     steps = args.study_steps
+    media = args.sweep_media
+    sweep_bytes = media_step_bytes_per_element if media else step_bytes_per_element
     rows = []
 
     def timed(s, q, res, dt):
@@ -585,7 +591,7 @@ def run_sweep_study(args):
         return a.elapsed_time(b) / steps
 
     def row(N, K, kernel, ms, **extra):
-        gbs = K * step_bytes_per_element(N) / (ms / 1e3) / 1e9
+        gbs = K * sweep_bytes(N) / (ms / 1e3) / 1e9
         r = {"N": N, "K": K, "kernel": kernel, "ms_per_step": ms,
              "element_stage_per_s": K * 5 / (ms / 1e3),
              "rhs_gflops": K * rhs_flops_per_element(N) * 5 / (ms / 1e3) / 1e9,
@@ -597,9 +603,10 @@ def run_sweep_study(args):
         Np = (N + 1) * (N + 2) // 2
         n = n_for_target_elements(1e7 / Np)
         mesh = jittered_delaunay_mesh(n, seed=2024)
+        eps = random_permittivity(mesh[2].shape[0], seed=5) if media else None
         kinds = ("fp32tc", "fp32simt") + (("fp32ept",) if N <= 5 else ())
         for kind in kinds:
-            s = P.Solver(*mesh, N=N, precision=kind)
+            s = P.Solver(*mesh, N=N, precision=kind, eps=eps)
             x, y = s.nodes()
             q = s.from_numpy(np.stack(gaussian_pulse(x, y)))
             res = s.new_fields()
@@ -628,8 +635,9 @@ def run_sweep_study(args):
                                 float(np.median(times[1])), faces_in_block=share))
             s.close()
     return {"study": "order sweep", "nodal_values_per_field": "~1e7", "steps": steps,
+            "media": "per-element permittivity, seed 5" if media else None,
             "peak_hbm_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind,
-            "bytes_per_element_step": {str(N): step_bytes_per_element(N) for N in range(1, 8)},
+            "bytes_per_element_step": {str(N): sweep_bytes(N) for N in range(1, 8)},
             "rows": rows}
 
 
@@ -1251,6 +1259,8 @@ def main(argv=None):
     ap.add_argument("--longrun-quick", action="store_true",
                     help="--study longrun on small meshes and few steps")
     ap.add_argument("--sweep-orders", type=int, nargs="+", default=list(range(1, 8)))
+    ap.add_argument("--sweep-media", action="store_true",
+                    help="--study sweep with a seeded per-element permittivity")
     ap.add_argument("--partition-parts", type=int, nargs="+", default=[1, 2, 4, 8])
     ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
                     help="single: the large-mesh benchmark line (default); batched: many "
