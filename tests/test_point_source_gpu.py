@@ -60,7 +60,8 @@ def _oracle_rhs(d, eps, src):
 
 @pytest.mark.parametrize("N,prec,media", [(3, "fp32", False), (5, "fp32simt", False),
                                           (4, "fp64", False), (5, "fp32", True),
-                                          (1, "fp32", False), (7, "fp32", False)])
+                                          (1, "fp32", False), (7, "fp32", False),
+                                          (2, "fp32", True)])
 def test_steps_with_source_match_oracle(P, N, prec, media):
     s, d, eps, dt, src, q0 = _setup(P, N, prec, media=media)
     rhs = _oracle_rhs(d, eps, src)
