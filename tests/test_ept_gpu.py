@@ -218,3 +218,23 @@ def test_media_same_result_as_node_thread_kernel_up_to_rounding(P):
         out.append(s.to_numpy(s.rhs(s.from_numpy(q))))
         s.close()
     assert _rel(out[0], out[1]) <= 1e-6
+
+
+def test_tiny_meshes(P):
+    # K = 1 (all faces PEC), 2 and 3: one partly filled block, every order
+    from synth import square_grid_mesh
+    meshes = [
+        (np.array([0.0, 1.0, 0.2]), np.array([0.0, 0.1, 0.9]), np.array([[0, 1, 2]])),
+        square_grid_mesh(1, 1),
+        (np.array([0.0, 1.0, 0.0, 1.0, 2.0]), np.array([0.0, 0.0, 1.0, 1.0, 0.5]),
+         np.array([[0, 1, 3], [0, 3, 2], [1, 4, 3]])),
+    ]
+    for mesh in meshes:
+        for N in ORDERS:
+            d = O.Discretization(*mesh, N)
+            q = random_fields(d.K, d.Np, seed=N)
+            s = P.Solver(*mesh, N=N, precision="fp32ept")
+            got = s.to_numpy(s.rhs(s.from_numpy(q)))
+            P.dg_sync_check(s.op)
+            s.close()
+            assert _rel(got, O.maxwell_rhs(d, q)) <= TOL, (d.K, N)
