@@ -33,10 +33,12 @@
 // block owns is contiguous in HBM (its q and residual values per field, its
 // geometry records and face codes) and is fetched by the warp's lanes with
 // 16-byte cp.async copies, one commit group per block, one block ahead: the
-// values, residual and geometry into a ring of S = 2 stage buffers, the face
-// codes -- all the neighbour gather needs -- one block earlier still, into a
-// ring of three.  So the gather of block it + 1 is issued as block it starts
-// and has that whole block to land, and so do block it + 1's bulk copies.
+// values, residual and geometry into a ring of S = 2 stage buffers (from
+// N = 2 on the residual into one buffer of its own, fetched as its block
+// starts: ept_res_single), the face codes -- all the neighbour gather needs
+// -- one block earlier still, into a ring of three.  So the gather of block
+// it + 1 is issued as block it starts and has that whole block to land, and
+// so do block it + 1's bulk copies.
 // A lane reads its element's values from the stage buffer (a stride of Np
 // words: conflict-free for odd Np, 8-byte loads for even Np), gathers its
 // neighbours' face-node traces from global memory (L2) into registers, writes
@@ -78,6 +80,27 @@ __host__ __device__ constexpr int ept_stages(int) { return 2; }
 // the code and the constant working set small at the higher orders.
 __host__ __device__ constexpr bool ept_table(int N) { return N >= 4; }
 
+// Register and shared-memory economies, per order (each measured A/B on
+// GB300, order-sweep meshes, ms per step):
+//   ept_prefetch  -- the neighbour traces of the next block are gathered
+//                    while this block computes (true), or this block's own
+//                    at its start, used after the deflation (false: the
+//                    traces are live only until the flux; 80 instead of 128
+//                    registers at N = 2, but slower: N = 2 0.703 vs 0.503,
+//                    N = 3 0.791 vs 0.615 with a single residual buffer);
+//   ept_reread    -- the update reads the element's values back from its
+//                    stage slots instead of keeping them in registers (with
+//                    the traces not prefetched: N = 2 0.681, N = 3 0.725);
+//   ept_res_single -- one residual buffer per warp instead of one per stage
+//                    buffer, fetched as its block starts and waited for just
+//                    before the update: less shared memory a warp, and the
+//                    residual no longer gates the block's start (N = 2 0.503
+//                    vs 0.639, N = 3 0.615 vs 0.645, N = 5 1.102 vs 1.131,
+//                    N = 4 even; N = 1 0.705 vs 0.675, so not there).
+__host__ __device__ constexpr bool ept_prefetch(int) { return true; }
+__host__ __device__ constexpr bool ept_reread(int) { return false; }
+__host__ __device__ constexpr bool ept_res_single(int N) { return N >= 2; }
+
 // c-th node of an element that is not a vertex node (0, N, Np - 1): the
 // deflated operands are zero at the vertex nodes
 __host__ __device__ constexpr int ept_interior_node(int N, int c) {
@@ -90,15 +113,22 @@ struct EptLayout {
   static constexpr int E = 32;             // elements per block: one per lane
   static constexpr int S = ept_stages(N);  // stage buffers of the warp's ring
   static constexpr int FQ = E * Np;        // floats of one field of a block
-  // stage buffer: q[3][E Np], res[3][E Np], geo[E][GEO] (MEDIA: the
-  // per-element-permittivity records, launch.h)
+  // geometry record length (MEDIA: the per-element-permittivity records,
+  // launch.h)
   static constexpr int GEO = MEDIA ? kGeoMedia : kGeo;
   static constexpr int QB = FQ * 4;
   static constexpr int GB = E * GEO * 4;
   static constexpr int CB = E * 3 * 4;
-  static constexpr int STAGE_BYTES = 6 * QB + GB;
+  static constexpr bool PREFETCH = ept_prefetch(N), REREAD = ept_reread(N);
+  static constexpr bool RES1 = ept_res_single(N);
+  // stage buffer: q[3][E Np], then (unless RES1) res[3][E Np], then
+  // geo[E][GEO]
+  static constexpr int GEO_OFF = (RES1 ? 3 : 6) * FQ;  // floats
+  static constexpr int STAGE_BYTES = GEO_OFF * 4 + GB;
+  // RES1: the warp's single residual buffer [3][E Np]
+  static constexpr int RES_OFF = S * STAGE_BYTES;
   // face codes: a ring of three blocks' codes, one block ahead of the stages
-  static constexpr int CONN_OFF = S * STAGE_BYTES, CONN_BYTES = 3 * CB;
+  static constexpr int CONN_OFF = RES_OFF + (RES1 ? 3 * QB : 0), CONN_BYTES = 3 * CB;
   // operator table (ept_table): row width RS floats, Dr and Ds parts DW
   // wide (Np - 3 interior nodes, padded to 4), LIFT part LW wide
   static constexpr bool TBL = ept_table(N);
@@ -209,13 +239,20 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
 #pragma unroll
     for (int f = 0; f < 3; ++f)
       ept_fetch<L::QB / 16>(st + f * FQ, p.qin + f * p.fstride + k0 * Np, lane);
-    if (MODE == kModeStage) {
+    if (MODE == kModeStage && !L::RES1) {
 #pragma unroll
       for (int f = 0; f < 3; ++f)
         ept_fetch<L::QB / 16>(st + (3 + f) * FQ, p.res + f * p.fstride + k0 * Np, lane);
     }
-    ept_fetch<L::GB / 16>(st + 6 * FQ, p.geo + k0 * GEO, lane);
+    ept_fetch<L::GB / 16>(st + L::GEO_OFF, p.geo + k0 * GEO, lane);
     if (it + 1 < niter) fetch_codes(it + 1);
+  };
+  float* resbuf = reinterpret_cast<float*>(smem + L::RES_OFF);  // RES1
+  auto fetch_res = [&](int it) {
+    const int64_t k0 = static_cast<int64_t>(b0 + it * G) * 32;
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+      ept_fetch<L::QB / 16>(resbuf + f * FQ, p.res + f * p.fstride + k0 * Np, lane);
   };
 
   // neighbour traces (Hx, Hy, Ez) of this lane's element at its Nafp face
@@ -273,19 +310,29 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
   cp_async_commit();
   cp_async_wait<0>();
   __syncwarp();
-  gather(0);
+  if (L::PREFETCH) gather(0);
 
   for (int it = 0; it < niter; ++it) {
+    // RES1: this block's residual into the buffer the previous block
+    // released (its own group, waited for before the update)
+    if (L::RES1) {
+      if (MODE == kModeStage) fetch_res(it);
+      cp_async_commit();
+    }
     // refill the stage the previous block released; then block it has
     // landed (its group was committed one block ago), and so have the codes
     // of block it + 1
     if (it + 1 < niter) issue(it + 1);
     cp_async_commit();
-    cp_async_wait<1>();
+    if (L::RES1)
+      cp_async_wait<2>();
+    else
+      cp_async_wait<1>();
     __syncwarp();
+    if (!L::PREFETCH) gather(it);
 
     float* sq = stage(it);
-    const float* sg = sq + 6 * FQ;
+    const float* sg = sq + L::GEO_OFF;
     const int* sc = codes(it);
     const int k0 = (b0 + it * G) * 32;
     float* own = sq + lane * Np;  // this lane's slot in field 0 (fields FQ apart)
@@ -298,6 +345,33 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
     const float rx = ge[0], ry = ge[1], sx = ge[2], sy = ge[3];
     // row scales of the right-hand side (media records; 1 otherwise)
     const float sH = MEDIA ? ge[17] : 1.f, sE = MEDIA ? ge[18] : 1.f;
+
+    // ---- volume operands minus their linear part (exactly zero at the
+    // vertex nodes 0, N, Np - 1), and the linear part's derivatives
+    float zd[Np], A[Np], B[Np];
+    float lin0, lin1, lin2;
+    auto deflate = [&]() {
+      const float x1 = hx[0], x2 = hx[N], x3 = hx[Np - 1];
+      const float y1 = hy[0], y2 = hy[N], y3 = hy[Np - 1];
+      const float z1 = ez[0], z2 = ez[N], z3 = ez[Np - 1];
+#pragma unroll
+      for (int j = 0; j < Np; ++j) {
+        if (j == 0 || j == N || j == Np - 1) {
+          zd[j] = A[j] = B[j] = 0.f;
+        } else {
+          const float dhx = (hx[j] - x1) - ((x2 - x1) * ops.l2[j] + (x3 - x1) * ops.l3[j]);
+          const float dhy = (hy[j] - y1) - ((y2 - y1) * ops.l2[j] + (y3 - y1) * ops.l3[j]);
+          zd[j] = (ez[j] - z1) - ((z2 - z1) * ops.l2[j] + (z3 - z1) * ops.l3[j]);
+          A[j] = rx * dhy - ry * dhx;
+          B[j] = sx * dhy - sy * dhx;
+        }
+      }
+      const float grz = 0.5f * (z2 - z1), gsz = 0.5f * (z3 - z1);
+      lin0 = -(ry * grz + sy * gsz);
+      lin1 = rx * grz + sx * gsz;
+      lin2 = 0.5f * (rx * (y2 - y1) - ry * (x2 - x1) + sx * (y3 - y1) - sy * (x3 - x1));
+    };
+    if (!L::PREFETCH) deflate();
 
     // ---- upwind flux (Eq. max2d-numflux) times Fscale/2 at every face node
     float F0[Nafp], F1[Nafp], F2[Nafp];
@@ -341,30 +415,17 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
 
     // ---- the next block's neighbour traces (their L2 latency hides behind
     // this block's products and stores)
-    if (it + 1 < niter) gather(it + 1);
-
-    // ---- volume operands minus their linear part (exactly zero at the
-    // vertex nodes 0, N, Np - 1), and the linear part's derivatives
-    const float x1 = hx[0], x2 = hx[N], x3 = hx[Np - 1];
-    const float y1 = hy[0], y2 = hy[N], y3 = hy[Np - 1];
-    const float z1 = ez[0], z2 = ez[N], z3 = ez[Np - 1];
-    float zd[Np], A[Np], B[Np];
-#pragma unroll
-    for (int j = 0; j < Np; ++j) {
-      if (j == 0 || j == N || j == Np - 1) {
-        zd[j] = A[j] = B[j] = 0.f;
-      } else {
-        const float dhx = (hx[j] - x1) - ((x2 - x1) * ops.l2[j] + (x3 - x1) * ops.l3[j]);
-        const float dhy = (hy[j] - y1) - ((y2 - y1) * ops.l2[j] + (y3 - y1) * ops.l3[j]);
-        zd[j] = (ez[j] - z1) - ((z2 - z1) * ops.l2[j] + (z3 - z1) * ops.l3[j]);
-        A[j] = rx * dhy - ry * dhx;
-        B[j] = sx * dhy - sy * dhx;
-      }
+    if (L::PREFETCH) {
+      if (it + 1 < niter) gather(it + 1);
+      deflate();
     }
-    const float grz = 0.5f * (z2 - z1), gsz = 0.5f * (z3 - z1);
-    const float lin0 = -(ry * grz + sy * gsz);
-    const float lin1 = rx * grz + sx * gsz;
-    const float lin2 = 0.5f * (rx * (y2 - y1) - ry * (x2 - x1) + sx * (y3 - y1) - sy * (x3 - x1));
+    // RES1: the residual of this block has landed
+    if (L::RES1 && MODE == kModeStage) {
+      cp_async_wait<1>();
+      __syncwarp();
+    }
+    float* rown = L::RES1 ? resbuf + lane * Np : own + 3 * FQ;  // residual slot, field 0
+
 
     // right-hand side at node i: volume products, chain rule, lift
     auto rhs_at = [&](int i, float& rHx, float& rHy, float& rEz) {
@@ -406,9 +467,9 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
         n1 = fmaf(p.a, r1, p.dt * rHy);
         n2 = fmaf(p.a, r2, p.dt * rEz);
       }
-      o0 = fmaf(p.b, n0, hx[i]);
-      o1 = fmaf(p.b, n1, hy[i]);
-      o2 = fmaf(p.b, n2, ez[i]);
+      o0 = fmaf(p.b, n0, L::REREAD ? own[i] : hx[i]);
+      o1 = fmaf(p.b, n1, L::REREAD ? own[FQ + i] : hy[i]);
+      o2 = fmaf(p.b, n2, L::REREAD ? own[2 * FQ + i] : ez[i]);
     };
     if constexpr (L::TBL) {
       // one output node per trip; own values re-read from the stage slots
@@ -461,16 +522,16 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
         } else {
           float n0 = p.dt * rHx, n1 = p.dt * rHy, n2 = p.dt * rEz;
           if (MODE == kModeStage) {
-            n0 = fmaf(p.a, own[3 * FQ + i], n0);
-            n1 = fmaf(p.a, own[4 * FQ + i], n1);
-            n2 = fmaf(p.a, own[5 * FQ + i], n2);
+            n0 = fmaf(p.a, rown[i], n0);
+            n1 = fmaf(p.a, rown[FQ + i], n1);
+            n2 = fmaf(p.a, rown[2 * FQ + i], n2);
           }
           own[i] = fmaf(p.b, n0, own[i]);
           own[FQ + i] = fmaf(p.b, n1, own[FQ + i]);
           own[2 * FQ + i] = fmaf(p.b, n2, own[2 * FQ + i]);
-          own[3 * FQ + i] = n0;
-          own[4 * FQ + i] = n1;
-          own[5 * FQ + i] = n2;
+          rown[i] = n0;
+          rown[FQ + i] = n1;
+          rown[2 * FQ + i] = n2;
         }
       }
     } else if constexpr (Np % 2 == 0) {
@@ -486,9 +547,9 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
         } else {
           float2 r0 = make_float2(0.f, 0.f), r1 = r0, r2 = r0;
           if (MODE == kModeStage) {
-            r0 = *reinterpret_cast<const float2*>(own + 3 * FQ + i);
-            r1 = *reinterpret_cast<const float2*>(own + 4 * FQ + i);
-            r2 = *reinterpret_cast<const float2*>(own + 5 * FQ + i);
+            r0 = *reinterpret_cast<const float2*>(rown + i);
+            r1 = *reinterpret_cast<const float2*>(rown + FQ + i);
+            r2 = *reinterpret_cast<const float2*>(rown + 2 * FQ + i);
           }
           float oa0, oa1, oa2, na0, na1, na2, ob0, ob1, ob2, nb0, nb1, nb2;
           update(i, a0, a1, a2, oa0, oa1, oa2, na0, na1, na2, r0.x, r1.x, r2.x);
@@ -496,9 +557,9 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
           *reinterpret_cast<float2*>(own + i) = make_float2(oa0, ob0);
           *reinterpret_cast<float2*>(own + FQ + i) = make_float2(oa1, ob1);
           *reinterpret_cast<float2*>(own + 2 * FQ + i) = make_float2(oa2, ob2);
-          *reinterpret_cast<float2*>(own + 3 * FQ + i) = make_float2(na0, nb0);
-          *reinterpret_cast<float2*>(own + 4 * FQ + i) = make_float2(na1, nb1);
-          *reinterpret_cast<float2*>(own + 5 * FQ + i) = make_float2(na2, nb2);
+          *reinterpret_cast<float2*>(rown + i) = make_float2(na0, nb0);
+          *reinterpret_cast<float2*>(rown + FQ + i) = make_float2(na1, nb1);
+          *reinterpret_cast<float2*>(rown + 2 * FQ + i) = make_float2(na2, nb2);
         }
       }
     } else {
@@ -513,18 +574,18 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
         } else {
           float r0 = 0.f, r1 = 0.f, r2 = 0.f;
           if (MODE == kModeStage) {
-            r0 = own[3 * FQ + i];
-            r1 = own[4 * FQ + i];
-            r2 = own[5 * FQ + i];
+            r0 = rown[i];
+            r1 = rown[FQ + i];
+            r2 = rown[2 * FQ + i];
           }
           float o0, o1, o2, n0, n1, n2;
           update(i, a0, a1, a2, o0, o1, o2, n0, n1, n2, r0, r1, r2);
           own[i] = o0;
           own[FQ + i] = o1;
           own[2 * FQ + i] = o2;
-          own[3 * FQ + i] = n0;
-          own[4 * FQ + i] = n1;
-          own[5 * FQ + i] = n2;
+          rown[i] = n0;
+          rown[FQ + i] = n1;
+          rown[2 * FQ + i] = n2;
         }
       }
     }
@@ -540,7 +601,8 @@ __global__ void __launch_bounds__(32) dg_stage_ept_kernel(const StageArgs<float>
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
         ept_store<Np>(p.qout + f * p.fstride + g0, sq + f * FQ, n, lane);
-        ept_store<Np>(p.res + f * p.fstride + g0, sq + (3 + f) * FQ, n, lane);
+        ept_store<Np>(p.res + f * p.fstride + g0,
+                      (L::RES1 ? resbuf : sq + 3 * FQ) + f * FQ, n, lane);
       }
     }
     __syncwarp();  // the stage is free for the next refill

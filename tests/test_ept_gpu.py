@@ -4,7 +4,8 @@ reference matrices as constant operands; N = 1..5, uniform medium and
 per-element permittivity) against the FP64 oracle on the same seeded inputs.
 
 Each warp of that kernel walks blocks of 32 elements through its own ring
-of S = 2 stage buffers.  Besides small
+of S = 2 stage buffers (from N = 2 on with one residual buffer beside
+them).  Besides small
 meshes, every order runs on a mesh large enough that each warp of the
 launch handles at least S + 2 blocks, so the ring wraps, the one-block-ahead
 neighbour gather crosses blocks many times, and the last block is ragged.
@@ -41,12 +42,14 @@ def _rel(a, b):
 
 def _warps_bound(N, sms=152, smem_per_sm=233472, reserved=1024, max_ctas=32):
     # one warp per CTA; its shared memory is S = 2 stage buffers of 32
-    # elements (q and residual: 6 Np values; 13 geometry values) and three
-    # blocks' face codes (3 each); more with media records or the operator
-    # table, which only lowers the bound
+    # elements (q: 3 Np values, 13 geometry values), the residual (3 Np
+    # values: in each stage buffer at N = 1, in one buffer of its own above)
+    # and three blocks' face codes (3 each); more with media records or the
+    # operator table, which only lowers the bound
     Np = (N + 1) * (N + 2) // 2
     S = 2
-    smem = S * 128 * (6 * Np + 13) + 3 * 384
+    res = S if N == 1 else 1
+    smem = S * 128 * (3 * Np + 13) + res * 128 * 3 * Np + 3 * 384
     return sms * min(max_ctas, smem_per_sm // (smem + reserved)), S
 
 
