@@ -542,9 +542,9 @@ dg_status operator_setup(const dg_mesh* mesh, int32_t N, const double* eps, int3
     op->flags = flags;
     // FP32 default: the element-thread kernel at N <= 2, the tensor cores
     // above (order sweep at ~1e7 nodal values per field, ms/step, element
-    // threads / node threads / tensor cores: N = 1 0.68, 0.87, 1.40; N = 2
-    // 0.64, 0.98, 0.83; N = 3 0.64, 0.90, 0.60; with a permittivity: N = 1
-    // 0.70, 0.86, 1.37; N = 2 0.70, -, 0.82; N = 3 0.64, -, 0.61)
+    // threads / node threads / tensor cores: N = 1 0.68, 0.87, 1.39; N = 2
+    // 0.50, 0.98, 0.83; N = 3 0.62, 0.90, 0.60; with a permittivity: N = 1
+    // 0.70, 0.86, 1.37; N = 2 0.64, 0.95, 0.82; N = 3 0.64, 0.89, 0.61)
     op->use_tc = (precision == DG_FP32) && !(flags & DG_SETUP_SIMT) &&
                  (N >= 2 || variants != 0 || (flags & DG_SETUP_TC));
     const int32_t chosen = DG_SETUP_SIMT | DG_SETUP_TC | DG_SETUP_TC_TF32 | DG_SETUP_TC_BF16 |
