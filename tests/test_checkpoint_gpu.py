@@ -26,10 +26,11 @@ def P():
     return P
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_resume_is_bitwise(P, tmp_path, prec):
+@pytest.mark.parametrize("prec,N", [("fp32", 5), ("fp64", 5), ("fp32", 2)])
+def test_resume_is_bitwise(P, tmp_path, prec, N):
+    # N = 2 in FP32 runs the element-thread kernel
     mesh = jittered_delaunay_mesh(9, seed=31)
-    a = P.Solver(*mesh, N=5, precision=prec)
+    a = P.Solver(*mesh, N=N, precision=prec)
     x, y = a.nodes()
     q0 = np.stack(gaussian_pulse(x, y, 0.5, 0.5, 0.15))
     dt = a.cfl_dt()
@@ -42,7 +43,7 @@ def test_resume_is_bitwise(P, tmp_path, prec):
     path = tmp_path / "resume.ckpt"
     a.save(q, path, t=3 * dt, step=3)
     a.close()
-    b = P.Solver(*mesh, N=5, precision=prec)
+    b = P.Solver(*mesh, N=N, precision=prec)
     q2 = b.new_fields()
     t, step = b.load(path, q2)
     assert step == 3 and t == 3 * dt

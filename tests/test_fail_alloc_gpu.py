@@ -62,6 +62,8 @@ def test_operator_setup(P):
         for prec, flags in ((P.DG_FP32, 0), (P.DG_FP64, 0), (P.DG_FP32, 2)):  # 2: CUDA cores
             n = _sweep(P, lambda: P.dg_operator_setup(mesh, 5, prec, flags), P.dg_op_destroy)
             assert n >= 8
+        # N = 2: the element-thread kernel's operator (default FP32 at that order)
+        _sweep(P, lambda: P.dg_operator_setup(mesh, 2, P.DG_FP32, 0), P.dg_op_destroy)
         eps = random_permittivity(EToV.shape[0], seed=2)
         _sweep(P, lambda: P.dg_operator_setup_media(mesh, 4, eps, P.DG_FP32, 0), P.dg_op_destroy)
     finally:

@@ -26,7 +26,8 @@ def _host(s, q3):
     return s.from_numpy(q3).cpu().pin_memory()
 
 
-@pytest.mark.parametrize("precision,N,nsteps", [("fp32", 5, 1), ("fp32", 3, 2), ("fp64", 4, 1)])
+@pytest.mark.parametrize("precision,N,nsteps", [("fp32", 5, 1), ("fp32", 3, 2), ("fp64", 4, 1),
+                                                ("fp32", 2, 2)])  # N = 2: element threads
 def test_jobs_equal_step_host(P, precision, N, nsteps):
     import torch
     s = P.Solver(*jittered_delaunay_mesh(24, seed=5), N=N, precision=precision)
